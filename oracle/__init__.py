@@ -1,0 +1,113 @@
+"""FP64 CPU oracle for the NNVISR frame-group enhancement path.
+
+TEST INFRASTRUCTURE -- NOT PART OF THE PRODUCT.  Only ``tests/``, the package's
+``__graft_entry__.smoke()`` check and ``bench.py``'s CPU-baseline / reference
+leg may import, call, link or run anything under ``oracle/``.  The CUDA path
+never routes through it and shares no code with it (the two only read the same
+seeded inputs from ``synth``).
+
+What it computes (plain definitions, FP64):
+
+* ingest: integer planes -> range normalise -> chroma upsample -> BT.709
+  Y'CbCr->R'G'B' (``colour.py``);
+* grouping: scenes from per-frame cut flags, sliding-window tuples, group-model
+  runs, the Figure 1 frame-store layout (``grouping.py``, Section 3.3);
+* network: direct convolution, LeakyReLU, residual add, PixelShuffle, skip,
+  modulated deformable convolution (``net.py`` + ``oracle_conv.c``,
+  Section 3.1);
+* requantise: R'G'B'->Y'CbCr, chroma downsample, range scale, round half to
+  even, clamp (``colour.py``);
+* ``run_filter``: the whole filter over a clip, outputs in presentation order.
+
+Pins (tests marked "not gpu"): textbook BT.709 colour-bar codes, closed-form
+range values, library routines (torch conv2d / pixel_shuffle / interpolate,
+scipy correlate), brute force on tiny inputs, the invariants of the method
+(zero residual + nearest skip reproduces the input, no leak across a cut,
+8-bit round trip within 1 LSB), and the Figure 1 layout as printed.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .colour import (KB, KG, KR, downsample_chroma, ingest, normalise_chroma,
+                     normalise_luma, quantise, requantise, rgb_to_ycbcr,
+                     scale_chroma, scale_luma, upsample_chroma, ycbcr_to_rgb)
+from .grouping import (fig1_layout, fig1_next_batch_copy, fig1_slot_frames,
+                       group_output_count, group_runs, scene_of,
+                       scenes_from_flags, tuple_indices, tuple_map)
+from .net import (Net, conv2d_direct, conv2d_im2col, dcn2d, leaky_relu,
+                  oracle_threads, pixel_shuffle, sigmoid, upsample_bilinear,
+                  upsample_nearest)
+
+__all__ = [
+    "KB", "KG", "KR", "Net", "conv2d_direct", "conv2d_im2col", "dcn2d",
+    "downsample_chroma", "fig1_layout", "fig1_next_batch_copy", "fig1_slot_frames",
+    "group_output_count", "group_runs", "ingest", "leaky_relu", "normalise_chroma",
+    "normalise_luma", "oracle_threads", "pad_to_align", "pixel_shuffle", "quantise",
+    "requantise", "rgb_to_ycbcr", "run_filter", "scale_chroma", "scale_luma",
+    "scene_of", "scenes_from_flags", "sigmoid", "tuple_indices", "tuple_map",
+    "upsample_bilinear", "upsample_chroma", "upsample_nearest", "ycbcr_to_rgb",
+]
+
+
+def pad_to_align(rgb, align: int):
+    """Edge-replicate a [3][H][W] frame up to multiples of ``align`` (network stride)."""
+    _, h, w = rgb.shape
+    ph = (-h) % align
+    pw = (-w) % align
+    if ph == 0 and pw == 0:
+        return rgb
+    return np.pad(rgb, ((0, 0), (0, ph), (0, pw)), mode="edge")
+
+
+def run_filter(frames, flags, net_text, blob, in_fmt, out_fmt, outputs=None, keep_float=False):
+    """Run the whole filter over a clip.
+
+    frames: list of {"Y","U","V"} integer planes; flags: per-frame scene-start
+    flags; in_fmt/out_fmt: dicts (bit_depth, subsampling, range, chroma_loc).
+    outputs: optional iterable of output indices to compute (others skipped).
+    Returns a list (presentation order) of output planes, or of float RGB
+    images when keep_float is set; skipped outputs are None.
+    """
+    net = Net(net_text, blob)
+    nframes = len(frames)
+    scenes = scenes_from_flags(flags, nframes)
+    cache = {}
+
+    def rgb(i):
+        if i not in cache:
+            cache[i] = pad_to_align(ingest(frames[i], in_fmt), net.align)
+        return cache[i]
+
+    h, w = frames[0]["Y"].shape
+    oh, ow = h * net.scale, w * net.scale
+    want = None if outputs is None else set(outputs)
+    results = []
+
+    def emit(img):
+        img = img[:, :oh, :ow]
+        results.append(img if keep_float else requantise(img, out_fmt))
+
+    if net.family == "tuple":
+        for t in range(nframes):
+            if want is not None and t not in want:
+                results.append(None)
+                continue
+            idx = tuple_indices(t, net.frames, *scene_of(t, scenes))
+            emit(net.forward([rgb(i) for i in idx])[0])
+    else:
+        interp = "interp" in net.flags
+        extra = "extra" in net.flags
+        double = "double" in net.flags
+        n = net.frames - (1 if extra else 0)
+        per_run = group_output_count(n, interp, double)
+        for s0, s1 in scenes:
+            for inputs, skip in group_runs(s0, s1, n, extra, interp):
+                base = len(results)
+                if want is not None and not any(base + k in want for k in range(per_run)):
+                    results.extend([None] * (per_run - skip))
+                    continue
+                outs = net.forward([rgb(i) for i in inputs])
+                for img in outs[skip:per_run]:
+                    emit(img)
+    return results

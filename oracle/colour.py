@@ -1,0 +1,189 @@
+"""Oracle, format side: range normalisation, BT.709 matrix, chroma resampling, requantisation.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  FP64 numpy, written as
+the plain per-sample definitions.
+
+The paper lets a network take and emit RGB or YUV and loads a network per
+colour space (Section 3.1, "Network Integration": RGB/YUV I/O, YUV420 halves
+two of the three channels' dimensions, colour-space-aware loading).  It fixes
+none of the numeric conventions, so these follow ITU-T H.273 / BT.709 as read
+in the design notes:
+
+* range (limited): Y' = (Y - 16*2^(b-8)) / (219*2^(b-8)),
+                   C' = (C - 128*2^(b-8)) / (224*2^(b-8));
+  range (full):    Y' = Y / (2^b - 1),  C' = (C - 2^(b-1)) / (2^b - 1).
+* BT.709: Kr = 0.2126, Kb = 0.0722, Kg = 1 - Kr - Kb.
+* chroma siting: LEFT (H.273 type 0: co-sited horizontally, centred between
+  rows vertically), CENTER (centred both ways), POINT (replicate; a test mode).
+  Edges clamp to the nearest sample.
+* requantisation: round half to even, clamp to the code range [0, 2^b - 1].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+KR = 0.2126
+KB = 0.0722
+KG = 1.0 - KR - KB
+
+
+# ---------------------------------------------------------------- range (C1)
+
+def normalise_luma(y, bit_depth: int, range_: str):
+    y = np.asarray(y, np.float64)
+    if range_ == "limited":
+        m = 2.0 ** (bit_depth - 8)
+        return (y - 16.0 * m) / (219.0 * m)
+    return y / (2.0 ** bit_depth - 1.0)
+
+
+def normalise_chroma(c, bit_depth: int, range_: str):
+    c = np.asarray(c, np.float64)
+    if range_ == "limited":
+        m = 2.0 ** (bit_depth - 8)
+        return (c - 128.0 * m) / (224.0 * m)
+    return (c - 2.0 ** (bit_depth - 1)) / (2.0 ** bit_depth - 1.0)
+
+
+def scale_luma(yp, bit_depth: int, range_: str):
+    """Inverse of normalise_luma, before rounding."""
+    if range_ == "limited":
+        m = 2.0 ** (bit_depth - 8)
+        return yp * 219.0 * m + 16.0 * m
+    return yp * (2.0 ** bit_depth - 1.0)
+
+
+def scale_chroma(cp, bit_depth: int, range_: str):
+    """Inverse of normalise_chroma, before rounding."""
+    if range_ == "limited":
+        m = 2.0 ** (bit_depth - 8)
+        return cp * 224.0 * m + 128.0 * m
+    return cp * (2.0 ** bit_depth - 1.0) + 2.0 ** (bit_depth - 1)
+
+
+def quantise(v, bit_depth: int):
+    """Round half to even (numpy rint), then clamp to [0, 2^b - 1]."""
+    q = np.rint(np.asarray(v, np.float64))
+    return np.clip(q, 0.0, 2.0 ** bit_depth - 1.0).astype(np.int64)
+
+
+# ---------------------------------------------------------------- matrix (C2)
+
+def ycbcr_to_rgb(yp, cb, cr):
+    """BT.709 Y'CbCr (normalised) -> R'G'B'.  No clamping."""
+    r = yp + 2.0 * (1.0 - KR) * cr
+    b = yp + 2.0 * (1.0 - KB) * cb
+    g = (yp - KR * r - KB * b) / KG
+    return r, g, b
+
+
+def rgb_to_ycbcr(r, g, b):
+    """BT.709 R'G'B' -> Y'CbCr (normalised)."""
+    yp = KR * r + KG * g + KB * b
+    cb = (b - yp) / (2.0 * (1.0 - KB))
+    cr = (r - yp) / (2.0 * (1.0 - KR))
+    return yp, cb, cr
+
+
+# ---------------------------------------------------------------- chroma (C3)
+
+def _clamp_idx(i, n):
+    return np.clip(i, 0, n - 1)
+
+
+def _up_axis(c, axis: int, mode: str):
+    """Double the length of one axis.
+
+    mode 'cosited': even output 2i = c_i, odd 2i+1 = (c_i + c_{i+1}) / 2.
+    mode 'centred': output 2i = 3/4 c_i + 1/4 c_{i-1}, 2i+1 = 3/4 c_i + 1/4 c_{i+1}.
+    mode 'replicate': output 2i = 2i+1 = c_i.
+    Indices outside the plane clamp to the nearest sample.
+    """
+    c = np.moveaxis(np.asarray(c, np.float64), axis, -1)
+    n = c.shape[-1]
+    i = np.arange(n)
+    out = np.empty(c.shape[:-1] + (2 * n,), np.float64)
+    if mode == "cosited":
+        out[..., 0::2] = c
+        out[..., 1::2] = 0.5 * (c + c[..., _clamp_idx(i + 1, n)])
+    elif mode == "centred":
+        out[..., 0::2] = 0.75 * c + 0.25 * c[..., _clamp_idx(i - 1, n)]
+        out[..., 1::2] = 0.75 * c + 0.25 * c[..., _clamp_idx(i + 1, n)]
+    elif mode == "replicate":
+        out[..., 0::2] = c
+        out[..., 1::2] = c
+    else:
+        raise ValueError(mode)
+    return np.moveaxis(out, -1, axis)
+
+
+def _down_axis(c, axis: int, mode: str):
+    """Halve the length of one (even-length) axis.
+
+    mode 'cosited': out_i = (c_{2i-1} + 2 c_{2i} + c_{2i+1}) / 4 (edge clamp).
+    mode 'pair':    out_i = (c_{2i} + c_{2i+1}) / 2.
+    """
+    c = np.moveaxis(np.asarray(c, np.float64), axis, -1)
+    n = c.shape[-1]
+    i = np.arange(n // 2)
+    if mode == "cosited":
+        out = 0.25 * (c[..., _clamp_idx(2 * i - 1, n)] + 2.0 * c[..., 2 * i]
+                      + c[..., _clamp_idx(2 * i + 1, n)])
+    elif mode == "pair":
+        out = 0.5 * (c[..., 2 * i] + c[..., 2 * i + 1])
+    else:
+        raise ValueError(mode)
+    return np.moveaxis(out, -1, axis)
+
+
+_UP = {"left": ("centred", "cosited"), "center": ("centred", "centred"),
+       "point": ("replicate", "replicate")}
+_DOWN = {"left": ("pair", "cosited"), "center": ("pair", "pair"),
+         "point": ("pair", "pair")}
+
+
+def upsample_chroma(c, subsampling: str, loc: str):
+    """4:2:0 -> 4:4:4 (vertical then horizontal); 4:4:4 passes through."""
+    if subsampling == "444":
+        return np.asarray(c, np.float64)
+    v, h = _UP[loc]
+    return _up_axis(_up_axis(c, 0, v), 1, h)
+
+
+def downsample_chroma(c, subsampling: str, loc: str):
+    """4:4:4 -> 4:2:0 (vertical then horizontal); 4:4:4 passes through."""
+    if subsampling == "444":
+        return np.asarray(c, np.float64)
+    v, h = _DOWN[loc]
+    return _down_axis(_down_axis(c, 0, v), 1, h)
+
+
+# ---------------------------------------------------------------- ingest / requantise
+
+def ingest(planes, fmt):
+    """Integer Y/U/V planes -> float64 R'G'B' [3][H][W] (network domain RGB, unclamped).
+
+    fmt: dict with bit_depth, subsampling ('420'|'444'), range ('limited'|'full'),
+    chroma_loc ('left'|'center'|'point').
+    """
+    b, rg = fmt["bit_depth"], fmt["range"]
+    yp = normalise_luma(planes["Y"], b, rg)
+    cb = upsample_chroma(normalise_chroma(planes["U"], b, rg), fmt["subsampling"], fmt["chroma_loc"])
+    cr = upsample_chroma(normalise_chroma(planes["V"], b, rg), fmt["subsampling"], fmt["chroma_loc"])
+    r, g, bb = ycbcr_to_rgb(yp, cb, cr)
+    return np.stack([r, g, bb])
+
+
+def requantise(rgb, fmt):
+    """float R'G'B' [3][H][W] -> integer planes {"Y","U","V"} (int64 arrays).
+
+    Y'CbCr from RGB, chroma downsampled in float, scaled to the code range,
+    rounded half to even and clamped to [0, 2^b - 1].
+    """
+    b, rg = fmt["bit_depth"], fmt["range"]
+    yp, cb, cr = rgb_to_ycbcr(rgb[0], rgb[1], rgb[2])
+    cb = downsample_chroma(cb, fmt["subsampling"], fmt["chroma_loc"])
+    cr = downsample_chroma(cr, fmt["subsampling"], fmt["chroma_loc"])
+    return {"Y": quantise(scale_luma(yp, b, rg), b),
+            "U": quantise(scale_chroma(cb, b, rg), b),
+            "V": quantise(scale_chroma(cr, b, rg), b)}
