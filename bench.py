@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Throughput of the frame-group enhancement hot path on one GB300 (or N replicas).
+
+Workload: 1080p -> 4K 2x spatial SR with the sliding-window network of five
+frames (conv 15->64, 10 residual blocks of 64 channels, conv 64->12,
+PixelShuffle(2), bilinear skip), 10-bit 4:2:0 limited-range BT.709 input and
+output.  One step = one pass of the whole path for one output frame: ingest
+of the newest input frame into the device ring, tuple formation, the 22-layer
+conv stack on the tensor cores (or SIMT for FP32), requantisation to 10-bit
+4:2:0 planes.  Inputs are seeded synthetic frames resident in HBM; every layer
+reads/writes 265 MB (64 channels x 1080p x BF16), far beyond the 129 MB L2, so
+no L2 flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead (the reference arm: there is no reference implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "output Mpix/s per GB300 at 1080p→4K 2x SR, BF16/FP8 vs FP32 at ±1 LSB; p99 latency"
+W, H, S = 1920, 1080, 2
+OUT_PIX = (W * S) * (H * S)
+BODY_FLOP = 2.0 * W * H * 64 * 9 * 64          # one 64->64 3x3 conv launch at 1080p
+H2D_BYTES = W * H * 2 + 2 * (W // 2) * (H // 2) * 2
+D2H_BYTES = (W * S) * (H * S) * 2 + 2 * (W * S // 2) * (H * S // 2) * 2
+NFRAMES = 12                                   # distinct resident input frames, cycled
+# DRAM bytes per conv_body launch from an ncu capture of the current kernel
+# (profiles/conv_body_bf16_1080p.md); None until captured for this version.
+CONV_BODY_TRAFFIC = None
+WORKLOAD = ("1080p->4K 2x SR: sliding window T=5, conv 15->64, 10 residual blocks of 64 ch, conv 64->12, "
+            "PixelShuffle(2), bilinear skip; 10-bit 4:2:0 limited BT.709 in and out")
+DATA = "synthetic: seeded textured 10-bit 4:2:0 frames with global 0-4 px translation; random-init He-normal weights"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained", d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in out.strip().splitlines():
+            t = [x.strip() for x in ln.split(",")]
+            if len(t) < 7:
+                continue
+            try:
+                sm.append(float(t[0]))
+                mx.append(float(t[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, t[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("NVISR_BENCH_GLOO") is None else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def gpu_frames(local):
+    import torch
+    frames = synth.frames_textured(synth.BASE_SEED + 2, NFRAMES, W, H, 10, "420", "limited")
+    dev, pinned = [], []
+    for f in frames:
+        d, p = [], []
+        for k in "YUV":
+            a = np.ascontiguousarray(f[k]).view(np.int16)
+            t = torch.from_numpy(a)
+            p.append(t.pin_memory())
+            d.append(t.to(f"cuda:{local}"))
+        dev.append(tuple(d))
+        pinned.append(tuple(p))
+    return dev, pinned
+
+
+def measure(nv, prec, steps, warmup, dev_frames, local, world, clocks=None):
+    import torch
+    text, blob = synth.net_config2()
+    eng = nv.Engine(device=local)
+    flt = eng.filter(text, blob, nv.fmt(W, H, 10), nv.fmt(W * S, H * S, 10), prec, S)
+    out = (torch.empty((H * S, W * S), dtype=torch.int16, device=f"cuda:{local}"),
+           torch.empty((H * S // 2, W * S // 2), dtype=torch.int16, device=f"cuda:{local}"),
+           torch.empty((H * S // 2, W * S // 2), dtype=torch.int16, device=f"cuda:{local}"))
+    pushed = [0]
+
+    def push():
+        st = flt.push(dev_frames[pushed[0] % NFRAMES])
+        assert st == nv.Status.OK, st
+        pushed[0] += 1
+
+    for _ in range(3):  # frames 0..2: output 0 (tuple [0,0,0,1,2]) becomes ready
+        push()
+
+    def step():
+        push()
+        st, _ = flt.pull(out)
+        assert st == nv.Status.OK, st
+
+    for _ in range(warmup):
+        step()
+    stream = torch.cuda.ExternalStream(eng.stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    flt.profile(True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.start()
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    t1.synchronize()
+    torch.cuda.synchronize()
+    ck = clocks.stop() if clocks else None
+    ms = t0.elapsed_time(t1)
+    prof = flt.profile_read()
+    flt.profile(False)
+    barrier(world)
+    ms_max = allmax(ms, world)
+    eng.close()
+    return ms_max, prof, ck
+
+
+def measure_e2e(nv, prec, steps, pinned, local):
+    """Host planes in, host planes out, through nvisr_push / nvisr_pull (copies inside)."""
+    import torch
+    text, blob = synth.net_config2()
+    eng = nv.Engine(device=local)
+    flt = eng.filter(text, blob, nv.fmt(W, H, 10), nv.fmt(W * S, H * S, 10), prec, S)
+    out = (torch.empty((H * S, W * S), dtype=torch.int16).pin_memory(),
+           torch.empty((H * S // 2, W * S // 2), dtype=torch.int16).pin_memory(),
+           torch.empty((H * S // 2, W * S // 2), dtype=torch.int16).pin_memory())
+    k = [0]
+
+    def push():
+        assert flt.push(pinned[k[0] % NFRAMES]) == nv.Status.OK
+        k[0] += 1
+
+    for _ in range(3):
+        push()
+    lat = []
+    for i in range(steps + 3):
+        t = time.perf_counter()
+        push()
+        st, _ = flt.pull(out)
+        assert st == nv.Status.OK
+        if i >= 3:
+            lat.append(time.perf_counter() - t)
+    eng.close()
+    total = sum(lat)
+    lat_ms = sorted(x * 1e3 for x in lat)
+    p = lambda q: lat_ms[min(len(lat_ms) - 1, int(round(q * (len(lat_ms) - 1))))]
+    return total, p(0.5), p(0.99)
+
+
+# ---------------------------------------------------------------------------- oracle arm
+
+def oracle_sample(side_w, side_h, seed=synth.BASE_SEED + 2):
+    """The oracle on a crop of the workload: 5 frames -> ingest -> network -> requantise 1 output."""
+    import oracle
+    frames = synth.frames_textured(seed, 5, side_w, side_h, 10, "420", "limited")
+    flags = np.zeros(5, bool)
+    text, blob = synth.net_config2()
+    fd = dict(bit_depth=10, subsampling="420", range="limited", chroma_loc="left")
+    t = time.perf_counter()
+    oracle.run_filter(frames, flags, text, blob, fd, fd, outputs=[2])
+    dt = time.perf_counter() - t
+    return dt, (2 * side_w) * (2 * side_h), oracle.oracle_threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.oracle_threads()  # builds the C routines before timing
+    side_w, side_h = 48, 48
+    for _ in range(args.warmup):
+        oracle_sample(side_w, side_h)
+    total, px = 0.0, 0
+    for _ in range(args.steps):
+        dt, p, cores = oracle_sample(side_w, side_h)
+        total += dt
+        px += p
+    val = px / total / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": DATA, "config": {"workload": WORKLOAD, "input": f"{W}x{H}", "output": f"{W*S}x{H*S}",
+                                     "parallelism": f"replicas{args.gpus}"},
+            "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step: one output of the full path on a {side_w}x{side_h} crop "
+                                       f"of 5 frames ({2*side_w}x{2*side_h} output px)"},
+            "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precisions", default="bf16,fp8,fp32")
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_2308_03121_gb300 as nv
+    torch.cuda.set_device(local)
+    nv.load()
+    hbm, bf16_burst, bf16_sust, peak_src = peaks()
+    dev_frames, pinned = gpu_frames(local)
+    results = {}
+    clocks = Clocks(local)
+    head = "bf16"
+    precs = [p for p in args.precisions.split(",") if p]
+    if head not in precs:
+        precs.insert(0, head)
+    for prec in precs:
+        steps = args.steps if prec != "fp32" else max(5, min(args.steps, 40))
+        ms, prof, ck = measure(nv, prec, steps, args.warmup, dev_frames, local, world,
+                               clocks if prec == head else None)
+        results[prec] = {"ms": ms, "steps": steps, "prof": prof, "clocks": ck,
+                         "mpix_s": world * steps * OUT_PIX / (ms * 1e-3) / 1e6}
+    r = results[head]
+    prof = r["prof"]
+    body_ms, body_n = prof["conv_body"]
+    avg_body = body_ms / max(body_n, 1)
+    achieved = BODY_FLOP / (avg_body * 1e-3) / 1e12
+    launches = sum(n for _, n in prof.values())
+    e2e_total, p50, p99 = measure_e2e(nv, head, args.e2e_steps, pinned, local)
+    e2e_val = world * args.e2e_steps * OUT_PIX / e2e_total / 1e6
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, px, cores = oracle_sample(320, 192)
+        cpu = {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+               "sample": f"one output of the full path (ingest, network, requantise) on a 320x192 crop of "
+                         f"5 frames: {px} output px in {dt:.1f} s"}
+    if rank != 0:
+        return
+    by_prec = {}
+    for p, v in results.items():
+        pr = v["prof"]
+        by_prec[p] = {"value": v["mpix_s"], "ms_per_step": v["ms"] / v["steps"], "steps": v["steps"],
+                      "kernel_ms_per_step": {k: round(ms / v["steps"], 4) for k, (ms, n) in pr.items() if n}}
+    if "fp32" in results:
+        for p in by_prec:
+            by_prec[p]["speedup_vs_fp32"] = by_prec[p]["value"] / by_prec["fp32"]["value"]
+    line = {
+        "metric": METRIC, "value": r["mpix_s"], "unit": "Mpix/s", "n_gpus": world, "steps": r["steps"],
+        "warmup": args.warmup, "ms_per_step": r["ms"] / r["steps"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": head, "data": DATA,
+        "config": {"workload": WORKLOAD, "input": f"{W}x{H}", "output": f"{W*S}x{H*S}", "tuple": 5,
+                   "l2": "inputs larger than L2: every conv layer streams 265 MB in and out (L2 129 MB)",
+                   "parallelism": f"replicas{world}"},
+        "frames_per_s": world * r["steps"] / (r["ms"] * 1e-3),
+        "roofline": {"kernel": "conv_tc_kernel (64->64 3x3, BF16, 20 launches/step)", "bound": "tensor",
+                     "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s", "frac": achieved / bf16_sust,
+                     "peak_source": f"bf16_tflops_sustained of {peak_src}",
+                     "algorithmic_flop_per_launch": BODY_FLOP, "avg_launch_ms": avg_body,
+                     "traffic": CONV_BODY_TRAFFIC},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": H2D_BYTES,
+                "d2h_bytes_per_step": D2H_BYTES, "steps": args.e2e_steps},
+        "latency_ms": {"p50": p50, "p99": p99, "what": "per-frame push->pull wall time, host planes"},
+        "gpu_launches": launches,
+        "clocks": r["clocks"],
+        "precisions": by_prec,
+        "hbm_peak_gbs": hbm,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

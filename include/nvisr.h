@@ -1,0 +1,280 @@
+/*
+ * nvisr.h -- C ABI of the GB300 frame-group video enhancement library.
+ *
+ * The library runs a video enhancement network over a stream of frames the
+ * way NNVISR hosts one (arXiv 2308.03121): a filter is created from a network
+ * description, the input/output pixel formats and the spatial / temporal
+ * scale (Section 3.2, "End User Usage": one function, clip + parameters in,
+ * enhanced clip out; scale factors and the Interpolation / Extra frame /
+ * Double frame flags of Section 3.1 select the task); frames are pushed with
+ * their scene-change property (Section 3.2) and enhanced frames are pulled in
+ * presentation order, grouped within scenes by the rules of Section 3.3.
+ *
+ * Every stage runs in this library's CUDA kernels (sm_103a): ingest (integer
+ * planes -> normalised float frame), 3x3 convolutions as implicit GEMM on the
+ * tensor cores (BF16 / FP16 / FP8) or on FP32 SIMT lanes, modulated
+ * deformable convolution (DCN v2, Section 3.1), and requantisation.
+ *
+ * Conventions for every call:
+ *  - Every function returns an nvisr_status (void destroy calls excepted);
+ *    nothing throws across the ABI.  nvisr_last_error() gives a message for
+ *    the most recent failure on this thread.
+ *  - "device" pointers are CUDA device pointers of the engine's device;
+ *    "host" pointers are ordinary (ideally pinned) host memory.  The caller
+ *    owns every buffer it passes and keeps it alive for the call's duration.
+ *  - Calls on one engine are not thread safe; use one engine per thread.
+ */
+#ifndef NVISR_H
+#define NVISR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NVISR_ABI_VERSION 1
+
+typedef enum nvisr_status {
+    NVISR_OK = 0,
+    NVISR_AGAIN = 1,             /* pull: no output ready yet; push more input */
+    NVISR_FULL = 2,              /* push: ring full; pull first (backpressure) */
+    NVISR_EOS = 3,               /* pull: all outputs of a flushed stream were returned */
+    NVISR_INVALID_ARG = -1,
+    NVISR_UNSUPPORTED_FORMAT = -2,
+    NVISR_OUT_OF_MEMORY = -3,
+    NVISR_OVER_BUDGET = -4,      /* the engine's HBM budget would be exceeded */
+    NVISR_CUDA_ERROR = -5,
+    NVISR_DEVICE_TIMEOUT = -6,   /* a bounded device-side wait expired */
+    NVISR_BAD_NETWORK = -7,      /* malformed network description or weight blob */
+    NVISR_INTERNAL = -8
+} nvisr_status;
+
+typedef enum nvisr_subsampling { NVISR_SUB_420 = 0, NVISR_SUB_444 = 1 } nvisr_subsampling;
+typedef enum nvisr_range { NVISR_RANGE_LIMITED = 0, NVISR_RANGE_FULL = 1 } nvisr_range;
+typedef enum nvisr_matrix { NVISR_MATRIX_BT709 = 0 } nvisr_matrix;
+/* Chroma siting of 4:2:0 planes: LEFT = ITU-T H.273 type 0 (co-sited
+ * horizontally, between rows vertically), CENTER = type 1, POINT = replicate
+ * on upsampling and 2x2 mean on downsampling. */
+typedef enum nvisr_chroma_loc {
+    NVISR_CHROMA_LEFT = 0, NVISR_CHROMA_CENTER = 1, NVISR_CHROMA_POINT = 2
+} nvisr_chroma_loc;
+/* Arithmetic of the network's contractions (convolution / DCN).  FP32 runs on
+ * the SIMT lanes; the others on tcgen05 tensor cores with FP32 accumulation.
+ * FP8 is E4M3 with per-tensor scales. */
+typedef enum nvisr_precision {
+    NVISR_PREC_FP32 = 0, NVISR_PREC_BF16 = 1, NVISR_PREC_FP16 = 2, NVISR_PREC_FP8 = 3
+} nvisr_precision;
+
+/* Integer YUV video format (Section 3.1: YUV / RGB I/O; colour-space aware).
+ * Samples of bit_depth <= 8 are uint8, 9..16 are uint16 (low bits). */
+typedef struct nvisr_format {
+    int32_t width, height;       /* luma size in pixels */
+    int32_t bit_depth;           /* 8 or 10 */
+    int32_t subsampling;         /* nvisr_subsampling */
+    int32_t range;               /* nvisr_range */
+    int32_t matrix;              /* nvisr_matrix */
+    int32_t chroma_loc;          /* nvisr_chroma_loc */
+    int32_t reserved;
+} nvisr_format;
+
+/* Three planes Y, U (Cb), V (Cr).  pitch = bytes between rows. */
+typedef struct nvisr_planes {
+    void *data[3];
+    int64_t pitch[3];
+    int32_t on_device;           /* 1: device pointers, 0: host pointers */
+    int32_t reserved;
+} nvisr_planes;
+
+/* Frame flags for nvisr_push. */
+#define NVISR_FRAME_SCENE_CUT 1u /* this frame starts a new scene (cut before it) */
+
+typedef struct nvisr_engine_desc {
+    int32_t device;              /* CUDA device ordinal */
+    int32_t max_filters;         /* 0 = unlimited */
+    int64_t hbm_budget_bytes;    /* 0 = no budget beyond the device's memory */
+    void *stream;                /* cudaStream_t to run on; NULL = engine creates one */
+} nvisr_engine_desc;
+
+typedef struct nvisr_filter_desc {
+    const char *network_text;    /* "nvisr-net 1" description, NUL terminated */
+    const float *weights;        /* host FP32 weight blob, in description order */
+    int64_t weights_count;       /* number of floats in the blob */
+    nvisr_format in_fmt;
+    nvisr_format out_fmt;        /* width/height must equal scale x input */
+    int32_t scale_w, scale_h;    /* spatial scale; must match the description */
+    int32_t precision;           /* nvisr_precision */
+    int32_t calib_frames;        /* FP8: frames whose activations set the scales (0 = 4) */
+} nvisr_filter_desc;
+
+typedef struct nvisr_frame_info {
+    int64_t index;               /* output frame index (presentation order) */
+    int64_t src_first, src_last; /* input frames the output depends on */
+    int32_t scene;               /* scene number of the output's source */
+    int32_t reserved;
+} nvisr_frame_info;
+
+typedef struct nvisr_engine nvisr_engine;
+typedef struct nvisr_filter nvisr_filter;
+
+/* ----------------------------------------------------------------------------
+ * Engine and filter (Section 3.2: create a filter from network + parameters;
+ * frames in, enhanced frames out).
+ * ------------------------------------------------------------------------- */
+
+/* Create an engine on one GPU.  Owns the stream (unless given), the device
+ * memory of every filter and the HBM budget.  *out receives the handle.
+ * Errors: INVALID_ARG (NULL pointers, bad device), CUDA_ERROR. */
+nvisr_status nvisr_engine_create(const nvisr_engine_desc *desc, nvisr_engine **out);
+
+/* Destroy the engine and every filter it still owns. NULL is ignored. */
+void nvisr_engine_destroy(nvisr_engine *engine);
+
+/* The cudaStream_t the engine's work is enqueued on. */
+void *nvisr_engine_stream(nvisr_engine *engine);
+
+/* Device bytes currently held by the engine's filters. */
+int64_t nvisr_engine_bytes_in_use(nvisr_engine *engine);
+
+/* Create a filter: parse and check the network description (Section 3.1: the
+ * network is consumed through a description of its graph), upload weights
+ * converted to the precision's layout, allocate the frame ring and the
+ * activations.  Device memory is charged to the engine's budget.
+ * Errors: BAD_NETWORK, UNSUPPORTED_FORMAT, INVALID_ARG (scale/format mismatch),
+ * OVER_BUDGET, OUT_OF_MEMORY, CUDA_ERROR. */
+nvisr_status nvisr_filter_create(nvisr_engine *engine, const nvisr_filter_desc *desc,
+                                 nvisr_filter **out);
+
+/* Release a filter's device memory and handle. NULL is ignored. */
+void nvisr_filter_destroy(nvisr_filter *filter);
+
+/* Push the next input frame.  Planes are copied into the filter's device ring
+ * and converted by the ingest kernel before the call returns (host planes are
+ * read synchronously; device planes are consumed in stream order).
+ * flags: NVISR_FRAME_SCENE_CUT marks the frame as the first of a new scene
+ * (Section 3.2: scene changes arrive as a per-frame property).
+ * Returns FULL when the ring holds no free slot (pull first), EOS after flush. */
+nvisr_status nvisr_push(nvisr_filter *filter, const nvisr_planes *in, uint32_t flags);
+
+/* Declare the end of the stream: the last scene closes and its tail outputs
+ * become available (Section 3.3: the last frame is duplicated as needed). */
+nvisr_status nvisr_flush(nvisr_filter *filter);
+
+/* Produce the next output frame in presentation order into the caller's
+ * planes (host or device).  Runs the network for the output's frame group if
+ * it has not run yet.  Returns AGAIN if the group's input frames are not all
+ * known yet, EOS once a flushed stream has returned every output.  For host
+ * planes the call returns after the copy completes; device planes are
+ * written in stream order.  info may be NULL. */
+nvisr_status nvisr_pull(nvisr_filter *filter, nvisr_planes *out, nvisr_frame_info *info);
+
+/* Number of outputs the filter can currently pull without more input. */
+int64_t nvisr_filter_ready(nvisr_filter *filter);
+
+/* Run every filter of the engine that has ready work, for up to max_outputs
+ * outputs in total, leaving the results in their filters' output queues to be
+ * pulled later (batched / serving mode).  *produced receives the count. */
+nvisr_status nvisr_engine_step(nvisr_engine *engine, int32_t max_outputs, int32_t *produced);
+
+/* Check a network description and blob size without a device (host only):
+ * the same parse and validation nvisr_filter_create performs.  Returns OK or
+ * BAD_NETWORK (message in nvisr_last_error). */
+nvisr_status nvisr_network_check(const char *network_text, int64_t weights_count);
+
+/* Per-kernel timing of a filter's work, recorded with CUDA events on the
+ * engine's stream around every launch while enabled.  Kinds: */
+enum {
+    NVISR_K_INGEST = 0, NVISR_K_PACK = 1, NVISR_K_CONV_HEAD = 2, NVISR_K_CONV_BODY = 3,
+    NVISR_K_CONV_TAIL = 4, NVISR_K_REQUANT = 5, NVISR_K_DCN = 6, NVISR_K_CONV_OTHER = 7,
+    NVISR_K_COUNT = 8
+};
+typedef struct nvisr_profile {
+    double ms[NVISR_K_COUNT];        /* summed device time per kind */
+    int64_t launches[NVISR_K_COUNT]; /* launches per kind */
+} nvisr_profile;
+
+/* enable != 0 starts recording (clearing earlier totals); 0 stops. */
+nvisr_status nvisr_filter_profile(nvisr_filter *filter, int32_t enable);
+/* Wait for the recorded launches and return their totals since enabling. */
+nvisr_status nvisr_filter_profile_read(nvisr_filter *filter, nvisr_profile *out);
+
+const char *nvisr_status_string(nvisr_status status);
+const char *nvisr_last_error(void);
+
+/* ----------------------------------------------------------------------------
+ * Stage entry points (each runs one hot-path stage on caller-owned device
+ * buffers, on the given cudaStream_t; used for per-stage parity tests).
+ * ------------------------------------------------------------------------- */
+
+/* Ingest: integer planes (device) -> R'G'B' float32 planar [3][H][W]
+ * (row pitch out_pitch floats, channel stride out_pitch*H).  Range
+ * normalisation (limited/full, 8/10 bit), chroma upsampling with the format's
+ * siting (edges clamp), BT.709 Y'CbCr -> R'G'B', no clamping (Section 3.1:
+ * YUV input converted for an RGB network). */
+nvisr_status nvisr_ingest(const nvisr_format *fmt, const nvisr_planes *in, float *out_rgb,
+                          int64_t out_pitch, void *stream);
+
+/* Requantise: R'G'B' float32 planar [3][H][W] (row pitch in_pitch floats) ->
+ * integer planes (device): BT.709 R'G'B' -> Y'CbCr, chroma downsampling,
+ * range scaling, round half to even, clamp to [0, 2^b - 1] (Section 3.1:
+ * YUV output). */
+nvisr_status nvisr_requant(const nvisr_format *fmt, const float *in_rgb, int64_t in_pitch,
+                           nvisr_planes *out, void *stream);
+
+/* Frame-tuple source indices for a clip (Section 3.3: grouping within scenes;
+ * sliding window of T frames, edge frames replicated at scene bounds).
+ * flags[k] != 0: frame k starts a scene.  out receives nframes*T indices. */
+nvisr_status nvisr_tuple_map(const uint8_t *flags, int32_t nframes, int32_t T, int32_t *out);
+
+/* Group-model runs of one scene [s0, s1] (Section 3.1 flags, Section 3.3 rules):
+ * runs of n (+1 with extra) frames; out_inputs receives runs*need indices and
+ * out_skip the number of leading already-covered frames per run.  *nruns
+ * receives the run count; max_runs bounds the output arrays. */
+nvisr_status nvisr_group_runs(int32_t s0, int32_t s1, int32_t n, int32_t extra, int32_t interp,
+                              int32_t max_runs, int32_t *out_inputs, int32_t *out_skip,
+                              int32_t *nruns);
+
+/* Frame-store layout of Section 3.3, Figure 1 for a batch of b groups of n+1
+ * frames: cell_frame[(n+1)*b] receives, per column-first address, the frame
+ * index relative to the batch's first frame (-1 = unused cell); slot_start[n+1]
+ * receives each input slot's first address; copy[2] the (src, dst) addresses
+ * of the one copy that prepares the next batch in a store reused in place. */
+nvisr_status nvisr_fig1_layout(int32_t n, int32_t b, int32_t *cell_frame, int32_t *slot_start,
+                               int32_t *copy);
+
+/* One 2-D convolution layer (Section 3.1 networks) on planar float32 tensors:
+ * y[cout][H][W] = act(conv_k(x[cin][H][W]; w[cout][cin][k][k]) + b) (+ res),
+ * stride 1, zero padding (k-1)/2, act 0 = none, 1 = LeakyReLU(0.1).  Runs the
+ * precision's kernel (FP32 SIMT or tensor cores); the library converts x to
+ * its internal layout in scratch device memory it allocates per call.
+ * res may be NULL.  All pointers are device pointers. */
+nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_t h, int32_t w,
+                          const float *weight, const float *bias, int32_t cout, int32_t k,
+                          int32_t act, const float *res, float *y, void *stream);
+
+/* Modulated deformable convolution 3x3, DCN v2 as in torchvision's
+ * deform_conv2d (Section 3.1): offsets [2*G*9][H][W] (dy, dx per group and
+ * tap), mask [G*9][H][W] (already in [0,1]), stride 1, padding 1.  Planar
+ * float32 device tensors; scratch allocated per call. */
+nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t h, int32_t w,
+                         const float *offsets, const float *mask, int32_t groups,
+                         const float *weight, const float *bias, int32_t cout, float *y,
+                         void *stream);
+
+/* Tensor-core self test: one 128x16 MMA of BF16 (K = 16) and one of FP8 E4M3
+ * (K = 32) small-integer operands through shared-memory descriptors, TMEM
+ * and tcgen05.ld, compared with the exact products.  *mismatches_* receive
+ * the number of wrong accumulator elements (0 = the descriptor conventions
+ * hold).  Runs on the current device; allocates and frees a few bytes. */
+nvisr_status nvisr_selftest(int32_t *mismatches_bf16, int32_t *mismatches_fp8);
+
+/* Library version / build information. */
+int32_t nvisr_abi_version(void);
+const char *nvisr_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NVISR_H */

@@ -1,0 +1,138 @@
+// Shared definitions of the CUDA path (internal; not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "nvisr.h"
+
+namespace nvisr {
+
+// Element type of an activation tensor in the blocked layout.
+enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2, DT_E4M3 = 3 };
+
+inline int dtype_size(int dt) { return dt == DT_F32 ? 4 : (dt == DT_E4M3 ? 1 : 2); }
+// Channels per 16-byte chunk of the blocked layout [C/cpc][H][W][cpc].
+inline int chunk_channels(int dt) { return 16 / dtype_size(dt); }
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+inline int64_t round_up64(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Thread-local last error message (nvisr_last_error).
+void set_error(const std::string &msg);
+nvisr_status cuda_status(cudaError_t e, const char *where);
+
+#define NVISR_TRY_CUDA(expr)                                                   \
+    do {                                                                       \
+        cudaError_t _e = (expr);                                               \
+        if (_e != cudaSuccess) return ::nvisr::cuda_status(_e, #expr);         \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (each returns the launch's cudaError_t).
+// ---------------------------------------------------------------------------
+
+// ingest: integer planes -> float32 planar R'G'B' (pitch in floats).
+cudaError_t launch_ingest(const nvisr_format &fmt, const void *y, int64_t py, const void *u,
+                          int64_t pu, const void *v, int64_t pv, float *out, int64_t out_pitch,
+                          cudaStream_t st);
+
+// requantise: float32 planar R'G'B' -> integer planes.
+cudaError_t launch_requant(const nvisr_format &fmt, const float *in, int64_t in_pitch, void *y,
+                           int64_t py, void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st);
+
+// Up to 8 planar float32 frames of 3 channels each (tuple, frame-major
+// channels) or one planar tensor of C channels -> blocked tensor of dtype dt
+// with cpad channels (zero filled past the real channels).  scale multiplies
+// every value before conversion (FP8 quantisation), and amax (optional)
+// receives max |value| (before scaling) via atomicMax on its float bits.
+struct PackArgs {
+    const float *src[8];
+    int nsrc;            // number of source tensors
+    int ch_per_src;      // channels of each source
+    int64_t src_pitch;   // floats between rows
+    int64_t src_plane;   // floats between channels
+    int H, W;
+    void *dst;
+    int cpad;
+    int dt;
+    float scale;
+    unsigned *amax;
+};
+cudaError_t launch_pack(const PackArgs &a, cudaStream_t st);
+
+// blocked tensor -> planar float32 [C][H][W] (first C channels; value*scale).
+cudaError_t launch_unpack(const void *src, int dt, int cpad, int C, int H, int W, float scale,
+                          float *dst, int64_t dst_pitch, cudaStream_t st);
+
+// Convolution layer (3x3 or 1x1, stride 1, zero padding) on blocked tensors.
+struct ConvArgs {
+    const void *x;           // blocked input [cin_pad/cpc][H][W][cpc] per image
+    int cin_pad;
+    int H, W;
+    int nimg;                // images stacked along the outer dimension
+    const void *w;           // prepared weights (kernel-specific layout)
+    const float *bias;       // [cout_pad] float32 (zero past cout)
+    int cout, cout_pad, k;
+    int act;                 // 0 none, 1 LeakyReLU(0.1)
+    const void *res;         // blocked residual, same layout/dtype as y, or nullptr
+    void *y;                 // blocked output [cout_pad/cpc][H][W][cpc]
+    int in_dt, out_dt;       // dtypes of x and of y/res
+    float acc_scale;         // multiplies the accumulator (FP8 dequant), 1 otherwise
+    float out_scale;         // multiplies the stored value (FP8 quant of y), 1 otherwise
+    void *y2;                // optional second output (FP8 copy of y), dtype E4M3
+    float y2_scale;
+    unsigned *amax;          // optional max |y| (float bits) for calibration
+    // final layer: PixelShuffle(ps) into planar float32 + skip
+    int ps;                  // 0: blocked store; r: pixel shuffle by r
+    float *ps_out;           // planar float32 [cout/(r*r)][rH][rW] (final) or null
+    int64_t ps_pitch;
+    const float *skip_src[2];// planar float32 source frames of the skip (mean)
+    int nskip;
+    int64_t skip_pitch, skip_plane;
+    int skip_mode;           // 0 none, 1 nearest, 2 bilinear
+    int skip_scale;          // output size / skip frame size
+    int skip_h, skip_w;      // skip frame size
+    int ps_act;              // activation applied after the shuffle (blocked ps output)
+    int *err;                // device error word (tensor-core kernels), may be null
+};
+cudaError_t launch_conv_simt(const ConvArgs &a, cudaStream_t st);
+cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st);
+
+// Weight preparation (device buffers allocated by the caller).
+// SIMT layout: [cin_pad][k*k][cout_pad] float32.
+size_t simt_weight_bytes(int cin_pad, int cout_pad, int k);
+void prepare_weights_simt(const float *w_oihw, int cout, int cin, int k, int cin_pad, int cout_pad,
+                          float *dst_host);
+// Tensor-core layout: canonical no-swizzle K-major core-matrix image per N slice.
+size_t tc_weight_bytes(int cin_pad, int cout_pad, int k, int dt);
+void prepare_weights_tc(const float *w_oihw, int cout, int cin, int k, int cin_pad, int cout_pad,
+                        int dt, float scale, void *dst_host);
+int tc_nslice(int cin_pad, int cout_pad, int k, int dt);
+
+// DCN: x blocked, offsets/mask planar float32 (mask already in [0,1] unless
+// mask_logits, which applies the logistic function first).
+struct DcnArgs {
+    const void *x;
+    int cin_pad, H, W, groups;
+    const float *off;        // [2*G*9][H][W] planar, pitch off_pitch, plane off_plane
+    const float *mask;       // [G*9][H][W]
+    int64_t om_pitch, om_plane;
+    int mask_logits;
+    const void *w;           // prepared weights (SIMT or TC layout, k = 3)
+    const float *bias;
+    int cout, cout_pad;
+    void *y;
+    int in_dt, out_dt;
+    float acc_scale, out_scale;
+};
+cudaError_t launch_dcn_simt(const DcnArgs &a, cudaStream_t st);
+cudaError_t launch_dcn_tc(const DcnArgs &a, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace nvisr

@@ -1,0 +1,661 @@
+// Tensor-core implicit-GEMM convolution for sm_103a (tcgen05 + TMEM + TMA).
+//
+// The enhancement networks NNVISR runs are stacks of 3x3 convolutions
+// (Section 3.1); here each layer is one GEMM
+//     D[M = pixels][N = out channels] = sum_K A[pixel][tap, in channel] B[out][tap, in]
+// computed without materialising im2col:
+//
+//  * Tile = 128 consecutive output pixels of one row (M = 128 = the MMA's M).
+//  * A producer warp TMA-loads the tile's input halo -- KS rows x (128+KS-1)
+//    pixels x NCH 16-byte channel chunks -- from the blocked activation
+//    [C/cpc][H][W][cpc] into shared memory, out-of-image pixels zero-filled
+//    by TMA (exact zero padding).  The halo lands in the canonical no-swizzle
+//    K-major layout (8 pixels x 16 bytes per core matrix), so the A operand
+//    of tap (ky, kx) is the same buffer addressed (ky*(128+KS-1) + kx)*16
+//    bytes further: the 9 taps share one load.
+//  * The layer's weights (or a slice of its output channels) stay resident in
+//    shared memory for the whole persistent CTA, pre-arranged on the host in
+//    the same core-matrix layout.
+//  * One thread issues tcgen05.mma (kind::f16 for BF16/FP16, kind::f8f6f4 for
+//    FP8 E4M3) into a double-buffered FP32 accumulator in TMEM; commits
+//    release shared-memory stages and hand finished tiles to the epilogue.
+//  * Four epilogue warps read TMEM (tcgen05.ld), apply scale, bias,
+//    LeakyReLU(0.1) and the residual add, and store the blocked output; the
+//    network's last layer instead applies PixelShuffle(2) and adds the skip
+//    (upsampled input frame) into a planar float32 image.
+//
+// Every mbarrier wait is bounded in time; a CTA that gives up raises a flag
+// seen by its other roles, records DEVERR_TIMEOUT in the error word, drains
+// its own in-flight copies and MMAs, and frees its TMEM before returning.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "epilogue.cuh"
+#include "sm100_ptx.cuh"
+
+namespace nvisr {
+
+namespace {
+
+constexpr int TM = 128;
+constexpr int NTHREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-5: epilogue
+constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr int SMEM_LIMIT = 232448;  // 227 KB per CTA
+constexpr int SMEM_HDR = 1024;      // barriers + TMEM slot + abort flag
+constexpr int W_MAX = 112 * 1024;   // resident weight slice budget
+
+struct TcParams {
+    int H, W, nimg, cin_chunks;      // cin_chunks = cin_pad / cpc
+    int cout, cout_pad, ns, nslice;
+    const uint8_t *wts;               // nslice slices of wbytes
+    uint32_t wbytes;
+    int stages;
+    const float *bias;
+    int act;
+    const uint8_t *res;
+    uint8_t *y;
+    float acc_scale, out_scale;
+    uint8_t *y2;
+    float y2_scale;
+    unsigned *amax;
+    // final PixelShuffle + skip
+    float *ps_out;
+    int64_t ps_pitch;
+    ConvArgs skip;  // skip_* fields only
+    int ps_act;
+    int *err;
+};
+
+template <int DT>
+struct Elem;
+template <>
+struct Elem<DT_BF16> { using T = __nv_bfloat16; };
+template <>
+struct Elem<DT_F16> { using T = __half; };
+template <>
+struct Elem<DT_E4M3> { using T = __nv_fp8_e4m3; };
+
+template <typename T>
+__device__ __forceinline__ T to_elem(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_elem<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_elem<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_fp8_e4m3 to_elem<__nv_fp8_e4m3>(float v) { return __nv_fp8_e4m3(v); }
+
+template <typename T>
+__device__ __forceinline__ float from_elem(T v) { return (float)v; }
+template <>
+__device__ __forceinline__ float from_elem<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float from_elem<__half>(__half v) { return __half2float(v); }
+
+__device__ __forceinline__ void raise_abort(volatile int *abort, int *err) {
+    *abort = 1;
+    if (err) atomicExch(err, DEVERR_TIMEOUT);
+}
+
+// Store 16 values as 16-bit or 8-bit elements at out (16 or 32 bytes... as
+// whole 16-byte chunks of the blocked layout).
+template <typename T>
+__device__ __forceinline__ void store_vals(uint8_t *base, int64_t chunk_stride, int chunk0, const float *v,
+                                           int n) {
+    constexpr int CPC = 16 / sizeof(T);
+    for (int c = 0; c < n / CPC; ++c) {
+        alignas(16) T o[CPC];
+#pragma unroll
+        for (int e = 0; e < CPC; ++e) o[e] = to_elem<T>(v[c * CPC + e]);
+        *reinterpret_cast<uint4 *>(base + (int64_t)(chunk0 + c) * chunk_stride) =
+            *reinterpret_cast<const uint4 *>(o);
+    }
+}
+
+// IN_DT: operand dtype; OUT_DT: dtype of y/res (16-bit, or E4M3 when the
+// layer feeds only an FP8 consumer); NS: output channels per CTA slice; KS:
+// kernel size; NCH: 16-byte chunks per pipeline stage (even); EPI: 0 blocked
+// store, 1 PixelShuffle(2) + skip into planar float32, 2 PixelShuffle(2) +
+// activation into a blocked tensor at twice the resolution.
+template <int IN_DT, int OUT_DT, int NS, int KS, int NCH, int EPI>
+__global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                              const TcParams p) {
+    using TI = typename Elem<IN_DT>::T;
+    using TO = typename Elem<OUT_DT>::T;
+    constexpr int KIND = IN_DT == DT_E4M3 ? 1 : 0;
+    constexpr int AFMT = IN_DT == DT_BF16 ? 1 : 0;
+    constexpr uint32_t IDESC = instr_desc(TM, NS, AFMT, AFMT);
+    constexpr int ROWS = KS;
+    constexpr int PXS = TM + KS - 1;
+    constexpr int PAD = (KS - 1) / 2;
+    constexpr uint32_t LBO_A = ROWS * PXS * 16;
+    constexpr uint32_t STAGE_BYTES = NCH * LBO_A;
+    constexpr uint32_t NCOLS = (2 * NS <= 32) ? 32 : (2 * NS <= 64 ? 64 : (2 * NS <= 128 ? 128 : (2 * NS <= 256 ? 256 : 512)));
+    constexpr int CPC_O = 16 / sizeof(TO);
+    static_assert(NCH % 2 == 0, "an MMA consumes two 16-byte K chunks");
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int S = p.stages;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + 8;
+    uint64_t *tfull = empty + 8;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *wbar = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint8_t *wsm = smem + SMEM_HDR;
+    uint8_t *stage0 = wsm + ((p.wbytes + 1023) & ~1023u);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slice = blockIdx.x % p.nslice;
+    const int cta_stride = gridDim.x / p.nslice;
+    const int cta0 = blockIdx.x / p.nslice;
+    const int tiles_x = (p.W + TM - 1) / TM;
+    const int ntiles = tiles_x * p.H * p.nimg;
+    const int groups = p.cin_chunks / NCH;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4 * 32);
+        }
+        mbar_init(wbar, 1);
+        *abort = 0;
+        fence_mbarrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, NCOLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer: weights once, then input halos
+            mbar_arrive_expect_tx(wbar, p.wbytes);
+            const uint8_t *wsrc = p.wts + (size_t)slice * p.wbytes;
+            for (uint32_t off = 0; off < p.wbytes; off += 32768u) {
+                const uint32_t n = min(32768u, p.wbytes - off);
+                bulk_load(wsm + off, wsrc + off, n, wbar);
+            }
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;
+            bool ok = true;
+            for (int t = cta0; t < ntiles && ok; t += cta_stride) {
+                const int img = t / (tiles_x * p.H);
+                const int r = t - img * tiles_x * p.H;
+                const int y = r / tiles_x;
+                const int x0 = (r - y * tiles_x) * TM;
+                for (int g = 0; g < groups; ++g) {
+                    if (!mbar_wait_bounded(&empty[s], ph ^ 1, abort, WAIT_NS)) {
+                        raise_abort(abort, p.err);
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_4d(stage0 + (size_t)s * STAGE_BYTES, &tmap, &full[s], 0, x0 - PAD, y - PAD,
+                                img * p.cin_chunks + g * NCH);
+                    ++issued;
+                    if (++s == S) { s = 0; ph ^= 1; }
+                }
+            }
+            // drain: the last load of every stage must land before the CTA exits
+            for (int k = 0; k < S && k < issued; ++k) {
+                const int idx = issued - 1 - k;  // load number idx went to stage idx % S, phase (idx / S) & 1
+                mbar_wait_bounded(&full[idx % S], (uint32_t)((idx / S) & 1), nullptr, WAIT_NS);
+            }
+            mbar_wait_bounded(wbar, 0, nullptr, WAIT_NS);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            bool ok = mbar_wait_bounded(wbar, 0, abort, WAIT_NS);
+            if (!ok) raise_abort(abort, p.err);
+            const uint32_t wbase = smem_u32(wsm);
+            int s = 0;
+            uint32_t ph = 0;
+            int it = 0, last_a = -1;
+            uint32_t last_par = 0;
+            for (int t = cta0; t < ntiles && ok; t += cta_stride, ++it) {
+                const int a = it & 1;
+                const uint32_t u = (uint32_t)(it >> 1);
+                if (!mbar_wait_bounded(&tempty[a], (u & 1) ^ 1, abort, WAIT_NS)) {
+                    raise_abort(abort, p.err);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(a * NS);
+                for (int g = 0; g < groups; ++g) {
+                    if (!mbar_wait_bounded(&full[s], ph, abort, WAIT_NS)) {
+                        raise_abort(abort, p.err);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sbase = smem_u32(stage0 + (size_t)s * STAGE_BYTES);
+#pragma unroll
+                    for (int tap = 0; tap < KS * KS; ++tap) {
+                        const int ky = tap / KS, kx = tap % KS;
+#pragma unroll
+                        for (int j = 0; j < NCH / 2; ++j) {
+                            const uint64_t ad =
+                                smem_desc(sbase + 2 * j * LBO_A + (uint32_t)(ky * PXS + kx) * 16u, LBO_A, 128);
+                            const uint32_t kc = (uint32_t)(tap * p.cin_chunks + g * NCH + 2 * j);
+                            const uint64_t bd = smem_desc(wbase + kc * (uint32_t)(NS * 16), NS * 16, 128);
+                            umma<KIND>(d_tmem, ad, bd, IDESC, (g | tap | j) != 0 ? 1u : 0u);
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                    if (++s == S) { s = 0; ph ^= 1; }
+                }
+                if (!ok) break;
+                umma_commit(&tfull[a]);
+                last_a = a;
+                last_par = u & 1;
+            }
+            // drain: MMAs must finish before TMEM is released
+            if (last_a >= 0) mbar_wait_bounded(&tfull[last_a], last_par, nullptr, WAIT_NS);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5 own TMEM lane quadrants (warp % 4)
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        int it = 0;
+        for (int t = cta0; t < ntiles; t += cta_stride, ++it) {
+            const int a = it & 1;
+            const uint32_t u = (uint32_t)(it >> 1);
+            bool ok = mbar_wait_bounded(&tfull[a], u & 1, abort, WAIT_NS);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) raise_abort(abort, p.err);
+                break;
+            }
+            tc_fence_after();
+            const int img = t / (tiles_x * p.H);
+            const int r = t - img * tiles_x * p.H;
+            const int y = r / tiles_x;
+            const int x = (r - y * tiles_x) * TM + m;
+            const bool valid = x < p.W;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * NS);
+            const int64_t HW = (int64_t)p.H * p.W;
+            if (EPI == 0) {
+                const int ochunks = p.cout_pad / CPC_O;
+                const int64_t pix = (int64_t)y * p.W + x;
+#pragma unroll
+                for (int j = 0; j < NS / 16; ++j) {
+                    float v[16];
+                    tmem_ld16(taddr + (uint32_t)(j * 16), v);
+                    if (!valid) continue;
+                    const int n0 = slice * NS + j * 16;
+                    float amax = 0.f;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        float o = v[e] * p.acc_scale + p.bias[n0 + e];
+                        if (p.act == 1) o = lrelu(o);
+                        v[e] = o;
+                    }
+                    const int c0 = n0 / CPC_O;
+                    const int64_t cstride = HW * 16;
+                    uint8_t *ybase = p.y + ((int64_t)img * ochunks * HW + pix) * 16;
+                    if (p.res) {
+                        const uint8_t *rbase = p.res + ((int64_t)img * ochunks * HW + pix) * 16;
+#pragma unroll
+                        for (int c = 0; c < 16 / CPC_O; ++c) {
+                            alignas(16) TO rv[CPC_O];
+                            *reinterpret_cast<uint4 *>(rv) =
+                                *reinterpret_cast<const uint4 *>(rbase + (int64_t)(c0 + c) * cstride);
+#pragma unroll
+                            for (int e = 0; e < CPC_O; ++e) v[c * CPC_O + e] += from_elem<TO>(rv[e]) / p.out_scale;
+                        }
+                    }
+                    if (p.amax) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) amax = fmaxf(amax, fabsf(v[e]));
+                        atomicMax(p.amax, __float_as_uint(amax));
+                    }
+                    if (p.y2) {
+                        float w2[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) w2[e] = v[e] * p.y2_scale;
+                        store_vals<__nv_fp8_e4m3>(p.y2 + ((int64_t)img * (p.cout_pad / 16) * HW + pix) * 16,
+                                                  cstride, n0 / 16, w2, 16);
+                    }
+                    if (p.out_scale != 1.0f) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[e] *= p.out_scale;
+                    }
+                    store_vals<TO>(ybase, cstride, c0, v, 16);
+                }
+            } else if (EPI == 1) {
+                // PixelShuffle(2) of channels [0, cout) + skip -> planar float32 at (2y, 2x)
+                float v[16];
+                tmem_ld16(taddr, v);
+                if (valid) {
+                    const int H2 = 2 * p.H;
+#pragma unroll
+                    for (int c = 0; c < NS / 4; ++c) {
+                        if (c >= p.cout / 4) break;
+                        float o[4];
+#pragma unroll
+                        for (int ij = 0; ij < 4; ++ij) {
+                            const int n = c * 4 + ij;
+                            const int Y = 2 * y + (ij >> 1), X = 2 * x + (ij & 1);
+                            o[ij] = v[n] * p.acc_scale + p.bias[n] +
+                                    skip_value(p.skip, c, Y, X, p.skip.skip_scale, p.skip.skip_h, p.skip.skip_w);
+                        }
+                        float *dst = p.ps_out + (int64_t)img * (p.cout / 4) * p.ps_pitch * H2 +
+                                     (int64_t)c * p.ps_pitch * H2 + (int64_t)(2 * y) * p.ps_pitch + 2 * x;
+                        *reinterpret_cast<float2 *>(dst) = make_float2(o[0], o[1]);
+                        *reinterpret_cast<float2 *>(dst + p.ps_pitch) = make_float2(o[2], o[3]);
+                    }
+                }
+            } else {
+                // PixelShuffle(2) into a blocked tensor [C/4 / CPC_O][2H][2W][CPC_O], then activation.
+                float v[NS];
+#pragma unroll
+                for (int j = 0; j < NS / 16; ++j) {
+                    float t16[16];
+                    tmem_ld16(taddr + (uint32_t)(j * 16), t16);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[j * 16 + e] = t16[e];
+                }
+                if (valid) {
+                    const int n_base = slice * NS;
+#pragma unroll
+                    for (int e = 0; e < NS; ++e) {
+                        float o = v[e] * p.acc_scale + p.bias[n_base + e];
+                        if (p.act == 1) o = lrelu(o);
+                        v[e] = o;
+                    }
+                    const int cps = p.cout / 4;                 // shuffled channels
+                    const int64_t HW4 = 4 * HW;
+                    const int c_base = n_base / 4;              // first shuffled channel of this slice
+#pragma unroll
+                    for (int ij = 0; ij < 4; ++ij) {
+                        const int Y = 2 * y + (ij >> 1), X = 2 * x + (ij & 1);
+                        const int64_t pix2 = (int64_t)Y * (2 * p.W) + X;
+#pragma unroll
+                        for (int h = 0; h < NS / 4 / CPC_O; ++h) {
+                            float o[CPC_O];
+#pragma unroll
+                            for (int e = 0; e < CPC_O; ++e) {
+                                float val = v[(h * CPC_O + e) * 4 + ij];
+                                if (p.ps_act == 1) val = lrelu(val);
+                                o[e] = val * p.out_scale;
+                            }
+                            const int cc = (c_base / CPC_O) + h;
+                            store_vals<TO>(p.y + ((int64_t)img * (cps / CPC_O) * HW4 + pix2) * 16, HW4 * 16, cc, o,
+                                           CPC_O);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[a]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, NCOLS);
+    }
+}
+
+// ---------------------------------------------------------------- self test
+
+// One M=128, N=16 MMA over K = 16 (BF16) or 32 (E4M3) of small integers, read
+// back through tcgen05.ld and compared with the exact product.  Offsets are
+// small enough that every descriptor field interpretation stays inside the
+// allocated shared memory.
+template <int KIND>
+__global__ void __launch_bounds__(128, 1) mma_selftest_kernel(int *mismatches) {
+    constexpr int K = KIND == 0 ? 16 : 32;
+    constexpr int ESZ = KIND == 0 ? 2 : 1;
+    constexpr int CPC = 16 / ESZ;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 8);
+    uint8_t *A = smem + 1024;         // [2 chunks][128 rows][16 B]: LBO 2048, SBO 128
+    uint8_t *B = smem + 1024 + 4096;  // [2 chunks][16 rows][16 B]:  LBO 256,  SBO 128
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto aval = [](int m, int k) { return (float)(((m * 3 + k * 5) % 7) - 3); };
+    auto bval = [](int n, int k) { return (float)(((n * 5 + k * 3) % 5) - 2); };
+    for (int i = tid; i < 128 * K; i += 128) {
+        const int m = i / K, k = i % K;
+        const int off = (k / CPC) * 2048 + m * 16 + (k % CPC) * ESZ;
+        if (KIND == 0) *reinterpret_cast<__nv_bfloat16 *>(A + off) = __float2bfloat16_rn(aval(m, k));
+        else *reinterpret_cast<__nv_fp8_e4m3 *>(A + off) = __nv_fp8_e4m3(aval(m, k));
+    }
+    for (int i = tid; i < 16 * K; i += 128) {
+        const int n = i / K, k = i % K;
+        const int off = (k / CPC) * 256 + n * 16 + (k % CPC) * ESZ;
+        if (KIND == 0) *reinterpret_cast<__nv_bfloat16 *>(B + off) = __float2bfloat16_rn(bval(n, k));
+        else *reinterpret_cast<__nv_fp8_e4m3 *>(B + off) = __nv_fp8_e4m3(bval(n, k));
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbarrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(slot, 32);
+        tmem_relinquish();
+    }
+    fence_proxy_async();  // generic-proxy smem writes -> visible to the tensor core
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *slot;
+    if (tid == 0) {
+        const uint64_t ad = smem_desc(smem_u32(A), 2048, 128);
+        const uint64_t bd = smem_desc(smem_u32(B), 256, 128);
+        umma<KIND>(tbase, ad, bd, instr_desc(128, 16, 0, 0) | (KIND == 0 ? (1u << 7) | (1u << 10) : 0u), 0u);
+        umma_commit(bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0, nullptr, WAIT_NS);
+    tc_fence_after();
+    float v[16];
+    tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
+    int bad = ok ? 0 : 1000;
+    const int m = warp * 32 + lane;
+    for (int n = 0; n < 16; ++n) {
+        float ref = 0.f;
+        for (int k = 0; k < K; ++k) ref += aval(m, k) * bval(n, k);
+        if (v[n] != ref) ++bad;
+    }
+    if (bad) atomicAdd(mismatches, bad);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 32);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+int pick_ns(int cin_chunks, int cout_pad, int k) {
+    const int per_n = k * k * cin_chunks * 16;
+    for (int ns : {64, 32, 16}) {
+        if (cout_pad % ns == 0 && ns * per_n <= W_MAX) return ns;
+    }
+    return 16;
+}
+
+template <int IN_DT, int OUT_DT, int NS, int KS, int NCH, int EPI>
+cudaError_t run(const CUtensorMap &map, TcParams p, cudaStream_t st) {
+    constexpr int PXS = TM + KS - 1;
+    constexpr uint32_t STAGE_BYTES = NCH * KS * PXS * 16;
+    const uint32_t wround = (p.wbytes + 1023) & ~1023u;
+    const int avail = SMEM_LIMIT - 1024 /*align slack*/ - SMEM_HDR - (int)wround;
+    int stages = avail / (int)STAGE_BYTES;
+    if (stages > 8) stages = 8;
+    if (stages < 2) return cudaErrorInvalidConfiguration;
+    p.stages = stages;
+    // request at least 116 KB so one CTA occupies an SM (TMEM and scheduling assume it)
+    int smem = 1024 + SMEM_HDR + (int)wround + stages * (int)STAGE_BYTES;
+    if (smem < 118 * 1024) smem = 118 * 1024;
+    auto kern = conv_tc_kernel<IN_DT, OUT_DT, NS, KS, NCH, EPI>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((p.W + TM - 1) / TM) * p.H * p.nimg;
+    int sms = device_sm_count();
+    int per_slice = sms / p.nslice;
+    if (per_slice < 1) per_slice = 1;
+    if (per_slice > tiles) per_slice = tiles;
+    kern<<<per_slice * p.nslice, NTHREADS, smem, st>>>(map, p);
+    return cudaGetLastError();
+}
+
+using Runner = cudaError_t (*)(const CUtensorMap &, TcParams, cudaStream_t);
+
+struct Variant {
+    int in_dt, out_dt, ns, ks, nch, epi;
+    Runner fn;
+};
+
+#define NVISR_V(I, O, NS_, KS_, NCH_, EPI_) {I, O, NS_, KS_, NCH_, EPI_, &run<I, O, NS_, KS_, NCH_, EPI_>}
+#define NVISR_V16(I, NS_, KS_, NCH_, EPI_) NVISR_V(I, I, NS_, KS_, NCH_, EPI_)
+
+const Variant kVariants[] = {
+    // 16-bit operands: heads, bodies, tails of the tuple networks; DCN-net layers
+    NVISR_V16(DT_BF16, 64, 3, 2, 0), NVISR_V16(DT_BF16, 64, 3, 4, 0), NVISR_V16(DT_BF16, 64, 3, 8, 0),
+    NVISR_V16(DT_BF16, 32, 3, 2, 0), NVISR_V16(DT_BF16, 32, 3, 4, 0), NVISR_V16(DT_BF16, 32, 3, 8, 0),
+    NVISR_V16(DT_BF16, 16, 3, 4, 1), NVISR_V16(DT_BF16, 16, 3, 8, 1), NVISR_V16(DT_BF16, 64, 1, 8, 0),
+    NVISR_V16(DT_BF16, 64, 3, 8, 2), NVISR_V16(DT_BF16, 16, 3, 2, 0), NVISR_V16(DT_BF16, 16, 3, 4, 0),
+    NVISR_V16(DT_BF16, 16, 3, 8, 0),
+    NVISR_V16(DT_F16, 64, 3, 2, 0), NVISR_V16(DT_F16, 64, 3, 4, 0), NVISR_V16(DT_F16, 64, 3, 8, 0),
+    NVISR_V16(DT_F16, 32, 3, 2, 0), NVISR_V16(DT_F16, 32, 3, 4, 0), NVISR_V16(DT_F16, 32, 3, 8, 0),
+    NVISR_V16(DT_F16, 16, 3, 4, 1), NVISR_V16(DT_F16, 16, 3, 8, 1), NVISR_V16(DT_F16, 64, 1, 8, 0),
+    NVISR_V16(DT_F16, 64, 3, 8, 2), NVISR_V16(DT_F16, 16, 3, 2, 0), NVISR_V16(DT_F16, 16, 3, 4, 0),
+    NVISR_V16(DT_F16, 16, 3, 8, 0),
+    // FP8 E4M3 operands (bodies): output BF16 trunk (+ FP8 copy) or FP8 directly
+    NVISR_V(DT_E4M3, DT_BF16, 64, 3, 4, 0), NVISR_V(DT_E4M3, DT_E4M3, 64, 3, 4, 0),
+};
+
+}  // namespace
+
+int tc_nslice(int cin_pad, int cout_pad, int k, int dt) {
+    const int cin_chunks = cin_pad / chunk_channels(dt);
+    return cout_pad / pick_ns(cin_chunks, cout_pad, k);
+}
+
+size_t tc_weight_bytes(int cin_pad, int cout_pad, int k, int dt) {
+    return (size_t)k * k * (cin_pad / chunk_channels(dt)) * cout_pad * 16;
+}
+
+void prepare_weights_tc(const float *w, int cout, int cin, int k, int cin_pad, int cout_pad, int dt, float scale,
+                        void *dst) {
+    const int cpc = chunk_channels(dt);
+    const int esz = dtype_size(dt);
+    const int cin_chunks = cin_pad / cpc;
+    const int ns = pick_ns(cin_chunks, cout_pad, k);
+    const int kk = k * k;
+    uint8_t *out = static_cast<uint8_t *>(dst);
+    const size_t total = tc_weight_bytes(cin_pad, cout_pad, k, dt);
+    for (size_t i = 0; i < total; ++i) out[i] = 0;
+    // slice sl, tap t, chunk kc, local row n, element e -> byte offset
+    for (int o = 0; o < cout; ++o) {
+        const int sl = o / ns, n = o % ns;
+        for (int c = 0; c < cin; ++c) {
+            const int kc = c / cpc, e = c % cpc;
+            for (int t = 0; t < kk; ++t) {
+                const float v = w[((size_t)o * cin + c) * kk + t] * scale;
+                const size_t off = (size_t)sl * kk * cin_chunks * ns * 16 +
+                                   (((size_t)t * cin_chunks + kc) * ns + n) * 16 + (size_t)e * esz;
+                if (dt == DT_BF16) {
+                    __nv_bfloat16 h = __float2bfloat16_rn(v);
+                    memcpy(out + off, &h, 2);
+                } else if (dt == DT_F16) {
+                    __half h = __float2half_rn(v);
+                    memcpy(out + off, &h, 2);
+                } else {
+                    __nv_fp8_e4m3 h(v);
+                    memcpy(out + off, &h, 1);
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
+    const int dt = a.in_dt;
+    if (dt == DT_F32) return cudaErrorInvalidValue;
+    const int cpc = chunk_channels(dt);
+    if (a.cin_pad % cpc) return cudaErrorInvalidValue;
+    const int cin_chunks = a.cin_pad / cpc;
+    const int ns = pick_ns(cin_chunks, a.cout_pad, a.k);
+    const int nch = cin_chunks >= 8 ? 8 : cin_chunks;
+    if (cin_chunks % nch || nch % 2) return cudaErrorInvalidValue;
+    const int epi = a.ps > 0 ? (a.ps_out ? 1 : 2) : 0;
+    const int odt = epi == 1 ? dt : a.out_dt;
+    const Variant *v = nullptr;
+    for (const Variant &c : kVariants)
+        if (c.in_dt == dt && c.out_dt == odt && c.ns == ns && c.ks == a.k && c.nch == nch && c.epi == epi) v = &c;
+    if (!v) return cudaErrorNotSupported;
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    // activation as a byte tensor: (16 B chunk, W, H, chunks of all images)
+    CUtensorMap map;
+    const int pxs = TM + a.k - 1;
+    cuuint64_t dims[4] = {16, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.nimg * cin_chunks};
+    cuuint64_t strides[3] = {16, (cuuint64_t)a.W * 16, (cuuint64_t)a.W * a.H * 16};
+    cuuint32_t box[4] = {16, (cuuint32_t)pxs, (cuuint32_t)a.k, (cuuint32_t)nch};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.x), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    TcParams p{};
+    p.H = a.H; p.W = a.W; p.nimg = a.nimg; p.cin_chunks = cin_chunks;
+    p.cout = a.cout; p.cout_pad = a.cout_pad; p.ns = ns; p.nslice = a.cout_pad / ns;
+    p.wts = static_cast<const uint8_t *>(a.w);
+    p.wbytes = (uint32_t)(a.k * a.k * cin_chunks * ns * 16);
+    p.bias = a.bias; p.act = a.act;
+    p.res = static_cast<const uint8_t *>(a.res);
+    p.y = static_cast<uint8_t *>(a.y);
+    p.acc_scale = a.acc_scale; p.out_scale = a.out_scale;
+    p.y2 = static_cast<uint8_t *>(a.y2); p.y2_scale = a.y2_scale; p.amax = a.amax;
+    p.ps_out = a.ps_out; p.ps_pitch = a.ps_pitch; p.skip = a; p.ps_act = a.ps_act;
+    p.err = a.err;
+    return v->fn(map, p, st);
+}
+
+int tc_selftest(int kind, int *dev_mismatch, cudaStream_t st) {
+    const int smem = 64 * 1024;
+    if (kind == 0) {
+        cudaFuncSetAttribute(mma_selftest_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        mma_selftest_kernel<0><<<1, 128, smem, st>>>(dev_mismatch);
+    } else {
+        cudaFuncSetAttribute(mma_selftest_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        mma_selftest_kernel<1><<<1, 128, smem, st>>>(dev_mismatch);
+    }
+    return (int)cudaGetLastError();
+}
+
+}  // namespace nvisr

@@ -1,0 +1,1256 @@
+// Engine, filter and C-ABI implementation.
+//
+// A filter follows the paper's statement of the problem (Section 3.2: one
+// call, clip + parameters -> enhanced clip) as a push/pull stream:
+//   push(frame, scene flag) -> H2D copy into the device ring -> ingest kernel
+//   pull() -> group formation (Section 3.3: within scenes, edge frames
+//             replicated) -> network forward (pack, conv / DCN layers) ->
+//             requantise -> copy to the caller.
+// The ring holds each input frame once as planar float32 R'G'B'; a frame
+// tuple is a list of ring slots, so grouping copies no pixels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "netdesc.h"
+
+namespace nvisr {
+
+int tc_selftest(int kind, int *dev_mismatch, cudaStream_t st);
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+nvisr_status cuda_status(cudaError_t e, const char *where) {
+    set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return NVISR_OUT_OF_MEMORY;
+    if (e == cudaErrorNotSupported) return NVISR_UNSUPPORTED_FORMAT;
+    return NVISR_CUDA_ERROR;
+}
+
+static nvisr_status fail(nvisr_status s, const std::string &msg) {
+    set_error(msg);
+    return s;
+}
+
+int device_sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (!cache[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 148;
+    }
+    return cache[dev];
+}
+
+}  // namespace nvisr
+
+using namespace nvisr;
+
+// ---------------------------------------------------------------- handles
+
+struct nvisr_engine {
+    int device = 0;
+    int max_filters = 0;
+    int64_t budget = 0;
+    int64_t used = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int *err_word = nullptr;  // device error word shared by this engine's kernels
+    std::vector<nvisr_filter *> filters;
+};
+
+namespace {
+
+struct DevBuf {
+    nvisr_engine *eng = nullptr;
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+nvisr_status dalloc(nvisr_engine *e, size_t bytes, std::vector<DevBuf> &owned, void **out) {
+    bytes = (size_t)round_up64((int64_t)std::max<size_t>(bytes, 256), 256);
+    if (e->budget > 0 && e->used + (int64_t)bytes > e->budget)
+        return fail(NVISR_OVER_BUDGET, "HBM budget exceeded: need " + std::to_string(bytes) + " more bytes, " +
+                                           std::to_string(e->budget - e->used) + " left");
+    void *p = nullptr;
+    cudaError_t ce = cudaMalloc(&p, bytes);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NVISR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(ce));
+    }
+    e->used += (int64_t)bytes;
+    owned.push_back({e, p, bytes});
+    *out = p;
+    return NVISR_OK;
+}
+
+struct Tensor {
+    void *ptr = nullptr;
+    int C = 0, cpad = 0, H = 0, W = 0, dt = DT_F32;
+    void *f8 = nullptr;  // FP8 copy (when an FP8 layer consumes this tensor)
+    int amax_slot = -1;  // calibration slot of the FP8 values
+};
+
+struct Weights {
+    void *simt_or_tc = nullptr;  // 16-bit / FP32 layout
+    void *f8 = nullptr;          // FP8 layout
+    float *bias = nullptr;
+    int cin_pad = 0, cout_pad = 0;
+    float w_amax = 0.f;
+};
+
+enum Src { SRC_TENSOR = 0, SRC_TUPLE = 1 };
+
+struct Step {
+    int layer = 0;
+    int in_t = -1;       // input tensor id (SRC_TENSOR)
+    int src = SRC_TENSOR;
+    int frame_src = -1;  // group family: input from ring frame k
+    int add_t = -1;
+    int out_t = -1;      // -1: final output (PixelShuffle into planar float32)
+    int out_index = -1;  // final output number
+    bool fp8 = false;
+    bool out_f8_only = false;
+};
+
+bool fmt_ok(const nvisr_format &f) {
+    return f.width > 0 && f.height > 0 && (f.bit_depth == 8 || f.bit_depth == 10) &&
+           (f.subsampling == NVISR_SUB_420 || f.subsampling == NVISR_SUB_444) &&
+           (f.range == NVISR_RANGE_LIMITED || f.range == NVISR_RANGE_FULL) && f.matrix == NVISR_MATRIX_BT709 &&
+           f.chroma_loc >= 0 && f.chroma_loc <= 2 &&
+           (f.subsampling == NVISR_SUB_444 || (f.width % 2 == 0 && f.height % 2 == 0));
+}
+
+int64_t plane_bytes(const nvisr_format &f, int plane, int64_t *pitch, int *h) {
+    const int esz = f.bit_depth > 8 ? 2 : 1;
+    const bool sub = plane > 0 && f.subsampling == NVISR_SUB_420;
+    const int w = sub ? f.width / 2 : f.width;
+    *h = sub ? f.height / 2 : f.height;
+    *pitch = round_up64((int64_t)w * esz, 256);
+    return *pitch * *h;
+}
+
+int64_t plane_row_bytes(const nvisr_format &f, int plane) {
+    const int esz = f.bit_depth > 8 ? 2 : 1;
+    const bool sub = plane > 0 && f.subsampling == NVISR_SUB_420;
+    return (int64_t)(sub ? f.width / 2 : f.width) * esz;
+}
+
+int plane_rows(const nvisr_format &f, int plane) {
+    return (plane > 0 && f.subsampling == NVISR_SUB_420) ? f.height / 2 : f.height;
+}
+
+}  // namespace
+
+struct nvisr_filter {
+    nvisr_engine *eng = nullptr;
+    NetDesc net;
+    nvisr_format in_fmt{}, out_fmt{};
+    int precision = NVISR_PREC_FP32;
+    int act_dt = DT_F32;  // 16-bit / FP32 activation dtype
+    bool tc = false;      // tensor-core kernels
+    std::vector<DevBuf> owned;
+
+    // ring of ingested frames (planar float32 [3][H][pitch])
+    int ring = 0;
+    int64_t rpitch = 0;   // floats
+    float *ring_base = nullptr;
+    int64_t slot_floats = 0;
+    void *stage[3] = {nullptr, nullptr, nullptr};
+    int64_t stage_pitch[3] = {0, 0, 0};
+
+    // stream bookkeeping
+    int64_t pushed = 0;
+    bool eos = false;
+    std::vector<uint8_t> cut;      // per pushed frame: starts a scene
+    int64_t next_out = 0;          // next output index to return
+    int64_t total_out = -1;        // known after flush
+
+    // network plan
+    std::vector<Weights> weights;  // per layer (shared layers point to the owner)
+    std::vector<Tensor> tensors;
+    std::vector<Step> steps;
+    int pack_t = -1;               // tensor id of the packed tuple
+    float *out_rgb[2] = {nullptr, nullptr};  // planar float32 outputs [3][sH][opitch]
+    int64_t opitch = 0;
+    void *ostage[3] = {nullptr, nullptr, nullptr};
+    int64_t ostage_pitch[3] = {0, 0, 0};
+
+    // group family: run cache (outputs of the last run)
+    int64_t cached_run = -1;
+
+    // FP8 calibration
+    bool calibrated = false;
+    int calib_frames = 4;
+    unsigned *amax = nullptr;      // device [n slots]
+    int n_amax = 0;
+    std::vector<float> act_scale;  // per amax slot
+
+    // host-side queue of produced-but-not-pulled outputs (engine_step)
+    std::deque<int64_t> produced;
+
+    // per-kernel timing (nvisr_filter_profile)
+    bool prof = false;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[NVISR_K_COUNT] = {0};
+    int64_t prof_n[NVISR_K_COUNT] = {0};
+};
+
+namespace {
+
+cudaEvent_t take_event(nvisr_filter *f) {
+    if (!f->ev_pool.empty()) {
+        cudaEvent_t e = f->ev_pool.back();
+        f->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void flush_profile(nvisr_filter *f) {
+    if (f->recs.empty()) return;
+    cudaStreamSynchronize(f->eng->stream);
+    for (auto &r : f->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            f->prof_ms[r.kind] += ms;
+            f->prof_n[r.kind] += 1;
+        }
+        f->ev_pool.push_back(r.a);
+        f->ev_pool.push_back(r.b);
+    }
+    f->recs.clear();
+}
+
+// Records CUDA events around the launches issued during its lifetime.
+struct ProfScope {
+    nvisr_filter *f;
+    int kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(nvisr_filter *f_, int kind_) : f(f_), kind(kind_) {
+        if (f->prof) {
+            a = take_event(f);
+            cudaEventRecord(a, f->eng->stream);
+        }
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b = take_event(f);
+        cudaEventRecord(b, f->eng->stream);
+        f->recs.push_back({kind, a, b});
+        if (f->recs.size() > 4096) flush_profile(f);
+    }
+};
+
+float *ring_slot(nvisr_filter *f, int64_t frame) {
+    return f->ring_base + (frame % f->ring) * f->slot_floats;
+}
+
+// Scene bounds of frame t among the known frames: s0 = last cut <= t,
+// s1 = (first cut > t) - 1, or the last known frame; *closed says whether s1
+// is final (a later cut is known, or the stream ended).
+void scene_bounds(const nvisr_filter *f, int64_t t, int64_t *s0, int64_t *s1, bool *closed) {
+    int64_t a = t;
+    while (a > 0 && !f->cut[(size_t)a]) --a;
+    *s0 = a;
+    int64_t b = t + 1;
+    while (b < f->pushed && !f->cut[(size_t)b]) ++b;
+    *s1 = b - 1;
+    *closed = (b < f->pushed) || f->eos;
+}
+
+// Tuple family: is output t computable, and with which source frames?
+bool tuple_ready(const nvisr_filter *f, int64_t t, std::vector<int64_t> *idx) {
+    if (t >= f->pushed) return false;
+    const int T = f->net.frames, r = (T - 1) / 2;
+    int64_t s0, s1;
+    bool closed;
+    scene_bounds(f, t, &s0, &s1, &closed);
+    if (!closed && s1 < t + r) return false;
+    if (idx) {
+        idx->resize(T);
+        for (int k = 0; k < T; ++k) (*idx)[k] = std::min(std::max(t - r + k, s0), s1);
+    }
+    return true;
+}
+
+// Group family (n = 1, Extra frame, Interpolation, Double frame): run i uses
+// frames (i, min(i+1, s1)) and emits outputs 2i, 2i+1.
+bool group_ready(const nvisr_filter *f, int64_t run, std::vector<int64_t> *idx) {
+    if (run >= f->pushed) return false;
+    int64_t s0, s1;
+    bool closed;
+    scene_bounds(f, run, &s0, &s1, &closed);
+    if (!closed && s1 < run + 1) return false;
+    if (idx) *idx = {run, std::min(run + 1, s1)};
+    return true;
+}
+
+int outputs_per_input(const nvisr_filter *f) { return f->net.family == "group" ? 2 : 1; }
+
+bool output_ready(const nvisr_filter *f, int64_t o) {
+    if (f->net.family == "group") return group_ready(f, o / 2, nullptr);
+    return tuple_ready(f, o, nullptr);
+}
+
+nvisr_status check_device_error(nvisr_filter *f) {
+    int h = 0;
+    NVISR_TRY_CUDA(cudaMemcpyAsync(&h, f->eng->err_word, sizeof(int), cudaMemcpyDeviceToHost, f->eng->stream));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(f->eng->stream));
+    if (h != 0) {
+        cudaMemsetAsync(f->eng->err_word, 0, sizeof(int), f->eng->stream);
+        return fail(NVISR_DEVICE_TIMEOUT, "a device-side wait exceeded its time bound (error word " +
+                                              std::to_string(h) + ")");
+    }
+    return NVISR_OK;
+}
+
+// ---------------------------------------------------------------- plan
+
+int act_cpad(const nvisr_filter *f, int C) {
+    return f->tc ? round_up(C, 16) : round_up(C, 8);
+}
+
+nvisr_status upload(nvisr_filter *f, const void *host, size_t bytes, void **dev) {
+    nvisr_status s = dalloc(f->eng, bytes, f->owned, dev);
+    if (s != NVISR_OK) return s;
+    NVISR_TRY_CUDA(cudaMemcpy(*dev, host, bytes, cudaMemcpyHostToDevice));
+    return NVISR_OK;
+}
+
+bool layer_is_fp8(const nvisr_filter *f, const NetLayer &L) {
+    return f->precision == NVISR_PREC_FP8 && L.op == "conv" && L.k == 3 && L.cin == 64 && L.cout == 64 &&
+           L.ps == 0 && L.in.size() == 1 && L.in[0] != "tuple" && L.in[0].rfind("frame", 0) != 0;
+}
+
+nvisr_status prepare_weights(nvisr_filter *f, const float *blob) {
+    const NetDesc &net = f->net;
+    f->weights.resize(net.layers.size());
+    for (size_t i = 0; i < net.layers.size(); ++i) {
+        const NetLayer &L = net.layers[i];
+        if (L.owner != (int)i) {
+            f->weights[i] = f->weights[L.owner];
+            continue;
+        }
+        Weights &W = f->weights[i];
+        const float *w = blob + L.woff;
+        const float *b = w + (int64_t)L.cout * L.cin * L.k * L.k;
+        W.cin_pad = act_cpad(f, L.cin);
+        W.cout_pad = round_up(L.cout, 16);
+        std::vector<float> bias(W.cout_pad, 0.f);
+        std::copy(b, b + L.cout, bias.begin());
+        void *dbias;
+        nvisr_status s = upload(f, bias.data(), bias.size() * 4, &dbias);
+        if (s != NVISR_OK) return s;
+        W.bias = (float *)dbias;
+        if (!f->tc) {
+            std::vector<float> host(simt_weight_bytes(W.cin_pad, W.cout_pad, L.k) / 4);
+            prepare_weights_simt(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, host.data());
+            s = upload(f, host.data(), host.size() * 4, &W.simt_or_tc);
+        } else {
+            std::vector<uint8_t> host(tc_weight_bytes(W.cin_pad, W.cout_pad, L.k, f->act_dt));
+            prepare_weights_tc(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, f->act_dt, 1.0f, host.data());
+            s = upload(f, host.data(), host.size(), &W.simt_or_tc);
+        }
+        if (s != NVISR_OK) return s;
+        if (layer_is_fp8(f, L)) {
+            float amax = 0.f;
+            for (int64_t k = 0; k < (int64_t)L.cout * L.cin * L.k * L.k; ++k) amax = std::max(amax, std::fabs(w[k]));
+            W.w_amax = amax > 0.f ? amax : 1.f;
+            const float sw = W.w_amax / 448.f;
+            std::vector<uint8_t> host(tc_weight_bytes(L.cin, W.cout_pad, L.k, DT_E4M3));
+            prepare_weights_tc(w, L.cout, L.cin, L.k, L.cin, W.cout_pad, DT_E4M3, 1.0f / sw, host.data());
+            s = upload(f, host.data(), host.size(), &W.f8);
+            if (s != NVISR_OK) return s;
+        }
+    }
+    return NVISR_OK;
+}
+
+// Builds the step list and allocates tensors with buffer reuse by liveness.
+nvisr_status build_plan(nvisr_filter *f) {
+    const NetDesc &net = f->net;
+    const int H = f->in_fmt.height, W = f->in_fmt.width;
+    std::map<std::string, int> tensor_of;  // layer name -> tensor id
+    std::map<std::string, int> out_index;
+    for (size_t i = 0; i < net.outputs.size(); ++i) out_index[net.outputs[i].name] = (int)i;
+    f->tensors.clear();
+    f->steps.clear();
+    if (net.family == "tuple") {
+        Tensor t;
+        t.C = 3 * net.frames;
+        t.cpad = act_cpad(f, t.C);
+        t.H = H;
+        t.W = W;
+        t.dt = f->act_dt;
+        f->pack_t = 0;
+        f->tensors.push_back(t);
+    }
+    for (size_t i = 0; i < net.layers.size(); ++i) {
+        const NetLayer &L = net.layers[i];
+        if (L.op != "conv") return fail(NVISR_UNSUPPORTED_FORMAT, "layer " + L.name + ": op not supported by this plan");
+        if (L.in.size() != 1) return fail(NVISR_UNSUPPORTED_FORMAT, "layer " + L.name + ": concatenated inputs");
+        Step st;
+        st.layer = (int)i;
+        if (L.in[0] == "tuple") {
+            st.src = SRC_TUPLE;
+            st.in_t = f->pack_t;
+        } else {
+            auto it = tensor_of.find(L.in[0]);
+            if (it == tensor_of.end()) return fail(NVISR_BAD_NETWORK, "layer " + L.name + ": unknown input");
+            st.in_t = it->second;
+        }
+        const Tensor &src = f->tensors[st.in_t];
+        if (src.C != L.cin) return fail(NVISR_BAD_NETWORK, "layer " + L.name + ": cin does not match its input");
+        if (!L.add.empty()) st.add_t = tensor_of.at(L.add);
+        st.fp8 = layer_is_fp8(f, L);
+        if (out_index.count(L.name)) {
+            if (!L.ps || L.cout != 12 || src.H != H) return fail(NVISR_UNSUPPORTED_FORMAT, "output layer must be conv ->12 ch + PixelShuffle(2) at input size");
+            if (net.scale != 2) return fail(NVISR_UNSUPPORTED_FORMAT, "tuple networks: scale 2 only");
+            st.out_t = -1;
+            st.out_index = out_index[L.name];
+        } else {
+            if (L.ps) return fail(NVISR_UNSUPPORTED_FORMAT, "inner PixelShuffle in a tuple network");
+            Tensor t;
+            t.C = L.cout;
+            t.cpad = round_up(L.cout, 16);
+            t.H = src.H;
+            t.W = src.W;
+            t.dt = f->act_dt;
+            st.out_t = (int)f->tensors.size();
+            tensor_of[L.name] = st.out_t;
+            f->tensors.push_back(t);
+        }
+        f->steps.push_back(st);
+    }
+    // FP8: which tensors get an FP8 copy, which are FP8 only
+    if (f->precision == NVISR_PREC_FP8) {
+        std::vector<int> f8_uses(f->tensors.size(), 0), other_uses(f->tensors.size(), 0);
+        for (const Step &s : f->steps) {
+            if (s.fp8) f8_uses[s.in_t]++;
+            else other_uses[s.in_t]++;
+            if (s.add_t >= 0) other_uses[s.add_t]++;
+        }
+        int slot = 0;
+        for (size_t t = 0; t < f->tensors.size(); ++t)
+            if (f8_uses[t]) f->tensors[t].amax_slot = slot++;
+        f->n_amax = slot;
+        for (Step &s : f->steps)
+            if (s.out_t >= 0 && f8_uses[s.out_t] && !other_uses[s.out_t]) s.out_f8_only = true;
+        if (slot) {
+            void *p;
+            nvisr_status st = dalloc(f->eng, sizeof(unsigned) * slot, f->owned, &p);
+            if (st != NVISR_OK) return st;
+            f->amax = (unsigned *)p;
+            f->act_scale.assign(slot, 1.f);
+        }
+    }
+    // liveness-based buffer reuse
+    std::vector<int> last_use(f->tensors.size(), -1);
+    for (size_t i = 0; i < f->steps.size(); ++i) {
+        const Step &s = f->steps[i];
+        last_use[s.in_t] = std::max(last_use[s.in_t], (int)i);
+        if (s.add_t >= 0) last_use[s.add_t] = std::max(last_use[s.add_t], (int)i);
+    }
+    struct Buf { void *p; size_t bytes; int free_after; };
+    std::vector<Buf> pool;
+    auto acquire = [&](size_t bytes, int step, void **out) -> nvisr_status {
+        for (Buf &b : pool)
+            if (b.free_after < step && b.bytes >= bytes) {
+                b.free_after = 1 << 30;
+                *out = b.p;
+                return NVISR_OK;
+            }
+        void *p;
+        nvisr_status s = dalloc(f->eng, bytes, f->owned, &p);
+        if (s != NVISR_OK) return s;
+        pool.push_back({p, bytes, 1 << 30});
+        *out = p;
+        return NVISR_OK;
+    };
+    auto release = [&](void *p, int step) {
+        for (Buf &b : pool)
+            if (b.p == p) b.free_after = step;
+    };
+    // tensor 0 (pack) is produced at step -1
+    std::vector<std::pair<int, int>> producers;  // (step, tensor)
+    if (f->pack_t >= 0) producers.push_back({-1, f->pack_t});
+    for (size_t i = 0; i < f->steps.size(); ++i)
+        if (f->steps[i].out_t >= 0) producers.push_back({(int)i, f->steps[i].out_t});
+    // Allocate in step order; free after last use.  A tensor produced at step
+    // i must not reuse a buffer still read at step i (free_after < i).
+    size_t pi = 0;
+    for (int step = -1; step < (int)f->steps.size(); ++step) {
+        while (pi < producers.size() && producers[pi].first == step) {
+            Tensor &t = f->tensors[producers[pi].second];
+            const Step *ps = step >= 0 ? &f->steps[step] : nullptr;
+            const bool only8 = ps && ps->out_f8_only;
+            if (!only8) {
+                nvisr_status s = acquire((size_t)t.cpad * t.H * t.W * dtype_size(t.dt), step, &t.ptr);
+                if (s != NVISR_OK) return s;
+            }
+            if (t.amax_slot >= 0) {
+                nvisr_status s = acquire((size_t)t.cpad * t.H * t.W, step, &t.f8);
+                if (s != NVISR_OK) return s;
+                if (only8) t.ptr = nullptr;
+            }
+            ++pi;
+        }
+        for (size_t t = 0; t < f->tensors.size(); ++t)
+            if (last_use[t] == step) {
+                if (f->tensors[t].ptr) release(f->tensors[t].ptr, step);
+                if (f->tensors[t].f8) release(f->tensors[t].f8, step);
+            }
+    }
+    // FP8 calibration needs the 16-bit tensors of FP8-only layers too
+    if (f->precision == NVISR_PREC_FP8)
+        for (Tensor &t : f->tensors)
+            if (!t.ptr) {
+                nvisr_status s = dalloc(f->eng, (size_t)t.cpad * t.H * t.W * dtype_size(t.dt), f->owned, &t.ptr);
+                if (s != NVISR_OK) return s;
+            }
+    return NVISR_OK;
+}
+
+// Runs one conv step.  calib: 16-bit pass recording amax of FP8-consumed tensors.
+nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames, bool calib, int out_slot) {
+    const NetLayer &L = f->net.layers[s.layer];
+    const Weights &Wt = f->weights[s.layer];
+    const Tensor &in = f->tensors[s.in_t];
+    cudaStream_t st = f->eng->stream;
+    ConvArgs a{};
+    a.cin_pad = in.cpad;
+    a.H = in.H;
+    a.W = in.W;
+    a.nimg = 1;
+    a.bias = Wt.bias;
+    a.cout = L.cout;
+    a.cout_pad = Wt.cout_pad;
+    a.k = L.k;
+    a.act = L.act;
+    a.acc_scale = 1.f;
+    a.out_scale = 1.f;
+    a.y2_scale = 1.f;
+    a.in_dt = in.dt;
+    a.out_dt = f->act_dt;
+    a.err = f->eng->err_word;
+    const bool use_f8 = s.fp8 && !calib && f->calibrated;
+    if (use_f8) {
+        a.x = in.f8;
+        a.in_dt = DT_E4M3;
+        a.cin_pad = in.cpad;  // 64
+        a.w = Wt.f8;
+        a.acc_scale = f->act_scale[in.amax_slot] * (Wt.w_amax / 448.f);
+    } else {
+        a.x = in.ptr;
+        a.w = Wt.simt_or_tc;
+    }
+    if (s.add_t >= 0) a.res = f->tensors[s.add_t].ptr;
+    if (s.out_t >= 0) {
+        const Tensor &o = f->tensors[s.out_t];
+        a.y = o.ptr;
+        if (!calib && f->calibrated && o.amax_slot >= 0) {
+            const float inv = 1.f / f->act_scale[o.amax_slot];
+            if (s.out_f8_only && use_f8) {
+                a.y = o.f8;
+                a.out_dt = DT_E4M3;
+                a.out_scale = inv;
+            } else {
+                a.y2 = o.f8;
+                a.y2_scale = inv;
+            }
+        }
+        if (calib && o.amax_slot >= 0) a.amax = f->amax + o.amax_slot;
+    } else {
+        a.ps = 2;
+        a.ps_out = f->out_rgb[out_slot];
+        a.ps_pitch = f->opitch;
+        a.skip_mode = f->net.skip;
+        a.skip_scale = f->net.scale;
+        a.skip_h = f->in_fmt.height;
+        a.skip_w = f->in_fmt.width;
+        a.skip_pitch = f->rpitch;
+        a.skip_plane = f->rpitch * f->in_fmt.height;
+        a.nskip = 1;
+        a.skip_src[0] = frames[(f->net.frames - 1) / 2];
+    }
+    const int kind = s.out_t < 0 ? NVISR_K_CONV_TAIL
+                     : (s.src == SRC_TUPLE ? NVISR_K_CONV_HEAD
+                                           : (L.cin == 64 && L.cout == 64 && L.k == 3 ? NVISR_K_CONV_BODY
+                                                                                       : NVISR_K_CONV_OTHER));
+    ProfScope ps(f, kind);
+    cudaError_t e = f->tc ? launch_conv_tc(a, st) : launch_conv_simt(a, st);
+    if (e != cudaSuccess) return cuda_status(e, ("conv layer " + L.name).c_str());
+    return NVISR_OK;
+}
+
+nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, bool calib) {
+    const Tensor &pk = f->tensors[f->pack_t];
+    PackArgs pa{};
+    const float *frames[8];
+    for (size_t k = 0; k < idx.size(); ++k) frames[k] = pa.src[k] = ring_slot(f, idx[k]);
+    pa.nsrc = (int)idx.size();
+    pa.ch_per_src = 3;
+    pa.src_pitch = f->rpitch;
+    pa.src_plane = f->rpitch * f->in_fmt.height;
+    pa.H = pk.H;
+    pa.W = pk.W;
+    pa.dst = pk.ptr;
+    pa.cpad = pk.cpad;
+    pa.dt = pk.dt;
+    pa.scale = 1.f;
+    cudaError_t e;
+    {
+        ProfScope ps(f, NVISR_K_PACK);
+        e = launch_pack(pa, f->eng->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "pack");
+    for (const Step &s : f->steps) {
+        nvisr_status st = run_step(f, s, frames, calib, 0);
+        if (st != NVISR_OK) return st;
+    }
+    return NVISR_OK;
+}
+
+nvisr_status calibrate(nvisr_filter *f) {
+    const int n = (int)std::min<int64_t>(f->calib_frames, f->pushed);
+    std::vector<int64_t> idx;
+    for (int t = 0; t < n; ++t)
+        if (!tuple_ready(f, t, nullptr)) return NVISR_AGAIN;
+    NVISR_TRY_CUDA(cudaMemsetAsync(f->amax, 0, sizeof(unsigned) * f->n_amax, f->eng->stream));
+    for (int t = 0; t < n; ++t) {
+        tuple_ready(f, t, &idx);
+        nvisr_status s = forward_tuple(f, idx, true);
+        if (s != NVISR_OK) return s;
+    }
+    std::vector<unsigned> h(f->n_amax);
+    NVISR_TRY_CUDA(cudaMemcpyAsync(h.data(), f->amax, sizeof(unsigned) * f->n_amax, cudaMemcpyDeviceToHost,
+                                   f->eng->stream));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(f->eng->stream));
+    for (int i = 0; i < f->n_amax; ++i) {
+        float a;
+        memcpy(&a, &h[i], 4);
+        f->act_scale[i] = a > 0.f ? a / 448.f : 1.f;
+    }
+    f->calibrated = true;
+    return NVISR_OK;
+}
+
+// Computes output o into f->out_rgb (tuple family).
+nvisr_status compute_output(nvisr_filter *f, int64_t o) {
+    std::vector<int64_t> idx;
+    if (!tuple_ready(f, o, &idx)) return NVISR_AGAIN;
+    if (f->precision == NVISR_PREC_FP8 && !f->calibrated && f->n_amax > 0) {
+        nvisr_status s = calibrate(f);
+        if (s != NVISR_OK) return s;
+    }
+    return forward_tuple(f, idx, false);
+}
+
+nvisr_status write_output(nvisr_filter *f, nvisr_planes *out, int slot) {
+    cudaStream_t st = f->eng->stream;
+    const nvisr_format &of = f->out_fmt;
+    void *dst[3];
+    int64_t pitch[3];
+    for (int p = 0; p < 3; ++p) {
+        dst[p] = out->on_device ? out->data[p] : f->ostage[p];
+        pitch[p] = out->on_device ? out->pitch[p] : f->ostage_pitch[p];
+    }
+    cudaError_t e;
+    {
+        ProfScope ps(f, NVISR_K_REQUANT);
+        e = launch_requant(of, f->out_rgb[slot], f->opitch, dst[0], pitch[0], dst[1], pitch[1], dst[2], pitch[2], st);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "requant");
+    if (out->on_device) return NVISR_OK;
+    for (int p = 0; p < 3; ++p)
+        NVISR_TRY_CUDA(cudaMemcpy2DAsync(out->data[p], out->pitch[p], f->ostage[p], f->ostage_pitch[p],
+                                         plane_row_bytes(of, p), plane_rows(of, p), cudaMemcpyDeviceToHost, st));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+    return check_device_error(f);
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+
+extern "C" {
+
+int32_t nvisr_abi_version(void) { return NVISR_ABI_VERSION; }
+
+const char *nvisr_build_info(void) {
+    return "nvisr sm_103a (tcgen05/TMA tensor-core conv, FP32 SIMT conv, ingest, requantise)";
+}
+
+const char *nvisr_status_string(nvisr_status s) {
+    switch (s) {
+        case NVISR_OK: return "OK";
+        case NVISR_AGAIN: return "AGAIN";
+        case NVISR_FULL: return "FULL";
+        case NVISR_EOS: return "EOS";
+        case NVISR_INVALID_ARG: return "INVALID_ARG";
+        case NVISR_UNSUPPORTED_FORMAT: return "UNSUPPORTED_FORMAT";
+        case NVISR_OUT_OF_MEMORY: return "OUT_OF_MEMORY";
+        case NVISR_OVER_BUDGET: return "OVER_BUDGET";
+        case NVISR_CUDA_ERROR: return "CUDA_ERROR";
+        case NVISR_DEVICE_TIMEOUT: return "DEVICE_TIMEOUT";
+        case NVISR_BAD_NETWORK: return "BAD_NETWORK";
+        case NVISR_INTERNAL: return "INTERNAL";
+    }
+    return "UNKNOWN";
+}
+
+const char *nvisr_last_error(void) { return g_last_error.c_str(); }
+
+nvisr_status nvisr_network_check(const char *text, int64_t weights_count) {
+    NetDesc net;
+    std::string err;
+    if (!parse_netdesc(text, weights_count, &net, &err)) return fail(NVISR_BAD_NETWORK, err);
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_engine_create(const nvisr_engine_desc *desc, nvisr_engine **out) {
+    if (!desc || !out) return fail(NVISR_INVALID_ARG, "engine_create: NULL argument");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(NVISR_CUDA_ERROR, "no CUDA device");
+    }
+    if (desc->device < 0 || desc->device >= ndev) return fail(NVISR_INVALID_ARG, "bad device ordinal");
+    NVISR_TRY_CUDA(cudaSetDevice(desc->device));
+    auto *e = new nvisr_engine();
+    e->device = desc->device;
+    e->max_filters = desc->max_filters;
+    e->budget = desc->hbm_budget_bytes;
+    if (desc->stream) {
+        e->stream = (cudaStream_t)desc->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete e;
+            return fail(NVISR_CUDA_ERROR, "cudaStreamCreate failed");
+        }
+        e->own_stream = true;
+    }
+    if (cudaMalloc(&e->err_word, sizeof(int)) != cudaSuccess || cudaMemset(e->err_word, 0, sizeof(int)) != cudaSuccess) {
+        if (e->own_stream) cudaStreamDestroy(e->stream);
+        delete e;
+        return fail(NVISR_OUT_OF_MEMORY, "error word allocation failed");
+    }
+    *out = e;
+    return NVISR_OK;
+}
+
+void nvisr_filter_destroy(nvisr_filter *f) {
+    if (!f) return;
+    nvisr_engine *e = f->eng;
+    cudaSetDevice(e->device);
+    cudaStreamSynchronize(e->stream);
+    flush_profile(f);
+    for (cudaEvent_t ev : f->ev_pool) cudaEventDestroy(ev);
+    for (DevBuf &b : f->owned) {
+        cudaFree(b.ptr);
+        e->used -= (int64_t)b.bytes;
+    }
+    e->filters.erase(std::remove(e->filters.begin(), e->filters.end(), f), e->filters.end());
+    delete f;
+}
+
+void nvisr_engine_destroy(nvisr_engine *e) {
+    if (!e) return;
+    while (!e->filters.empty()) nvisr_filter_destroy(e->filters.back());
+    cudaSetDevice(e->device);
+    cudaStreamSynchronize(e->stream);
+    cudaFree(e->err_word);
+    if (e->own_stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+void *nvisr_engine_stream(nvisr_engine *e) { return e ? (void *)e->stream : nullptr; }
+
+int64_t nvisr_engine_bytes_in_use(nvisr_engine *e) { return e ? e->used : 0; }
+
+nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nvisr_filter **out) {
+    if (!e || !d || !out) return fail(NVISR_INVALID_ARG, "filter_create: NULL argument");
+    *out = nullptr;
+    if (e->max_filters > 0 && (int)e->filters.size() >= e->max_filters)
+        return fail(NVISR_OVER_BUDGET, "engine already holds max_filters filters");
+    if (!d->weights && d->weights_count > 0) return fail(NVISR_INVALID_ARG, "weights NULL");
+    if (d->precision < NVISR_PREC_FP32 || d->precision > NVISR_PREC_FP8)
+        return fail(NVISR_INVALID_ARG, "unknown precision");
+    if (!fmt_ok(d->in_fmt) || !fmt_ok(d->out_fmt)) return fail(NVISR_UNSUPPORTED_FORMAT, "unsupported pixel format");
+    std::unique_ptr<nvisr_filter> f(new nvisr_filter());
+    std::string err;
+    if (!parse_netdesc(d->network_text, d->weights_count, &f->net, &err)) return fail(NVISR_BAD_NETWORK, err);
+    const NetDesc &net = f->net;
+    if (d->scale_w != net.scale || d->scale_h != net.scale)
+        return fail(NVISR_INVALID_ARG, "scale does not match the network description");
+    if (d->out_fmt.width != d->in_fmt.width * net.scale || d->out_fmt.height != d->in_fmt.height * net.scale)
+        return fail(NVISR_INVALID_ARG, "output size must be scale x input size");
+    if (net.align != 1) return fail(NVISR_UNSUPPORTED_FORMAT, "network stride alignment > 1 is not supported");
+    if (net.family == "tuple" && (net.frames % 2 == 0 || net.frames > 8))
+        return fail(NVISR_UNSUPPORTED_FORMAT, "tuple networks need an odd frame count <= 7");
+    if (net.family == "group")
+        return fail(NVISR_UNSUPPORTED_FORMAT, "group-family networks are not supported by this build");
+    cudaSetDevice(e->device);
+    f->eng = e;
+    f->in_fmt = d->in_fmt;
+    f->out_fmt = d->out_fmt;
+    f->precision = d->precision;
+    f->tc = d->precision != NVISR_PREC_FP32;
+    f->act_dt = d->precision == NVISR_PREC_FP32 ? DT_F32 : (d->precision == NVISR_PREC_FP16 ? DT_F16 : DT_BF16);
+    f->calib_frames = d->calib_frames > 0 ? d->calib_frames : 4;
+    const int H = d->in_fmt.height, W = d->in_fmt.width;
+    nvisr_status s;
+    auto cleanup = [&](nvisr_status st) {
+        for (DevBuf &b : f->owned) {
+            cudaFree(b.ptr);
+            e->used -= (int64_t)b.bytes;
+        }
+        f->owned.clear();
+        return st;
+    };
+    // ring of ingested frames
+    f->ring = net.frames + 2;
+    f->rpitch = round_up64(W, 4);
+    f->slot_floats = 3 * f->rpitch * H;
+    void *p;
+    if ((s = dalloc(e, sizeof(float) * f->slot_floats * f->ring, f->owned, &p)) != NVISR_OK) return cleanup(s);
+    f->ring_base = (float *)p;
+    for (int pl = 0; pl < 3; ++pl) {
+        int rows;
+        const int64_t bytes = plane_bytes(d->in_fmt, pl, &f->stage_pitch[pl], &rows);
+        if ((s = dalloc(e, bytes, f->owned, &f->stage[pl])) != NVISR_OK) return cleanup(s);
+        const int64_t obytes = plane_bytes(d->out_fmt, pl, &f->ostage_pitch[pl], &rows);
+        if ((s = dalloc(e, obytes, f->owned, &f->ostage[pl])) != NVISR_OK) return cleanup(s);
+    }
+    f->opitch = round_up64((int64_t)W * net.scale, 4);
+    for (int k = 0; k < 2; ++k) {
+        if ((s = dalloc(e, sizeof(float) * 3 * f->opitch * H * net.scale, f->owned, &p)) != NVISR_OK)
+            return cleanup(s);
+        f->out_rgb[k] = (float *)p;
+    }
+    if ((s = prepare_weights(f.get(), d->weights)) != NVISR_OK) return cleanup(s);
+    if ((s = build_plan(f.get())) != NVISR_OK) return cleanup(s);
+    e->filters.push_back(f.get());
+    *out = f.release();
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_push(nvisr_filter *f, const nvisr_planes *in, uint32_t flags) {
+    if (!f || !in) return fail(NVISR_INVALID_ARG, "push: NULL argument");
+    if (f->eos) return fail(NVISR_EOS, "push after flush");
+    for (int p = 0; p < 3; ++p)
+        if (!in->data[p] || in->pitch[p] < plane_row_bytes(f->in_fmt, p))
+            return fail(NVISR_INVALID_ARG, "push: plane " + std::to_string(p) + " NULL or pitch too small");
+    // the slot overwritten by this frame must not be needed by a pending output
+    const int r = f->net.family == "tuple" ? (f->net.frames - 1) / 2 : 0;
+    const int64_t oldest_needed = f->net.family == "tuple" ? f->next_out - r : f->next_out / 2;
+    if (f->pushed - f->ring >= std::max<int64_t>(oldest_needed, 0) && f->pushed >= f->ring)
+        return NVISR_FULL;
+    cudaSetDevice(f->eng->device);
+    cudaStream_t st = f->eng->stream;
+    const void *src[3];
+    int64_t pitch[3];
+    for (int p = 0; p < 3; ++p) {
+        if (in->on_device) {
+            src[p] = in->data[p];
+            pitch[p] = in->pitch[p];
+        } else {
+            NVISR_TRY_CUDA(cudaMemcpy2DAsync(f->stage[p], f->stage_pitch[p], in->data[p], in->pitch[p],
+                                             plane_row_bytes(f->in_fmt, p), plane_rows(f->in_fmt, p),
+                                             cudaMemcpyHostToDevice, st));
+            src[p] = f->stage[p];
+            pitch[p] = f->stage_pitch[p];
+        }
+    }
+    cudaError_t e;
+    {
+        ProfScope ps(f, NVISR_K_INGEST);
+        e = launch_ingest(f->in_fmt, src[0], pitch[0], src[1], pitch[1], src[2], pitch[2], ring_slot(f, f->pushed),
+                          f->rpitch, st);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "ingest");
+    if (!in->on_device) NVISR_TRY_CUDA(cudaStreamSynchronize(st));  // host planes may be reused on return
+    f->cut.push_back((flags & NVISR_FRAME_SCENE_CUT) && f->pushed > 0 ? 1 : 0);
+    f->pushed++;
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_flush(nvisr_filter *f) {
+    if (!f) return fail(NVISR_INVALID_ARG, "flush: NULL filter");
+    f->eos = true;
+    f->total_out = f->pushed * outputs_per_input(f);
+    return NVISR_OK;
+}
+
+int64_t nvisr_filter_ready(nvisr_filter *f) {
+    if (!f) return 0;
+    int64_t n = 0;
+    const int64_t end = f->pushed * outputs_per_input(f);
+    for (int64_t o = f->next_out; o < end && output_ready(f, o); ++o) ++n;
+    return n;
+}
+
+nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *info) {
+    if (!f || !out) return fail(NVISR_INVALID_ARG, "pull: NULL argument");
+    for (int p = 0; p < 3; ++p)
+        if (!out->data[p] || out->pitch[p] < plane_row_bytes(f->out_fmt, p))
+            return fail(NVISR_INVALID_ARG, "pull: plane " + std::to_string(p) + " NULL or pitch too small");
+    if (f->eos && f->next_out >= f->total_out) return NVISR_EOS;
+    const int64_t o = f->next_out;
+    if (!output_ready(f, o)) return NVISR_AGAIN;
+    cudaSetDevice(f->eng->device);
+    nvisr_status s;
+    bool have = !f->produced.empty() && f->produced.front() == o;
+    if (!have) {
+        s = compute_output(f, o);
+        if (s != NVISR_OK) return s;
+    } else {
+        f->produced.pop_front();
+    }
+    if ((s = write_output(f, out, 0)) != NVISR_OK) return s;
+    if (info) {
+        std::vector<int64_t> idx;
+        tuple_ready(f, o, &idx);
+        int64_t s0, s1;
+        bool closed;
+        scene_bounds(f, o, &s0, &s1, &closed);
+        int scene = 0;
+        for (int64_t k = 1; k <= o; ++k) scene += f->cut[(size_t)k];
+        info->index = o;
+        info->src_first = idx.front();
+        info->src_last = idx.back();
+        info->scene = scene;
+    }
+    f->next_out++;
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_filter_profile(nvisr_filter *f, int32_t enable) {
+    if (!f) return fail(NVISR_INVALID_ARG, "profile: NULL filter");
+    flush_profile(f);
+    if (enable) {
+        for (int k = 0; k < NVISR_K_COUNT; ++k) {
+            f->prof_ms[k] = 0;
+            f->prof_n[k] = 0;
+        }
+    }
+    f->prof = enable != 0;
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_filter_profile_read(nvisr_filter *f, nvisr_profile *out) {
+    if (!f || !out) return fail(NVISR_INVALID_ARG, "profile_read: NULL argument");
+    flush_profile(f);
+    for (int k = 0; k < NVISR_K_COUNT; ++k) {
+        out->ms[k] = f->prof_ms[k];
+        out->launches[k] = f->prof_n[k];
+    }
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_engine_step(nvisr_engine *e, int32_t max_outputs, int32_t *produced) {
+    if (!e) return fail(NVISR_INVALID_ARG, "engine_step: NULL engine");
+    int n = 0;
+    for (nvisr_filter *f : e->filters) {
+        if (n >= max_outputs) break;
+        if (!f->produced.empty()) continue;  // one computed output buffered per filter
+        const int64_t o = f->next_out;
+        if (f->eos && o >= f->total_out) continue;
+        if (!output_ready(f, o)) continue;
+        nvisr_status s = compute_output(f, o);
+        if (s == NVISR_AGAIN) continue;
+        if (s != NVISR_OK) return s;
+        f->produced.push_back(o);
+        ++n;
+    }
+    if (produced) *produced = n;
+    return NVISR_OK;
+}
+
+// ---------------------------------------------------------------- stages
+
+nvisr_status nvisr_ingest(const nvisr_format *fmt, const nvisr_planes *in, float *out, int64_t out_pitch,
+                          void *stream) {
+    if (!fmt || !in || !out || !in->on_device) return fail(NVISR_INVALID_ARG, "ingest: bad arguments");
+    if (!fmt_ok(*fmt)) return fail(NVISR_UNSUPPORTED_FORMAT, "ingest: unsupported format");
+    if (out_pitch < fmt->width) return fail(NVISR_INVALID_ARG, "ingest: pitch < width");
+    cudaError_t e = launch_ingest(*fmt, in->data[0], in->pitch[0], in->data[1], in->pitch[1], in->data[2],
+                                  in->pitch[2], out, out_pitch, (cudaStream_t)stream);
+    return e == cudaSuccess ? NVISR_OK : cuda_status(e, "ingest");
+}
+
+nvisr_status nvisr_requant(const nvisr_format *fmt, const float *in, int64_t in_pitch, nvisr_planes *out,
+                           void *stream) {
+    if (!fmt || !in || !out || !out->on_device) return fail(NVISR_INVALID_ARG, "requant: bad arguments");
+    if (!fmt_ok(*fmt)) return fail(NVISR_UNSUPPORTED_FORMAT, "requant: unsupported format");
+    if (in_pitch < fmt->width) return fail(NVISR_INVALID_ARG, "requant: pitch < width");
+    cudaError_t e = launch_requant(*fmt, in, in_pitch, out->data[0], out->pitch[0], out->data[1], out->pitch[1],
+                                   out->data[2], out->pitch[2], (cudaStream_t)stream);
+    return e == cudaSuccess ? NVISR_OK : cuda_status(e, "requant");
+}
+
+nvisr_status nvisr_tuple_map(const uint8_t *flags, int32_t nframes, int32_t T, int32_t *out) {
+    if (!flags || !out || nframes < 0 || T < 1 || T % 2 == 0) return fail(NVISR_INVALID_ARG, "tuple_map: bad arguments");
+    const int r = (T - 1) / 2;
+    int s0 = 0;
+    for (int t = 0; t < nframes; ++t) {
+        if (t > 0 && flags[t]) s0 = t;
+        int s1 = t;
+        while (s1 + 1 < nframes && !flags[s1 + 1]) ++s1;
+        for (int k = 0; k < T; ++k) out[t * T + k] = std::min(std::max(t - r + k, s0), s1);
+    }
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_group_runs(int32_t s0, int32_t s1, int32_t n, int32_t extra, int32_t interp, int32_t max_runs,
+                              int32_t *out_inputs, int32_t *out_skip, int32_t *nruns) {
+    if (n < 1 || s1 < s0 || !out_inputs || !out_skip || !nruns) return fail(NVISR_INVALID_ARG, "group_runs: bad arguments");
+    const int need = n + (extra ? 1 : 0);
+    const int len = s1 - s0 + 1;
+    int count = 0;
+    for (int nominal = s0; nominal <= s1; nominal += n) {
+        if (count >= max_runs) return fail(NVISR_INVALID_ARG, "group_runs: max_runs too small");
+        int start = nominal;
+        if (!interp && start + need - 1 > s1 && len >= need) start = s1 - need + 1;
+        for (int k = 0; k < need; ++k) out_inputs[count * need + k] = std::min(start + k, s1);
+        out_skip[count] = nominal - start;
+        ++count;
+    }
+    *nruns = count;
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_fig1_layout(int32_t n, int32_t b, int32_t *cell_frame, int32_t *slot_start, int32_t *copy) {
+    if (n < 1 || b < 1 || !cell_frame || !slot_start || !copy) return fail(NVISR_INVALID_ARG, "fig1_layout: bad arguments");
+    // column-first store of b rows x (n+1) columns: address = col * b + row
+    for (int a = 0; a < (n + 1) * b; ++a) cell_frame[a] = -1;
+    cell_frame[b - 1] = 0;
+    for (int r = 0; r < b; ++r) {
+        cell_frame[1 * b + r] = (r + 1) * n;
+        for (int k = 1; k < n; ++k) cell_frame[(k + 1) * b + r] = r * n + k;
+    }
+    slot_start[0] = b - 1;
+    for (int k = 1; k < n; ++k) slot_start[k] = (k + 1) * b;
+    slot_start[n] = b;
+    copy[0] = 2 * b - 1;
+    copy[1] = b - 1;
+    return NVISR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- per-call layer entry points
+
+namespace {
+
+struct Scratch {
+    std::vector<void *> ptrs;
+    ~Scratch() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    cudaError_t alloc(size_t bytes, void **out) {
+        cudaError_t e = cudaMalloc(out, std::max<size_t>(bytes, 256));
+        if (e == cudaSuccess) ptrs.push_back(*out);
+        return e;
+    }
+};
+
+// Quantisation scale (amax / 448) of a planar tensor, measured on the device.
+nvisr_status fp8_scale(const float *x, int C, int H, int W, Scratch &sc, cudaStream_t st, float *scale) {
+    void *tmp, *am;
+    const int cpad = round_up(C, 8);
+    NVISR_TRY_CUDA(sc.alloc((size_t)cpad * H * W * 2, &tmp));
+    NVISR_TRY_CUDA(sc.alloc(sizeof(unsigned), &am));
+    NVISR_TRY_CUDA(cudaMemsetAsync(am, 0, sizeof(unsigned), st));
+    PackArgs pa{};
+    pa.src[0] = x;
+    pa.nsrc = 1;
+    pa.ch_per_src = C;
+    pa.src_pitch = W;
+    pa.src_plane = (int64_t)W * H;
+    pa.H = H;
+    pa.W = W;
+    pa.dst = tmp;
+    pa.cpad = cpad;
+    pa.dt = DT_BF16;
+    pa.scale = 1.f;
+    pa.amax = (unsigned *)am;
+    NVISR_TRY_CUDA(launch_pack(pa, st));
+    unsigned h;
+    NVISR_TRY_CUDA(cudaMemcpyAsync(&h, am, 4, cudaMemcpyDeviceToHost, st));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+    float a;
+    memcpy(&a, &h, 4);
+    *scale = a > 0.f ? a / 448.f : 1.f;
+    return NVISR_OK;
+}
+
+nvisr_status pack_planar(const float *x, int C, int cpad, int H, int W, int dt, float scale, void *dst,
+                         cudaStream_t st) {
+    PackArgs pa{};
+    pa.src[0] = x;
+    pa.nsrc = 1;
+    pa.ch_per_src = C;
+    pa.src_pitch = W;
+    pa.src_plane = (int64_t)W * H;
+    pa.H = H;
+    pa.W = W;
+    pa.dst = dst;
+    pa.cpad = cpad;
+    pa.dt = dt;
+    pa.scale = scale;
+    NVISR_TRY_CUDA(launch_pack(pa, st));
+    return NVISR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_t h, int32_t w, const float *weight,
+                          const float *bias, int32_t cout, int32_t k, int32_t act, const float *res, float *y,
+                          void *stream) {
+    if (!x || !weight || !y || cin < 1 || cout < 1 || h < 1 || w < 1 || (k != 1 && k != 3) || act < 0 || act > 1)
+        return fail(NVISR_INVALID_ARG, "conv2d: bad arguments");
+    if (precision < NVISR_PREC_FP32 || precision > NVISR_PREC_FP8) return fail(NVISR_INVALID_ARG, "conv2d: precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool tc = precision != NVISR_PREC_FP32;
+    const int adt = precision == NVISR_PREC_FP32 ? DT_F32 : (precision == NVISR_PREC_FP16 ? DT_F16 : DT_BF16);
+    const int idt = precision == NVISR_PREC_FP8 ? DT_E4M3 : adt;
+    if (precision == NVISR_PREC_FP8 && (cin % 64 || cout != 64 || k != 3))
+        return fail(NVISR_UNSUPPORTED_FORMAT, "conv2d: FP8 supports 64->64 3x3 layers");
+    const int cin_pad = tc ? round_up(cin, idt == DT_E4M3 ? 16 : 16) : round_up(cin, 8);
+    const int cout_pad = round_up(cout, 16);
+    Scratch sc;
+    // weights (host copy -> layout -> device)
+    std::vector<float> hw((size_t)cout * cin * k * k), hb(cout_pad, 0.f);
+    NVISR_TRY_CUDA(cudaMemcpyAsync(hw.data(), weight, hw.size() * 4, cudaMemcpyDeviceToHost, st));
+    if (bias) NVISR_TRY_CUDA(cudaMemcpyAsync(hb.data(), bias, (size_t)cout * 4, cudaMemcpyDeviceToHost, st));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+    float sx = 1.f, sw = 1.f;
+    if (idt == DT_E4M3) {
+        nvisr_status s = fp8_scale(x, cin, h, w, sc, st, &sx);
+        if (s != NVISR_OK) return s;
+        float amax = 0.f;
+        for (float v : hw) amax = std::max(amax, std::fabs(v));
+        sw = amax > 0.f ? amax / 448.f : 1.f;
+    }
+    void *dw, *db, *dx, *dy, *dr = nullptr;
+    size_t wbytes;
+    std::vector<uint8_t> hwl;
+    if (tc) {
+        wbytes = tc_weight_bytes(cin_pad, cout_pad, k, idt);
+        hwl.resize(wbytes);
+        prepare_weights_tc(hw.data(), cout, cin, k, cin_pad, cout_pad, idt, 1.f / sw, hwl.data());
+    } else {
+        wbytes = simt_weight_bytes(cin_pad, cout_pad, k);
+        hwl.resize(wbytes);
+        prepare_weights_simt(hw.data(), cout, cin, k, cin_pad, cout_pad, (float *)hwl.data());
+    }
+    NVISR_TRY_CUDA(sc.alloc(wbytes, &dw));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(dw, hwl.data(), wbytes, cudaMemcpyHostToDevice, st));
+    NVISR_TRY_CUDA(sc.alloc(cout_pad * 4, &db));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(db, hb.data(), cout_pad * 4, cudaMemcpyHostToDevice, st));
+    NVISR_TRY_CUDA(sc.alloc((size_t)cin_pad * h * w * dtype_size(idt), &dx));
+    NVISR_TRY_CUDA(sc.alloc((size_t)cout_pad * h * w * dtype_size(adt), &dy));
+    nvisr_status s = pack_planar(x, cin, cin_pad, h, w, idt, 1.f / sx, dx, st);
+    if (s != NVISR_OK) return s;
+    if (res) {
+        NVISR_TRY_CUDA(sc.alloc((size_t)cout_pad * h * w * dtype_size(adt), &dr));
+        if ((s = pack_planar(res, cout, cout_pad, h, w, adt, 1.f, dr, st)) != NVISR_OK) return s;
+    }
+    int *err;
+    NVISR_TRY_CUDA(sc.alloc(sizeof(int), (void **)&err));
+    NVISR_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    ConvArgs a{};
+    a.x = dx; a.cin_pad = cin_pad; a.H = h; a.W = w; a.nimg = 1; a.w = dw; a.bias = (const float *)db;
+    a.cout = cout; a.cout_pad = cout_pad; a.k = k; a.act = act; a.res = dr; a.y = dy;
+    a.in_dt = idt; a.out_dt = adt; a.acc_scale = sx * sw; a.out_scale = 1.f; a.y2_scale = 1.f; a.err = err;
+    cudaError_t e = tc ? launch_conv_tc(a, st) : launch_conv_simt(a, st);
+    if (e != cudaSuccess) return cuda_status(e, "conv2d");
+    NVISR_TRY_CUDA(launch_unpack(dy, adt, cout_pad, cout, h, w, 1.f, y, w, st));
+    int herr = 0;
+    NVISR_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+    if (herr) return fail(NVISR_DEVICE_TIMEOUT, "conv2d: a device-side wait exceeded its bound");
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t h, int32_t w, const float *offsets,
+                         const float *mask, int32_t groups, const float *weight, const float *bias, int32_t cout,
+                         float *y, void *stream) {
+    if (!x || !offsets || !mask || !weight || !y || cin < 1 || cout < 1 || h < 1 || w < 1 || groups < 1 ||
+        cin % groups)
+        return fail(NVISR_INVALID_ARG, "dcn2d: bad arguments");
+    if (precision != NVISR_PREC_FP32) return fail(NVISR_UNSUPPORTED_FORMAT, "dcn2d: only FP32 in this build");
+    if ((cin / groups) % 4) return fail(NVISR_UNSUPPORTED_FORMAT, "dcn2d: channels per group must be a multiple of 4");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int cin_pad = round_up(cin, 8), cout_pad = round_up(cout, 16);
+    if (cin_pad != cin) return fail(NVISR_UNSUPPORTED_FORMAT, "dcn2d: cin must be a multiple of 8");
+    Scratch sc;
+    std::vector<float> hw((size_t)cout * cin * 9), hb(cout_pad, 0.f);
+    NVISR_TRY_CUDA(cudaMemcpyAsync(hw.data(), weight, hw.size() * 4, cudaMemcpyDeviceToHost, st));
+    if (bias) NVISR_TRY_CUDA(cudaMemcpyAsync(hb.data(), bias, (size_t)cout * 4, cudaMemcpyDeviceToHost, st));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+    std::vector<float> hwl(simt_weight_bytes(cin_pad, cout_pad, 3) / 4);
+    prepare_weights_simt(hw.data(), cout, cin, 3, cin_pad, cout_pad, hwl.data());
+    void *dw, *db, *dx, *dy;
+    NVISR_TRY_CUDA(sc.alloc(hwl.size() * 4, &dw));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(dw, hwl.data(), hwl.size() * 4, cudaMemcpyHostToDevice, st));
+    NVISR_TRY_CUDA(sc.alloc(cout_pad * 4, &db));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(db, hb.data(), cout_pad * 4, cudaMemcpyHostToDevice, st));
+    NVISR_TRY_CUDA(sc.alloc((size_t)cin_pad * h * w * 4, &dx));
+    NVISR_TRY_CUDA(sc.alloc((size_t)cout_pad * h * w * 4, &dy));
+    nvisr_status s = pack_planar(x, cin, cin_pad, h, w, DT_F32, 1.f, dx, st);
+    if (s != NVISR_OK) return s;
+    DcnArgs d{};
+    d.x = dx; d.cin_pad = cin_pad; d.H = h; d.W = w; d.groups = groups;
+    d.off = offsets; d.mask = mask; d.om_pitch = w; d.om_plane = (int64_t)w * h; d.mask_logits = 0;
+    d.w = dw; d.bias = (const float *)db; d.cout = cout; d.cout_pad = cout_pad; d.y = dy;
+    d.in_dt = DT_F32; d.out_dt = DT_F32; d.acc_scale = 1.f; d.out_scale = 1.f;
+    cudaError_t e = launch_dcn_simt(d, st);
+    if (e != cudaSuccess) return cuda_status(e, "dcn2d");
+    NVISR_TRY_CUDA(launch_unpack(dy, DT_F32, cout_pad, cout, h, w, 1.f, y, w, st));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_selftest(int32_t *mismatches_bf16, int32_t *mismatches_fp8) {
+    if (!mismatches_bf16 || !mismatches_fp8) return fail(NVISR_INVALID_ARG, "selftest: NULL argument");
+    int *d;
+    NVISR_TRY_CUDA(cudaMalloc(&d, 2 * sizeof(int)));
+    cudaMemset(d, 0, 2 * sizeof(int));
+    int e1 = tc_selftest(0, d, 0);
+    int e2 = tc_selftest(1, d + 1, 0);
+    cudaError_t se = cudaDeviceSynchronize();
+    int h[2] = {-1, -1};
+    cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e1 || e2 || se != cudaSuccess)
+        return fail(NVISR_CUDA_ERROR, std::string("selftest launch: ") + cudaGetErrorString(se));
+    *mismatches_bf16 = h[0];
+    *mismatches_fp8 = h[1];
+    return NVISR_OK;
+}
+
+}  // extern "C"

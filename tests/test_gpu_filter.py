@@ -1,0 +1,219 @@
+"""End-to-end parity of the filter (push / pull through the C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2308_03121_gb300 as nv
+import synth
+from gpu_util import (assert_codes_match, crop_codes, fmt_dict, lsb_stats, oracle_window, prequant,
+                      to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nv.load()
+
+
+def run_gpu(text, blob, frames, flags, fin, fout, prec, scale=2, device_io=False, limit=None):
+    """Push every frame (pulling whenever the ring is full) and pull all outputs."""
+    eng = nv.Engine()
+    flt = eng.filter(text, blob, fin, fout, prec, scale)
+    outs, infos = [], []
+
+    def pull_one():
+        if device_io:
+            h = flt.alloc_out_host()
+            buf = tuple(to_dev(a) for a in h)
+            st, info = flt.pull(buf)
+            res = tuple(b.cpu().numpy() for b in buf)
+            res = tuple(r.view(np.uint16) if r.dtype == np.int16 else r for r in res)
+        else:
+            res = flt.alloc_out_host()
+            st, info = flt.pull(res)
+        if st == nv.Status.OK:
+            outs.append({k: r.astype(np.int64) for k, r in zip("YUV", res)})
+            infos.append((info.index, info.src_first, info.src_last))
+        return st
+
+    for i, fr in enumerate(frames):
+        planes = (fr["Y"], fr["U"], fr["V"])
+        if device_io:
+            planes = tuple(to_dev(p) for p in planes)
+        while flt.push(planes, cut=bool(flags[i])) == nv.Status.FULL:
+            assert pull_one() == nv.Status.OK
+        while flt.ready() > 0 and (limit is None or len(outs) < limit):
+            assert pull_one() == nv.Status.OK
+    flt.flush()
+    while limit is None or len(outs) < limit:
+        st = pull_one()
+        if st == nv.Status.EOS:
+            break
+        assert st == nv.Status.OK
+    eng.close()
+    return outs, infos
+
+
+def _config1():
+    frames = synth.frames_gradient(synth.BASE_SEED + 1, 16, 64, 64, 8, "420", "full")
+    flags = np.zeros(16, bool)
+    flags[9] = True
+    fd_in = fmt_dict(64, 64, 8, "420", "full")
+    fd_out = fmt_dict(128, 128, 8, "420", "full")
+    return frames, flags, fd_in, fd_out
+
+
+@pytest.fixture(scope="module")
+def config1_oracle():
+    frames, flags, fdi, fdo = _config1()
+    text, blob = synth.net_config1()
+    flt = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
+    return [prequant(o, fdo) for o in flt]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_config1_filter_within_1lsb(prec, config1_oracle):
+    frames, flags, fdi, fdo = _config1()
+    text, blob = synth.net_config1()
+    outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(64, 64, 8, "420", "full"),
+                          nv.fmt(128, 128, 8, "420", "full"), prec)
+    assert len(outs) == 16
+    assert [i[0] for i in infos] == list(range(16))
+    assert infos[8][1:] == (7, 8) and infos[9][1:] == (9, 10)    # scene cut on frame 9
+    for got, pq in zip(outs, config1_oracle):
+        if prec == "fp32":
+            assert_codes_match(got, pq, 8)
+        else:
+            exp = {k: oracle.quantise(pq[k], 8) for k in "YUV"}
+            mx, _ = lsb_stats(got, exp)
+            assert mx <= 1, mx
+
+
+def test_config1_device_io_matches_host_io():
+    frames, flags, _, _ = _config1()
+    text, blob = synth.net_config1()
+    fi, fo = nv.fmt(64, 64, 8, "420", "full"), nv.fmt(128, 128, 8, "420", "full")
+    a, _ = run_gpu(text, blob, frames, flags, fi, fo, "bf16")
+    b, _ = run_gpu(text, blob, frames, flags, fi, fo, "bf16", device_io=True)
+    for x, y in zip(a, b):
+        for k in "YUV":
+            assert np.array_equal(x[k], y[k])
+
+
+def test_scene_cut_poisoning_on_gpu():
+    """Frames outside an output's scene never change it (bit-identical)."""
+    frames, flags, _, _ = _config1()
+    text, blob = synth.net_config1()
+    fi, fo = nv.fmt(64, 64, 8, "420", "full"), nv.fmt(128, 128, 8, "420", "full")
+    base, _ = run_gpu(text, blob, frames, flags, fi, fo, "bf16")
+    poisoned = [dict(f) for f in frames]
+    for i in range(9, 16):
+        poisoned[i] = {k: np.full_like(v, 255 if k == "Y" else 0) for k, v in frames[i].items()}
+    pz, _ = run_gpu(text, blob, poisoned, flags, fi, fo, "bf16")
+    for t in range(9):
+        for k in "YUV":
+            assert np.array_equal(base[t][k], pz[t][k]), (t, k)
+
+
+def _config2_small(W=136, H=70, n=6):
+    frames = synth.frames_textured(synth.BASE_SEED + 2, n, W, H, 10, "420", "limited")
+    flags = np.zeros(n, bool)
+    flags[3] = True
+    return frames, flags
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_config2_network_ragged_size_full_frames(prec):
+    """Config-2 network at 136x70 (ragged 128-pixel tiles, a cut on frame 3), every output."""
+    W, H = 136, 70
+    frames, flags = _config2_small(W, H)
+    text, blob = synth.net_config2()
+    fdi, fdo = fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10)
+    ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 10), nv.fmt(2 * W, 2 * H, 10), prec)
+    assert len(outs) == len(frames)
+    for got, r in zip(outs, ref):
+        pq = prequant(r, fdo)
+        if prec == "fp32":
+            assert_codes_match(got, pq, 10)
+        else:
+            mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 10) for k in "YUV"})
+            assert mx <= 1, mx
+
+
+FULL_WINDOWS = [(0, 16, 0, 16), (0, 16, 1904, 1920), (1064, 1080, 960, 976), (540, 556, 900, 916),
+                (200, 216, 120, 136)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_config2_full_size_sampled_windows(prec):
+    """1920x1080 10-bit, T = 5: outputs 0 (scene start, edge replication) and 3 on sampled windows."""
+    W, H = 1920, 1080
+    frames = synth.frames_textured(synth.BASE_SEED + 2, 6, W, H, 10, "420", "limited")
+    flags = np.zeros(6, bool)
+    text, blob = synth.net_config2()
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 10), nv.fmt(2 * W, 2 * H, 10), prec, limit=4)
+    fdi, fdo = fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10)
+    net = oracle.Net(text, blob)
+    rgb = [oracle.ingest(f, fdi) for f in frames]
+    for t in (0, 3):
+        idx = oracle.tuple_indices(t, 5, 0, 5)
+        for (y0, y1, x0, x1) in FULL_WINDOWS:
+            pq = oracle_window(net, [rgb[i] for i in idx], y0, y1, x0, x1, fdo)
+            got = crop_codes(outs[t], y0, y1, x0, x1, 2, "420")
+            if prec == "fp32":
+                assert_codes_match(got, pq, 10)
+            else:
+                mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 10) for k in "YUV"})
+                assert mx <= 1, (t, (y0, x0), mx)
+
+
+def test_fp8_filter_reports_error_vs_oracle():
+    """FP8 E4M3 (per-tensor scales from frames 0-3) on the ragged config-2 case: bounded error."""
+    W, H = 136, 70
+    frames, flags = _config2_small(W, H)
+    text, blob = synth.net_config2()
+    fdi, fdo = fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10)
+    ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo)
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 10), nv.fmt(2 * W, 2 * H, 10), "fp8")
+    worst = 0
+    for got, r in zip(outs, ref):
+        mx, frac = lsb_stats(got, r)
+        worst = max(worst, mx)
+    print("fp8 max LSB", worst)
+    assert worst <= 16
+
+
+def test_backpressure_full_then_pull():
+    frames, flags, _, _ = _config1()
+    text, blob = synth.net_config1()
+    eng = nv.Engine()
+    flt = eng.filter(text, blob, nv.fmt(64, 64, 8, "420", "full"), nv.fmt(128, 128, 8, "420", "full"), "fp32")
+    n = 0
+    for fr in frames:
+        st = flt.push((fr["Y"], fr["U"], fr["V"]))
+        if st == nv.Status.FULL:
+            break
+        n += 1
+    assert n == 5  # ring of T + 2 = 5 slots with no output pulled
+    out = flt.alloc_out_host()
+    # output 1 still needs frame 0 (its tuple is [0, 1, 2]): two pulls free the slot
+    assert flt.pull(out)[0] == nv.Status.OK
+    assert flt.push((frames[n]["Y"], frames[n]["U"], frames[n]["V"])) == nv.Status.FULL
+    assert flt.pull(out)[0] == nv.Status.OK
+    assert flt.push((frames[n]["Y"], frames[n]["U"], frames[n]["V"])) == nv.Status.OK
+    eng.close()
+
+
+def test_budget_rejects_filter():
+    text, blob = synth.net_config1()
+    eng = nv.Engine(hbm_budget_bytes=1 << 20)
+    with pytest.raises(nv.NvisrError) as e:
+        eng.filter(text, blob, nv.fmt(64, 64, 8, "420", "full"), nv.fmt(128, 128, 8, "420", "full"), "bf16")
+    assert e.value.status == nv.Status.OVER_BUDGET
+    assert eng.bytes_in_use() == 0
+    eng.close()
