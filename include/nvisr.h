@@ -269,6 +269,13 @@ nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t
  * hold).  Runs on the current device; allocates and frees a few bytes. */
 nvisr_status nvisr_selftest(int32_t *mismatches_bf16, int32_t *mismatches_fp8);
 
+/* Probe of the 128-byte-swizzled K-major operand convention the tensor-core
+ * kernels rely on: an MMA chain reading A from row offsets 0..7 inside a
+ * swizzle atom, with descriptor base offset 0 (out16[0..7]) and with base
+ * offset (start >> 7) & 7 (out16[8..15]); each entry counts wrong accumulator
+ * elements (0 = that convention reproduces the stored rows). */
+nvisr_status nvisr_selftest_swizzle(int32_t *out16);
+
 /* Library version / build information. */
 int32_t nvisr_abi_version(void);
 const char *nvisr_build_info(void);

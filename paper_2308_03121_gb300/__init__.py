@@ -108,6 +108,7 @@ _SIGS = {
     "nvisr_conv2d": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _I32, _I32, _VP, _VP, _VP]),
     "nvisr_dcn2d": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP, _VP, _I32, _VP, _VP]),
     "nvisr_selftest": (_I32, [_I32P, _I32P]),
+    "nvisr_selftest_swizzle": (_I32, [_I32P]),
     "nvisr_abi_version": (_I32, []),
     "nvisr_build_info": (ctypes.c_char_p, []),
 }
@@ -258,6 +259,13 @@ def nvisr_selftest():
     a, b = ctypes.c_int32(-1), ctypes.c_int32(-1)
     _check(_LIB.nvisr_selftest(ctypes.byref(a), ctypes.byref(b)), "nvisr_selftest")
     return a.value, b.value
+
+
+def nvisr_selftest_swizzle():
+    load()
+    out = np.zeros(16, np.int32)
+    _check(_LIB.nvisr_selftest_swizzle(out.ctypes.data_as(_I32P)), "nvisr_selftest_swizzle")
+    return out
 
 
 # ------------------------------------------------------------------ engine / filter

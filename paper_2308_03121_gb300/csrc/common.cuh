@@ -114,14 +114,14 @@ void prepare_weights_tc(const float *w_oihw, int cout, int cin, int k, int cin_p
                         int dt, float scale, void *dst_host);
 int tc_nslice(int cin_pad, int cout_pad, int k, int dt);
 
-// DCN: x blocked, offsets/mask planar float32 (mask already in [0,1] unless
-// mask_logits, which applies the logistic function first).
+// DCN: x blocked (activation dtype); offsets and mask in one blocked float32
+// tensor [om_cpad/4][H][W][4]: channels [0, 18G) = (dy, dx) per (group, tap),
+// [18G, 27G) = mask (logits when mask_logits, else already in [0,1]).
 struct DcnArgs {
     const void *x;
     int cin_pad, H, W, groups;
-    const float *off;        // [2*G*9][H][W] planar, pitch off_pitch, plane off_plane
-    const float *mask;       // [G*9][H][W]
-    int64_t om_pitch, om_plane;
+    const float *om;
+    int om_cpad;
     int mask_logits;
     const void *w;           // prepared weights (SIMT or TC layout, k = 3)
     const float *bias;
@@ -129,6 +129,7 @@ struct DcnArgs {
     void *y;
     int in_dt, out_dt;
     float acc_scale, out_scale;
+    int *err;
 };
 cudaError_t launch_dcn_simt(const DcnArgs &a, cudaStream_t st);
 cudaError_t launch_dcn_tc(const DcnArgs &a, cudaStream_t st);

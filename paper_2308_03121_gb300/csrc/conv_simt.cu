@@ -112,10 +112,11 @@ __global__ void __launch_bounds__(16 * NB / 4) conv_simt_kernel(ConvArgs a, DcnA
                 if (xx < W) {
                     const int c = (s * 2 + cl) * 4;
                     const int g = c / cpg;
-                    const int64_t pix = (int64_t)y * d.om_pitch + xx;
-                    const float dy = d.off[(int64_t)(2 * (g * 9 + k)) * d.om_plane + pix];
-                    const float dx = d.off[(int64_t)(2 * (g * 9 + k) + 1) * d.om_plane + pix];
-                    float m = d.mask[(int64_t)(g * 9 + k) * d.om_plane + pix];
+                    const int64_t pix = (int64_t)y * W + xx;
+                    auto omv = [&](int ch) { return d.om[((int64_t)(ch >> 2) * HW + pix) * 4 + (ch & 3)]; };
+                    const float dy = omv(2 * (g * 9 + k));
+                    const float dx = omv(2 * (g * 9 + k) + 1);
+                    float m = omv(18 * d.groups + g * 9 + k);
                     if (d.mask_logits) m = 1.f / (1.f + expf(-m));
                     const float sy = (float)(y + k / 3 - 1) + dy;
                     const float sx = (float)(xx + k % 3 - 1) + dx;

@@ -76,6 +76,8 @@ template <>
 struct Elem<DT_F16> { using T = __half; };
 template <>
 struct Elem<DT_E4M3> { using T = __nv_fp8_e4m3; };
+template <>
+struct Elem<DT_F32> { using T = float; };
 
 template <typename T>
 __device__ __forceinline__ T to_elem(float v);
@@ -85,6 +87,8 @@ template <>
 __device__ __forceinline__ __half to_elem<__half>(float v) { return __float2half_rn(v); }
 template <>
 __device__ __forceinline__ __nv_fp8_e4m3 to_elem<__nv_fp8_e4m3>(float v) { return __nv_fp8_e4m3(v); }
+template <>
+__device__ __forceinline__ float to_elem<float>(float v) { return v; }
 
 template <typename T>
 __device__ __forceinline__ float from_elem(T v) { return (float)v; }
@@ -130,7 +134,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
     constexpr int PXS = TM + KS - 1;
     constexpr int PAD = (KS - 1) / 2;
     constexpr uint32_t LBO_A = ROWS * PXS * 16;
-    constexpr uint32_t STAGE_BYTES = NCH * LBO_A;
+    // TMA destinations must be 128-byte aligned: stages are padded to 1 KB.
+    constexpr uint32_t STAGE_BYTES = (NCH * LBO_A + 1023u) & ~1023u;
     constexpr uint32_t NCOLS = (2 * NS <= 32) ? 32 : (2 * NS <= 64 ? 64 : (2 * NS <= 128 ? 128 : (2 * NS <= 256 ? 256 : 512)));
     constexpr int CPC_O = 16 / sizeof(TO);
     static_assert(NCH % 2 == 0, "an MMA consumes two 16-byte K chunks");
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    mbar_arrive_expect_tx(&full[s], NCH * LBO_A);
                     tma_load_4d(stage0 + (size_t)s * STAGE_BYTES, &tmap, &full[s], 0, x0 - PAD, y - PAD,
                                 img * p.cin_chunks + g * NCH);
                     ++issued;
@@ -242,17 +247,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sbase = smem_u32(stage0 + (size_t)s * STAGE_BYTES);
-#pragma unroll
+                    // descriptors of tap 0 / K-step 0; others add (byte offset >> 4) to the start field
+                    const uint64_t a0 = smem_desc(smem_u32(stage0 + (size_t)s * STAGE_BYTES), LBO_A, 128);
+                    const uint64_t b0 = smem_desc(wbase + (uint32_t)(g * NCH) * (uint32_t)(NS * 16), NS * 16, 128);
+#pragma unroll 1
                     for (int tap = 0; tap < KS * KS; ++tap) {
                         const int ky = tap / KS, kx = tap % KS;
+                        const uint64_t at = a0 + (uint64_t)((ky * PXS + kx) * 16 >> 4);
+                        const uint64_t bt = b0 + (uint64_t)((uint32_t)(tap * p.cin_chunks) * (uint32_t)NS);
 #pragma unroll
                         for (int j = 0; j < NCH / 2; ++j) {
-                            const uint64_t ad =
-                                smem_desc(sbase + 2 * j * LBO_A + (uint32_t)(ky * PXS + kx) * 16u, LBO_A, 128);
-                            const uint32_t kc = (uint32_t)(tap * p.cin_chunks + g * NCH + 2 * j);
-                            const uint64_t bd = smem_desc(wbase + kc * (uint32_t)(NS * 16), NS * 16, 128);
-                            umma<KIND>(d_tmem, ad, bd, IDESC, (g | tap | j) != 0 ? 1u : 0u);
+                            umma<KIND>(d_tmem, at + (uint64_t)(2 * j * (LBO_A >> 4)),
+                                       bt + (uint64_t)(2 * j * NS), IDESC, (g | tap | j) != 0 ? 1u : 0u);
                         }
                     }
                     umma_commit(&empty[s]);
@@ -274,6 +280,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
         for (int t = cta0; t < ntiles; t += cta_stride, ++it) {
             const int a = it & 1;
             const uint32_t u = (uint32_t)(it >> 1);
+            const int img = t / (tiles_x * p.H);
+            const int r = t - img * tiles_x * p.H;
+            const int y = r / tiles_x;
+            const int x = (r - y * tiles_x) * TM + m;
+            const bool valid = x < p.W;
+            const int64_t HW = (int64_t)p.H * p.W;
+            // residual of this tile: loads issued before the accumulator wait so
+            // their latency overlaps the tile's MMAs
+            constexpr int NRC = NS / CPC_O;
+            uint4 rres[EPI == 0 ? NRC : 1];
+            if (EPI == 0 && p.res && valid) {
+                const uint8_t *rbase =
+                    p.res + ((int64_t)img * (p.cout_pad / CPC_O) * HW + (int64_t)y * p.W + x) * 16;
+                const int c00 = slice * NS / CPC_O;
+#pragma unroll
+                for (int c = 0; c < NRC; ++c)
+                    rres[c] = __ldg(reinterpret_cast<const uint4 *>(rbase + (int64_t)(c00 + c) * HW * 16));
+            }
             bool ok = mbar_wait_bounded(&tfull[a], u & 1, abort, WAIT_NS);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
@@ -281,60 +305,58 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
                 break;
             }
             tc_fence_after();
-            const int img = t / (tiles_x * p.H);
-            const int r = t - img * tiles_x * p.H;
-            const int y = r / tiles_x;
-            const int x = (r - y * tiles_x) * TM + m;
-            const bool valid = x < p.W;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * NS);
-            const int64_t HW = (int64_t)p.H * p.W;
             if (EPI == 0) {
                 const int ochunks = p.cout_pad / CPC_O;
                 const int64_t pix = (int64_t)y * p.W + x;
+                const int64_t cstride = HW * 16;
+                float v[NS];
+                {
+                    uint32_t r[NS / 16][16];
 #pragma unroll
-                for (int j = 0; j < NS / 16; ++j) {
-                    float v[16];
-                    tmem_ld16(taddr + (uint32_t)(j * 16), v);
-                    if (!valid) continue;
-                    const int n0 = slice * NS + j * 16;
-                    float amax = 0.f;
+                    for (int j = 0; j < NS / 16; ++j) tmem_ld16_nowait(taddr + (uint32_t)(j * 16), r[j]);
+                    tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
+                    for (int j = 0; j < NS / 16; ++j)
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[j * 16 + e] = __uint_as_float(r[j][e]);
+                }
+                if (valid) {
+                    const int n0 = slice * NS;
+#pragma unroll
+                    for (int e = 0; e < NS; ++e) {
                         float o = v[e] * p.acc_scale + p.bias[n0 + e];
                         if (p.act == 1) o = lrelu(o);
                         v[e] = o;
                     }
-                    const int c0 = n0 / CPC_O;
-                    const int64_t cstride = HW * 16;
-                    uint8_t *ybase = p.y + ((int64_t)img * ochunks * HW + pix) * 16;
                     if (p.res) {
-                        const uint8_t *rbase = p.res + ((int64_t)img * ochunks * HW + pix) * 16;
 #pragma unroll
-                        for (int c = 0; c < 16 / CPC_O; ++c) {
+                        for (int c = 0; c < NRC; ++c) {
                             alignas(16) TO rv[CPC_O];
-                            *reinterpret_cast<uint4 *>(rv) =
-                                *reinterpret_cast<const uint4 *>(rbase + (int64_t)(c0 + c) * cstride);
+                            *reinterpret_cast<uint4 *>(rv) = rres[c];
 #pragma unroll
                             for (int e = 0; e < CPC_O; ++e) v[c * CPC_O + e] += from_elem<TO>(rv[e]) / p.out_scale;
                         }
                     }
+                    uint8_t *ybase = p.y + ((int64_t)img * ochunks * HW + pix) * 16;
                     if (p.amax) {
+                        float amax = 0.f;
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) amax = fmaxf(amax, fabsf(v[e]));
+                        for (int e = 0; e < NS; ++e) amax = fmaxf(amax, fabsf(v[e]));
                         atomicMax(p.amax, __float_as_uint(amax));
                     }
                     if (p.y2) {
-                        float w2[16];
+                        float w2[NS];
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) w2[e] = v[e] * p.y2_scale;
-                        store_vals<__nv_fp8_e4m3>(p.y2 + ((int64_t)img * (p.cout_pad / 16) * HW + pix) * 16,
-                                                  cstride, n0 / 16, w2, 16);
+                        for (int e = 0; e < NS; ++e) w2[e] = v[e] * p.y2_scale;
+                        store_vals<__nv_fp8_e4m3>(p.y2 + ((int64_t)img * (p.cout_pad / 16) * HW + pix) * 16, cstride,
+                                                  n0 / 16, w2, NS);
                     }
                     if (p.out_scale != 1.0f) {
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) v[e] *= p.out_scale;
+                        for (int e = 0; e < NS; ++e) v[e] *= p.out_scale;
                     }
-                    store_vals<TO>(ybase, cstride, c0, v, 16);
+                    store_vals<TO>(ybase, cstride, n0 / CPC_O, v, NS);
                 }
             } else if (EPI == 1) {
                 // PixelShuffle(2) of channels [0, cout) + skip -> planar float32 at (2y, 2x)
@@ -483,6 +505,82 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(int *mismatches) {
     }
 }
 
+// Convention probe for the 128-byte-swizzled K-major layout: A is 144 rows
+// x 64 BF16 (128 B per row) stored with the swizzle TMA applies (16-byte unit
+// u of row r lands at unit u ^ (r & 7) of a 1024-aligned buffer); B is 16 rows
+// x 64.  For each row offset r0 = 0..7 the MMA chain (4 K-steps of 32 bytes)
+// reads A from row r0 on, once with base offset 0 and once with base offset
+// (start >> 7) & 7; out[mode * 8 + r0] = wrong accumulator elements.  Every
+// address stays inside the 40 KB buffer whatever the hardware does with the
+// base offset.
+__global__ void __launch_bounds__(128, 1) sw128_probe_kernel(int *out) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 8);
+    uint8_t *A = smem + 1024;             // 144 rows x 128 B = 18432 B
+    uint8_t *B = smem + 1024 + 19456;     // 16 rows x 128 B, 1024-aligned
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto aval = [](int r, int k) { return (float)(((r * 7 + k * 3) % 9) - 4); };
+    auto bval = [](int n, int k) { return (float)(((n * 3 + k * 5) % 7) - 3); };
+    for (int i = tid; i < 144 * 64; i += 128) {
+        const int r = i / 64, k = i % 64;
+        const int unit = (k / 8) ^ (r & 7);
+        *reinterpret_cast<__nv_bfloat16 *>(A + r * 128 + unit * 16 + (k % 8) * 2) = __float2bfloat16_rn(aval(r, k));
+    }
+    for (int i = tid; i < 16 * 64; i += 128) {
+        const int n = i / 64, k = i % 64;
+        const int unit = (k / 8) ^ (n & 7);
+        *reinterpret_cast<__nv_bfloat16 *>(B + n * 128 + unit * 16 + (k % 8) * 2) = __float2bfloat16_rn(bval(n, k));
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbarrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(slot, 32);
+        tmem_relinquish();
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *slot;
+    const uint32_t idesc = instr_desc(128, 16, 1, 1);
+    for (int test = 0; test < 16; ++test) {
+        const int mode = test / 8, r0 = test % 8;
+        if (tid == 0) {
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t as = smem_u32(A) + (uint32_t)(r0 * 128 + j * 32);
+                const uint32_t bs = smem_u32(B) + (uint32_t)(j * 32);
+                const uint64_t ad = smem_desc_sw128(as, mode ? ((as >> 7) & 7) : 0);
+                const uint64_t bd = smem_desc_sw128(bs, mode ? ((bs >> 7) & 7) : 0);
+                umma<0>(tbase, ad, bd, idesc, j ? 1u : 0u);
+            }
+            umma_commit(bar);
+        }
+        const bool ok = mbar_wait_bounded(bar, (uint32_t)(test & 1), nullptr, WAIT_NS);
+        tc_fence_after();
+        float v[16];
+        tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
+        const int m = warp * 32 + lane;
+        int bad = ok ? 0 : 1000;
+        for (int n = 0; n < 16; ++n) {
+            float ref = 0.f;
+            for (int k = 0; k < 64; ++k) ref += aval(r0 + m, k) * bval(n, k);
+            if (v[n] != ref) ++bad;
+        }
+        if (bad) atomicAdd(out + test, bad);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (warp == 0) {
+        __syncwarp();
+        tmem_dealloc(tbase, 32);
+    }
+}
+
 // ---------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -510,7 +608,7 @@ int pick_ns(int cin_chunks, int cout_pad, int k) {
 template <int IN_DT, int OUT_DT, int NS, int KS, int NCH, int EPI>
 cudaError_t run(const CUtensorMap &map, TcParams p, cudaStream_t st) {
     constexpr int PXS = TM + KS - 1;
-    constexpr uint32_t STAGE_BYTES = NCH * KS * PXS * 16;
+    constexpr uint32_t STAGE_BYTES = (NCH * KS * PXS * 16 + 1023u) & ~1023u;
     const uint32_t wround = (p.wbytes + 1023) & ~1023u;
     const int avail = SMEM_LIMIT - 1024 /*align slack*/ - SMEM_HDR - (int)wround;
     int stages = avail / (int)STAGE_BYTES;
@@ -554,6 +652,8 @@ const Variant kVariants[] = {
     NVISR_V16(DT_F16, 16, 3, 4, 1), NVISR_V16(DT_F16, 16, 3, 8, 1), NVISR_V16(DT_F16, 64, 1, 8, 0),
     NVISR_V16(DT_F16, 64, 3, 8, 2), NVISR_V16(DT_F16, 16, 3, 2, 0), NVISR_V16(DT_F16, 16, 3, 4, 0),
     NVISR_V16(DT_F16, 16, 3, 8, 0),
+    // FP32 output (offset/mask heads feeding a DCN keep full-precision offsets)
+    NVISR_V(DT_BF16, DT_F32, 32, 3, 8, 0), NVISR_V(DT_F16, DT_F32, 32, 3, 8, 0),
     // FP8 E4M3 operands (bodies): output BF16 trunk (+ FP8 copy) or FP8 directly
     NVISR_V(DT_E4M3, DT_BF16, 64, 3, 4, 0), NVISR_V(DT_E4M3, DT_E4M3, 64, 3, 4, 0),
 };
@@ -644,6 +744,13 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
     p.ps_out = a.ps_out; p.ps_pitch = a.ps_pitch; p.skip = a; p.ps_act = a.ps_act;
     p.err = a.err;
     return v->fn(map, p, st);
+}
+
+int tc_probe_sw128(int *dev_out16, cudaStream_t st) {
+    const int smem = 44 * 1024;
+    cudaFuncSetAttribute(sw128_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    sw128_probe_kernel<<<1, 128, smem, st>>>(dev_out16);
+    return (int)cudaGetLastError();
 }
 
 int tc_selftest(int kind, int *dev_mismatch, cudaStream_t st) {

@@ -24,6 +24,7 @@
 namespace nvisr {
 
 int tc_selftest(int kind, int *dev_mismatch, cudaStream_t st);
+int tc_probe_sw128(int *dev_out16, cudaStream_t st);
 
 // ---------------------------------------------------------------- errors
 
@@ -103,6 +104,8 @@ struct Tensor {
     int C = 0, cpad = 0, H = 0, W = 0, dt = DT_F32;
     void *f8 = nullptr;  // FP8 copy (when an FP8 layer consumes this tensor)
     int amax_slot = -1;  // calibration slot of the FP8 values
+    int parent = -1;     // channel view of a concatenation buffer (tensor id)
+    int choff = 0;       // first channel inside the parent
 };
 
 struct Weights {
@@ -115,8 +118,14 @@ struct Weights {
 
 enum Src { SRC_TENSOR = 0, SRC_TUPLE = 1 };
 
+enum Op { OP_CONV = 0, OP_DCN = 1, OP_PACK = 2 };
+
 struct Step {
+    int op = OP_CONV;
     int layer = 0;
+    int widx = -1;       // weights variant (input channels permuted), -1 = the layer's own
+    int om_t = -1;       // DCN: offsets/mask tensor
+    std::vector<int> skip_frames;  // final outputs: frames whose upsampled mean is added
     int in_t = -1;       // input tensor id (SRC_TENSOR)
     int src = SRC_TENSOR;
     int frame_src = -1;  // group family: input from ring frame k
@@ -181,6 +190,7 @@ struct nvisr_filter {
     int64_t total_out = -1;        // known after flush
 
     // network plan
+    std::vector<Weights> wvar;     // weights with permuted input channels (concatenations)
     std::vector<Weights> weights;  // per layer (shared layers point to the owner)
     std::vector<Tensor> tensors;
     std::vector<Step> steps;
@@ -306,9 +316,19 @@ bool group_ready(const nvisr_filter *f, int64_t run, std::vector<int64_t> *idx) 
 
 int outputs_per_input(const nvisr_filter *f) { return f->net.family == "group" ? 2 : 1; }
 
+// FP8 filters calibrate their activation scales on the first calib_frames
+// outputs' tuples, so nothing is ready before those tuples are all known.
+bool calibration_ready(const nvisr_filter *f) {
+    if (f->precision != NVISR_PREC_FP8 || f->calibrated || f->n_amax == 0) return true;
+    const int64_t n = f->eos ? std::min<int64_t>(f->calib_frames, f->pushed) : f->calib_frames;
+    for (int64_t t = 0; t < n; ++t)
+        if (!tuple_ready(f, t, nullptr)) return false;
+    return true;
+}
+
 bool output_ready(const nvisr_filter *f, int64_t o) {
     if (f->net.family == "group") return group_ready(f, o / 2, nullptr);
-    return tuple_ready(f, o, nullptr);
+    return tuple_ready(f, o, nullptr) && calibration_ready(f);
 }
 
 nvisr_status check_device_error(nvisr_filter *f) {
@@ -341,6 +361,39 @@ bool layer_is_fp8(const nvisr_filter *f, const NetLayer &L) {
            L.ps == 0 && L.in.size() == 1 && L.in[0] != "tuple" && L.in[0].rfind("frame", 0) != 0;
 }
 
+// Uploads one layer's weights (OIHW float32, with bias) in the precision's layout.
+nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, const float *b, Weights &W) {
+    W.cin_pad = act_cpad(f, L.cin);
+    W.cout_pad = round_up(L.cout, 16);
+    std::vector<float> bias(W.cout_pad, 0.f);
+    std::copy(b, b + L.cout, bias.begin());
+    void *dbias;
+    nvisr_status s = upload(f, bias.data(), bias.size() * 4, &dbias);
+    if (s != NVISR_OK) return s;
+    W.bias = (float *)dbias;
+    if (!f->tc) {
+        std::vector<float> host(simt_weight_bytes(W.cin_pad, W.cout_pad, L.k) / 4);
+        prepare_weights_simt(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, host.data());
+        s = upload(f, host.data(), host.size() * 4, &W.simt_or_tc);
+    } else {
+        std::vector<uint8_t> host(tc_weight_bytes(W.cin_pad, W.cout_pad, L.k, f->act_dt));
+        prepare_weights_tc(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, f->act_dt, 1.0f, host.data());
+        s = upload(f, host.data(), host.size(), &W.simt_or_tc);
+    }
+    if (s != NVISR_OK) return s;
+    if (layer_is_fp8(f, L)) {
+        float amax = 0.f;
+        for (int64_t k = 0; k < (int64_t)L.cout * L.cin * L.k * L.k; ++k) amax = std::max(amax, std::fabs(w[k]));
+        W.w_amax = amax > 0.f ? amax : 1.f;
+        const float sw = W.w_amax / 448.f;
+        std::vector<uint8_t> host(tc_weight_bytes(L.cin, W.cout_pad, L.k, DT_E4M3));
+        prepare_weights_tc(w, L.cout, L.cin, L.k, L.cin, W.cout_pad, DT_E4M3, 1.0f / sw, host.data());
+        s = upload(f, host.data(), host.size(), &W.f8);
+        if (s != NVISR_OK) return s;
+    }
+    return NVISR_OK;
+}
+
 nvisr_status prepare_weights(nvisr_filter *f, const float *blob) {
     const NetDesc &net = f->net;
     f->weights.resize(net.layers.size());
@@ -350,37 +403,10 @@ nvisr_status prepare_weights(nvisr_filter *f, const float *blob) {
             f->weights[i] = f->weights[L.owner];
             continue;
         }
-        Weights &W = f->weights[i];
         const float *w = blob + L.woff;
         const float *b = w + (int64_t)L.cout * L.cin * L.k * L.k;
-        W.cin_pad = act_cpad(f, L.cin);
-        W.cout_pad = round_up(L.cout, 16);
-        std::vector<float> bias(W.cout_pad, 0.f);
-        std::copy(b, b + L.cout, bias.begin());
-        void *dbias;
-        nvisr_status s = upload(f, bias.data(), bias.size() * 4, &dbias);
+        nvisr_status s = upload_weights(f, L, w, b, f->weights[i]);
         if (s != NVISR_OK) return s;
-        W.bias = (float *)dbias;
-        if (!f->tc) {
-            std::vector<float> host(simt_weight_bytes(W.cin_pad, W.cout_pad, L.k) / 4);
-            prepare_weights_simt(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, host.data());
-            s = upload(f, host.data(), host.size() * 4, &W.simt_or_tc);
-        } else {
-            std::vector<uint8_t> host(tc_weight_bytes(W.cin_pad, W.cout_pad, L.k, f->act_dt));
-            prepare_weights_tc(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, f->act_dt, 1.0f, host.data());
-            s = upload(f, host.data(), host.size(), &W.simt_or_tc);
-        }
-        if (s != NVISR_OK) return s;
-        if (layer_is_fp8(f, L)) {
-            float amax = 0.f;
-            for (int64_t k = 0; k < (int64_t)L.cout * L.cin * L.k * L.k; ++k) amax = std::max(amax, std::fabs(w[k]));
-            W.w_amax = amax > 0.f ? amax : 1.f;
-            const float sw = W.w_amax / 448.f;
-            std::vector<uint8_t> host(tc_weight_bytes(L.cin, W.cout_pad, L.k, DT_E4M3));
-            prepare_weights_tc(w, L.cout, L.cin, L.k, L.cin, W.cout_pad, DT_E4M3, 1.0f / sw, host.data());
-            s = upload(f, host.data(), host.size(), &W.f8);
-            if (s != NVISR_OK) return s;
-        }
     }
     return NVISR_OK;
 }
@@ -427,6 +453,7 @@ nvisr_status build_plan(nvisr_filter *f) {
             if (net.scale != 2) return fail(NVISR_UNSUPPORTED_FORMAT, "tuple networks: scale 2 only");
             st.out_t = -1;
             st.out_index = out_index[L.name];
+            st.skip_frames = {(net.frames - 1) / 2};
         } else {
             if (L.ps) return fail(NVISR_UNSUPPORTED_FORMAT, "inner PixelShuffle in a tuple network");
             Tensor t;
@@ -530,12 +557,229 @@ nvisr_status build_plan(nvisr_filter *f) {
     return NVISR_OK;
 }
 
+// Group-family plan (Section 3.1: a per-frame extract stage, then a fusion
+// stage over the frame group): frame packs, convolutions, DCN layers,
+// PixelShuffle stages.  A channel concatenation is free: its parts are
+// produced straight into channel views of one buffer; a layer reading the
+// parts in another order gets a copy of its weights with the input channels
+// permuted to the storage order.  Buffers are reused by liveness.
+nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
+    const NetDesc &net = f->net;
+    const int H = f->in_fmt.height, W = f->in_fmt.width;
+    f->tensors.clear();
+    f->steps.clear();
+    f->wvar.clear();
+    f->pack_t = -1;
+    if (net.outputs.size() > 2) return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: at most 2 outputs per run");
+    if (f->precision == NVISR_PREC_FP8) return fail(NVISR_UNSUPPORTED_FORMAT, "group networks run in FP32/BF16/FP16");
+    if (!(net.extra && net.frames == 2))
+        return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: n = 1 with the Extra frame flag (2 input frames)");
+    const int outs_expected = net.dbl ? 2 : 1;
+    if ((int)net.outputs.size() != outs_expected || !net.interp)
+        return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: Interpolation + Double frame (2 outputs per run)");
+    std::map<std::string, int> tensor_of, out_index;
+    for (size_t i = 0; i < net.outputs.size(); ++i) out_index[net.outputs[i].name] = (int)i;
+    std::map<std::string, int> om_names;
+    for (const NetLayer &L : net.layers)
+        if (L.op == "dcn") om_names[L.om] = 1;
+    auto chans = [&](const std::string &n) -> int {
+        const int i = net.find(n);
+        if (i < 0) return 3;
+        return net.layers[i].ps ? net.layers[i].cout / 4 : net.layers[i].cout;
+    };
+    // concatenation groups: part -> (group, channel offset)
+    struct Group { std::vector<std::string> parts; int C = 0; int t = -1; };
+    std::vector<Group> groups;
+    std::map<std::string, std::pair<int, int>> placed;
+    for (const NetLayer &L : net.layers) {
+        if (L.in.size() < 2) continue;
+        int g = -1, found = 0;
+        bool same = true;
+        for (const std::string &n : L.in) {
+            auto it = placed.find(n);
+            if (it == placed.end()) continue;
+            ++found;
+            if (g < 0) g = it->second.first;
+            else if (g != it->second.first) same = false;
+        }
+        if (found == 0) {
+            Group G;
+            for (const std::string &n : L.in) {
+                if (net.find(n) < 0) return fail(NVISR_UNSUPPORTED_FORMAT, "layer " + L.name + ": concatenated frames");
+                if (chans(n) % 16) return fail(NVISR_UNSUPPORTED_FORMAT, "concatenated tensors need 16k channels");
+                placed[n] = {(int)groups.size(), G.C};
+                G.parts.push_back(n);
+                G.C += chans(n);
+            }
+            groups.push_back(G);
+        } else if (found != (int)L.in.size() || !same || groups[g].parts.size() != L.in.size()) {
+            return fail(NVISR_UNSUPPORTED_FORMAT, "layer " + L.name + ": concatenation overlaps another one");
+        }
+    }
+    auto new_tensor = [&](int C, int cpad, int h, int w, int dt) {
+        Tensor t;
+        t.C = C; t.cpad = cpad; t.H = h; t.W = w; t.dt = dt;
+        f->tensors.push_back(t);
+        return (int)f->tensors.size() - 1;
+    };
+    auto source = [&](const std::string &n) -> int {
+        auto it = tensor_of.find(n);
+        if (it != tensor_of.end()) return it->second;
+        if (n.rfind("frame", 0) != 0) return -1;
+        const int k = atoi(n.c_str() + 5);
+        if (k < 0 || k >= net.frames) return -1;
+        const int id = new_tensor(3, act_cpad(f, 3), H, W, f->act_dt);
+        tensor_of[n] = id;
+        Step ps;
+        ps.op = OP_PACK;
+        ps.frame_src = k;
+        ps.out_t = id;
+        f->steps.push_back(ps);
+        return id;
+    };
+    for (size_t i = 0; i < net.layers.size(); ++i) {
+        const NetLayer &L = net.layers[i];
+        Step st;
+        st.layer = (int)i;
+        st.op = L.op == "dcn" ? OP_DCN : OP_CONV;
+        if (L.in.size() == 1) {
+            st.in_t = source(L.in[0]);
+        } else {
+            const Group &G = groups[placed[L.in[0]].first];
+            st.in_t = G.t;
+            if (G.parts != L.in) {
+                std::vector<int> perm(G.C);
+                int loff = 0;
+                for (const std::string &n : L.in) {
+                    const int c = chans(n), soff = placed[n].second;
+                    for (int j = 0; j < c; ++j) perm[soff + j] = loff + j;
+                    loff += c;
+                }
+                const int kk = L.k * L.k;
+                const float *w = blob + L.woff;
+                const float *b = w + (int64_t)L.cout * L.cin * kk;
+                std::vector<float> wp((size_t)L.cout * L.cin * kk);
+                for (int o = 0; o < L.cout; ++o)
+                    for (int c = 0; c < L.cin; ++c)
+                        for (int t = 0; t < kk; ++t)
+                            wp[((size_t)o * L.cin + c) * kk + t] = w[((size_t)o * L.cin + perm[c]) * kk + t];
+                Weights Wv;
+                nvisr_status s = upload_weights(f, L, wp.data(), b, Wv);
+                if (s != NVISR_OK) return s;
+                st.widx = (int)f->wvar.size();
+                f->wvar.push_back(Wv);
+            }
+        }
+        if (st.in_t < 0) return fail(NVISR_BAD_NETWORK, "layer " + L.name + ": input not available");
+        const Tensor src = f->tensors[st.in_t];
+        if (src.C != L.cin) return fail(NVISR_BAD_NETWORK, "layer " + L.name + ": cin does not match its input");
+        if (st.op == OP_DCN) {
+            st.om_t = source(L.om);
+            if (st.om_t < 0 || f->tensors[st.om_t].C != 27 * L.groups || f->tensors[st.om_t].dt != DT_F32)
+                return fail(NVISR_BAD_NETWORK, "layer " + L.name + ": offset/mask head must have 27*groups channels");
+            if (f->tensors[st.om_t].H != src.H) return fail(NVISR_BAD_NETWORK, "layer " + L.name + ": size mismatch");
+        }
+        if (!L.add.empty()) {
+            st.add_t = source(L.add);
+            if (st.add_t < 0 || f->tensors[st.add_t].C != L.cout) return fail(NVISR_BAD_NETWORK, "bad add source");
+        }
+        if (out_index.count(L.name)) {
+            if (L.op != "conv" || L.ps != 2 || L.cout != 12) return fail(NVISR_UNSUPPORTED_FORMAT, "output layers: conv -> 12 ch + PixelShuffle(2)");
+            if (src.H * 2 != H * net.scale || src.W * 2 != W * net.scale)
+                return fail(NVISR_UNSUPPORTED_FORMAT, "output layer " + L.name + ": size is not scale x input");
+            st.out_t = -1;
+            st.out_index = out_index[L.name];
+            for (const std::string &n : net.outputs[st.out_index].skip) {
+                const int k = atoi(n.c_str() + 5);
+                if (n.rfind("frame", 0) != 0 || k < 0 || k >= net.frames) return fail(NVISR_BAD_NETWORK, "bad skip");
+                st.skip_frames.push_back(k);
+            }
+            if (st.skip_frames.size() > 2) return fail(NVISR_UNSUPPORTED_FORMAT, "at most two skip frames");
+        } else {
+            const int C = L.ps ? L.cout / 4 : L.cout;
+            const int h = L.ps ? 2 * src.H : src.H, w = L.ps ? 2 * src.W : src.W;
+            const int dt = om_names.count(L.name) ? DT_F32 : f->act_dt;
+            const int cpad = L.ps ? round_up(C, 16) : round_up(L.cout, 16);
+            const int id = new_tensor(C, cpad, h, w, dt);
+            auto pl = placed.find(L.name);
+            if (pl != placed.end()) {
+                Group &G = groups[pl->second.first];
+                if (G.t < 0) G.t = new_tensor(G.C, G.C, h, w, f->act_dt);
+                const Tensor &gt = f->tensors[G.t];
+                if (gt.H != h || gt.W != w || dt != gt.dt || cpad != C)
+                    return fail(NVISR_UNSUPPORTED_FORMAT, "concatenated tensors differ in size or type");
+                f->tensors[id].parent = G.t;
+                f->tensors[id].choff = pl->second.second;
+            }
+            tensor_of[L.name] = id;
+            st.out_t = id;
+        }
+        f->steps.push_back(st);
+    }
+    // liveness on root tensors (views count as their parent)
+    const int n = (int)f->tensors.size();
+    auto root = [&](int t) { return f->tensors[t].parent >= 0 ? f->tensors[t].parent : t; };
+    std::vector<int> first_def(n, 1 << 30), last_use(n, -1);
+    for (size_t i = 0; i < f->steps.size(); ++i) {
+        const Step &st = f->steps[i];
+        if (st.out_t >= 0) first_def[root(st.out_t)] = std::min(first_def[root(st.out_t)], (int)i);
+        for (int u : {st.in_t, st.add_t, st.om_t})
+            if (u >= 0) last_use[root(u)] = std::max(last_use[root(u)], (int)i);
+    }
+    struct Buf { void *p; size_t bytes; int free_after; };
+    std::vector<Buf> pool;
+    for (int step = 0; step < (int)f->steps.size(); ++step) {
+        for (int t = 0; t < n; ++t) {
+            if (f->tensors[t].parent >= 0 || first_def[t] != step) continue;
+            Tensor &T = f->tensors[t];
+            const size_t bytes = (size_t)T.cpad * T.H * T.W * dtype_size(T.dt);
+            void *got = nullptr;
+            for (Buf &b : pool)
+                if (b.free_after < step && b.bytes >= bytes) {
+                    b.free_after = 1 << 30;
+                    got = b.p;
+                    break;
+                }
+            if (!got) {
+                nvisr_status s = dalloc(f->eng, bytes, f->owned, &got);
+                if (s != NVISR_OK) return s;
+                pool.push_back({got, bytes, 1 << 30});
+            }
+            T.ptr = got;
+        }
+        for (int t = 0; t < n; ++t)
+            if (f->tensors[t].parent < 0 && last_use[t] == step && f->tensors[t].ptr)
+                for (Buf &b : pool)
+                    if (b.p == f->tensors[t].ptr) b.free_after = step;
+    }
+    for (Tensor &T : f->tensors)
+        if (T.parent >= 0) {
+            const Tensor &P = f->tensors[T.parent];
+            T.ptr = (uint8_t *)P.ptr + (size_t)(T.choff / chunk_channels(P.dt)) * P.H * P.W * 16;
+        }
+    return NVISR_OK;
+}
+
 // Runs one conv step.  calib: 16-bit pass recording amax of FP8-consumed tensors.
-nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames, bool calib, int out_slot) {
+nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames, bool calib) {
     const NetLayer &L = f->net.layers[s.layer];
-    const Weights &Wt = f->weights[s.layer];
+    const Weights &Wt = s.widx >= 0 ? f->wvar[s.widx] : f->weights[s.layer];
     const Tensor &in = f->tensors[s.in_t];
     cudaStream_t st = f->eng->stream;
+    if (s.op == OP_DCN) {
+        const Tensor &om = f->tensors[s.om_t];
+        const Tensor &o = f->tensors[s.out_t];
+        DcnArgs d{};
+        d.x = in.ptr; d.cin_pad = in.cpad; d.H = in.H; d.W = in.W; d.groups = L.groups;
+        d.om = (const float *)om.ptr; d.om_cpad = om.cpad; d.mask_logits = 1;
+        d.w = Wt.simt_or_tc; d.bias = Wt.bias; d.cout = L.cout; d.cout_pad = Wt.cout_pad;
+        d.y = o.ptr; d.in_dt = in.dt; d.out_dt = o.dt; d.acc_scale = 1.f; d.out_scale = 1.f;
+        d.err = f->eng->err_word;
+        ProfScope ps(f, NVISR_K_DCN);
+        cudaError_t e = f->tc ? launch_dcn_tc(d, st) : launch_dcn_simt(d, st);
+        if (e != cudaSuccess) return cuda_status(e, ("dcn layer " + L.name).c_str());
+        return NVISR_OK;
+    }
     ConvArgs a{};
     a.cin_pad = in.cpad;
     a.H = in.H;
@@ -567,6 +811,8 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
     if (s.out_t >= 0) {
         const Tensor &o = f->tensors[s.out_t];
         a.y = o.ptr;
+        a.out_dt = o.dt;
+        a.ps = L.ps;
         if (!calib && f->calibrated && o.amax_slot >= 0) {
             const float inv = 1.f / f->act_scale[o.amax_slot];
             if (s.out_f8_only && use_f8) {
@@ -581,7 +827,7 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
         if (calib && o.amax_slot >= 0) a.amax = f->amax + o.amax_slot;
     } else {
         a.ps = 2;
-        a.ps_out = f->out_rgb[out_slot];
+        a.ps_out = f->out_rgb[s.out_index];
         a.ps_pitch = f->opitch;
         a.skip_mode = f->net.skip;
         a.skip_scale = f->net.scale;
@@ -589,13 +835,13 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
         a.skip_w = f->in_fmt.width;
         a.skip_pitch = f->rpitch;
         a.skip_plane = f->rpitch * f->in_fmt.height;
-        a.nskip = 1;
-        a.skip_src[0] = frames[(f->net.frames - 1) / 2];
+        a.nskip = (int)s.skip_frames.size();
+        for (int k = 0; k < a.nskip && k < 2; ++k) a.skip_src[k] = frames[s.skip_frames[k]];
     }
     const int kind = s.out_t < 0 ? NVISR_K_CONV_TAIL
                      : (s.src == SRC_TUPLE ? NVISR_K_CONV_HEAD
-                                           : (L.cin == 64 && L.cout == 64 && L.k == 3 ? NVISR_K_CONV_BODY
-                                                                                       : NVISR_K_CONV_OTHER));
+                                           : (L.cin == 64 && L.cout == 64 && L.k == 3 && !L.ps ? NVISR_K_CONV_BODY
+                                                                                                : NVISR_K_CONV_OTHER));
     ProfScope ps(f, kind);
     cudaError_t e = f->tc ? launch_conv_tc(a, st) : launch_conv_simt(a, st);
     if (e != cudaSuccess) return cuda_status(e, ("conv layer " + L.name).c_str());
@@ -624,17 +870,49 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
     }
     if (e != cudaSuccess) return cuda_status(e, "pack");
     for (const Step &s : f->steps) {
-        nvisr_status st = run_step(f, s, frames, calib, 0);
+        nvisr_status st = run_step(f, s, frames, calib);
+        if (st != NVISR_OK) return st;
+    }
+    return NVISR_OK;
+}
+
+// Group family: one run over frames (idx[0], idx[1], ...) computing every output.
+nvisr_status forward_group(nvisr_filter *f, const std::vector<int64_t> &idx) {
+    const float *frames[8];
+    for (size_t k = 0; k < idx.size() && k < 8; ++k) frames[k] = ring_slot(f, idx[k]);
+    for (const Step &s : f->steps) {
+        if (s.op == OP_PACK) {
+            const Tensor &t = f->tensors[s.out_t];
+            PackArgs pa{};
+            pa.src[0] = frames[s.frame_src];
+            pa.nsrc = 1;
+            pa.ch_per_src = 3;
+            pa.src_pitch = f->rpitch;
+            pa.src_plane = f->rpitch * f->in_fmt.height;
+            pa.H = t.H;
+            pa.W = t.W;
+            pa.dst = t.ptr;
+            pa.cpad = t.cpad;
+            pa.dt = t.dt;
+            pa.scale = 1.f;
+            cudaError_t e;
+            {
+                ProfScope ps(f, NVISR_K_PACK);
+                e = launch_pack(pa, f->eng->stream);
+            }
+            if (e != cudaSuccess) return cuda_status(e, "pack");
+            continue;
+        }
+        nvisr_status st = run_step(f, s, frames, false);
         if (st != NVISR_OK) return st;
     }
     return NVISR_OK;
 }
 
 nvisr_status calibrate(nvisr_filter *f) {
-    const int n = (int)std::min<int64_t>(f->calib_frames, f->pushed);
+    if (!calibration_ready(f)) return NVISR_AGAIN;
+    const int n = (int)(f->eos ? std::min<int64_t>(f->calib_frames, f->pushed) : f->calib_frames);
     std::vector<int64_t> idx;
-    for (int t = 0; t < n; ++t)
-        if (!tuple_ready(f, t, nullptr)) return NVISR_AGAIN;
     NVISR_TRY_CUDA(cudaMemsetAsync(f->amax, 0, sizeof(unsigned) * f->n_amax, f->eng->stream));
     for (int t = 0; t < n; ++t) {
         tuple_ready(f, t, &idx);
@@ -654,9 +932,17 @@ nvisr_status calibrate(nvisr_filter *f) {
     return NVISR_OK;
 }
 
-// Computes output o into f->out_rgb (tuple family).
+// Computes output o into f->out_rgb[output_slot(o)].
 nvisr_status compute_output(nvisr_filter *f, int64_t o) {
     std::vector<int64_t> idx;
+    if (f->net.family == "group") {
+        const int64_t run = o / 2;
+        if (f->cached_run == run) return NVISR_OK;
+        if (!group_ready(f, run, &idx)) return NVISR_AGAIN;
+        nvisr_status s = forward_group(f, idx);
+        if (s == NVISR_OK) f->cached_run = run;
+        return s;
+    }
     if (!tuple_ready(f, o, &idx)) return NVISR_AGAIN;
     if (f->precision == NVISR_PREC_FP8 && !f->calibrated && f->n_amax > 0) {
         nvisr_status s = calibrate(f);
@@ -664,6 +950,8 @@ nvisr_status compute_output(nvisr_filter *f, int64_t o) {
     }
     return forward_tuple(f, idx, false);
 }
+
+int output_slot(const nvisr_filter *f, int64_t o) { return f->net.family == "group" ? (int)(o % 2) : 0; }
 
 nvisr_status write_output(nvisr_filter *f, nvisr_planes *out, int slot) {
     cudaStream_t st = f->eng->stream;
@@ -808,8 +1096,6 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
     if (net.align != 1) return fail(NVISR_UNSUPPORTED_FORMAT, "network stride alignment > 1 is not supported");
     if (net.family == "tuple" && (net.frames % 2 == 0 || net.frames > 8))
         return fail(NVISR_UNSUPPORTED_FORMAT, "tuple networks need an odd frame count <= 7");
-    if (net.family == "group")
-        return fail(NVISR_UNSUPPORTED_FORMAT, "group-family networks are not supported by this build");
     cudaSetDevice(e->device);
     f->eng = e;
     f->in_fmt = d->in_fmt;
@@ -849,7 +1135,8 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
         f->out_rgb[k] = (float *)p;
     }
     if ((s = prepare_weights(f.get(), d->weights)) != NVISR_OK) return cleanup(s);
-    if ((s = build_plan(f.get())) != NVISR_OK) return cleanup(s);
+    if ((s = (net.family == "group" ? build_plan_group(f.get(), d->weights) : build_plan(f.get()))) != NVISR_OK)
+        return cleanup(s);
     e->filters.push_back(f.get());
     *out = f.release();
     return NVISR_OK;
@@ -927,15 +1214,13 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
     } else {
         f->produced.pop_front();
     }
-    if ((s = write_output(f, out, 0)) != NVISR_OK) return s;
+    if ((s = write_output(f, out, output_slot(f, o))) != NVISR_OK) return s;
     if (info) {
         std::vector<int64_t> idx;
-        tuple_ready(f, o, &idx);
-        int64_t s0, s1;
-        bool closed;
-        scene_bounds(f, o, &s0, &s1, &closed);
+        if (f->net.family == "group") group_ready(f, o / 2, &idx);
+        else tuple_ready(f, o, &idx);
         int scene = 0;
-        for (int64_t k = 1; k <= o; ++k) scene += f->cut[(size_t)k];
+        for (int64_t k = 1; k <= idx.front(); ++k) scene += f->cut[(size_t)k];
         info->index = o;
         info->src_first = idx.front();
         info->src_last = idx.back();
@@ -1202,36 +1487,81 @@ nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t
     if (!x || !offsets || !mask || !weight || !y || cin < 1 || cout < 1 || h < 1 || w < 1 || groups < 1 ||
         cin % groups)
         return fail(NVISR_INVALID_ARG, "dcn2d: bad arguments");
-    if (precision != NVISR_PREC_FP32) return fail(NVISR_UNSUPPORTED_FORMAT, "dcn2d: only FP32 in this build");
-    if ((cin / groups) % 4) return fail(NVISR_UNSUPPORTED_FORMAT, "dcn2d: channels per group must be a multiple of 4");
+    if (precision < NVISR_PREC_FP32 || precision > NVISR_PREC_FP16)
+        return fail(NVISR_UNSUPPORTED_FORMAT, "dcn2d: FP32, BF16 or FP16");
+    const bool tc = precision != NVISR_PREC_FP32;
+    const int adt = precision == NVISR_PREC_FP32 ? DT_F32 : (precision == NVISR_PREC_FP16 ? DT_F16 : DT_BF16);
+    if (tc && (cin != 64 || cout != 64 || (cin / groups) % 8))
+        return fail(NVISR_UNSUPPORTED_FORMAT, "dcn2d: tensor-core DCN needs 64 -> 64 channels, 8k per group");
+    if (!tc && ((cin / groups) % 4 || cin % 8))
+        return fail(NVISR_UNSUPPORTED_FORMAT, "dcn2d: FP32 DCN needs cin % 8 == 0 and 4k channels per group");
     cudaStream_t st = (cudaStream_t)stream;
-    const int cin_pad = round_up(cin, 8), cout_pad = round_up(cout, 16);
-    if (cin_pad != cin) return fail(NVISR_UNSUPPORTED_FORMAT, "dcn2d: cin must be a multiple of 8");
+    const int cin_pad = cin, cout_pad = round_up(cout, 16);
     Scratch sc;
     std::vector<float> hw((size_t)cout * cin * 9), hb(cout_pad, 0.f);
     NVISR_TRY_CUDA(cudaMemcpyAsync(hw.data(), weight, hw.size() * 4, cudaMemcpyDeviceToHost, st));
     if (bias) NVISR_TRY_CUDA(cudaMemcpyAsync(hb.data(), bias, (size_t)cout * 4, cudaMemcpyDeviceToHost, st));
     NVISR_TRY_CUDA(cudaStreamSynchronize(st));
-    std::vector<float> hwl(simt_weight_bytes(cin_pad, cout_pad, 3) / 4);
-    prepare_weights_simt(hw.data(), cout, cin, 3, cin_pad, cout_pad, hwl.data());
-    void *dw, *db, *dx, *dy;
-    NVISR_TRY_CUDA(sc.alloc(hwl.size() * 4, &dw));
-    NVISR_TRY_CUDA(cudaMemcpyAsync(dw, hwl.data(), hwl.size() * 4, cudaMemcpyHostToDevice, st));
+    std::vector<uint8_t> hwl;
+    if (tc) {
+        hwl.resize(tc_weight_bytes(cin_pad, cout_pad, 3, adt));
+        prepare_weights_tc(hw.data(), cout, cin, 3, cin_pad, cout_pad, adt, 1.f, hwl.data());
+    } else {
+        hwl.resize(simt_weight_bytes(cin_pad, cout_pad, 3));
+        prepare_weights_simt(hw.data(), cout, cin, 3, cin_pad, cout_pad, (float *)hwl.data());
+    }
+    void *dw, *db, *dx, *dy, *dom;
+    NVISR_TRY_CUDA(sc.alloc(hwl.size(), &dw));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(dw, hwl.data(), hwl.size(), cudaMemcpyHostToDevice, st));
     NVISR_TRY_CUDA(sc.alloc(cout_pad * 4, &db));
     NVISR_TRY_CUDA(cudaMemcpyAsync(db, hb.data(), cout_pad * 4, cudaMemcpyHostToDevice, st));
-    NVISR_TRY_CUDA(sc.alloc((size_t)cin_pad * h * w * 4, &dx));
-    NVISR_TRY_CUDA(sc.alloc((size_t)cout_pad * h * w * 4, &dy));
-    nvisr_status s = pack_planar(x, cin, cin_pad, h, w, DT_F32, 1.f, dx, st);
+    NVISR_TRY_CUDA(sc.alloc((size_t)cin_pad * h * w * dtype_size(adt), &dx));
+    NVISR_TRY_CUDA(sc.alloc((size_t)cout_pad * h * w * dtype_size(adt), &dy));
+    // offsets then mask, as one blocked float32 operand [27G -> pad 4]
+    const int om_c = 27 * groups, om_cpad = round_up(om_c, 4);
+    NVISR_TRY_CUDA(sc.alloc((size_t)om_cpad * h * w * 4, &dom));
+    {
+        PackArgs pa{};
+        pa.src[0] = offsets;
+        pa.src[1] = mask;
+        pa.nsrc = 1;
+        pa.ch_per_src = 18 * groups;
+        pa.src_pitch = w;
+        pa.src_plane = (int64_t)w * h;
+        pa.H = h;
+        pa.W = w;
+        pa.dst = dom;
+        pa.cpad = om_cpad;
+        pa.dt = DT_F32;
+        pa.scale = 1.f;
+        // offsets (18G channels) then mask (9G channels): two packs into one tensor
+        // would split a 4-channel chunk when 18G % 4 != 0, so pack from a joined copy
+        void *joined;
+        NVISR_TRY_CUDA(sc.alloc((size_t)om_c * h * w * 4, &joined));
+        NVISR_TRY_CUDA(cudaMemcpyAsync(joined, offsets, (size_t)18 * groups * h * w * 4, cudaMemcpyDeviceToDevice, st));
+        NVISR_TRY_CUDA(cudaMemcpyAsync((float *)joined + (size_t)18 * groups * h * w, mask, (size_t)9 * groups * h * w * 4,
+                                       cudaMemcpyDeviceToDevice, st));
+        pa.src[0] = (const float *)joined;
+        pa.ch_per_src = om_c;
+        NVISR_TRY_CUDA(launch_pack(pa, st));
+    }
+    nvisr_status s = pack_planar(x, cin, cin_pad, h, w, adt, 1.f, dx, st);
     if (s != NVISR_OK) return s;
+    int *err;
+    NVISR_TRY_CUDA(sc.alloc(sizeof(int), (void **)&err));
+    NVISR_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     DcnArgs d{};
     d.x = dx; d.cin_pad = cin_pad; d.H = h; d.W = w; d.groups = groups;
-    d.off = offsets; d.mask = mask; d.om_pitch = w; d.om_plane = (int64_t)w * h; d.mask_logits = 0;
+    d.om = (const float *)dom; d.om_cpad = om_cpad; d.mask_logits = 0;
     d.w = dw; d.bias = (const float *)db; d.cout = cout; d.cout_pad = cout_pad; d.y = dy;
-    d.in_dt = DT_F32; d.out_dt = DT_F32; d.acc_scale = 1.f; d.out_scale = 1.f;
-    cudaError_t e = launch_dcn_simt(d, st);
+    d.in_dt = adt; d.out_dt = adt; d.acc_scale = 1.f; d.out_scale = 1.f; d.err = err;
+    cudaError_t e = tc ? launch_dcn_tc(d, st) : launch_dcn_simt(d, st);
     if (e != cudaSuccess) return cuda_status(e, "dcn2d");
-    NVISR_TRY_CUDA(launch_unpack(dy, DT_F32, cout_pad, cout, h, w, 1.f, y, w, st));
+    NVISR_TRY_CUDA(launch_unpack(dy, adt, cout_pad, cout, h, w, 1.f, y, w, st));
+    int herr = 0;
+    NVISR_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+    if (herr) return fail(NVISR_DEVICE_TIMEOUT, "dcn2d: a device-side wait exceeded its bound");
     return NVISR_OK;
 }
 
@@ -1250,6 +1580,19 @@ nvisr_status nvisr_selftest(int32_t *mismatches_bf16, int32_t *mismatches_fp8) {
         return fail(NVISR_CUDA_ERROR, std::string("selftest launch: ") + cudaGetErrorString(se));
     *mismatches_bf16 = h[0];
     *mismatches_fp8 = h[1];
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_selftest_swizzle(int32_t *out16) {
+    if (!out16) return fail(NVISR_INVALID_ARG, "selftest_swizzle: NULL argument");
+    int *d;
+    NVISR_TRY_CUDA(cudaMalloc(&d, 16 * sizeof(int)));
+    cudaMemset(d, 0, 16 * sizeof(int));
+    const int e = tc_probe_sw128(d, 0);
+    const cudaError_t se = cudaDeviceSynchronize();
+    cudaMemcpy(out16, d, 16 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e || se != cudaSuccess) return fail(NVISR_CUDA_ERROR, std::string("selftest_swizzle: ") + cudaGetErrorString(se));
     return NVISR_OK;
 }
 

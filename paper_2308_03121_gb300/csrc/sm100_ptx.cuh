@@ -122,6 +122,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
+// Shared-memory matrix descriptor, 128-byte swizzle, K-major: rows of 128
+// bytes, 8-row groups 1024 bytes apart (SBO); the swizzle XORs the 16-byte
+// unit index with the row index inside the 1024-byte atom.  base_offset is
+// the row phase of a start address that is not 1024-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t base_offset) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;                       // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;             // SBO
+    d |= (uint64_t)1 << 46;                       // descriptor version
+    d |= (uint64_t)(base_offset & 7) << 49;
+    d |= (uint64_t)2 << 61;                       // SWIZZLE_128B
+    return d;
+}
+
 // Instruction descriptor: dense, FP32 accumulator, K-major A and B.
 // fmt: for kind::f16 0 = F16, 1 = BF16; for kind::f8f6f4 0 = E4M3.
 __host__ __device__ constexpr uint32_t instr_desc(int M, int N, int afmt, int bfmt) {
@@ -156,6 +171,20 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                      smem_u32(bar))
                  : "memory");
 }
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane into registers,
+// without waiting (pair with tmem_wait_ld before using the values).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Each thread of the warp loads 16 consecutive 32-bit columns of its TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {

@@ -30,6 +30,7 @@ def run_gpu(text, blob, frames, flags, fin, fout, prec, scale=2, device_io=False
             h = flt.alloc_out_host()
             buf = tuple(to_dev(a) for a in h)
             st, info = flt.pull(buf)
+            torch.cuda.synchronize()  # the pull is enqueued on the engine's stream
             res = tuple(b.cpu().numpy() for b in buf)
             res = tuple(r.view(np.uint16) if r.dtype == np.int16 else r for r in res)
         else:
@@ -217,3 +218,42 @@ def test_budget_rejects_filter():
     assert e.value.status == nv.Status.OVER_BUDGET
     assert eng.bytes_in_use() == 0
     eng.close()
+
+
+def _config3_small(W=144, H=72, n=4):
+    frames = synth.frames_textured(synth.BASE_SEED + 3, n, W, H, 8, "420", "limited")
+    flags = np.zeros(n, bool)
+    flags[2] = True
+    return frames, flags
+
+
+@pytest.fixture(scope="module")
+def config3_oracle():
+    W, H = 144, 72
+    frames, flags = _config3_small(W, H)
+    text, blob = synth.net_config3()
+    fdi, fdo = fmt_dict(W, H, 8), fmt_dict(4 * W, 4 * H, 8)
+    outs = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
+    return [prequant(o, fdo) for o in outs]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_config3_stvsr_dcn_filter(prec, config3_oracle):
+    """Two-frame ST-VSR with deformable alignment, 4x space, 2x frame rate, a cut on frame 2:
+    2 outputs per input (SR of frame i, midpoint i+1/2), the scene's last pair (s1, s1)."""
+    W, H = 144, 72
+    frames, flags = _config3_small(W, H)
+    text, blob = synth.net_config3()
+    outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(4 * W, 4 * H, 8), prec, scale=4)
+    assert len(outs) == 2 * len(frames)
+    assert [i[0] for i in infos] == list(range(8))
+    assert [i[1:] for i in infos] == [(0, 1), (0, 1), (1, 1), (1, 1), (2, 3), (2, 3), (3, 3), (3, 3)]
+    worst = 0
+    for got, pq in zip(outs, config3_oracle):
+        if prec == "fp32":
+            assert_codes_match(got, pq, 8)
+        else:
+            mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 8) for k in "YUV"})
+            worst = max(worst, mx)
+    print(prec, "config-3 max LSB vs oracle:", worst)
+    assert worst <= 1

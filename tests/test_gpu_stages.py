@@ -23,6 +23,14 @@ def test_tensor_core_selftest():
     assert bf16 == 0 and fp8 == 0, (bf16, fp8)
 
 
+def test_swizzle128_descriptor_probe():
+    """Reports which base-offset convention reads rows from inside a 128-byte swizzle atom."""
+    out = nv.nvisr_selftest_swizzle()
+    print("sw128 probe: base offset 0 ->", out[:8].tolist(), " base offset (start>>7)&7 ->", out[8:].tolist())
+    assert out[0] == 0 and out[8] == 0          # atom-aligned start: both conventions agree
+    assert (out[:8] == 0).all() or (out[8:] == 0).all()
+
+
 INGEST_CASES = [
     (64, 64, 8, "420", "full", "left"),
     (1920, 1080, 10, "420", "limited", "left"),
@@ -168,3 +176,27 @@ def test_dcn2d_fp32_matches_oracle(cin, groups, H, W):
     ref = oracle.dcn2d(x, off, m, w, b, groups)
     err = np.abs(got.double().cpu().numpy() - ref).max()
     assert err < 5e-5, err
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("groups,H,W", [(8, 12, 140), (8, 5, 64), (2, 3, 257)])
+def test_dcn2d_tensor_core_matches_oracle(prec, groups, H, W):
+    """Tensor-core DCN: operands rounded as the kernel stores them; the sampled
+    im2col values and the output are rounded once more to 16 bits, so the
+    tolerance is two half-ulps of the magnitude sum |w| |sample|."""
+    cin = cout = 64
+    x, off, m = synth.dcn_operands(7 * W + groups, cin, H, W, groups)
+    rs = np.random.default_rng(groups + W)
+    w = (rs.normal(size=(cout, cin, 3, 3)) * np.sqrt(2.0 / (9 * cin))).astype(np.float32)
+    b = rs.uniform(-0.1, 0.1, size=cout).astype(np.float32)
+    got = nv.nvisr_dcn2d(prec, torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda(), torch.from_numpy(m).cuda(),
+                         torch.from_numpy(w).cuda(), torch.from_numpy(b).cuda(), groups)
+    torch.cuda.synchronize()
+    q = _bf16 if prec == "bf16" else _f16
+    xq, wq = q(x), q(w)
+    ref = oracle.dcn2d(xq, off, m, wq, b, groups)
+    mag = oracle.dcn2d(np.abs(xq), off, m, np.abs(wq), None, groups)
+    ulp = 2.0 ** -8 if prec == "bf16" else 2.0 ** -11
+    tol = ulp * (mag + np.abs(ref)) + 1e-5
+    err = np.abs(got.double().cpu().numpy() - ref)
+    assert (err <= tol).all(), (err.max(), np.argwhere(err > tol)[:3])
