@@ -17,8 +17,16 @@ namespace nvisr {
 enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2, DT_E4M3 = 3 };
 
 inline int dtype_size(int dt) { return dt == DT_F32 ? 4 : (dt == DT_E4M3 ? 1 : 2); }
-// Channels per 16-byte chunk of the blocked layout [C/cpc][H][W][cpc].
+// Channels per 16-byte unit.
 inline int chunk_channels(int dt) { return 16 / dtype_size(dt); }
+// Channels per chunk of the blocked layout [C/cpc][H][W][cpc] of a tensor:
+// 16-bit tensors whose padded channel count is a multiple of 64 use 64-channel
+// (128-byte) chunks -- one 128-byte-swizzled TMA row per pixel -- and every
+// other tensor uses 16-byte chunks.
+inline int layout_cpc(int dt, int cpad) {
+    if ((dt == DT_BF16 || dt == DT_F16) && cpad % 64 == 0) return 64;
+    return chunk_channels(dt);
+}
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 inline int64_t round_up64(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
@@ -41,9 +49,20 @@ cudaError_t launch_ingest(const nvisr_format &fmt, const void *y, int64_t py, co
                           int64_t pu, const void *v, int64_t pv, float *out, int64_t out_pitch,
                           cudaStream_t st);
 
-// requantise: float32 planar R'G'B' -> integer planes.
+// The network's skip path: the mean of up to two input frames (planar float32
+// [3][h][pitch]) upsampled by an integer scale (1 nearest, 2 bilinear with
+// align_corners = false and edge clamp), added to the network's residual.
+struct SkipArgs {
+    const float *src[2];
+    int n;               // 0 = no skip
+    int64_t pitch, plane;
+    int h, w, scale, mode;
+};
+
+// requantise: float32 planar R'G'B' (+ skip) -> integer planes.
 cudaError_t launch_requant(const nvisr_format &fmt, const float *in, int64_t in_pitch, void *y,
-                           int64_t py, void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st);
+                           int64_t py, void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st,
+                           const SkipArgs *skip = nullptr);
 
 // Up to 8 planar float32 frames of 3 channels each (tuple, frame-major
 // channels) or one planar tensor of C channels -> blocked tensor of dtype dt
@@ -60,19 +79,22 @@ struct PackArgs {
     void *dst;
     int cpad;
     int dt;
+    int cpc;             // channels per chunk of dst (0 = one 16-byte unit)
     float scale;
     unsigned *amax;
 };
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t st);
 
-// blocked tensor -> planar float32 [C][H][W] (first C channels; value*scale).
-cudaError_t launch_unpack(const void *src, int dt, int cpad, int C, int H, int W, float scale,
+// blocked tensor (cpc channels per chunk) -> planar float32 [C][H][W]
+// (first C channels; value*scale).
+cudaError_t launch_unpack(const void *src, int dt, int cpad, int cpc, int C, int H, int W, float scale,
                           float *dst, int64_t dst_pitch, cudaStream_t st);
 
 // Convolution layer (3x3 or 1x1, stride 1, zero padding) on blocked tensors.
 struct ConvArgs {
     const void *x;           // blocked input [cin_pad/cpc][H][W][cpc] per image
     int cin_pad;
+    int in_cpc, out_cpc;     // channels per chunk of x and of y/res (0 = 16-byte units)
     int H, W;
     int nimg;                // images stacked along the outer dimension
     const void *w;           // prepared weights (kernel-specific layout)
@@ -110,8 +132,10 @@ void prepare_weights_simt(const float *w_oihw, int cout, int cin, int k, int cin
                           float *dst_host);
 // Tensor-core layout: canonical no-swizzle K-major core-matrix image per N slice.
 size_t tc_weight_bytes(int cin_pad, int cout_pad, int k, int dt);
+// sw128: 128-byte-swizzled image in 64-channel K chunks (for inputs stored with
+// 64-channel chunks); otherwise the no-swizzle image in 16-byte K chunks.
 void prepare_weights_tc(const float *w_oihw, int cout, int cin, int k, int cin_pad, int cout_pad,
-                        int dt, float scale, void *dst_host);
+                        int dt, float scale, void *dst_host, bool sw128);
 int tc_nslice(int cin_pad, int cout_pad, int k, int dt);
 
 // DCN: x blocked (activation dtype); offsets and mask in one blocked float32
@@ -120,6 +144,7 @@ int tc_nslice(int cin_pad, int cout_pad, int k, int dt);
 struct DcnArgs {
     const void *x;
     int cin_pad, H, W, groups;
+    int x_cpc, y_cpc;        // channels per chunk of x and y (0 = 16-byte units)
     const float *om;
     int om_cpad;
     int mask_logits;

@@ -40,7 +40,10 @@ namespace nvisr {
 namespace {
 
 constexpr int TM = 128;
-constexpr int NTHREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-5: epilogue
+// warp 0: TMA producer, warp 1: MMA issuer + TMEM owner, warps 2-9: epilogue
+// (two warps per TMEM lane quadrant, each owning half of the accumulator columns)
+constexpr int NTHREADS = 320;
+constexpr int NEPI = 256;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 232448;  // 227 KB per CTA
 constexpr int SMEM_HDR = 1024;      // barriers + TMEM slot + abort flag
@@ -122,7 +125,7 @@ __device__ __forceinline__ void store_vals(uint8_t *base, int64_t chunk_stride, 
 // kernel size; NCH: 16-byte chunks per pipeline stage (even); EPI: 0 blocked
 // store, 1 PixelShuffle(2) + skip into planar float32, 2 PixelShuffle(2) +
 // activation into a blocked tensor at twice the resolution.
-template <int IN_DT, int OUT_DT, int NS, int KS, int NCH, int EPI>
+template <int IN_DT, int OUT_DT, int NS, int KS, int NCH, int EPI, int CBI, int CBO>
 __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                               const TcParams p) {
     using TI = typename Elem<IN_DT>::T;
@@ -133,12 +136,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
     constexpr int ROWS = KS;
     constexpr int PXS = TM + KS - 1;
     constexpr int PAD = (KS - 1) / 2;
+    // CBI == 16: input chunks are 16 bytes, the stage is [chunk][row][px][16 B]
+    //            (no swizzle; LBO_A = chunk stride).
+    // CBI == 128: input chunks are 64 channels (128 bytes), TMA writes each as
+    //            a 128-byte-swizzled [row][px][128 B] region of CREG bytes.
     constexpr uint32_t LBO_A = ROWS * PXS * 16;
-    // TMA destinations must be 128-byte aligned: stages are padded to 1 KB.
-    constexpr uint32_t STAGE_BYTES = (NCH * LBO_A + 1023u) & ~1023u;
+    constexpr uint32_t CREG = (ROWS * PXS * 128 + 1023u) & ~1023u;
+    // TMA destinations must be 128-byte aligned (1 KB for the swizzled atoms).
+    constexpr uint32_t STAGE_BYTES = CBI == 16 ? ((NCH * LBO_A + 1023u) & ~1023u) : NCH * CREG;
+    constexpr uint32_t TX_BYTES = CBI == 16 ? NCH * LBO_A : NCH * ROWS * PXS * 128;
     constexpr uint32_t NCOLS = (2 * NS <= 32) ? 32 : (2 * NS <= 64 ? 64 : (2 * NS <= 128 ? 128 : (2 * NS <= 256 ? 256 : 512)));
-    constexpr int CPC_O = 16 / sizeof(TO);
-    static_assert(NCH % 2 == 0, "an MMA consumes two 16-byte K chunks");
+    constexpr int CPC_O = CBO / sizeof(TO);  // output channels per chunk
+    constexpr int UPC_O = 16 / sizeof(TO);   // output channels per 16-byte unit
+    static_assert(CBI == 128 || NCH % 2 == 0, "an MMA consumes two 16-byte K chunks");
+    static_assert(CBI == 16 || KIND == 0, "swizzled inputs are 16-bit");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -150,11 +161,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
     uint64_t *wbar = tempty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *sbias = reinterpret_cast<float *>(smem + 512);  // this slice's NS biases
     uint8_t *wsm = smem + SMEM_HDR;
     uint8_t *stage0 = wsm + ((p.wbytes + 1023) & ~1023u);
+    static_assert(NS * 4 <= 512, "bias staging fits the header");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slice = blockIdx.x % p.nslice;
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + NS) sbias[threadIdx.x - 64] = p.bias[slice * NS + threadIdx.x - 64];
     const int cta_stride = gridDim.x / p.nslice;
     const int cta0 = blockIdx.x / p.nslice;
     const int tiles_x = (p.W + TM - 1) / TM;
@@ -168,7 +182,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 4 * 32);
+            mbar_init(&tempty[a], NEPI);
         }
         mbar_init(wbar, 1);
         *abort = 0;
@@ -207,9 +221,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[s], NCH * LBO_A);
-                    tma_load_4d(stage0 + (size_t)s * STAGE_BYTES, &tmap, &full[s], 0, x0 - PAD, y - PAD,
-                                img * p.cin_chunks + g * NCH);
+                    mbar_arrive_expect_tx(&full[s], TX_BYTES);
+                    if (CBI == 16) {
+                        tma_load_4d(stage0 + (size_t)s * STAGE_BYTES, &tmap, &full[s], 0, x0 - PAD, y - PAD,
+                                    img * p.cin_chunks + g * NCH);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c)
+                            tma_load_4d(stage0 + (size_t)s * STAGE_BYTES + c * CREG, &tmap, &full[s], 0, x0 - PAD,
+                                        y - PAD, img * p.cin_chunks + g * NCH + c);
+                    }
                     ++issued;
                     if (++s == S) { s = 0; ph ^= 1; }
                 }
@@ -248,17 +269,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
                     }
                     tc_fence_after();
                     // descriptors of tap 0 / K-step 0; others add (byte offset >> 4) to the start field
-                    const uint64_t a0 = smem_desc(smem_u32(stage0 + (size_t)s * STAGE_BYTES), LBO_A, 128);
-                    const uint64_t b0 = smem_desc(wbase + (uint32_t)(g * NCH) * (uint32_t)(NS * 16), NS * 16, 128);
+                    if (CBI == 16) {
+                        const uint64_t a0 = smem_desc(smem_u32(stage0 + (size_t)s * STAGE_BYTES), LBO_A, 128);
+                        const uint64_t b0 = smem_desc(wbase + (uint32_t)(g * NCH) * (uint32_t)(NS * 16), NS * 16, 128);
 #pragma unroll 1
-                    for (int tap = 0; tap < KS * KS; ++tap) {
-                        const int ky = tap / KS, kx = tap % KS;
-                        const uint64_t at = a0 + (uint64_t)((ky * PXS + kx) * 16 >> 4);
-                        const uint64_t bt = b0 + (uint64_t)((uint32_t)(tap * p.cin_chunks) * (uint32_t)NS);
+                        for (int tap = 0; tap < KS * KS; ++tap) {
+                            const int ky = tap / KS, kx = tap % KS;
+                            const uint64_t at = a0 + (uint64_t)((ky * PXS + kx) * 16 >> 4);
+                            const uint64_t bt = b0 + (uint64_t)((uint32_t)(tap * p.cin_chunks) * (uint32_t)NS);
 #pragma unroll
-                        for (int j = 0; j < NCH / 2; ++j) {
-                            umma<KIND>(d_tmem, at + (uint64_t)(2 * j * (LBO_A >> 4)),
-                                       bt + (uint64_t)(2 * j * NS), IDESC, (g | tap | j) != 0 ? 1u : 0u);
+                            for (int j = 0; j < NCH / 2; ++j) {
+                                umma<KIND>(d_tmem, at + (uint64_t)(2 * j * (LBO_A >> 4)),
+                                           bt + (uint64_t)(2 * j * NS), IDESC, (g | tap | j) != 0 ? 1u : 0u);
+                            }
+                        }
+                    } else {
+                        // 128-byte swizzle: a tap's A rows start (ky*PXS + kx) rows into the region;
+                        // the swizzle is a function of the address, so any row start is valid with
+                        // base offset 0.  K advances 32 bytes (16 BF16/FP16) per MMA inside a row.
+                        const uint64_t a0 = smem_desc_sw128(smem_u32(stage0 + (size_t)s * STAGE_BYTES), 0);
+                        const uint64_t b0 = smem_desc_sw128(wbase + (uint32_t)(g * NCH) * (uint32_t)(NS * 128), 0);
+#pragma unroll 1
+                        for (int tap = 0; tap < KS * KS; ++tap) {
+                            const int ky = tap / KS, kx = tap % KS;
+                            const uint64_t at = a0 + (uint64_t)((ky * PXS + kx) * 128 >> 4);
+                            const uint64_t bt = b0 + (uint64_t)((uint32_t)(tap * p.cin_chunks) * (uint32_t)(NS * 128 >> 4));
+#pragma unroll
+                            for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j)
+                                    umma<KIND>(d_tmem, at + (uint64_t)((c * CREG + j * 32) >> 4),
+                                               bt + (uint64_t)((c * NS * 128 + j * 32) >> 4), IDESC,
+                                               (g | tap | c | j) != 0 ? 1u : 0u);
                         }
                     }
                     umma_commit(&empty[s]);
@@ -273,9 +315,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
             if (last_a >= 0) mbar_wait_bounded(&tfull[last_a], last_par, nullptr, WAIT_NS);
         }
     } else {
-        // ---------------- epilogue: warps 2..5 own TMEM lane quadrants (warp % 4)
+        // ---------------- epilogue: warps 2..9; warp w owns TMEM lane quadrant (w % 4)
+        // and accumulator columns [half * NH, (half + 1) * NH) of the slice
         const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        constexpr int NH = NS / 2;
+        constexpr int NRU = (EPI == 0) ? NH / UPC_O : 1;  // 16-byte output units per thread
         const int m = q * 32 + lane;
+        const int col0 = half * NH;                        // first column (slice-local channel)
+        const int64_t HW = (int64_t)p.H * p.W;
+        auto unit_addr = [&](uint8_t *base, int ocn, int img, int n, int64_t pix, int64_t hw) -> uint8_t * {
+            return base + (((int64_t)img * (ocn / CPC_O) + n / CPC_O) * hw + pix) * CBO +
+                   (int64_t)(n % CPC_O) * (int64_t)sizeof(TO);
+        };
+        // residual prefetch one tile ahead: the next tile's loads are in flight
+        // while this tile is finished
+        uint4 rnext[NRU];
+        auto prefetch = [&](int t2) {
+            if (EPI != 0 || !p.res || t2 >= ntiles) return;
+            const int img2 = t2 / (tiles_x * p.H);
+            const int r2 = t2 - img2 * tiles_x * p.H;
+            const int y2 = r2 / tiles_x;
+            const int x2 = (r2 - y2 * tiles_x) * TM + m;
+            if (x2 >= p.W) return;
+            const int64_t pix2 = (int64_t)y2 * p.W + x2;
+#pragma unroll
+            for (int uu = 0; uu < NRU; ++uu)
+                rnext[uu] = __ldg(reinterpret_cast<const uint4 *>(unit_addr(
+                    const_cast<uint8_t *>(p.res), p.cout_pad, img2, slice * NS + col0 + uu * UPC_O, pix2, HW)));
+        };
+        prefetch(cta0);
         int it = 0;
         for (int t = cta0; t < ntiles; t += cta_stride, ++it) {
             const int a = it & 1;
@@ -285,19 +354,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
             const int y = r / tiles_x;
             const int x = (r - y * tiles_x) * TM + m;
             const bool valid = x < p.W;
-            const int64_t HW = (int64_t)p.H * p.W;
-            // residual of this tile: loads issued before the accumulator wait so
-            // their latency overlaps the tile's MMAs
-            constexpr int NRC = NS / CPC_O;
-            uint4 rres[EPI == 0 ? NRC : 1];
-            if (EPI == 0 && p.res && valid) {
-                const uint8_t *rbase =
-                    p.res + ((int64_t)img * (p.cout_pad / CPC_O) * HW + (int64_t)y * p.W + x) * 16;
-                const int c00 = slice * NS / CPC_O;
+            uint4 rres[NRU];
 #pragma unroll
-                for (int c = 0; c < NRC; ++c)
-                    rres[c] = __ldg(reinterpret_cast<const uint4 *>(rbase + (int64_t)(c00 + c) * HW * 16));
-            }
+            for (int uu = 0; uu < NRU; ++uu) rres[uu] = rnext[uu];
+            prefetch(t + cta_stride);
             bool ok = mbar_wait_bounded(&tfull[a], u & 1, abort, WAIT_NS);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
@@ -305,119 +365,104 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
                 break;
             }
             tc_fence_after();
-            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * NS);
-            if (EPI == 0) {
-                const int ochunks = p.cout_pad / CPC_O;
-                const int64_t pix = (int64_t)y * p.W + x;
-                const int64_t cstride = HW * 16;
-                float v[NS];
-                {
-                    uint32_t r[NS / 16][16];
-#pragma unroll
-                    for (int j = 0; j < NS / 16; ++j) tmem_ld16_nowait(taddr + (uint32_t)(j * 16), r[j]);
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * NS + col0);
+            float v[NH];
+            {
+                if constexpr (NH == 8) {
+                    uint32_t r8[8];
+                    tmem_ld8_nowait(taddr, r8);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < NS / 16; ++j)
+                    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r8[e]);
+                } else {
+                    uint32_t rr[NH / 16][16];
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) v[j * 16 + e] = __uint_as_float(r[j][e]);
+                    for (int j = 0; j < NH / 16; ++j) tmem_ld16_nowait(taddr + (uint32_t)(j * 16), rr[j]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < NH / 16; ++j)
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[j * 16 + e] = __uint_as_float(rr[j][e]);
                 }
-                if (valid) {
-                    const int n0 = slice * NS;
+            }
+            if (valid) {
 #pragma unroll
-                    for (int e = 0; e < NS; ++e) {
-                        float o = v[e] * p.acc_scale + p.bias[n0 + e];
-                        if (p.act == 1) o = lrelu(o);
-                        v[e] = o;
-                    }
+                for (int e = 0; e < NH; ++e) {
+                    float o = v[e] * p.acc_scale + sbias[col0 + e];
+                    if (EPI != 1 && p.act == 1) o = lrelu(o);
+                    v[e] = o;
+                }
+                if (EPI == 0) {
+                    const int64_t pix = (int64_t)y * p.W + x;
+                    const int n0 = slice * NS + col0;
                     if (p.res) {
 #pragma unroll
-                        for (int c = 0; c < NRC; ++c) {
-                            alignas(16) TO rv[CPC_O];
-                            *reinterpret_cast<uint4 *>(rv) = rres[c];
+                        for (int uu = 0; uu < NRU; ++uu) {
+                            alignas(16) TO rv[UPC_O];
+                            *reinterpret_cast<uint4 *>(rv) = rres[uu];
 #pragma unroll
-                            for (int e = 0; e < CPC_O; ++e) v[c * CPC_O + e] += from_elem<TO>(rv[e]) / p.out_scale;
+                            for (int e = 0; e < UPC_O; ++e) v[uu * UPC_O + e] += from_elem<TO>(rv[e]) / p.out_scale;
                         }
                     }
-                    uint8_t *ybase = p.y + ((int64_t)img * ochunks * HW + pix) * 16;
                     if (p.amax) {
                         float amax = 0.f;
 #pragma unroll
-                        for (int e = 0; e < NS; ++e) amax = fmaxf(amax, fabsf(v[e]));
+                        for (int e = 0; e < NH; ++e) amax = fmaxf(amax, fabsf(v[e]));
                         atomicMax(p.amax, __float_as_uint(amax));
                     }
-                    if (p.y2) {
-                        float w2[NS];
+                    if (p.y2) {  // FP8 copy, 16-channel (16-byte) chunks
 #pragma unroll
-                        for (int e = 0; e < NS; ++e) w2[e] = v[e] * p.y2_scale;
-                        store_vals<__nv_fp8_e4m3>(p.y2 + ((int64_t)img * (p.cout_pad / 16) * HW + pix) * 16, cstride,
-                                                  n0 / 16, w2, NS);
-                    }
-                    if (p.out_scale != 1.0f) {
+                        for (int c = 0; c < NH / 16; ++c) {
+                            alignas(16) __nv_fp8_e4m3 o8[16];
 #pragma unroll
-                        for (int e = 0; e < NS; ++e) v[e] *= p.out_scale;
+                            for (int e = 0; e < 16; ++e) o8[e] = __nv_fp8_e4m3(v[c * 16 + e] * p.y2_scale);
+                            *reinterpret_cast<uint4 *>(
+                                p.y2 + (((int64_t)img * (p.cout_pad / 16) + n0 / 16 + c) * HW + pix) * 16) =
+                                *reinterpret_cast<const uint4 *>(o8);
+                        }
                     }
-                    store_vals<TO>(ybase, cstride, n0 / CPC_O, v, NS);
-                }
-            } else if (EPI == 1) {
-                // PixelShuffle(2) of channels [0, cout) + skip -> planar float32 at (2y, 2x)
-                float v[16];
-                tmem_ld16(taddr, v);
-                if (valid) {
+#pragma unroll
+                    for (int uu = 0; uu < NRU; ++uu) {
+                        alignas(16) TO o[UPC_O];
+#pragma unroll
+                        for (int e = 0; e < UPC_O; ++e) o[e] = to_elem<TO>(v[uu * UPC_O + e] * p.out_scale);
+                        *reinterpret_cast<uint4 *>(unit_addr(p.y, p.cout_pad, img, n0 + uu * UPC_O, pix, HW)) =
+                            *reinterpret_cast<const uint4 *>(o);
+                    }
+                } else if (EPI == 1) {
+                    // PixelShuffle(2): this warp's channels col0..col0+NH-1 are shuffled channels
+                    // col0/4 .. at sub-positions (i, j) = (n % 4) / 2, n % 2; planar float32 out
                     const int H2 = 2 * p.H;
 #pragma unroll
-                    for (int c = 0; c < NS / 4; ++c) {
+                    for (int cl = 0; cl < NH / 4; ++cl) {
+                        const int c = col0 / 4 + cl;
                         if (c >= p.cout / 4) break;
-                        float o[4];
-#pragma unroll
-                        for (int ij = 0; ij < 4; ++ij) {
-                            const int n = c * 4 + ij;
-                            const int Y = 2 * y + (ij >> 1), X = 2 * x + (ij & 1);
-                            o[ij] = v[n] * p.acc_scale + p.bias[n] +
-                                    skip_value(p.skip, c, Y, X, p.skip.skip_scale, p.skip.skip_h, p.skip.skip_w);
-                        }
                         float *dst = p.ps_out + (int64_t)img * (p.cout / 4) * p.ps_pitch * H2 +
                                      (int64_t)c * p.ps_pitch * H2 + (int64_t)(2 * y) * p.ps_pitch + 2 * x;
-                        *reinterpret_cast<float2 *>(dst) = make_float2(o[0], o[1]);
-                        *reinterpret_cast<float2 *>(dst + p.ps_pitch) = make_float2(o[2], o[3]);
+                        *reinterpret_cast<float2 *>(dst) = make_float2(v[cl * 4 + 0], v[cl * 4 + 1]);
+                        *reinterpret_cast<float2 *>(dst + p.ps_pitch) = make_float2(v[cl * 4 + 2], v[cl * 4 + 3]);
                     }
-                }
-            } else {
-                // PixelShuffle(2) into a blocked tensor [C/4 / CPC_O][2H][2W][CPC_O], then activation.
-                float v[NS];
-#pragma unroll
-                for (int j = 0; j < NS / 16; ++j) {
-                    float t16[16];
-                    tmem_ld16(taddr + (uint32_t)(j * 16), t16);
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) v[j * 16 + e] = t16[e];
-                }
-                if (valid) {
-                    const int n_base = slice * NS;
-#pragma unroll
-                    for (int e = 0; e < NS; ++e) {
-                        float o = v[e] * p.acc_scale + p.bias[n_base + e];
-                        if (p.act == 1) o = lrelu(o);
-                        v[e] = o;
-                    }
-                    const int cps = p.cout / 4;                 // shuffled channels
+                } else {
+                    // PixelShuffle(2) into a blocked tensor of cout/4 channels at twice the resolution:
+                    // this warp's NH columns are shuffled channels c_base .. c_base + NH/4 - 1
+                    const int cps = p.cout / 4;
                     const int64_t HW4 = 4 * HW;
-                    const int c_base = n_base / 4;              // first shuffled channel of this slice
+                    const int c_base = (slice * NS + col0) / 4;
 #pragma unroll
                     for (int ij = 0; ij < 4; ++ij) {
                         const int Y = 2 * y + (ij >> 1), X = 2 * x + (ij & 1);
                         const int64_t pix2 = (int64_t)Y * (2 * p.W) + X;
 #pragma unroll
-                        for (int h = 0; h < NS / 4 / CPC_O; ++h) {
-                            float o[CPC_O];
+                        for (int h = 0; h < NH / 4 / UPC_O; ++h) {
+                            alignas(16) TO o[UPC_O];
 #pragma unroll
-                            for (int e = 0; e < CPC_O; ++e) {
-                                float val = v[(h * CPC_O + e) * 4 + ij];
+                            for (int e = 0; e < UPC_O; ++e) {
+                                float val = v[(h * UPC_O + e) * 4 + ij];
                                 if (p.ps_act == 1) val = lrelu(val);
-                                o[e] = val * p.out_scale;
+                                o[e] = to_elem<TO>(val * p.out_scale);
                             }
-                            const int cc = (c_base / CPC_O) + h;
-                            store_vals<TO>(p.y + ((int64_t)img * (cps / CPC_O) * HW4 + pix2) * 16, HW4 * 16, cc, o,
-                                           CPC_O);
+                            *reinterpret_cast<uint4 *>(unit_addr(p.y, cps, img, c_base + h * UPC_O, pix2, HW4)) =
+                                *reinterpret_cast<const uint4 *>(o);
                         }
                     }
                 }
@@ -597,18 +642,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-int pick_ns(int cin_chunks, int cout_pad, int k) {
-    const int per_n = k * k * cin_chunks * 16;
+// Output channels per CTA slice: the largest of 64/32/16 dividing cout_pad whose
+// weights (k*k*cin_bytes per output channel) fit the resident budget.
+int pick_ns(int cin_bytes, int cout_pad, int k) {
+    const int per_n = k * k * cin_bytes;
     for (int ns : {64, 32, 16}) {
         if (cout_pad % ns == 0 && ns * per_n <= W_MAX) return ns;
     }
     return 16;
 }
 
-template <int IN_DT, int OUT_DT, int NS, int KS, int NCH, int EPI>
+template <int IN_DT, int OUT_DT, int NS, int KS, int NCH, int EPI, int CBI, int CBO>
 cudaError_t run(const CUtensorMap &map, TcParams p, cudaStream_t st) {
     constexpr int PXS = TM + KS - 1;
-    constexpr uint32_t STAGE_BYTES = (NCH * KS * PXS * 16 + 1023u) & ~1023u;
+    constexpr uint32_t CREG = (KS * PXS * 128 + 1023u) & ~1023u;
+    constexpr uint32_t STAGE_BYTES = CBI == 16 ? ((NCH * KS * PXS * 16 + 1023u) & ~1023u) : NCH * CREG;
     const uint32_t wround = (p.wbytes + 1023) & ~1023u;
     const int avail = SMEM_LIMIT - 1024 /*align slack*/ - SMEM_HDR - (int)wround;
     int stages = avail / (int)STAGE_BYTES;
@@ -618,7 +666,7 @@ cudaError_t run(const CUtensorMap &map, TcParams p, cudaStream_t st) {
     // request at least 116 KB so one CTA occupies an SM (TMEM and scheduling assume it)
     int smem = 1024 + SMEM_HDR + (int)wround + stages * (int)STAGE_BYTES;
     if (smem < 118 * 1024) smem = 118 * 1024;
-    auto kern = conv_tc_kernel<IN_DT, OUT_DT, NS, KS, NCH, EPI>;
+    auto kern = conv_tc_kernel<IN_DT, OUT_DT, NS, KS, NCH, EPI, CBI, CBO>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int tiles = ((p.W + TM - 1) / TM) * p.H * p.nimg;
@@ -633,61 +681,63 @@ cudaError_t run(const CUtensorMap &map, TcParams p, cudaStream_t st) {
 using Runner = cudaError_t (*)(const CUtensorMap &, TcParams, cudaStream_t);
 
 struct Variant {
-    int in_dt, out_dt, ns, ks, nch, epi;
+    int in_dt, out_dt, ns, ks, nch, epi, cbi, cbo;
     Runner fn;
 };
 
-#define NVISR_V(I, O, NS_, KS_, NCH_, EPI_) {I, O, NS_, KS_, NCH_, EPI_, &run<I, O, NS_, KS_, NCH_, EPI_>}
-#define NVISR_V16(I, NS_, KS_, NCH_, EPI_) NVISR_V(I, I, NS_, KS_, NCH_, EPI_)
+#define NVISR_V(I, O, NS_, KS_, NCH_, EPI_, CBI_, CBO_) \
+    {I, O, NS_, KS_, NCH_, EPI_, CBI_, CBO_, &run<I, O, NS_, KS_, NCH_, EPI_, CBI_, CBO_>}
+#define NVISR_V16(I, NS_, KS_, NCH_, EPI_, CBI_, CBO_) NVISR_V(I, I, NS_, KS_, NCH_, EPI_, CBI_, CBO_)
+#define NVISR_VSET(I)                                                                                   \
+    /* 64-channel (128-byte swizzled) inputs: bodies, tails, 1x1 blends, upsamplers */                  \
+    NVISR_V16(I, 64, 3, 1, 0, 128, 128), NVISR_V16(I, 16, 3, 1, 1, 128, 16),                             \
+    NVISR_V16(I, 64, 1, 1, 0, 128, 128), NVISR_V16(I, 64, 3, 1, 2, 128, 128),                           \
+    NVISR_V16(I, 32, 3, 1, 0, 128, 16), NVISR_V16(I, 16, 3, 1, 0, 128, 16),                              \
+    NVISR_V(I, DT_F32, 32, 3, 1, 0, 128, 16),                                                           \
+    /* 16-byte-chunk inputs (16 / 32 channels): heads, extract convs, narrow nets */                     \
+    NVISR_V16(I, 64, 3, 2, 0, 16, 128), NVISR_V16(I, 64, 3, 4, 0, 16, 128),                              \
+    NVISR_V16(I, 32, 3, 2, 0, 16, 16), NVISR_V16(I, 32, 3, 4, 0, 16, 16),                                \
+    NVISR_V16(I, 16, 3, 2, 0, 16, 16), NVISR_V16(I, 16, 3, 4, 0, 16, 16), NVISR_V16(I, 16, 3, 4, 1, 16, 16)
 
 const Variant kVariants[] = {
-    // 16-bit operands: heads, bodies, tails of the tuple networks; DCN-net layers
-    NVISR_V16(DT_BF16, 64, 3, 2, 0), NVISR_V16(DT_BF16, 64, 3, 4, 0), NVISR_V16(DT_BF16, 64, 3, 8, 0),
-    NVISR_V16(DT_BF16, 32, 3, 2, 0), NVISR_V16(DT_BF16, 32, 3, 4, 0), NVISR_V16(DT_BF16, 32, 3, 8, 0),
-    NVISR_V16(DT_BF16, 16, 3, 4, 1), NVISR_V16(DT_BF16, 16, 3, 8, 1), NVISR_V16(DT_BF16, 64, 1, 8, 0),
-    NVISR_V16(DT_BF16, 64, 3, 8, 2), NVISR_V16(DT_BF16, 16, 3, 2, 0), NVISR_V16(DT_BF16, 16, 3, 4, 0),
-    NVISR_V16(DT_BF16, 16, 3, 8, 0),
-    NVISR_V16(DT_F16, 64, 3, 2, 0), NVISR_V16(DT_F16, 64, 3, 4, 0), NVISR_V16(DT_F16, 64, 3, 8, 0),
-    NVISR_V16(DT_F16, 32, 3, 2, 0), NVISR_V16(DT_F16, 32, 3, 4, 0), NVISR_V16(DT_F16, 32, 3, 8, 0),
-    NVISR_V16(DT_F16, 16, 3, 4, 1), NVISR_V16(DT_F16, 16, 3, 8, 1), NVISR_V16(DT_F16, 64, 1, 8, 0),
-    NVISR_V16(DT_F16, 64, 3, 8, 2), NVISR_V16(DT_F16, 16, 3, 2, 0), NVISR_V16(DT_F16, 16, 3, 4, 0),
-    NVISR_V16(DT_F16, 16, 3, 8, 0),
-    // FP32 output (offset/mask heads feeding a DCN keep full-precision offsets)
-    NVISR_V(DT_BF16, DT_F32, 32, 3, 8, 0), NVISR_V(DT_F16, DT_F32, 32, 3, 8, 0),
-    // FP8 E4M3 operands (bodies): output BF16 trunk (+ FP8 copy) or FP8 directly
-    NVISR_V(DT_E4M3, DT_BF16, 64, 3, 4, 0), NVISR_V(DT_E4M3, DT_E4M3, 64, 3, 4, 0),
+    NVISR_VSET(DT_BF16),
+    NVISR_VSET(DT_F16),
+    // FP8 E4M3 operands (64-channel bodies, 16-byte chunks): BF16 trunk out, or FP8 out
+    NVISR_V(DT_E4M3, DT_BF16, 64, 3, 4, 0, 16, 128), NVISR_V(DT_E4M3, DT_E4M3, 64, 3, 4, 0, 16, 16),
 };
 
 }  // namespace
 
 int tc_nslice(int cin_pad, int cout_pad, int k, int dt) {
-    const int cin_chunks = cin_pad / chunk_channels(dt);
-    return cout_pad / pick_ns(cin_chunks, cout_pad, k);
+    return cout_pad / pick_ns(cin_pad * dtype_size(dt), cout_pad, k);
 }
 
 size_t tc_weight_bytes(int cin_pad, int cout_pad, int k, int dt) {
-    return (size_t)k * k * (cin_pad / chunk_channels(dt)) * cout_pad * 16;
+    return (size_t)k * k * cin_pad * dtype_size(dt) * cout_pad;
 }
 
 void prepare_weights_tc(const float *w, int cout, int cin, int k, int cin_pad, int cout_pad, int dt, float scale,
-                        void *dst) {
-    const int cpc = chunk_channels(dt);
+                        void *dst, bool sw128) {
     const int esz = dtype_size(dt);
-    const int cin_chunks = cin_pad / cpc;
-    const int ns = pick_ns(cin_chunks, cout_pad, k);
+    const int ns = pick_ns(cin_pad * esz, cout_pad, k);
     const int kk = k * k;
     uint8_t *out = static_cast<uint8_t *>(dst);
     const size_t total = tc_weight_bytes(cin_pad, cout_pad, k, dt);
     for (size_t i = 0; i < total; ++i) out[i] = 0;
-    // slice sl, tap t, chunk kc, local row n, element e -> byte offset
+    // no swizzle: [slice][tap][16-byte K chunk][n][16 B]
+    // sw128:      [slice][tap][64-channel K chunk][n][128 B], 16-byte unit u of row n at u ^ (n & 7)
+    const int cpc = sw128 ? 64 : 16 / esz;
+    const int cb = cpc * esz;
+    const int cin_chunks = cin_pad / cpc;
     for (int o = 0; o < cout; ++o) {
         const int sl = o / ns, n = o % ns;
         for (int c = 0; c < cin; ++c) {
             const int kc = c / cpc, e = c % cpc;
             for (int t = 0; t < kk; ++t) {
                 const float v = w[((size_t)o * cin + c) * kk + t] * scale;
-                const size_t off = (size_t)sl * kk * cin_chunks * ns * 16 +
-                                   (((size_t)t * cin_chunks + kc) * ns + n) * 16 + (size_t)e * esz;
+                size_t off = (size_t)sl * kk * cin_chunks * ns * cb + (((size_t)t * cin_chunks + kc) * ns + n) * cb;
+                if (sw128) off += (size_t)(((e * esz / 16) ^ (n & 7)) * 16 + (e * esz) % 16);
+                else off += (size_t)e * esz;
                 if (dt == DT_BF16) {
                     __nv_bfloat16 h = __float2bfloat16_rn(v);
                     memcpy(out + off, &h, 2);
@@ -706,36 +756,44 @@ void prepare_weights_tc(const float *w, int cout, int cin, int k, int cin_pad, i
 cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
     const int dt = a.in_dt;
     if (dt == DT_F32) return cudaErrorInvalidValue;
-    const int cpc = chunk_channels(dt);
-    if (a.cin_pad % cpc) return cudaErrorInvalidValue;
-    const int cin_chunks = a.cin_pad / cpc;
-    const int ns = pick_ns(cin_chunks, a.cout_pad, a.k);
-    const int nch = cin_chunks >= 8 ? 8 : cin_chunks;
-    if (cin_chunks % nch || nch % 2) return cudaErrorInvalidValue;
+    const int esz = dtype_size(dt);
+    const int in_cpc = a.in_cpc ? a.in_cpc : 16 / esz;
+    const int cbi = in_cpc * esz == 128 ? 128 : 16;
+    if (in_cpc * esz != cbi || a.cin_pad % in_cpc) return cudaErrorInvalidValue;
+    const int cin_chunks = a.cin_pad / in_cpc;
+    const int ns = pick_ns(a.cin_pad * esz, a.cout_pad, a.k);
+    const int nch = cbi == 128 ? 1 : (cin_chunks >= 8 ? 8 : cin_chunks);
+    if (cin_chunks % nch || (cbi == 16 && nch % 2)) return cudaErrorInvalidValue;
     const int epi = a.ps > 0 ? (a.ps_out ? 1 : 2) : 0;
     const int odt = epi == 1 ? dt : a.out_dt;
+    const int out_cpc = epi == 1 ? 16 / esz : (a.out_cpc ? a.out_cpc : 16 / dtype_size(odt));
+    const int cbo = out_cpc * dtype_size(odt);
+    if (cbo != 16 && cbo != 128) return cudaErrorInvalidValue;
     const Variant *v = nullptr;
     for (const Variant &c : kVariants)
-        if (c.in_dt == dt && c.out_dt == odt && c.ns == ns && c.ks == a.k && c.nch == nch && c.epi == epi) v = &c;
+        if (c.in_dt == dt && c.out_dt == odt && c.ns == ns && c.ks == a.k && c.nch == nch && c.epi == epi &&
+            c.cbi == cbi && c.cbo == cbo)
+            v = &c;
     if (!v) return cudaErrorNotSupported;
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    // activation as a byte tensor: (16 B chunk, W, H, chunks of all images)
+    // activation as a byte tensor: (chunk bytes, W, H, chunks of all images)
     CUtensorMap map;
     const int pxs = TM + a.k - 1;
-    cuuint64_t dims[4] = {16, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.nimg * cin_chunks};
-    cuuint64_t strides[3] = {16, (cuuint64_t)a.W * 16, (cuuint64_t)a.W * a.H * 16};
-    cuuint32_t box[4] = {16, (cuuint32_t)pxs, (cuuint32_t)a.k, (cuuint32_t)nch};
+    cuuint64_t dims[4] = {(cuuint64_t)cbi, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.nimg * cin_chunks};
+    cuuint64_t strides[3] = {(cuuint64_t)cbi, (cuuint64_t)a.W * cbi, (cuuint64_t)a.W * a.H * cbi};
+    cuuint32_t box[4] = {(cuuint32_t)cbi, (cuuint32_t)pxs, (cuuint32_t)a.k, (cuuint32_t)(cbi == 128 ? 1 : nch)};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.x), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     cbi == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     TcParams p{};
     p.H = a.H; p.W = a.W; p.nimg = a.nimg; p.cin_chunks = cin_chunks;
     p.cout = a.cout; p.cout_pad = a.cout_pad; p.ns = ns; p.nslice = a.cout_pad / ns;
     p.wts = static_cast<const uint8_t *>(a.w);
-    p.wbytes = (uint32_t)(a.k * a.k * cin_chunks * ns * 16);
+    p.wbytes = (uint32_t)(a.k * a.k * a.cin_pad * esz * ns);
     p.bias = a.bias; p.act = a.act;
     p.res = static_cast<const uint8_t *>(a.res);
     p.y = static_cast<uint8_t *>(a.y);

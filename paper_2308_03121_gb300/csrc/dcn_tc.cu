@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int H = a.H, W = a.W;
+    // blocked layouts [C/cpc][H][W][cpc]: byte address of the 8-channel unit starting at channel c
+    const int xcpc = a.x_cpc, ycpc = a.y_cpc;
     const int64_t HW = (int64_t)H * W;
     const int tiles_x = (W + TM - 1) / TM;
     const int ntiles = tiles_x * H;
@@ -134,7 +136,8 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                         float acc[CPC];
 #pragma unroll
                         for (int e = 0; e < CPC; ++e) acc[e] = 0.f;
-                        const uint8_t *plane = x + (int64_t)cc * HW * 16;
+                        const int c0 = cc * CPC;
+                        const uint8_t *plane = x + (int64_t)(c0 / xcpc) * HW * xcpc * 2 + (c0 % xcpc) * 2;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int yy = y0 + (q >> 1), xq = x0 + (q & 1);
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                             const float wgt = ((q >> 1) ? ly : 1.f - ly) * ((q & 1) ? lx : 1.f - lx);
                             alignas(16) T v[CPC];
                             *reinterpret_cast<uint4 *>(v) =
-                                __ldg(reinterpret_cast<const uint4 *>(plane + ((int64_t)yy * W + xq) * 16));
+                                __ldg(reinterpret_cast<const uint4 *>(plane + ((int64_t)yy * W + xq) * xcpc * 2));
 #pragma unroll
                             for (int e = 0; e < CPC; ++e) acc[e] += wgt * Cv<T>::in(v[e]);
                         }
@@ -245,7 +248,8 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                         const int n = j * 16 + h * 8 + e;
                         o[e] = Cv<T>::out(v[h * 8 + e] * a.acc_scale + a.bias[n]);
                     }
-                    *reinterpret_cast<uint4 *>(yb + ((int64_t)(j * 2 + h) * HW + pix) * 16) =
+                    const int n = j * 16 + h * 8;
+                    *reinterpret_cast<uint4 *>(yb + ((int64_t)(n / ycpc) * HW + pix) * ycpc * 2 + (n % ycpc) * 2) =
                         *reinterpret_cast<const uint4 *>(o);
                 }
             }
@@ -283,8 +287,12 @@ cudaError_t run(const DcnArgs &a, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_dcn_tc(const DcnArgs &a, cudaStream_t st) {
+cudaError_t launch_dcn_tc(const DcnArgs &a0, cudaStream_t st) {
+    DcnArgs a = a0;
+    if (a.x_cpc == 0) a.x_cpc = 8;
+    if (a.y_cpc == 0) a.y_cpc = 8;
     if (a.cin_pad != 64 || a.cout_pad != 64 || (a.cin_pad / a.groups) % 8) return cudaErrorNotSupported;
+    if ((a.x_cpc != 8 && a.x_cpc != 64) || (a.y_cpc != 8 && a.y_cpc != 64)) return cudaErrorNotSupported;
     if (a.in_dt == DT_BF16 && a.out_dt == DT_BF16) return run<__nv_bfloat16, 64, 64>(a, st);
     if (a.in_dt == DT_F16 && a.out_dt == DT_F16) return run<__half, 64, 64>(a, st);
     return cudaErrorNotSupported;

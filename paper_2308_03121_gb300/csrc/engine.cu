@@ -106,6 +106,7 @@ struct Tensor {
     int amax_slot = -1;  // calibration slot of the FP8 values
     int parent = -1;     // channel view of a concatenation buffer (tensor id)
     int choff = 0;       // first channel inside the parent
+    int cpc = 0;         // channels per chunk of the blocked layout (layout_cpc)
 };
 
 struct Weights {
@@ -195,7 +196,8 @@ struct nvisr_filter {
     std::vector<Tensor> tensors;
     std::vector<Step> steps;
     int pack_t = -1;               // tensor id of the packed tuple
-    float *out_rgb[2] = {nullptr, nullptr};  // planar float32 outputs [3][sH][opitch]
+    float *out_rgb[2] = {nullptr, nullptr};  // planar float32 residuals [3][sH][opitch]
+    SkipArgs skip[2] = {};                   // skip path of each output slot (added by requantise)
     int64_t opitch = 0;
     void *ostage[3] = {nullptr, nullptr, nullptr};
     int64_t ostage_pitch[3] = {0, 0, 0};
@@ -377,7 +379,10 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
         s = upload(f, host.data(), host.size() * 4, &W.simt_or_tc);
     } else {
         std::vector<uint8_t> host(tc_weight_bytes(W.cin_pad, W.cout_pad, L.k, f->act_dt));
-        prepare_weights_tc(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, f->act_dt, 1.0f, host.data());
+        // the conv kernel reads 64-channel inputs through 128-byte-swizzled operands;
+        // the DCN kernel builds its own no-swizzle sampled tile
+        const bool sw128 = L.op == "conv" && layout_cpc(f->act_dt, W.cin_pad) == 64;
+        prepare_weights_tc(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, f->act_dt, 1.0f, host.data(), sw128);
         s = upload(f, host.data(), host.size(), &W.simt_or_tc);
     }
     if (s != NVISR_OK) return s;
@@ -387,7 +392,7 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
         W.w_amax = amax > 0.f ? amax : 1.f;
         const float sw = W.w_amax / 448.f;
         std::vector<uint8_t> host(tc_weight_bytes(L.cin, W.cout_pad, L.k, DT_E4M3));
-        prepare_weights_tc(w, L.cout, L.cin, L.k, L.cin, W.cout_pad, DT_E4M3, 1.0f / sw, host.data());
+        prepare_weights_tc(w, L.cout, L.cin, L.k, L.cin, W.cout_pad, DT_E4M3, 1.0f / sw, host.data(), false);
         s = upload(f, host.data(), host.size(), &W.f8);
         if (s != NVISR_OK) return s;
     }
@@ -554,6 +559,7 @@ nvisr_status build_plan(nvisr_filter *f) {
                 nvisr_status s = dalloc(f->eng, (size_t)t.cpad * t.H * t.W * dtype_size(t.dt), f->owned, &t.ptr);
                 if (s != NVISR_OK) return s;
             }
+    for (Tensor &T : f->tensors) T.cpc = layout_cpc(T.dt, T.cpad);
     return NVISR_OK;
 }
 
@@ -752,10 +758,12 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
                 for (Buf &b : pool)
                     if (b.p == f->tensors[t].ptr) b.free_after = step;
     }
+    for (Tensor &T : f->tensors) T.cpc = layout_cpc(T.dt, T.cpad);
     for (Tensor &T : f->tensors)
         if (T.parent >= 0) {
             const Tensor &P = f->tensors[T.parent];
-            T.ptr = (uint8_t *)P.ptr + (size_t)(T.choff / chunk_channels(P.dt)) * P.H * P.W * 16;
+            if (T.cpc != P.cpc || T.choff % P.cpc) return fail(NVISR_INTERNAL, "view layout mismatch");
+            T.ptr = (uint8_t *)P.ptr + (size_t)(T.choff / P.cpc) * P.H * P.W * P.cpc * dtype_size(P.dt);
         }
     return NVISR_OK;
 }
@@ -771,6 +779,7 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
         const Tensor &o = f->tensors[s.out_t];
         DcnArgs d{};
         d.x = in.ptr; d.cin_pad = in.cpad; d.H = in.H; d.W = in.W; d.groups = L.groups;
+        d.x_cpc = in.cpc; d.y_cpc = o.cpc;
         d.om = (const float *)om.ptr; d.om_cpad = om.cpad; d.mask_logits = 1;
         d.w = Wt.simt_or_tc; d.bias = Wt.bias; d.cout = L.cout; d.cout_pad = Wt.cout_pad;
         d.y = o.ptr; d.in_dt = in.dt; d.out_dt = o.dt; d.acc_scale = 1.f; d.out_scale = 1.f;
@@ -782,6 +791,7 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
     }
     ConvArgs a{};
     a.cin_pad = in.cpad;
+    a.in_cpc = in.cpc;
     a.H = in.H;
     a.W = in.W;
     a.nimg = 1;
@@ -801,6 +811,7 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
         a.x = in.f8;
         a.in_dt = DT_E4M3;
         a.cin_pad = in.cpad;  // 64
+        a.in_cpc = 16;        // FP8 copies use 16-channel (16-byte) chunks
         a.w = Wt.f8;
         a.acc_scale = f->act_scale[in.amax_slot] * (Wt.w_amax / 448.f);
     } else {
@@ -812,12 +823,14 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
         const Tensor &o = f->tensors[s.out_t];
         a.y = o.ptr;
         a.out_dt = o.dt;
+        a.out_cpc = o.cpc;
         a.ps = L.ps;
         if (!calib && f->calibrated && o.amax_slot >= 0) {
             const float inv = 1.f / f->act_scale[o.amax_slot];
             if (s.out_f8_only && use_f8) {
                 a.y = o.f8;
                 a.out_dt = DT_E4M3;
+                a.out_cpc = 16;
                 a.out_scale = inv;
             } else {
                 a.y2 = o.f8;
@@ -826,17 +839,23 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
         }
         if (calib && o.amax_slot >= 0) a.amax = f->amax + o.amax_slot;
     } else {
+        // the network's last layer: PixelShuffle(2) residual into planar float32; the
+        // skip (upsampled input frames) is added by the requantise kernel
         a.ps = 2;
         a.ps_out = f->out_rgb[s.out_index];
         a.ps_pitch = f->opitch;
-        a.skip_mode = f->net.skip;
-        a.skip_scale = f->net.scale;
-        a.skip_h = f->in_fmt.height;
-        a.skip_w = f->in_fmt.width;
-        a.skip_pitch = f->rpitch;
-        a.skip_plane = f->rpitch * f->in_fmt.height;
-        a.nskip = (int)s.skip_frames.size();
-        for (int k = 0; k < a.nskip && k < 2; ++k) a.skip_src[k] = frames[s.skip_frames[k]];
+        a.skip_mode = 0;
+        a.nskip = 0;
+        SkipArgs &k = f->skip[s.out_index];
+        k = SkipArgs{};
+        k.n = f->net.skip ? std::min<int>((int)s.skip_frames.size(), 2) : 0;
+        for (int i = 0; i < k.n; ++i) k.src[i] = frames[s.skip_frames[i]];
+        k.pitch = f->rpitch;
+        k.plane = f->rpitch * f->in_fmt.height;
+        k.h = f->in_fmt.height;
+        k.w = f->in_fmt.width;
+        k.scale = f->net.scale;
+        k.mode = f->net.skip;
     }
     const int kind = s.out_t < 0 ? NVISR_K_CONV_TAIL
                      : (s.src == SRC_TUPLE ? NVISR_K_CONV_HEAD
@@ -862,6 +881,7 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
     pa.dst = pk.ptr;
     pa.cpad = pk.cpad;
     pa.dt = pk.dt;
+    pa.cpc = pk.cpc;
     pa.scale = 1.f;
     cudaError_t e;
     {
@@ -894,6 +914,7 @@ nvisr_status forward_group(nvisr_filter *f, const std::vector<int64_t> &idx) {
             pa.dst = t.ptr;
             pa.cpad = t.cpad;
             pa.dt = t.dt;
+            pa.cpc = t.cpc;
             pa.scale = 1.f;
             cudaError_t e;
             {
@@ -965,7 +986,8 @@ nvisr_status write_output(nvisr_filter *f, nvisr_planes *out, int slot) {
     cudaError_t e;
     {
         ProfScope ps(f, NVISR_K_REQUANT);
-        e = launch_requant(of, f->out_rgb[slot], f->opitch, dst[0], pitch[0], dst[1], pitch[1], dst[2], pitch[2], st);
+        e = launch_requant(of, f->out_rgb[slot], f->opitch, dst[0], pitch[0], dst[1], pitch[1], dst[2], pitch[2], st,
+                           &f->skip[slot]);
     }
     if (e != cudaSuccess) return cuda_status(e, "requant");
     if (out->on_device) return NVISR_OK;
@@ -1391,7 +1413,7 @@ nvisr_status fp8_scale(const float *x, int C, int H, int W, Scratch &sc, cudaStr
 }
 
 nvisr_status pack_planar(const float *x, int C, int cpad, int H, int W, int dt, float scale, void *dst,
-                         cudaStream_t st) {
+                         cudaStream_t st, int cpc = 0) {
     PackArgs pa{};
     pa.src[0] = x;
     pa.nsrc = 1;
@@ -1403,6 +1425,7 @@ nvisr_status pack_planar(const float *x, int C, int cpad, int H, int W, int dt, 
     pa.dst = dst;
     pa.cpad = cpad;
     pa.dt = dt;
+    pa.cpc = cpc;
     pa.scale = scale;
     NVISR_TRY_CUDA(launch_pack(pa, st));
     return NVISR_OK;
@@ -1446,7 +1469,8 @@ nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_
     if (tc) {
         wbytes = tc_weight_bytes(cin_pad, cout_pad, k, idt);
         hwl.resize(wbytes);
-        prepare_weights_tc(hw.data(), cout, cin, k, cin_pad, cout_pad, idt, 1.f / sw, hwl.data());
+        prepare_weights_tc(hw.data(), cout, cin, k, cin_pad, cout_pad, idt, 1.f / sw, hwl.data(),
+                           layout_cpc(idt, cin_pad) == 64);
     } else {
         wbytes = simt_weight_bytes(cin_pad, cout_pad, k);
         hwl.resize(wbytes);
@@ -1458,11 +1482,12 @@ nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_
     NVISR_TRY_CUDA(cudaMemcpyAsync(db, hb.data(), cout_pad * 4, cudaMemcpyHostToDevice, st));
     NVISR_TRY_CUDA(sc.alloc((size_t)cin_pad * h * w * dtype_size(idt), &dx));
     NVISR_TRY_CUDA(sc.alloc((size_t)cout_pad * h * w * dtype_size(adt), &dy));
-    nvisr_status s = pack_planar(x, cin, cin_pad, h, w, idt, 1.f / sx, dx, st);
+    const int in_cpc = layout_cpc(idt, cin_pad), out_cpc = layout_cpc(adt, cout_pad);
+    nvisr_status s = pack_planar(x, cin, cin_pad, h, w, idt, 1.f / sx, dx, st, in_cpc);
     if (s != NVISR_OK) return s;
     if (res) {
         NVISR_TRY_CUDA(sc.alloc((size_t)cout_pad * h * w * dtype_size(adt), &dr));
-        if ((s = pack_planar(res, cout, cout_pad, h, w, adt, 1.f, dr, st)) != NVISR_OK) return s;
+        if ((s = pack_planar(res, cout, cout_pad, h, w, adt, 1.f, dr, st, out_cpc)) != NVISR_OK) return s;
     }
     int *err;
     NVISR_TRY_CUDA(sc.alloc(sizeof(int), (void **)&err));
@@ -1471,9 +1496,10 @@ nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_
     a.x = dx; a.cin_pad = cin_pad; a.H = h; a.W = w; a.nimg = 1; a.w = dw; a.bias = (const float *)db;
     a.cout = cout; a.cout_pad = cout_pad; a.k = k; a.act = act; a.res = dr; a.y = dy;
     a.in_dt = idt; a.out_dt = adt; a.acc_scale = sx * sw; a.out_scale = 1.f; a.y2_scale = 1.f; a.err = err;
+    a.in_cpc = in_cpc; a.out_cpc = out_cpc;
     cudaError_t e = tc ? launch_conv_tc(a, st) : launch_conv_simt(a, st);
     if (e != cudaSuccess) return cuda_status(e, "conv2d");
-    NVISR_TRY_CUDA(launch_unpack(dy, adt, cout_pad, cout, h, w, 1.f, y, w, st));
+    NVISR_TRY_CUDA(launch_unpack(dy, adt, cout_pad, out_cpc, cout, h, w, 1.f, y, w, st));
     int herr = 0;
     NVISR_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     NVISR_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1505,7 +1531,7 @@ nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t
     std::vector<uint8_t> hwl;
     if (tc) {
         hwl.resize(tc_weight_bytes(cin_pad, cout_pad, 3, adt));
-        prepare_weights_tc(hw.data(), cout, cin, 3, cin_pad, cout_pad, adt, 1.f, hwl.data());
+        prepare_weights_tc(hw.data(), cout, cin, 3, cin_pad, cout_pad, adt, 1.f, hwl.data(), false);
     } else {
         hwl.resize(simt_weight_bytes(cin_pad, cout_pad, 3));
         prepare_weights_simt(hw.data(), cout, cin, 3, cin_pad, cout_pad, (float *)hwl.data());
@@ -1545,7 +1571,8 @@ nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t
         pa.ch_per_src = om_c;
         NVISR_TRY_CUDA(launch_pack(pa, st));
     }
-    nvisr_status s = pack_planar(x, cin, cin_pad, h, w, adt, 1.f, dx, st);
+    const int x_cpc = layout_cpc(adt, cin_pad), y_cpc = layout_cpc(adt, cout_pad);
+    nvisr_status s = pack_planar(x, cin, cin_pad, h, w, adt, 1.f, dx, st, x_cpc);
     if (s != NVISR_OK) return s;
     int *err;
     NVISR_TRY_CUDA(sc.alloc(sizeof(int), (void **)&err));
@@ -1555,9 +1582,10 @@ nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t
     d.om = (const float *)dom; d.om_cpad = om_cpad; d.mask_logits = 0;
     d.w = dw; d.bias = (const float *)db; d.cout = cout; d.cout_pad = cout_pad; d.y = dy;
     d.in_dt = adt; d.out_dt = adt; d.acc_scale = 1.f; d.out_scale = 1.f; d.err = err;
+    d.x_cpc = x_cpc; d.y_cpc = y_cpc;
     cudaError_t e = tc ? launch_dcn_tc(d, st) : launch_dcn_simt(d, st);
     if (e != cudaSuccess) return cuda_status(e, "dcn2d");
-    NVISR_TRY_CUDA(launch_unpack(dy, adt, cout_pad, cout, h, w, 1.f, y, w, st));
+    NVISR_TRY_CUDA(launch_unpack(dy, adt, cout_pad, y_cpc, cout, h, w, 1.f, y, w, st));
     int herr = 0;
     NVISR_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     NVISR_TRY_CUDA(cudaStreamSynchronize(st));

@@ -146,6 +146,39 @@ __device__ __forceinline__ void st_sample(uint8_t *base, int64_t pitch, int y, i
     reinterpret_cast<S *>(base + (int64_t)y * pitch)[x] = (S)(int)v;
 }
 
+// Skip value (mean of the skip frames, upsampled) at output (c, Y, X).
+__device__ __forceinline__ float skip_at(const SkipArgs &k, int c, int Y, int X) {
+    float acc = 0.f;
+    for (int f = 0; f < k.n; ++f) {
+        const float *p = k.src[f] + (int64_t)c * k.plane;
+        float v;
+        if (k.mode == 1) {
+            v = p[(int64_t)(Y / k.scale) * k.pitch + X / k.scale];
+        } else {
+            const float inv = 1.0f / (float)k.scale;
+            const float sy = fmaxf(((float)Y + 0.5f) * inv - 0.5f, 0.f);
+            const float sx = fmaxf(((float)X + 0.5f) * inv - 0.5f, 0.f);
+            const int y0 = min((int)sy, k.h - 1), x0 = min((int)sx, k.w - 1);
+            const int y1 = min(y0 + 1, k.h - 1), x1 = min(x0 + 1, k.w - 1);
+            const float ly = sy - (float)y0, lx = sx - (float)x0;
+            const float *r0 = p + (int64_t)y0 * k.pitch;
+            const float *r1 = p + (int64_t)y1 * k.pitch;
+            const float top = r0[x0] * (1.f - lx) + r0[x1] * lx;
+            const float bot = r1[x0] * (1.f - lx) + r1[x1] * lx;
+            v = top * (1.f - ly) + bot * ly;
+        }
+        acc += v;
+    }
+    return k.n == 2 ? acc * 0.5f : acc;
+}
+
+// Network output sample (residual + skip) of channel c at (Y, X).
+__device__ __forceinline__ float out_at(const float *in, int64_t pitch, int64_t plane, const SkipArgs &k, int c,
+                                        int Y, int X) {
+    const float v = in[(int64_t)c * plane + (int64_t)Y * pitch + X];
+    return k.n ? v + skip_at(k, c, Y, X) : v;
+}
+
 __device__ __forceinline__ void rgb2ycc(float r, float g, float b, float &y, float &cb, float &cr) {
     y = KR * r + KG * g + KB * b;
     cb = (b - y) / (2.0f * (1.0f - KB));
@@ -157,15 +190,15 @@ template <typename S>
 __global__ void __launch_bounds__(256) requant444_kernel(const float *__restrict__ in, int64_t pitch,
                                                          int H, int W, RangeConst rc, uint8_t *yp,
                                                          int64_t py, uint8_t *up, int64_t pu,
-                                                         uint8_t *vp, int64_t pv) {
+                                                         uint8_t *vp, int64_t pv, SkipArgs sk) {
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const int y = blockIdx.y;
     if (x0 >= W) return;
     const int64_t plane = pitch * H;
-    const float *row = in + (int64_t)y * pitch;
     for (int e = 0; e < 4 && x0 + e < W; ++e) {
         float Y, cb, cr;
-        rgb2ycc(row[x0 + e], row[plane + x0 + e], row[2 * plane + x0 + e], Y, cb, cr);
+        rgb2ycc(out_at(in, pitch, plane, sk, 0, y, x0 + e), out_at(in, pitch, plane, sk, 1, y, x0 + e),
+                out_at(in, pitch, plane, sk, 2, y, x0 + e), Y, cb, cr);
         st_sample<S>(yp, py, y, x0 + e, quant(Y * rc.y_mul + rc.y_add, rc.vmax));
         st_sample<S>(up, pu, y, x0 + e, quant(cb * rc.c_mul + rc.c_add, rc.vmax));
         st_sample<S>(vp, pv, y, x0 + e, quant(cr * rc.c_mul + rc.c_add, rc.vmax));
@@ -174,17 +207,46 @@ __global__ void __launch_bounds__(256) requant444_kernel(const float *__restrict
 
 // 4:2:0: one thread per (chroma row j, 4 chroma columns): luma rows 2j, 2j+1,
 // columns 8q .. 8q+7; chroma needs columns 8q-1 .. 8q+7 for LEFT siting.
-template <typename S>
+// SKIP2: the skip is one frame upsampled 2x bilinearly (align_corners = false,
+// edge clamp).  Output rows 2j, 2j+1 and columns 8q-1 .. 8q+7 then read
+// low-resolution rows j-1 .. j+1 and columns 4q-1 .. 4q+4 (clamped), loaded
+// once into registers; every output sample blends two rows and two columns
+// with the fixed weights 1/4, 3/4 in the same order as the general formula.
+template <typename S, bool SKIP2>
 __global__ void __launch_bounds__(256) requant420_kernel(const float *__restrict__ in, int64_t pitch,
                                                          int H, int W, int loc, RangeConst rc,
                                                          uint8_t *yp, int64_t py, uint8_t *up,
-                                                         int64_t pu, uint8_t *vp, int64_t pv) {
+                                                         int64_t pu, uint8_t *vp, int64_t pv, SkipArgs sk) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     const int xb = q * 8;
     if (xb >= W) return;
     const int64_t plane = pitch * H;
     const int Wc = W / 2;
+    float lr[SKIP2 ? 3 : 1][3][6];
+    if (SKIP2) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr) {
+                const float *row = sk.src[0] + (int64_t)c * sk.plane + (int64_t)clampi(j - 1 + rr, 0, sk.h - 1) * sk.pitch;
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) lr[c][rr][cc] = __ldg(row + clampi(4 * q - 1 + cc, 0, sk.w - 1));
+            }
+    }
+    // output (row 2j + a, column xb - 1 + c9) of channel ch: residual + skip
+    auto sample = [&](int ch, int a, int c9, int x) -> float {
+        const float v = in[(int64_t)ch * plane + (int64_t)(2 * j + a) * pitch + x];
+        if (!SKIP2) return sk.n ? v + skip_at(sk, ch, 2 * j + a, x) : v;
+        // horizontal: even c9 -> odd column 2i+1 (3/4 col i, 1/4 col i+1), odd c9 -> even 2i (1/4 col i-1, 3/4 col i)
+        const int c0 = (c9 & 1) ? (c9 - 1) / 2 : c9 / 2;
+        const float wl = (c9 & 1) ? 0.25f : 0.75f, wr = (c9 & 1) ? 0.75f : 0.25f;
+        const int r0 = a;  // a = 0: rows (j-1, j) with (1/4, 3/4); a = 1: rows (j, j+1) with (3/4, 1/4)
+        const float wt = a ? 0.75f : 0.25f, wb = a ? 0.25f : 0.75f;
+        const float top = lr[ch][r0][c0] * wl + lr[ch][r0][c0 + 1] * wr;
+        const float bot = lr[ch][r0 + 1][c0] * wl + lr[ch][r0 + 1][c0 + 1] * wr;
+        return v + (top * wt + bot * wb);
+    };
     // columns xb-1 .. xb+7 (9 columns), clamped; two rows.
     float cbv[9], crv[9];  // row-pair mean of full-resolution chroma
 #pragma unroll
@@ -194,9 +256,8 @@ __global__ void __launch_bounds__(256) requant420_kernel(const float *__restrict
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr) {
             const int y = 2 * j + rr;
-            const float *row = in + (int64_t)y * pitch;
             float Y, cb, cr;
-            rgb2ycc(row[x], row[plane + x], row[2 * plane + x], Y, cb, cr);
+            rgb2ycc(sample(0, rr, c, x), sample(1, rr, c, x), sample(2, rr, c, x), Y, cb, cr);
             cb2[rr] = cb;
             cr2[rr] = cr;
             if (c >= 1 && c <= 8 && xb - 1 + c < W)
@@ -241,30 +302,33 @@ __device__ __forceinline__ float cvt_in<__nv_bfloat16>(__nv_bfloat16 v) { return
 template <>
 __device__ __forceinline__ float cvt_in<__half>(__half v) { return __half2float(v); }
 
-// One thread per (pixel, 16-byte chunk).
+// One thread per 16-byte unit of the destination, in memory order: unit idx
+// is (chunk c, pixel p, unit v of the chunk) with idx = (c*HW + p)*upch + v.
 template <typename T>
 __global__ void __launch_bounds__(256) pack_kernel(PackArgs a) {
-    constexpr int CPC = 16 / sizeof(T);
+    constexpr int UPC = 16 / sizeof(T);  // channels per unit
     const int64_t HW = (int64_t)a.H * a.W;
-    const int nchunks = a.cpad / CPC;
+    const int upch = a.cpc / UPC;         // units per chunk
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= HW * nchunks) return;
-    const int cc = (int)(idx / HW);
-    const int64_t p = idx - (int64_t)cc * HW;
+    if (idx >= HW * (a.cpad / UPC)) return;
+    const int64_t cp = idx / upch;
+    const int v = (int)(idx - cp * upch);
+    const int c = (int)(cp / HW);
+    const int64_t p = cp - (int64_t)c * HW;
     const int y = (int)(p / a.W), x = (int)(p - (int64_t)y * a.W);
     const int creal = a.nsrc * a.ch_per_src;
-    alignas(16) T vals[CPC];
+    alignas(16) T vals[UPC];
     float amax = 0.f;
 #pragma unroll
-    for (int e = 0; e < CPC; ++e) {
-        const int ch = cc * CPC + e;
-        float v = 0.f;
+    for (int e = 0; e < UPC; ++e) {
+        const int ch = c * a.cpc + v * UPC + e;
+        float val = 0.f;
         if (ch < creal) {
-            const int s = ch / a.ch_per_src, c = ch - s * a.ch_per_src;
-            v = a.src[s][c * a.src_plane + (int64_t)y * a.src_pitch + x];
+            const int s = ch / a.ch_per_src, cc = ch - s * a.ch_per_src;
+            val = a.src[s][cc * a.src_plane + (int64_t)y * a.src_pitch + x];
         }
-        amax = fmaxf(amax, fabsf(v));
-        vals[e] = cvt_out<T>(v * a.scale);
+        amax = fmaxf(amax, fabsf(val));
+        vals[e] = cvt_out<T>(val * a.scale);
     }
     *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(a.dst) + idx * 16) =
         *reinterpret_cast<const uint4 *>(vals);
@@ -272,21 +336,23 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__ src, int cpad, int C,
-                                                     int H, int W, float scale, float *dst,
-                                                     int64_t pitch) {
-    constexpr int CPC = 16 / sizeof(T);
+__global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__ src, int cpad, int cpc, int C,
+                                                     int H, int W, float scale, float *dst, int64_t pitch) {
+    constexpr int UPC = 16 / sizeof(T);
     const int64_t HW = (int64_t)H * W;
+    const int upch = cpc / UPC;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= HW * (cpad / CPC)) return;
-    const int cc = (int)(idx / HW);
-    const int64_t p = idx - (int64_t)cc * HW;
+    if (idx >= HW * (cpad / UPC)) return;
+    const int64_t cp = idx / upch;
+    const int v = (int)(idx - cp * upch);
+    const int c = (int)(cp / HW);
+    const int64_t p = cp - (int64_t)c * HW;
     const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
-    alignas(16) T vals[CPC];
+    alignas(16) T vals[UPC];
     *reinterpret_cast<uint4 *>(vals) = *reinterpret_cast<const uint4 *>(src + idx * 16);
 #pragma unroll
-    for (int e = 0; e < CPC; ++e) {
-        const int ch = cc * CPC + e;
+    for (int e = 0; e < UPC; ++e) {
+        const int ch = c * cpc + v * UPC + e;
         if (ch < C) dst[(int64_t)ch * pitch * H + (int64_t)y * pitch + x] = cvt_in<T>(vals[e]) * scale;
     }
 }
@@ -311,36 +377,45 @@ cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, cons
 }
 
 cudaError_t launch_requant(const nvisr_format &f, const float *in, int64_t in_pitch, void *y, int64_t py,
-                           void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st) {
+                           void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st, const SkipArgs *skip) {
     const RangeConst rc = range_const(f.bit_depth, f.range);
+    SkipArgs sk{};
+    if (skip) sk = *skip;
     dim3 block(64);
     if (f.subsampling == NVISR_SUB_420) {
         dim3 grid((f.width / 8 + 1 + block.x - 1) / block.x, f.height / 2);
-        if (f.bit_depth <= 8)
-            requant420_kernel<uint8_t><<<grid, block, 0, st>>>(in, in_pitch, f.height, f.width, f.chroma_loc,
-                                                               rc, (uint8_t *)y, py, (uint8_t *)u, pu,
-                                                               (uint8_t *)v, pv);
-        else
-            requant420_kernel<uint16_t><<<grid, block, 0, st>>>(in, in_pitch, f.height, f.width, f.chroma_loc,
-                                                                rc, (uint8_t *)y, py, (uint8_t *)u, pu,
-                                                                (uint8_t *)v, pv);
+        const bool skip2 = sk.n == 1 && sk.mode == 2 && sk.scale == 2 && sk.h * 2 == f.height && sk.w * 2 == f.width;
+#define NVISR_RQ(S_, K_)                                                                                     \
+    requant420_kernel<S_, K_><<<grid, block, 0, st>>>(in, in_pitch, f.height, f.width, f.chroma_loc, rc,  \
+                                                      (uint8_t *)y, py, (uint8_t *)u, pu, (uint8_t *)v, pv, sk)
+        if (f.bit_depth <= 8) {
+            if (skip2) NVISR_RQ(uint8_t, true);
+            else NVISR_RQ(uint8_t, false);
+        } else {
+            if (skip2) NVISR_RQ(uint16_t, true);
+            else NVISR_RQ(uint16_t, false);
+        }
+#undef NVISR_RQ
     } else {
         dim3 grid((f.width / 4 + 1 + block.x - 1) / block.x, f.height);
         if (f.bit_depth <= 8)
             requant444_kernel<uint8_t><<<grid, block, 0, st>>>(in, in_pitch, f.height, f.width, rc,
                                                                (uint8_t *)y, py, (uint8_t *)u, pu,
-                                                               (uint8_t *)v, pv);
+                                                               (uint8_t *)v, pv, sk);
         else
             requant444_kernel<uint16_t><<<grid, block, 0, st>>>(in, in_pitch, f.height, f.width, rc,
                                                                 (uint8_t *)y, py, (uint8_t *)u, pu,
-                                                                (uint8_t *)v, pv);
+                                                                (uint8_t *)v, pv, sk);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const PackArgs &a, cudaStream_t st) {
-    const int cpc = chunk_channels(a.dt);
-    const int64_t n = (int64_t)a.H * a.W * (a.cpad / cpc);
+cudaError_t launch_pack(const PackArgs &a0, cudaStream_t st) {
+    PackArgs a = a0;
+    const int upc = chunk_channels(a.dt);
+    if (a.cpc == 0) a.cpc = upc;
+    if (a.cpc % upc || a.cpad % a.cpc) return cudaErrorInvalidValue;
+    const int64_t n = (int64_t)a.H * a.W * (a.cpad / upc);
     const int block = 256;
     const int64_t grid = (n + block - 1) / block;
     switch (a.dt) {
@@ -352,18 +427,20 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(const void *src, int dt, int cpad, int C, int H, int W, float scale, float *dst,
+cudaError_t launch_unpack(const void *src, int dt, int cpad, int cpc, int C, int H, int W, float scale, float *dst,
                           int64_t dst_pitch, cudaStream_t st) {
-    const int cpc = chunk_channels(dt);
-    const int64_t n = (int64_t)H * W * (cpad / cpc);
+    const int upc = chunk_channels(dt);
+    if (cpc == 0) cpc = upc;
+    if (cpc % upc || cpad % cpc) return cudaErrorInvalidValue;
+    const int64_t n = (int64_t)H * W * (cpad / upc);
     const int block = 256;
     const unsigned grid = (unsigned)((n + block - 1) / block);
     const uint8_t *s = (const uint8_t *)src;
     switch (dt) {
-        case DT_F32: unpack_kernel<float><<<grid, block, 0, st>>>(s, cpad, C, H, W, scale, dst, dst_pitch); break;
-        case DT_BF16: unpack_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(s, cpad, C, H, W, scale, dst, dst_pitch); break;
-        case DT_F16: unpack_kernel<__half><<<grid, block, 0, st>>>(s, cpad, C, H, W, scale, dst, dst_pitch); break;
-        default: unpack_kernel<__nv_fp8_e4m3><<<grid, block, 0, st>>>(s, cpad, C, H, W, scale, dst, dst_pitch); break;
+        case DT_F32: unpack_kernel<float><<<grid, block, 0, st>>>(s, cpad, cpc, C, H, W, scale, dst, dst_pitch); break;
+        case DT_BF16: unpack_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(s, cpad, cpc, C, H, W, scale, dst, dst_pitch); break;
+        case DT_F16: unpack_kernel<__half><<<grid, block, 0, st>>>(s, cpad, cpc, C, H, W, scale, dst, dst_pitch); break;
+        default: unpack_kernel<__nv_fp8_e4m3><<<grid, block, 0, st>>>(s, cpad, cpc, C, H, W, scale, dst, dst_pitch); break;
     }
     return cudaGetLastError();
 }

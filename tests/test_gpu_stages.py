@@ -27,8 +27,8 @@ def test_swizzle128_descriptor_probe():
     """Reports which base-offset convention reads rows from inside a 128-byte swizzle atom."""
     out = nv.nvisr_selftest_swizzle()
     print("sw128 probe: base offset 0 ->", out[:8].tolist(), " base offset (start>>7)&7 ->", out[8:].tolist())
-    assert out[0] == 0 and out[8] == 0          # atom-aligned start: both conventions agree
-    assert (out[:8] == 0).all() or (out[8:] == 0).all()
+    # the conv kernels start A operands at any 128-byte row inside an atom with base offset 0
+    assert (out[:8] == 0).all(), out
 
 
 INGEST_CASES = [
