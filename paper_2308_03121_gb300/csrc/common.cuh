@@ -98,6 +98,7 @@ struct ConvArgs {
     int H, W;
     int nimg;                // images stacked along the outer dimension
     const void *w;           // prepared weights (kernel-specific layout)
+    const void *w_rows;      // 64->64 3x3 only: weights for the row-streaming kernel, or null
     const float *bias;       // [cout_pad] float32 (zero past cout)
     int cout, cout_pad, k;
     int act;                 // 0 none, 1 LeakyReLU(0.1)
@@ -137,6 +138,9 @@ size_t tc_weight_bytes(int cin_pad, int cout_pad, int k, int dt);
 void prepare_weights_tc(const float *w_oihw, int cout, int cin, int k, int cin_pad, int cout_pad,
                         int dt, float scale, void *dst_host, bool sw128);
 int tc_nslice(int cin_pad, int cout_pad, int k, int dt);
+// Row-streaming 64 -> 64 3x3 layout: [kx][2 - ky][64 out][128 B swizzled 64 in].
+size_t tc_rows_weight_bytes();
+void prepare_weights_rows(const float *w_oihw, int dt, void *dst_host);
 
 // DCN: x blocked (activation dtype); offsets and mask in one blocked float32
 // tensor [om_cpad/4][H][W][4]: channels [0, 18G) = (dy, dx) per (group, tap),

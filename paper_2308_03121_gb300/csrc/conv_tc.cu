@@ -60,6 +60,7 @@ struct TcParams {
     const uint8_t *res;
     uint8_t *y;
     float acc_scale, out_scale;
+    float res_scale;                  // 1 / out_scale: residual values are stored pre-scaled
     uint8_t *y2;
     float y2_scale;
     unsigned *amax;
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
                             alignas(16) TO rv[UPC_O];
                             *reinterpret_cast<uint4 *>(rv) = rres[uu];
 #pragma unroll
-                            for (int e = 0; e < UPC_O; ++e) v[uu * UPC_O + e] += from_elem<TO>(rv[e]) / p.out_scale;
+                            for (int e = 0; e < UPC_O; ++e) v[uu * UPC_O + e] += from_elem<TO>(rv[e]) * p.res_scale;
                         }
                     }
                     if (p.amax) {
@@ -469,6 +470,368 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
             }
             tc_fence_before();
             mbar_arrive(&tempty[a]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, NCOLS);
+    }
+}
+
+// ---------------------------------------------------------------- row-streaming 3x3 conv
+
+// Row-streaming variant for 64 -> 64 channel 3x3 layers (the residual trunks).
+// A CTA owns a vertical strip of one 128-pixel column and walks its input rows
+// top to bottom.  Input row r feeds output rows r+1, r and r-1 through the
+// vertical taps ky = 0, 1, 2, so the three taps' weights are stacked along N:
+// one N = 192 MMA per (kx, 16-channel K step) reads the input row once and
+// accumulates into three consecutive output-row accumulators.  Accumulators
+// live in a TMEM ring of 8 output rows (64 columns each); output row o
+// receives its first product (accumulate = 0) from input row o-1 at kx = 0,
+// K step 0, is complete after input row o+1, and is then drained by the
+// epilogue, which frees its slot.  Per output row: 13 MMAs, one 130-pixel TMA
+// row load (plus 2 halo rows per strip) and a third of the operand traffic of
+// the per-tap form.
+struct RowPlan {
+    int xtiles;   // 128-pixel columns per row
+    int bands;    // row bands per column (strips = xtiles * bands * nimg)
+    int rps;      // rows per band
+};
+
+template <int IN_DT, int OUT_DT, int CBO>
+__global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                const __grid_constant__ CUtensorMap ymap,
+                                                                const __grid_constant__ CUtensorMap rmap,
+                                                                const TcParams p, const RowPlan rp) {
+    using TO = typename Elem<OUT_DT>::T;
+    constexpr int AFMT = IN_DT == DT_BF16 ? 1 : 0;
+    constexpr int PXS = TM + 2;
+    constexpr uint32_t ROWB = (PXS * 128 + 1023u) & ~1023u;  // one 130-pixel input row, 64 channels
+    constexpr uint32_t WKX = 3 * 64 * 128;                    // weights of one kx: [ky' = 2 - ky][64][128 B]
+    constexpr uint32_t TILEB = TM * 128;                      // one 128-pixel output / residual row tile
+    constexpr int NSLOT = 8;                                  // output-row accumulators in TMEM
+    constexpr uint32_t NCOLS = 512;
+    constexpr int UPC_O = 16 / sizeof(TO);
+    constexpr int NU = 64 / UPC_O;                            // 16-byte units of a pixel's 64 channels
+    constexpr int NGRP = 128;                                 // threads of one epilogue group
+    static_assert(CBO == 128 && sizeof(TO) == 2, "row kernel writes 64-channel 16-bit tiles");
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int S = p.stages;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + 8;
+    uint64_t *rowdone = empty + 8;
+    uint64_t *slotfree = rowdone + NSLOT;
+    uint64_t *resfull = slotfree + NSLOT;  // one per epilogue group
+    uint64_t *wbar = resfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    // per-group stop flags: written between a group's two per-row named
+    // barriers, read after the second, so a group's warps leave on the same row
+    volatile int *grp_stop = reinterpret_cast<volatile int *>(tmem_slot + 2);
+    float *sbias = reinterpret_cast<float *>(smem + 512);
+    uint8_t *wsm = smem + SMEM_HDR;
+    uint8_t *stage0 = wsm + 3 * WKX;
+    uint8_t *obuf = stage0 + (size_t)S * ROWB;   // output staging tile per group
+    uint8_t *rbuf = obuf + 2 * TILEB;            // residual tile per group
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int strips_per_img = rp.xtiles * rp.bands;
+    const int nstrips = strips_per_img * p.nimg;
+    const bool has_res = p.res != nullptr;
+    auto strip_of = [&](int sidx, int &img, int &x0, int &ra, int &rb) {
+        img = sidx / strips_per_img;
+        const int rem = sidx - img * strips_per_img;
+        const int band = rem / rp.xtiles;
+        x0 = (rem - band * rp.xtiles) * TM;
+        ra = band * rp.rps;
+        rb = min(p.H, ra + rp.rps);
+    };
+    if (threadIdx.x >= 64 && threadIdx.x < 128) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int k = 0; k < NSLOT; ++k) {
+            mbar_init(&rowdone[k], 1);
+            mbar_init(&slotfree[k], NGRP);
+        }
+        mbar_init(&resfull[0], 1);
+        mbar_init(&resfull[1], 1);
+        mbar_init(wbar, 1);
+        *abort = 0;
+        grp_stop[0] = 0;
+        grp_stop[1] = 0;
+        fence_mbarrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, NCOLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer: weights, then one input row per stage
+            mbar_arrive_expect_tx(wbar, 3 * WKX);
+            for (uint32_t off = 0; off < 3 * WKX; off += 32768u)
+                bulk_load(wsm + off, p.wts + off, min(32768u, 3 * WKX - off), wbar);
+            int gin = 0;
+            bool ok = true;
+            for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
+                int img, x0, ra, rb;
+                strip_of(sidx, img, x0, ra, rb);
+                for (int r = ra - 1; r <= rb; ++r, ++gin) {
+                    const int s = gin % S;
+                    if (!mbar_wait_bounded(&empty[s], ((gin / S) & 1) ^ 1, abort, WAIT_NS)) {
+                        raise_abort(abort, p.err);
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[s], PXS * 128);
+                    tma_load_4d(stage0 + (size_t)s * ROWB, &tmap, &full[s], 0, x0 - 1, r, img);
+                }
+            }
+            for (int k = 0; k < S && k < gin; ++k) {
+                const int idx = gin - 1 - k;
+                mbar_wait_bounded(&full[idx % S], (uint32_t)((idx / S) & 1), nullptr, WAIT_NS);
+            }
+            mbar_wait_bounded(wbar, 0, nullptr, WAIT_NS);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer.  Per input row the output rows it touches
+            // form at most two contiguous TMEM slot runs (the ring may wrap); the
+            // runs' descriptors are computed once per row, then the 12 (kx, K step)
+            // MMAs per run only add constant offsets.
+            bool ok = mbar_wait_bounded(wbar, 0, abort, WAIT_NS);
+            if (!ok) raise_abort(abort, p.err);
+            const uint64_t b_base = smem_desc_sw128(smem_u32(wsm), 0);
+            const uint32_t idn[4] = {0u, instr_desc(TM, 64, AFMT, AFMT), instr_desc(TM, 128, AFMT, AFMT),
+                                     instr_desc(TM, 192, AFMT, AFMT)};
+            int gin = 0, gout = 0, last_slot = -1;
+            uint32_t last_par = 0;
+            for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
+                int img, x0, ra, rb;
+                strip_of(sidx, img, x0, ra, rb);
+                for (int r = ra - 1; r <= rb && ok; ++r, ++gin) {
+                    const int s = gin % S;
+                    const int o_lo = max(r - 1, ra), o_hi = min(r + 1, rb - 1);
+                    const bool fresh = (r + 1 <= rb - 1) && (r + 1 >= ra);
+                    if (fresh) {
+                        const int i = gout + (r + 1 - ra);
+                        if (!mbar_wait_bounded(&slotfree[i % NSLOT], ((i / NSLOT) & 1) ^ 1, abort, WAIT_NS)) {
+                            raise_abort(abort, p.err);
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (!mbar_wait_bounded(&full[s], (uint32_t)((gin / S) & 1), abort, WAIT_NS)) {
+                        raise_abort(abort, p.err);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (o_lo <= o_hi) {
+                        const uint64_t a_base = smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0);
+                        // Runs of contiguous TMEM slots.  The first MMA of the row (kx = 0, K step 0)
+                        // must not accumulate into the fresh row r+1, so it uses set F = runs over
+                        // [o_lo, min(r, o_hi)] + the fresh row alone; every later MMA uses set M =
+                        // runs over [o_lo, o_hi] (one N = 192 MMA unless the ring wraps).
+                        uint32_t fd[3], fid[3], md[2], mid[2];
+                        uint64_t fbd[3], mbd[2];
+                        int nf = 0, nm = 0, nfold = 0;
+                        auto runs = [&](int a0, int a1, uint32_t *dd, uint32_t *ii, uint64_t *bb, int &n) {
+                            int o = a0;
+                            while (o <= a1) {
+                                const int slot = (gout + o - ra) % NSLOT;
+                                const int run = min(a1 - o + 1, NSLOT - slot);
+                                dd[n] = tmem_base + (uint32_t)(slot * 64);
+                                ii[n] = idn[run];
+                                bb[n] = b_base + (uint64_t)(((o - r + 1) * 64 * 128) >> 4);
+                                ++n;
+                                o += run;
+                            }
+                        };
+                        const int old_hi = fresh ? min(r, o_hi) : o_hi;
+                        if (o_lo <= old_hi) runs(o_lo, old_hi, fd, fid, fbd, nf);
+                        nfold = nf;
+                        if (fresh) runs(r + 1, r + 1, fd, fid, fbd, nf);
+                        runs(o_lo, o_hi, md, mid, mbd, nm);
+#pragma unroll 1
+                        for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const uint64_t ad = a_base + (uint64_t)((kx * 128 + j * 32) >> 4);
+                                const uint64_t boff = (uint64_t)((kx * WKX + j * 32) >> 4);
+                                if (kx == 0 && j == 0) {
+#pragma unroll
+                                    for (int k = 0; k < 3; ++k) {
+                                        if (k >= nf) break;
+                                        umma<0>(fd[k], ad, fbd[k] + boff, fid[k], k < nfold ? 1u : 0u);
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int k = 0; k < 2; ++k) {
+                                        if (k >= nm) break;
+                                        umma<0>(md[k], ad, mbd[k] + boff, mid[k], 1u);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                    if (r - 1 >= ra) {
+                        const int i = gout + (r - 1 - ra);
+                        umma_commit(&rowdone[i % NSLOT]);
+                        last_slot = i % NSLOT;
+                        last_par = (uint32_t)((i / NSLOT) & 1);
+                    }
+                }
+                gout += rb - ra;
+            }
+            if (last_slot >= 0) mbar_wait_bounded(&rowdone[last_slot], last_par, nullptr, WAIT_NS);
+        }
+    } else {
+        // ---------------- epilogue: two independent groups of 4 warps (warps 2-5
+        // and 6-9) take alternate output rows; warp w reads TMEM lane quadrant
+        // w % 4 (pixels) and all 64 columns.  A row is staged in shared memory
+        // (128-byte swizzled, as the TMA store reads it) and written by one TMA
+        // store; its residual arrives by TMA, issued two rows ahead.
+        const int q = warp & 3;
+        const int g = (warp - 2) >> 2;
+        const int m = q * 32 + lane;
+        const bool leader = warp == 2 + 4 * g && lane == 0;
+        const int bar_id = 1 + g;
+        const int64_t HW = (int64_t)p.H * p.W;
+        uint8_t *ot = obuf + g * TILEB + m * 128;
+        const uint8_t *rt = rbuf + g * TILEB + m * 128;
+        int gout = 0;
+        int res_loads = 0;  // leader: residual loads issued into this group's buffer
+        int last_res = -1;
+        bool ok = true;
+        for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
+            int img, x0, ra, rb;
+            strip_of(sidx, img, x0, ra, rb);
+            const int x = x0 + m;
+            const bool valid = x < p.W;
+            // this group's rows of the strip: global index i = gout + (o - ra) with i % 2 == g
+            int o = ra + ((g - (gout & 1)) & 1);
+            if (leader && has_res && o < rb) {
+                mbar_arrive_expect_tx(&resfull[g], TILEB);
+                tma_load_4d(rbuf + g * TILEB, &rmap, &resfull[g], 0, x0, o, img);
+                last_res = res_loads++;
+            }
+            for (; o < rb; o += 2) {
+                const int i = gout + (o - ra);
+                const int slot = i % NSLOT;
+                const int k = i >> 1;  // this group's row count (phase of its residual barrier)
+                if (leader) bulk_wait_group_read<0>();  // the group's previous store finished reading
+                named_barrier(bar_id, NGRP);
+                bool w = mbar_wait_bounded(&rowdone[slot], (uint32_t)((i / NSLOT) & 1), abort, WAIT_NS);
+                w = __all_sync(0xffffffffu, w);
+                float v[64];
+                if (w) {
+                    tc_fence_after();
+                    uint32_t rr[4][16];
+                    const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * 64);
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) tmem_ld16_nowait(taddr + (uint32_t)(jj * 16), rr[jj]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[jj * 16 + e] = __uint_as_float(rr[jj][e]);
+                    tc_fence_before();
+                    mbar_arrive(&slotfree[slot]);  // the accumulator is in registers now
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) v[e] = 0.f;
+                    if (lane == 0) {
+                        raise_abort(abort, p.err);
+                        grp_stop[g] = 1;
+                    }
+                }
+                const float as = p.acc_scale;
+#pragma unroll
+                for (int e = 0; e < 64; ++e) {
+                    float ov = v[e] * as + sbias[e];
+                    if (p.act == 1) ov = lrelu(ov);
+                    v[e] = ov;
+                }
+                if (has_res) {
+                    bool rw = mbar_wait_bounded(&resfull[g], (uint32_t)(k & 1), abort, WAIT_NS);
+                    rw = __all_sync(0xffffffffu, rw);
+                    if (!rw && lane == 0) {
+                        raise_abort(abort, p.err);
+                        grp_stop[g] = 1;
+                    }
+                    const float rs = p.res_scale;
+#pragma unroll
+                    for (int uu = 0; uu < NU; ++uu) {
+                        const int unit = uu ^ (m & 7);
+                        alignas(16) TO rv[UPC_O];
+                        *reinterpret_cast<uint4 *>(rv) = *reinterpret_cast<const uint4 *>(rt + unit * 16);
+#pragma unroll
+                        for (int e = 0; e < UPC_O; ++e) v[uu * UPC_O + e] += from_elem<TO>(rv[e]) * rs;
+                    }
+                }
+                if (valid && p.amax) {
+                    float amax = 0.f;
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) amax = fmaxf(amax, fabsf(v[e]));
+                    atomicMax(p.amax, __float_as_uint(amax));
+                }
+                if (valid && p.y2) {
+                    const int64_t pix = (int64_t)o * p.W + x;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        alignas(16) __nv_fp8_e4m3 o8[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) o8[e] = __nv_fp8_e4m3(v[c * 16 + e] * p.y2_scale);
+                        *reinterpret_cast<uint4 *>(p.y2 + (((int64_t)img * (p.cout_pad / 16) + c) * HW + pix) * 16) =
+                            *reinterpret_cast<const uint4 *>(o8);
+                    }
+                }
+                const float os = p.out_scale;
+#pragma unroll
+                for (int uu = 0; uu < NU; ++uu) {
+                    const int unit = uu ^ (m & 7);
+                    alignas(16) TO ov[UPC_O];
+#pragma unroll
+                    for (int e = 0; e < UPC_O; ++e) ov[e] = to_elem<TO>(v[uu * UPC_O + e] * os);
+                    *reinterpret_cast<uint4 *>(ot + unit * 16) = *reinterpret_cast<const uint4 *>(ov);
+                }
+                fence_proxy_async();  // staging writes (and residual reads) before the async proxy
+                if (leader && *abort) grp_stop[g] = 1;
+                named_barrier(bar_id, NGRP);
+                if (grp_stop[g]) {
+                    ok = false;
+                    break;
+                }
+                if (leader) {
+                    tma_store_4d(&ymap, obuf + g * TILEB, 0, x0, o, img);
+                    bulk_commit_group();
+                    if (has_res && o + 2 < rb) {  // this group's next row; the buffer's readers are done
+                        mbar_arrive_expect_tx(&resfull[g], TILEB);
+                        tma_load_4d(rbuf + g * TILEB, &rmap, &resfull[g], 0, x0, o + 2, img);
+                        last_res = res_loads++;
+                    }
+                }
+            }
+            gout += rb - ra;
+        }
+        if (leader) {
+            bulk_wait_group<0>();
+            // a residual load still in flight after an early exit lands before the CTA ends
+            if (last_res >= 0) mbar_wait_bounded(&resfull[g], (uint32_t)(last_res & 1), nullptr, WAIT_NS);
         }
     }
     __syncthreads();
@@ -753,8 +1116,98 @@ void prepare_weights_tc(const float *w, int cout, int cin, int k, int cin_pad, i
     }
 }
 
+size_t tc_rows_weight_bytes() { return (size_t)3 * 3 * 64 * 128; }
+
+void prepare_weights_rows(const float *w, int dt, void *dst) {
+    uint8_t *out = static_cast<uint8_t *>(dst);
+    memset(out, 0, tc_rows_weight_bytes());
+    for (int n = 0; n < 64; ++n)
+        for (int c = 0; c < 64; ++c)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx) {
+                    const float v = w[((size_t)n * 64 + c) * 9 + ky * 3 + kx];
+                    const size_t row = (size_t)(2 - ky) * 64 + n;
+                    const size_t off = (size_t)kx * 3 * 64 * 128 + row * 128 + (((c / 8) ^ (n & 7)) * 16) + (c % 8) * 2;
+                    if (dt == DT_BF16) {
+                        __nv_bfloat16 h = __float2bfloat16_rn(v);
+                        memcpy(out + off, &h, 2);
+                    } else {
+                        __half h = __float2half_rn(v);
+                        memcpy(out + off, &h, 2);
+                    }
+                }
+}
+
+namespace {
+
+template <int IN_DT, int OUT_DT, int CBO>
+cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUtensorMap &rmap, TcParams p,
+                     cudaStream_t st) {
+    constexpr uint32_t ROWB = ((TM + 2) * 128 + 1023u) & ~1023u;
+    constexpr uint32_t WB = 3 * 3 * 64 * 128;
+    constexpr uint32_t TILES = 4 * TM * 128;  // 2 output staging + 2 residual tiles
+    int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES) / (int)ROWB;
+    if (stages > 8) stages = 8;
+    if (stages < 2) return cudaErrorInvalidConfiguration;
+    p.stages = stages;
+    const int smem = 1024 + SMEM_HDR + (int)WB + stages * (int)ROWB + (int)TILES;
+    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    RowPlan rp;
+    rp.xtiles = (p.W + TM - 1) / TM;
+    const int sms = device_sm_count();
+    int bands = sms / (rp.xtiles * p.nimg);
+    if (bands < 1) bands = 1;
+    if (bands > p.H) bands = p.H;
+    rp.rps = (p.H + bands - 1) / bands;
+    rp.bands = (p.H + rp.rps - 1) / rp.rps;
+    int grid = rp.xtiles * rp.bands * p.nimg;
+    if (grid > sms) grid = sms;
+    kern<<<grid, NTHREADS, smem, st>>>(map, ymap, rmap, p, rp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
     const int dt = a.in_dt;
+    // 64 -> 64 3x3 layers with 64-channel 16-bit input and output: row-streaming kernel
+    if (a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.out_dt == dt && a.cin_pad == 64 &&
+        a.cout_pad == 64 && a.cout == 64 && a.in_cpc == 64 && a.out_cpc == 64 && a.ps == 0) {
+        auto enc = encode_fn();
+        if (!enc) return cudaErrorNotSupported;
+        CUtensorMap map, ymap, rmap;
+        cuuint64_t dims[4] = {128, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.nimg};
+        cuuint64_t strides[3] = {128, (cuuint64_t)a.W * 128, (cuuint64_t)a.W * a.H * 128};
+        cuuint32_t box[4] = {128, (cuuint32_t)(TM + 2), 1, 1};
+        cuuint32_t tbox[4] = {128, (cuuint32_t)TM, 1, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.x), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        r = enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, a.y, dims, strides, tbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        r = enc(&rmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.res ? a.res : a.y), dims, strides, tbox,
+                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        TcParams p{};
+        p.H = a.H; p.W = a.W; p.nimg = a.nimg; p.cin_chunks = 1;
+        p.cout = 64; p.cout_pad = 64; p.ns = 64; p.nslice = 1;
+        p.wts = static_cast<const uint8_t *>(a.w_rows);
+        p.wbytes = (uint32_t)tc_rows_weight_bytes();
+        p.bias = a.bias; p.act = a.act;
+        p.res = static_cast<const uint8_t *>(a.res);
+        p.y = static_cast<uint8_t *>(a.y);
+        p.acc_scale = a.acc_scale; p.out_scale = a.out_scale; p.res_scale = 1.0f / a.out_scale;
+        p.y2 = static_cast<uint8_t *>(a.y2); p.y2_scale = a.y2_scale; p.amax = a.amax;
+        p.err = a.err;
+        return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128>(map, ymap, rmap, p, st)
+                             : run_rows<DT_F16, DT_F16, 128>(map, ymap, rmap, p, st);
+    }
     if (dt == DT_F32) return cudaErrorInvalidValue;
     const int esz = dtype_size(dt);
     const int in_cpc = a.in_cpc ? a.in_cpc : 16 / esz;
@@ -797,7 +1250,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
     p.bias = a.bias; p.act = a.act;
     p.res = static_cast<const uint8_t *>(a.res);
     p.y = static_cast<uint8_t *>(a.y);
-    p.acc_scale = a.acc_scale; p.out_scale = a.out_scale;
+    p.acc_scale = a.acc_scale; p.out_scale = a.out_scale; p.res_scale = 1.0f / a.out_scale;
     p.y2 = static_cast<uint8_t *>(a.y2); p.y2_scale = a.y2_scale; p.amax = a.amax;
     p.ps_out = a.ps_out; p.ps_pitch = a.ps_pitch; p.skip = a; p.ps_act = a.ps_act;
     p.err = a.err;

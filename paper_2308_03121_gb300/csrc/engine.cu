@@ -110,6 +110,7 @@ struct Tensor {
 };
 
 struct Weights {
+    void *rows = nullptr;        // row-streaming 64->64 3x3 layout (tensor-core path)
     void *simt_or_tc = nullptr;  // 16-bit / FP32 layout
     void *f8 = nullptr;          // FP8 layout
     float *bias = nullptr;
@@ -384,6 +385,11 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
         const bool sw128 = L.op == "conv" && layout_cpc(f->act_dt, W.cin_pad) == 64;
         prepare_weights_tc(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, f->act_dt, 1.0f, host.data(), sw128);
         s = upload(f, host.data(), host.size(), &W.simt_or_tc);
+        if (s == NVISR_OK && L.op == "conv" && L.k == 3 && L.cin == 64 && L.cout == 64 && !L.ps) {
+            std::vector<uint8_t> rows(tc_rows_weight_bytes());
+            prepare_weights_rows(w, f->act_dt, rows.data());
+            s = upload(f, rows.data(), rows.size(), &W.rows);
+        }
     }
     if (s != NVISR_OK) return s;
     if (layer_is_fp8(f, L)) {
@@ -817,6 +823,7 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
     } else {
         a.x = in.ptr;
         a.w = Wt.simt_or_tc;
+        a.w_rows = Wt.rows;
     }
     if (s.add_t >= 0) a.res = f->tensors[s.add_t].ptr;
     if (s.out_t >= 0) {
@@ -1478,6 +1485,14 @@ nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_
     }
     NVISR_TRY_CUDA(sc.alloc(wbytes, &dw));
     NVISR_TRY_CUDA(cudaMemcpyAsync(dw, hwl.data(), wbytes, cudaMemcpyHostToDevice, st));
+    void *dwr = nullptr;
+    std::vector<uint8_t> hrows;
+    if (tc && idt != DT_E4M3 && k == 3 && cin == 64 && cout == 64) {
+        hrows.resize(tc_rows_weight_bytes());
+        prepare_weights_rows(hw.data(), idt, hrows.data());
+        NVISR_TRY_CUDA(sc.alloc(hrows.size(), &dwr));
+        NVISR_TRY_CUDA(cudaMemcpyAsync(dwr, hrows.data(), hrows.size(), cudaMemcpyHostToDevice, st));
+    }
     NVISR_TRY_CUDA(sc.alloc(cout_pad * 4, &db));
     NVISR_TRY_CUDA(cudaMemcpyAsync(db, hb.data(), cout_pad * 4, cudaMemcpyHostToDevice, st));
     NVISR_TRY_CUDA(sc.alloc((size_t)cin_pad * h * w * dtype_size(idt), &dx));
@@ -1493,7 +1508,7 @@ nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_
     NVISR_TRY_CUDA(sc.alloc(sizeof(int), (void **)&err));
     NVISR_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     ConvArgs a{};
-    a.x = dx; a.cin_pad = cin_pad; a.H = h; a.W = w; a.nimg = 1; a.w = dw; a.bias = (const float *)db;
+    a.x = dx; a.cin_pad = cin_pad; a.H = h; a.W = w; a.nimg = 1; a.w = dw; a.w_rows = dwr; a.bias = (const float *)db;
     a.cout = cout; a.cout_pad = cout_pad; a.k = k; a.act = act; a.res = dr; a.y = dy;
     a.in_dt = idt; a.out_dt = adt; a.acc_scale = sx * sw; a.out_scale = 1.f; a.y2_scale = 1.f; a.err = err;
     a.in_cpc = in_cpc; a.out_cpc = out_cpc;
