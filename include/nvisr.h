@@ -253,6 +253,33 @@ nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_
                           const float *weight, const float *bias, int32_t cout, int32_t k,
                           int32_t act, const float *res, float *y, void *stream);
 
+/* Size of the fixed device area behind nvisr_conv2d_static (32 MiB per device). */
+#define NVISR_CONV2D_STATIC_SCRATCH_BYTES (32 * 1024 * 1024)
+
+/* nvisr_conv2d without any allocation.  The paper has no counterpart: this is
+ * a library convenience for callers that must not allocate while they run
+ * (device memory handed out in advance, or real-time work that cannot let
+ * cudaFree synchronise the device).  Same arguments, results and error codes
+ * as nvisr_conv2d, except:
+ *  - every working buffer (blocked x, y and res, weight image, bias, error
+ *    word) is carved from one static device array of
+ *    NVISR_CONV2D_STATIC_SCRATCH_BYTES per device, set aside when the module
+ *    loads; weights are laid out by device kernels, so nothing is staged on
+ *    the host.  A problem that does not fit returns NVISR_OVER_BUDGET before
+ *    any device work.  Need: (cin_pad + cout_pad * (res ? 2 : 1)) * H * W
+ *    element bytes plus the weight image; 64 -> 64 channels with a residual
+ *    fit ~43k pixels in FP32 and ~87k in BF16 / FP16;
+ *  - precision is FP32, BF16 or FP16 (FP8 returns NVISR_UNSUPPORTED_FORMAT);
+ *  - the area is shared by every call on a device: calls that overlap in time
+ *    on one device (several threads or streams) race and must be serialised
+ *    by the caller;
+ *  - the first call on each device, made with that device current, looks up
+ *    the area's address; make that first call before any stream capture.
+ * Returns after the stream has finished the layer (it reads the error word). */
+nvisr_status nvisr_conv2d_static(int32_t precision, const float *x, int32_t cin, int32_t h, int32_t w,
+                                 const float *weight, const float *bias, int32_t cout, int32_t k,
+                                 int32_t act, const float *res, float *y, void *stream);
+
 /* Modulated deformable convolution 3x3, DCN v2 as in torchvision's
  * deform_conv2d (Section 3.1): offsets [2*G*9][H][W] (dy, dx per group and
  * tap), mask [G*9][H][W] (already in [0,1]), stride 1, padding 1.  Planar

@@ -19,7 +19,7 @@ from . import build as _build
 
 __all__ = [
     "Engine", "Filter", "NvisrError", "PREC", "Status", "fmt", "lib", "load",
-    "nvisr_conv2d", "nvisr_dcn2d", "nvisr_fig1_layout", "nvisr_group_runs",
+    "nvisr_conv2d", "nvisr_conv2d_static", "nvisr_dcn2d", "nvisr_fig1_layout", "nvisr_group_runs",
     "nvisr_ingest", "nvisr_network_check", "nvisr_requant", "nvisr_selftest",
     "nvisr_tuple_map",
 ]
@@ -106,6 +106,7 @@ _SIGS = {
     "nvisr_group_runs": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32P, _I32P, _I32P]),
     "nvisr_fig1_layout": (_I32, [_I32, _I32, _I32P, _I32P, _I32P]),
     "nvisr_conv2d": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _I32, _I32, _VP, _VP, _VP]),
+    "nvisr_conv2d_static": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _I32, _I32, _VP, _VP, _VP]),
     "nvisr_dcn2d": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP, _VP, _I32, _VP, _VP]),
     "nvisr_selftest": (_I32, [_I32P, _I32P]),
     "nvisr_selftest_swizzle": (_I32, [_I32P]),
@@ -202,6 +203,22 @@ def nvisr_conv2d(precision, x, weight, bias, act=0, res=None, stream=None):
                              res.data_ptr() if res is not None else None, y.data_ptr(), _stream_ptr(stream)),
            "nvisr_conv2d")
     return y
+
+
+def nvisr_conv2d_static(precision, x, weight, bias, act=0, res=None, stream=None, out=None):
+    """nvisr_conv2d through the allocation-free entry point (fixed device scratch area).
+    out: optional preallocated [cout][H][W] float32 cuda tensor."""
+    load()
+    cin, h, w = x.shape
+    cout, _, k, _ = weight.shape
+    if out is None:
+        import torch
+        out = torch.empty((cout, h, w), dtype=torch.float32, device=x.device)
+    _check(_LIB.nvisr_conv2d_static(PREC.get(precision, precision), x.data_ptr(), cin, h, w, weight.data_ptr(),
+                                    bias.data_ptr() if bias is not None else None, cout, k, act,
+                                    res.data_ptr() if res is not None else None, out.data_ptr(),
+                                    _stream_ptr(stream)), "nvisr_conv2d_static")
+    return out
 
 
 def nvisr_dcn2d(precision, x, offsets, mask, weight, bias, groups, stream=None):
