@@ -614,8 +614,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
             bool ok = mbar_wait_bounded(wbar, 0, abort, WAIT_NS);
             if (!ok) raise_abort(abort, p.err);
             const uint64_t b_base = smem_desc_sw128(smem_u32(wsm), 0);
-            const uint32_t idn[4] = {0u, instr_desc(TM, 64, AFMT, AFMT), instr_desc(TM, 128, AFMT, AFMT),
-                                     instr_desc(TM, 192, AFMT, AFMT)};
             int gin = 0, gout = 0, last_slot = -1;
             uint32_t last_par = 0;
             for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
@@ -641,49 +639,50 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
                     tc_fence_after();
                     if (o_lo <= o_hi) {
                         const uint64_t a_base = smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0);
-                        // Runs of contiguous TMEM slots.  The first MMA of the row (kx = 0, K step 0)
-                        // must not accumulate into the fresh row r+1, so it uses set F = runs over
-                        // [o_lo, min(r, o_hi)] + the fresh row alone; every later MMA uses set M =
-                        // runs over [o_lo, o_hi] (one N = 192 MMA unless the ring wraps).
-                        uint32_t fd[3], fid[3], md[2], mid[2];
-                        uint64_t fbd[3], mbd[2];
-                        int nf = 0, nm = 0, nfold = 0;
-                        auto runs = [&](int a0, int a1, uint32_t *dd, uint32_t *ii, uint64_t *bb, int &n) {
-                            int o = a0;
-                            while (o <= a1) {
-                                const int slot = (gout + o - ra) % NSLOT;
-                                const int run = min(a1 - o + 1, NSLOT - slot);
-                                dd[n] = tmem_base + (uint32_t)(slot * 64);
-                                ii[n] = idn[run];
-                                bb[n] = b_base + (uint64_t)(((o - r + 1) * 64 * 128) >> 4);
-                                ++n;
-                                o += run;
+                        // Output rows [o_lo, o_hi] occupy one run of contiguous TMEM slots, or two
+                        // where the ring wraps.  The first MMA of the row (kx = 0, K step 0) must not
+                        // accumulate into the fresh row r+1, so it is issued per run of the old rows
+                        // plus once for the fresh row (accumulate = 0); the other 11 MMAs cover all
+                        // of [o_lo, o_hi] with one N = 64 * rows MMA per run.  Everything is held in
+                        // scalars so the unrolled issue sequence is only descriptor adds.
+                        const uint32_t id0 = instr_desc(TM, 0, AFMT, AFMT);
+                        const uint32_t nstep = 8u << 17;  // N += 64
+                        auto slot_of = [&](int o) { return (gout + o - ra) % NSLOT; };
+                        auto bd_of = [&](int o) { return b_base + (uint64_t)(((o - r + 1) * 64 * 128) >> 4); };
+                        const int sl0 = slot_of(o_lo);
+                        const int len = o_hi - o_lo + 1;
+                        const int m0 = min(len, NSLOT - sl0), m1 = len - m0;
+                        const uint32_t md0 = tmem_base + (uint32_t)(sl0 * 64), md1 = tmem_base;
+                        const uint32_t mi0 = id0 + nstep * (uint32_t)m0, mi1 = id0 + nstep * (uint32_t)max(m1, 1);
+                        const uint64_t mb0 = bd_of(o_lo), mb1 = bd_of(o_lo + m0);
+                        // first MMA: old rows [o_lo, old_hi] (split at the wrap), then the fresh row
+                        {
+                            const int old_hi = fresh ? min(r, o_hi) : o_hi;
+                            const int olen = old_hi - o_lo + 1;
+                            if (olen > 0) {
+                                const int f0 = min(olen, m0), f1 = olen - f0;
+                                umma<0>(md0, a_base, mb0, id0 + nstep * (uint32_t)f0, 1u);
+                                if (f1 > 0) umma<0>(md1, a_base, mb1, id0 + nstep * (uint32_t)f1, 1u);
                             }
-                        };
-                        const int old_hi = fresh ? min(r, o_hi) : o_hi;
-                        if (o_lo <= old_hi) runs(o_lo, old_hi, fd, fid, fbd, nf);
-                        nfold = nf;
-                        if (fresh) runs(r + 1, r + 1, fd, fid, fbd, nf);
-                        runs(o_lo, o_hi, md, mid, mbd, nm);
-#pragma unroll 1
-                        for (int kx = 0; kx < 3; ++kx) {
+                            if (fresh)
+                                umma<0>(tmem_base + (uint32_t)(slot_of(r + 1) * 64), a_base, bd_of(r + 1),
+                                        id0 + nstep, 0u);
+                        }
+                        if (m1 == 0) {
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
+                            for (int t = 1; t < 12; ++t) {
+                                const int kx = t >> 2, j = t & 3;
+                                umma<0>(md0, a_base + (uint64_t)((kx * 128 + j * 32) >> 4),
+                                        mb0 + (uint64_t)((kx * WKX + j * 32) >> 4), mi0, 1u);
+                            }
+                        } else {
+#pragma unroll
+                            for (int t = 1; t < 12; ++t) {
+                                const int kx = t >> 2, j = t & 3;
                                 const uint64_t ad = a_base + (uint64_t)((kx * 128 + j * 32) >> 4);
                                 const uint64_t boff = (uint64_t)((kx * WKX + j * 32) >> 4);
-                                if (kx == 0 && j == 0) {
-#pragma unroll
-                                    for (int k = 0; k < 3; ++k) {
-                                        if (k >= nf) break;
-                                        umma<0>(fd[k], ad, fbd[k] + boff, fid[k], k < nfold ? 1u : 0u);
-                                    }
-                                } else {
-#pragma unroll
-                                    for (int k = 0; k < 2; ++k) {
-                                        if (k >= nm) break;
-                                        umma<0>(md[k], ad, mbd[k] + boff, mid[k], 1u);
-                                    }
-                                }
+                                umma<0>(md0, ad, mb0 + boff, mi0, 1u);
+                                umma<0>(md1, ad, mb1 + boff, mi1, 1u);
                             }
                         }
                     }
