@@ -512,6 +512,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
     constexpr uint32_t WKX = 3 * 64 * 128;                    // weights of one kx: [ky' = 2 - ky][64][128 B]
     constexpr uint32_t TILEB = TM * 128;                      // one 128-pixel output / residual row tile
     constexpr int NSLOT = 8;                                  // output-row accumulators in TMEM
+    static_assert(NSLOT == 8, "slot index and phase use & 7 and >> 3");
     constexpr uint32_t NCOLS = 512;
     constexpr int UPC_O = 16 / sizeof(TO);
     constexpr int NU = 64 / UPC_O;                            // 16-byte units of a pixel's 64 channels
@@ -614,24 +615,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
             bool ok = mbar_wait_bounded(wbar, 0, abort, WAIT_NS);
             if (!ok) raise_abort(abort, p.err);
             const uint64_t b_base = smem_desc_sw128(smem_u32(wsm), 0);
-            int gin = 0, gout = 0, last_slot = -1;
-            uint32_t last_par = 0;
+            // Work between two MMA issues is not overlapped with the tensor pipe
+            // beyond about one MMA, so the per-row bookkeeping is kept lean: stage and
+            // phase advance incrementally, slots are (base + row) & 7, and the waits
+            // first take a non-blocking test (cheap when the phase is already done).
+            int s = 0, gout = 0, last_slot = -1;
+            uint32_t ph = 0, last_par = 0;
+            auto wait_fast = [&](uint64_t *bar, uint32_t par) {
+                return mbar_test_wait(bar, par) || mbar_wait_bounded(bar, par, abort, WAIT_NS);
+            };
             for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
                 int img, x0, ra, rb;
                 strip_of(sidx, img, x0, ra, rb);
-                for (int r = ra - 1; r <= rb && ok; ++r, ++gin) {
-                    const int s = gin % S;
+                const int base = gout - ra;  // global index of this strip's output row o is base + o
+                for (int r = ra - 1; r <= rb && ok; ++r) {
                     const int o_lo = max(r - 1, ra), o_hi = min(r + 1, rb - 1);
-                    const bool fresh = (r + 1 <= rb - 1) && (r + 1 >= ra);
+                    const bool fresh = r + 1 <= rb - 1;
                     if (fresh) {
-                        const int i = gout + (r + 1 - ra);
-                        if (!mbar_wait_bounded(&slotfree[i % NSLOT], ((i / NSLOT) & 1) ^ 1, abort, WAIT_NS)) {
+                        const int i = base + r + 1;
+                        if (!wait_fast(&slotfree[i & (NSLOT - 1)], (uint32_t)((i >> 3) & 1) ^ 1u)) {
                             raise_abort(abort, p.err);
                             ok = false;
                             break;
                         }
                     }
-                    if (!mbar_wait_bounded(&full[s], (uint32_t)((gin / S) & 1), abort, WAIT_NS)) {
+                    if (!wait_fast(&full[s], ph)) {
                         raise_abort(abort, p.err);
                         ok = false;
                         break;
@@ -647,7 +655,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
                         // scalars so the unrolled issue sequence is only descriptor adds.
                         const uint32_t id0 = instr_desc(TM, 0, AFMT, AFMT);
                         const uint32_t nstep = 8u << 17;  // N += 64
-                        auto slot_of = [&](int o) { return (gout + o - ra) % NSLOT; };
+                        auto slot_of = [&](int o) { return (base + o) & (NSLOT - 1); };
                         auto bd_of = [&](int o) { return b_base + (uint64_t)(((o - r + 1) * 64 * 128) >> 4); };
                         const int sl0 = slot_of(o_lo);
                         const int len = o_hi - o_lo + 1;
@@ -688,10 +696,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
                     }
                     umma_commit(&empty[s]);
                     if (r - 1 >= ra) {
-                        const int i = gout + (r - 1 - ra);
-                        umma_commit(&rowdone[i % NSLOT]);
-                        last_slot = i % NSLOT;
-                        last_par = (uint32_t)((i / NSLOT) & 1);
+                        const int i = base + r - 1;
+                        umma_commit(&rowdone[i & (NSLOT - 1)]);
+                        last_slot = i & (NSLOT - 1);
+                        last_par = (uint32_t)((i >> 3) & 1);
+                    }
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
                     }
                 }
                 gout += rb - ra;
@@ -1144,7 +1156,9 @@ cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUte
                      cudaStream_t st) {
     constexpr uint32_t ROWB = ((TM + 2) * 128 + 1023u) & ~1023u;
     constexpr uint32_t WB = 3 * 3 * 64 * 128;
-    constexpr uint32_t TILES = 4 * TM * 128;  // 2 output staging + 2 residual tiles
+    // 2 output staging tiles, + 2 residual tiles when the layer adds a residual
+    // (without one, their room goes to deeper input prefetch)
+    const uint32_t TILES = (p.res ? 4u : 2u) * TM * 128;
     int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES) / (int)ROWB;
     if (stages > 8) stages = 8;
     if (stages < 2) return cudaErrorInvalidConfiguration;
