@@ -480,6 +480,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
     }
 }
 
+// Packed two-lane FP32 arithmetic (IEEE round-to-nearest per lane, as the scalar ops).
+__device__ __forceinline__ void add_f32x2(float &a, float &b, float c, float d) {
+    uint64_t x, y;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a), "f"(b));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(c), "f"(d));
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(x) : "l"(y));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+}
+__device__ __forceinline__ void mul_f32x2(float &a, float &b, float c, float d) {
+    uint64_t x, y;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a), "f"(b));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(c), "f"(d));
+    asm("mul.rn.f32x2 %0, %0, %1;" : "+l"(x) : "l"(y));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+}
+// Two 16-bit elements of one 32-bit word (element 0 in the low half) <-> two floats.
+template <typename T>
+__device__ __forceinline__ void unpack2(uint32_t w, float &lo, float &hi);
+template <>
+__device__ __forceinline__ void unpack2<__nv_bfloat16>(uint32_t w, float &lo, float &hi) {
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xffff0000u);
+}
+template <>
+__device__ __forceinline__ void unpack2<__half>(uint32_t w, float &lo, float &hi) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    lo = f.x;
+    hi = f.y;
+}
+template <typename T>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <>
+__device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+template <>
+__device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
 // ---------------------------------------------------------------- row-streaming 3x3 conv
 
 // Row-streaming variant for 64 -> 64 channel 3x3 layers (the residual trunks).
@@ -543,6 +585,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
     const int strips_per_img = rp.xtiles * rp.bands;
     const int nstrips = strips_per_img * p.nimg;
     const bool has_res = p.res != nullptr;
+    const bool plain = p.acc_scale == 1.f && p.out_scale == 1.f && p.res_scale == 1.f && !p.amax && !p.y2;
     auto strip_of = [&](int sidx, int &img, int &x0, int &ra, int &rb) {
         img = sidx / strips_per_img;
         const int rem = sidx - img * strips_per_img;
@@ -770,12 +813,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
                         grp_stop[g] = 1;
                     }
                 }
-                const float as = p.acc_scale;
+                if (plain) {
+                    // 16-bit trunk layer (unit scales, no calibration): packed f32x2 arithmetic
+                    // keeps the epilogue's instruction stream short, because its warps share
+                    // issue slots with the MMA-issuing warp (same results as the general path)
 #pragma unroll
-                for (int e = 0; e < 64; ++e) {
-                    float ov = v[e] * as + sbias[e];
-                    if (p.act == 1) ov = lrelu(ov);
-                    v[e] = ov;
+                    for (int e = 0; e < 64; e += 4) {
+                        const float4 b = *reinterpret_cast<const float4 *>(sbias + e);
+                        add_f32x2(v[e], v[e + 1], b.x, b.y);
+                        add_f32x2(v[e + 2], v[e + 3], b.z, b.w);
+                    }
+                    if (p.act == 1) {
+#pragma unroll
+                        for (int e = 0; e < 64; e += 2) {
+                            float t0 = v[e], t1 = v[e + 1];
+                            mul_f32x2(t0, t1, 0.1f, 0.1f);
+                            v[e] = fmaxf(v[e], t0);
+                            v[e + 1] = fmaxf(v[e + 1], t1);
+                        }
+                    }
+                } else {
+                    const float as = p.acc_scale;
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) {
+                        float ov = v[e] * as + sbias[e];
+                        if (p.act == 1) ov = lrelu(ov);
+                        v[e] = ov;
+                    }
                 }
                 if (has_res) {
                     bool rw = mbar_wait_bounded(&resfull[g], (uint32_t)(k & 1), abort, WAIT_NS);
@@ -788,10 +852,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
 #pragma unroll
                     for (int uu = 0; uu < NU; ++uu) {
                         const int unit = uu ^ (m & 7);
-                        alignas(16) TO rv[UPC_O];
-                        *reinterpret_cast<uint4 *>(rv) = *reinterpret_cast<const uint4 *>(rt + unit * 16);
+                        const uint4 raw = *reinterpret_cast<const uint4 *>(rt + unit * 16);
+                        const uint32_t wd[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
-                        for (int e = 0; e < UPC_O; ++e) v[uu * UPC_O + e] += from_elem<TO>(rv[e]) * rs;
+                        for (int h = 0; h < 4; ++h) {
+                            float r0, r1;
+                            unpack2<TO>(wd[h], r0, r1);
+                            if (plain) {
+                                add_f32x2(v[uu * 8 + 2 * h], v[uu * 8 + 2 * h + 1], r0, r1);
+                            } else {
+                                v[uu * 8 + 2 * h] += r0 * rs;
+                                v[uu * 8 + 2 * h + 1] += r1 * rs;
+                            }
+                        }
                     }
                 }
                 if (valid && p.amax) {
@@ -811,14 +884,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
                             *reinterpret_cast<const uint4 *>(o8);
                     }
                 }
-                const float os = p.out_scale;
+                if (!plain) {
+                    const float os = p.out_scale;
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) v[e] *= os;
+                }
 #pragma unroll
                 for (int uu = 0; uu < NU; ++uu) {
                     const int unit = uu ^ (m & 7);
-                    alignas(16) TO ov[UPC_O];
-#pragma unroll
-                    for (int e = 0; e < UPC_O; ++e) ov[e] = to_elem<TO>(v[uu * UPC_O + e] * os);
-                    *reinterpret_cast<uint4 *>(ot + unit * 16) = *reinterpret_cast<const uint4 *>(ov);
+                    uint4 ov;
+                    ov.x = pack2<TO>(v[uu * 8 + 0], v[uu * 8 + 1]);
+                    ov.y = pack2<TO>(v[uu * 8 + 2], v[uu * 8 + 3]);
+                    ov.z = pack2<TO>(v[uu * 8 + 4], v[uu * 8 + 5]);
+                    ov.w = pack2<TO>(v[uu * 8 + 6], v[uu * 8 + 7]);
+                    *reinterpret_cast<uint4 *>(ot + unit * 16) = ov;
                 }
                 fence_proxy_async();  // staging writes (and residual reads) before the async proxy
                 if (leader && *abort) grp_stop[g] = 1;
