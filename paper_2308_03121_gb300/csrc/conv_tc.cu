@@ -43,6 +43,7 @@ constexpr int TM = 128;
 // warp 0: TMA producer, warp 1: MMA issuer + TMEM owner, warps 2-9: epilogue
 // (two warps per TMEM lane quadrant, each owning half of the accumulator columns)
 constexpr int NTHREADS = 320;
+constexpr int ROWS_THREADS = 352;     // row kernel: + one warp that performs the MMA issuer's waits
 constexpr int NEPI = 256;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 232448;  // 227 KB per CTA
@@ -543,7 +544,7 @@ struct RowPlan {
 };
 
 template <int IN_DT, int OUT_DT, int CBO>
-__global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 const __grid_constant__ CUtensorMap ymap,
                                                                 const __grid_constant__ CUtensorMap rmap,
                                                                 const TcParams p, const RowPlan rp) {
@@ -575,6 +576,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
     // per-group stop flags: written between a group's two per-row named
     // barriers, read after the second, so a group's warps leave on the same row
     volatile int *grp_stop = reinterpret_cast<volatile int *>(tmem_slot + 2);
+    // input rows (global count) whose input has landed and whose fresh TMEM slot is
+    // drained, published by the wait warp for the MMA issuer
+    int *ready = reinterpret_cast<int *>(tmem_slot + 4);
     float *sbias = reinterpret_cast<float *>(smem + 512);
     uint8_t *wsm = smem + SMEM_HDR;
     uint8_t *stage0 = wsm + 3 * WKX;
@@ -610,6 +614,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
         *abort = 0;
         grp_stop[0] = 0;
         grp_stop[1] = 0;
+        *ready = 0;
         fence_mbarrier_init();
     }
     if (warp == 1) {
@@ -658,36 +663,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
             bool ok = mbar_wait_bounded(wbar, 0, abort, WAIT_NS);
             if (!ok) raise_abort(abort, p.err);
             const uint64_t b_base = smem_desc_sw128(smem_u32(wsm), 0);
-            // Work between two MMA issues is not overlapped with the tensor pipe
-            // beyond about one MMA, so the per-row bookkeeping is kept lean: stage and
-            // phase advance incrementally, slots are (base + row) & 7, and the waits
-            // first take a non-blocking test (cheap when the phase is already done).
-            int s = 0, gout = 0, last_slot = -1;
-            uint32_t ph = 0, last_par = 0;
-            auto wait_fast = [&](uint64_t *bar, uint32_t par) {
-                return mbar_test_wait(bar, par) || mbar_wait_bounded(bar, par, abort, WAIT_NS);
+            // Work between MMA issues leaves the tensor pipe idle once the few queued
+            // MMAs have run, and an mbarrier test made while MMAs are queued costs
+            // about a hundred pipe cycles.  So this thread makes no mbarrier waits per
+            // row: the wait warp publishes how many input rows are ready (input
+            // landed, fresh slot drained) and the issuer re-reads that count only
+            // when it runs out of ready rows.  Stage and phase advance incrementally.
+            int s = 0, gout = 0, last_slot = -1, gin = 0, nready = 0;
+            uint32_t last_par = 0;
+            auto await_row = [&](int row) -> bool {
+                if (row < nready) return true;
+                nready = ld_acquire_cta(ready);
+                if (row >= nready) {
+                    const uint64_t t0 = globaltimer_ns();
+                    for (uint32_t it = 1; row >= (nready = ld_acquire_cta(ready)); ++it) {
+                        if ((it & 63) == 0 && (*abort || globaltimer_ns() - t0 > WAIT_NS)) return false;
+                    }
+                }
+                tc_fence_after();  // the MMAs of the newly ready rows come after the acquire
+                return true;
             };
             for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
                 int img, x0, ra, rb;
                 strip_of(sidx, img, x0, ra, rb);
                 const int base = gout - ra;  // global index of this strip's output row o is base + o
-                for (int r = ra - 1; r <= rb && ok; ++r) {
+                for (int r = ra - 1; r <= rb && ok; ++r, ++gin) {
                     const int o_lo = max(r - 1, ra), o_hi = min(r + 1, rb - 1);
                     const bool fresh = r + 1 <= rb - 1;
-                    if (fresh) {
-                        const int i = base + r + 1;
-                        if (!wait_fast(&slotfree[i & (NSLOT - 1)], (uint32_t)((i >> 3) & 1) ^ 1u)) {
-                            raise_abort(abort, p.err);
-                            ok = false;
-                            break;
-                        }
-                    }
-                    if (!wait_fast(&full[s], ph)) {
+                    if (!await_row(gin)) {
                         raise_abort(abort, p.err);
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
                     if (o_lo <= o_hi) {
                         const uint64_t a_base = smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0);
                         // Output rows [o_lo, o_hi] occupy one run of contiguous TMEM slots, or two
@@ -744,6 +751,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
                         last_slot = i & (NSLOT - 1);
                         last_par = (uint32_t)((i >> 3) & 1);
                     }
+                    if (++s == S) s = 0;
+                }
+                gout += rb - ra;
+            }
+            if (last_slot >= 0) mbar_wait_bounded(&rowdone[last_slot], last_par, nullptr, WAIT_NS);
+        }
+    } else if (warp == 10) {
+        if (lane == 0) {
+            // ---------------- wait warp: for each input row in the issuer's order, wait
+            // until the slot of its fresh output row is drained and its input row has
+            // landed, then publish the count of ready rows (release).
+            int s = 0, gout = 0, gin = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
+                int img, x0, ra, rb;
+                strip_of(sidx, img, x0, ra, rb);
+                const int base = gout - ra;
+                for (int r = ra - 1; r <= rb; ++r) {
+                    if (r + 1 <= rb - 1) {
+                        const int i = base + r + 1;
+                        if (!mbar_wait_bounded(&slotfree[i & (NSLOT - 1)], (uint32_t)((i >> 3) & 1) ^ 1u, abort,
+                                               WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (!mbar_wait_bounded(&full[s], ph, abort, WAIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    st_release_cta(ready, ++gin);
                     if (++s == S) {
                         s = 0;
                         ph ^= 1u;
@@ -751,7 +790,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_rows_kernel(const __grid_con
                 }
                 gout += rb - ra;
             }
-            if (last_slot >= 0) mbar_wait_bounded(&rowdone[last_slot], last_par, nullptr, WAIT_NS);
+            if (!ok) raise_abort(abort, p.err);
         }
     } else {
         // ---------------- epilogue: two independent groups of 4 warps (warps 2-5
@@ -1256,7 +1295,7 @@ cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUte
     rp.bands = (p.H + rp.rps - 1) / rp.rps;
     int grid = rp.xtiles * rp.bands * p.nimg;
     if (grid > sms) grid = sms;
-    kern<<<grid, NTHREADS, smem, st>>>(map, ymap, rmap, p, rp);
+    kern<<<grid, ROWS_THREADS, smem, st>>>(map, ymap, rmap, p, rp);
     return cudaGetLastError();
 }
 
