@@ -31,6 +31,7 @@ struct RangeConst {
     float y_off, y_den, c_off, c_den;  // normalise: (v - off) / den
     float y_mul, y_add, c_mul, c_add;  // scale back: v * mul + add
     float vmax;
+    float y_rden, c_rden;              // 1 / den (the streaming kernels multiply)
 };
 
 RangeConst range_const(int bits, int range) {
@@ -45,6 +46,8 @@ RangeConst range_const(int bits, int range) {
         r.y_mul = top; r.y_add = 0.f; r.c_mul = top; r.c_add = (float)(1 << (bits - 1));
     }
     r.vmax = (float)((1 << bits) - 1);
+    r.y_rden = 1.0f / r.y_den;
+    r.c_rden = 1.0f / r.c_den;
     return r;
 }
 
@@ -136,6 +139,96 @@ __global__ void __launch_bounds__(256) ingest_kernel(
     }
 }
 
+// 4:2:0 ingest, one thread per 2 luma rows x 8 columns (one chroma row, 4
+// chroma columns): the chroma rows j-1 .. j+1 and columns 4q-1 .. 4q+4 the
+// block needs are read once into registers (normalised), then every luma
+// sample's chroma is interpolated from them in the same order as the scalar
+// form (vertical, then horizontal), and the three planes are written with
+// 16-byte stores.  Divisions are replaced by multiplications with the
+// reciprocal.
+template <typename S>
+__global__ void __launch_bounds__(128) ingest420_kernel(
+    const uint8_t *__restrict__ yp, int64_t py, const uint8_t *__restrict__ up, int64_t pu,
+    const uint8_t *__restrict__ vp, int64_t pv, int H, int W, int loc, RangeConst rc,
+    float *__restrict__ out, int64_t pitch) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const int x0 = q * 8;
+    if (x0 >= W) return;
+    const int Hc = H / 2, Wc = W / 2;
+    float cu[3][6], cv[3][6];
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr) {
+        const int row = clampi(j - 1 + rr, 0, Hc - 1);
+        const S *ur = reinterpret_cast<const S *>(up + (int64_t)row * pu);
+        const S *vr = reinterpret_cast<const S *>(vp + (int64_t)row * pv);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) {
+            const int col = clampi(4 * q - 1 + cc, 0, Wc - 1);
+            cu[rr][cc] = ((float)__ldg(ur + col) - rc.c_off) * rc.c_rden;
+            cv[rr][cc] = ((float)__ldg(vr + col) - rc.c_off) * rc.c_rden;
+        }
+    }
+    const int64_t plane = pitch * H;
+    const bool vec = x0 + 8 <= W && (pitch & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int y = 2 * j + a;
+        if (y >= H) break;
+        // vertical interpolation: luma row 2j uses chroma rows (j, j-1), row 2j+1 uses (j, j+1)
+        float vu[6], vvv[6];
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) {
+            if (loc == NVISR_CHROMA_POINT) {
+                vu[cc] = cu[1][cc];
+                vvv[cc] = cv[1][cc];
+            } else {
+                vu[cc] = 0.75f * cu[1][cc] + 0.25f * cu[a ? 2 : 0][cc];
+                vvv[cc] = 0.75f * cv[1][cc] + 0.25f * cv[a ? 2 : 0][cc];
+            }
+        }
+        const S *yr = reinterpret_cast<const S *>(yp + (int64_t)y * py);
+        float r[8], g[8], b[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int x = min(x0 + e, W - 1);
+            const int li = (e >> 1) + 1;  // local index of chroma column x >> 1
+            float cb, cr;
+            if (loc == NVISR_CHROMA_LEFT) {
+                cb = (e & 1) ? 0.5f * (vu[li] + vu[li + 1]) : vu[li];
+                cr = (e & 1) ? 0.5f * (vvv[li] + vvv[li + 1]) : vvv[li];
+            } else if (loc == NVISR_CHROMA_CENTER) {
+                cb = (e & 1) ? 0.75f * vu[li] + 0.25f * vu[li + 1] : 0.75f * vu[li] + 0.25f * vu[li - 1];
+                cr = (e & 1) ? 0.75f * vvv[li] + 0.25f * vvv[li + 1] : 0.75f * vvv[li] + 0.25f * vvv[li - 1];
+            } else {
+                cb = vu[li];
+                cr = vvv[li];
+            }
+            const float Y = ((float)__ldg(yr + x) - rc.y_off) * rc.y_rden;
+            r[e] = Y + (2.0f * (1.0f - KR)) * cr;
+            b[e] = Y + (2.0f * (1.0f - KB)) * cb;
+            g[e] = (Y - KR * r[e] - KB * b[e]) * (1.0f / KG);
+        }
+        float *o = out + (int64_t)y * pitch + x0;
+        if (vec) {
+            *reinterpret_cast<float4 *>(o) = make_float4(r[0], r[1], r[2], r[3]);
+            *reinterpret_cast<float4 *>(o + 4) = make_float4(r[4], r[5], r[6], r[7]);
+            *reinterpret_cast<float4 *>(o + plane) = make_float4(g[0], g[1], g[2], g[3]);
+            *reinterpret_cast<float4 *>(o + plane + 4) = make_float4(g[4], g[5], g[6], g[7]);
+            *reinterpret_cast<float4 *>(o + 2 * plane) = make_float4(b[0], b[1], b[2], b[3]);
+            *reinterpret_cast<float4 *>(o + 2 * plane + 4) = make_float4(b[4], b[5], b[6], b[7]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                if (x0 + e >= W) break;
+                o[e] = r[e];
+                o[plane + e] = g[e];
+                o[2 * plane + e] = b[e];
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ float quant(float v, float vmax) {
     v = rintf(v);  // round half to even
     return fminf(fmaxf(v, 0.0f), vmax);
@@ -181,8 +274,8 @@ __device__ __forceinline__ float out_at(const float *in, int64_t pitch, int64_t 
 
 __device__ __forceinline__ void rgb2ycc(float r, float g, float b, float &y, float &cb, float &cr) {
     y = KR * r + KG * g + KB * b;
-    cb = (b - y) / (2.0f * (1.0f - KB));
-    cr = (r - y) / (2.0f * (1.0f - KR));
+    cb = (b - y) * (1.0f / (2.0f * (1.0f - KB)));
+    cr = (r - y) * (1.0f / (2.0f * (1.0f - KR)));
 }
 
 // 4:4:4: one thread per 4 pixels of a row.
@@ -190,7 +283,7 @@ template <typename S>
 __global__ void __launch_bounds__(256) requant444_kernel(const float *__restrict__ in, int64_t pitch,
                                                          int H, int W, RangeConst rc, uint8_t *yp,
                                                          int64_t py, uint8_t *up, int64_t pu,
-                                                         uint8_t *vp, int64_t pv, SkipArgs sk) {
+                                                         uint8_t *vp, int64_t pv, const __grid_constant__ SkipArgs sk) {
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const int y = blockIdx.y;
     if (x0 >= W) return;
@@ -206,23 +299,45 @@ __global__ void __launch_bounds__(256) requant444_kernel(const float *__restrict
 }
 
 // 4:2:0: one thread per (chroma row j, 4 chroma columns): luma rows 2j, 2j+1,
-// columns 8q .. 8q+7; chroma needs columns 8q-1 .. 8q+7 for LEFT siting.
+// columns 8q .. 8q+7; chroma needs columns 8q-1 .. 8q+7 for LEFT siting.  The
+// network output of those 2 x 9 pixels is loaded once (two 16-byte loads and
+// one scalar per row and channel when the rows are 16-byte aligned), luma is
+// written with one 8- or 16-byte store per row and chroma with one per plane.
 // SKIP2: the skip is one frame upsampled 2x bilinearly (align_corners = false,
 // edge clamp).  Output rows 2j, 2j+1 and columns 8q-1 .. 8q+7 then read
 // low-resolution rows j-1 .. j+1 and columns 4q-1 .. 4q+4 (clamped), loaded
 // once into registers; every output sample blends two rows and two columns
 // with the fixed weights 1/4, 3/4 in the same order as the general formula.
 template <typename S, bool SKIP2>
-__global__ void __launch_bounds__(256) requant420_kernel(const float *__restrict__ in, int64_t pitch,
+__global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict__ in, int64_t pitch,
                                                          int H, int W, int loc, RangeConst rc,
                                                          uint8_t *yp, int64_t py, uint8_t *up,
-                                                         int64_t pu, uint8_t *vp, int64_t pv, SkipArgs sk) {
+                                                         int64_t pu, uint8_t *vp, int64_t pv, const __grid_constant__ SkipArgs sk) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     const int xb = q * 8;
     if (xb >= W) return;
     const int64_t plane = pitch * H;
     const int Wc = W / 2;
+    // px[ch][a][c9]: network output of channel ch, row 2j + a, column xb - 1 + c9 (clamped)
+    float px[3][2][9];
+    const bool vin = xb + 8 <= W && (pitch & 3) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const float *row = in + (int64_t)ch * plane + (int64_t)(2 * j + a) * pitch;
+            px[ch][a][0] = __ldg(row + clampi(xb - 1, 0, W - 1));
+            if (vin) {
+                const float4 v0 = __ldg(reinterpret_cast<const float4 *>(row + xb));
+                const float4 v1 = __ldg(reinterpret_cast<const float4 *>(row + xb + 4));
+                px[ch][a][1] = v0.x; px[ch][a][2] = v0.y; px[ch][a][3] = v0.z; px[ch][a][4] = v0.w;
+                px[ch][a][5] = v1.x; px[ch][a][6] = v1.y; px[ch][a][7] = v1.z; px[ch][a][8] = v1.w;
+            } else {
+#pragma unroll
+                for (int c = 1; c < 9; ++c) px[ch][a][c] = __ldg(row + clampi(xb - 1 + c, 0, W - 1));
+            }
+        }
     float lr[SKIP2 ? 3 : 1][3][6];
     if (SKIP2) {
 #pragma unroll
@@ -236,7 +351,7 @@ __global__ void __launch_bounds__(256) requant420_kernel(const float *__restrict
     }
     // output (row 2j + a, column xb - 1 + c9) of channel ch: residual + skip
     auto sample = [&](int ch, int a, int c9, int x) -> float {
-        const float v = in[(int64_t)ch * plane + (int64_t)(2 * j + a) * pitch + x];
+        const float v = px[ch][a][c9];
         if (!SKIP2) return sk.n ? v + skip_at(sk, ch, 2 * j + a, x) : v;
         // horizontal: even c9 -> odd column 2i+1 (3/4 col i, 1/4 col i+1), odd c9 -> even 2i (1/4 col i-1, 3/4 col i)
         const int c0 = (c9 & 1) ? (c9 - 1) / 2 : c9 / 2;
@@ -249,27 +364,47 @@ __global__ void __launch_bounds__(256) requant420_kernel(const float *__restrict
     };
     // columns xb-1 .. xb+7 (9 columns), clamped; two rows.
     float cbv[9], crv[9];  // row-pair mean of full-resolution chroma
+    float yq[2][8];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
         const int x = clampi(xb - 1 + c, 0, W - 1);
         float cb2[2], cr2[2];
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr) {
-            const int y = 2 * j + rr;
             float Y, cb, cr;
             rgb2ycc(sample(0, rr, c, x), sample(1, rr, c, x), sample(2, rr, c, x), Y, cb, cr);
             cb2[rr] = cb;
             cr2[rr] = cr;
-            if (c >= 1 && c <= 8 && xb - 1 + c < W)
-                st_sample<S>(yp, py, y, x, quant(Y * rc.y_mul + rc.y_add, rc.vmax));
+            if (c >= 1) yq[rr][c - 1] = quant(Y * rc.y_mul + rc.y_add, rc.vmax);
         }
         cbv[c] = 0.5f * (cb2[0] + cb2[1]);
         crv[c] = 0.5f * (cr2[0] + cr2[1]);
     }
 #pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        S *yrow = reinterpret_cast<S *>(yp + (int64_t)(2 * j + rr) * py) + xb;
+        if (xb + 8 <= W && (reinterpret_cast<uintptr_t>(yrow) & (8 * sizeof(S) - 1)) == 0) {
+            uint32_t w[4];
+            if (sizeof(S) == 2) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) w[k] = (uint32_t)(int)yq[rr][2 * k] | ((uint32_t)(int)yq[rr][2 * k + 1] << 16);
+                *reinterpret_cast<uint4 *>(yrow) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    w[k] = (uint32_t)(int)yq[rr][4 * k] | ((uint32_t)(int)yq[rr][4 * k + 1] << 8) |
+                           ((uint32_t)(int)yq[rr][4 * k + 2] << 16) | ((uint32_t)(int)yq[rr][4 * k + 3] << 24);
+                *reinterpret_cast<uint2 *>(yrow) = make_uint2(w[0], w[1]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (xb + e < W) yrow[e] = (S)(int)yq[rr][e];
+        }
+    }
+    float cq[2][4];
+#pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const int i = q * 4 + e;
-        if (i >= Wc) break;
         const int c = 1 + 2 * e;  // index of column 2i
         float cb, cr;
         if (loc == NVISR_CHROMA_LEFT) {
@@ -279,8 +414,26 @@ __global__ void __launch_bounds__(256) requant420_kernel(const float *__restrict
             cb = 0.5f * (cbv[c] + cbv[c + 1]);
             cr = 0.5f * (crv[c] + crv[c + 1]);
         }
-        st_sample<S>(up, pu, j, i, quant(cb * rc.c_mul + rc.c_add, rc.vmax));
-        st_sample<S>(vp, pv, j, i, quant(cr * rc.c_mul + rc.c_add, rc.vmax));
+        cq[0][e] = quant(cb * rc.c_mul + rc.c_add, rc.vmax);
+        cq[1][e] = quant(cr * rc.c_mul + rc.c_add, rc.vmax);
+    }
+    const int i0 = q * 4;
+#pragma unroll
+    for (int pl = 0; pl < 2; ++pl) {
+        S *crow = reinterpret_cast<S *>((pl ? vp : up) + (int64_t)j * (pl ? pv : pu)) + i0;
+        if (i0 + 4 <= Wc && (reinterpret_cast<uintptr_t>(crow) & (4 * sizeof(S) - 1)) == 0) {
+            if (sizeof(S) == 2)
+                *reinterpret_cast<uint2 *>(crow) =
+                    make_uint2((uint32_t)(int)cq[pl][0] | ((uint32_t)(int)cq[pl][1] << 16),
+                               (uint32_t)(int)cq[pl][2] | ((uint32_t)(int)cq[pl][3] << 16));
+            else
+                *reinterpret_cast<uint32_t *>(crow) = (uint32_t)(int)cq[pl][0] | ((uint32_t)(int)cq[pl][1] << 8) |
+                                                      ((uint32_t)(int)cq[pl][2] << 16) | ((uint32_t)(int)cq[pl][3] << 24);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (i0 + e < Wc) crow[e] = (S)(int)cq[pl][e];
+        }
     }
 }
 
@@ -335,6 +488,89 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a) {
     if (a.amax) atomicMax(a.amax, __float_as_uint(amax));
 }
 
+// 16 bytes of UPC consecutive channels, converted from float.
+template <typename T>
+__device__ __forceinline__ uint4 pack_unit(const float *v);
+template <>
+__device__ __forceinline__ uint4 pack_unit<float>(const float *v) {
+    return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+}
+template <>
+__device__ __forceinline__ uint4 pack_unit<__nv_bfloat16>(const float *v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+        w[k] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+template <>
+__device__ __forceinline__ uint4 pack_unit<__half>(const float *v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const __half2 h = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+        w[k] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+template <>
+__device__ __forceinline__ uint4 pack_unit<__nv_fp8_e4m3>(const float *v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t b = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) b |= (uint32_t)__nv_fp8_e4m3(v[4 * k + e]).__x << (8 * e);
+        w[k] = b;
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Row-tiled pack: one thread per 4 consecutive pixels of a row and all padded
+// channels.  Each source channel row segment is one 16-byte load; each
+// destination unit of the 4 pixels is one 16-byte store, contiguous across the
+// 4 pixels (and across the warp) for every unit index.  Needs W % 4 == 0 and
+// 16-byte aligned source rows; otherwise the per-unit kernel above runs.
+template <typename T>
+__global__ void __launch_bounds__(128) pack_rows_kernel(const __grid_constant__ PackArgs a) {
+    constexpr int UPC = 16 / sizeof(T);
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int y = blockIdx.y;
+    if (x0 >= a.W) return;
+    const int64_t HW = (int64_t)a.H * a.W;
+    const int upch = a.cpc / UPC;
+    const int creal = a.nsrc * a.ch_per_src;
+    const int64_t p0 = (int64_t)y * a.W + x0;
+    float amax = 0.f;
+    for (int u = 0; u < a.cpad / UPC; ++u) {  // unit index over all channels
+        float v[4][UPC];
+#pragma unroll
+        for (int e = 0; e < UPC; ++e) {
+            const int ch = u * UPC + e;
+            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ch < creal) {
+                const int s = ch / a.ch_per_src, cc = ch - s * a.ch_per_src;
+                f = __ldg(reinterpret_cast<const float4 *>(a.src[s] + cc * a.src_plane + (int64_t)y * a.src_pitch + x0));
+            }
+            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(f.x), fabsf(f.y)), fmaxf(fabsf(f.z), fabsf(f.w))));
+            v[0][e] = f.x * a.scale;
+            v[1][e] = f.y * a.scale;
+            v[2][e] = f.z * a.scale;
+            v[3][e] = f.w * a.scale;
+        }
+        const int c = u / upch, vv = u - c * upch;
+        uint8_t *d = reinterpret_cast<uint8_t *>(a.dst) + (((int64_t)c * HW + p0) * upch + vv) * 16;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) *reinterpret_cast<uint4 *>(d + (int64_t)k * upch * 16) = pack_unit<T>(v[k]);
+    }
+    if (a.amax) {
+        const unsigned m = __reduce_max_sync(__activemask(), __float_as_uint(amax));
+        if ((threadIdx.x & 31) == (__ffs(__activemask()) - 1)) atomicMax(a.amax, m);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__ src, int cpad, int cpc, int C,
                                                      int H, int W, float scale, float *dst, int64_t pitch) {
@@ -362,6 +598,19 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
 cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, const void *u, int64_t pu,
                           const void *v, int64_t pv, float *out, int64_t out_pitch, cudaStream_t st) {
     const RangeConst rc = range_const(f.bit_depth, f.range);
+    if (f.subsampling == NVISR_SUB_420) {
+        dim3 blk(128);
+        dim3 grd((f.width + 8 * 128 - 1) / (8 * 128), (f.height + 1) / 2);
+        if (f.bit_depth <= 8)
+            ingest420_kernel<uint8_t><<<grd, blk, 0, st>>>((const uint8_t *)y, py, (const uint8_t *)u, pu,
+                                                          (const uint8_t *)v, pv, f.height, f.width, f.chroma_loc,
+                                                          rc, out, out_pitch);
+        else
+            ingest420_kernel<uint16_t><<<grd, blk, 0, st>>>((const uint8_t *)y, py, (const uint8_t *)u, pu,
+                                                           (const uint8_t *)v, pv, f.height, f.width, f.chroma_loc,
+                                                           rc, out, out_pitch);
+        return cudaGetLastError();
+    }
     dim3 block(64);
     dim3 grid((f.width / 4 + 1 + block.x - 1) / block.x, f.height);
     const int sub = f.subsampling == NVISR_SUB_420;
@@ -383,7 +632,8 @@ cudaError_t launch_requant(const nvisr_format &f, const float *in, int64_t in_pi
     if (skip) sk = *skip;
     dim3 block(64);
     if (f.subsampling == NVISR_SUB_420) {
-        dim3 grid((f.width / 8 + 1 + block.x - 1) / block.x, f.height / 2);
+        block = dim3(128);
+        dim3 grid((f.width + 8 * 128 - 1) / (8 * 128), f.height / 2);
         const bool skip2 = sk.n == 1 && sk.mode == 2 && sk.scale == 2 && sk.h * 2 == f.height && sk.w * 2 == f.width;
 #define NVISR_RQ(S_, K_)                                                                                     \
     requant420_kernel<S_, K_><<<grid, block, 0, st>>>(in, in_pitch, f.height, f.width, f.chroma_loc, rc,  \
@@ -415,6 +665,18 @@ cudaError_t launch_pack(const PackArgs &a0, cudaStream_t st) {
     const int upc = chunk_channels(a.dt);
     if (a.cpc == 0) a.cpc = upc;
     if (a.cpc % upc || a.cpad % a.cpc) return cudaErrorInvalidValue;
+    bool rows = a.W % 4 == 0 && a.src_pitch % 4 == 0 && a.src_plane % 4 == 0;
+    for (int s = 0; s < a.nsrc; ++s) rows = rows && (reinterpret_cast<uintptr_t>(a.src[s]) & 15) == 0;
+    if (rows) {
+        dim3 blk(128), grd((a.W / 4 + 127) / 128, a.H);
+        switch (a.dt) {
+            case DT_F32: pack_rows_kernel<float><<<grd, blk, 0, st>>>(a); break;
+            case DT_BF16: pack_rows_kernel<__nv_bfloat16><<<grd, blk, 0, st>>>(a); break;
+            case DT_F16: pack_rows_kernel<__half><<<grd, blk, 0, st>>>(a); break;
+            default: pack_rows_kernel<__nv_fp8_e4m3><<<grd, blk, 0, st>>>(a); break;
+        }
+        return cudaGetLastError();
+    }
     const int64_t n = (int64_t)a.H * a.W * (a.cpad / upc);
     const int block = 256;
     const int64_t grid = (n + block - 1) / block;
