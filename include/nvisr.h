@@ -243,6 +243,40 @@ nvisr_status nvisr_group_runs(int32_t s0, int32_t s1, int32_t n, int32_t extra, 
 nvisr_status nvisr_fig1_layout(int32_t n, int32_t b, int32_t *cell_frame, int32_t *slot_start,
                                int32_t *copy);
 
+/* ----------------------------------------------------------------------------
+ * Batched multi-stream stepping.
+ *
+ * A batch groups filters of one engine.  Each nvisr_batch_step computes the
+ * next output of every member whose output is ready (its input frames have
+ * been pushed, its previous output pulled); outputs are then pulled per
+ * filter with nvisr_pull.  When the members run the same tuple network (equal
+ * description text, weight blob and BF16/FP16 precision) the step shares its
+ * launches across them, whatever their frame sizes and pixel formats:
+ *  - the tuple packs of all participants run as one launch;
+ *  - every 64->64 3x3 layer runs as one row-streaming launch over all
+ *    participants' images (a table of per-image tensor maps and strips);
+ *    the other layers run per participant;
+ *  - the launch sequence of a set of participants is captured once as a CUDA
+ *    graph and replayed on later steps with the same set;
+ *  - the strip height of the shared launches is chosen per set by timing
+ *    candidate heights on the set's first step (autotuner).
+ * Other batches (mixed networks, FP32, FP8, group networks) step their
+ * members one by one.  Ingest (push) and requantise (pull) stay per filter.
+ * Destroy the batch before its filters.  Calls on one batch are not thread
+ * safe.  Errors: INVALID_ARG (NULL, filters of another engine, duplicates),
+ * CUDA_ERROR, INTERNAL (a member's tuple layout the batched pack cannot take).
+ * ------------------------------------------------------------------------- */
+typedef struct nvisr_batch nvisr_batch;
+nvisr_status nvisr_batch_create(nvisr_engine *engine, nvisr_filter *const *filters, int32_t n,
+                                nvisr_batch **out);
+/* *produced (may be NULL) receives the number of outputs computed. */
+nvisr_status nvisr_batch_step(nvisr_batch *batch, int32_t *produced);
+/* Introspection: *shared = 1 when launches are shared, *graphs = CUDA graphs
+ * captured so far, *rows_per_strip = the autotuned strip height of the most
+ * recent participant set (0 before the first shared step).  Any may be NULL. */
+nvisr_status nvisr_batch_info(nvisr_batch *batch, int32_t *shared, int32_t *graphs, int32_t *rows_per_strip);
+void nvisr_batch_destroy(nvisr_batch *batch);
+
 /* One 2-D convolution layer (Section 3.1 networks) on planar float32 tensors:
  * y[cout][H][W] = act(conv_k(x[cin][H][W]; w[cout][cin][k][k]) + b) (+ res),
  * stride 1, zero padding (k-1)/2, act 0 = none, 1 = LeakyReLU(0.1).  Runs the

@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "Engine", "Filter", "NvisrError", "PREC", "Status", "fmt", "lib", "load",
+    "Batch", "Engine", "Filter", "NvisrError", "PREC", "Status", "fmt", "lib", "load",
     "nvisr_conv2d", "nvisr_conv2d_static", "nvisr_dcn2d", "nvisr_fig1_layout", "nvisr_group_runs",
     "nvisr_ingest", "nvisr_network_check", "nvisr_requant", "nvisr_selftest",
     "nvisr_tuple_map",
@@ -110,6 +110,10 @@ _SIGS = {
     "nvisr_dcn2d": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP, _VP, _I32, _VP, _VP]),
     "nvisr_selftest": (_I32, [_I32P, _I32P]),
     "nvisr_selftest_swizzle": (_I32, [_I32P]),
+    "nvisr_batch_create": (_I32, [_VP, ctypes.POINTER(_VP), _I32, ctypes.POINTER(_VP)]),
+    "nvisr_batch_step": (_I32, [_VP, _I32P]),
+    "nvisr_batch_info": (_I32, [_VP, _I32P, _I32P, _I32P]),
+    "nvisr_batch_destroy": (None, [_VP]),
     "nvisr_abi_version": (_I32, []),
     "nvisr_build_info": (ctypes.c_char_p, []),
 }
@@ -313,13 +317,56 @@ class Engine:
     def filter(self, net_text, blob, in_fmt, out_fmt, precision="fp32", scale=2, calib_frames=0):
         return Filter(self, net_text, blob, in_fmt, out_fmt, precision, scale, calib_frames)
 
+    def batch(self, filters):
+        return Batch(self, filters)
+
     def close(self):
         if self.h:
+            for b in list(getattr(self, "batches", [])):
+                b.close()
             for f in self.filters:
                 f.h = None
             self.filters = []
             _LIB.nvisr_engine_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched multi-stream stepping over filters of one engine (shared launches + CUDA graphs)."""
+
+    def __init__(self, engine, filters):
+        self.engine = engine
+        self.filters = list(filters)
+        arr = (_VP * len(self.filters))(*[f.h for f in self.filters])
+        h = ctypes.c_void_p()
+        _check(_LIB.nvisr_batch_create(engine.h, arr, len(self.filters), ctypes.byref(h)), "nvisr_batch_create")
+        self.h = h
+        if not hasattr(engine, "batches"):
+            engine.batches = []
+        engine.batches.append(self)
+
+    def step(self):
+        n = ctypes.c_int32(0)
+        _check(_LIB.nvisr_batch_step(self.h, ctypes.byref(n)), "nvisr_batch_step")
+        return n.value
+
+    def info(self):
+        s, g, r = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(_LIB.nvisr_batch_info(self.h, ctypes.byref(s), ctypes.byref(g), ctypes.byref(r)), "nvisr_batch_info")
+        return {"shared": bool(s.value), "graphs": g.value, "rows_per_strip": r.value}
+
+    def close(self):
+        if self.h:
+            _LIB.nvisr_batch_destroy(self.h)
+            self.h = None
+            if self in getattr(self.engine, "batches", []):
+                self.engine.batches.remove(self)
 
     def __del__(self):
         try:
@@ -380,6 +427,9 @@ class Filter:
 
     def close(self):
         if self.h:
+            for b in list(getattr(self.engine, "batches", [])):
+                if self in b.filters:
+                    b.close()
             _LIB.nvisr_filter_destroy(self.h)
             self.h = None
             if self in self.engine.filters:

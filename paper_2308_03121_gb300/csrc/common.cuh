@@ -1,6 +1,7 @@
 // Shared definitions of the CUDA path (internal; not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -84,6 +85,10 @@ struct PackArgs {
     unsigned *amax;
 };
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t st);
+// Batched pack: n packs whose arguments (cpc set explicitly, same dtype) are in
+// host_tab (for the grid) and, identically, in the device table dev_tab.
+bool pack_rows_fits(const PackArgs &a);
+cudaError_t launch_pack_table(const PackArgs *host_tab, const PackArgs *dev_tab, int n, cudaStream_t st);
 
 // blocked tensor (cpc channels per chunk) -> planar float32 [C][H][W]
 // (first C channels; value*scale).
@@ -125,6 +130,22 @@ struct ConvArgs {
 };
 cudaError_t launch_conv_simt(const ConvArgs &a, cudaStream_t st);
 cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st);
+
+// One image of a batched 64 -> 64 3x3 row-streaming launch: its tensor maps (in
+// global memory, 64-byte aligned) and its strips [strip0, strip0 + nstrips).
+struct alignas(64) RowProblem {
+    CUtensorMap tmap, ymap, rmap;
+    int H, W, xtiles, rps, strip0, nstrips, has_res, pad_;
+};
+// True when launch_conv_rows_multi takes layers of this shape.
+bool rows_kernel_fits(const ConvArgs &a);
+// One launch over n problems (same weights, bias, activation and dtypes; each
+// its own x / y / res and size).  host_tab and dev_tab hold n RowProblem
+// entries; the table is written to host_tab, copied to dev_tab on `st`, and
+// must stay unchanged until the launch has run (a captured graph reuses it).
+// rps = rows per strip (0 = automatic).  launch = false only fills (and copies) the table.
+cudaError_t launch_conv_rows_multi(const ConvArgs *args, int n, RowProblem *host_tab, RowProblem *dev_tab, int rps,
+                                   cudaStream_t st, bool copy_table = true, bool launch = true);
 
 // Weight preparation (device buffers allocated by the caller).
 // SIMT layout: [cin_pad][k*k][cout_pad] float32.

@@ -543,11 +543,12 @@ struct RowPlan {
     int rps;      // rows per band
 };
 
-template <int IN_DT, int OUT_DT, int CBO>
+template <int IN_DT, int OUT_DT, int CBO, bool MULTI>
 __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 const __grid_constant__ CUtensorMap ymap,
                                                                 const __grid_constant__ CUtensorMap rmap,
-                                                                const TcParams p, const RowPlan rp) {
+                                                                const TcParams p, const RowPlan rp,
+                                                                const RowProblem *__restrict__ probs, int nprob) {
     using TO = typename Elem<OUT_DT>::T;
     constexpr int AFMT = IN_DT == DT_BF16 ? 1 : 0;
     constexpr int PXS = TM + 2;
@@ -586,11 +587,26 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     uint8_t *rbuf = obuf + 2 * TILEB;            // residual tile per group
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // MULTI: the strips of several images of different sizes (one per problem,
+    // each with its own tensor maps in global memory) share the launch
     const int strips_per_img = rp.xtiles * rp.bands;
-    const int nstrips = strips_per_img * p.nimg;
-    const bool has_res = p.res != nullptr;
+    const int nstrips = MULTI ? probs[nprob - 1].strip0 + probs[nprob - 1].nstrips : strips_per_img * p.nimg;
+    const bool has_res = MULTI ? probs[0].has_res != 0 : p.res != nullptr;
     const bool plain = p.acc_scale == 1.f && p.out_scale == 1.f && p.res_scale == 1.f && !p.amax && !p.y2;
-    auto strip_of = [&](int sidx, int &img, int &x0, int &ra, int &rb) {
+    auto strip_of = [&](int sidx, int &img, int &x0, int &ra, int &rb, int &pi) {
+        if (MULTI) {
+            pi = 0;
+            while (pi + 1 < nprob && sidx >= probs[pi + 1].strip0) ++pi;
+            const RowProblem &q = probs[pi];
+            const int local = sidx - q.strip0;
+            const int band = local / q.xtiles;
+            img = 0;
+            x0 = (local - band * q.xtiles) * TM;
+            ra = band * q.rps;
+            rb = min(q.H, ra + q.rps);
+            return;
+        }
+        pi = 0;
         img = sidx / strips_per_img;
         const int rem = sidx - img * strips_per_img;
         const int band = rem / rp.xtiles;
@@ -598,6 +614,10 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
         ra = band * rp.rps;
         rb = min(p.H, ra + rp.rps);
     };
+    auto tmap_of = [&](int pi) { return MULTI ? &probs[pi].tmap : &tmap; };
+    auto ymap_of = [&](int pi) { return MULTI ? &probs[pi].ymap : &ymap; };
+    auto rmap_of = [&](int pi) { return MULTI ? &probs[pi].rmap : &rmap; };
+    auto width_of = [&](int pi) { return MULTI ? probs[pi].W : p.W; };
     if (threadIdx.x >= 64 && threadIdx.x < 128) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -635,8 +655,8 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
             int gin = 0;
             bool ok = true;
             for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
-                int img, x0, ra, rb;
-                strip_of(sidx, img, x0, ra, rb);
+                int img, x0, ra, rb, pi;
+                strip_of(sidx, img, x0, ra, rb, pi);
                 for (int r = ra - 1; r <= rb; ++r, ++gin) {
                     const int s = gin % S;
                     if (!mbar_wait_bounded(&empty[s], ((gin / S) & 1) ^ 1, abort, WAIT_NS)) {
@@ -645,7 +665,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         break;
                     }
                     mbar_arrive_expect_tx(&full[s], PXS * 128);
-                    tma_load_4d(stage0 + (size_t)s * ROWB, &tmap, &full[s], 0, x0 - 1, r, img);
+                    tma_load_4d(stage0 + (size_t)s * ROWB, tmap_of(pi), &full[s], 0, x0 - 1, r, img);
                 }
             }
             for (int k = 0; k < S && k < gin; ++k) {
@@ -684,8 +704,8 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                 return true;
             };
             for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
-                int img, x0, ra, rb;
-                strip_of(sidx, img, x0, ra, rb);
+                int img, x0, ra, rb, pi;
+                strip_of(sidx, img, x0, ra, rb, pi);
                 const int base = gout - ra;  // global index of this strip's output row o is base + o
                 for (int r = ra - 1; r <= rb && ok; ++r, ++gin) {
                     const int o_lo = max(r - 1, ra), o_hi = min(r + 1, rb - 1);
@@ -766,8 +786,8 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
             uint32_t ph = 0;
             bool ok = true;
             for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
-                int img, x0, ra, rb;
-                strip_of(sidx, img, x0, ra, rb);
+                int img, x0, ra, rb, pi;
+                strip_of(sidx, img, x0, ra, rb, pi);
                 const int base = gout - ra;
                 for (int r = ra - 1; r <= rb; ++r) {
                     if (r + 1 <= rb - 1) {
@@ -811,15 +831,15 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
         int last_res = -1;
         bool ok = true;
         for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
-            int img, x0, ra, rb;
-            strip_of(sidx, img, x0, ra, rb);
+            int img, x0, ra, rb, pi;
+            strip_of(sidx, img, x0, ra, rb, pi);
             const int x = x0 + m;
-            const bool valid = x < p.W;
+            const bool valid = x < width_of(pi);
             // this group's rows of the strip: global index i = gout + (o - ra) with i % 2 == g
             int o = ra + ((g - (gout & 1)) & 1);
             if (leader && has_res && o < rb) {
                 mbar_arrive_expect_tx(&resfull[g], TILEB);
-                tma_load_4d(rbuf + g * TILEB, &rmap, &resfull[g], 0, x0, o, img);
+                tma_load_4d(rbuf + g * TILEB, rmap_of(pi), &resfull[g], 0, x0, o, img);
                 last_res = res_loads++;
             }
             for (; o < rb; o += 2) {
@@ -946,11 +966,11 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                     break;
                 }
                 if (leader) {
-                    tma_store_4d(&ymap, obuf + g * TILEB, 0, x0, o, img);
+                    tma_store_4d(ymap_of(pi), obuf + g * TILEB, 0, x0, o, img);
                     bulk_commit_group();
                     if (has_res && o + 2 < rb) {  // this group's next row; the buffer's readers are done
                         mbar_arrive_expect_tx(&resfull[g], TILEB);
-                        tma_load_4d(rbuf + g * TILEB, &rmap, &resfull[g], 0, x0, o + 2, img);
+                        tma_load_4d(rbuf + g * TILEB, rmap_of(pi), &resfull[g], 0, x0, o + 2, img);
                         last_res = res_loads++;
                     }
                 }
@@ -1159,7 +1179,7 @@ cudaError_t run(const CUtensorMap &map, TcParams p, cudaStream_t st) {
     int smem = 1024 + SMEM_HDR + (int)wround + stages * (int)STAGE_BYTES;
     if (smem < 118 * 1024) smem = 118 * 1024;
     auto kern = conv_tc_kernel<IN_DT, OUT_DT, NS, KS, NCH, EPI, CBI, CBO>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = set_smem_limit<conv_tc_kernel<IN_DT, OUT_DT, NS, KS, NCH, EPI, CBI, CBO>>(smem);
     if (e != cudaSuccess) return e;
     const int tiles = ((p.W + TM - 1) / TM) * p.H * p.nimg;
     int sms = device_sm_count();
@@ -1269,21 +1289,27 @@ void prepare_weights_rows(const float *w, int dt, void *dst) {
 
 namespace {
 
+// Shared memory of the row kernel: 72 KB weights, the input-row ring, 2 output
+// staging tiles and, when the layer adds a residual, 2 residual tiles (without
+// one, their room goes to deeper input prefetch).
+inline int rows_stages(bool res, int *smem) {
+    constexpr uint32_t ROWB = ((TM + 2) * 128 + 1023u) & ~1023u;
+    constexpr uint32_t WB = 3 * 3 * 64 * 128;
+    const uint32_t TILES = (res ? 4u : 2u) * TM * 128;
+    int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES) / (int)ROWB;
+    if (stages > 8) stages = 8;
+    *smem = 1024 + SMEM_HDR + (int)WB + stages * (int)ROWB + (int)TILES;
+    return stages;
+}
+
 template <int IN_DT, int OUT_DT, int CBO>
 cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUtensorMap &rmap, TcParams p,
                      cudaStream_t st) {
-    constexpr uint32_t ROWB = ((TM + 2) * 128 + 1023u) & ~1023u;
-    constexpr uint32_t WB = 3 * 3 * 64 * 128;
-    // 2 output staging tiles, + 2 residual tiles when the layer adds a residual
-    // (without one, their room goes to deeper input prefetch)
-    const uint32_t TILES = (p.res ? 4u : 2u) * TM * 128;
-    int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES) / (int)ROWB;
-    if (stages > 8) stages = 8;
-    if (stages < 2) return cudaErrorInvalidConfiguration;
-    p.stages = stages;
-    const int smem = 1024 + SMEM_HDR + (int)WB + stages * (int)ROWB + (int)TILES;
-    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int smem;
+    p.stages = rows_stages(p.res != nullptr, &smem);
+    if (p.stages < 2) return cudaErrorInvalidConfiguration;
+    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, false>;
+    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, false>>(smem);
     if (e != cudaSuccess) return e;
     RowPlan rp;
     rp.xtiles = (p.W + TM - 1) / TM;
@@ -1295,47 +1321,117 @@ cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUte
     rp.bands = (p.H + rp.rps - 1) / rp.rps;
     int grid = rp.xtiles * rp.bands * p.nimg;
     if (grid > sms) grid = sms;
-    kern<<<grid, ROWS_THREADS, smem, st>>>(map, ymap, rmap, p, rp);
+    kern<<<grid, ROWS_THREADS, smem, st>>>(map, ymap, rmap, p, rp, nullptr, 0);
     return cudaGetLastError();
+}
+
+template <int IN_DT, int OUT_DT, int CBO>
+cudaError_t run_rows_multi(const CUtensorMap &dummy, TcParams p, const RowProblem *dev_tab, int n, int total,
+                           cudaStream_t st) {
+    int smem;
+    p.stages = rows_stages(p.res != nullptr, &smem);
+    if (p.stages < 2) return cudaErrorInvalidConfiguration;
+    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, true>;
+    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, true>>(smem);
+    if (e != cudaSuccess) return e;
+    RowPlan rp{};
+    const int grid = std::min(total, device_sm_count());
+    kern<<<grid, ROWS_THREADS, smem, st>>>(dummy, dummy, dummy, p, rp, dev_tab, n);
+    return cudaGetLastError();
+}
+
+// The row kernel's three tensor maps for one image set (x: 130-pixel row boxes
+// with OOB zero fill; y and residual: 128-pixel row tiles).
+cudaError_t encode_row_maps(const ConvArgs &a, CUtensorMap *map, CUtensorMap *ymap, CUtensorMap *rmap) {
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    cuuint64_t dims[4] = {128, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.nimg};
+    cuuint64_t strides[3] = {128, (cuuint64_t)a.W * 128, (cuuint64_t)a.W * a.H * 128};
+    cuuint32_t box[4] = {128, (cuuint32_t)(TM + 2), 1, 1};
+    cuuint32_t tbox[4] = {128, (cuuint32_t)TM, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.x), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    r = enc(ymap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, a.y, dims, strides, tbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    r = enc(rmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.res ? a.res : a.y), dims, strides, tbox,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+TcParams rows_params(const ConvArgs &a) {
+    TcParams p{};
+    p.H = a.H; p.W = a.W; p.nimg = a.nimg; p.cin_chunks = 1;
+    p.cout = 64; p.cout_pad = 64; p.ns = 64; p.nslice = 1;
+    p.wts = static_cast<const uint8_t *>(a.w_rows);
+    p.wbytes = (uint32_t)tc_rows_weight_bytes();
+    p.bias = a.bias; p.act = a.act;
+    p.res = static_cast<const uint8_t *>(a.res);
+    p.y = static_cast<uint8_t *>(a.y);
+    p.acc_scale = a.acc_scale; p.out_scale = a.out_scale; p.res_scale = 1.0f / a.out_scale;
+    p.y2 = static_cast<uint8_t *>(a.y2); p.y2_scale = a.y2_scale; p.amax = a.amax;
+    p.err = a.err;
+    return p;
 }
 
 }  // namespace
 
+bool rows_kernel_fits(const ConvArgs &a) {
+    const int dt = a.in_dt;
+    return a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.out_dt == dt && a.cin_pad == 64 &&
+           a.cout_pad == 64 && a.cout == 64 && a.in_cpc == 64 && a.out_cpc == 64 && a.ps == 0;
+}
+
+cudaError_t launch_conv_rows_multi(const ConvArgs *args, int n, RowProblem *host_tab, RowProblem *dev_tab, int rps,
+                                   cudaStream_t st, bool copy_table, bool launch) {
+    if (n < 1) return cudaSuccess;
+    const ConvArgs &a0 = args[0];
+    for (int i = 0; i < n; ++i) {
+        const ConvArgs &a = args[i];
+        if (!rows_kernel_fits(a) || a.in_dt != a0.in_dt || a.w_rows != a0.w_rows || a.bias != a0.bias ||
+            a.act != a0.act || (a.res != nullptr) != (a0.res != nullptr) || a.y2 || a.amax || a.acc_scale != 1.f ||
+            a.out_scale != 1.f || a.nimg != 1)
+            return cudaErrorInvalidValue;
+    }
+    int total = 0;
+    for (int i = 0; i < n; ++i) {
+        const ConvArgs &a = args[i];
+        RowProblem &q = host_tab[i];
+        cudaError_t e = encode_row_maps(a, &q.tmap, &q.ymap, &q.rmap);
+        if (e != cudaSuccess) return e;
+        q.H = a.H;
+        q.W = a.W;
+        q.xtiles = (a.W + TM - 1) / TM;
+        q.rps = rps > 0 ? std::min(rps, a.H) : std::max(1, std::min(a.H, 64));
+        q.strip0 = total;
+        q.nstrips = q.xtiles * ((a.H + q.rps - 1) / q.rps);
+        q.has_res = a.res != nullptr;
+        q.pad_ = 0;
+        total += q.nstrips;
+    }
+    if (copy_table) {
+        cudaError_t e = cudaMemcpyAsync(dev_tab, host_tab, sizeof(RowProblem) * n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (!launch) return cudaSuccess;
+    TcParams p = rows_params(a0);
+    return a0.in_dt == DT_BF16 ? run_rows_multi<DT_BF16, DT_BF16, 128>(host_tab[0].tmap, p, dev_tab, n, total, st)
+                               : run_rows_multi<DT_F16, DT_F16, 128>(host_tab[0].tmap, p, dev_tab, n, total, st);
+}
+
 cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
     const int dt = a.in_dt;
     // 64 -> 64 3x3 layers with 64-channel 16-bit input and output: row-streaming kernel
-    if (a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.out_dt == dt && a.cin_pad == 64 &&
-        a.cout_pad == 64 && a.cout == 64 && a.in_cpc == 64 && a.out_cpc == 64 && a.ps == 0) {
-        auto enc = encode_fn();
-        if (!enc) return cudaErrorNotSupported;
+    if (rows_kernel_fits(a)) {
         CUtensorMap map, ymap, rmap;
-        cuuint64_t dims[4] = {128, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.nimg};
-        cuuint64_t strides[3] = {128, (cuuint64_t)a.W * 128, (cuuint64_t)a.W * a.H * 128};
-        cuuint32_t box[4] = {128, (cuuint32_t)(TM + 2), 1, 1};
-        cuuint32_t tbox[4] = {128, (cuuint32_t)TM, 1, 1};
-        cuuint32_t estr[4] = {1, 1, 1, 1};
-        CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.x), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        r = enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, a.y, dims, strides, tbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        r = enc(&rmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.res ? a.res : a.y), dims, strides, tbox,
-                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        TcParams p{};
-        p.H = a.H; p.W = a.W; p.nimg = a.nimg; p.cin_chunks = 1;
-        p.cout = 64; p.cout_pad = 64; p.ns = 64; p.nslice = 1;
-        p.wts = static_cast<const uint8_t *>(a.w_rows);
-        p.wbytes = (uint32_t)tc_rows_weight_bytes();
-        p.bias = a.bias; p.act = a.act;
-        p.res = static_cast<const uint8_t *>(a.res);
-        p.y = static_cast<uint8_t *>(a.y);
-        p.acc_scale = a.acc_scale; p.out_scale = a.out_scale; p.res_scale = 1.0f / a.out_scale;
-        p.y2 = static_cast<uint8_t *>(a.y2); p.y2_scale = a.y2_scale; p.amax = a.amax;
-        p.err = a.err;
+        cudaError_t e = encode_row_maps(a, &map, &ymap, &rmap);
+        if (e != cudaSuccess) return e;
+        const TcParams p = rows_params(a);
         return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128>(map, ymap, rmap, p, st)
                              : run_rows<DT_F16, DT_F16, 128>(map, ymap, rmap, p, st);
     }

@@ -170,6 +170,9 @@ int plane_rows(const nvisr_format &f, int plane) {
 struct nvisr_filter {
     nvisr_engine *eng = nullptr;
     NetDesc net;
+    std::string net_text;          // the description and a hash of the weight blob: filters with
+    uint64_t blob_hash = 0;        // equal text, blob and precision may share batched launches
+    int64_t blob_count = 0;
     nvisr_format in_fmt{}, out_fmt{};
     int precision = NVISR_PREC_FP32;
     int act_dt = DT_F32;  // 16-bit / FP32 activation dtype
@@ -775,26 +778,26 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
 }
 
 // Runs one conv step.  calib: 16-bit pass recording amax of FP8-consumed tensors.
-nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames, bool calib) {
+// Skip path of a final output: the frames whose upsampled mean requantise adds.
+void set_final_skip(nvisr_filter *f, const Step &s, const float *const *frames) {
+    SkipArgs &k = f->skip[s.out_index];
+    k = SkipArgs{};
+    k.n = f->net.skip ? std::min<int>((int)s.skip_frames.size(), 2) : 0;
+    for (int i = 0; i < k.n; ++i) k.src[i] = frames[s.skip_frames[i]];
+    k.pitch = f->rpitch;
+    k.plane = f->rpitch * f->in_fmt.height;
+    k.h = f->in_fmt.height;
+    k.w = f->in_fmt.width;
+    k.scale = f->net.scale;
+    k.mode = f->net.skip;
+}
+
+// Arguments of a conv step (no launch).  For the final layer it also sets the
+// filter's skip arguments (the frames whose upsampled mean requantise adds).
+ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, bool calib, int *kind) {
     const NetLayer &L = f->net.layers[s.layer];
     const Weights &Wt = s.widx >= 0 ? f->wvar[s.widx] : f->weights[s.layer];
     const Tensor &in = f->tensors[s.in_t];
-    cudaStream_t st = f->eng->stream;
-    if (s.op == OP_DCN) {
-        const Tensor &om = f->tensors[s.om_t];
-        const Tensor &o = f->tensors[s.out_t];
-        DcnArgs d{};
-        d.x = in.ptr; d.cin_pad = in.cpad; d.H = in.H; d.W = in.W; d.groups = L.groups;
-        d.x_cpc = in.cpc; d.y_cpc = o.cpc;
-        d.om = (const float *)om.ptr; d.om_cpad = om.cpad; d.mask_logits = 1;
-        d.w = Wt.simt_or_tc; d.bias = Wt.bias; d.cout = L.cout; d.cout_pad = Wt.cout_pad;
-        d.y = o.ptr; d.in_dt = in.dt; d.out_dt = o.dt; d.acc_scale = 1.f; d.out_scale = 1.f;
-        d.err = f->eng->err_word;
-        ProfScope ps(f, NVISR_K_DCN);
-        cudaError_t e = f->tc ? launch_dcn_tc(d, st) : launch_dcn_simt(d, st);
-        if (e != cudaSuccess) return cuda_status(e, ("dcn layer " + L.name).c_str());
-        return NVISR_OK;
-    }
     ConvArgs a{};
     a.cin_pad = in.cpad;
     a.in_cpc = in.cpc;
@@ -853,21 +856,37 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
         a.ps_pitch = f->opitch;
         a.skip_mode = 0;
         a.nskip = 0;
-        SkipArgs &k = f->skip[s.out_index];
-        k = SkipArgs{};
-        k.n = f->net.skip ? std::min<int>((int)s.skip_frames.size(), 2) : 0;
-        for (int i = 0; i < k.n; ++i) k.src[i] = frames[s.skip_frames[i]];
-        k.pitch = f->rpitch;
-        k.plane = f->rpitch * f->in_fmt.height;
-        k.h = f->in_fmt.height;
-        k.w = f->in_fmt.width;
-        k.scale = f->net.scale;
-        k.mode = f->net.skip;
+        set_final_skip(f, s, frames);
     }
-    const int kind = s.out_t < 0 ? NVISR_K_CONV_TAIL
-                     : (s.src == SRC_TUPLE ? NVISR_K_CONV_HEAD
-                                           : (L.cin == 64 && L.cout == 64 && L.k == 3 && !L.ps ? NVISR_K_CONV_BODY
-                                                                                                : NVISR_K_CONV_OTHER));
+    *kind = s.out_t < 0 ? NVISR_K_CONV_TAIL
+                        : (s.src == SRC_TUPLE ? NVISR_K_CONV_HEAD
+                                              : (L.cin == 64 && L.cout == 64 && L.k == 3 && !L.ps ? NVISR_K_CONV_BODY
+                                                                                                   : NVISR_K_CONV_OTHER));
+    return a;
+}
+
+nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames, bool calib) {
+    const NetLayer &L = f->net.layers[s.layer];
+    const Weights &Wt = s.widx >= 0 ? f->wvar[s.widx] : f->weights[s.layer];
+    const Tensor &in = f->tensors[s.in_t];
+    cudaStream_t st = f->eng->stream;
+    if (s.op == OP_DCN) {
+        const Tensor &om = f->tensors[s.om_t];
+        const Tensor &o = f->tensors[s.out_t];
+        DcnArgs d{};
+        d.x = in.ptr; d.cin_pad = in.cpad; d.H = in.H; d.W = in.W; d.groups = L.groups;
+        d.x_cpc = in.cpc; d.y_cpc = o.cpc;
+        d.om = (const float *)om.ptr; d.om_cpad = om.cpad; d.mask_logits = 1;
+        d.w = Wt.simt_or_tc; d.bias = Wt.bias; d.cout = L.cout; d.cout_pad = Wt.cout_pad;
+        d.y = o.ptr; d.in_dt = in.dt; d.out_dt = o.dt; d.acc_scale = 1.f; d.out_scale = 1.f;
+        d.err = f->eng->err_word;
+        ProfScope ps(f, NVISR_K_DCN);
+        cudaError_t e = f->tc ? launch_dcn_tc(d, st) : launch_dcn_simt(d, st);
+        if (e != cudaSuccess) return cuda_status(e, ("dcn layer " + L.name).c_str());
+        return NVISR_OK;
+    }
+    int kind = 0;
+    const ConvArgs a = conv_args(f, s, frames, calib, &kind);
     ProfScope ps(f, kind);
     cudaError_t e = f->tc ? launch_conv_tc(a, st) : launch_conv_simt(a, st);
     if (e != cudaSuccess) return cuda_status(e, ("conv layer " + L.name).c_str());
@@ -1007,6 +1026,158 @@ nvisr_status write_output(nvisr_filter *f, nvisr_planes *out, int slot) {
 
 }  // namespace
 
+// ==================================================================== batched stepping
+
+struct nvisr_batch {
+    nvisr_engine *eng = nullptr;
+    std::vector<nvisr_filter *> members;
+    bool shared = false;  // every member runs one tuple network on the tensor cores
+    struct Plan {
+        std::vector<int> parts;                       // participating members
+        PackArgs *pack_dev = nullptr;                 // per-step pack table (device)
+        std::vector<RowProblem *> tab_host, tab_dev;  // per step: shared-launch table, or null
+        int rps = 0;                                  // rows per strip chosen by the autotuner
+        cudaGraphExec_t exec = nullptr;
+        bool no_graph = false;                        // capture failed: launch directly
+        uint64_t last_use = 0;
+    };
+    std::vector<Plan> plans;
+    uint64_t tick = 0;
+    int graphs = 0;
+};
+
+namespace {
+
+constexpr int kMaxPlans = 4;
+
+void free_plan(nvisr_batch::Plan &p) {
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    if (p.pack_dev) cudaFree(p.pack_dev);
+    for (RowProblem *t : p.tab_host)
+        if (t) cudaFreeHost(t);
+    for (RowProblem *t : p.tab_dev)
+        if (t) cudaFree(t);
+    p = nvisr_batch::Plan{};
+}
+
+// Batched tuple members must share the weight blob; launches use member 0's weights.
+bool batchable(const nvisr_filter *f) {
+    return f->net.family == "tuple" && f->tc && f->precision != NVISR_PREC_FP8;
+}
+
+// Conv arguments of step si for a participant, with the (identical) weights of member 0.
+ConvArgs member_args(nvisr_batch *b, nvisr_filter *f, size_t si, const float *const *frames) {
+    int kind;
+    ConvArgs a = conv_args(f, f->steps[si], frames, false, &kind);
+    const nvisr_filter *f0 = b->members[0];
+    const Step &s0 = f0->steps[si];
+    const Weights &W0 = s0.widx >= 0 ? f0->wvar[s0.widx] : f0->weights[s0.layer];
+    a.w = W0.simt_or_tc;
+    a.w_rows = W0.rows;
+    a.bias = W0.bias;
+    return a;
+}
+
+struct PartFrames {
+    std::vector<std::vector<const float *>> frames;  // per participant: the tuple's ring slots
+};
+
+// Enqueues one batched forward: the packs, then per layer one shared launch
+// (row kernel over every participant's image) or per-participant launches.
+nvisr_status enqueue_forward(nvisr_batch *b, nvisr_batch::Plan &P, const std::vector<PackArgs> &pack_host,
+                             const PartFrames &pf, cudaStream_t st) {
+    const int n = (int)P.parts.size();
+    cudaError_t e = launch_pack_table(pack_host.data(), P.pack_dev, n, st);
+    if (e != cudaSuccess) return cuda_status(e, "batched pack");
+    std::vector<ConvArgs> args(n);
+    const size_t nsteps = b->members[0]->steps.size();
+    for (size_t si = 0; si < nsteps; ++si) {
+        for (int i = 0; i < n; ++i) args[i] = member_args(b, b->members[P.parts[i]], si, pf.frames[i].data());
+        if (P.tab_host[si]) {
+            e = launch_conv_rows_multi(args.data(), n, P.tab_host[si], P.tab_dev[si], P.rps, st, false, true);
+            if (e != cudaSuccess) return cuda_status(e, "batched conv");
+            continue;
+        }
+        for (int i = 0; i < n; ++i) {
+            e = launch_conv_tc(args[i], st);
+            if (e != cudaSuccess) return cuda_status(e, "batched conv (per member)");
+        }
+    }
+    return NVISR_OK;
+}
+
+// Autotuner: rows per strip of the shared 64 -> 64 launches, chosen by timing
+// candidate heights on one layer of this participant set (the layer is
+// recomputed in place; its output is rewritten by the real forward).
+int tune_rps(nvisr_batch *b, nvisr_batch::Plan &P, const PartFrames &pf, cudaStream_t st) {
+    const int n = (int)P.parts.size();
+    size_t probe = SIZE_MAX;
+    int maxh = 0;
+    for (size_t si = 0; si < P.tab_host.size(); ++si)
+        if (P.tab_host[si] && probe == SIZE_MAX) probe = si;
+    if (probe == SIZE_MAX) return 64;
+    std::vector<ConvArgs> args(n);
+    for (int i = 0; i < n; ++i) {
+        args[i] = member_args(b, b->members[P.parts[i]], probe, pf.frames[i].data());
+        maxh = std::max(maxh, args[i].H);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 64;
+    float best_ms = 1e30f;
+    for (int rps : {16, 24, 32, 48, 64, 96, 128, 192}) {
+        if (rps > 2 * maxh && rps != 16) continue;
+        if (launch_conv_rows_multi(args.data(), n, P.tab_host[probe], P.tab_dev[probe], rps, st, true, true) !=
+            cudaSuccess)
+            continue;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r)
+            launch_conv_rows_multi(args.data(), n, P.tab_host[probe], P.tab_dev[probe], rps, st, false, true);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = rps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+nvisr_status build_batch_plan(nvisr_batch *b, nvisr_batch::Plan &P, const PartFrames &pf, cudaStream_t st) {
+    const int n = (int)P.parts.size();
+    NVISR_TRY_CUDA(cudaMalloc(&P.pack_dev, sizeof(PackArgs) * n));
+    const size_t nsteps = b->members[0]->steps.size();
+    P.tab_host.assign(nsteps, nullptr);
+    P.tab_dev.assign(nsteps, nullptr);
+    std::vector<ConvArgs> args(n);
+    for (size_t si = 0; si < nsteps; ++si) {
+        bool rows = n > 1 && b->members[0]->steps[si].op == OP_CONV;
+        for (int i = 0; i < n && rows; ++i) {
+            args[i] = member_args(b, b->members[P.parts[i]], si, pf.frames[i].data());
+            rows = rows_kernel_fits(args[i]) && !args[i].y2 && !args[i].amax;
+        }
+        if (!rows) continue;
+        NVISR_TRY_CUDA(cudaMallocHost(&P.tab_host[si], sizeof(RowProblem) * n));
+        NVISR_TRY_CUDA(cudaMalloc(&P.tab_dev[si], sizeof(RowProblem) * n));
+    }
+    P.rps = tune_rps(b, P, pf, st);
+    for (size_t si = 0; si < nsteps; ++si) {
+        if (!P.tab_host[si]) continue;
+        for (int i = 0; i < n; ++i) args[i] = member_args(b, b->members[P.parts[i]], si, pf.frames[i].data());
+        cudaError_t e = launch_conv_rows_multi(args.data(), n, P.tab_host[si], P.tab_dev[si], P.rps, st, true, false);
+        if (e != cudaSuccess) return cuda_status(e, "batched conv table");
+    }
+    NVISR_TRY_CUDA(cudaStreamSynchronize(st));  // tables are in place before any capture
+    return NVISR_OK;
+}
+
+}  // namespace
+
 // ==================================================================== C ABI
 
 extern "C" {
@@ -1133,6 +1304,14 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
     f->tc = d->precision != NVISR_PREC_FP32;
     f->act_dt = d->precision == NVISR_PREC_FP32 ? DT_F32 : (d->precision == NVISR_PREC_FP16 ? DT_F16 : DT_BF16);
     f->calib_frames = d->calib_frames > 0 ? d->calib_frames : 4;
+    f->net_text = d->network_text;
+    f->blob_count = d->weights_count;
+    {
+        uint64_t h = 1469598103934665603ull;  // FNV-1a over the blob bytes
+        const uint8_t *b = reinterpret_cast<const uint8_t *>(d->weights);
+        for (int64_t i = 0; i < d->weights_count * 4; ++i) h = (h ^ b[i]) * 1099511628211ull;
+        f->blob_hash = h;
+    }
     const int H = d->in_fmt.height, W = d->in_fmt.width;
     nvisr_status s;
     auto cleanup = [&](nvisr_status st) {
@@ -1299,6 +1478,163 @@ nvisr_status nvisr_engine_step(nvisr_engine *e, int32_t max_outputs, int32_t *pr
     }
     if (produced) *produced = n;
     return NVISR_OK;
+}
+
+// ---------------------------------------------------------------- batched stepping
+
+nvisr_status nvisr_batch_create(nvisr_engine *e, nvisr_filter *const *filters, int32_t n, nvisr_batch **out) {
+    if (!e || !filters || n < 1 || !out) return fail(NVISR_INVALID_ARG, "batch_create: bad arguments");
+    *out = nullptr;
+    std::unique_ptr<nvisr_batch> b(new nvisr_batch());
+    b->eng = e;
+    for (int i = 0; i < n; ++i) {
+        nvisr_filter *f = filters[i];
+        if (!f || f->eng != e) return fail(NVISR_INVALID_ARG, "batch_create: filter of another engine or NULL");
+        for (nvisr_filter *g : b->members)
+            if (g == f) return fail(NVISR_INVALID_ARG, "batch_create: filter listed twice");
+        b->members.push_back(f);
+    }
+    const nvisr_filter *f0 = b->members[0];
+    b->shared = true;
+    for (const nvisr_filter *f : b->members)
+        b->shared = b->shared && batchable(f) && f->net_text == f0->net_text && f->blob_hash == f0->blob_hash &&
+                    f->blob_count == f0->blob_count && f->precision == f0->precision;
+    *out = b.release();
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_batch_step(nvisr_batch *b, int32_t *produced) {
+    if (!b) return fail(NVISR_INVALID_ARG, "batch_step: NULL batch");
+    int nprod = 0;
+    nvisr_batch::Plan probe;
+    PartFrames pf;
+    std::vector<int64_t> outs;
+    for (int m = 0; m < (int)b->members.size(); ++m) {
+        nvisr_filter *f = b->members[m];
+        if (!f->produced.empty()) continue;  // one computed output buffered per filter
+        const int64_t o = f->next_out;
+        if (f->eos && o >= f->total_out) continue;
+        if (!output_ready(f, o)) continue;
+        if (!b->shared) {
+            nvisr_status s = compute_output(f, o);
+            if (s == NVISR_AGAIN) continue;
+            if (s != NVISR_OK) return s;
+            f->produced.push_back(o);
+            ++nprod;
+            continue;
+        }
+        std::vector<int64_t> idx;
+        if (!tuple_ready(f, o, &idx)) continue;
+        std::vector<const float *> fr(8, nullptr);
+        for (size_t k = 0; k < idx.size() && k < 8; ++k) fr[k] = ring_slot(f, idx[k]);
+        probe.parts.push_back(m);
+        pf.frames.push_back(fr);
+        outs.push_back(o);
+    }
+    if (!probe.parts.empty()) {
+        cudaStream_t st = b->eng->stream;
+        const int n = (int)probe.parts.size();
+        std::vector<PackArgs> pack(n);
+        for (int i = 0; i < n; ++i) {
+            nvisr_filter *f = b->members[probe.parts[i]];
+            const Tensor &pk = f->tensors[f->pack_t];
+            PackArgs &pa = pack[i];
+            pa = PackArgs{};
+            pa.nsrc = f->net.frames;
+            for (int k = 0; k < pa.nsrc; ++k) pa.src[k] = pf.frames[i][k];
+            pa.ch_per_src = 3;
+            pa.src_pitch = f->rpitch;
+            pa.src_plane = f->rpitch * f->in_fmt.height;
+            pa.H = pk.H;
+            pa.W = pk.W;
+            pa.dst = pk.ptr;
+            pa.cpad = pk.cpad;
+            pa.dt = pk.dt;
+            pa.cpc = pk.cpc ? pk.cpc : chunk_channels(pk.dt);
+            pa.scale = 1.f;
+            if (!pack_rows_fits(pa)) return fail(NVISR_INTERNAL, "batch_step: tuple pack layout not supported");
+            for (const Step &s : f->steps)
+                if (s.op == OP_CONV && s.out_t < 0) set_final_skip(f, s, pf.frames[i].data());
+        }
+        nvisr_batch::Plan *P = nullptr;
+        for (nvisr_batch::Plan &q : b->plans)
+            if (q.parts == probe.parts) P = &q;
+        if (!P) {
+            if ((int)b->plans.size() >= kMaxPlans) {
+                auto lru = std::min_element(b->plans.begin(), b->plans.end(),
+                                            [](const nvisr_batch::Plan &x, const nvisr_batch::Plan &y) {
+                                                return x.last_use < y.last_use;
+                                            });
+                NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+                free_plan(*lru);
+                b->plans.erase(lru);
+            }
+            b->plans.emplace_back();
+            P = &b->plans.back();
+            P->parts = probe.parts;
+            nvisr_status s = build_batch_plan(b, *P, pf, st);
+            if (s != NVISR_OK) {
+                cudaStreamSynchronize(st);
+                free_plan(*P);
+                b->plans.pop_back();
+                return s;
+            }
+        }
+        P->last_use = ++b->tick;
+        // pageable source: the runtime copies it out before returning, so the
+        // table can be rewritten by the next step at once
+        NVISR_TRY_CUDA(cudaMemcpyAsync(P->pack_dev, pack.data(), sizeof(PackArgs) * n, cudaMemcpyHostToDevice, st));
+        if (P->exec) {
+            NVISR_TRY_CUDA(cudaGraphLaunch(P->exec, st));
+        } else {
+            nvisr_status s = enqueue_forward(b, *P, pack, pf, st);
+            if (s != NVISR_OK) return s;
+            // capture the same launch sequence for the next steps of this participant set
+            cudaGraph_t g = nullptr;
+            if (!P->no_graph && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const nvisr_status cs = enqueue_forward(b, *P, pack, pf, st);
+                const cudaError_t ce = cudaStreamEndCapture(st, &g);
+                if (cs == NVISR_OK && ce == cudaSuccess && g &&
+                    cudaGraphInstantiate(&P->exec, g, 0) == cudaSuccess)
+                    ++b->graphs;
+                else
+                    P->exec = nullptr;
+                P->no_graph = P->exec == nullptr;
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();  // a failed capture leaves the uncaptured path in use
+            }
+        }
+        for (int i = 0; i < n; ++i) {
+            b->members[probe.parts[i]]->produced.push_back(outs[i]);
+            ++nprod;
+        }
+    }
+    if (produced) *produced = nprod;
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_batch_info(nvisr_batch *b, int32_t *shared, int32_t *graphs, int32_t *rows_per_strip) {
+    if (!b) return fail(NVISR_INVALID_ARG, "batch_info: NULL batch");
+    if (shared) *shared = b->shared ? 1 : 0;
+    if (graphs) *graphs = b->graphs;
+    if (rows_per_strip) {
+        int rps = 0;
+        uint64_t last = 0;
+        for (const nvisr_batch::Plan &q : b->plans)
+            if (q.last_use >= last) {
+                last = q.last_use;
+                rps = q.rps;
+            }
+        *rows_per_strip = rps;
+    }
+    return NVISR_OK;
+}
+
+void nvisr_batch_destroy(nvisr_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->eng->stream);
+    for (nvisr_batch::Plan &q : b->plans) free_plan(q);
+    delete b;
 }
 
 // ---------------------------------------------------------------- stages

@@ -157,16 +157,42 @@ __global__ void __launch_bounds__(128) ingest420_kernel(
     if (x0 >= W) return;
     const int Hc = H / 2, Wc = W / 2;
     float cu[3][6], cv[3][6];
+    // chroma columns 4q .. 4q+3 as one 4-sample load when inside the row and aligned
+    const bool cvec = 4 * q + 3 <= Wc - 1 && ((pu | pv) % (4 * (int64_t)sizeof(S))) == 0 &&
+                      ((reinterpret_cast<uintptr_t>(up) | reinterpret_cast<uintptr_t>(vp)) % (4 * sizeof(S))) == 0;
+    auto load4 = [&](const S *r, float *dst) {
+        float t[4];
+        if (sizeof(S) == 2) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(r));
+            t[0] = (float)(w.x & 0xffffu); t[1] = (float)(w.x >> 16); t[2] = (float)(w.y & 0xffffu); t[3] = (float)(w.y >> 16);
+        } else {
+            const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(r));
+            t[0] = (float)(w & 0xffu); t[1] = (float)((w >> 8) & 0xffu); t[2] = (float)((w >> 16) & 0xffu); t[3] = (float)(w >> 24);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = (t[k] - rc.c_off) * rc.c_rden;
+    };
 #pragma unroll
     for (int rr = 0; rr < 3; ++rr) {
         const int row = clampi(j - 1 + rr, 0, Hc - 1);
         const S *ur = reinterpret_cast<const S *>(up + (int64_t)row * pu);
         const S *vr = reinterpret_cast<const S *>(vp + (int64_t)row * pv);
+        if (cvec) {
+            load4(ur + 4 * q, &cu[rr][1]);
+            load4(vr + 4 * q, &cv[rr][1]);
 #pragma unroll
-        for (int cc = 0; cc < 6; ++cc) {
-            const int col = clampi(4 * q - 1 + cc, 0, Wc - 1);
-            cu[rr][cc] = ((float)__ldg(ur + col) - rc.c_off) * rc.c_rden;
-            cv[rr][cc] = ((float)__ldg(vr + col) - rc.c_off) * rc.c_rden;
+            for (int cc = 0; cc < 6; cc += 5) {
+                const int col = clampi(4 * q - 1 + cc, 0, Wc - 1);
+                cu[rr][cc] = ((float)__ldg(ur + col) - rc.c_off) * rc.c_rden;
+                cv[rr][cc] = ((float)__ldg(vr + col) - rc.c_off) * rc.c_rden;
+            }
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) {
+                const int col = clampi(4 * q - 1 + cc, 0, Wc - 1);
+                cu[rr][cc] = ((float)__ldg(ur + col) - rc.c_off) * rc.c_rden;
+                cv[rr][cc] = ((float)__ldg(vr + col) - rc.c_off) * rc.c_rden;
+            }
         }
     }
     const int64_t plane = pitch * H;
@@ -188,10 +214,29 @@ __global__ void __launch_bounds__(128) ingest420_kernel(
             }
         }
         const S *yr = reinterpret_cast<const S *>(yp + (int64_t)y * py);
+        float ys[8];
+        if (x0 + 8 <= W && (reinterpret_cast<uintptr_t>(yr + x0) & (8 * sizeof(S) - 1)) == 0) {
+            if (sizeof(S) == 2) {
+                const uint4 w = __ldg(reinterpret_cast<const uint4 *>(yr + x0));
+                const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    ys[2 * k] = (float)(ww[k] & 0xffffu);
+                    ys[2 * k + 1] = (float)(ww[k] >> 16);
+                }
+            } else {
+                const uint2 w = __ldg(reinterpret_cast<const uint2 *>(yr + x0));
+                const uint32_t ww[2] = {w.x, w.y};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) ys[k] = (float)((ww[k >> 2] >> (8 * (k & 3))) & 0xffu);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) ys[e] = (float)__ldg(yr + min(x0 + e, W - 1));
+        }
         float r[8], g[8], b[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int x = min(x0 + e, W - 1);
             const int li = (e >> 1) + 1;  // local index of chroma column x >> 1
             float cb, cr;
             if (loc == NVISR_CHROMA_LEFT) {
@@ -204,7 +249,7 @@ __global__ void __launch_bounds__(128) ingest420_kernel(
                 cb = vu[li];
                 cr = vvv[li];
             }
-            const float Y = ((float)__ldg(yr + x) - rc.y_off) * rc.y_rden;
+            const float Y = (ys[e] - rc.y_off) * rc.y_rden;
             r[e] = Y + (2.0f * (1.0f - KR)) * cr;
             b[e] = Y + (2.0f * (1.0f - KB)) * cb;
             g[e] = (Y - KR * r[e] - KB * b[e]) * (1.0f / KG);
@@ -340,13 +385,22 @@ __global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict
         }
     float lr[SKIP2 ? 3 : 1][3][6];
     if (SKIP2) {
+        const bool svec = 4 * q + 3 <= sk.w - 1 && (sk.pitch & 3) == 0 && (sk.plane & 3) == 0 &&
+                          (reinterpret_cast<uintptr_t>(sk.src[0]) & 15) == 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int rr = 0; rr < 3; ++rr) {
                 const float *row = sk.src[0] + (int64_t)c * sk.plane + (int64_t)clampi(j - 1 + rr, 0, sk.h - 1) * sk.pitch;
+                if (svec) {
+                    const float4 m = __ldg(reinterpret_cast<const float4 *>(row + 4 * q));
+                    lr[c][rr][0] = __ldg(row + max(4 * q - 1, 0));
+                    lr[c][rr][1] = m.x; lr[c][rr][2] = m.y; lr[c][rr][3] = m.z; lr[c][rr][4] = m.w;
+                    lr[c][rr][5] = __ldg(row + min(4 * q + 4, sk.w - 1));
+                } else {
 #pragma unroll
-                for (int cc = 0; cc < 6; ++cc) lr[c][rr][cc] = __ldg(row + clampi(4 * q - 1 + cc, 0, sk.w - 1));
+                    for (int cc = 0; cc < 6; ++cc) lr[c][rr][cc] = __ldg(row + clampi(4 * q - 1 + cc, 0, sk.w - 1));
+                }
             }
     }
     // output (row 2j + a, column xb - 1 + c9) of channel ch: residual + skip
@@ -531,14 +585,16 @@ __device__ __forceinline__ uint4 pack_unit<__nv_fp8_e4m3>(const float *v) {
 // Row-tiled pack: one thread per 4 consecutive pixels of a row and all padded
 // channels.  Each source channel row segment is one 16-byte load; each
 // destination unit of the 4 pixels is one 16-byte store, contiguous across the
-// 4 pixels (and across the warp) for every unit index.  Needs W % 4 == 0 and
-// 16-byte aligned source rows; otherwise the per-unit kernel above runs.
+// 4 pixels (and across the warp) for every unit index.  Needs 16-byte aligned
+// source rows whose pitch covers W rounded up to 4 (the last group of a row
+// reads into that padding and stores only pixels < W); otherwise the per-unit
+// kernel above runs.
 template <typename T>
-__global__ void __launch_bounds__(128) pack_rows_kernel(const __grid_constant__ PackArgs a) {
+__device__ __forceinline__ void pack_rows(const PackArgs &a) {
     constexpr int UPC = 16 / sizeof(T);
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const int y = blockIdx.y;
-    if (x0 >= a.W) return;
+    if (x0 >= a.W || y >= a.H) return;
     const int64_t HW = (int64_t)a.H * a.W;
     const int upch = a.cpc / UPC;
     const int creal = a.nsrc * a.ch_per_src;
@@ -563,12 +619,25 @@ __global__ void __launch_bounds__(128) pack_rows_kernel(const __grid_constant__ 
         const int c = u / upch, vv = u - c * upch;
         uint8_t *d = reinterpret_cast<uint8_t *>(a.dst) + (((int64_t)c * HW + p0) * upch + vv) * 16;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) *reinterpret_cast<uint4 *>(d + (int64_t)k * upch * 16) = pack_unit<T>(v[k]);
+        for (int k = 0; k < 4; ++k)
+            if (x0 + k < a.W) *reinterpret_cast<uint4 *>(d + (int64_t)k * upch * 16) = pack_unit<T>(v[k]);
     }
     if (a.amax) {
         const unsigned m = __reduce_max_sync(__activemask(), __float_as_uint(amax));
         if ((threadIdx.x & 31) == (__ffs(__activemask()) - 1)) atomicMax(a.amax, m);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) pack_rows_kernel(const __grid_constant__ PackArgs a) {
+    pack_rows<T>(a);
+}
+
+// Batched form: blockIdx.z selects one of several packs (e.g. the tuples of
+// several streams) whose arguments are read from a device table.
+template <typename T>
+__global__ void __launch_bounds__(128) pack_rows_table_kernel(const PackArgs *__restrict__ tab) {
+    pack_rows<T>(tab[blockIdx.z]);
 }
 
 template <typename T>
@@ -665,9 +734,7 @@ cudaError_t launch_pack(const PackArgs &a0, cudaStream_t st) {
     const int upc = chunk_channels(a.dt);
     if (a.cpc == 0) a.cpc = upc;
     if (a.cpc % upc || a.cpad % a.cpc) return cudaErrorInvalidValue;
-    bool rows = a.W % 4 == 0 && a.src_pitch % 4 == 0 && a.src_plane % 4 == 0;
-    for (int s = 0; s < a.nsrc; ++s) rows = rows && (reinterpret_cast<uintptr_t>(a.src[s]) & 15) == 0;
-    if (rows) {
+    if (pack_rows_fits(a)) {
         dim3 blk(128), grd((a.W / 4 + 127) / 128, a.H);
         switch (a.dt) {
             case DT_F32: pack_rows_kernel<float><<<grd, blk, 0, st>>>(a); break;
@@ -685,6 +752,34 @@ cudaError_t launch_pack(const PackArgs &a0, cudaStream_t st) {
         case DT_BF16: pack_kernel<__nv_bfloat16><<<(unsigned)grid, block, 0, st>>>(a); break;
         case DT_F16: pack_kernel<__half><<<(unsigned)grid, block, 0, st>>>(a); break;
         default: pack_kernel<__nv_fp8_e4m3><<<(unsigned)grid, block, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+bool pack_rows_fits(const PackArgs &a) {
+    const int upc = chunk_channels(a.dt);
+    const int cpc = a.cpc ? a.cpc : upc;
+    bool ok = a.src_pitch % 4 == 0 && a.src_pitch >= (a.W + 3) / 4 * 4 && a.src_plane % 4 == 0 && cpc % upc == 0 &&
+              a.cpad % cpc == 0;
+    for (int s = 0; s < a.nsrc; ++s) ok = ok && (reinterpret_cast<uintptr_t>(a.src[s]) & 15) == 0;
+    return ok;
+}
+
+cudaError_t launch_pack_table(const PackArgs *host_tab, const PackArgs *dev_tab, int n, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    int maxw = 0, maxh = 0;
+    for (int i = 0; i < n; ++i) {
+        const PackArgs &a = host_tab[i];
+        if (!pack_rows_fits(a) || a.dt != host_tab[0].dt || a.cpc == 0) return cudaErrorInvalidValue;
+        maxw = std::max(maxw, a.W);
+        maxh = std::max(maxh, a.H);
+    }
+    dim3 blk(128), grd((maxw / 4 + 127) / 128, maxh, n);
+    switch (host_tab[0].dt) {
+        case DT_F32: pack_rows_table_kernel<float><<<grd, blk, 0, st>>>(dev_tab); break;
+        case DT_BF16: pack_rows_table_kernel<__nv_bfloat16><<<grd, blk, 0, st>>>(dev_tab); break;
+        case DT_F16: pack_rows_table_kernel<__half><<<grd, blk, 0, st>>>(dev_tab); break;
+        default: pack_rows_table_kernel<__nv_fp8_e4m3><<<grd, blk, 0, st>>>(dev_tab); break;
     }
     return cudaGetLastError();
 }

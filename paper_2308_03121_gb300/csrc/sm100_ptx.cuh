@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace nvisr {
@@ -141,6 +142,20 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
             smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Raise a kernel's dynamic shared-memory limit once per device (the setting
+// persists, and later calls, e.g. while a CUDA graph is being captured, make
+// no runtime call).
+template <auto KERN>
+inline cudaError_t set_smem_limit(int smem) {
+    static int done[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (done[dev] >= smem) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) done[dev] = smem;
+    return e;
 }
 
 // ---------------------------------------------------------------- tcgen05
