@@ -277,6 +277,44 @@ nvisr_status nvisr_batch_step(nvisr_batch *batch, int32_t *produced);
 nvisr_status nvisr_batch_info(nvisr_batch *batch, int32_t *shared, int32_t *graphs, int32_t *rows_per_strip);
 void nvisr_batch_destroy(nvisr_batch *batch);
 
+/* ----------------------------------------------------------------------------
+ * Serving (continuous batching).
+ *
+ * A server owns the clips submitted to one engine.  A clip is one video
+ * stream described like a filter (nvisr_filter_desc; the server copies the
+ * description and the weights).  It waits in arrival order until it can be
+ * created as a filter: fewer than max_active clips are active (0 = no limit)
+ * and the engine's HBM budget holds its ring, activations and weights.  Every
+ * nvisr_server_step first admits waiting clips, then steps each group of
+ * active clips that run the same network as one batch (nvisr_batch): a clip
+ * admitted while others are in flight joins the next step's shared launches.
+ * Closing a clip frees its memory and admits waiting clips at once.
+ * nvisr_server_push / _flush / _pull are nvisr_push / _flush / _pull on the
+ * clip's filter and return AGAIN while the clip is still waiting.  Latency of
+ * an output = the time its planes are written (pull of host planes; for device
+ * planes the server waits for the engine stream) minus the push time of the
+ * newest input frame it depends on; queueing delay = admission minus
+ * submission.
+ * Errors: INVALID_ARG (NULL, unknown clip), the filter and batch errors.
+ * ------------------------------------------------------------------------- */
+typedef struct nvisr_server nvisr_server;
+typedef struct nvisr_server_stats_t {
+    double latency_p50_ms, latency_p99_ms;  /* per output frame */
+    double queue_p50_ms, queue_p99_ms;      /* per admitted clip */
+    int64_t admitted, pending, active, completed, outputs;
+    int64_t deferred_steps;                 /* admission attempts stopped by the HBM budget */
+} nvisr_server_stats_t;
+nvisr_status nvisr_server_create(nvisr_engine *engine, int32_t max_active, nvisr_server **out);
+nvisr_status nvisr_server_submit(nvisr_server *server, const nvisr_filter_desc *desc, int64_t *clip);
+nvisr_status nvisr_server_push(nvisr_server *server, int64_t clip, const nvisr_planes *in, uint32_t flags);
+nvisr_status nvisr_server_flush(nvisr_server *server, int64_t clip);
+/* *produced (may be NULL): outputs computed by this step over all clips. */
+nvisr_status nvisr_server_step(nvisr_server *server, int32_t *produced);
+nvisr_status nvisr_server_pull(nvisr_server *server, int64_t clip, nvisr_planes *out, nvisr_frame_info *info);
+nvisr_status nvisr_server_close(nvisr_server *server, int64_t clip);
+nvisr_status nvisr_server_stats(nvisr_server *server, nvisr_server_stats_t *out);
+void nvisr_server_destroy(nvisr_server *server);
+
 /* One 2-D convolution layer (Section 3.1 networks) on planar float32 tensors:
  * y[cout][H][W] = act(conv_k(x[cin][H][W]; w[cout][cin][k][k]) + b) (+ res),
  * stride 1, zero padding (k-1)/2, act 0 = none, 1 = LeakyReLU(0.1).  Runs the

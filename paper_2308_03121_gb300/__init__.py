@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "Batch", "Engine", "Filter", "NvisrError", "PREC", "Status", "fmt", "lib", "load",
+    "Batch", "Engine", "Filter", "NvisrError", "Server", "PREC", "Status", "fmt", "lib", "load",
     "nvisr_conv2d", "nvisr_conv2d_static", "nvisr_dcn2d", "nvisr_fig1_layout", "nvisr_group_runs",
     "nvisr_ingest", "nvisr_network_check", "nvisr_requant", "nvisr_selftest",
     "nvisr_tuple_map",
@@ -53,6 +53,13 @@ class Format(ctypes.Structure):
 class Planes(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p * 3), ("pitch", ctypes.c_int64 * 3),
                 ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("queue_p50_ms", ctypes.c_double), ("queue_p99_ms", ctypes.c_double),
+                ("admitted", ctypes.c_int64), ("pending", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("outputs", ctypes.c_int64), ("deferred_steps", ctypes.c_int64)]
 
 
 class EngineDesc(ctypes.Structure):
@@ -114,6 +121,15 @@ _SIGS = {
     "nvisr_batch_step": (_I32, [_VP, _I32P]),
     "nvisr_batch_info": (_I32, [_VP, _I32P, _I32P, _I32P]),
     "nvisr_batch_destroy": (None, [_VP]),
+    "nvisr_server_create": (_I32, [_VP, _I32, ctypes.POINTER(_VP)]),
+    "nvisr_server_submit": (_I32, [_VP, ctypes.POINTER(FilterDesc), ctypes.POINTER(_I64)]),
+    "nvisr_server_push": (_I32, [_VP, _I64, ctypes.POINTER(Planes), ctypes.c_uint32]),
+    "nvisr_server_flush": (_I32, [_VP, _I64]),
+    "nvisr_server_step": (_I32, [_VP, _I32P]),
+    "nvisr_server_pull": (_I32, [_VP, _I64, ctypes.POINTER(Planes), ctypes.POINTER(FrameInfo)]),
+    "nvisr_server_close": (_I32, [_VP, _I64]),
+    "nvisr_server_stats": (_I32, [_VP, ctypes.POINTER(ServerStats)]),
+    "nvisr_server_destroy": (None, [_VP]),
     "nvisr_abi_version": (_I32, []),
     "nvisr_build_info": (ctypes.c_char_p, []),
 }
@@ -367,6 +383,74 @@ class Batch:
             self.h = None
             if self in getattr(self.engine, "batches", []):
                 self.engine.batches.remove(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving runtime on one engine: submit clips at any time; admitted clips share batched steps."""
+
+    def __init__(self, engine, max_active=0):
+        self.engine = engine
+        h = ctypes.c_void_p()
+        _check(_LIB.nvisr_server_create(engine.h, max_active, ctypes.byref(h)), "nvisr_server_create")
+        self.h = h
+        self.fmts = {}
+
+    def submit(self, net_text, blob, in_fmt, out_fmt, precision="bf16", scale=2, calib_frames=0):
+        blob = np.ascontiguousarray(np.asarray(blob, np.float32))
+        text = net_text.encode()
+        d = FilterDesc(text, blob.ctypes.data_as(_F32P), blob.size, in_fmt, out_fmt, scale, scale,
+                       PREC[precision] if isinstance(precision, str) else precision, calib_frames)
+        cid = ctypes.c_int64(0)
+        _check(_LIB.nvisr_server_submit(self.h, ctypes.byref(d), ctypes.byref(cid)), "nvisr_server_submit")
+        self.fmts[cid.value] = out_fmt
+        return cid.value
+
+    def push(self, clip, planes, cut=False):
+        dev = hasattr(planes[0], "is_cuda") and planes[0].is_cuda
+        p = planes_of(planes, dev)
+        return _check(_LIB.nvisr_server_push(self.h, clip, ctypes.byref(p), SCENE_CUT if cut else 0),
+                      "nvisr_server_push")
+
+    def flush(self, clip):
+        return _check(_LIB.nvisr_server_flush(self.h, clip), "nvisr_server_flush")
+
+    def step(self):
+        n = ctypes.c_int32(0)
+        _check(_LIB.nvisr_server_step(self.h, ctypes.byref(n)), "nvisr_server_step")
+        return n.value
+
+    def pull(self, clip, out):
+        dev = hasattr(out[0], "is_cuda") and out[0].is_cuda
+        p = planes_of(out, dev)
+        info = FrameInfo()
+        st = _check(_LIB.nvisr_server_pull(self.h, clip, ctypes.byref(p), ctypes.byref(info)), "nvisr_server_pull")
+        return st, info
+
+    def alloc_out_host(self, clip):
+        f = self.fmts[clip]
+        dt = np.uint8 if f.bit_depth <= 8 else np.uint16
+        cw, ch = (f.width // 2, f.height // 2) if f.subsampling == 0 else (f.width, f.height)
+        return (np.zeros((f.height, f.width), dt), np.zeros((ch, cw), dt), np.zeros((ch, cw), dt))
+
+    def close_clip(self, clip):
+        _check(_LIB.nvisr_server_close(self.h, clip), "nvisr_server_close")
+        self.fmts.pop(clip, None)
+
+    def stats(self):
+        st = ServerStats()
+        _check(_LIB.nvisr_server_stats(self.h, ctypes.byref(st)), "nvisr_server_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            _LIB.nvisr_server_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:
