@@ -283,6 +283,90 @@ def measure_batched(nv, steps, warmup, local):
             "timing": "wall clock between device synchronisations (host launch work included)"}
 
 
+SERVE_RES = [(854, 480), (1280, 720), (1920, 1080), (2560, 1440)]
+
+
+def measure_serving(nv, seconds, rate, budget_gb, local, seed=synth.BASE_SEED + 5):
+    """Serving loop: clips arrive as a Poisson process (rate per second) for
+    `seconds`; each has log-uniform [30, 600] frames, a resolution from
+    SERVE_RES, 8 or 10 bits 4:2:0, and runs the 2x tuple network or the 4x
+    two-frame deformable network (50/50) in BF16, under an HBM budget.  Host
+    input planes are pushed one frame per clip per server step; outputs are
+    pulled into device planes.  Clips still running when the window closes
+    count with the outputs they produced."""
+    import torch
+    rng = np.random.default_rng(seed)
+    nets = {"c2": (synth.net_config2(), 2), "c3": (synth.net_config3(), 4)}
+    frames = {}
+    outbuf = {}
+    eng = nv.Engine(device=local, hbm_budget_bytes=int(budget_gb * 2 ** 30))
+    srv = nv.Server(eng)
+    dev = f"cuda:{local}"
+    clips = {}
+    out_pix = 0
+    t0 = time.perf_counter()
+    next_arrival = t0 + rng.exponential(1.0 / rate)
+    submitted = 0
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        now = time.perf_counter()
+        while next_arrival <= now:
+            w, h = SERVE_RES[rng.integers(len(SERVE_RES))]
+            bits = 8 if rng.uniform() < 0.5 else 10
+            net = "c2" if rng.uniform() < 0.5 else "c3"
+            n = int(round(np.exp(rng.uniform(np.log(30), np.log(600)))))
+            (text, blob), sc = nets[net]
+            key = (w, h, bits)
+            if key not in frames:
+                frames[key] = synth.frames_textured(seed, 2, w, h, bits, "420", "limited")
+            okey = (sc * w, sc * h, bits)
+            if okey not in outbuf:
+                dt = torch.int16 if bits > 8 else torch.uint8
+                outbuf[okey] = (torch.empty((sc * h, sc * w), dtype=dt, device=dev),
+                                torch.empty((sc * h // 2, sc * w // 2), dtype=dt, device=dev),
+                                torch.empty((sc * h // 2, sc * w // 2), dtype=dt, device=dev))
+            cid = srv.submit(text, blob, nv.fmt(w, h, bits), nv.fmt(sc * w, sc * h, bits), "bf16", sc)
+            clips[cid] = {"key": key, "okey": okey, "n": n, "next": 0, "flushed": False}
+            submitted += 1
+            next_arrival += rng.exponential(1.0 / rate)
+        for cid, c in clips.items():
+            if c["next"] < c["n"]:
+                fr = frames[c["key"]][c["next"] % 2]
+                if srv.push(cid, (fr["Y"], fr["U"], fr["V"])) == nv.Status.OK:
+                    c["next"] += 1
+            elif not c["flushed"] and srv.flush(cid) == nv.Status.OK:
+                c["flushed"] = True
+        srv.step()
+        steps += 1
+        done = []
+        for cid, c in clips.items():
+            while True:
+                st, _ = srv.pull(cid, outbuf[c["okey"]])
+                if st == nv.Status.OK:
+                    out_pix += c["okey"][0] * c["okey"][1]
+                    continue
+                if st == nv.Status.EOS:
+                    done.append(cid)
+                break
+        for cid in done:
+            srv.close_clip(cid)
+            del clips[cid]
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    eng.close()
+    return {"workload": f"Poisson clip arrivals at {rate}/s for {seconds} s; 30-600 frames (log-uniform); "
+                        "480p/720p/1080p/1440p, 8/10-bit 4:2:0; 2x tuple network or 4x deformable two-frame "
+                        f"network (50/50), BF16; {budget_gb} GB HBM budget",
+            "metric": "output Mpix/s", "value": out_pix / elapsed / 1e6, "seconds": elapsed,
+            "latency_p50_ms": st["latency_p50_ms"], "latency_p99_ms": st["latency_p99_ms"],
+            "queue_p50_ms": st["queue_p50_ms"], "queue_p99_ms": st["queue_p99_ms"],
+            "submitted": submitted, "admitted": st["admitted"], "completed": st["completed"],
+            "pending_at_end": st["pending"], "active_at_end": st["active"], "outputs": st["outputs"],
+            "deferred_admissions": st["deferred_steps"], "server_steps": steps}
+
+
 def measure_e2e(nv, prec, steps, pinned, local):
     """Host planes in, host planes out, through nvisr_push / nvisr_pull (copies inside)."""
     import torch
@@ -373,6 +457,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=12, help="steps of the 24-stream batched run (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving-loop window (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=6.0, help="clip arrivals per second")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     rank, world, local = dist_init()
     if args.impl == "reference":
@@ -411,6 +498,12 @@ def main():
     achieved_gbs = BODY_BYTES / (avg_body * 1e-3) / 1e9
     launches = sum(n for _, n in prof.values())
     e2e_total, p50, p99 = measure_e2e(nv, head, args.e2e_steps, pinned, local)
+    serving = None
+    if args.serve_seconds > 0:
+        try:
+            serving = measure_serving(nv, args.serve_seconds, args.serve_rate, args.serve_budget_gb, local)
+        except Exception as e:  # the secondary workload must not hide the headline
+            errors["serving"] = repr(e)
     batched = None
     if args.batched_steps > 0:
         try:
@@ -461,6 +554,7 @@ def main():
         "clocks": r["clocks"],
         "precisions": by_prec,
         "batched": batched,
+        "serving": serving,
         "hbm_peak_gbs": hbm,
     }
     if errors:
