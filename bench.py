@@ -119,6 +119,11 @@ def barrier(world):
         dist.barrier()
 
 
+def job_value(world, steps, pix_per_step, ms_max):
+    """Whole-job output Mpix/s: the pixels every rank produced over the slowest rank's time."""
+    return world * steps * pix_per_step / (ms_max * 1e-3) / 1e6
+
+
 def allmax(v, world):
     if world == 1:
         return v
@@ -489,7 +494,7 @@ def main():
             errors[prec] = repr(e)
             continue
         results[prec] = {"ms": ms, "steps": steps, "prof": prof, "clocks": ck,
-                         "mpix_s": world * steps * OUT_PIX / (ms * 1e-3) / 1e6}
+                         "mpix_s": job_value(world, steps, OUT_PIX, ms)}
     r = results[head]
     prof = r["prof"]
     body_ms, body_n = prof["conv_body"]
