@@ -103,7 +103,8 @@ struct ConvArgs {
     int H, W;
     int nimg;                // images stacked along the outer dimension
     const void *w;           // prepared weights (kernel-specific layout)
-    const void *w_rows;      // 64->64 3x3 only: weights for the row-streaming kernel, or null
+    const void *w_rows;      // 3x3 with 64 input channels: weights for the row-streaming kernel (64 outputs,
+                             // or <= 16 outputs shuffled into planar float32), or null
     const float *bias;       // [cout_pad] float32 (zero past cout)
     int cout, cout_pad, k;
     int act;                 // 0 none, 1 LeakyReLU(0.1)
@@ -160,8 +161,9 @@ void prepare_weights_tc(const float *w_oihw, int cout, int cin, int k, int cin_p
                         int dt, float scale, void *dst_host, bool sw128);
 int tc_nslice(int cin_pad, int cout_pad, int k, int dt);
 // Row-streaming 64 -> 64 3x3 layout: [kx][2 - ky][64 out][128 B swizzled 64 in].
-size_t tc_rows_weight_bytes();
-void prepare_weights_rows(const float *w_oihw, int dt, void *dst_host);
+size_t tc_rows_weight_bytes(int npr = 64);
+// npr = 16: the PixelShuffle output form (cout <= 16 channels in 16 rows per tap).
+void prepare_weights_rows(const float *w_oihw, int dt, void *dst_host, int cout = 64, int npr = 64);
 
 // DCN: x blocked (activation dtype); offsets and mask in one blocked float32
 // tensor [om_cpad/4][H][W][4]: channels [0, 18G) = (dy, dx) per (group, tap),

@@ -543,7 +543,7 @@ struct RowPlan {
     int rps;      // rows per band
 };
 
-template <int IN_DT, int OUT_DT, int CBO, bool MULTI>
+template <int IN_DT, int OUT_DT, int CBO, bool MULTI, int NPR, bool PS>
 __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 const __grid_constant__ CUtensorMap ymap,
                                                                 const __grid_constant__ CUtensorMap rmap,
@@ -553,11 +553,15 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     constexpr int AFMT = IN_DT == DT_BF16 ? 1 : 0;
     constexpr int PXS = TM + 2;
     constexpr uint32_t ROWB = (PXS * 128 + 1023u) & ~1023u;  // one 130-pixel input row, 64 channels
-    constexpr uint32_t WKX = 3 * 64 * 128;                    // weights of one kx: [ky' = 2 - ky][64][128 B]
+    // NPR: accumulator columns of one output row (= padded output channels: 64 for the
+    // trunk, 16 for the 12-channel PixelShuffle tail); PS: PixelShuffle(2) epilogue
+    // into planar float32 instead of the blocked 16-bit row store
+    static_assert(NPR == 64 || (NPR == 16 && PS), "64-channel trunk rows or 16-channel shuffle tail");
+    constexpr uint32_t WKX = 3 * NPR * 128;                   // weights of one kx: [ky' = 2 - ky][NPR][128 B]
     constexpr uint32_t TILEB = TM * 128;                      // one 128-pixel output / residual row tile
     constexpr int NSLOT = 8;                                  // output-row accumulators in TMEM
     static_assert(NSLOT == 8, "slot index and phase use & 7 and >> 3");
-    constexpr uint32_t NCOLS = 512;
+    constexpr uint32_t NCOLS = NPR == 64 ? 512 : 128;
     constexpr int UPC_O = 16 / sizeof(TO);
     constexpr int NU = 64 / UPC_O;                            // 16-byte units of a pixel's 64 channels
     constexpr int NGRP = 128;                                 // threads of one epilogue group
@@ -618,7 +622,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     auto ymap_of = [&](int pi) { return MULTI ? &probs[pi].ymap : &ymap; };
     auto rmap_of = [&](int pi) { return MULTI ? &probs[pi].rmap : &rmap; };
     auto width_of = [&](int pi) { return MULTI ? probs[pi].W : p.W; };
-    if (threadIdx.x >= 64 && threadIdx.x < 128) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + NPR) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -724,13 +728,13 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         // of [o_lo, o_hi] with one N = 64 * rows MMA per run.  Everything is held in
                         // scalars so the unrolled issue sequence is only descriptor adds.
                         const uint32_t id0 = instr_desc(TM, 0, AFMT, AFMT);
-                        const uint32_t nstep = 8u << 17;  // N += 64
+                        const uint32_t nstep = (uint32_t)(NPR / 8) << 17;  // N += NPR
                         auto slot_of = [&](int o) { return (base + o) & (NSLOT - 1); };
-                        auto bd_of = [&](int o) { return b_base + (uint64_t)(((o - r + 1) * 64 * 128) >> 4); };
+                        auto bd_of = [&](int o) { return b_base + (uint64_t)(((o - r + 1) * NPR * 128) >> 4); };
                         const int sl0 = slot_of(o_lo);
                         const int len = o_hi - o_lo + 1;
                         const int m0 = min(len, NSLOT - sl0), m1 = len - m0;
-                        const uint32_t md0 = tmem_base + (uint32_t)(sl0 * 64), md1 = tmem_base;
+                        const uint32_t md0 = tmem_base + (uint32_t)(sl0 * NPR), md1 = tmem_base;
                         const uint32_t mi0 = id0 + nstep * (uint32_t)m0, mi1 = id0 + nstep * (uint32_t)max(m1, 1);
                         const uint64_t mb0 = bd_of(o_lo), mb1 = bd_of(o_lo + m0);
                         // first MMA: old rows [o_lo, old_hi] (split at the wrap), then the fresh row
@@ -743,7 +747,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                                 if (f1 > 0) umma<0>(md1, a_base, mb1, id0 + nstep * (uint32_t)f1, 1u);
                             }
                             if (fresh)
-                                umma<0>(tmem_base + (uint32_t)(slot_of(r + 1) * 64), a_base, bd_of(r + 1),
+                                umma<0>(tmem_base + (uint32_t)(slot_of(r + 1) * NPR), a_base, bd_of(r + 1),
                                         id0 + nstep, 0u);
                         }
                         if (m1 == 0) {
@@ -850,6 +854,52 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                 named_barrier(bar_id, NGRP);
                 bool w = mbar_wait_bounded(&rowdone[slot], (uint32_t)((i / NSLOT) & 1), abort, WAIT_NS);
                 w = __all_sync(0xffffffffu, w);
+                if constexpr (PS) {
+                    // 12 shuffled channels: channel 4c + 2dy + dx -> output (c, 2o + dy, 2x + dx)
+                    float v[16];
+                    if (w) {
+                        tc_fence_after();
+                        uint32_t rr[16];
+                        tmem_ld16_nowait(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * NPR), rr);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(rr[e]);
+                        tc_fence_before();
+                        mbar_arrive(&slotfree[slot]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[e] = 0.f;
+                        if (lane == 0) {
+                            raise_abort(abort, p.err);
+                            grp_stop[g] = 1;
+                        }
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        float ov = v[e] * p.acc_scale + sbias[e];
+                        if (p.act == 1) ov = lrelu(ov);
+                        if (p.ps_act == 1) ov = lrelu(ov);
+                        v[e] = ov;
+                    }
+                    if (valid && w) {
+                        const int64_t plane = p.ps_pitch * 2 * p.H;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            if (c >= p.cout / 4) break;
+#pragma unroll
+                            for (int dy = 0; dy < 2; ++dy)
+                                *reinterpret_cast<float2 *>(p.ps_out + c * plane + (int64_t)(2 * o + dy) * p.ps_pitch +
+                                                            2 * x) = make_float2(v[4 * c + 2 * dy], v[4 * c + 2 * dy + 1]);
+                        }
+                    }
+                    if (leader && *abort) grp_stop[g] = 1;
+                    named_barrier(bar_id, NGRP);
+                    if (grp_stop[g]) {
+                        ok = false;
+                        break;
+                    }
+                    continue;
+                }
                 float v[64];
                 if (w) {
                     tc_fence_after();
@@ -1265,18 +1315,18 @@ void prepare_weights_tc(const float *w, int cout, int cin, int k, int cin_pad, i
     }
 }
 
-size_t tc_rows_weight_bytes() { return (size_t)3 * 3 * 64 * 128; }
+size_t tc_rows_weight_bytes(int npr) { return (size_t)3 * 3 * npr * 128; }
 
-void prepare_weights_rows(const float *w, int dt, void *dst) {
+void prepare_weights_rows(const float *w, int dt, void *dst, int cout, int npr) {
     uint8_t *out = static_cast<uint8_t *>(dst);
-    memset(out, 0, tc_rows_weight_bytes());
-    for (int n = 0; n < 64; ++n)
+    memset(out, 0, tc_rows_weight_bytes(npr));
+    for (int n = 0; n < cout; ++n)
         for (int c = 0; c < 64; ++c)
             for (int ky = 0; ky < 3; ++ky)
                 for (int kx = 0; kx < 3; ++kx) {
                     const float v = w[((size_t)n * 64 + c) * 9 + ky * 3 + kx];
-                    const size_t row = (size_t)(2 - ky) * 64 + n;
-                    const size_t off = (size_t)kx * 3 * 64 * 128 + row * 128 + (((c / 8) ^ (n & 7)) * 16) + (c % 8) * 2;
+                    const size_t row = (size_t)(2 - ky) * npr + n;
+                    const size_t off = (size_t)kx * 3 * npr * 128 + row * 128 + (((c / 8) ^ (n & 7)) * 16) + (c % 8) * 2;
                     if (dt == DT_BF16) {
                         __nv_bfloat16 h = __float2bfloat16_rn(v);
                         memcpy(out + off, &h, 2);
@@ -1292,24 +1342,24 @@ namespace {
 // Shared memory of the row kernel: 72 KB weights, the input-row ring, 2 output
 // staging tiles and, when the layer adds a residual, 2 residual tiles (without
 // one, their room goes to deeper input prefetch).
-inline int rows_stages(bool res, int *smem) {
+inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false) {
     constexpr uint32_t ROWB = ((TM + 2) * 128 + 1023u) & ~1023u;
-    constexpr uint32_t WB = 3 * 3 * 64 * 128;
-    const uint32_t TILES = (res ? 4u : 2u) * TM * 128;
+    const uint32_t WB = 3 * 3 * (uint32_t)npr * 128;
+    const uint32_t TILES = ps ? 0u : (res ? 4u : 2u) * TM * 128;
     int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES) / (int)ROWB;
     if (stages > 8) stages = 8;
     *smem = 1024 + SMEM_HDR + (int)WB + stages * (int)ROWB + (int)TILES;
     return stages;
 }
 
-template <int IN_DT, int OUT_DT, int CBO>
+template <int IN_DT, int OUT_DT, int CBO, int NPR = 64, bool PS = false>
 cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUtensorMap &rmap, TcParams p,
                      cudaStream_t st) {
     int smem;
-    p.stages = rows_stages(p.res != nullptr, &smem);
+    p.stages = rows_stages(p.res != nullptr, &smem, NPR, PS);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
-    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, false>;
-    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, false>>(smem);
+    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS>;
+    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS>>(smem);
     if (e != cudaSuccess) return e;
     RowPlan rp;
     rp.xtiles = (p.W + TM - 1) / TM;
@@ -1331,8 +1381,8 @@ cudaError_t run_rows_multi(const CUtensorMap &dummy, TcParams p, const RowProble
     int smem;
     p.stages = rows_stages(p.res != nullptr, &smem);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
-    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, true>;
-    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, true>>(smem);
+    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, true, 64, false>;
+    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, true, 64, false>>(smem);
     if (e != cudaSuccess) return e;
     RowPlan rp{};
     const int grid = std::min(total, device_sm_count());
@@ -1387,6 +1437,14 @@ bool rows_kernel_fits(const ConvArgs &a) {
            a.cout_pad == 64 && a.cout == 64 && a.in_cpc == 64 && a.out_cpc == 64 && a.ps == 0;
 }
 
+// PixelShuffle(2) output layer with 64 input channels (<= 16 outputs, planar float32).
+bool rows_ps_fits(const ConvArgs &a) {
+    const int dt = a.in_dt;
+    return a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.cin_pad == 64 && a.in_cpc == 64 &&
+           a.cout_pad == 16 && a.cout <= 12 && a.cout % 4 == 0 && a.ps == 2 && a.ps_out && !a.res && !a.y2 &&
+           !a.amax && a.nimg == 1;
+}
+
 cudaError_t launch_conv_rows_multi(const ConvArgs *args, int n, RowProblem *host_tab, RowProblem *dev_tab, int rps,
                                    cudaStream_t st, bool copy_table, bool launch) {
     if (n < 1) return cudaSuccess;
@@ -1434,6 +1492,23 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
         const TcParams p = rows_params(a);
         return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128>(map, ymap, rmap, p, st)
                              : run_rows<DT_F16, DT_F16, 128>(map, ymap, rmap, p, st);
+    }
+    if (rows_ps_fits(a)) {
+        ConvArgs b = a;
+        b.y = const_cast<void *>(a.x);  // the shuffle epilogue stores directly; the y / residual maps are unused
+        CUtensorMap map, ymap, rmap;
+        cudaError_t e = encode_row_maps(b, &map, &ymap, &rmap);
+        if (e != cudaSuccess) return e;
+        TcParams p = rows_params(a);
+        p.cout = a.cout;
+        p.cout_pad = 16;
+        p.ns = 16;
+        p.wbytes = (uint32_t)tc_rows_weight_bytes(16);
+        p.ps_out = a.ps_out;
+        p.ps_pitch = a.ps_pitch;
+        p.ps_act = a.ps_act;
+        return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128, 16, true>(map, ymap, rmap, p, st)
+                             : run_rows<DT_F16, DT_F16, 128, 16, true>(map, ymap, rmap, p, st);
     }
     if (dt == DT_F32) return cudaErrorInvalidValue;
     const int esz = dtype_size(dt);

@@ -392,6 +392,11 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
             std::vector<uint8_t> rows(tc_rows_weight_bytes());
             prepare_weights_rows(w, f->act_dt, rows.data());
             s = upload(f, rows.data(), rows.size(), &W.rows);
+        } else if (s == NVISR_OK && L.op == "conv" && L.k == 3 && L.cin == 64 && L.cout <= 16 && L.cout % 4 == 0) {
+            // a PixelShuffle(2) output layer: the row kernel's 16-column shuffle form
+            std::vector<uint8_t> rows(tc_rows_weight_bytes(16));
+            prepare_weights_rows(w, f->act_dt, rows.data(), L.cout, 16);
+            s = upload(f, rows.data(), rows.size(), &W.rows);
         }
     }
     if (s != NVISR_OK) return s;
