@@ -162,6 +162,10 @@ void prepare_weights_tc(const float *w_oihw, int cout, int cin, int k, int cin_p
 int tc_nslice(int cin_pad, int cout_pad, int k, int dt);
 // Row-streaming 64 -> 64 3x3 layout: [kx][2 - ky][64 out][128 B swizzled 64 in].
 size_t tc_rows_weight_bytes(int npr = 64);
+// Row-streaming image of a 3x3 layer from <= 16 input channels to 64:
+// [kx][16-byte channel chunk][2 - ky][64 out][8 channels], no swizzle.
+size_t tc_rows16_weight_bytes();
+void prepare_weights_rows16(const float *w_oihw, int cin, int dt, void *dst_host);
 // npr = 16: the PixelShuffle output form (cout <= 16 channels in 16 rows per tap).
 void prepare_weights_rows(const float *w_oihw, int dt, void *dst_host, int cout = 64, int npr = 64);
 

@@ -543,7 +543,7 @@ struct RowPlan {
     int rps;      // rows per band
 };
 
-template <int IN_DT, int OUT_DT, int CBO, bool MULTI, int NPR, bool PS>
+template <int IN_DT, int OUT_DT, int CBO, bool MULTI, int NPR, bool PS, int CIN>
 __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 const __grid_constant__ CUtensorMap ymap,
                                                                 const __grid_constant__ CUtensorMap rmap,
@@ -552,12 +552,20 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     using TO = typename Elem<OUT_DT>::T;
     constexpr int AFMT = IN_DT == DT_BF16 ? 1 : 0;
     constexpr int PXS = TM + 2;
-    constexpr uint32_t ROWB = (PXS * 128 + 1023u) & ~1023u;  // one 130-pixel input row, 64 channels
+    // CIN: input channels of a row.  64: one 128-byte line per pixel, 128-byte swizzled;
+    // 16 (the tuple head): two 16-byte channel chunks per pixel, canonical no-swizzle
+    // layout [chunk][pixel][16 B] (K core matrices LBO_A apart)
+    static_assert(CIN == 64 || (CIN == 16 && NPR == 64 && !PS), "64-channel rows or the 16-channel head");
+    constexpr int KSTEPS = CIN == 64 ? 4 : 1;                 // 16-channel MMA K steps per kx
+    constexpr uint32_t AROW = CIN == 64 ? PXS * 128 : 2 * PXS * 16;  // bytes of one 130-pixel input row
+    constexpr uint32_t ROWB = (AROW + 1023u) & ~1023u;
+    constexpr uint32_t LBO_A = PXS * 16, LBO_B = 3 * NPR * 16;
     // NPR: accumulator columns of one output row (= padded output channels: 64 for the
     // trunk, 16 for the 12-channel PixelShuffle tail); PS: PixelShuffle(2) epilogue
     // into planar float32 instead of the blocked 16-bit row store
     static_assert(NPR == 64 || (NPR == 16 && PS), "64-channel trunk rows or 16-channel shuffle tail");
-    constexpr uint32_t WKX = 3 * NPR * 128;                   // weights of one kx: [ky' = 2 - ky][NPR][128 B]
+    // weights of one kx: [ky' = 2 - ky][NPR][128 B] (CIN 64) or [2 chunks][3 * NPR][16 B] (CIN 16)
+    constexpr uint32_t WKX = CIN == 64 ? 3 * NPR * 128 : 2 * 3 * NPR * 16;
     constexpr uint32_t TILEB = TM * 128;                      // one 128-pixel output / residual row tile
     constexpr int NSLOT = 8;                                  // output-row accumulators in TMEM
     static_assert(NSLOT == 8, "slot index and phase use & 7 and >> 3");
@@ -668,8 +676,8 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[s], PXS * 128);
-                    tma_load_4d(stage0 + (size_t)s * ROWB, tmap_of(pi), &full[s], 0, x0 - 1, r, img);
+                    mbar_arrive_expect_tx(&full[s], AROW);
+                    tma_load_4d(stage0 + (size_t)s * ROWB, tmap_of(pi), &full[s], 0, x0 - 1, r, CIN == 64 ? img : 2 * img);
                 }
             }
             for (int k = 0; k < S && k < gin; ++k) {
@@ -686,7 +694,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
             // MMAs per run only add constant offsets.
             bool ok = mbar_wait_bounded(wbar, 0, abort, WAIT_NS);
             if (!ok) raise_abort(abort, p.err);
-            const uint64_t b_base = smem_desc_sw128(smem_u32(wsm), 0);
+            const uint64_t b_base = CIN == 64 ? smem_desc_sw128(smem_u32(wsm), 0) : smem_desc(smem_u32(wsm), LBO_B, 128);
             // Work between MMA issues leaves the tensor pipe idle once the few queued
             // MMAs have run, and an mbarrier test made while MMAs are queued costs
             // about a hundred pipe cycles.  So this thread makes no mbarrier waits per
@@ -720,7 +728,8 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         break;
                     }
                     if (o_lo <= o_hi) {
-                        const uint64_t a_base = smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0);
+                        const uint64_t a_base = CIN == 64 ? smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0)
+                                                          : smem_desc(smem_u32(stage0 + (size_t)s * ROWB), LBO_A, 128);
                         // Output rows [o_lo, o_hi] occupy one run of contiguous TMEM slots, or two
                         // where the ring wraps.  The first MMA of the row (kx = 0, K step 0) must not
                         // accumulate into the fresh row r+1, so it is issued per run of the old rows
@@ -730,7 +739,9 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         const uint32_t id0 = instr_desc(TM, 0, AFMT, AFMT);
                         const uint32_t nstep = (uint32_t)(NPR / 8) << 17;  // N += NPR
                         auto slot_of = [&](int o) { return (base + o) & (NSLOT - 1); };
-                        auto bd_of = [&](int o) { return b_base + (uint64_t)(((o - r + 1) * NPR * 128) >> 4); };
+                        auto bd_of = [&](int o) {
+                            return b_base + (uint64_t)(((o - r + 1) * NPR * (CIN == 64 ? 128 : 16)) >> 4);
+                        };
                         const int sl0 = slot_of(o_lo);
                         const int len = o_hi - o_lo + 1;
                         const int m0 = min(len, NSLOT - sl0), m1 = len - m0;
@@ -750,19 +761,24 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                                 umma<0>(tmem_base + (uint32_t)(slot_of(r + 1) * NPR), a_base, bd_of(r + 1),
                                         id0 + nstep, 0u);
                         }
+                        // (kx, K step) t: A advances one pixel per kx and 32 bytes per K step
+                        // inside the swizzled 64-channel line (CIN 64); B one kx block per kx
+                        auto a_off = [&](int t) {
+                            const int kx = t / KSTEPS, j = t % KSTEPS;
+                            return (uint64_t)((CIN == 64 ? kx * 128 + j * 32 : kx * 16) >> 4);
+                        };
+                        auto b_off = [&](int t) {
+                            const int kx = t / KSTEPS, j = t % KSTEPS;
+                            return (uint64_t)((kx * WKX + (CIN == 64 ? j * 32 : 0)) >> 4);
+                        };
                         if (m1 == 0) {
 #pragma unroll
-                            for (int t = 1; t < 12; ++t) {
-                                const int kx = t >> 2, j = t & 3;
-                                umma<0>(md0, a_base + (uint64_t)((kx * 128 + j * 32) >> 4),
-                                        mb0 + (uint64_t)((kx * WKX + j * 32) >> 4), mi0, 1u);
-                            }
+                            for (int t = 1; t < 3 * KSTEPS; ++t)
+                                umma<0>(md0, a_base + a_off(t), mb0 + b_off(t), mi0, 1u);
                         } else {
 #pragma unroll
-                            for (int t = 1; t < 12; ++t) {
-                                const int kx = t >> 2, j = t & 3;
-                                const uint64_t ad = a_base + (uint64_t)((kx * 128 + j * 32) >> 4);
-                                const uint64_t boff = (uint64_t)((kx * WKX + j * 32) >> 4);
+                            for (int t = 1; t < 3 * KSTEPS; ++t) {
+                                const uint64_t ad = a_base + a_off(t), boff = b_off(t);
                                 umma<0>(md0, ad, mb0 + boff, mi0, 1u);
                                 umma<0>(md1, ad, mb1 + boff, mi1, 1u);
                             }
@@ -1315,6 +1331,29 @@ void prepare_weights_tc(const float *w, int cout, int cin, int k, int cin_pad, i
     }
 }
 
+size_t tc_rows16_weight_bytes() { return (size_t)3 * 2 * 3 * 64 * 16; }
+
+void prepare_weights_rows16(const float *w, int cin, int dt, void *dst) {
+    uint8_t *out = static_cast<uint8_t *>(dst);
+    memset(out, 0, tc_rows16_weight_bytes());
+    // [kx][16-byte channel chunk kc][ky' = 2 - ky][64 out][8 channels], no swizzle
+    for (int n = 0; n < 64; ++n)
+        for (int c = 0; c < cin; ++c)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx) {
+                    const float v = w[((size_t)n * cin + c) * 9 + ky * 3 + kx];
+                    const size_t row = (size_t)(2 - ky) * 64 + n;
+                    const size_t off = (size_t)kx * 2 * 192 * 16 + (size_t)(c / 8) * 192 * 16 + row * 16 + (c % 8) * 2;
+                    if (dt == DT_BF16) {
+                        __nv_bfloat16 h = __float2bfloat16_rn(v);
+                        memcpy(out + off, &h, 2);
+                    } else {
+                        __half h = __float2half_rn(v);
+                        memcpy(out + off, &h, 2);
+                    }
+                }
+}
+
 size_t tc_rows_weight_bytes(int npr) { return (size_t)3 * 3 * npr * 128; }
 
 void prepare_weights_rows(const float *w, int dt, void *dst, int cout, int npr) {
@@ -1342,9 +1381,9 @@ namespace {
 // Shared memory of the row kernel: 72 KB weights, the input-row ring, 2 output
 // staging tiles and, when the layer adds a residual, 2 residual tiles (without
 // one, their room goes to deeper input prefetch).
-inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false) {
-    constexpr uint32_t ROWB = ((TM + 2) * 128 + 1023u) & ~1023u;
-    const uint32_t WB = 3 * 3 * (uint32_t)npr * 128;
+inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false, int cin = 64) {
+    const uint32_t ROWB = cin == 64 ? (((TM + 2) * 128 + 1023u) & ~1023u) : ((2 * (TM + 2) * 16 + 1023u) & ~1023u);
+    const uint32_t WB = cin == 64 ? 3 * 3 * (uint32_t)npr * 128 : 3 * 2 * 3 * (uint32_t)npr * 16;
     const uint32_t TILES = ps ? 0u : (res ? 4u : 2u) * TM * 128;
     int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES) / (int)ROWB;
     if (stages > 8) stages = 8;
@@ -1352,14 +1391,14 @@ inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false) {
     return stages;
 }
 
-template <int IN_DT, int OUT_DT, int CBO, int NPR = 64, bool PS = false>
+template <int IN_DT, int OUT_DT, int CBO, int NPR = 64, bool PS = false, int CIN = 64>
 cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUtensorMap &rmap, TcParams p,
                      cudaStream_t st) {
     int smem;
-    p.stages = rows_stages(p.res != nullptr, &smem, NPR, PS);
+    p.stages = rows_stages(p.res != nullptr, &smem, NPR, PS, CIN);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
-    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS>;
-    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS>>(smem);
+    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS, CIN>;
+    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS, CIN>>(smem);
     if (e != cudaSuccess) return e;
     RowPlan rp;
     rp.xtiles = (p.W + TM - 1) / TM;
@@ -1381,8 +1420,8 @@ cudaError_t run_rows_multi(const CUtensorMap &dummy, TcParams p, const RowProble
     int smem;
     p.stages = rows_stages(p.res != nullptr, &smem);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
-    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, true, 64, false>;
-    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, true, 64, false>>(smem);
+    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, true, 64, false, 64>;
+    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, true, 64, false, 64>>(smem);
     if (e != cudaSuccess) return e;
     RowPlan rp{};
     const int grid = std::min(total, device_sm_count());
@@ -1435,6 +1474,14 @@ bool rows_kernel_fits(const ConvArgs &a) {
     const int dt = a.in_dt;
     return a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.out_dt == dt && a.cin_pad == 64 &&
            a.cout_pad == 64 && a.cout == 64 && a.in_cpc == 64 && a.out_cpc == 64 && a.ps == 0;
+}
+
+// 3x3 layer from a 16-channel (two 16-byte chunks) 16-bit input to 64 channels.
+bool rows_head_fits(const ConvArgs &a) {
+    const int dt = a.in_dt;
+    return a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.out_dt == dt && a.cin_pad == 16 &&
+           a.in_cpc == 8 && a.cout_pad == 64 && a.cout == 64 && a.out_cpc == 64 && a.ps == 0 && !a.res && !a.y2 &&
+           !a.amax;
 }
 
 // PixelShuffle(2) output layer with 64 input channels (<= 16 outputs, planar float32).
@@ -1492,6 +1539,24 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
         const TcParams p = rows_params(a);
         return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128>(map, ymap, rmap, p, st)
                              : run_rows<DT_F16, DT_F16, 128>(map, ymap, rmap, p, st);
+    }
+    if (rows_head_fits(a)) {
+        CUtensorMap map, ymap, rmap;
+        cudaError_t e = encode_row_maps(a, &map, &ymap, &rmap);  // y (64 channels) and residual maps
+        if (e != cudaSuccess) return e;
+        auto enc = encode_fn();
+        cuuint64_t dims[4] = {16, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)(2 * a.nimg)};
+        cuuint64_t strides[3] = {16, (cuuint64_t)a.W * 16, (cuuint64_t)a.W * a.H * 16};
+        cuuint32_t box[4] = {16, (cuuint32_t)(TM + 2), 1, 2};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.x), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        TcParams p = rows_params(a);
+        p.wbytes = (uint32_t)tc_rows16_weight_bytes();
+        return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128, 64, false, 16>(map, ymap, rmap, p, st)
+                             : run_rows<DT_F16, DT_F16, 128, 64, false, 16>(map, ymap, rmap, p, st);
     }
     if (rows_ps_fits(a)) {
         ConvArgs b = a;

@@ -392,6 +392,12 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
             std::vector<uint8_t> rows(tc_rows_weight_bytes());
             prepare_weights_rows(w, f->act_dt, rows.data());
             s = upload(f, rows.data(), rows.size(), &W.rows);
+        } else if (s == NVISR_OK && L.op == "conv" && L.k == 3 && L.cin <= 16 && L.cout == 64 && !L.ps &&
+                   f->act_dt != DT_F32) {
+            // a 16-channel input (the tuple head): the row kernel's no-swizzle 16-channel form
+            std::vector<uint8_t> rows(tc_rows16_weight_bytes());
+            prepare_weights_rows16(w, L.cin, f->act_dt, rows.data());
+            s = upload(f, rows.data(), rows.size(), &W.rows);
         } else if (s == NVISR_OK && L.op == "conv" && L.k == 3 && L.cin == 64 && L.cout <= 16 && L.cout % 4 == 0) {
             // a PixelShuffle(2) output layer: the row kernel's 16-column shuffle form
             std::vector<uint8_t> rows(tc_rows_weight_bytes(16));
