@@ -30,6 +30,7 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "epilogue.cuh"
@@ -715,21 +716,27 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                 tc_fence_after();  // the MMAs of the newly ready rows come after the acquire
                 return true;
             };
-            for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
-                int img, x0, ra, rb, pi;
-                strip_of(sidx, img, x0, ra, rb, pi);
-                const int base = gout - ra;  // global index of this strip's output row o is base + o
-                for (int r = ra - 1; r <= rb && ok; ++r, ++gin) {
+            // (kx, K step) t: A advances one pixel per kx and 32 bytes per K step
+            // inside the swizzled 64-channel line (CIN 64); B one kx block per kx
+            auto a_off = [&](int t) {
+                const int kx = t / KSTEPS, j = t % KSTEPS;
+                return (uint64_t)((CIN == 64 ? kx * 128 + j * 32 : kx * 16) >> 4);
+            };
+            auto b_off = [&](int t) {
+                const int kx = t / KSTEPS, j = t % KSTEPS;
+                return (uint64_t)((kx * WKX + (CIN == 64 ? j * 32 : 0)) >> 4);
+            };
+            auto a_desc = [&]() {
+                return CIN == 64 ? smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0)
+                                 : smem_desc(smem_u32(stage0 + (size_t)s * ROWB), LBO_A, 128);
+            };
+            // Any row of a strip: runs and descriptors computed from the row's position.
+            auto generic_row = [&](int r, int base, int ra, int rb) -> bool {
                     const int o_lo = max(r - 1, ra), o_hi = min(r + 1, rb - 1);
                     const bool fresh = r + 1 <= rb - 1;
-                    if (!await_row(gin)) {
-                        raise_abort(abort, p.err);
-                        ok = false;
-                        break;
-                    }
+                    if (!await_row(gin)) return false;
                     if (o_lo <= o_hi) {
-                        const uint64_t a_base = CIN == 64 ? smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0)
-                                                          : smem_desc(smem_u32(stage0 + (size_t)s * ROWB), LBO_A, 128);
+                        const uint64_t a_base = a_desc();
                         // Output rows [o_lo, o_hi] occupy one run of contiguous TMEM slots, or two
                         // where the ring wraps.  The first MMA of the row (kx = 0, K step 0) must not
                         // accumulate into the fresh row r+1, so it is issued per run of the old rows
@@ -761,16 +768,6 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                                 umma<0>(tmem_base + (uint32_t)(slot_of(r + 1) * NPR), a_base, bd_of(r + 1),
                                         id0 + nstep, 0u);
                         }
-                        // (kx, K step) t: A advances one pixel per kx and 32 bytes per K step
-                        // inside the swizzled 64-channel line (CIN 64); B one kx block per kx
-                        auto a_off = [&](int t) {
-                            const int kx = t / KSTEPS, j = t % KSTEPS;
-                            return (uint64_t)((CIN == 64 ? kx * 128 + j * 32 : kx * 16) >> 4);
-                        };
-                        auto b_off = [&](int t) {
-                            const int kx = t / KSTEPS, j = t % KSTEPS;
-                            return (uint64_t)((kx * WKX + (CIN == 64 ? j * 32 : 0)) >> 4);
-                        };
                         if (m1 == 0) {
 #pragma unroll
                             for (int t = 1; t < 3 * KSTEPS; ++t)
@@ -792,7 +789,70 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         last_par = (uint32_t)((i >> 3) & 1);
                     }
                     if (++s == S) s = 0;
+                    ++gin;
+                    return true;
+            };
+            // An interior row (r-1 .. r+1 inside the strip) whose first output row sits in TMEM
+            // slot SL0: every run, instruction descriptor and operand offset is a compile-time
+            // constant, so issuing the row is only MMAs (rows come in aligned blocks of 8, the
+            // ring period, and the done-row parity is the block's).
+            auto fast_row = [&](auto slc, uint32_t par) -> bool {
+                constexpr int SL0 = decltype(slc)::value;
+                if (!await_row(gin)) return false;
+                const uint64_t a_base = a_desc();
+                constexpr int M0 = SL0 <= NSLOT - 3 ? 3 : NSLOT - SL0, M1 = 3 - M0;
+                constexpr int F0 = M0 >= 2 ? 2 : M0, F1 = 2 - F0;
+                constexpr uint32_t ID0 = instr_desc(TM, 0, AFMT, AFMT), NST = (uint32_t)(NPR / 8) << 17;
+                constexpr uint32_t MI0 = ID0 + NST * M0, MI1 = ID0 + NST * (M1 > 0 ? M1 : 1);
+                constexpr uint32_t BROW = NPR * (CIN == 64 ? 128 : 16);  // B bytes of one output row's taps
+                const uint32_t md0 = tmem_base + (uint32_t)(SL0 * NPR), md1 = tmem_base;
+                const uint64_t mb0 = b_base, mb1 = b_base + (uint64_t)((M0 * BROW) >> 4);
+                umma<0>(md0, a_base, mb0, ID0 + NST * F0, 1u);
+                if constexpr (F1 > 0) umma<0>(md1, a_base, mb1, ID0 + NST * F1, 1u);
+                umma<0>(tmem_base + (uint32_t)(((SL0 + 2) & (NSLOT - 1)) * NPR), a_base,
+                        b_base + (uint64_t)((2 * BROW) >> 4), ID0 + NST, 0u);
+#pragma unroll
+                for (int t = 1; t < 3 * KSTEPS; ++t) {
+                    const uint64_t ad = a_base + a_off(t), boff = b_off(t);
+                    umma<0>(md0, ad, mb0 + boff, MI0, 1u);
+                    if constexpr (M1 > 0) umma<0>(md1, ad, mb1 + boff, MI1, 1u);
                 }
+                umma_commit(&empty[s]);
+                umma_commit(&rowdone[SL0]);
+                last_slot = SL0;
+                last_par = par;
+                if (++s == S) s = 0;
+                ++gin;
+                return true;
+            };
+            using I0 = std::integral_constant<int, 0>;
+            using I1 = std::integral_constant<int, 1>;
+            using I2 = std::integral_constant<int, 2>;
+            using I3 = std::integral_constant<int, 3>;
+            using I4 = std::integral_constant<int, 4>;
+            using I5 = std::integral_constant<int, 5>;
+            using I6 = std::integral_constant<int, 6>;
+            using I7 = std::integral_constant<int, 7>;
+            for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
+                int img, x0, ra, rb, pi;
+                strip_of(sidx, img, x0, ra, rb, pi);
+                const int base = gout - ra;  // global index of this strip's output row o is base + o
+                int r = ra - 1;
+                while (r <= rb && ok) {
+                    // (measured: the unrolled form pays for the 16-column shuffle tail; for the
+                    // 64-column rows the larger code slowed the issue, so those stay generic)
+                    if (NPR == 16 && r >= ra + 1 && ((base + r - 1) & (NSLOT - 1)) == 0 && r + 7 <= rb - 2) {
+                        const uint32_t par = (uint32_t)(((base + r - 1) >> 3) & 1);
+                        ok = fast_row(I0{}, par) && fast_row(I1{}, par) && fast_row(I2{}, par) &&
+                             fast_row(I3{}, par) && fast_row(I4{}, par) && fast_row(I5{}, par) &&
+                             fast_row(I6{}, par) && fast_row(I7{}, par);
+                        r += 8;
+                    } else {
+                        ok = generic_row(r, base, ra, rb);
+                        ++r;
+                    }
+                }
+                if (!ok) raise_abort(abort, p.err);
                 gout += rb - ra;
             }
             if (last_slot >= 0) mbar_wait_bounded(&rowdone[last_slot], last_par, nullptr, WAIT_NS);
