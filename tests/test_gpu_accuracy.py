@@ -1,0 +1,71 @@
+"""Accuracy report of the reduced-precision paths on the config-2 network (ragged
+136x70 clip with a scene cut): codes identical to the FP32 GPU path, max LSB
+and PSNR against the FP64 oracle.  Asserts the bounds the other tests hold
+(BF16 / FP16 within 1 LSB of the oracle, FP8 within 16) and prints the rest."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2308_03121_gb300 as nv
+import synth
+from gpu_util import fmt_dict
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nv.load()
+
+
+def _run(text, blob, frames, flags, W, H, prec):
+    eng = nv.Engine()
+    flt = eng.filter(text, blob, nv.fmt(W, H, 10), nv.fmt(2 * W, 2 * H, 10), prec, 2)
+    outs = []
+
+    def pull():
+        res = flt.alloc_out_host()
+        st, _ = flt.pull(res)
+        if st == nv.Status.OK:
+            outs.append({k: r.astype(np.int64) for k, r in zip("YUV", res)})
+        return st
+
+    for i, fr in enumerate(frames):
+        while flt.push((fr["Y"], fr["U"], fr["V"]), cut=bool(flags[i])) == nv.Status.FULL:
+            assert pull() == nv.Status.OK
+    flt.flush()
+    while pull() == nv.Status.OK:
+        pass
+    eng.close()
+    return outs
+
+
+def _psnr(a, b, peak):
+    mse = np.mean((a.astype(np.float64) - b) ** 2)
+    return float("inf") if mse == 0 else 10 * np.log10(peak * peak / mse)
+
+
+def test_precision_report():
+    W, H = 136, 70
+    frames = synth.frames_textured(synth.BASE_SEED + 2, 6, W, H, 10, "420", "limited")
+    flags = np.zeros(6, bool)
+    flags[3] = True
+    text, blob = synth.net_config2()
+    ref = oracle.run_filter(frames, flags, text, blob, fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10))
+    outs = {p: _run(text, blob, frames, flags, W, H, p) for p in ("fp32", "bf16", "fp16", "fp8")}
+    for prec in ("fp32", "bf16", "fp16", "fp8"):
+        same = total = 0
+        worst = 0
+        psnrs = []
+        for got, g32, r in zip(outs[prec], outs["fp32"], ref):
+            for k in "YUV":
+                same += int((got[k] == g32[k]).sum())
+                total += got[k].size
+                worst = max(worst, int(np.abs(got[k] - r[k]).max()))
+            psnrs.append(_psnr(got["Y"], r["Y"], 1023))
+        print(f"{prec}: identical to FP32 GPU {same / total:.4%}, max |LSB| vs oracle {worst}, "
+              f"luma PSNR vs oracle {min(psnrs):.1f} dB")
+        assert worst <= (16 if prec == "fp8" else 1), (prec, worst)
