@@ -47,7 +47,7 @@ NFRAMES = 12                                   # distinct resident input frames,
 # DRAM bytes per conv_body launch (mean of a launch with and one without residual)
 # from an ncu capture of the current kernel (profiles/conv_rows_bf16_1080p.md);
 # None until captured for this version.
-CONV_BODY_TRAFFIC = 620.4e6
+CONV_BODY_TRAFFIC = None
 WORKLOAD = ("1080p->4K 2x SR: sliding window T=5, conv 15->64, 10 residual blocks of 64 ch, conv 64->12, "
             "PixelShuffle(2), bilinear skip; 10-bit 4:2:0 limited BT.709 in and out")
 DATA = "synthetic: seeded textured 10-bit 4:2:0 frames with global 0-4 px translation; random-init He-normal weights"

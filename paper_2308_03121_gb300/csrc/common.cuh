@@ -134,7 +134,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st);
 
 // One image of a batched 64 -> 64 3x3 row-streaming launch: its tensor maps (in
 // global memory, 64-byte aligned) and its strips [strip0, strip0 + nstrips).
-struct alignas(64) RowProblem {
+struct RowProblem {  // aligned as its tensor maps (at least 64 bytes)
     CUtensorMap tmap, ymap, rmap;
     int H, W, xtiles, rps, strip0, nstrips, has_res, pad_;
 };

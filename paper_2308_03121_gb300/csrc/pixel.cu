@@ -139,13 +139,14 @@ __global__ void __launch_bounds__(256) ingest_kernel(
     }
 }
 
-// 4:2:0 ingest, one thread per 2 luma rows x 8 columns (one chroma row, 4
-// chroma columns): the chroma rows j-1 .. j+1 and columns 4q-1 .. 4q+4 the
-// block needs are read once into registers (normalised), then every luma
-// sample's chroma is interpolated from them in the same order as the scalar
-// form (vertical, then horizontal), and the three planes are written with
-// 16-byte stores.  Divisions are replaced by multiplications with the
-// reciprocal.
+// 4:2:0 ingest, one thread per luma row 2j + blockIdx.z and 8 columns (4 chroma
+// columns): the chroma rows j-1 .. j+1 and columns 4q-1 .. 4q+4 it needs are
+// read into registers (normalised), then every luma sample's chroma is
+// interpolated from them in the same order as the scalar form (vertical, then
+// horizontal), and the three planes are written with 16-byte stores.
+// Divisions are replaced by multiplications with the reciprocal.  (One row
+// per thread rather than the chroma row's two doubles the threads of this
+// short, latency-bound pass; the repeated chroma reads hit L2.)
 template <typename S>
 __global__ void __launch_bounds__(128) ingest420_kernel(
     const uint8_t *__restrict__ yp, int64_t py, const uint8_t *__restrict__ up, int64_t pu,
@@ -197,10 +198,10 @@ __global__ void __launch_bounds__(128) ingest420_kernel(
     }
     const int64_t plane = pitch * H;
     const bool vec = x0 + 8 <= W && (pitch & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
+    {
+        const int a = blockIdx.z;
         const int y = 2 * j + a;
-        if (y >= H) break;
+        if (y >= H) return;
         // vertical interpolation: luma row 2j uses chroma rows (j, j-1), row 2j+1 uses (j, j+1)
         float vu[6], vvv[6];
 #pragma unroll
@@ -669,7 +670,7 @@ cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, cons
     const RangeConst rc = range_const(f.bit_depth, f.range);
     if (f.subsampling == NVISR_SUB_420) {
         dim3 blk(128);
-        dim3 grd((f.width + 8 * 128 - 1) / (8 * 128), (f.height + 1) / 2);
+        dim3 grd((f.width + 8 * 128 - 1) / (8 * 128), (f.height + 1) / 2, 2);
         if (f.bit_depth <= 8)
             ingest420_kernel<uint8_t><<<grd, blk, 0, st>>>((const uint8_t *)y, py, (const uint8_t *)u, pu,
                                                           (const uint8_t *)v, pv, f.height, f.width, f.chroma_loc,
