@@ -8,14 +8,15 @@
 // with out-of-image bilinear corners contributing zero.
 //
 // Kernel: one CTA per SM walks 128-pixel row tiles.  For each tile and tap,
-// four producer warps (one thread per pixel) read the tap's offsets and mask,
-// gather the four bilinear corners of every 8-channel group as 16-byte loads
-// from the blocked feature map, blend them in FP32, scale by the mask and
-// store the result as one 16-byte row of the canonical no-swizzle K-major
-// A tile in shared memory (the sampled im2col tile of that tap).  A single
-// thread issues the tap's tcgen05.mma's against the resident weights into a
-// double-buffered TMEM accumulator; four epilogue warps add the bias and store
-// the blocked output.  Every wait is bounded in time.
+// eight producer warps (two threads per pixel, each taking half of the
+// 8-channel groups) read the tap's offsets and mask, issue the four bilinear
+// corner loads of all their channel groups before using any (so many gathers
+// are in flight at once), blend them in FP32, scale by the mask and store
+// 16-byte rows of the canonical no-swizzle K-major A tile in shared memory
+// (the sampled im2col tile of that tap).  A single thread issues the tap's
+// tcgen05.mma's against the resident weights into a double-buffered TMEM
+// accumulator; four epilogue warps add the bias and store the blocked
+// output.  Every wait is bounded in time.
 #include "common.cuh"
 #include "sm100_ptx.cuh"
 
@@ -24,7 +25,9 @@ namespace nvisr {
 namespace {
 
 constexpr int TM = 128;
-constexpr int NT = 288;  // warps 0-3 gather, warp 4 MMA/TMEM/weights, warps 5-8 epilogue
+constexpr int NT = 416;        // warps 0-7 gather, warp 8 MMA/TMEM/weights, warps 9-12 epilogue
+constexpr int NGATHER = 256;   // gather threads (two per pixel)
+constexpr int MMA_WARP = 8;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 232448;
 
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 128);
+            mbar_init(&full[s], NGATHER);
             mbar_init(&empty[s], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
         *abort = 0;
         fence_mbarrier_init();
     }
-    if (warp == 4) {
+    if (warp == MMA_WARP) {
         tmem_alloc(tmem_slot, NCOLS);
         tmem_relinquish();
     }
@@ -97,11 +100,14 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp < 4) {
+    if (warp < NGATHER / 32) {
         // ------------------------------------------------ gather producers
-        const int m = threadIdx.x;  // pixel within the tile
+        constexpr int CPT = NCH / 2;                 // channel groups per thread
+        const int m = threadIdx.x & (TM - 1);        // pixel within the tile
+        const int half = threadIdx.x >> 7;           // which half of the channel groups
         const uint8_t *x = static_cast<const uint8_t *>(a.x);
         const int cpg = a.cin_pad / a.groups;
+        const int G = a.groups;
         int s = 0;
         uint32_t ph = 0;
         bool ok = true;
@@ -118,51 +124,72 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                     break;
                 }
                 uint8_t *dst = stage0 + (size_t)s * STAGE + (size_t)m * 16;
-#pragma unroll 2
-                for (int cc = 0; cc < NCH; ++cc) {
-                    alignas(16) T o[CPC];
-                    if (valid) {
-                        const int g = (cc * CPC) / cpg;
-                        auto omv = [&](int ch) { return a.om[((int64_t)(ch >> 2) * HW + pix) * 4 + (ch & 3)]; };
-                        const float dy = omv(2 * (g * 9 + k));
-                        const float dx = omv(2 * (g * 9 + k) + 1);
-                        float msk = omv(18 * a.groups + g * 9 + k);
-                        if (a.mask_logits) msk = 1.f / (1.f + expf(-msk));
-                        const float sy = (float)(y + k / 3 - 1) + dy;
-                        const float sx = (float)(xx + k % 3 - 1) + dx;
+                if (valid) {
+                    // offsets (dy, dx are adjacent channels of one 4-channel unit) and mask of
+                    // each of this thread's channel groups for tap k
+                    float dy[CPT], dx[CPT], msk[CPT];
+#pragma unroll
+                    for (int i = 0; i < CPT; ++i) {
+                        const int g = ((half * CPT + i) * CPC) / cpg;
+                        const int cd = 2 * (g * 9 + k);
+                        const float2 d = __ldg(reinterpret_cast<const float2 *>(
+                            a.om + ((int64_t)(cd >> 2) * HW + pix) * 4 + (cd & 3)));
+                        dy[i] = d.x;
+                        dx[i] = d.y;
+                        const int cm = 18 * G + g * 9 + k;
+                        msk[i] = __ldg(a.om + ((int64_t)(cm >> 2) * HW + pix) * 4 + (cm & 3));
+                    }
+                    // every corner load of every group first, then the blends
+                    uint4 v[CPT][4];
+                    float wq[CPT][4];
+#pragma unroll
+                    for (int i = 0; i < CPT; ++i) {
+                        const int c0 = (half * CPT + i) * CPC;
+                        const uint8_t *plane = x + (int64_t)(c0 / xcpc) * HW * xcpc * 2 + (c0 % xcpc) * 2;
+                        const float sy = (float)(y + k / 3 - 1) + dy[i];
+                        const float sx = (float)(xx + k % 3 - 1) + dx[i];
                         const float fy = floorf(sy), fx = floorf(sx);
                         const int y0 = (int)fy, x0 = (int)fx;
                         const float ly = sy - fy, lx = sx - fx;
-                        float acc[CPC];
-#pragma unroll
-                        for (int e = 0; e < CPC; ++e) acc[e] = 0.f;
-                        const int c0 = cc * CPC;
-                        const uint8_t *plane = x + (int64_t)(c0 / xcpc) * HW * xcpc * 2 + (c0 % xcpc) * 2;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int yy = y0 + (q >> 1), xq = x0 + (q & 1);
-                            if (yy < 0 || yy >= H || xq < 0 || xq >= W) continue;
-                            const float wgt = ((q >> 1) ? ly : 1.f - ly) * ((q & 1) ? lx : 1.f - lx);
-                            alignas(16) T v[CPC];
-                            *reinterpret_cast<uint4 *>(v) =
-                                __ldg(reinterpret_cast<const uint4 *>(plane + ((int64_t)yy * W + xq) * xcpc * 2));
-#pragma unroll
-                            for (int e = 0; e < CPC; ++e) acc[e] += wgt * Cv<T>::in(v[e]);
+                            const bool in = yy >= 0 && yy < H && xq >= 0 && xq < W;
+                            wq[i][q] = in ? ((q >> 1) ? ly : 1.f - ly) * ((q & 1) ? lx : 1.f - lx) : 0.f;
+                            v[i][q] = in ? __ldg(reinterpret_cast<const uint4 *>(plane + ((int64_t)yy * W + xq) * xcpc * 2))
+                                         : make_uint4(0u, 0u, 0u, 0u);
                         }
-#pragma unroll
-                        for (int e = 0; e < CPC; ++e) o[e] = Cv<T>::out(acc[e] * msk);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < CPC; ++e) o[e] = Cv<T>::out(0.f);
                     }
-                    *reinterpret_cast<uint4 *>(dst + (size_t)cc * LBO) = *reinterpret_cast<const uint4 *>(o);
+#pragma unroll
+                    for (int i = 0; i < CPT; ++i) {
+                        float acc[CPC];
+#pragma unroll
+                        for (int e = 0; e < CPC; ++e) acc[e] = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const T *vv = reinterpret_cast<const T *>(&v[i][q]);
+#pragma unroll
+                            for (int e = 0; e < CPC; ++e) acc[e] += wq[i][q] * Cv<T>::in(vv[e]);
+                        }
+                        float mm = msk[i];
+                        if (a.mask_logits) mm = 1.f / (1.f + expf(-mm));
+                        alignas(16) T o[CPC];
+#pragma unroll
+                        for (int e = 0; e < CPC; ++e) o[e] = Cv<T>::out(acc[e] * mm);
+                        *reinterpret_cast<uint4 *>(dst + (size_t)(half * CPT + i) * LBO) =
+                            *reinterpret_cast<const uint4 *>(o);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < CPT; ++i)
+                        *reinterpret_cast<uint4 *>(dst + (size_t)(half * CPT + i) * LBO) = make_uint4(0u, 0u, 0u, 0u);
                 }
                 fence_proxy_async();  // generic smem writes -> visible to the tensor core
                 mbar_arrive(&full[s]);
                 if (++s == S) { s = 0; ph ^= 1; }
             }
         }
-    } else if (warp == 4) {
+    } else if (warp == MMA_WARP) {
         if (lane == 0) {
             // ------------------------------------------------ weights + MMA issue
             mbar_arrive_expect_tx(wbar, wbytes);
@@ -213,7 +240,7 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
             mbar_wait_bounded(wbar, 0, nullptr, WAIT_NS);
         }
     } else {
-        // ------------------------------------------------ epilogue (warps 5..8)
+        // ------------------------------------------------ epilogue (warps 9..12, one per lane quadrant)
         const int q = warp & 3;
         const int m = q * 32 + lane;
         uint8_t *yb = static_cast<uint8_t *>(a.y);
@@ -258,7 +285,7 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
         }
     }
     __syncthreads();
-    if (warp == 4) {
+    if (warp == MMA_WARP) {
         __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem_base, NCOLS);
