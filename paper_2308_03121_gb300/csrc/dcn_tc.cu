@@ -8,8 +8,8 @@
 // with out-of-image bilinear corners contributing zero.
 //
 // Kernel: one CTA per SM walks 128-pixel row tiles.  For each tile and tap,
-// eight producer warps (two threads per pixel, each taking half of the
-// 8-channel groups) read the tap's offsets and mask, issue the four bilinear
+// sixteen producer warps (four threads per pixel, each taking a quarter of
+// the 8-channel groups) read the tap's offsets and mask, issue the four bilinear
 // corner loads of all their channel groups before using any (so many gathers
 // are in flight at once), blend them in FP32, scale by the mask and store
 // 16-byte rows of the canonical no-swizzle K-major A tile in shared memory
@@ -25,9 +25,9 @@ namespace nvisr {
 namespace {
 
 constexpr int TM = 128;
-constexpr int NT = 416;        // warps 0-7 gather, warp 8 MMA/TMEM/weights, warps 9-12 epilogue
-constexpr int NGATHER = 256;   // gather threads (two per pixel)
-constexpr int MMA_WARP = 8;
+constexpr int NGATHER = 512;            // gather threads (four per pixel)
+constexpr int MMA_WARP = NGATHER / 32;  // then the MMA / TMEM / weights warp, then 4 epilogue warps
+constexpr int NT = NGATHER + 32 + 128;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 232448;
 
@@ -102,20 +102,24 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
 
     if (warp < NGATHER / 32) {
         // ------------------------------------------------ gather producers
-        constexpr int CPT = NCH / 2;                 // channel groups per thread
-        const int m = threadIdx.x & (TM - 1);        // pixel within the tile
-        const int half = threadIdx.x >> 7;           // which half of the channel groups
+        // thread = (8-channel group cc, pixel): the 8 threads of a pixel read the
+        // pixel's 128-byte channel line of a corner together (full-line loads)
+        constexpr int PPP = NGATHER / NCH;           // pixels per pass
+        constexpr int NPASS = TM / PPP;              // passes over the tile's pixels
+        static_assert(NGATHER % NCH == 0 && TM % PPP == 0, "gather mapping");
+        const int cc = threadIdx.x % NCH;            // channel group (16-byte chunk)
+        const int mp = threadIdx.x / NCH;            // pixel within a pass
         const uint8_t *x = static_cast<const uint8_t *>(a.x);
         const int cpg = a.cin_pad / a.groups;
         const int G = a.groups;
+        const int g = (cc * CPC) / cpg;
+        const uint8_t *plane = x + (int64_t)((cc * CPC) / xcpc) * HW * xcpc * 2 + ((cc * CPC) % xcpc) * 2;
         int s = 0;
         uint32_t ph = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int y = t / tiles_x;
-            const int xx = (t - y * tiles_x) * TM + m;
-            const bool valid = xx < W;
-            const int64_t pix = (int64_t)y * W + (valid ? xx : 0);
+            const int xb = (t - y * tiles_x) * TM;
             for (int k = 0; k < 9; ++k) {
                 if (!mbar_wait_bounded(&empty[s], ph ^ 1, abort, WAIT_NS)) {
                     *abort = 1;
@@ -123,66 +127,57 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                     ok = false;
                     break;
                 }
-                uint8_t *dst = stage0 + (size_t)s * STAGE + (size_t)m * 16;
-                if (valid) {
-                    // offsets (dy, dx are adjacent channels of one 4-channel unit) and mask of
-                    // each of this thread's channel groups for tap k
-                    float dy[CPT], dx[CPT], msk[CPT];
+                uint8_t *stg = stage0 + (size_t)s * STAGE + (size_t)cc * LBO;
+                const int cd = 2 * (g * 9 + k), cm = 18 * G + g * 9 + k;
+                // offsets (dy, dx adjacent in one 4-channel unit) and mask of every pass's pixel
+                float dy[NPASS], dx[NPASS], msk[NPASS];
 #pragma unroll
-                    for (int i = 0; i < CPT; ++i) {
-                        const int g = ((half * CPT + i) * CPC) / cpg;
-                        const int cd = 2 * (g * 9 + k);
-                        const float2 d = __ldg(reinterpret_cast<const float2 *>(
-                            a.om + ((int64_t)(cd >> 2) * HW + pix) * 4 + (cd & 3)));
-                        dy[i] = d.x;
-                        dx[i] = d.y;
-                        const int cm = 18 * G + g * 9 + k;
-                        msk[i] = __ldg(a.om + ((int64_t)(cm >> 2) * HW + pix) * 4 + (cm & 3));
+                for (int h = 0; h < NPASS; ++h) {
+                    const int xx = xb + mp + h * PPP;
+                    const int64_t pix = (int64_t)y * W + min(xx, W - 1);
+                    const float2 d = __ldg(reinterpret_cast<const float2 *>(
+                        a.om + ((int64_t)(cd >> 2) * HW + pix) * 4 + (cd & 3)));
+                    dy[h] = d.x;
+                    dx[h] = d.y;
+                    msk[h] = __ldg(a.om + ((int64_t)(cm >> 2) * HW + pix) * 4 + (cm & 3));
+                }
+                // every corner load of every pass first, then the blends
+                uint4 v[NPASS][4];
+                float wq[NPASS][4];
+#pragma unroll
+                for (int h = 0; h < NPASS; ++h) {
+                    const int xx = xb + mp + h * PPP;
+                    const float sy = (float)(y + k / 3 - 1) + dy[h];
+                    const float sx = (float)(xx + k % 3 - 1) + dx[h];
+                    const float fy = floorf(sy), fx = floorf(sx);
+                    const int y0 = (int)fy, x0 = (int)fx;
+                    const float ly = sy - fy, lx = sx - fx;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int yy = y0 + (q >> 1), xq = x0 + (q & 1);
+                        const bool in = xx < W && yy >= 0 && yy < H && xq >= 0 && xq < W;
+                        wq[h][q] = in ? ((q >> 1) ? ly : 1.f - ly) * ((q & 1) ? lx : 1.f - lx) : 0.f;
+                        v[h][q] = in ? __ldg(reinterpret_cast<const uint4 *>(plane + ((int64_t)yy * W + xq) * xcpc * 2))
+                                     : make_uint4(0u, 0u, 0u, 0u);
                     }
-                    // every corner load of every group first, then the blends
-                    uint4 v[CPT][4];
-                    float wq[CPT][4];
+                }
 #pragma unroll
-                    for (int i = 0; i < CPT; ++i) {
-                        const int c0 = (half * CPT + i) * CPC;
-                        const uint8_t *plane = x + (int64_t)(c0 / xcpc) * HW * xcpc * 2 + (c0 % xcpc) * 2;
-                        const float sy = (float)(y + k / 3 - 1) + dy[i];
-                        const float sx = (float)(xx + k % 3 - 1) + dx[i];
-                        const float fy = floorf(sy), fx = floorf(sx);
-                        const int y0 = (int)fy, x0 = (int)fx;
-                        const float ly = sy - fy, lx = sx - fx;
+                for (int h = 0; h < NPASS; ++h) {
+                    float acc[CPC];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int yy = y0 + (q >> 1), xq = x0 + (q & 1);
-                            const bool in = yy >= 0 && yy < H && xq >= 0 && xq < W;
-                            wq[i][q] = in ? ((q >> 1) ? ly : 1.f - ly) * ((q & 1) ? lx : 1.f - lx) : 0.f;
-                            v[i][q] = in ? __ldg(reinterpret_cast<const uint4 *>(plane + ((int64_t)yy * W + xq) * xcpc * 2))
-                                         : make_uint4(0u, 0u, 0u, 0u);
-                        }
+                    for (int e = 0; e < CPC; ++e) acc[e] = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const T *vv = reinterpret_cast<const T *>(&v[h][q]);
+#pragma unroll
+                        for (int e = 0; e < CPC; ++e) acc[e] += wq[h][q] * Cv<T>::in(vv[e]);
                     }
+                    float mm = msk[h];
+                    if (a.mask_logits) mm = 1.f / (1.f + expf(-mm));
+                    alignas(16) T o[CPC];
 #pragma unroll
-                    for (int i = 0; i < CPT; ++i) {
-                        float acc[CPC];
-#pragma unroll
-                        for (int e = 0; e < CPC; ++e) acc[e] = 0.f;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const T *vv = reinterpret_cast<const T *>(&v[i][q]);
-#pragma unroll
-                            for (int e = 0; e < CPC; ++e) acc[e] += wq[i][q] * Cv<T>::in(vv[e]);
-                        }
-                        float mm = msk[i];
-                        if (a.mask_logits) mm = 1.f / (1.f + expf(-mm));
-                        alignas(16) T o[CPC];
-#pragma unroll
-                        for (int e = 0; e < CPC; ++e) o[e] = Cv<T>::out(acc[e] * mm);
-                        *reinterpret_cast<uint4 *>(dst + (size_t)(half * CPT + i) * LBO) =
-                            *reinterpret_cast<const uint4 *>(o);
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < CPT; ++i)
-                        *reinterpret_cast<uint4 *>(dst + (size_t)(half * CPT + i) * LBO) = make_uint4(0u, 0u, 0u, 0u);
+                    for (int e = 0; e < CPC; ++e) o[e] = Cv<T>::out(acc[e] * mm);
+                    *reinterpret_cast<uint4 *>(stg + (size_t)(mp + h * PPP) * 16) = *reinterpret_cast<const uint4 *>(o);
                 }
                 fence_proxy_async();  // generic smem writes -> visible to the tensor core
                 mbar_arrive(&full[s]);
@@ -240,7 +235,7 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
             mbar_wait_bounded(wbar, 0, nullptr, WAIT_NS);
         }
     } else {
-        // ------------------------------------------------ epilogue (warps 9..12, one per lane quadrant)
+        // ------------------------------------------------ epilogue (the last 4 warps, one per lane quadrant)
         const int q = warp & 3;
         const int m = q * 32 + lane;
         uint8_t *yb = static_cast<uint8_t *>(a.y);
