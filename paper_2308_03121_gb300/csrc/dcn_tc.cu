@@ -117,10 +117,31 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
         int s = 0;
         uint32_t ph = 0;
         bool ok = true;
+        // offsets (dy, dx adjacent in one 4-channel unit) and mask of every pass's pixel
+        // for tap k; the next tap's are loaded while this tap's corners are in flight
+        auto load_om = [&](int y, int xb, int k, float2 (&d)[NPASS], float (&mk)[NPASS]) {
+            const int cd = 2 * (g * 9 + k), cm = 18 * G + g * 9 + k;
+#pragma unroll
+            for (int h = 0; h < NPASS; ++h) {
+                const int64_t pix = (int64_t)y * W + min(xb + mp + h * PPP, W - 1);
+                d[h] = __ldg(reinterpret_cast<const float2 *>(a.om + ((int64_t)(cd >> 2) * HW + pix) * 4 + (cd & 3)));
+                mk[h] = __ldg(a.om + ((int64_t)(cm >> 2) * HW + pix) * 4 + (cm & 3));
+            }
+        };
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int y = t / tiles_x;
             const int xb = (t - y * tiles_x) * TM;
+            float2 dn[NPASS];
+            float mn[NPASS];
+            load_om(y, xb, 0, dn, mn);
             for (int k = 0; k < 9; ++k) {
+                float dy[NPASS], dx[NPASS], msk[NPASS];
+#pragma unroll
+                for (int h = 0; h < NPASS; ++h) {
+                    dy[h] = dn[h].x;
+                    dx[h] = dn[h].y;
+                    msk[h] = mn[h];
+                }
                 if (!mbar_wait_bounded(&empty[s], ph ^ 1, abort, WAIT_NS)) {
                     *abort = 1;
                     if (a.err) atomicExch(a.err, DEVERR_TIMEOUT);
@@ -128,19 +149,6 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                     break;
                 }
                 uint8_t *stg = stage0 + (size_t)s * STAGE + (size_t)cc * LBO;
-                const int cd = 2 * (g * 9 + k), cm = 18 * G + g * 9 + k;
-                // offsets (dy, dx adjacent in one 4-channel unit) and mask of every pass's pixel
-                float dy[NPASS], dx[NPASS], msk[NPASS];
-#pragma unroll
-                for (int h = 0; h < NPASS; ++h) {
-                    const int xx = xb + mp + h * PPP;
-                    const int64_t pix = (int64_t)y * W + min(xx, W - 1);
-                    const float2 d = __ldg(reinterpret_cast<const float2 *>(
-                        a.om + ((int64_t)(cd >> 2) * HW + pix) * 4 + (cd & 3)));
-                    dy[h] = d.x;
-                    dx[h] = d.y;
-                    msk[h] = __ldg(a.om + ((int64_t)(cm >> 2) * HW + pix) * 4 + (cm & 3));
-                }
                 // every corner load of every pass first, then the blends
                 uint4 v[NPASS][4];
                 float wq[NPASS][4];
@@ -161,6 +169,7 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                                      : make_uint4(0u, 0u, 0u, 0u);
                     }
                 }
+                if (k < 8) load_om(y, xb, k + 1, dn, mn);
 #pragma unroll
                 for (int h = 0; h < NPASS; ++h) {
                     float acc[CPC];
