@@ -170,14 +170,24 @@ void prepare_weights_rows16(const float *w_oihw, int cin, int dt, void *dst_host
 void prepare_weights_rows(const float *w_oihw, int dt, void *dst_host, int cout = 64, int npr = 64);
 
 // DCN: x blocked (activation dtype); offsets and mask in one blocked float32
-// tensor [om_cpad/4][H][W][4]: channels [0, 18G) = (dy, dx) per (group, tap),
-// [18G, 27G) = mask (logits when mask_logits, else already in [0,1]).
+// tensor [om_cpad/4][H][W][4].  Channel order: torchvision's ([0, 18G) = (dy, dx)
+// per (group, tap), [18G, 27G) = mask per (group, tap)), or tap-major (for tap
+// k a block of 3G channels: (dy, dx) of each group, then each group's mask),
+// which puts all of a tap's offsets and masks in 3G/4 adjacent 4-channel
+// planes.  Masks are logits when mask_logits, else already in [0,1].
+__host__ __device__ inline int dcn_off_channel(int g, int k, int G, bool tap_major) {
+    return tap_major ? 3 * G * k + 2 * g : 2 * (g * 9 + k);
+}
+__host__ __device__ inline int dcn_mask_channel(int g, int k, int G, bool tap_major) {
+    return tap_major ? 3 * G * k + 2 * G + g : 18 * G + g * 9 + k;
+}
 struct DcnArgs {
     const void *x;
     int cin_pad, H, W, groups;
     int x_cpc, y_cpc;        // channels per chunk of x and y (0 = 16-byte units)
     const float *om;
     int om_cpad;
+    int om_tap_major;        // channel order of om (tap-major needs an even G)
     int mask_logits;
     const void *w;           // prepared weights (SIMT or TC layout, k = 3)
     const float *bias;
@@ -189,6 +199,9 @@ struct DcnArgs {
 };
 cudaError_t launch_dcn_simt(const DcnArgs &a, cudaStream_t st);
 cudaError_t launch_dcn_tc(const DcnArgs &a, cudaStream_t st);
+// Copies a 16-bit activation from the blocked layout with x_cpc channels per
+// chunk into 8-channel planes [cpad/8][H][W][8] (the DCN gather's layout).
+cudaError_t launch_dcn_relayout8(const void *x, int cpad, int H, int W, int x_cpc, void *y, cudaStream_t st);
 
 int device_sm_count();
 

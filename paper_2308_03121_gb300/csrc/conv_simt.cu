@@ -114,9 +114,10 @@ __global__ void __launch_bounds__(16 * NB / 4) conv_simt_kernel(ConvArgs a, DcnA
                     const int g = c / cpg;
                     const int64_t pix = (int64_t)y * W + xx;
                     auto omv = [&](int ch) { return d.om[((int64_t)(ch >> 2) * HW + pix) * 4 + (ch & 3)]; };
-                    const float dy = omv(2 * (g * 9 + k));
-                    const float dx = omv(2 * (g * 9 + k) + 1);
-                    float m = omv(18 * d.groups + g * 9 + k);
+                    const int cd = dcn_off_channel(g, k, d.groups, d.om_tap_major != 0);
+                    const float dy = omv(cd);
+                    const float dx = omv(cd + 1);
+                    float m = omv(dcn_mask_channel(g, k, d.groups, d.om_tap_major != 0));
                     if (d.mask_logits) m = 1.f / (1.f + expf(-m));
                     const float sy = (float)(y + k / 3 - 1) + dy;
                     const float sx = (float)(xx + k % 3 - 1) + dx;

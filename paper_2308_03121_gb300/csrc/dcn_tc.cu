@@ -8,15 +8,17 @@
 // with out-of-image bilinear corners contributing zero.
 //
 // Kernel: one CTA per SM walks 128-pixel row tiles.  For each tile and tap,
-// sixteen producer warps (four threads per pixel, each taking a quarter of
-// the 8-channel groups) read the tap's offsets and mask, issue the four bilinear
-// corner loads of all their channel groups before using any (so many gathers
-// are in flight at once), blend them in FP32, scale by the mask and store
-// 16-byte rows of the canonical no-swizzle K-major A tile in shared memory
-// (the sampled im2col tile of that tap).  A single thread issues the tap's
+// sixteen producer warps (a warp per 8-channel chunk and half tile, a lane pair
+// per pixel) read the tap's offsets and mask, issue the bilinear corner loads
+// of all their pixels before using any (so many gathers are in flight at
+// once), blend them in FP32, scale by the mask and store 8-byte halves of the
+// 16-byte rows of the canonical no-swizzle K-major A tile in shared memory (the
+// sampled im2col tile of that tap).  A single thread issues the tap's
 // tcgen05.mma's against the resident weights into a double-buffered TMEM
-// accumulator; four epilogue warps add the bias and store the blocked
-// output.  Every wait is bounded in time.
+// accumulator; four epilogue warps add the bias and store the blocked output.
+// Every wait is bounded in time.  x is best given in 8-channel planes
+// (launch_dcn_relayout8), where the two columns of a bilinear corner pair share
+// a cache line; any supported layout gives the same result.
 #include "common.cuh"
 #include "sm100_ptx.cuh"
 
@@ -25,9 +27,9 @@ namespace nvisr {
 namespace {
 
 constexpr int TM = 128;
-constexpr int NGATHER = 512;            // gather threads (four per pixel)
-constexpr int MMA_WARP = NGATHER / 32;  // then the MMA / TMEM / weights warp, then 4 epilogue warps
-constexpr int NT = NGATHER + 32 + 128;
+constexpr int NGATHER = 512;            // gather threads (a lane pair per pixel and chunk)
+constexpr int MMA_WARP = NGATHER / 32;  // then 4 epilogue warps, the first also loads the weights and issues the MMAs
+constexpr int NT = NGATHER + 128;       // 20 warps: 5 per SM sub-partition leaves 96 registers a thread
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 232448;
 
@@ -102,164 +104,205 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
 
     if (warp < NGATHER / 32) {
         // ------------------------------------------------ gather producers
-        // thread = (8-channel group cc, pixel): the 8 threads of a pixel read the
-        // pixel's 128-byte channel line of a corner together (full-line loads)
-        constexpr int PPP = NGATHER / NCH;           // pixels per pass
-        constexpr int NPASS = TM / PPP;              // passes over the tile's pixels
-        static_assert(NGATHER % NCH == 0 && TM % PPP == 0, "gather mapping");
-        const int cc = threadIdx.x % NCH;            // channel group (16-byte chunk)
-        const int mp = threadIdx.x / NCH;            // pixel within a pass
+        // A lane pair holds one sample row of one (pixel, 8-channel chunk): lane c
+        // loads column x0 + c.  With x in 8-channel planes both columns sit in one
+        // 128-byte line (unless x0 ends a line), so a warp's load of 16 pixels of
+        // one chunk touches about 18 lines instead of 32 (the L1 data stage takes
+        // a wavefront per line).  The pair then swaps halves: lane 0 blends
+        // channels 0-3 and lane 1 channels 4-7, each from all four corners.
+        constexpr int NGW = NGATHER / 32;  // gather warps
+        constexpr int WPC = NGW / NCH;     // warps per chunk
+        constexpr int PPW = TM / WPC;      // pixels per warp
+        constexpr int NPASS = PPW / 16;    // 16 pixels (32 lanes) per pass
+        static_assert(NGW % NCH == 0 && PPW % 16 == 0, "gather mapping");
+        const int cc = warp % NCH;         // channel chunk of this warp
+        const int c = lane & 1;            // column x0 + c of the corner pair
+        const int pb = (warp / NCH) * PPW + (lane >> 1);
         const uint8_t *x = static_cast<const uint8_t *>(a.x);
-        const int cpg = a.cin_pad / a.groups;
         const int G = a.groups;
-        const int g = (cc * CPC) / cpg;
+        const int g = (cc * CPC) / (a.cin_pad / G);
+        const bool tapm = a.om_tap_major != 0;
         const uint8_t *plane = x + (int64_t)((cc * CPC) / xcpc) * HW * xcpc * 2 + ((cc * CPC) % xcpc) * 2;
+        const uint32_t pstride = (uint32_t)xcpc * 2;  // bytes per pixel in the plane (the plane is < 2 GiB)
         int s = 0;
         uint32_t ph = 0;
         bool ok = true;
-        // offsets (dy, dx adjacent in one 4-channel unit) and mask of every pass's pixel
-        // for tap k; the next tap's are loaded while this tap's corners are in flight
+        // offsets (dy, dx adjacent in one 4-channel unit) and mask of every pass's pixel for tap k
         auto load_om = [&](int y, int xb, int k, float2 (&d)[NPASS], float (&mk)[NPASS]) {
-            const int cd = 2 * (g * 9 + k), cm = 18 * G + g * 9 + k;
+            const int cd = dcn_off_channel(g, k, G, tapm), cm = dcn_mask_channel(g, k, G, tapm);
+            // float offsets in 32 bits (the tensor is < 2^31 floats)
+            const uint32_t od = (uint32_t)(cd >> 2) * (uint32_t)HW * 4u + (cd & 3);
+            const uint32_t oms = (uint32_t)(cm >> 2) * (uint32_t)HW * 4u + (cm & 3);
 #pragma unroll
             for (int h = 0; h < NPASS; ++h) {
-                const int64_t pix = (int64_t)y * W + min(xb + mp + h * PPP, W - 1);
-                d[h] = __ldg(reinterpret_cast<const float2 *>(a.om + ((int64_t)(cd >> 2) * HW + pix) * 4 + (cd & 3)));
-                mk[h] = __ldg(a.om + ((int64_t)(cm >> 2) * HW + pix) * 4 + (cm & 3));
+                const uint32_t pix4 = (uint32_t)(y * W + min(xb + pb + h * 16, W - 1)) * 4u;
+                d[h] = __ldg(reinterpret_cast<const float2 *>(a.om + od + pix4));
+                mk[h] = __ldg(a.om + oms + pix4);
             }
         };
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int y = t / tiles_x;
             const int xb = (t - y * tiles_x) * TM;
-            float2 dn[NPASS];
-            float mn[NPASS];
-            load_om(y, xb, 0, dn, mn);
             for (int k = 0; k < 9; ++k) {
-                float dy[NPASS], dx[NPASS], msk[NPASS];
-#pragma unroll
-                for (int h = 0; h < NPASS; ++h) {
-                    dy[h] = dn[h].x;
-                    dx[h] = dn[h].y;
-                    msk[h] = mn[h];
-                }
-                if (!mbar_wait_bounded(&empty[s], ph ^ 1, abort, WAIT_NS)) {
+                float2 dd[NPASS];
+                float msk[NPASS];
+                load_om(y, xb, k, dd, msk);
+                // the shuffles below need the whole warp: it leaves together
+                const bool got = mbar_wait_bounded(&empty[s], ph ^ 1, abort, WAIT_NS);
+                if (!__all_sync(0xffffffffu, got)) {
                     *abort = 1;
                     if (a.err) atomicExch(a.err, DEVERR_TIMEOUT);
                     ok = false;
                     break;
                 }
-                uint8_t *stg = stage0 + (size_t)s * STAGE + (size_t)cc * LBO;
+                uint8_t *stg = stage0 + (size_t)s * STAGE + (size_t)cc * LBO + c * 8;
                 // every corner load of every pass first, then the blends
-                uint4 v[NPASS][4];
-                float wq[NPASS][4];
+                uint4 v[NPASS][2];
+                float fly[NPASS], flx[NPASS];  // fractional position
+                uint32_t inb = 0;              // bit 4h + q: corner q of pass h inside the image
 #pragma unroll
                 for (int h = 0; h < NPASS; ++h) {
-                    const int xx = xb + mp + h * PPP;
-                    const float sy = (float)(y + k / 3 - 1) + dy[h];
-                    const float sx = (float)(xx + k % 3 - 1) + dx[h];
+                    const int xx = xb + pb + h * 16;
+                    const float sy = (float)(y + k / 3 - 1) + dd[h].x;
+                    const float sx = (float)(xx + k % 3 - 1) + dd[h].y;
                     const float fy = floorf(sy), fx = floorf(sx);
                     const int y0 = (int)fy, x0 = (int)fx;
-                    const float ly = sy - fy, lx = sx - fx;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int yy = y0 + (q >> 1), xq = x0 + (q & 1);
-                        const bool in = xx < W && yy >= 0 && yy < H && xq >= 0 && xq < W;
-                        wq[h][q] = in ? ((q >> 1) ? ly : 1.f - ly) * ((q & 1) ? lx : 1.f - lx) : 0.f;
-                        v[h][q] = in ? __ldg(reinterpret_cast<const uint4 *>(plane + ((int64_t)yy * W + xq) * xcpc * 2))
-                                     : make_uint4(0u, 0u, 0u, 0u);
-                    }
+                    fly[h] = sy - fy;
+                    flx[h] = sx - fx;
+                    const bool py = xx < W;
+                    const bool r0 = py && y0 >= 0 && y0 < H, r1 = py && y0 + 1 >= 0 && y0 + 1 < H;
+                    const bool c0 = x0 >= 0 && x0 < W, c1 = x0 + 1 >= 0 && x0 + 1 < W;
+                    inb |= (uint32_t)((r0 && c0) | ((r0 && c1) << 1) | ((r1 && c0) << 2) | ((r1 && c1) << 3)) << (4 * h);
+                    const bool mc = c ? c1 : c0;
+                    // byte offsets of rows y0 and y0 + 1, each formed in full before it meets
+                    // the pointer (y0 may be -1, where only the second is used)
+                    const uint32_t o0 = (uint32_t)(y0 * W + x0 + c) * pstride;
+                    const uint32_t o1 = o0 + (uint32_t)W * pstride;
+                    v[h][0] = r0 && mc ? __ldg(reinterpret_cast<const uint4 *>(plane + o0)) : make_uint4(0u, 0u, 0u, 0u);
+                    v[h][1] = r1 && mc ? __ldg(reinterpret_cast<const uint4 *>(plane + o1)) : make_uint4(0u, 0u, 0u, 0u);
                 }
-                if (k < 8) load_om(y, xb, k + 1, dn, mn);
 #pragma unroll
                 for (int h = 0; h < NPASS; ++h) {
-                    float acc[CPC];
+                    // row r: swap halves with the partner lane, then add corners (r, 0) and
+                    // (r, 1) of this lane's 4 channels (2 words) in corner order
+                    float acc[4];
 #pragma unroll
-                    for (int e = 0; e < CPC; ++e) acc[e] = 0.f;
+                    for (int e = 0; e < 4; ++e) acc[e] = 0.f;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const T *vv = reinterpret_cast<const T *>(&v[h][q]);
+                    for (int r = 0; r < 2; ++r) {
+                        const uint4 o = v[h][r];
+                        const uint32_t s0 = c ? o.x : o.z, s1 = c ? o.y : o.w;
+                        const uint32_t g0 = __shfl_xor_sync(0xffffffffu, s0, 1);
+                        const uint32_t g1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+                        uint32_t cw[2][2];
+                        cw[0][0] = c ? g0 : o.x;
+                        cw[0][1] = c ? g1 : o.y;
+                        cw[1][0] = c ? o.z : g0;
+                        cw[1][1] = c ? o.w : g1;
 #pragma unroll
-                        for (int e = 0; e < CPC; ++e) acc[e] += wq[h][q] * Cv<T>::in(vv[e]);
+                        for (int col = 0; col < 2; ++col) {
+                            const int q = 2 * r + col;
+                            const float wq = (inb >> (4 * h + q)) & 1u
+                                                 ? (r ? fly[h] : 1.f - fly[h]) * (col ? flx[h] : 1.f - flx[h])
+                                                 : 0.f;
+                            const T *vv = reinterpret_cast<const T *>(cw[col]);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[e] += wq * Cv<T>::in(vv[e]);
+                        }
                     }
                     float mm = msk[h];
                     if (a.mask_logits) mm = 1.f / (1.f + expf(-mm));
-                    alignas(16) T o[CPC];
+                    alignas(8) T o[4];
 #pragma unroll
-                    for (int e = 0; e < CPC; ++e) o[e] = Cv<T>::out(acc[e] * mm);
-                    *reinterpret_cast<uint4 *>(stg + (size_t)(mp + h * PPP) * 16) = *reinterpret_cast<const uint4 *>(o);
+                    for (int e = 0; e < 4; ++e) o[e] = Cv<T>::out(acc[e] * mm);
+                    *reinterpret_cast<uint2 *>(stg + (size_t)(pb + h * 16) * 16) = *reinterpret_cast<const uint2 *>(o);
                 }
                 fence_proxy_async();  // generic smem writes -> visible to the tensor core
                 mbar_arrive(&full[s]);
                 if (++s == S) { s = 0; ph ^= 1; }
             }
         }
-    } else if (warp == MMA_WARP) {
-        if (lane == 0) {
-            // ------------------------------------------------ weights + MMA issue
-            mbar_arrive_expect_tx(wbar, wbytes);
-            for (uint32_t off = 0; off < wbytes; off += 32768u)
-                bulk_load(wsm + off, static_cast<const uint8_t *>(a.w) + off, min(32768u, wbytes - off), wbar);
-            bool ok = mbar_wait_bounded(wbar, 0, abort, WAIT_NS);
-            if (!ok) {
-                *abort = 1;
-                if (a.err) atomicExch(a.err, DEVERR_TIMEOUT);
-            }
-            const uint32_t wbase = smem_u32(wsm);
-            int s = 0, it = 0, last_a = -1;
-            uint32_t ph = 0, last_par = 0;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
-                const int ab = it & 1;
-                const uint32_t u = (uint32_t)(it >> 1);
-                if (!mbar_wait_bounded(&tempty[ab], (u & 1) ^ 1, abort, WAIT_NS)) {
-                    *abort = 1;
-                    if (a.err) atomicExch(a.err, DEVERR_TIMEOUT);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(ab * NS);
-                for (int k = 0; k < 9; ++k) {
-                    if (!mbar_wait_bounded(&full[s], ph, abort, WAIT_NS)) {
-                        *abort = 1;
-                        if (a.err) atomicExch(a.err, DEVERR_TIMEOUT);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t sb = smem_u32(stage0 + (size_t)s * STAGE);
-#pragma unroll
-                    for (int j = 0; j < NCH / 2; ++j) {
-                        const uint64_t ad = smem_desc(sb + 2 * j * LBO, LBO, 128);
-                        const uint64_t bd = smem_desc(wbase + (uint32_t)((k * NCH + 2 * j) * NS * 16), NS * 16, 128);
-                        umma<0>(d_tmem, ad, bd, IDESC, (k | j) != 0 ? 1u : 0u);
-                    }
-                    umma_commit(&empty[s]);
-                    if (++s == S) { s = 0; ph ^= 1; }
-                }
-                if (!ok) break;
-                umma_commit(&tfull[ab]);
-                last_a = ab;
-                last_par = u & 1;
-            }
-            if (last_a >= 0) mbar_wait_bounded(&tfull[last_a], last_par, nullptr, WAIT_NS);
-            mbar_wait_bounded(wbar, 0, nullptr, WAIT_NS);
-        }
     } else {
-        // ------------------------------------------------ epilogue (the last 4 warps, one per lane quadrant)
+        // ------------------------------------------------ epilogue (the last 4 warps, one per lane quadrant);
+        // lane 0 of the first also loads the weights and issues every tile's MMAs, and
+        // that warp stores its quadrant of tile i - 1 after issuing tile i
+        const bool issuer = warp == MMA_WARP;
         const int q = warp & 3;
         const int m = q * 32 + lane;
         uint8_t *yb = static_cast<uint8_t *>(a.y);
-        int it = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const uint32_t wbase = smem_u32(wsm);
+        bool run = true;     // this warp's epilogue still runs
+        bool issue = true;   // the issuer still issues
+        int s = 0, last_ab = -1;
+        uint32_t ph = 0, last_par = 0;
+        if (issuer) {
+            if (lane == 0) {
+                mbar_arrive_expect_tx(wbar, wbytes);
+                for (uint32_t off = 0; off < wbytes; off += 32768u)
+                    bulk_load(wsm + off, static_cast<const uint8_t *>(a.w) + off, min(32768u, wbytes - off), wbar);
+                issue = mbar_wait_bounded(wbar, 0, abort, WAIT_NS);
+                if (!issue) {
+                    *abort = 1;
+                    if (a.err) atomicExch(a.err, DEVERR_TIMEOUT);
+                }
+            }
+            issue = __shfl_sync(0xffffffffu, issue, 0);
+        }
+        // issues the 9 taps of tile number it (buffer it & 1); false when a wait gave up
+        auto issue_tile = [&](int it) -> bool {
+            bool good = true;
+            if (lane == 0) {
+                const int ab = it & 1;
+                const uint32_t u = (uint32_t)(it >> 1);
+                good = mbar_wait_bounded(&tempty[ab], (u & 1) ^ 1, abort, WAIT_NS);
+                if (good) {
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(ab * NS);
+                    for (int k = 0; k < 9 && good; ++k) {
+                        good = mbar_wait_bounded(&full[s], ph, abort, WAIT_NS);
+                        if (!good) {
+                            if (k > 0) {  // the final wait then covers the taps already issued
+                                umma_commit(&tfull[ab]);
+                                last_ab = ab;
+                                last_par = u & 1;
+                            }
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sb = smem_u32(stage0 + (size_t)s * STAGE);
+#pragma unroll
+                        for (int j = 0; j < NCH / 2; ++j) {
+                            const uint64_t ad = smem_desc(sb + 2 * j * LBO, LBO, 128);
+                            const uint64_t bd = smem_desc(wbase + (uint32_t)((k * NCH + 2 * j) * NS * 16), NS * 16, 128);
+                            umma<0>(d_tmem, ad, bd, IDESC, (k | j) != 0 ? 1u : 0u);
+                        }
+                        umma_commit(&empty[s]);
+                        if (++s == S) { s = 0; ph ^= 1; }
+                    }
+                    if (good) {
+                        umma_commit(&tfull[ab]);
+                        last_ab = ab;
+                        last_par = u & 1;
+                    }
+                }
+                if (!good) {
+                    *abort = 1;
+                    if (a.err) atomicExch(a.err, DEVERR_TIMEOUT);
+                }
+            }
+            return __shfl_sync(0xffffffffu, good, 0);
+        };
+        // stores this warp's quadrant of tile t (number it); false when the wait gave up
+        auto store_tile = [&](int t, int it) -> bool {
             const int ab = it & 1;
             const uint32_t u = (uint32_t)(it >> 1);
-            bool ok = mbar_wait_bounded(&tfull[ab], u & 1, abort, WAIT_NS);
-            ok = __all_sync(0xffffffffu, ok);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[ab], u & 1, abort, WAIT_NS));
             if (!ok) {
                 if (lane == 0) {
                     *abort = 1;
                     if (a.err) atomicExch(a.err, DEVERR_TIMEOUT);
                 }
-                break;
+                return false;
             }
             tc_fence_after();
             const int y = t / tiles_x;
@@ -286,6 +329,24 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
             }
             tc_fence_before();
             mbar_arrive(&tempty[ab]);
+            return true;
+        };
+        int it = 0, prev_t = -1;
+        for (int t = blockIdx.x; t < ntiles && run; t += gridDim.x, ++it) {
+            if (issuer) {
+                if (issue) issue = issue_tile(it);
+                if (!issue) break;
+                if (prev_t >= 0) run = store_tile(prev_t, it - 1);
+                prev_t = t;
+            } else {
+                run = store_tile(t, it);
+            }
+        }
+        if (issuer && issue && run && prev_t >= 0) store_tile(prev_t, it - 1);
+        if (issuer && lane == 0) {
+            // nothing of this CTA's may still be in flight when it leaves
+            if (last_ab >= 0) mbar_wait_bounded(&tfull[last_ab], last_par, nullptr, WAIT_NS);
+            mbar_wait_bounded(wbar, 0, nullptr, WAIT_NS);
         }
     }
     __syncthreads();
@@ -316,14 +377,40 @@ cudaError_t run(const DcnArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// One thread per (pixel, 8-channel chunk), chunk fastest: a warp reads four
+// pixels' 128-byte channel lines and writes 64-byte runs of eight planes.
+__global__ void relayout8_kernel(const uint4 *__restrict__ x, int64_t HW, int nch, int xcpc, uint4 *__restrict__ y) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= HW * nch) return;
+    const int64_t p = u / nch;
+    const int cc = (int)(u - p * nch);
+    const int per = xcpc / 8;  // 16-byte chunks per pixel in the source layout
+    y[(int64_t)cc * HW + p] = __ldg(x + ((int64_t)(cc / per) * HW + p) * per + cc % per);
+}
+
 }  // namespace
+
+cudaError_t launch_dcn_relayout8(const void *x, int cpad, int H, int W, int x_cpc, void *y, cudaStream_t st) {
+    if (cpad % 8 || x_cpc % 8 || cpad % x_cpc) return cudaErrorInvalidValue;
+    const int64_t HW = (int64_t)H * W, units = HW * (cpad / 8);
+    if (units == 0) return cudaSuccess;
+    const int64_t blocks = (units + 255) / 256;
+    relayout8_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const uint4 *>(x), HW, cpad / 8, x_cpc,
+                                                       static_cast<uint4 *>(y));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dcn_tc(const DcnArgs &a0, cudaStream_t st) {
     DcnArgs a = a0;
     if (a.x_cpc == 0) a.x_cpc = 8;
     if (a.y_cpc == 0) a.y_cpc = 8;
     if (a.cin_pad != 64 || a.cout_pad != 64 || (a.cin_pad / a.groups) % 8) return cudaErrorNotSupported;
-    if ((a.x_cpc != 8 && a.x_cpc != 64) || (a.y_cpc != 8 && a.y_cpc != 64)) return cudaErrorNotSupported;
+    // x in 8-channel planes (launch_dcn_relayout8); y blocked by 8 or 64 channels
+    if (a.x_cpc != 8 || (a.y_cpc != 8 && a.y_cpc != 64)) return cudaErrorNotSupported;
+    if (a.om_tap_major && a.groups % 2) return cudaErrorNotSupported;
+    // 32-bit gather offsets into a plane of x and into om
+    if ((int64_t)a.H * a.W * a.x_cpc * 2 >= (int64_t(1) << 31) || (int64_t)a.H * a.W * a.om_cpad >= (int64_t(1) << 31))
+        return cudaErrorNotSupported;
     if (a.in_dt == DT_BF16 && a.out_dt == DT_BF16) return run<__nv_bfloat16, 64, 64>(a, st);
     if (a.in_dt == DT_F16 && a.out_dt == DT_F16) return run<__half, 64, 64>(a, st);
     return cudaErrorNotSupported;

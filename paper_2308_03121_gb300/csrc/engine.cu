@@ -127,6 +127,7 @@ struct Step {
     int layer = 0;
     int widx = -1;       // weights variant (input channels permuted), -1 = the layer's own
     int om_t = -1;       // DCN: offsets/mask tensor
+    bool om_tap_major = false;  // DCN: om channels in tap-major order (its head's rows permuted)
     std::vector<int> skip_frames;  // final outputs: frames whose upsampled mean is added
     int in_t = -1;       // input tensor id (SRC_TENSOR)
     int src = SRC_TENSOR;
@@ -197,7 +198,9 @@ struct nvisr_filter {
     // network plan
     std::vector<Weights> wvar;     // weights with permuted input channels (concatenations)
     std::vector<Weights> weights;  // per layer (shared layers point to the owner)
+    std::vector<int> om_tap_g;     // per layer: G when its output rows are stored tap-major, else 0
     std::vector<Tensor> tensors;
+    void *dcn_x8 = nullptr;        // DCN input in 8-channel planes (tensor-core path)
     std::vector<Step> steps;
     int pack_t = -1;               // tensor id of the packed tuple
     float *out_rgb[2] = {nullptr, nullptr};  // planar float32 residuals [3][sH][opitch]
@@ -419,9 +422,69 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
     return NVISR_OK;
 }
 
+// Offset/mask heads whose output rows are stored tap-major (see DcnArgs): the
+// head of a DCN layer with an even group count G, read by DCN layers only, and
+// sharing its weights only with other such heads of the same G.  Returns per
+// layer G, or 0 to keep torchvision's order.
+std::vector<int> om_tap_major_groups(const NetDesc &net) {
+    const int n = (int)net.layers.size();
+    std::vector<int> G(n, 0);  // 0 = not a head, -1 = keep the order
+    for (const NetLayer &D : net.layers) {
+        if (D.op != "dcn") continue;
+        const int p = net.find(D.om);
+        if (p < 0) continue;
+        const NetLayer &H = net.layers[p];
+        const int want = D.groups % 2 == 0 && H.cout == 27 * D.groups && !H.ps ? D.groups : -1;
+        G[p] = G[p] == 0 || G[p] == want ? want : -1;
+    }
+    for (const NetLayer &X : net.layers) {
+        for (const std::string &nm : X.in) {
+            const int p = net.find(nm);
+            if (p >= 0) G[p] = G[p] ? -1 : 0;
+        }
+        const int a = X.add.empty() ? -1 : net.find(X.add);
+        if (a >= 0) G[a] = G[a] ? -1 : 0;
+    }
+    for (const auto &o : net.outputs) {
+        const int p = net.find(o.name);
+        if (p >= 0) G[p] = G[p] ? -1 : 0;
+    }
+    std::vector<int> own(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const int o = net.layers[i].owner, gi = G[i] > 0 ? G[i] : -1;
+        own[o] = own[o] == 0 || own[o] == gi ? gi : -1;
+    }
+    std::vector<int> out(n, 0);
+    for (int i = 0; i < n; ++i) out[i] = std::max(own[net.layers[i].owner], 0);
+    return out;
+}
+
+// Head rows in tap-major order: the torchvision row that new row j takes.
+int om_row_source(int j, int G) {
+    const int k = j / (3 * G), r = j % (3 * G);
+    return r < 2 * G ? 2 * ((r / 2) * 9 + k) + (r % 2) : 18 * G + (r - 2 * G) * 9 + k;
+}
+
+// Uploads a layer's weights, with its output rows permuted to tap-major order
+// when it is such a head.
+nvisr_status upload_layer(nvisr_filter *f, int li, const float *w, const float *b, Weights &W) {
+    const NetLayer &L = f->net.layers[li];
+    const int G = f->om_tap_g[li];
+    if (G == 0) return upload_weights(f, L, w, b, W);
+    const size_t per = (size_t)L.cin * L.k * L.k;
+    std::vector<float> wo(per * L.cout), bo(L.cout);
+    for (int j = 0; j < L.cout; ++j) {
+        const int o = om_row_source(j, G);
+        std::copy(w + o * per, w + (o + 1) * per, wo.begin() + j * per);
+        bo[j] = b[o];
+    }
+    return upload_weights(f, L, wo.data(), bo.data(), W);
+}
+
 nvisr_status prepare_weights(nvisr_filter *f, const float *blob) {
     const NetDesc &net = f->net;
     f->weights.resize(net.layers.size());
+    f->om_tap_g = om_tap_major_groups(net);
     for (size_t i = 0; i < net.layers.size(); ++i) {
         const NetLayer &L = net.layers[i];
         if (L.owner != (int)i) {
@@ -430,7 +493,7 @@ nvisr_status prepare_weights(nvisr_filter *f, const float *blob) {
         }
         const float *w = blob + L.woff;
         const float *b = w + (int64_t)L.cout * L.cin * L.k * L.k;
-        nvisr_status s = upload_weights(f, L, w, b, f->weights[i]);
+        nvisr_status s = upload_layer(f, (int)i, w, b, f->weights[i]);
         if (s != NVISR_OK) return s;
     }
     return NVISR_OK;
@@ -690,7 +753,7 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
                         for (int t = 0; t < kk; ++t)
                             wp[((size_t)o * L.cin + c) * kk + t] = w[((size_t)o * L.cin + perm[c]) * kk + t];
                 Weights Wv;
-                nvisr_status s = upload_weights(f, L, wp.data(), b, Wv);
+                nvisr_status s = upload_layer(f, (int)i, wp.data(), b, Wv);
                 if (s != NVISR_OK) return s;
                 st.widx = (int)f->wvar.size();
                 f->wvar.push_back(Wv);
@@ -704,6 +767,8 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
             if (st.om_t < 0 || f->tensors[st.om_t].C != 27 * L.groups || f->tensors[st.om_t].dt != DT_F32)
                 return fail(NVISR_BAD_NETWORK, "layer " + L.name + ": offset/mask head must have 27*groups channels");
             if (f->tensors[st.om_t].H != src.H) return fail(NVISR_BAD_NETWORK, "layer " + L.name + ": size mismatch");
+            const int p = net.find(L.om);
+            st.om_tap_major = p >= 0 && f->om_tap_g[p] == L.groups;
         }
         if (!L.add.empty()) {
             st.add_t = source(L.add);
@@ -779,6 +844,17 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
                     if (b.p == f->tensors[t].ptr) b.free_after = step;
     }
     for (Tensor &T : f->tensors) T.cpc = layout_cpc(T.dt, T.cpad);
+    // the tensor-core DCN gathers from its input copied into 8-channel planes
+    size_t x8 = 0;
+    for (const Step &st : f->steps)
+        if (st.op == OP_DCN && f->tc && f->tensors[st.in_t].cpc != 8) {
+            const Tensor &T = f->tensors[st.in_t];
+            x8 = std::max(x8, (size_t)T.cpad * T.H * T.W * dtype_size(T.dt));
+        }
+    if (x8) {
+        nvisr_status s = dalloc(f->eng, x8, f->owned, &f->dcn_x8);
+        if (s != NVISR_OK) return s;
+    }
     for (Tensor &T : f->tensors)
         if (T.parent >= 0) {
             const Tensor &P = f->tensors[T.parent];
@@ -887,11 +963,17 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
         DcnArgs d{};
         d.x = in.ptr; d.cin_pad = in.cpad; d.H = in.H; d.W = in.W; d.groups = L.groups;
         d.x_cpc = in.cpc; d.y_cpc = o.cpc;
-        d.om = (const float *)om.ptr; d.om_cpad = om.cpad; d.mask_logits = 1;
+        d.om = (const float *)om.ptr; d.om_cpad = om.cpad; d.om_tap_major = s.om_tap_major; d.mask_logits = 1;
         d.w = Wt.simt_or_tc; d.bias = Wt.bias; d.cout = L.cout; d.cout_pad = Wt.cout_pad;
         d.y = o.ptr; d.in_dt = in.dt; d.out_dt = o.dt; d.acc_scale = 1.f; d.out_scale = 1.f;
         d.err = f->eng->err_word;
         ProfScope ps(f, NVISR_K_DCN);
+        if (f->tc && in.cpc != 8) {
+            cudaError_t e = launch_dcn_relayout8(in.ptr, in.cpad, in.H, in.W, in.cpc, f->dcn_x8, st);
+            if (e != cudaSuccess) return cuda_status(e, ("dcn layer " + L.name + " relayout").c_str());
+            d.x = f->dcn_x8;
+            d.x_cpc = 8;
+        }
         cudaError_t e = f->tc ? launch_dcn_tc(d, st) : launch_dcn_simt(d, st);
         if (e != cudaSuccess) return cuda_status(e, ("dcn layer " + L.name).c_str());
         return NVISR_OK;
@@ -1933,7 +2015,8 @@ nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t
         pa.ch_per_src = om_c;
         NVISR_TRY_CUDA(launch_pack(pa, st));
     }
-    const int x_cpc = layout_cpc(adt, cin_pad), y_cpc = layout_cpc(adt, cout_pad);
+    // the tensor-core gather reads x in 8-channel planes
+    const int x_cpc = tc ? 8 : layout_cpc(adt, cin_pad), y_cpc = layout_cpc(adt, cout_pad);
     nvisr_status s = pack_planar(x, cin, cin_pad, h, w, adt, 1.f, dx, st, x_cpc);
     if (s != NVISR_OK) return s;
     int *err;
