@@ -285,6 +285,13 @@ __device__ __forceinline__ void st_sample(uint8_t *base, int64_t pitch, int y, i
     reinterpret_cast<S *>(base + (int64_t)y * pitch)[x] = (S)(int)v;
 }
 
+// Bilinear blend of the corners (row 0: a00, a01; row 1: a10, a11) at fractions (lx, ly).
+__device__ __forceinline__ float bilerp(float a00, float a01, float a10, float a11, float lx, float ly) {
+    const float top = a00 * (1.f - lx) + a01 * lx;
+    const float bot = a10 * (1.f - lx) + a11 * lx;
+    return top * (1.f - ly) + bot * ly;
+}
+
 // Skip value (mean of the skip frames, upsampled) at output (c, Y, X).
 __device__ __forceinline__ float skip_at(const SkipArgs &k, int c, int Y, int X) {
     float acc = 0.f;
@@ -302,9 +309,7 @@ __device__ __forceinline__ float skip_at(const SkipArgs &k, int c, int Y, int X)
             const float ly = sy - (float)y0, lx = sx - (float)x0;
             const float *r0 = p + (int64_t)y0 * k.pitch;
             const float *r1 = p + (int64_t)y1 * k.pitch;
-            const float top = r0[x0] * (1.f - lx) + r0[x1] * lx;
-            const float bot = r1[x0] * (1.f - lx) + r1[x1] * lx;
-            v = top * (1.f - ly) + bot * ly;
+            v = bilerp(r0[x0], r0[x1], r1[x0], r1[x1], lx, ly);
         }
         acc += v;
     }
@@ -349,12 +354,20 @@ __global__ void __launch_bounds__(256) requant444_kernel(const float *__restrict
 // network output of those 2 x 9 pixels is loaded once (two 16-byte loads and
 // one scalar per row and channel when the rows are 16-byte aligned), luma is
 // written with one 8- or 16-byte store per row and chroma with one per plane.
-// SKIP2: the skip is one frame upsampled 2x bilinearly (align_corners = false,
+// SKS = 2: the skip is one frame upsampled 2x bilinearly (align_corners = false,
 // edge clamp).  Output rows 2j, 2j+1 and columns 8q-1 .. 8q+7 then read
 // low-resolution rows j-1 .. j+1 and columns 4q-1 .. 4q+4 (clamped), loaded
 // once into registers; every output sample blends two rows and two columns
 // with the fixed weights 1/4, 3/4 in the same order as the general formula.
-template <typename S, bool SKIP2>
+// SKS = 4: the mean of NF frames upsampled 4x bilinearly.  Both output rows
+// blend the same two low-resolution rows, and columns 8q-1 .. 8q+7 blend
+// columns 2q-1 .. 2q+2 with the fractions 3/8, 5/8, 7/8, 1/8, ... that the
+// general formula gives exactly; those 2 x 4 values per channel and frame are
+// loaded once, at columns clamped to the image.  At the right edge this is the
+// general formula's arithmetic; at the left edge, where the formula clamps the
+// position to column 0, it blends two copies of column 0 (within one FP32 ulp
+// of it).  Columns past W - 1 are computed but never stored.
+template <typename S, int SKS, int NF>
 __global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict__ in, int64_t pitch,
                                                          int H, int W, int loc, RangeConst rc,
                                                          uint8_t *yp, int64_t py, uint8_t *up,
@@ -384,7 +397,37 @@ __global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict
                 for (int c = 1; c < 9; ++c) px[ch][a][c] = __ldg(row + clampi(xb - 1 + c, 0, W - 1));
             }
         }
+    constexpr bool SKIP2 = SKS == 2;
     float lr[SKIP2 ? 3 : 1][3][6];
+    float l4[SKS == 4 ? NF : 1][3][2][4];
+    float ly4[2] = {0.f, 0.f};
+    if (SKS == 4) {
+        int r0 = 0, r1 = 0;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            // the general formula; rows 2j and 2j + 1 give the same (y0, y1)
+            const float sy = fmaxf(((float)(2 * j + a) + 0.5f) * 0.25f - 0.5f, 0.f);
+            const int y0 = min((int)sy, sk.h - 1);
+            ly4[a] = sy - (float)y0;
+            if (a == 0) {
+                r0 = y0;
+                r1 = min(y0 + 1, sk.h - 1);
+            }
+        }
+        int lc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) lc[i] = clampi(2 * q - 1 + i, 0, sk.w - 1);
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr) {
+                    const float *row = sk.src[f] + (int64_t)c * sk.plane + (int64_t)(rr ? r1 : r0) * sk.pitch;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) l4[f][c][rr][i] = __ldg(row + lc[i]);
+                }
+    }
     if (SKIP2) {
         const bool svec = 4 * q + 3 <= sk.w - 1 && (sk.pitch & 3) == 0 && (sk.plane & 3) == 0 &&
                           (reinterpret_cast<uintptr_t>(sk.src[0]) & 15) == 0;
@@ -407,6 +450,15 @@ __global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict
     // output (row 2j + a, column xb - 1 + c9) of channel ch: residual + skip
     auto sample = [&](int ch, int a, int c9, int x) -> float {
         const float v = px[ch][a][c9];
+        if (SKS == 4) {
+            const int i0 = (c9 + 1) / 4;                     // column 2q - 1 + i0
+            const float lx = (float)((c9 + 1) % 4) * 0.25f + 0.125f;
+            float acc = 0.f;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                acc += bilerp(l4[f][ch][0][i0], l4[f][ch][0][i0 + 1], l4[f][ch][1][i0], l4[f][ch][1][i0 + 1], lx, ly4[a]);
+            return v + (NF == 2 ? acc * 0.5f : acc);
+        }
         if (!SKIP2) return sk.n ? v + skip_at(sk, ch, 2 * j + a, x) : v;
         // horizontal: even c9 -> odd column 2i+1 (3/4 col i, 1/4 col i+1), odd c9 -> even 2i (1/4 col i-1, 3/4 col i)
         const int c0 = (c9 & 1) ? (c9 - 1) / 2 : c9 / 2;
@@ -705,16 +757,22 @@ cudaError_t launch_requant(const nvisr_format &f, const float *in, int64_t in_pi
         block = dim3(128);
         dim3 grid((f.width + 8 * 128 - 1) / (8 * 128), f.height / 2);
         const bool skip2 = sk.n == 1 && sk.mode == 2 && sk.scale == 2 && sk.h * 2 == f.height && sk.w * 2 == f.width;
-#define NVISR_RQ(S_, K_)                                                                                     \
-    requant420_kernel<S_, K_><<<grid, block, 0, st>>>(in, in_pitch, f.height, f.width, f.chroma_loc, rc,  \
-                                                      (uint8_t *)y, py, (uint8_t *)u, pu, (uint8_t *)v, pv, sk)
+        const bool skip4 = (sk.n == 1 || sk.n == 2) && sk.mode == 2 && sk.scale == 4 && sk.h * 4 == f.height &&
+                           sk.w * 4 == f.width;
+#define NVISR_RQ(S_, K_, N_)                                                                                     \
+    requant420_kernel<S_, K_, N_><<<grid, block, 0, st>>>(in, in_pitch, f.height, f.width, f.chroma_loc, rc,  \
+                                                          (uint8_t *)y, py, (uint8_t *)u, pu, (uint8_t *)v, pv, sk)
+#define NVISR_RQ_ALL(S_)                  \
+    if (skip2) NVISR_RQ(S_, 2, 1);        \
+    else if (skip4 && sk.n == 1) NVISR_RQ(S_, 4, 1); \
+    else if (skip4) NVISR_RQ(S_, 4, 2);   \
+    else NVISR_RQ(S_, 0, 1)
         if (f.bit_depth <= 8) {
-            if (skip2) NVISR_RQ(uint8_t, true);
-            else NVISR_RQ(uint8_t, false);
+            NVISR_RQ_ALL(uint8_t);
         } else {
-            if (skip2) NVISR_RQ(uint16_t, true);
-            else NVISR_RQ(uint16_t, false);
+            NVISR_RQ_ALL(uint16_t);
         }
+#undef NVISR_RQ_ALL
 #undef NVISR_RQ
     } else {
         dim3 grid((f.width / 4 + 1 + block.x - 1) / block.x, f.height);
