@@ -168,6 +168,10 @@ size_t tc_rows16_weight_bytes();
 void prepare_weights_rows16(const float *w_oihw, int cin, int dt, void *dst_host);
 // npr = 16: the PixelShuffle output form (cout <= 16 channels in 16 rows per tap).
 void prepare_weights_rows(const float *w_oihw, int dt, void *dst_host, int cout = 64, int npr = 64);
+// Row-streaming image of a 3x3 layer from 128 input channels to <= 256 outputs:
+// [64-output slice][kx][64-channel chunk][2 - ky][64 out][128 B swizzled].
+size_t tc_rows128_weight_bytes(int nslice);
+void prepare_weights_rows128(const float *w_oihw, int cout, int dt, void *dst_host);
 
 // DCN: x blocked (activation dtype); offsets and mask in one blocked float32
 // tensor [om_cpad/4][H][W][4].  Channel order: torchvision's ([0, 18G) = (dy, dx)

@@ -554,19 +554,26 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     constexpr int AFMT = IN_DT == DT_BF16 ? 1 : 0;
     constexpr int PXS = TM + 2;
     // CIN: input channels of a row.  64: one 128-byte line per pixel, 128-byte swizzled;
+    // 128: two such lines per pixel, one 130-pixel region per 64-channel chunk
+    // (chunk 1 starts 130 lines after chunk 0: the swizzle is a function of the
+    // address, so a region may start inside a 1 KB atom);
     // 16 (the tuple head): two 16-byte channel chunks per pixel, canonical no-swizzle
     // layout [chunk][pixel][16 B] (K core matrices LBO_A apart)
-    static_assert(CIN == 64 || (CIN == 16 && NPR == 64 && !PS), "64-channel rows or the 16-channel head");
-    constexpr int KSTEPS = CIN == 64 ? 4 : 1;                 // 16-channel MMA K steps per kx
-    constexpr uint32_t AROW = CIN == 64 ? PXS * 128 : 2 * PXS * 16;  // bytes of one 130-pixel input row
+    static_assert(CIN == 64 || (CIN == 128 && NPR == 64 && !PS && !MULTI) || (CIN == 16 && NPR == 64 && !PS),
+                  "64- or 128-channel rows or the 16-channel head");
+    constexpr bool SW = CIN != 16;                            // 128-byte swizzled operands
+    constexpr int KSTEPS = CIN == 16 ? 1 : CIN / 16;         // 16-channel MMA K steps per kx
+    constexpr uint32_t AREG = PXS * 128;                      // one 64-channel chunk of a row (swizzled forms)
+    constexpr uint32_t AROW = SW ? (CIN / 64) * AREG : 2 * PXS * 16;  // bytes of one 130-pixel input row
     constexpr uint32_t ROWB = (AROW + 1023u) & ~1023u;
     constexpr uint32_t LBO_A = PXS * 16, LBO_B = 3 * NPR * 16;
     // NPR: accumulator columns of one output row (= padded output channels: 64 for the
     // trunk, 16 for the 12-channel PixelShuffle tail); PS: PixelShuffle(2) epilogue
     // into planar float32 instead of the blocked 16-bit row store
     static_assert(NPR == 64 || (NPR == 16 && PS), "64-channel trunk rows or 16-channel shuffle tail");
-    // weights of one kx: [ky' = 2 - ky][NPR][128 B] (CIN 64) or [2 chunks][3 * NPR][16 B] (CIN 16)
-    constexpr uint32_t WKX = CIN == 64 ? 3 * NPR * 128 : 2 * 3 * NPR * 16;
+    // weights of one kx: [64-channel chunk][ky' = 2 - ky][NPR][128 B] (CIN 64, 128) or
+    // [2 chunks][3 * NPR][16 B] (CIN 16)
+    constexpr uint32_t WKX = SW ? (CIN / 64) * 3 * NPR * 128 : 2 * 3 * NPR * 16;
     constexpr uint32_t TILEB = TM * 128;                      // one 128-pixel output / residual row tile
     constexpr int NSLOT = 8;                                  // output-row accumulators in TMEM
     static_assert(NSLOT == 8, "slot index and phase use & 7 and >> 3");
@@ -574,7 +581,12 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     constexpr int UPC_O = 16 / sizeof(TO);
     constexpr int NU = 64 / UPC_O;                            // 16-byte units of a pixel's 64 channels
     constexpr int NGRP = 128;                                 // threads of one epilogue group
-    static_assert(CBO == 128 && sizeof(TO) == 2, "row kernel writes 64-channel 16-bit tiles");
+    // OUT_DT F32: float32 output in 4-channel (16-byte) units, stored straight from
+    // registers (no staging tile); the layer's output channels come in 64-channel
+    // slices, one per CTA group (see slice below)
+    constexpr bool F32OUT = OUT_DT == DT_F32;
+    static_assert((CBO == 128 && sizeof(TO) == 2) || (F32OUT && CBO == 16 && CIN == 128),
+                  "64-channel 16-bit tiles, or float32 4-channel units from 128-channel rows");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -605,6 +617,10 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     const int strips_per_img = rp.xtiles * rp.bands;
     const int nstrips = MULTI ? probs[nprob - 1].strip0 + probs[nprob - 1].nstrips : strips_per_img * p.nimg;
     const bool has_res = MULTI ? probs[0].has_res != 0 : p.res != nullptr;
+    // output-channel slices: CTA b computes slice b % nslice of strips b / nslice, + step, ...
+    const int nsl = MULTI ? 1 : p.nslice;
+    const int slice = (int)blockIdx.x % nsl;
+    const int cta0 = (int)blockIdx.x / nsl, cstride = (int)gridDim.x / nsl;
     const bool plain = p.acc_scale == 1.f && p.out_scale == 1.f && p.res_scale == 1.f && !p.amax && !p.y2;
     auto strip_of = [&](int sidx, int &img, int &x0, int &ra, int &rb, int &pi) {
         if (MULTI) {
@@ -631,7 +647,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     auto ymap_of = [&](int pi) { return MULTI ? &probs[pi].ymap : &ymap; };
     auto rmap_of = [&](int pi) { return MULTI ? &probs[pi].rmap : &rmap; };
     auto width_of = [&](int pi) { return MULTI ? probs[pi].W : p.W; };
-    if (threadIdx.x >= 64 && threadIdx.x < 64 + NPR) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + NPR) sbias[threadIdx.x - 64] = p.bias[slice * NPR + threadIdx.x - 64];
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -663,11 +679,12 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
         if (lane == 0) {
             // ---------------- producer: weights, then one input row per stage
             mbar_arrive_expect_tx(wbar, 3 * WKX);
+            const uint8_t *wsrc = p.wts + (size_t)slice * 3 * WKX;
             for (uint32_t off = 0; off < 3 * WKX; off += 32768u)
-                bulk_load(wsm + off, p.wts + off, min(32768u, 3 * WKX - off), wbar);
+                bulk_load(wsm + off, wsrc + off, min(32768u, 3 * WKX - off), wbar);
             int gin = 0;
             bool ok = true;
-            for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
+            for (int sidx = cta0; sidx < nstrips && ok; sidx += cstride) {
                 int img, x0, ra, rb, pi;
                 strip_of(sidx, img, x0, ra, rb, pi);
                 for (int r = ra - 1; r <= rb; ++r, ++gin) {
@@ -679,6 +696,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                     }
                     mbar_arrive_expect_tx(&full[s], AROW);
                     tma_load_4d(stage0 + (size_t)s * ROWB, tmap_of(pi), &full[s], 0, x0 - 1, r, CIN == 64 ? img : 2 * img);
+                    // (CIN 128 and 16: one box of both channel chunks of the row)
                 }
             }
             for (int k = 0; k < S && k < gin; ++k) {
@@ -695,7 +713,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
             // MMAs per run only add constant offsets.
             bool ok = mbar_wait_bounded(wbar, 0, abort, WAIT_NS);
             if (!ok) raise_abort(abort, p.err);
-            const uint64_t b_base = CIN == 64 ? smem_desc_sw128(smem_u32(wsm), 0) : smem_desc(smem_u32(wsm), LBO_B, 128);
+            const uint64_t b_base = SW ? smem_desc_sw128(smem_u32(wsm), 0) : smem_desc(smem_u32(wsm), LBO_B, 128);
             // Work between MMA issues leaves the tensor pipe idle once the few queued
             // MMAs have run, and an mbarrier test made while MMAs are queued costs
             // about a hundred pipe cycles.  So this thread makes no mbarrier waits per
@@ -717,18 +735,20 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                 return true;
             };
             // (kx, K step) t: A advances one pixel per kx and 32 bytes per K step
-            // inside the swizzled 64-channel line (CIN 64); B one kx block per kx
+            // inside the swizzled 64-channel line (CIN 64, 128: K steps 4..7 read the
+            // second chunk's region); B one kx block per kx, one ky-stacked chunk
+            // block per 64 channels
             auto a_off = [&](int t) {
                 const int kx = t / KSTEPS, j = t % KSTEPS;
-                return (uint64_t)((CIN == 64 ? kx * 128 + j * 32 : kx * 16) >> 4);
+                return (uint64_t)((SW ? kx * 128 + (j >> 2) * (int)AREG + (j & 3) * 32 : kx * 16) >> 4);
             };
             auto b_off = [&](int t) {
                 const int kx = t / KSTEPS, j = t % KSTEPS;
-                return (uint64_t)((kx * WKX + (CIN == 64 ? j * 32 : 0)) >> 4);
+                return (uint64_t)((kx * WKX + (SW ? (j >> 2) * 3 * NPR * 128 + (j & 3) * 32 : 0)) >> 4);
             };
             auto a_desc = [&]() {
-                return CIN == 64 ? smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0)
-                                 : smem_desc(smem_u32(stage0 + (size_t)s * ROWB), LBO_A, 128);
+                return SW ? smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0)
+                          : smem_desc(smem_u32(stage0 + (size_t)s * ROWB), LBO_A, 128);
             };
             // Any row of a strip: runs and descriptors computed from the row's position.
             auto generic_row = [&](int r, int base, int ra, int rb) -> bool {
@@ -747,7 +767,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         const uint32_t nstep = (uint32_t)(NPR / 8) << 17;  // N += NPR
                         auto slot_of = [&](int o) { return (base + o) & (NSLOT - 1); };
                         auto bd_of = [&](int o) {
-                            return b_base + (uint64_t)(((o - r + 1) * NPR * (CIN == 64 ? 128 : 16)) >> 4);
+                            return b_base + (uint64_t)(((o - r + 1) * NPR * (SW ? 128 : 16)) >> 4);
                         };
                         const int sl0 = slot_of(o_lo);
                         const int len = o_hi - o_lo + 1;
@@ -804,7 +824,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                 constexpr int F0 = M0 >= 2 ? 2 : M0, F1 = 2 - F0;
                 constexpr uint32_t ID0 = instr_desc(TM, 0, AFMT, AFMT), NST = (uint32_t)(NPR / 8) << 17;
                 constexpr uint32_t MI0 = ID0 + NST * M0, MI1 = ID0 + NST * (M1 > 0 ? M1 : 1);
-                constexpr uint32_t BROW = NPR * (CIN == 64 ? 128 : 16);  // B bytes of one output row's taps
+                constexpr uint32_t BROW = NPR * (SW ? 128 : 16);  // B bytes of one output row's taps
                 const uint32_t md0 = tmem_base + (uint32_t)(SL0 * NPR), md1 = tmem_base;
                 const uint64_t mb0 = b_base, mb1 = b_base + (uint64_t)((M0 * BROW) >> 4);
                 umma<0>(md0, a_base, mb0, ID0 + NST * F0, 1u);
@@ -833,7 +853,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
             using I5 = std::integral_constant<int, 5>;
             using I6 = std::integral_constant<int, 6>;
             using I7 = std::integral_constant<int, 7>;
-            for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
+            for (int sidx = cta0; sidx < nstrips && ok; sidx += cstride) {
                 int img, x0, ra, rb, pi;
                 strip_of(sidx, img, x0, ra, rb, pi);
                 const int base = gout - ra;  // global index of this strip's output row o is base + o
@@ -865,7 +885,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
             int s = 0, gout = 0, gin = 0;
             uint32_t ph = 0;
             bool ok = true;
-            for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
+            for (int sidx = cta0; sidx < nstrips && ok; sidx += cstride) {
                 int img, x0, ra, rb, pi;
                 strip_of(sidx, img, x0, ra, rb, pi);
                 const int base = gout - ra;
@@ -910,7 +930,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
         int res_loads = 0;  // leader: residual loads issued into this group's buffer
         int last_res = -1;
         bool ok = true;
-        for (int sidx = blockIdx.x; sidx < nstrips && ok; sidx += gridDim.x) {
+        for (int sidx = cta0; sidx < nstrips && ok; sidx += cstride) {
             int img, x0, ra, rb, pi;
             strip_of(sidx, img, x0, ra, rb, pi);
             const int x = x0 + m;
@@ -1026,7 +1046,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         v[e] = ov;
                     }
                 }
-                if (has_res) {
+                if constexpr (!F32OUT) if (has_res) {
                     bool rw = mbar_wait_bounded(&resfull[g], (uint32_t)(k & 1), abort, WAIT_NS);
                     rw = __all_sync(0xffffffffu, rw);
                     if (!rw && lane == 0) {
@@ -1074,24 +1094,38 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
 #pragma unroll
                     for (int e = 0; e < 64; ++e) v[e] *= os;
                 }
+                if constexpr (F32OUT) {
+                    // this slice's 16 4-channel units of pixel (o, x), those inside cout_pad;
+                    // a warp writes 512 contiguous bytes per unit
+                    if (valid && w) {
+                        const int u0 = slice * (NPR / 4), nun = p.cout_pad / 4;
+                        float4 *yo = reinterpret_cast<float4 *>(p.y) + ((int64_t)img * nun + u0) * HW +
+                                     (int64_t)o * p.W + x;
 #pragma unroll
-                for (int uu = 0; uu < NU; ++uu) {
-                    const int unit = uu ^ (m & 7);
-                    uint4 ov;
-                    ov.x = pack2<TO>(v[uu * 8 + 0], v[uu * 8 + 1]);
-                    ov.y = pack2<TO>(v[uu * 8 + 2], v[uu * 8 + 3]);
-                    ov.z = pack2<TO>(v[uu * 8 + 4], v[uu * 8 + 5]);
-                    ov.w = pack2<TO>(v[uu * 8 + 6], v[uu * 8 + 7]);
-                    *reinterpret_cast<uint4 *>(ot + unit * 16) = ov;
+                        for (int uu = 0; uu < NU; ++uu)
+                            if (u0 + uu < nun)
+                                yo[(int64_t)uu * HW] = make_float4(v[4 * uu], v[4 * uu + 1], v[4 * uu + 2], v[4 * uu + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int uu = 0; uu < NU; ++uu) {
+                        const int unit = uu ^ (m & 7);
+                        uint4 ov;
+                        ov.x = pack2<TO>(v[uu * 8 + 0], v[uu * 8 + 1]);
+                        ov.y = pack2<TO>(v[uu * 8 + 2], v[uu * 8 + 3]);
+                        ov.z = pack2<TO>(v[uu * 8 + 4], v[uu * 8 + 5]);
+                        ov.w = pack2<TO>(v[uu * 8 + 6], v[uu * 8 + 7]);
+                        *reinterpret_cast<uint4 *>(ot + unit * 16) = ov;
+                    }
+                    fence_proxy_async();  // staging writes (and residual reads) before the async proxy
                 }
-                fence_proxy_async();  // staging writes (and residual reads) before the async proxy
                 if (leader && *abort) grp_stop[g] = 1;
                 named_barrier(bar_id, NGRP);
                 if (grp_stop[g]) {
                     ok = false;
                     break;
                 }
-                if (leader) {
+                if (!F32OUT && leader) {
                     tma_store_4d(ymap_of(pi), obuf + g * TILEB, 0, x0, o, img);
                     bulk_commit_group();
                     if (has_res && o + 2 < rb) {  // this group's next row; the buffer's readers are done
@@ -1436,15 +1470,43 @@ void prepare_weights_rows(const float *w, int dt, void *dst, int cout, int npr) 
                 }
 }
 
+size_t tc_rows128_weight_bytes(int nslice) { return (size_t)nslice * 3 * 2 * 3 * 64 * 128; }
+
+void prepare_weights_rows128(const float *w, int cout, int dt, void *dst) {
+    const int nslice = (round_up(cout, 16) + 63) / 64;
+    uint8_t *out = static_cast<uint8_t *>(dst);
+    memset(out, 0, tc_rows128_weight_bytes(nslice));
+    // [64-output slice][kx][64-channel chunk][ky' = 2 - ky][64 out][128 B swizzled]
+    for (int o = 0; o < cout; ++o)
+        for (int c = 0; c < 128; ++c)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx) {
+                    const float v = w[((size_t)o * 128 + c) * 9 + ky * 3 + kx];
+                    const int sl = o / 64, n = o % 64, ch = c / 64, cc = c % 64;
+                    const size_t row = (size_t)(2 - ky) * 64 + n;
+                    const size_t off = (((size_t)sl * 3 + kx) * 2 + ch) * 3 * 64 * 128 + row * 128 +
+                                       (((cc / 8) ^ (n & 7)) * 16) + (cc % 8) * 2;
+                    if (dt == DT_BF16) {
+                        __nv_bfloat16 h = __float2bfloat16_rn(v);
+                        memcpy(out + off, &h, 2);
+                    } else {
+                        __half h = __float2half_rn(v);
+                        memcpy(out + off, &h, 2);
+                    }
+                }
+}
+
 namespace {
 
-// Shared memory of the row kernel: 72 KB weights, the input-row ring, 2 output
-// staging tiles and, when the layer adds a residual, 2 residual tiles (without
-// one, their room goes to deeper input prefetch).
-inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false, int cin = 64) {
-    const uint32_t ROWB = cin == 64 ? (((TM + 2) * 128 + 1023u) & ~1023u) : ((2 * (TM + 2) * 16 + 1023u) & ~1023u);
-    const uint32_t WB = cin == 64 ? 3 * 3 * (uint32_t)npr * 128 : 3 * 2 * 3 * (uint32_t)npr * 16;
-    const uint32_t TILES = ps ? 0u : (res ? 4u : 2u) * TM * 128;
+// Shared memory of the row kernel: the weights (72 KB for 64 input channels),
+// the input-row ring, 2 output staging tiles (16-bit outputs) and, when the
+// layer adds a residual, 2 residual tiles (without one, their room goes to
+// deeper input prefetch).
+inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false, int cin = 64, bool f32out = false) {
+    const uint32_t ROWB = cin != 16 ? (((uint32_t)(cin / 64) * (TM + 2) * 128 + 1023u) & ~1023u)
+                                    : ((2 * (TM + 2) * 16 + 1023u) & ~1023u);
+    const uint32_t WB = cin != 16 ? 3 * 3 * (uint32_t)(cin / 64) * (uint32_t)npr * 128 : 3 * 2 * 3 * (uint32_t)npr * 16;
+    const uint32_t TILES = ps || f32out ? 0u : (res ? 4u : 2u) * TM * 128;
     int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES) / (int)ROWB;
     if (stages > 8) stages = 8;
     *smem = 1024 + SMEM_HDR + (int)WB + stages * (int)ROWB + (int)TILES;
@@ -1471,6 +1533,39 @@ cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUte
     int grid = rp.xtiles * rp.bands * p.nimg;
     if (grid > sms) grid = sms;
     kern<<<grid, ROWS_THREADS, smem, st>>>(map, ymap, rmap, p, rp, nullptr, 0);
+    return cudaGetLastError();
+}
+
+// 3x3 layer from 128 16-bit input channels (two 64-channel chunks) to float32
+// outputs in 64-channel slices: CTAs per slice = SMs / slices, each walking
+// strips of one slice; the band height is the one that gives the fewest input
+// rows per CTA (strips per CTA x (rows + 2 halo rows)).
+template <int IN_DT>
+cudaError_t run_rows128(const CUtensorMap &map, TcParams p, cudaStream_t st) {
+    int smem;
+    p.stages = rows_stages(false, &smem, 64, false, 128, true);
+    if (p.stages < 2) return cudaErrorInvalidConfiguration;
+    auto kern = conv_rows_kernel<IN_DT, DT_F32, 16, false, 64, false, 128>;
+    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, DT_F32, 16, false, 64, false, 128>>(smem);
+    if (e != cudaSuccess) return e;
+    const int ctas = std::max(1, device_sm_count() / p.nslice);
+    RowPlan rp;
+    rp.xtiles = (p.W + TM - 1) / TM;
+    int best = 1 << 30;
+    rp.rps = p.H;
+    for (int bands = 1; bands <= p.H; ++bands) {
+        const int rps = (p.H + bands - 1) / bands;
+        const int strips = rp.xtiles * ((p.H + rps - 1) / rps) * p.nimg;
+        const int per = (strips + ctas - 1) / ctas * (rps + 2);
+        if (per < best) {
+            best = per;
+            rp.rps = rps;
+        }
+    }
+    rp.bands = (p.H + rp.rps - 1) / rp.rps;
+    const int strips = rp.xtiles * rp.bands * p.nimg;
+    const int grid = std::min(ctas, strips) * p.nslice;
+    kern<<<grid, ROWS_THREADS, smem, st>>>(map, map, map, p, rp, nullptr, 0);
     return cudaGetLastError();
 }
 
@@ -1542,6 +1637,15 @@ bool rows_head_fits(const ConvArgs &a) {
     return a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.out_dt == dt && a.cin_pad == 16 &&
            a.in_cpc == 8 && a.cout_pad == 64 && a.cout == 64 && a.out_cpc == 64 && a.ps == 0 && !a.res && !a.y2 &&
            !a.amax;
+}
+
+// 3x3 layer from 128 16-bit channels (64-channel chunks) to <= 256 float32
+// channels in 4-channel units (the offset/mask head of a deformable layer).
+bool rows128_fits(const ConvArgs &a) {
+    const int dt = a.in_dt;
+    return a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.cin_pad == 128 && a.in_cpc == 64 &&
+           a.out_dt == DT_F32 && a.out_cpc == 4 && a.cout_pad % 4 == 0 && a.cout_pad <= 256 && a.cout <= a.cout_pad &&
+           a.ps == 0 && !a.res && !a.y2 && !a.amax && a.nimg == 1 && a.acc_scale == 1.f && a.out_scale == 1.f;
 }
 
 // PixelShuffle(2) output layer with 64 input channels (<= 16 outputs, planar float32).
@@ -1617,6 +1721,25 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
         p.wbytes = (uint32_t)tc_rows16_weight_bytes();
         return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128, 64, false, 16>(map, ymap, rmap, p, st)
                              : run_rows<DT_F16, DT_F16, 128, 64, false, 16>(map, ymap, rmap, p, st);
+    }
+    if (rows128_fits(a)) {
+        auto enc = encode_fn();
+        if (!enc) return cudaErrorNotSupported;
+        CUtensorMap map;
+        cuuint64_t dims[4] = {128, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)(2 * a.nimg)};
+        cuuint64_t strides[3] = {128, (cuuint64_t)a.W * 128, (cuuint64_t)a.W * a.H * 128};
+        cuuint32_t box[4] = {128, (cuuint32_t)(TM + 2), 1, 2};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.x), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        TcParams p = rows_params(a);
+        p.cout = a.cout;
+        p.cout_pad = a.cout_pad;
+        p.nslice = (a.cout_pad + 63) / 64;
+        p.wbytes = (uint32_t)tc_rows128_weight_bytes(1);
+        return dt == DT_BF16 ? run_rows128<DT_BF16>(map, p, st) : run_rows128<DT_F16>(map, p, st);
     }
     if (rows_ps_fits(a)) {
         ConvArgs b = a;

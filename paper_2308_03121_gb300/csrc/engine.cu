@@ -374,7 +374,8 @@ bool layer_is_fp8(const nvisr_filter *f, const NetLayer &L) {
 nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, const float *b, Weights &W) {
     W.cin_pad = act_cpad(f, L.cin);
     W.cout_pad = round_up(L.cout, 16);
-    std::vector<float> bias(W.cout_pad, 0.f);
+    // padded to whole 64-channel slices (the row kernels read a slice's 64 biases)
+    std::vector<float> bias(round_up(W.cout_pad, 64), 0.f);
     std::copy(b, b + L.cout, bias.begin());
     void *dbias;
     nvisr_status s = upload(f, bias.data(), bias.size() * 4, &dbias);
@@ -400,6 +401,12 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
             // a 16-channel input (the tuple head): the row kernel's no-swizzle 16-channel form
             std::vector<uint8_t> rows(tc_rows16_weight_bytes());
             prepare_weights_rows16(w, L.cin, f->act_dt, rows.data());
+            s = upload(f, rows.data(), rows.size(), &W.rows);
+        } else if (s == NVISR_OK && L.op == "conv" && L.k == 3 && L.cin == 128 && L.cout <= 256 && !L.ps) {
+            // 128 input channels (a concatenation of two 64-channel tensors), e.g. a DCN
+            // offset/mask head: the row kernel's 128-channel form in 64-output slices
+            std::vector<uint8_t> rows(tc_rows128_weight_bytes((W.cout_pad + 63) / 64));
+            prepare_weights_rows128(w, L.cout, f->act_dt, rows.data());
             s = upload(f, rows.data(), rows.size(), &W.rows);
         } else if (s == NVISR_OK && L.op == "conv" && L.k == 3 && L.cin == 64 && L.cout <= 16 && L.cout % 4 == 0) {
             // a PixelShuffle(2) output layer: the row kernel's 16-column shuffle form
