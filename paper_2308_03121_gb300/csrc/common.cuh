@@ -172,6 +172,9 @@ void prepare_weights_rows(const float *w_oihw, int dt, void *dst_host, int cout 
 // [64-output slice][kx][64-channel chunk][2 - ky][64 out][128 B swizzled].
 size_t tc_rows128_weight_bytes(int nslice);
 void prepare_weights_rows128(const float *w_oihw, int cout, int dt, void *dst_host);
+// 3x3 64 -> 256 layer followed by PixelShuffle(2): 4 row-streaming images of 64
+// outputs (tc_rows_weight_bytes() each), image s holding conv channels 4n + s.
+void prepare_weights_rows_ps4(const float *w_oihw, int dt, void *dst_host);
 
 // DCN: x blocked (activation dtype); offsets and mask in one blocked float32
 // tensor [om_cpad/4][H][W][4].  Channel order: torchvision's ([0, 18G) = (dy, dx)

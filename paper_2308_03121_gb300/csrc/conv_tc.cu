@@ -31,6 +31,7 @@
 
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "epilogue.cuh"
@@ -568,9 +569,13 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     constexpr uint32_t ROWB = (AROW + 1023u) & ~1023u;
     constexpr uint32_t LBO_A = PXS * 16, LBO_B = 3 * NPR * 16;
     // NPR: accumulator columns of one output row (= padded output channels: 64 for the
-    // trunk, 16 for the 12-channel PixelShuffle tail); PS: PixelShuffle(2) epilogue
-    // into planar float32 instead of the blocked 16-bit row store
+    // trunk, 16 for the 12-channel PixelShuffle tail); PS: PixelShuffle(2) epilogue,
+    // with NPR 16 into planar float32 instead of the blocked 16-bit row store, with
+    // NPR 64 (a 64 -> 256 layer) into a blocked 64-channel 16-bit tensor at twice the
+    // size: slice s = 2i + j holds conv channels 4n + s, i.e. all 64 channels of
+    // output pixel (2o + i, 2x + j), written as one 128-byte line per pixel
     static_assert(NPR == 64 || (NPR == 16 && PS), "64-channel trunk rows or 16-channel shuffle tail");
+    constexpr bool PSB = PS && NPR == 64;
     // weights of one kx: [64-channel chunk][ky' = 2 - ky][NPR][128 B] (CIN 64, 128) or
     // [2 chunks][3 * NPR][16 B] (CIN 16)
     constexpr uint32_t WKX = SW ? (CIN / 64) * 3 * NPR * 128 : 2 * 3 * NPR * 16;
@@ -647,7 +652,8 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     auto ymap_of = [&](int pi) { return MULTI ? &probs[pi].ymap : &ymap; };
     auto rmap_of = [&](int pi) { return MULTI ? &probs[pi].rmap : &rmap; };
     auto width_of = [&](int pi) { return MULTI ? probs[pi].W : p.W; };
-    if (threadIdx.x >= 64 && threadIdx.x < 64 + NPR) sbias[threadIdx.x - 64] = p.bias[slice * NPR + threadIdx.x - 64];
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + NPR)
+        sbias[threadIdx.x - 64] = p.bias[PSB ? 4 * (threadIdx.x - 64) + slice : slice * NPR + threadIdx.x - 64];
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -950,7 +956,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                 named_barrier(bar_id, NGRP);
                 bool w = mbar_wait_bounded(&rowdone[slot], (uint32_t)((i / NSLOT) & 1), abort, WAIT_NS);
                 w = __all_sync(0xffffffffu, w);
-                if constexpr (PS) {
+                if constexpr (PS && !PSB) {
                     // 12 shuffled channels: channel 4c + 2dy + dx -> output (c, 2o + dy, 2x + dx)
                     float v[16];
                     if (w) {
@@ -1094,7 +1100,28 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
 #pragma unroll
                     for (int e = 0; e < 64; ++e) v[e] *= os;
                 }
-                if constexpr (F32OUT) {
+                if constexpr (PSB) {
+                    // output pixel (2o + i, 2x + j) of the shuffled tensor (64 channels, one
+                    // 128-byte line), after the post-shuffle activation
+                    if (valid && w) {
+                        if (p.ps_act == 1) {
+#pragma unroll
+                            for (int e = 0; e < 64; ++e) v[e] = lrelu(v[e]);
+                        }
+                        const int si = slice >> 1, sj = slice & 1;
+                        uint4 *yo = reinterpret_cast<uint4 *>(p.y) +
+                                    (((int64_t)img * 2 * p.H + 2 * o + si) * (2 * p.W) + 2 * x + sj) * 8;
+#pragma unroll
+                        for (int uu = 0; uu < 8; ++uu) {
+                            uint4 ov;
+                            ov.x = pack2<TO>(v[uu * 8 + 0], v[uu * 8 + 1]);
+                            ov.y = pack2<TO>(v[uu * 8 + 2], v[uu * 8 + 3]);
+                            ov.z = pack2<TO>(v[uu * 8 + 4], v[uu * 8 + 5]);
+                            ov.w = pack2<TO>(v[uu * 8 + 6], v[uu * 8 + 7]);
+                            yo[uu] = ov;
+                        }
+                    }
+                } else if constexpr (F32OUT) {
                     // this slice's 16 4-channel units of pixel (o, x), those inside cout_pad;
                     // a warp writes 512 contiguous bytes per unit
                     if (valid && w) {
@@ -1125,7 +1152,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                     ok = false;
                     break;
                 }
-                if (!F32OUT && leader) {
+                if (!F32OUT && !PSB && leader) {
                     tma_store_4d(ymap_of(pi), obuf + g * TILEB, 0, x0, o, img);
                     bulk_commit_group();
                     if (has_res && o + 2 < rb) {  // this group's next row; the buffer's readers are done
@@ -1496,6 +1523,16 @@ void prepare_weights_rows128(const float *w, int cout, int dt, void *dst) {
                 }
 }
 
+void prepare_weights_rows_ps4(const float *w, int dt, void *dst) {
+    // slice s = 2i + j: conv channels 4n + s (output channel n at shuffle offset (i, j))
+    std::vector<float> ws((size_t)64 * 64 * 9);
+    for (int sl = 0; sl < 4; ++sl) {
+        for (int n = 0; n < 64; ++n)
+            memcpy(ws.data() + (size_t)n * 64 * 9, w + (size_t)(4 * n + sl) * 64 * 9, sizeof(float) * 64 * 9);
+        prepare_weights_rows(ws.data(), dt, static_cast<uint8_t *>(dst) + (size_t)sl * tc_rows_weight_bytes(64), 64, 64);
+    }
+}
+
 namespace {
 
 // Shared memory of the row kernel: the weights (72 KB for 64 input channels),
@@ -1536,17 +1573,19 @@ cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUte
     return cudaGetLastError();
 }
 
-// 3x3 layer from 128 16-bit input channels (two 64-channel chunks) to float32
-// outputs in 64-channel slices: CTAs per slice = SMs / slices, each walking
-// strips of one slice; the band height is the one that gives the fewest input
-// rows per CTA (strips per CTA x (rows + 2 halo rows)).
-template <int IN_DT>
-cudaError_t run_rows128(const CUtensorMap &map, TcParams p, cudaStream_t st) {
+// Row kernel over output-channel slices (p.nslice of 64): CTAs per slice =
+// SMs / slices, each walking strips of one slice; the band height is the one
+// that gives the fewest input rows per CTA (strips per CTA x (rows + 2 halo
+// rows)).  Forms: 128 16-bit input channels (two 64-channel chunks) to float32
+// 4-channel units; 64 -> 256 channels shuffled by PixelShuffle(2) into a
+// blocked 16-bit tensor.
+template <int IN_DT, int OUT_DT, int CBO, bool PS, int CIN>
+cudaError_t run_rows_sliced(const CUtensorMap &map, TcParams p, cudaStream_t st) {
     int smem;
-    p.stages = rows_stages(false, &smem, 64, false, 128, true);
+    p.stages = rows_stages(false, &smem, 64, PS, CIN, OUT_DT == DT_F32);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
-    auto kern = conv_rows_kernel<IN_DT, DT_F32, 16, false, 64, false, 128>;
-    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, DT_F32, 16, false, 64, false, 128>>(smem);
+    auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, false, 64, PS, CIN>;
+    cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, false, 64, PS, CIN>>(smem);
     if (e != cudaSuccess) return e;
     const int ctas = std::max(1, device_sm_count() / p.nslice);
     RowPlan rp;
@@ -1648,6 +1687,14 @@ bool rows128_fits(const ConvArgs &a) {
            a.ps == 0 && !a.res && !a.y2 && !a.amax && a.nimg == 1 && a.acc_scale == 1.f && a.out_scale == 1.f;
 }
 
+// 64 -> 256 channels, PixelShuffle(2) into a blocked 64-channel 16-bit tensor.
+bool rows_psb_fits(const ConvArgs &a) {
+    const int dt = a.in_dt;
+    return a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.out_dt == dt && a.cin_pad == 64 &&
+           a.in_cpc == 64 && a.cout == 256 && a.cout_pad == 256 && a.ps == 2 && !a.ps_out && a.out_cpc == 64 &&
+           !a.res && !a.y2 && !a.amax && a.nimg == 1 && a.acc_scale == 1.f && a.out_scale == 1.f;
+}
+
 // PixelShuffle(2) output layer with 64 input channels (<= 16 outputs, planar float32).
 bool rows_ps_fits(const ConvArgs &a) {
     const int dt = a.in_dt;
@@ -1739,7 +1786,22 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
         p.cout_pad = a.cout_pad;
         p.nslice = (a.cout_pad + 63) / 64;
         p.wbytes = (uint32_t)tc_rows128_weight_bytes(1);
-        return dt == DT_BF16 ? run_rows128<DT_BF16>(map, p, st) : run_rows128<DT_F16>(map, p, st);
+        return dt == DT_BF16 ? run_rows_sliced<DT_BF16, DT_F32, 16, false, 128>(map, p, st)
+                             : run_rows_sliced<DT_F16, DT_F32, 16, false, 128>(map, p, st);
+    }
+    if (rows_psb_fits(a)) {
+        ConvArgs b = a;
+        b.y = const_cast<void *>(a.x);  // the shuffle epilogue stores directly; the y / residual maps are unused
+        CUtensorMap map, ymap, rmap;
+        cudaError_t e = encode_row_maps(b, &map, &ymap, &rmap);
+        if (e != cudaSuccess) return e;
+        TcParams p = rows_params(a);
+        p.cout = a.cout;
+        p.cout_pad = a.cout_pad;
+        p.nslice = 4;
+        p.ps_act = a.ps_act;
+        return dt == DT_BF16 ? run_rows_sliced<DT_BF16, DT_BF16, 128, true, 64>(map, p, st)
+                             : run_rows_sliced<DT_F16, DT_F16, 128, true, 64>(map, p, st);
     }
     if (rows_ps_fits(a)) {
         ConvArgs b = a;

@@ -408,6 +408,11 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
             std::vector<uint8_t> rows(tc_rows128_weight_bytes((W.cout_pad + 63) / 64));
             prepare_weights_rows128(w, L.cout, f->act_dt, rows.data());
             s = upload(f, rows.data(), rows.size(), &W.rows);
+        } else if (s == NVISR_OK && L.op == "conv" && L.k == 3 && L.cin == 64 && L.cout == 256 && L.ps == 2) {
+            // an upsampler (64 -> 256, PixelShuffle(2)): one row image per shuffle offset
+            std::vector<uint8_t> rows(4 * tc_rows_weight_bytes(64));
+            prepare_weights_rows_ps4(w, f->act_dt, rows.data());
+            s = upload(f, rows.data(), rows.size(), &W.rows);
         } else if (s == NVISR_OK && L.op == "conv" && L.k == 3 && L.cin == 64 && L.cout <= 16 && L.cout % 4 == 0) {
             // a PixelShuffle(2) output layer: the row kernel's 16-column shuffle form
             std::vector<uint8_t> rows(tc_rows_weight_bytes(16));
