@@ -46,6 +46,40 @@ struct Cv<__half> {
     static __device__ __forceinline__ __half out(float v) { return __float2half_rn(v); }
 };
 
+// Two 16-bit elements of a 32-bit word (element 0 in the low half) <-> two floats.
+template <typename T>
+__device__ __forceinline__ float2 unpack_pair(uint32_t w);
+template <>
+__device__ __forceinline__ float2 unpack_pair<__nv_bfloat16>(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+template <>
+__device__ __forceinline__ float2 unpack_pair<__half>(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+template <typename T>
+__device__ __forceinline__ uint32_t pack_pair(float lo, float hi);
+template <>
+__device__ __forceinline__ uint32_t pack_pair<__nv_bfloat16>(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+template <>
+__device__ __forceinline__ uint32_t pack_pair<__half>(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// acc += s * v on two lanes: one packed FP32 FMA (each lane an IEEE fma, as the scalar form).
+__device__ __forceinline__ void ffma2(float2 &acc, float s, float2 v) {
+    uint64_t d, x, w;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(acc.x), "f"(acc.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(v.x), "f"(v.y));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(w) : "f"(s));
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(w), "l"(x));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(acc.x), "=f"(acc.y) : "l"(d));
+}
+
 // T: 16-bit element type of x / y; NS: output channels (one slice); C: input channels.
 template <typename T, int NS, int C>
 __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stages) {
@@ -159,20 +193,21 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                 // every corner load of every pass first, then the blends
                 uint4 v[NPASS][2];
                 float fly[NPASS], flx[NPASS];  // fractional position
-                uint32_t inb = 0;              // bit 4h + q: corner q of pass h inside the image
+                uint32_t rin = 0, cin_ = 0;    // bits 2h, 2h + 1: rows y0, y0 + 1 / columns x0, x0 + 1 inside
+                const float oy = (float)(y + k / 3 - 1), ox = (float)(xb + pb + k % 3 - 1);
 #pragma unroll
                 for (int h = 0; h < NPASS; ++h) {
-                    const int xx = xb + pb + h * 16;
-                    const float sy = (float)(y + k / 3 - 1) + dd[h].x;
-                    const float sx = (float)(xx + k % 3 - 1) + dd[h].y;
+                    const float sy = oy + dd[h].x;
+                    const float sx = (ox + (float)(h * 16)) + dd[h].y;
                     const float fy = floorf(sy), fx = floorf(sx);
                     const int y0 = (int)fy, x0 = (int)fx;
                     fly[h] = sy - fy;
                     flx[h] = sx - fx;
-                    const bool py = xx < W;
-                    const bool r0 = py && y0 >= 0 && y0 < H, r1 = py && y0 + 1 >= 0 && y0 + 1 < H;
-                    const bool c0 = x0 >= 0 && x0 < W, c1 = x0 + 1 >= 0 && x0 + 1 < W;
-                    inb |= (uint32_t)((r0 && c0) | ((r0 && c1) << 1) | ((r1 && c0) << 2) | ((r1 && c1) << 3)) << (4 * h);
+                    const bool py = xb + pb + h * 16 < W;
+                    const bool r0 = py && (unsigned)y0 < (unsigned)H, r1 = py && (unsigned)(y0 + 1) < (unsigned)H;
+                    const bool c0 = (unsigned)x0 < (unsigned)W, c1 = (unsigned)(x0 + 1) < (unsigned)W;
+                    rin |= ((uint32_t)r0 | ((uint32_t)r1 << 1)) << (2 * h);
+                    cin_ |= ((uint32_t)c0 | ((uint32_t)c1 << 1)) << (2 * h);
                     const bool mc = c ? c1 : c0;
                     // byte offsets of rows y0 and y0 + 1, each formed in full before it meets
                     // the pointer (y0 may be -1, where only the second is used)
@@ -183,39 +218,31 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                 }
 #pragma unroll
                 for (int h = 0; h < NPASS; ++h) {
-                    // row r: swap halves with the partner lane, then add corners (r, 0) and
-                    // (r, 1) of this lane's 4 channels (2 words) in corner order
-                    float acc[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[e] = 0.f;
+                    // corner (r, col) weight = row factor x column factor, each zero outside the image
+                    const float wy[2] = {(rin >> (2 * h)) & 1u ? 1.f - fly[h] : 0.f, (rin >> (2 * h + 1)) & 1u ? fly[h] : 0.f};
+                    const float wx[2] = {(cin_ >> (2 * h)) & 1u ? 1.f - flx[h] : 0.f,
+                                         (cin_ >> (2 * h + 1)) & 1u ? flx[h] : 0.f};
+                    // row r: swap halves with the partner lane (lane 0 keeps channels 0-3, lane 1
+                    // channels 4-7), then add corners (r, 0) and (r, 1) in corner order, two
+                    // channels per packed FMA
+                    float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
                         const uint4 o = v[h][r];
-                        const uint32_t s0 = c ? o.x : o.z, s1 = c ? o.y : o.w;
-                        const uint32_t g0 = __shfl_xor_sync(0xffffffffu, s0, 1);
-                        const uint32_t g1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-                        uint32_t cw[2][2];
-                        cw[0][0] = c ? g0 : o.x;
-                        cw[0][1] = c ? g1 : o.y;
-                        cw[1][0] = c ? o.z : g0;
-                        cw[1][1] = c ? o.w : g1;
-#pragma unroll
-                        for (int col = 0; col < 2; ++col) {
-                            const int q = 2 * r + col;
-                            const float wq = (inb >> (4 * h + q)) & 1u
-                                                 ? (r ? fly[h] : 1.f - fly[h]) * (col ? flx[h] : 1.f - flx[h])
-                                                 : 0.f;
-                            const T *vv = reinterpret_cast<const T *>(cw[col]);
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) acc[e] += wq * Cv<T>::in(vv[e]);
-                        }
+                        const uint32_t g0 = __shfl_xor_sync(0xffffffffu, c ? o.x : o.z, 1);
+                        const uint32_t g1 = __shfl_xor_sync(0xffffffffu, c ? o.y : o.w, 1);
+                        const uint32_t a0 = c ? g0 : o.x, a1 = c ? g1 : o.y;  // column x0
+                        const uint32_t b0 = c ? o.z : g0, b1 = c ? o.w : g1;  // column x0 + 1
+                        const float wa = wy[r] * wx[0], wb = wy[r] * wx[1];
+                        ffma2(acc[0], wa, unpack_pair<T>(a0));
+                        ffma2(acc[1], wa, unpack_pair<T>(a1));
+                        ffma2(acc[0], wb, unpack_pair<T>(b0));
+                        ffma2(acc[1], wb, unpack_pair<T>(b1));
                     }
                     float mm = msk[h];
-                    if (a.mask_logits) mm = 1.f / (1.f + expf(-mm));
-                    alignas(8) T o[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) o[e] = Cv<T>::out(acc[e] * mm);
-                    *reinterpret_cast<uint2 *>(stg + (size_t)(pb + h * 16) * 16) = *reinterpret_cast<const uint2 *>(o);
+                    if (a.mask_logits) mm = __frcp_rn(1.f + expf(-mm));
+                    *reinterpret_cast<uint2 *>(stg + (size_t)(pb + h * 16) * 16) =
+                        make_uint2(pack_pair<T>(acc[0].x * mm, acc[0].y * mm), pack_pair<T>(acc[1].x * mm, acc[1].y * mm));
                 }
                 fence_proxy_async();  // generic smem writes -> visible to the tensor core
                 mbar_arrive(&full[s]);
