@@ -70,7 +70,9 @@ struct nvisr_engine {
     int64_t used = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;  // host <-> device copies of push / pull, beside the compute stream
     int *err_word = nullptr;  // device error word shared by this engine's kernels
+    int *err_host = nullptr;  // pinned host copy of it, read after a pull's copies
     std::vector<nvisr_filter *> filters;
 };
 
@@ -206,8 +208,17 @@ struct nvisr_filter {
     float *out_rgb[2] = {nullptr, nullptr};  // planar float32 residuals [3][sH][opitch]
     SkipArgs skip[2] = {};                   // skip path of each output slot (added by requantise)
     int64_t opitch = 0;
-    void *ostage[3] = {nullptr, nullptr, nullptr};
+    void *ostage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // alternate per pull
     int64_t ostage_pitch[3] = {0, 0, 0};
+    int obuf = 0;
+
+    // host-plane copies on the engine's copy stream: the H2D of a push and the
+    // D2H of a pull overlap the compute stream's work; a pull of host planes
+    // also starts the next ready output (read-ahead), unless the filter has
+    // joined a batch (whose step computes its outputs)
+    cudaEvent_t ev_h2d = nullptr, ev_stage = nullptr, ev_req = nullptr, ev_d2h = nullptr;
+    bool stage_used = false;
+    bool batched = false;
 
     // group family: run cache (outputs of the last run)
     int64_t cached_run = -1;
@@ -224,8 +235,9 @@ struct nvisr_filter {
 
     // per-kernel timing (nvisr_filter_profile)
     bool prof = false;
-    struct Rec { int kind; cudaEvent_t a, b; };
+    struct Rec { int kind; cudaEvent_t a, b; int n; };  // n launches of one kind, back to back
     std::vector<Rec> recs;
+    bool prof_join = false;  // the next scope of the last record's kind may extend it
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms[NVISR_K_COUNT] = {0};
     int64_t prof_n[NVISR_K_COUNT] = {0};
@@ -251,33 +263,48 @@ void flush_profile(nvisr_filter *f) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
             f->prof_ms[r.kind] += ms;
-            f->prof_n[r.kind] += 1;
+            f->prof_n[r.kind] += r.n;
         }
         f->ev_pool.push_back(r.a);
         f->ev_pool.push_back(r.b);
     }
     f->recs.clear();
+    f->prof_join = false;
 }
 
-// Records CUDA events around the launches issued during its lifetime.
+// Records CUDA events around the launches issued during its lifetime.  Back-to-back
+// scopes of one kind (a trunk's 20 body layers) share one event pair: the later
+// scope moves the record's end event, so the timed stream carries few events.
 struct ProfScope {
     nvisr_filter *f;
     int kind;
     cudaEvent_t a = nullptr;
+    bool join = false;
     ProfScope(nvisr_filter *f_, int kind_) : f(f_), kind(kind_) {
-        if (f->prof) {
+        if (!f->prof) return;
+        join = f->prof_join && !f->recs.empty() && f->recs.back().kind == kind;
+        if (!join) {
             a = take_event(f);
             cudaEventRecord(a, f->eng->stream);
         }
     }
     ~ProfScope() {
+        if (join) {
+            cudaEventRecord(f->recs.back().b, f->eng->stream);
+            f->recs.back().n += 1;
+            return;
+        }
         if (!a) return;
         cudaEvent_t b = take_event(f);
         cudaEventRecord(b, f->eng->stream);
-        f->recs.push_back({kind, a, b});
+        f->recs.push_back({kind, a, b, 1});
+        f->prof_join = true;
         if (f->recs.size() > 4096) flush_profile(f);
     }
 };
+
+// Stream work outside a ProfScope: the next scope starts a record of its own.
+void prof_gap(nvisr_filter *f) { f->prof_join = false; }
 
 float *ring_slot(nvisr_filter *f, int64_t frame) {
     return f->ring_base + (frame % f->ring) * f->slot_floats;
@@ -338,18 +365,6 @@ bool calibration_ready(const nvisr_filter *f) {
 bool output_ready(const nvisr_filter *f, int64_t o) {
     if (f->net.family == "group") return group_ready(f, o / 2, nullptr);
     return tuple_ready(f, o, nullptr) && calibration_ready(f);
-}
-
-nvisr_status check_device_error(nvisr_filter *f) {
-    int h = 0;
-    NVISR_TRY_CUDA(cudaMemcpyAsync(&h, f->eng->err_word, sizeof(int), cudaMemcpyDeviceToHost, f->eng->stream));
-    NVISR_TRY_CUDA(cudaStreamSynchronize(f->eng->stream));
-    if (h != 0) {
-        cudaMemsetAsync(f->eng->err_word, 0, sizeof(int), f->eng->stream);
-        return fail(NVISR_DEVICE_TIMEOUT, "a device-side wait exceeded its time bound (error word " +
-                                              std::to_string(h) + ")");
-    }
-    return NVISR_OK;
 }
 
 // ---------------------------------------------------------------- plan
@@ -1066,6 +1081,7 @@ nvisr_status calibrate(nvisr_filter *f) {
     const int n = (int)(f->eos ? std::min<int64_t>(f->calib_frames, f->pushed) : f->calib_frames);
     std::vector<int64_t> idx;
     NVISR_TRY_CUDA(cudaMemsetAsync(f->amax, 0, sizeof(unsigned) * f->n_amax, f->eng->stream));
+    prof_gap(f);
     for (int t = 0; t < n; ++t) {
         tuple_ready(f, t, &idx);
         nvisr_status s = forward_tuple(f, idx, true);
@@ -1105,13 +1121,16 @@ nvisr_status compute_output(nvisr_filter *f, int64_t o) {
 
 int output_slot(const nvisr_filter *f, int64_t o) { return f->net.family == "group" ? (int)(o % 2) : 0; }
 
-nvisr_status write_output(nvisr_filter *f, nvisr_planes *out, int slot) {
+// Requantises output slot `slot` into the caller's device planes, or into the
+// current staging buffer followed by its D2H copy (and the error word's) on the
+// copy stream; write_output_end waits for those copies.
+nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, int slot) {
     cudaStream_t st = f->eng->stream;
     const nvisr_format &of = f->out_fmt;
     void *dst[3];
     int64_t pitch[3];
     for (int p = 0; p < 3; ++p) {
-        dst[p] = out->on_device ? out->data[p] : f->ostage[p];
+        dst[p] = out->on_device ? out->data[p] : f->ostage[f->obuf][p];
         pitch[p] = out->on_device ? out->pitch[p] : f->ostage_pitch[p];
     }
     cudaError_t e;
@@ -1122,11 +1141,28 @@ nvisr_status write_output(nvisr_filter *f, nvisr_planes *out, int slot) {
     }
     if (e != cudaSuccess) return cuda_status(e, "requant");
     if (out->on_device) return NVISR_OK;
+    cudaStream_t cs = f->eng->copy_stream;
+    NVISR_TRY_CUDA(cudaEventRecord(f->ev_req, st));
+    NVISR_TRY_CUDA(cudaStreamWaitEvent(cs, f->ev_req, 0));
     for (int p = 0; p < 3; ++p)
-        NVISR_TRY_CUDA(cudaMemcpy2DAsync(out->data[p], out->pitch[p], f->ostage[p], f->ostage_pitch[p],
-                                         plane_row_bytes(of, p), plane_rows(of, p), cudaMemcpyDeviceToHost, st));
-    NVISR_TRY_CUDA(cudaStreamSynchronize(st));
-    return check_device_error(f);
+        NVISR_TRY_CUDA(cudaMemcpy2DAsync(out->data[p], out->pitch[p], f->ostage[f->obuf][p], f->ostage_pitch[p],
+                                         plane_row_bytes(of, p), plane_rows(of, p), cudaMemcpyDeviceToHost, cs));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(f->eng->err_host, f->eng->err_word, sizeof(int), cudaMemcpyDeviceToHost, cs));
+    NVISR_TRY_CUDA(cudaEventRecord(f->ev_d2h, cs));
+    return NVISR_OK;
+}
+
+nvisr_status write_output_end(nvisr_filter *f) {
+    NVISR_TRY_CUDA(cudaEventSynchronize(f->ev_d2h));
+    f->obuf ^= 1;  // the next requantise writes the other staging buffer
+    const int h = *f->eng->err_host;
+    if (h != 0) {
+        cudaMemsetAsync(f->eng->err_word, 0, sizeof(int), f->eng->stream);
+        prof_gap(f);
+        return fail(NVISR_DEVICE_TIMEOUT, "a device-side wait exceeded its time bound (error word " +
+                                              std::to_string(h) + ")");
+    }
+    return NVISR_OK;
 }
 
 }  // namespace
@@ -1343,11 +1379,16 @@ nvisr_status nvisr_engine_create(const nvisr_engine_desc *desc, nvisr_engine **o
         }
         e->own_stream = true;
     }
-    if (cudaMalloc(&e->err_word, sizeof(int)) != cudaSuccess || cudaMemset(e->err_word, 0, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&e->err_word, sizeof(int)) != cudaSuccess || cudaMemset(e->err_word, 0, sizeof(int)) != cudaSuccess ||
+        cudaHostAlloc(&e->err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&e->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(e->err_word);
+        if (e->err_host) cudaFreeHost(e->err_host);
         if (e->own_stream) cudaStreamDestroy(e->stream);
         delete e;
-        return fail(NVISR_OUT_OF_MEMORY, "error word allocation failed");
+        return fail(NVISR_OUT_OF_MEMORY, "error word or copy stream allocation failed");
     }
+    *e->err_host = 0;
     *out = e;
     return NVISR_OK;
 }
@@ -1357,8 +1398,11 @@ void nvisr_filter_destroy(nvisr_filter *f) {
     nvisr_engine *e = f->eng;
     cudaSetDevice(e->device);
     cudaStreamSynchronize(e->stream);
+    cudaStreamSynchronize(e->copy_stream);
     flush_profile(f);
     for (cudaEvent_t ev : f->ev_pool) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : {f->ev_h2d, f->ev_stage, f->ev_req, f->ev_d2h})
+        if (ev) cudaEventDestroy(ev);
     for (DevBuf &b : f->owned) {
         cudaFree(b.ptr);
         e->used -= (int64_t)b.bytes;
@@ -1372,8 +1416,11 @@ void nvisr_engine_destroy(nvisr_engine *e) {
     while (!e->filters.empty()) nvisr_filter_destroy(e->filters.back());
     cudaSetDevice(e->device);
     cudaStreamSynchronize(e->stream);
+    cudaStreamSynchronize(e->copy_stream);
     cudaFree(e->err_word);
+    cudaFreeHost(e->err_host);
     if (e->own_stream) cudaStreamDestroy(e->stream);
+    cudaStreamDestroy(e->copy_stream);
     delete e;
 }
 
@@ -1439,8 +1486,12 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
         const int64_t bytes = plane_bytes(d->in_fmt, pl, &f->stage_pitch[pl], &rows);
         if ((s = dalloc(e, bytes, f->owned, &f->stage[pl])) != NVISR_OK) return cleanup(s);
         const int64_t obytes = plane_bytes(d->out_fmt, pl, &f->ostage_pitch[pl], &rows);
-        if ((s = dalloc(e, obytes, f->owned, &f->ostage[pl])) != NVISR_OK) return cleanup(s);
+        for (int b = 0; b < 2; ++b)
+            if ((s = dalloc(e, obytes, f->owned, &f->ostage[b][pl])) != NVISR_OK) return cleanup(s);
     }
+    for (cudaEvent_t *ev : {&f->ev_h2d, &f->ev_stage, &f->ev_req, &f->ev_d2h})
+        if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess)
+            return cleanup(fail(NVISR_CUDA_ERROR, "cudaEventCreate failed"));
     f->opitch = round_up64((int64_t)W * net.scale, 4);
     for (int k = 0; k < 2; ++k) {
         if ((s = dalloc(e, sizeof(float) * 3 * f->opitch * H * net.scale, f->owned, &p)) != NVISR_OK)
@@ -1470,17 +1521,22 @@ nvisr_status nvisr_push(nvisr_filter *f, const nvisr_planes *in, uint32_t flags)
     cudaStream_t st = f->eng->stream;
     const void *src[3];
     int64_t pitch[3];
-    for (int p = 0; p < 3; ++p) {
-        if (in->on_device) {
-            src[p] = in->data[p];
-            pitch[p] = in->pitch[p];
-        } else {
+    if (!in->on_device) {
+        // host planes go through the staging planes on the copy stream, once the previous
+        // frame's ingest has read them; the compute stream waits for the copy
+        cudaStream_t cs = f->eng->copy_stream;
+        if (f->stage_used) NVISR_TRY_CUDA(cudaEventSynchronize(f->ev_stage));
+        for (int p = 0; p < 3; ++p)
             NVISR_TRY_CUDA(cudaMemcpy2DAsync(f->stage[p], f->stage_pitch[p], in->data[p], in->pitch[p],
                                              plane_row_bytes(f->in_fmt, p), plane_rows(f->in_fmt, p),
-                                             cudaMemcpyHostToDevice, st));
-            src[p] = f->stage[p];
-            pitch[p] = f->stage_pitch[p];
-        }
+                                             cudaMemcpyHostToDevice, cs));
+        NVISR_TRY_CUDA(cudaEventRecord(f->ev_h2d, cs));
+        NVISR_TRY_CUDA(cudaStreamWaitEvent(st, f->ev_h2d, 0));
+        prof_gap(f);
+    }
+    for (int p = 0; p < 3; ++p) {
+        src[p] = in->on_device ? in->data[p] : f->stage[p];
+        pitch[p] = in->on_device ? in->pitch[p] : f->stage_pitch[p];
     }
     cudaError_t e;
     {
@@ -1489,7 +1545,11 @@ nvisr_status nvisr_push(nvisr_filter *f, const nvisr_planes *in, uint32_t flags)
                           f->rpitch, st);
     }
     if (e != cudaSuccess) return cuda_status(e, "ingest");
-    if (!in->on_device) NVISR_TRY_CUDA(cudaStreamSynchronize(st));  // host planes may be reused on return
+    if (!in->on_device) {
+        NVISR_TRY_CUDA(cudaEventRecord(f->ev_stage, st));
+        f->stage_used = true;
+        NVISR_TRY_CUDA(cudaEventSynchronize(f->ev_h2d));  // host planes may be reused on return
+    }
     f->cut.push_back((flags & NVISR_FRAME_SCENE_CUT) && f->pushed > 0 ? 1 : 0);
     f->pushed++;
     return NVISR_OK;
@@ -1527,7 +1587,16 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
     } else {
         f->produced.pop_front();
     }
-    if ((s = write_output(f, out, output_slot(f, o))) != NVISR_OK) return s;
+    if ((s = write_output_begin(f, out, output_slot(f, o))) != NVISR_OK) return s;
+    if (!out->on_device) {
+        // read-ahead: the next output's network runs on the compute stream while this
+        // output's planes are copied out
+        const int64_t n = o + 1;
+        if (!f->batched && f->produced.empty() && !(f->eos && n >= f->total_out) && output_ready(f, n) &&
+            compute_output(f, n) == NVISR_OK)
+            f->produced.push_back(n);
+        if ((s = write_output_end(f)) != NVISR_OK) return s;
+    }
     if (info) {
         std::vector<int64_t> idx;
         if (f->net.family == "group") group_ready(f, o / 2, &idx);
@@ -1599,6 +1668,7 @@ nvisr_status nvisr_batch_create(nvisr_engine *e, nvisr_filter *const *filters, i
             if (g == f) return fail(NVISR_INVALID_ARG, "batch_create: filter listed twice");
         b->members.push_back(f);
     }
+    for (nvisr_filter *f : b->members) f->batched = true;  // its outputs are the batch step's
     const nvisr_filter *f0 = b->members[0];
     b->shared = true;
     for (const nvisr_filter *f : b->members)
