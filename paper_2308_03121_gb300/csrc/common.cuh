@@ -175,6 +175,10 @@ void prepare_weights_rows128(const float *w_oihw, int cout, int dt, void *dst_ho
 // 3x3 64 -> 256 layer followed by PixelShuffle(2): 4 row-streaming images of 64
 // outputs (tc_rows_weight_bytes() each), image s holding conv channels 4n + s.
 void prepare_weights_rows_ps4(const float *w_oihw, int dt, void *dst_host);
+// FP8 row-streaming image of a 64 -> 64 3x3 layer (weights x scale, E4M3):
+// [kx][16-byte chunk][2 - ky][64 out][16 channels], no swizzle.
+size_t tc_rows_f8_weight_bytes();
+void prepare_weights_rows_f8(const float *w_oihw, float scale, void *dst_host);
 
 // DCN: x blocked (activation dtype); offsets and mask in one blocked float32
 // tensor [om_cpad/4][H][W][4].  Channel order: torchvision's ([0, 18G) = (dy, dx)

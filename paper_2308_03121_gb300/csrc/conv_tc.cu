@@ -72,6 +72,7 @@ struct TcParams {
     int64_t ps_pitch;
     ConvArgs skip;  // skip_* fields only
     int ps_act;
+    int no_main;                      // row kernel: no 16-bit output, the FP8 copy (y2) is the output
     int *err;
 };
 
@@ -491,6 +492,14 @@ __device__ __forceinline__ void add_f32x2(float &a, float &b, float c, float d) 
     asm("add.rn.f32x2 %0, %0, %1;" : "+l"(x) : "l"(y));
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
 }
+__device__ __forceinline__ void fma_f32x2(float &a, float &b, float s0, float s1, float c0, float c1) {
+    uint64_t x, y, z;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a), "f"(b));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(s0), "f"(s1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(z) : "f"(c0), "f"(c1));
+    asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x) : "l"(y), "l"(z));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+}
 __device__ __forceinline__ void mul_f32x2(float &a, float &b, float c, float d) {
     uint64_t x, y;
     asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a), "f"(b));
@@ -552,7 +561,9 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                                                                 const TcParams p, const RowPlan rp,
                                                                 const RowProblem *__restrict__ probs, int nprob) {
     using TO = typename Elem<OUT_DT>::T;
-    constexpr int AFMT = IN_DT == DT_BF16 ? 1 : 0;
+    constexpr int AFMT = IN_DT == DT_BF16 ? 1 : 0;       // BF16 (kind::f16) or E4M3 / F16 (0)
+    constexpr bool F8IN = IN_DT == DT_E4M3;              // FP8 rows: kind::f8f6f4, K = 32
+    constexpr int KIND = F8IN ? 1 : 0;
     constexpr int PXS = TM + 2;
     // CIN: input channels of a row.  64: one 128-byte line per pixel, 128-byte swizzled;
     // 128: two such lines per pixel, one 130-pixel region per 64-channel chunk
@@ -560,12 +571,16 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     // address, so a region may start inside a 1 KB atom);
     // 16 (the tuple head): two 16-byte channel chunks per pixel, canonical no-swizzle
     // layout [chunk][pixel][16 B] (K core matrices LBO_A apart)
+    // FP8 (64 channels): four 16-byte chunks per pixel in the same no-swizzle
+    // [chunk][pixel][16 B] layout as the 16-channel head, two chunks per K = 32 step
     static_assert(CIN == 64 || (CIN == 128 && NPR == 64 && !PS && !MULTI) || (CIN == 16 && NPR == 64 && !PS),
                   "64- or 128-channel rows or the 16-channel head");
-    constexpr bool SW = CIN != 16;                            // 128-byte swizzled operands
-    constexpr int KSTEPS = CIN == 16 ? 1 : CIN / 16;         // 16-channel MMA K steps per kx
+    static_assert(!F8IN || (CIN == 64 && NPR == 64 && !PS && !MULTI), "FP8 rows: 64 -> 64 trunk layers");
+    constexpr bool SW = CIN != 16 && !F8IN;                   // 128-byte swizzled operands
+    constexpr int NCHK = F8IN ? 4 : 2;                        // 16-byte chunks per pixel (no-swizzle forms)
+    constexpr int KSTEPS = SW ? CIN / 16 : NCHK / 2;         // MMA K steps per kx
     constexpr uint32_t AREG = PXS * 128;                      // one 64-channel chunk of a row (swizzled forms)
-    constexpr uint32_t AROW = SW ? (CIN / 64) * AREG : 2 * PXS * 16;  // bytes of one 130-pixel input row
+    constexpr uint32_t AROW = SW ? (CIN / 64) * AREG : NCHK * PXS * 16;  // bytes of one 130-pixel input row
     constexpr uint32_t ROWB = (AROW + 1023u) & ~1023u;
     constexpr uint32_t LBO_A = PXS * 16, LBO_B = 3 * NPR * 16;
     // NPR: accumulator columns of one output row (= padded output channels: 64 for the
@@ -576,9 +591,9 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     // output pixel (2o + i, 2x + j), written as one 128-byte line per pixel
     static_assert(NPR == 64 || (NPR == 16 && PS), "64-channel trunk rows or 16-channel shuffle tail");
     constexpr bool PSB = PS && NPR == 64;
-    // weights of one kx: [64-channel chunk][ky' = 2 - ky][NPR][128 B] (CIN 64, 128) or
-    // [2 chunks][3 * NPR][16 B] (CIN 16)
-    constexpr uint32_t WKX = SW ? (CIN / 64) * 3 * NPR * 128 : 2 * 3 * NPR * 16;
+    // weights of one kx: [64-channel chunk][ky' = 2 - ky][NPR][128 B] (swizzled forms) or
+    // [NCHK chunks][3 * NPR][16 B] (CIN 16, FP8)
+    constexpr uint32_t WKX = SW ? (CIN / 64) * 3 * NPR * 128 : NCHK * 3 * NPR * 16;
     constexpr uint32_t TILEB = TM * 128;                      // one 128-pixel output / residual row tile
     constexpr int NSLOT = 8;                                  // output-row accumulators in TMEM
     static_assert(NSLOT == 8, "slot index and phase use & 7 and >> 3");
@@ -626,7 +641,9 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     const int nsl = MULTI ? 1 : p.nslice;
     const int slice = (int)blockIdx.x % nsl;
     const int cta0 = (int)blockIdx.x / nsl, cstride = (int)gridDim.x / nsl;
-    const bool plain = p.acc_scale == 1.f && p.out_scale == 1.f && p.res_scale == 1.f && !p.amax && !p.y2;
+    // unit scales: packed bias / activation / residual arithmetic (the FP8 copy and the
+    // amax read the same values either way)
+    const bool plain = p.acc_scale == 1.f && p.out_scale == 1.f && p.res_scale == 1.f;
     auto strip_of = [&](int sidx, int &img, int &x0, int &ra, int &rb, int &pi) {
         if (MULTI) {
             pi = 0;
@@ -701,8 +718,9 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         break;
                     }
                     mbar_arrive_expect_tx(&full[s], AROW);
-                    tma_load_4d(stage0 + (size_t)s * ROWB, tmap_of(pi), &full[s], 0, x0 - 1, r, CIN == 64 ? img : 2 * img);
-                    // (CIN 128 and 16: one box of both channel chunks of the row)
+                    tma_load_4d(stage0 + (size_t)s * ROWB, tmap_of(pi), &full[s], 0, x0 - 1, r,
+                                SW ? (CIN == 64 ? img : 2 * img) : NCHK * img);
+                    // (CIN 128, 16 and FP8: one box of all channel chunks of the row)
                 }
             }
             for (int k = 0; k < S && k < gin; ++k) {
@@ -746,11 +764,11 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
             // block per 64 channels
             auto a_off = [&](int t) {
                 const int kx = t / KSTEPS, j = t % KSTEPS;
-                return (uint64_t)((SW ? kx * 128 + (j >> 2) * (int)AREG + (j & 3) * 32 : kx * 16) >> 4);
+                return (uint64_t)((SW ? kx * 128 + (j >> 2) * (int)AREG + (j & 3) * 32 : kx * 16 + j * 2 * (int)LBO_A) >> 4);
             };
             auto b_off = [&](int t) {
                 const int kx = t / KSTEPS, j = t % KSTEPS;
-                return (uint64_t)((kx * WKX + (SW ? (j >> 2) * 3 * NPR * 128 + (j & 3) * 32 : 0)) >> 4);
+                return (uint64_t)((kx * WKX + (SW ? (j >> 2) * 3 * NPR * 128 + (j & 3) * 32 : j * 2 * (int)LBO_B)) >> 4);
             };
             auto a_desc = [&]() {
                 return SW ? smem_desc_sw128(smem_u32(stage0 + (size_t)s * ROWB), 0)
@@ -787,23 +805,23 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                             const int olen = old_hi - o_lo + 1;
                             if (olen > 0) {
                                 const int f0 = min(olen, m0), f1 = olen - f0;
-                                umma<0>(md0, a_base, mb0, id0 + nstep * (uint32_t)f0, 1u);
-                                if (f1 > 0) umma<0>(md1, a_base, mb1, id0 + nstep * (uint32_t)f1, 1u);
+                                umma<KIND>(md0, a_base, mb0, id0 + nstep * (uint32_t)f0, 1u);
+                                if (f1 > 0) umma<KIND>(md1, a_base, mb1, id0 + nstep * (uint32_t)f1, 1u);
                             }
                             if (fresh)
-                                umma<0>(tmem_base + (uint32_t)(slot_of(r + 1) * NPR), a_base, bd_of(r + 1),
+                                umma<KIND>(tmem_base + (uint32_t)(slot_of(r + 1) * NPR), a_base, bd_of(r + 1),
                                         id0 + nstep, 0u);
                         }
                         if (m1 == 0) {
 #pragma unroll
                             for (int t = 1; t < 3 * KSTEPS; ++t)
-                                umma<0>(md0, a_base + a_off(t), mb0 + b_off(t), mi0, 1u);
+                                umma<KIND>(md0, a_base + a_off(t), mb0 + b_off(t), mi0, 1u);
                         } else {
 #pragma unroll
                             for (int t = 1; t < 3 * KSTEPS; ++t) {
                                 const uint64_t ad = a_base + a_off(t), boff = b_off(t);
-                                umma<0>(md0, ad, mb0 + boff, mi0, 1u);
-                                umma<0>(md1, ad, mb1 + boff, mi1, 1u);
+                                umma<KIND>(md0, ad, mb0 + boff, mi0, 1u);
+                                umma<KIND>(md1, ad, mb1 + boff, mi1, 1u);
                             }
                         }
                     }
@@ -833,15 +851,15 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                 constexpr uint32_t BROW = NPR * (SW ? 128 : 16);  // B bytes of one output row's taps
                 const uint32_t md0 = tmem_base + (uint32_t)(SL0 * NPR), md1 = tmem_base;
                 const uint64_t mb0 = b_base, mb1 = b_base + (uint64_t)((M0 * BROW) >> 4);
-                umma<0>(md0, a_base, mb0, ID0 + NST * F0, 1u);
-                if constexpr (F1 > 0) umma<0>(md1, a_base, mb1, ID0 + NST * F1, 1u);
-                umma<0>(tmem_base + (uint32_t)(((SL0 + 2) & (NSLOT - 1)) * NPR), a_base,
+                umma<KIND>(md0, a_base, mb0, ID0 + NST * F0, 1u);
+                if constexpr (F1 > 0) umma<KIND>(md1, a_base, mb1, ID0 + NST * F1, 1u);
+                umma<KIND>(tmem_base + (uint32_t)(((SL0 + 2) & (NSLOT - 1)) * NPR), a_base,
                         b_base + (uint64_t)((2 * BROW) >> 4), ID0 + NST, 0u);
 #pragma unroll
                 for (int t = 1; t < 3 * KSTEPS; ++t) {
                     const uint64_t ad = a_base + a_off(t), boff = b_off(t);
-                    umma<0>(md0, ad, mb0 + boff, MI0, 1u);
-                    if constexpr (M1 > 0) umma<0>(md1, ad, mb1 + boff, MI1, 1u);
+                    umma<KIND>(md0, ad, mb0 + boff, MI0, 1u);
+                    if constexpr (M1 > 0) umma<KIND>(md1, ad, mb1 + boff, MI1, 1u);
                 }
                 umma_commit(&empty[s]);
                 umma_commit(&rowdone[SL0]);
@@ -1024,15 +1042,22 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         grp_stop[g] = 1;
                     }
                 }
-                if (plain) {
-                    // 16-bit trunk layer (unit scales, no calibration): packed f32x2 arithmetic
-                    // keeps the epilogue's instruction stream short, because its warps share
-                    // issue slots with the MMA-issuing warp (same results as the general path)
+                if (plain || F8IN) {
+                    // 16-bit trunk layer (unit scales, no calibration) or FP8 layer: packed
+                    // f32x2 arithmetic keeps the epilogue's instruction stream short, because
+                    // its warps share issue slots with the MMA-issuing warp (same results as
+                    // the general path)
+                    const float as = p.acc_scale;
 #pragma unroll
                     for (int e = 0; e < 64; e += 4) {
                         const float4 b = *reinterpret_cast<const float4 *>(sbias + e);
-                        add_f32x2(v[e], v[e + 1], b.x, b.y);
-                        add_f32x2(v[e + 2], v[e + 3], b.z, b.w);
+                        if (F8IN) {
+                            fma_f32x2(v[e], v[e + 1], as, as, b.x, b.y);
+                            fma_f32x2(v[e + 2], v[e + 3], as, as, b.z, b.w);
+                        } else {
+                            add_f32x2(v[e], v[e + 1], b.x, b.y);
+                            add_f32x2(v[e + 2], v[e + 3], b.z, b.w);
+                        }
                     }
                     if (p.act == 1) {
 #pragma unroll
@@ -1069,7 +1094,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                         for (int h = 0; h < 4; ++h) {
                             float r0, r1;
                             unpack2<TO>(wd[h], r0, r1);
-                            if (plain) {
+                            if (plain || (F8IN && rs == 1.f)) {
                                 add_f32x2(v[uu * 8 + 2 * h], v[uu * 8 + 2 * h + 1], r0, r1);
                             } else {
                                 v[uu * 8 + 2 * h] += r0 * rs;
@@ -1085,17 +1110,26 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                     atomicMax(p.amax, __float_as_uint(amax));
                 }
                 if (valid && p.y2) {
+                    // FP8 copy: scaled in pairs, converted two values per instruction
                     const int64_t pix = (int64_t)o * p.W + x;
+                    const float ys = p.y2_scale;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        alignas(16) __nv_fp8_e4m3 o8[16];
+                        uint32_t w8[4];
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) o8[e] = __nv_fp8_e4m3(v[c * 16 + e] * p.y2_scale);
+                        for (int h = 0; h < 4; ++h) {
+                            float a0 = v[c * 16 + 4 * h], a1 = v[c * 16 + 4 * h + 1];
+                            float a2 = v[c * 16 + 4 * h + 2], a3 = v[c * 16 + 4 * h + 3];
+                            mul_f32x2(a0, a1, ys, ys);
+                            mul_f32x2(a2, a3, ys, ys);
+                            const __nv_fp8x2_e4m3 lo(make_float2(a0, a1)), hi(make_float2(a2, a3));
+                            w8[h] = (uint32_t)lo.__x | ((uint32_t)hi.__x << 16);
+                        }
                         *reinterpret_cast<uint4 *>(p.y2 + (((int64_t)img * (p.cout_pad / 16) + c) * HW + pix) * 16) =
-                            *reinterpret_cast<const uint4 *>(o8);
+                            make_uint4(w8[0], w8[1], w8[2], w8[3]);
                     }
                 }
-                if (!plain) {
+                if (!plain && !F8IN) {
                     const float os = p.out_scale;
 #pragma unroll
                     for (int e = 0; e < 64; ++e) v[e] *= os;
@@ -1133,7 +1167,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                             if (u0 + uu < nun)
                                 yo[(int64_t)uu * HW] = make_float4(v[4 * uu], v[4 * uu + 1], v[4 * uu + 2], v[4 * uu + 3]);
                     }
-                } else {
+                } else if (!p.no_main) {
 #pragma unroll
                     for (int uu = 0; uu < NU; ++uu) {
                         const int unit = uu ^ (m & 7);
@@ -1152,7 +1186,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
                     ok = false;
                     break;
                 }
-                if (!F32OUT && !PSB && leader) {
+                if (!F32OUT && !PSB && !p.no_main && leader) {
                     tma_store_4d(ymap_of(pi), obuf + g * TILEB, 0, x0, o, img);
                     bulk_commit_group();
                     if (has_res && o + 2 < rb) {  // this group's next row; the buffer's readers are done
@@ -1523,6 +1557,24 @@ void prepare_weights_rows128(const float *w, int cout, int dt, void *dst) {
                 }
 }
 
+size_t tc_rows_f8_weight_bytes() { return (size_t)3 * 4 * 3 * 64 * 16; }
+
+void prepare_weights_rows_f8(const float *w, float scale, void *dst) {
+    uint8_t *out = static_cast<uint8_t *>(dst);
+    memset(out, 0, tc_rows_f8_weight_bytes());
+    // [kx][16-byte chunk kc][ky' = 2 - ky][64 out][16 channels], E4M3, no swizzle
+    for (int n = 0; n < 64; ++n)
+        for (int c = 0; c < 64; ++c)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx) {
+                    const float v = w[((size_t)n * 64 + c) * 9 + ky * 3 + kx] * scale;
+                    const size_t row = (size_t)(2 - ky) * 64 + n;
+                    const size_t off = ((size_t)kx * 4 + c / 16) * 192 * 16 + row * 16 + (c % 16);
+                    const __nv_fp8_e4m3 q(v);
+                    memcpy(out + off, &q, 1);
+                }
+}
+
 void prepare_weights_rows_ps4(const float *w, int dt, void *dst) {
     // slice s = 2i + j: conv channels 4n + s (output channel n at shuffle offset (i, j))
     std::vector<float> ws((size_t)64 * 64 * 9);
@@ -1539,10 +1591,13 @@ namespace {
 // the input-row ring, 2 output staging tiles (16-bit outputs) and, when the
 // layer adds a residual, 2 residual tiles (without one, their room goes to
 // deeper input prefetch).
-inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false, int cin = 64, bool f32out = false) {
-    const uint32_t ROWB = cin != 16 ? (((uint32_t)(cin / 64) * (TM + 2) * 128 + 1023u) & ~1023u)
-                                    : ((2 * (TM + 2) * 16 + 1023u) & ~1023u);
-    const uint32_t WB = cin != 16 ? 3 * 3 * (uint32_t)(cin / 64) * (uint32_t)npr * 128 : 3 * 2 * 3 * (uint32_t)npr * 16;
+inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false, int cin = 64, bool f32out = false,
+                       bool f8 = false) {
+    const uint32_t nchk = f8 ? 4u : 2u;  // 16-byte chunks per pixel of the no-swizzle forms
+    const bool sw = cin != 16 && !f8;
+    const uint32_t ROWB = sw ? (((uint32_t)(cin / 64) * (TM + 2) * 128 + 1023u) & ~1023u)
+                             : ((nchk * (TM + 2) * 16 + 1023u) & ~1023u);
+    const uint32_t WB = sw ? 3 * 3 * (uint32_t)(cin / 64) * (uint32_t)npr * 128 : 3 * nchk * 3 * (uint32_t)npr * 16;
     const uint32_t TILES = ps || f32out ? 0u : (res ? 4u : 2u) * TM * 128;
     int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES) / (int)ROWB;
     if (stages > 8) stages = 8;
@@ -1554,7 +1609,7 @@ template <int IN_DT, int OUT_DT, int CBO, int NPR = 64, bool PS = false, int CIN
 cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUtensorMap &rmap, TcParams p,
                      cudaStream_t st) {
     int smem;
-    p.stages = rows_stages(p.res != nullptr, &smem, NPR, PS, CIN);
+    p.stages = rows_stages(p.res != nullptr, &smem, NPR, PS, CIN, false, IN_DT == DT_E4M3);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
     auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS, CIN>;
     cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS, CIN>>(smem);
@@ -1674,8 +1729,7 @@ bool rows_kernel_fits(const ConvArgs &a) {
 bool rows_head_fits(const ConvArgs &a) {
     const int dt = a.in_dt;
     return a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.out_dt == dt && a.cin_pad == 16 &&
-           a.in_cpc == 8 && a.cout_pad == 64 && a.cout == 64 && a.out_cpc == 64 && a.ps == 0 && !a.res && !a.y2 &&
-           !a.amax;
+           a.in_cpc == 8 && a.cout_pad == 64 && a.cout == 64 && a.out_cpc == 64 && a.ps == 0 && !a.res;
 }
 
 // 3x3 layer from 128 16-bit channels (64-channel chunks) to <= 256 float32
@@ -1685,6 +1739,15 @@ bool rows128_fits(const ConvArgs &a) {
     return a.w_rows && a.k == 3 && (dt == DT_BF16 || dt == DT_F16) && a.cin_pad == 128 && a.in_cpc == 64 &&
            a.out_dt == DT_F32 && a.out_cpc == 4 && a.cout_pad % 4 == 0 && a.cout_pad <= 256 && a.cout <= a.cout_pad &&
            a.ps == 0 && !a.res && !a.y2 && !a.amax && a.nimg == 1 && a.acc_scale == 1.f && a.out_scale == 1.f;
+}
+
+// FP8 64 -> 64 3x3 trunk layer: E4M3 input in 16-channel chunks; BF16 output (with
+// an optional FP8 copy and residual), or an FP8-only output in 16-channel chunks.
+bool rows_f8_fits(const ConvArgs &a) {
+    const bool bf16_out = a.out_dt == DT_BF16 && a.out_cpc == 64;
+    const bool f8_out = a.out_dt == DT_E4M3 && a.out_cpc == 16 && !a.res && !a.y2;
+    return a.w_rows && a.k == 3 && a.in_dt == DT_E4M3 && a.cin_pad == 64 && a.in_cpc == 16 && a.cout == 64 &&
+           a.cout_pad == 64 && a.ps == 0 && a.nimg == 1 && !a.amax && (bf16_out || f8_out);
 }
 
 // 64 -> 256 channels, PixelShuffle(2) into a blocked 64-channel 16-bit tensor.
@@ -1788,6 +1851,34 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
         p.wbytes = (uint32_t)tc_rows128_weight_bytes(1);
         return dt == DT_BF16 ? run_rows_sliced<DT_BF16, DT_F32, 16, false, 128>(map, p, st)
                              : run_rows_sliced<DT_F16, DT_F32, 16, false, 128>(map, p, st);
+    }
+    if (rows_f8_fits(a)) {
+        auto enc = encode_fn();
+        if (!enc) return cudaErrorNotSupported;
+        CUtensorMap map, ymap, rmap;
+        cuuint64_t dims[4] = {16, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)(4 * a.nimg)};
+        cuuint64_t strides[3] = {16, (cuuint64_t)a.W * 16, (cuuint64_t)a.W * a.H * 16};
+        cuuint32_t box[4] = {16, (cuuint32_t)(TM + 2), 1, 4};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void *>(a.x), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        TcParams p = rows_params(a);
+        ConvArgs b = a;
+        if (a.out_dt == DT_E4M3) {
+            // FP8-only output: the FP8 copy path writes it; the 16-bit tile maps are unused
+            p.no_main = 1;
+            p.y2 = static_cast<uint8_t *>(a.y);
+            p.y2_scale = a.out_scale;
+            p.out_scale = 1.f;
+            p.res_scale = 1.f;
+            b.y = const_cast<void *>(b.res ? b.res : a.x);
+        }
+        b.x = b.y;  // the 16-bit row map is not used by this form
+        cudaError_t e = encode_row_maps(b, &ymap, &ymap, &rmap);
+        if (e != cudaSuccess) return e;
+        return run_rows<DT_E4M3, DT_BF16, 128, 64, false, 64>(map, ymap, rmap, p, st);
     }
     if (rows_psb_fits(a)) {
         ConvArgs b = a;

@@ -115,6 +115,7 @@ struct Weights {
     void *rows = nullptr;        // row-streaming 64->64 3x3 layout (tensor-core path)
     void *simt_or_tc = nullptr;  // 16-bit / FP32 layout
     void *f8 = nullptr;          // FP8 layout
+    void *rows_f8 = nullptr;     // FP8 row-streaming layout (64 -> 64 3x3)
     float *bias = nullptr;
     int cin_pad = 0, cout_pad = 0;
     float w_amax = 0.f;
@@ -444,6 +445,10 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
         std::vector<uint8_t> host(tc_weight_bytes(L.cin, W.cout_pad, L.k, DT_E4M3));
         prepare_weights_tc(w, L.cout, L.cin, L.k, L.cin, W.cout_pad, DT_E4M3, 1.0f / sw, host.data(), false);
         s = upload(f, host.data(), host.size(), &W.f8);
+        if (s != NVISR_OK) return s;
+        std::vector<uint8_t> rows(tc_rows_f8_weight_bytes());
+        prepare_weights_rows_f8(w, 1.0f / sw, rows.data());
+        s = upload(f, rows.data(), rows.size(), &W.rows_f8);
         if (s != NVISR_OK) return s;
     }
     return NVISR_OK;
@@ -936,6 +941,7 @@ ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, b
         a.cin_pad = in.cpad;  // 64
         a.in_cpc = 16;        // FP8 copies use 16-channel (16-byte) chunks
         a.w = Wt.f8;
+        a.w_rows = Wt.rows_f8;
         a.acc_scale = f->act_scale[in.amax_slot] * (Wt.w_amax / 448.f);
     } else {
         a.x = in.ptr;
