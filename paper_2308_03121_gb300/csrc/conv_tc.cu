@@ -1918,7 +1918,8 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
     if (in_cpc * esz != cbi || a.cin_pad % in_cpc) return cudaErrorInvalidValue;
     const int cin_chunks = a.cin_pad / in_cpc;
     const int ns = pick_ns(a.cin_pad * esz, a.cout_pad, a.k);
-    const int nch = cbi == 128 ? 1 : (cin_chunks >= 8 ? 8 : cin_chunks);
+    // 16-byte chunks per stage: the largest built group (4 or 2) that divides the chunk count
+    const int nch = cbi == 128 ? 1 : (cin_chunks % 4 == 0 ? 4 : 2);
     if (cin_chunks % nch || (cbi == 16 && nch % 2)) return cudaErrorInvalidValue;
     const int epi = a.ps > 0 ? (a.ps_out ? 1 : 2) : 0;
     const int odt = epi == 1 ? dt : a.out_dt;

@@ -206,8 +206,11 @@ struct nvisr_filter {
     void *dcn_x8 = nullptr;        // DCN input in 8-channel planes (tensor-core path)
     std::vector<Step> steps;
     int pack_t = -1;               // tensor id of the packed tuple
-    float *out_rgb[2] = {nullptr, nullptr};  // planar float32 residuals [3][sH][opitch]
-    SkipArgs skip[2] = {};                   // skip path of each output slot (added by requantise)
+    float *out_rgb[8] = {};   // planar float32 residuals [3][sH][opitch], one per output of a run
+    SkipArgs skip[8] = {};    // skip path of each output slot (added by requantise)
+    // group family (Section 3.1): n frames per run (+1 with Extra frame), run_out outputs per run
+    int grp_n = 1, grp_need = 1, run_out = 1;
+    bool grp_interp = false;
     int64_t opitch = 0;
     void *ostage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // alternate per pull
     int64_t ostage_pitch[3] = {0, 0, 0};
@@ -341,17 +344,81 @@ bool tuple_ready(const nvisr_filter *f, int64_t t, std::vector<int64_t> *idx) {
 
 // Group family (n = 1, Extra frame, Interpolation, Double frame): run i uses
 // frames (i, min(i+1, s1)) and emits outputs 2i, 2i+1.
-bool group_ready(const nvisr_filter *f, int64_t run, std::vector<int64_t> *idx) {
-    if (run >= f->pushed) return false;
-    int64_t s0, s1;
-    bool closed;
-    scene_bounds(f, run, &s0, &s1, &closed);
-    if (!closed && s1 < run + 1) return false;
-    if (idx) *idx = {run, std::min(run + 1, s1)};
-    return true;
+// Group family: where output o comes from.  Scenes are cut by the per-frame
+// flags; a scene [s0, s1] is covered by runs at nominal starts s0, s0 + n, ...,
+// each taking need = n (+1 with Extra frame) frames, indices past s1 taking s1.
+// Without Interpolation a run that would pass s1 is moved back to end at s1 when
+// the scene holds need frames, and its first (nominal - start) outputs, already
+// emitted by the previous run, are dropped (Section 3.3).  A run is known once
+// its frames are pushed inside its scene, or once the scene is closed (a later
+// cut is known or the stream ended).
+struct RunLoc {
+    int64_t key = -1;             // nominal start frame (unique per run)
+    int64_t oldest = 0;           // earliest frame the run may read (its start once known)
+    std::vector<int64_t> inputs;  // the run's input frames (known runs)
+    int k = 0;                    // o's index among the run's outputs
+};
+
+// True when output o's run is known (and then *loc describes it); false with
+// loc->oldest set to a lower bound of the frames that run will read.
+bool group_locate(const nvisr_filter *f, int64_t o, RunLoc *loc) {
+    const int n = f->grp_n, need = f->grp_need, R = f->run_out;
+    int64_t base = 0, s0 = 0;
+    loc->oldest = 0;
+    while (s0 < f->pushed) {
+        int64_t s1 = s0;
+        while (s1 + 1 < f->pushed && !f->cut[(size_t)(s1 + 1)]) ++s1;
+        const bool closed = s1 + 1 < f->pushed || f->eos;
+        const int64_t len = s1 - s0 + 1;
+        for (int64_t nominal = s0; nominal <= s1; nominal += n) {
+            int64_t start = nominal;
+            const bool past = start + need - 1 > s1;
+            if (past && !closed) {
+                // the run's frames are not all pushed and its form is not final yet
+                loc->oldest = f->grp_interp ? nominal : std::max<int64_t>(s0, nominal - need + 1);
+                return false;
+            }
+            if (past && !f->grp_interp && len >= need) start = s1 - need + 1;
+            const int skip = (int)(nominal - start);
+            const int cnt = R - skip;
+            if (o < base + cnt) {
+                loc->key = nominal;
+                loc->oldest = start;
+                loc->inputs.clear();
+                for (int k = 0; k < need; ++k) loc->inputs.push_back(std::min(start + k, s1));
+                loc->k = skip + (int)(o - base);
+                return true;
+            }
+            base += cnt;
+        }
+        s0 = s1 + 1;
+    }
+    loc->oldest = f->pushed;
+    return false;
 }
 
-int outputs_per_input(const nvisr_filter *f) { return f->net.family == "group" ? 2 : 1; }
+// Output count of a group-family stream once it has ended.
+int64_t group_total(const nvisr_filter *f) {
+    const int n = f->grp_n, need = f->grp_need, R = f->run_out;
+    int64_t total = 0, s0 = 0;
+    while (s0 < f->pushed) {
+        int64_t s1 = s0;
+        while (s1 + 1 < f->pushed && !f->cut[(size_t)(s1 + 1)]) ++s1;
+        const int64_t len = s1 - s0 + 1;
+        for (int64_t nominal = s0; nominal <= s1; nominal += n) {
+            int64_t start = nominal;
+            if (start + need - 1 > s1 && !f->grp_interp && len >= need) start = s1 - need + 1;
+            total += R - (nominal - start);
+        }
+        s0 = s1 + 1;
+    }
+    return total;
+}
+
+bool group_ready(const nvisr_filter *f, int64_t o, RunLoc *loc) {
+    RunLoc tmp;
+    return group_locate(f, o, loc ? loc : &tmp);
+}
 
 // FP8 filters calibrate their activation scales on the first calib_frames
 // outputs' tuples, so nothing is ready before those tuples are all known.
@@ -364,7 +431,7 @@ bool calibration_ready(const nvisr_filter *f) {
 }
 
 bool output_ready(const nvisr_filter *f, int64_t o) {
-    if (f->net.family == "group") return group_ready(f, o / 2, nullptr);
+    if (f->net.family == "group") return group_ready(f, o, nullptr);
     return tuple_ready(f, o, nullptr) && calibration_ready(f);
 }
 
@@ -691,13 +758,15 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
     f->steps.clear();
     f->wvar.clear();
     f->pack_t = -1;
-    if (net.outputs.size() > 2) return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: at most 2 outputs per run");
     if (f->precision == NVISR_PREC_FP8) return fail(NVISR_UNSUPPORTED_FORMAT, "group networks run in FP32/BF16/FP16");
-    if (!(net.extra && net.frames == 2))
-        return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: n = 1 with the Extra frame flag (2 input frames)");
-    const int outs_expected = net.dbl ? 2 : 1;
-    if ((int)net.outputs.size() != outs_expected || !net.interp)
-        return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: Interpolation + Double frame (2 outputs per run)");
+    f->grp_n = net.frames - (net.extra ? 1 : 0);
+    f->grp_need = net.frames;
+    f->grp_interp = net.interp;
+    f->run_out = net.dbl ? 2 * f->grp_n : f->grp_n;
+    if (f->grp_n < 1 || net.frames > 8 || f->run_out > 8)
+        return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: at most 8 input frames and 8 outputs per run");
+    if ((int)net.outputs.size() != f->run_out)
+        return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: the description lists n outputs (2n with Double frame)");
     std::map<std::string, int> tensor_of, out_index;
     for (size_t i = 0; i < net.outputs.size(); ++i) out_index[net.outputs[i].name] = (int)i;
     std::map<std::string, int> om_names;
@@ -1110,11 +1179,11 @@ nvisr_status calibrate(nvisr_filter *f) {
 nvisr_status compute_output(nvisr_filter *f, int64_t o) {
     std::vector<int64_t> idx;
     if (f->net.family == "group") {
-        const int64_t run = o / 2;
-        if (f->cached_run == run) return NVISR_OK;
-        if (!group_ready(f, run, &idx)) return NVISR_AGAIN;
-        nvisr_status s = forward_group(f, idx);
-        if (s == NVISR_OK) f->cached_run = run;
+        RunLoc loc;
+        if (!group_locate(f, o, &loc)) return NVISR_AGAIN;
+        if (f->cached_run == loc.key) return NVISR_OK;  // an earlier output of the same run computed it
+        nvisr_status s = forward_group(f, loc.inputs);
+        if (s == NVISR_OK) f->cached_run = loc.key;
         return s;
     }
     if (!tuple_ready(f, o, &idx)) return NVISR_AGAIN;
@@ -1125,7 +1194,11 @@ nvisr_status compute_output(nvisr_filter *f, int64_t o) {
     return forward_tuple(f, idx, false);
 }
 
-int output_slot(const nvisr_filter *f, int64_t o) { return f->net.family == "group" ? (int)(o % 2) : 0; }
+int output_slot(const nvisr_filter *f, int64_t o) {
+    if (f->net.family != "group") return 0;
+    RunLoc loc;
+    return group_locate(f, o, &loc) ? loc.k : 0;
+}
 
 // Requantises output slot `slot` into the caller's device planes, or into the
 // current staging buffer followed by its D2H copy (and the error word's) on the
@@ -1481,7 +1554,11 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
         return st;
     };
     // ring of ingested frames
-    f->ring = net.frames + 2;
+    // ring: a tuple, or a group run plus the frames a recycled last run may reach back to
+    f->ring = net.family == "group" ? 2 * net.frames + 2 : net.frames + 2;
+    f->run_out = net.family == "group" ? (net.dbl ? 2 : 1) * (net.frames - (net.extra ? 1 : 0)) : 1;
+    if (f->run_out < 1 || f->run_out > 8)
+        return cleanup(fail(NVISR_UNSUPPORTED_FORMAT, "group networks: 1 to 8 outputs per run"));
     f->rpitch = round_up64(W, 4);
     f->slot_floats = 3 * f->rpitch * H;
     void *p;
@@ -1499,7 +1576,7 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
         if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess)
             return cleanup(fail(NVISR_CUDA_ERROR, "cudaEventCreate failed"));
     f->opitch = round_up64((int64_t)W * net.scale, 4);
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < f->run_out; ++k) {
         if ((s = dalloc(e, sizeof(float) * 3 * f->opitch * H * net.scale, f->owned, &p)) != NVISR_OK)
             return cleanup(s);
         f->out_rgb[k] = (float *)p;
@@ -1519,8 +1596,14 @@ nvisr_status nvisr_push(nvisr_filter *f, const nvisr_planes *in, uint32_t flags)
         if (!in->data[p] || in->pitch[p] < plane_row_bytes(f->in_fmt, p))
             return fail(NVISR_INVALID_ARG, "push: plane " + std::to_string(p) + " NULL or pitch too small");
     // the slot overwritten by this frame must not be needed by a pending output
-    const int r = f->net.family == "tuple" ? (f->net.frames - 1) / 2 : 0;
-    const int64_t oldest_needed = f->net.family == "tuple" ? f->next_out - r : f->next_out / 2;
+    int64_t oldest_needed;
+    if (f->net.family == "tuple") {
+        oldest_needed = f->next_out - (f->net.frames - 1) / 2;
+    } else {
+        RunLoc loc;
+        group_locate(f, f->next_out, &loc);
+        oldest_needed = loc.oldest;
+    }
     if (f->pushed - f->ring >= std::max<int64_t>(oldest_needed, 0) && f->pushed >= f->ring)
         return NVISR_FULL;
     cudaSetDevice(f->eng->device);
@@ -1564,14 +1647,14 @@ nvisr_status nvisr_push(nvisr_filter *f, const nvisr_planes *in, uint32_t flags)
 nvisr_status nvisr_flush(nvisr_filter *f) {
     if (!f) return fail(NVISR_INVALID_ARG, "flush: NULL filter");
     f->eos = true;
-    f->total_out = f->pushed * outputs_per_input(f);
+    f->total_out = f->net.family == "group" ? group_total(f) : f->pushed;
     return NVISR_OK;
 }
 
 int64_t nvisr_filter_ready(nvisr_filter *f) {
     if (!f) return 0;
     int64_t n = 0;
-    const int64_t end = f->pushed * outputs_per_input(f);
+    const int64_t end = f->eos ? f->total_out : f->pushed * std::max(1, f->run_out);
     for (int64_t o = f->next_out; o < end && output_ready(f, o); ++o) ++n;
     return n;
 }
@@ -1605,7 +1688,11 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
     }
     if (info) {
         std::vector<int64_t> idx;
-        if (f->net.family == "group") group_ready(f, o / 2, &idx);
+        if (f->net.family == "group") {
+            RunLoc loc;
+            group_locate(f, o, &loc);
+            idx = loc.inputs;
+        }
         else tuple_ready(f, o, &idx);
         int scene = 0;
         for (int64_t k = 1; k <= idx.front(); ++k) scene += f->cut[(size_t)k];

@@ -257,3 +257,36 @@ def test_config3_stvsr_dcn_filter(prec, config3_oracle):
             worst = max(worst, mx)
     print(prec, "config-3 max LSB vs oracle:", worst)
     assert worst <= 1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("n,extra,interp,double", [(2, True, True, True), (3, False, False, False),
+                                                   (2, False, False, True)])
+def test_group_model_general_n(n, extra, interp, double, prec):
+    """Group family with n > 1 and each flag set (Section 3.1 / 3.3): runs of n (+1) frames,
+    2n outputs with Double frame, a non-interpolating scene's last run moved back inside
+    the scene with its recycled outputs dropped; a cut before frame 5."""
+    W, H, N = 48, 32, 9
+    frames = synth.frames_textured(synth.BASE_SEED + 61, N, W, H, 8, "420", "limited")
+    flags = np.zeros(N, bool)
+    flags[5] = True
+    text, blob = synth.net_group_general(synth.BASE_SEED + 60, n, extra, interp, double)
+    fdo = fmt_dict(2 * W, 2 * H, 8)
+    ref = [prequant(o, fdo) for o in
+           oracle.run_filter(frames, flags, text, blob, fmt_dict(W, H, 8), fdo, keep_float=True)]
+    # expected source range of every output, from the oracle's run enumeration
+    need, per_run = n + (1 if extra else 0), (2 * n if double else n)
+    src = []
+    for s0, s1 in oracle.scenes_from_flags(flags, N):
+        for inputs, skip in oracle.group_runs(s0, s1, n, extra, interp):
+            src += [(inputs[0], inputs[-1])] * (per_run - skip)
+    outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(2 * W, 2 * H, 8), prec, scale=2)
+    assert len(outs) == len(ref) == len(src)
+    assert [i[0] for i in infos] == list(range(len(ref)))
+    assert [i[1:] for i in infos] == src
+    for got, pq in zip(outs, ref):
+        if prec == "fp32":
+            assert_codes_match(got, pq, 8)
+        else:
+            mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 8) for k in "YUV"})
+            assert mx <= 1, mx
