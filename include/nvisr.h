@@ -53,7 +53,9 @@ typedef enum nvisr_status {
 
 typedef enum nvisr_subsampling { NVISR_SUB_420 = 0, NVISR_SUB_444 = 1 } nvisr_subsampling;
 typedef enum nvisr_range { NVISR_RANGE_LIMITED = 0, NVISR_RANGE_FULL = 1 } nvisr_range;
-typedef enum nvisr_matrix { NVISR_MATRIX_BT709 = 0 } nvisr_matrix;
+/* Colour matrix: BT.709, or BT.2020 non-constant luminance (same equations,
+ * weights Kr 0.2627 / Kb 0.0593).  No transfer-function change is applied. */
+typedef enum nvisr_matrix { NVISR_MATRIX_BT709 = 0, NVISR_MATRIX_BT2020 = 1 } nvisr_matrix;
 /* Chroma siting of 4:2:0 planes: LEFT = ITU-T H.273 type 0 (co-sited
  * horizontally, between rows vertically), CENTER = type 1, POINT = replicate
  * on upsampling and 2x2 mean on downsampling. */
@@ -71,7 +73,7 @@ typedef enum nvisr_precision {
  * Samples of bit_depth <= 8 are uint8, 9..16 are uint16 (low bits). */
 typedef struct nvisr_format {
     int32_t width, height;       /* luma size in pixels */
-    int32_t bit_depth;           /* 8 or 10 */
+    int32_t bit_depth;           /* 8, 10, 12 or 16 (more than 8: 16-bit samples) */
     int32_t subsampling;         /* nvisr_subsampling */
     int32_t range;               /* nvisr_range */
     int32_t matrix;              /* nvisr_matrix */

@@ -12,7 +12,9 @@ in the design notes:
 * range (limited): Y' = (Y - 16*2^(b-8)) / (219*2^(b-8)),
                    C' = (C - 128*2^(b-8)) / (224*2^(b-8));
   range (full):    Y' = Y / (2^b - 1),  C' = (C - 2^(b-1)) / (2^b - 1).
-* BT.709: Kr = 0.2126, Kb = 0.0722, Kg = 1 - Kr - Kb.
+* BT.709: Kr = 0.2126, Kb = 0.0722, Kg = 1 - Kr - Kb; BT.2020 (non-constant
+  luminance): Kr = 0.2627, Kb = 0.0593 (the same equations with its weights).
+  Bit depths 8 to 16 use the same range equations.
 * chroma siting: LEFT (H.273 type 0: co-sited horizontally, centred between
   rows vertically), CENTER (centred both ways), POINT (replicate; a test mode).
   Edges clamp to the nearest sample.
@@ -25,6 +27,9 @@ import numpy as np
 KR = 0.2126
 KB = 0.0722
 KG = 1.0 - KR - KB
+
+# (Kr, Kb) of each supported matrix; Kg = 1 - Kr - Kb
+MATRICES = {"bt709": (0.2126, 0.0722), "bt2020": (0.2627, 0.0593)}
 
 
 # ---------------------------------------------------------------- range (C1)
@@ -69,19 +74,23 @@ def quantise(v, bit_depth: int):
 
 # ---------------------------------------------------------------- matrix (C2)
 
-def ycbcr_to_rgb(yp, cb, cr):
-    """BT.709 Y'CbCr (normalised) -> R'G'B'.  No clamping."""
-    r = yp + 2.0 * (1.0 - KR) * cr
-    b = yp + 2.0 * (1.0 - KB) * cb
-    g = (yp - KR * r - KB * b) / KG
+def ycbcr_to_rgb(yp, cb, cr, matrix: str = "bt709"):
+    """Y'CbCr (normalised) -> R'G'B' with the matrix's weights.  No clamping."""
+    kr, kb = MATRICES[matrix]
+    kg = 1.0 - kr - kb
+    r = yp + 2.0 * (1.0 - kr) * cr
+    b = yp + 2.0 * (1.0 - kb) * cb
+    g = (yp - kr * r - kb * b) / kg
     return r, g, b
 
 
-def rgb_to_ycbcr(r, g, b):
-    """BT.709 R'G'B' -> Y'CbCr (normalised)."""
-    yp = KR * r + KG * g + KB * b
-    cb = (b - yp) / (2.0 * (1.0 - KB))
-    cr = (r - yp) / (2.0 * (1.0 - KR))
+def rgb_to_ycbcr(r, g, b, matrix: str = "bt709"):
+    """R'G'B' -> Y'CbCr (normalised) with the matrix's weights."""
+    kr, kb = MATRICES[matrix]
+    kg = 1.0 - kr - kb
+    yp = kr * r + kg * g + kb * b
+    cb = (b - yp) / (2.0 * (1.0 - kb))
+    cr = (r - yp) / (2.0 * (1.0 - kr))
     return yp, cb, cr
 
 
@@ -164,13 +173,13 @@ def ingest(planes, fmt):
     """Integer Y/U/V planes -> float64 R'G'B' [3][H][W] (network domain RGB, unclamped).
 
     fmt: dict with bit_depth, subsampling ('420'|'444'), range ('limited'|'full'),
-    chroma_loc ('left'|'center'|'point').
+    chroma_loc ('left'|'center'|'point') and optionally matrix ('bt709' default, 'bt2020').
     """
     b, rg = fmt["bit_depth"], fmt["range"]
     yp = normalise_luma(planes["Y"], b, rg)
     cb = upsample_chroma(normalise_chroma(planes["U"], b, rg), fmt["subsampling"], fmt["chroma_loc"])
     cr = upsample_chroma(normalise_chroma(planes["V"], b, rg), fmt["subsampling"], fmt["chroma_loc"])
-    r, g, bb = ycbcr_to_rgb(yp, cb, cr)
+    r, g, bb = ycbcr_to_rgb(yp, cb, cr, fmt.get("matrix", "bt709"))
     return np.stack([r, g, bb])
 
 
@@ -181,7 +190,7 @@ def requantise(rgb, fmt):
     rounded half to even and clamped to [0, 2^b - 1].
     """
     b, rg = fmt["bit_depth"], fmt["range"]
-    yp, cb, cr = rgb_to_ycbcr(rgb[0], rgb[1], rgb[2])
+    yp, cb, cr = rgb_to_ycbcr(rgb[0], rgb[1], rgb[2], fmt.get("matrix", "bt709"))
     cb = downsample_chroma(cb, fmt["subsampling"], fmt["chroma_loc"])
     cr = downsample_chroma(cr, fmt["subsampling"], fmt["chroma_loc"])
     return {"Y": quantise(scale_luma(yp, b, rg), b),

@@ -163,8 +163,11 @@ def _check(status, what):
     return status
 
 
-def fmt(width, height, bit_depth, subsampling="420", range_="limited", chroma_loc="left"):
-    return Format(width, height, bit_depth, SUB[subsampling], RANGE[range_], 0, LOC[chroma_loc], 0)
+MATRIX = {"bt709": 0, "bt2020": 1}
+
+
+def fmt(width, height, bit_depth, subsampling="420", range_="limited", chroma_loc="left", matrix="bt709"):
+    return Format(width, height, bit_depth, SUB[subsampling], RANGE[range_], MATRIX[matrix], LOC[chroma_loc], 0)
 
 
 def _ptr(t):

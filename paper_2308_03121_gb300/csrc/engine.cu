@@ -143,9 +143,11 @@ struct Step {
 };
 
 bool fmt_ok(const nvisr_format &f) {
-    return f.width > 0 && f.height > 0 && (f.bit_depth == 8 || f.bit_depth == 10) &&
+    return f.width > 0 && f.height > 0 &&
+           (f.bit_depth == 8 || f.bit_depth == 10 || f.bit_depth == 12 || f.bit_depth == 16) &&
            (f.subsampling == NVISR_SUB_420 || f.subsampling == NVISR_SUB_444) &&
-           (f.range == NVISR_RANGE_LIMITED || f.range == NVISR_RANGE_FULL) && f.matrix == NVISR_MATRIX_BT709 &&
+           (f.range == NVISR_RANGE_LIMITED || f.range == NVISR_RANGE_FULL) &&
+           (f.matrix == NVISR_MATRIX_BT709 || f.matrix == NVISR_MATRIX_BT2020) &&
            f.chroma_loc >= 0 && f.chroma_loc <= 2 &&
            (f.subsampling == NVISR_SUB_444 || (f.width % 2 == 0 && f.height % 2 == 0));
 }

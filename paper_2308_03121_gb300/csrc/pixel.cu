@@ -23,19 +23,27 @@ namespace nvisr {
 
 namespace {
 
-constexpr float KR = 0.2126f;
-constexpr float KB = 0.0722f;
-constexpr float KG = 1.0f - 0.2126f - 0.0722f;
 
 struct RangeConst {
     float y_off, y_den, c_off, c_den;  // normalise: (v - off) / den
     float y_mul, y_add, c_mul, c_add;  // scale back: v * mul + add
     float vmax;
     float y_rden, c_rden;              // 1 / den (the streaming kernels multiply)
+    // colour matrix (BT.709 or BT.2020 non-constant luminance): luma weights and
+    // the derived factors 2(1 - Kr), 2(1 - Kb), 1 / Kg, 1 / (2(1 - Kb)), 1 / (2(1 - Kr))
+    float kr, kb, kg, cr_r, cb_b, rkg, cb_s, cr_s;
 };
 
-RangeConst range_const(int bits, int range) {
+RangeConst range_const(int bits, int range, int matrix) {
     RangeConst r;
+    r.kr = matrix == NVISR_MATRIX_BT2020 ? 0.2627f : 0.2126f;
+    r.kb = matrix == NVISR_MATRIX_BT2020 ? 0.0593f : 0.0722f;
+    r.kg = 1.0f - r.kr - r.kb;
+    r.cr_r = 2.0f * (1.0f - r.kr);
+    r.cb_b = 2.0f * (1.0f - r.kb);
+    r.rkg = 1.0f / r.kg;
+    r.cb_s = 1.0f / (2.0f * (1.0f - r.kb));
+    r.cr_s = 1.0f / (2.0f * (1.0f - r.kr));
     if (range == NVISR_RANGE_LIMITED) {
         float m = (float)(1 << (bits - 8));
         r.y_off = 16.f * m; r.y_den = 219.f * m; r.c_off = 128.f * m; r.c_den = 224.f * m;
@@ -119,9 +127,9 @@ __global__ void __launch_bounds__(256) ingest_kernel(
             cb = chroma_at<S>(up, pu, Hc, Wc, y, x, rc.c_off, rc.c_den);
             cr = chroma_at<S>(vp, pv, Hc, Wc, y, x, rc.c_off, rc.c_den);
         }
-        r[e] = Y + (2.0f * (1.0f - KR)) * cr;
-        b[e] = Y + (2.0f * (1.0f - KB)) * cb;
-        g[e] = (Y - KR * r[e] - KB * b[e]) / KG;
+        r[e] = Y + rc.cr_r * cr;
+        b[e] = Y + rc.cb_b * cb;
+        g[e] = (Y - rc.kr * r[e] - rc.kb * b[e]) / rc.kg;
     }
     const int64_t plane = pitch * H;
     float *o = out + (int64_t)y * pitch + x0;
@@ -251,9 +259,9 @@ __global__ void __launch_bounds__(128) ingest420_kernel(
                 cr = vvv[li];
             }
             const float Y = (ys[e] - rc.y_off) * rc.y_rden;
-            r[e] = Y + (2.0f * (1.0f - KR)) * cr;
-            b[e] = Y + (2.0f * (1.0f - KB)) * cb;
-            g[e] = (Y - KR * r[e] - KB * b[e]) * (1.0f / KG);
+            r[e] = Y + rc.cr_r * cr;
+            b[e] = Y + rc.cb_b * cb;
+            g[e] = (Y - rc.kr * r[e] - rc.kb * b[e]) * rc.rkg;
         }
         float *o = out + (int64_t)y * pitch + x0;
         if (vec) {
@@ -323,10 +331,11 @@ __device__ __forceinline__ float out_at(const float *in, int64_t pitch, int64_t 
     return k.n ? v + skip_at(k, c, Y, X) : v;
 }
 
-__device__ __forceinline__ void rgb2ycc(float r, float g, float b, float &y, float &cb, float &cr) {
-    y = KR * r + KG * g + KB * b;
-    cb = (b - y) * (1.0f / (2.0f * (1.0f - KB)));
-    cr = (r - y) * (1.0f / (2.0f * (1.0f - KR)));
+__device__ __forceinline__ void rgb2ycc(const RangeConst &rc, float r, float g, float b, float &y, float &cb,
+                                        float &cr) {
+    y = rc.kr * r + rc.kg * g + rc.kb * b;
+    cb = (b - y) * rc.cb_s;
+    cr = (r - y) * rc.cr_s;
 }
 
 // 4:4:4: one thread per 4 pixels of a row.
@@ -341,7 +350,7 @@ __global__ void __launch_bounds__(256) requant444_kernel(const float *__restrict
     const int64_t plane = pitch * H;
     for (int e = 0; e < 4 && x0 + e < W; ++e) {
         float Y, cb, cr;
-        rgb2ycc(out_at(in, pitch, plane, sk, 0, y, x0 + e), out_at(in, pitch, plane, sk, 1, y, x0 + e),
+        rgb2ycc(rc, out_at(in, pitch, plane, sk, 0, y, x0 + e), out_at(in, pitch, plane, sk, 1, y, x0 + e),
                 out_at(in, pitch, plane, sk, 2, y, x0 + e), Y, cb, cr);
         st_sample<S>(yp, py, y, x0 + e, quant(Y * rc.y_mul + rc.y_add, rc.vmax));
         st_sample<S>(up, pu, y, x0 + e, quant(cb * rc.c_mul + rc.c_add, rc.vmax));
@@ -479,7 +488,7 @@ __global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr) {
             float Y, cb, cr;
-            rgb2ycc(sample(0, rr, c, x), sample(1, rr, c, x), sample(2, rr, c, x), Y, cb, cr);
+            rgb2ycc(rc, sample(0, rr, c, x), sample(1, rr, c, x), sample(2, rr, c, x), Y, cb, cr);
             cb2[rr] = cb;
             cr2[rr] = cr;
             if (c >= 1) yq[rr][c - 1] = quant(Y * rc.y_mul + rc.y_add, rc.vmax);
@@ -719,7 +728,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
 
 cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, const void *u, int64_t pu,
                           const void *v, int64_t pv, float *out, int64_t out_pitch, cudaStream_t st) {
-    const RangeConst rc = range_const(f.bit_depth, f.range);
+    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix);
     if (f.subsampling == NVISR_SUB_420) {
         dim3 blk(128);
         dim3 grd((f.width + 8 * 128 - 1) / (8 * 128), (f.height + 1) / 2, 2);
@@ -749,7 +758,7 @@ cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, cons
 
 cudaError_t launch_requant(const nvisr_format &f, const float *in, int64_t in_pitch, void *y, int64_t py,
                            void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st, const SkipArgs *skip) {
-    const RangeConst rc = range_const(f.bit_depth, f.range);
+    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix);
     SkipArgs sk{};
     if (skip) sk = *skip;
     dim3 block(64);

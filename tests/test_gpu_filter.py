@@ -290,3 +290,24 @@ def test_group_model_general_n(n, extra, interp, double, prec):
         else:
             mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 8) for k in "YUV"})
             assert mx <= 1, mx
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_filter_bt2020_12bit(prec):
+    """The whole filter on 12-bit BT.2020 4:2:0 in and out (config-1 network, a cut on frame 5)."""
+    frames = synth.frames_textured(synth.BASE_SEED + 71, 8, 64, 48, 12, "420", "limited")
+    flags = np.zeros(8, bool)
+    flags[5] = True
+    fdi = fmt_dict(64, 48, 12, "420", "limited", "left", "bt2020")
+    fdo = fmt_dict(128, 96, 12, "420", "limited", "left", "bt2020")
+    text, blob = synth.net_config1()
+    ref = [prequant(o, fdo) for o in oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)]
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(64, 48, 12, "420", "limited", "left", "bt2020"),
+                      nv.fmt(128, 96, 12, "420", "limited", "left", "bt2020"), prec)
+    assert len(outs) == len(ref) == 8
+    for got, pq in zip(outs, ref):
+        if prec == "fp32":
+            assert_codes_match(got, pq, 12)
+        else:
+            mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 12) for k in "YUV"})
+            assert mx <= 4, mx  # 12-bit codes: the 10-bit +-1 LSB bound, scaled by 4

@@ -77,6 +77,47 @@ def test_requant_matches_oracle(W, H, bits, sub, rng, loc):
     assert_codes_match(got, prequant(rgb.astype(np.float64), fd), bits)
 
 
+FORMAT_CASES = [  # BT.2020 and 12 / 16-bit samples (W, H, bits, subsampling, range, siting, matrix)
+    (96, 40, 12, "420", "limited", "left", "bt2020"),
+    (70, 34, 16, "444", "full", "center", "bt2020"),
+    (64, 32, 12, "420", "full", "left", "bt709"),
+    (130, 66, 16, "420", "limited", "center", "bt709"),
+]
+
+
+@pytest.mark.parametrize("W,H,bits,sub,rng,loc,matrix", FORMAT_CASES)
+def test_ingest_matrix_and_depth_match_oracle(W, H, bits, sub, rng, loc, matrix):
+    fr = synth.frames_textured(12, 1, W, H, bits, sub, rng)[0]
+    fd = fmt_dict(W, H, bits, sub, rng, loc, matrix)
+    f = nv.fmt(W, H, bits, sub, rng, loc, matrix)
+    pitch = (W + 3) // 4 * 4
+    out = torch.full((3, H, pitch), float("nan"), device="cuda")
+    nv.nvisr_ingest(f, to_dev(fr["Y"]), to_dev(fr["U"]), to_dev(fr["V"]), out)
+    torch.cuda.synchronize()
+    err = np.abs(out[:, :, :W].double().cpu().numpy() - oracle.ingest(fr, fd)).max()
+    assert err < 4e-6, err
+
+
+@pytest.mark.parametrize("W,H,bits,sub,rng,loc,matrix", FORMAT_CASES)
+def test_requant_matrix_and_depth_match_oracle(W, H, bits, sub, rng, loc, matrix):
+    rs = np.random.default_rng(W * H + bits + 1)
+    rgb = rs.uniform(-0.08, 1.08, size=(3, H, W)).astype(np.float32)
+    fd = fmt_dict(W, H, bits, sub, rng, loc, matrix)
+    f = nv.fmt(W, H, bits, sub, rng, loc, matrix)
+    pitch = (W + 3) // 4 * 4
+    dev = torch.zeros((3, H, pitch), device="cuda")
+    dev[:, :, :W] = torch.from_numpy(rgb).cuda()
+    dt = torch.uint8 if bits <= 8 else torch.int16
+    cw, ch = (W // 2, H // 2) if sub == "420" else (W, H)
+    y = torch.zeros((H, W), dtype=dt, device="cuda")
+    u = torch.zeros((ch, cw), dtype=dt, device="cuda")
+    v = torch.zeros((ch, cw), dtype=dt, device="cuda")
+    nv.nvisr_requant(f, dev, y, u, v)
+    torch.cuda.synchronize()
+    got = {"Y": from_dev(y, bits), "U": from_dev(u, bits), "V": from_dev(v, bits)}
+    assert_codes_match(got, prequant(rgb.astype(np.float64), fd), bits)
+
+
 def _bf16(a):
     return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).double().numpy()
 

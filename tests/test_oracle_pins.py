@@ -91,6 +91,39 @@ def test_matrix_rows_luma_weights():
     assert oracle.rgb_to_ycbcr(0.0, 0.0, 1.0)[1] == pytest.approx(0.5)
 
 
+@pytest.mark.parametrize("matrix", ["bt709", "bt2020"])
+def test_matrix_fp64_round_trip_each_matrix(matrix):
+    rng = np.random.default_rng(2)
+    y, cb, cr = rng.uniform(-0.5, 1.5, (3, 64))
+    r, g, b = oracle.ycbcr_to_rgb(y, cb, cr, matrix)
+    y2, cb2, cr2 = oracle.rgb_to_ycbcr(r, g, b, matrix)
+    assert max(abs(y - y2).max(), abs(cb - cb2).max(), abs(cr - cr2).max()) < 1e-12
+
+
+def test_bt2020_luma_weights():
+    """BT.2020 (non-constant luminance): Y' of a pure primary is its weight (Kr 0.2627,
+    Kb 0.0593, Kg 0.6780), grey has zero chroma and a primary's own chroma is +-0.5."""
+    r = oracle.rgb_to_ycbcr(1.0, 0.0, 0.0, "bt2020")
+    g = oracle.rgb_to_ycbcr(0.0, 1.0, 0.0, "bt2020")
+    b = oracle.rgb_to_ycbcr(0.0, 0.0, 1.0, "bt2020")
+    assert r[0] == pytest.approx(0.2627) and g[0] == pytest.approx(0.6780) and b[0] == pytest.approx(0.0593)
+    assert r[2] == pytest.approx(0.5) and b[1] == pytest.approx(0.5)
+    y, cb, cr = oracle.rgb_to_ycbcr(np.array(0.4), np.array(0.4), np.array(0.4), "bt2020")
+    assert abs(cb) < 1e-15 and abs(cr) < 1e-15 and abs(y - 0.4) < 1e-15
+
+
+@pytest.mark.parametrize("bits", [12, 16])
+def test_range_pins_high_bit_depths(bits):
+    """Limited range at b bits scales the 8-bit anchors by 2^(b-8); full range spans the codes."""
+    m = 2 ** (bits - 8)
+    assert oracle.normalise_luma(16 * m, bits, "limited") == 0.0
+    assert oracle.normalise_luma(235 * m, bits, "limited") == pytest.approx(1.0)
+    assert oracle.normalise_chroma(128 * m, bits, "limited") == 0.0
+    assert oracle.normalise_chroma(240 * m, bits, "limited") == pytest.approx(0.5)
+    assert oracle.normalise_luma(2 ** bits - 1, bits, "full") == 1.0
+    assert oracle.quantise(oracle.scale_luma(1.0, bits, "limited"), bits) == 235 * m
+
+
 @pytest.mark.parametrize("rng_name", ["limited", "full"])
 def test_8bit_round_trip_within_1lsb(rng_name):
     """8-bit YUV -> RGB -> 8-bit RGB -> YUV stays within +-1 LSB for in-gamut colours."""
