@@ -95,3 +95,64 @@ def crop_codes(planes, y0, y1, x0, x1, s, sub):
         out["U"] = planes["U"][y0 * s:y1 * s, x0 * s:x1 * s]
         out["V"] = planes["V"][y0 * s:y1 * s, x0 * s:x1 * s]
     return out
+
+
+def _run_layer(layer, env):
+    """One layer of the oracle graph on the tensors of env (as oracle.Net.forward does)."""
+    srcs = layer.get("in").split(",")
+    x = np.concatenate([env[s] for s in srcs]) if len(srcs) > 1 else env[srcs[0]]
+    y = oracle.conv2d_direct(x, layer.w, layer.b)
+    if layer.get("act") == "lrelu":
+        y = oracle.leaky_relu(y)
+    if layer.get("add"):
+        y = y + env[layer.get("add")]
+    if layer.get("ps"):
+        y = oracle.pixel_shuffle(y, layer.get("ps"))
+    return y
+
+
+def stvsr_window(net, rgb, y0, y1, x0, x1, out_fmt, margin=16):
+    """Oracle codes of the LR window [y0,y1) x [x0,x1) of both outputs of the first run
+    of the deformable space-time SR network (synth.net_group_stvsr), at full size.
+
+    The DCN's reach is data dependent, so it cannot be cropped like a plain conv
+    stack.  Instead: the extract convs run on the whole frames; the offset/mask
+    heads and everything after the DCNs run on a crop of `margin` LR pixels around
+    the window (the radius of the layers after the DCN, plus the head's); the DCNs
+    sample the whole-frame features at the crop's pixels.  Entries away from the
+    crop's artificial borders equal the whole-frame result.
+    """
+    L = {layer.name: layer for layer in net.layers}
+    H, W = rgb[0].shape[1:]
+    s = net.scale
+    cy0, cy1 = max(y0 - margin, 0), min(y1 + margin, H)
+    cx0, cx1 = max(x0 - margin, 0), min(x1 + margin, W)
+    cy0 -= cy0 % 2
+    cx0 -= cx0 % 2
+    full = {"frame0": rgb[0], "frame1": rgb[1]}
+    full["f0"] = _run_layer(L["f0"], full)
+    full["f1"] = _run_layer(L["f1"], full)
+    crop = {k: v[:, cy0:cy1, cx0:cx1] for k, v in full.items()}
+    for a, head in (("a0", "om01"), ("a1", "om10")):
+        om_c = _run_layer(L[head], crop)  # exact inside the crop's interior
+        om = np.zeros((om_c.shape[0], H, W))
+        om[:, cy0:cy1, cx0:cx1] = om_c
+        d = L[a]
+        g = d.get("groups")
+        y = oracle.dcn2d(full[d.get("in")], om[:18 * g], oracle.sigmoid(om[18 * g:27 * g]), d.w, d.b, g,
+                         window=(cy0, cy1, cx0, cx1))
+        crop[a] = y[:, cy0:cy1, cx0:cx1]
+    names = [layer.name for layer in net.layers if layer.name not in ("f0", "f1", "om01", "om10", "a0", "a1")]
+    for name in names:
+        crop[name] = _run_layer(L[name], crop)
+    res = []
+    for name, skip in net.outputs:
+        frames = (skip or "").split(",")
+        sk = sum(net._skip(crop[f]) for f in frames) / len(frames)
+        pq = prequant(crop[name] + sk, out_fmt)
+        oy, ox = (y0 - cy0) * s, (x0 - cx0) * s
+        hy, hx = (y1 - y0) * s, (x1 - x0) * s
+        res.append({"Y": pq["Y"][oy:oy + hy, ox:ox + hx],
+                    "U": pq["U"][oy // 2:(oy + hy) // 2, ox // 2:(ox + hx) // 2],
+                    "V": pq["V"][oy // 2:(oy + hy) // 2, ox // 2:(ox + hx) // 2]})
+    return res

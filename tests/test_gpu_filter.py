@@ -7,7 +7,7 @@ import oracle
 import paper_2308_03121_gb300 as nv
 import synth
 from gpu_util import (assert_codes_match, crop_codes, fmt_dict, lsb_stats, oracle_window, prequant,
-                      to_dev)
+                      stvsr_window, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -171,6 +171,34 @@ def test_config2_full_size_sampled_windows(prec):
             else:
                 mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 10) for k in "YUV"})
                 assert mx <= 1, (t, (y0, x0), mx)
+
+
+STVSR_WINDOWS = [(0, 16, 0, 16), (0, 16, 944, 960), (524, 540, 944, 960), (270, 286, 480, 496),
+                 (100, 116, 120, 136)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_config3_full_size_sampled_windows(prec):
+    """960x540 8-bit, the deformable ST-SR network in the bench's launch shapes: both outputs
+    of the first run on sampled windows (corners, the ragged last column tile, interior)."""
+    W, H = 960, 540
+    frames = synth.frames_textured(synth.BASE_SEED + 3, 2, W, H, 8, "420", "limited")
+    flags = np.zeros(2, bool)
+    text, blob = synth.net_config3()
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(4 * W, 4 * H, 8), prec, scale=4,
+                      limit=2)
+    fdi, fdo = fmt_dict(W, H, 8), fmt_dict(4 * W, 4 * H, 8)
+    net = oracle.Net(text, blob)
+    rgb = [oracle.ingest(f, fdi) for f in frames]
+    for (y0, y1, x0, x1) in STVSR_WINDOWS:
+        exp = stvsr_window(net, rgb, y0, y1, x0, x1, fdo)
+        for k in range(2):
+            got = crop_codes(outs[k], y0, y1, x0, x1, 4, "420")
+            if prec == "fp32":
+                assert_codes_match(got, exp[k], 8)
+            else:
+                mx, _ = lsb_stats(got, {p: oracle.quantise(exp[k][p], 8) for p in "YUV"})
+                assert mx <= 1, ((y0, x0), k, mx)
 
 
 def test_fp8_filter_reports_error_vs_oracle():
