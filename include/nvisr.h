@@ -151,9 +151,10 @@ nvisr_status nvisr_filter_create(nvisr_engine *engine, const nvisr_filter_desc *
 /* Release a filter's device memory and handle. NULL is ignored. */
 void nvisr_filter_destroy(nvisr_filter *filter);
 
-/* Push the next input frame.  Planes are copied into the filter's device ring
- * and converted by the ingest kernel before the call returns (host planes are
- * read synchronously; device planes are consumed in stream order).
+/* Push the next input frame.  Host planes are copied to the device (on the
+ * engine's copy stream) before the call returns and may be reused at once;
+ * the ingest kernel that converts them into the filter's ring runs in stream
+ * order on the engine's stream, as it does for device planes.
  * flags: NVISR_FRAME_SCENE_CUT marks the frame as the first of a new scene
  * (Section 3.2: scene changes arrive as a per-frame property).
  * Returns FULL when the ring holds no free slot (pull first), EOS after flush. */
@@ -167,8 +168,14 @@ nvisr_status nvisr_flush(nvisr_filter *filter);
  * planes (host or device).  Runs the network for the output's frame group if
  * it has not run yet.  Returns AGAIN if the group's input frames are not all
  * known yet, EOS once a flushed stream has returned every output.  For host
- * planes the call returns after the copy completes; device planes are
- * written in stream order.  info may be NULL. */
+ * planes the call returns after the copy completes; while the copy runs (on
+ * the engine's copy stream) the next ready output of a filter outside any
+ * batch is already computed on the engine's stream.  Device planes are
+ * written in stream order.  Group networks (Section 3.1) take n frames per
+ * run (+1 with Extra frame, n <= 8 inputs) and emit n outputs per run (2n
+ * with Double frame, <= 8); without Interpolation a scene's last run is moved
+ * back inside the scene and the outputs an earlier run emitted are skipped
+ * (Section 3.3).  info may be NULL. */
 nvisr_status nvisr_pull(nvisr_filter *filter, nvisr_planes *out, nvisr_frame_info *info);
 
 /* Number of outputs the filter can currently pull without more input. */
