@@ -76,7 +76,7 @@ def run_filter(frames, flags, net_text, blob, in_fmt, out_fmt, outputs=None, kee
 
     def rgb(i):
         if i not in cache:
-            cache[i] = pad_to_align(ingest(frames[i], in_fmt), net.align)
+            cache[i] = pad_to_align(ingest(frames[i], in_fmt, net.domain), net.align)
         return cache[i]
 
     h, w = frames[0]["Y"].shape
@@ -86,7 +86,7 @@ def run_filter(frames, flags, net_text, blob, in_fmt, out_fmt, outputs=None, kee
 
     def emit(img):
         img = img[:, :oh, :ow]
-        results.append(img if keep_float else requantise(img, out_fmt))
+        results.append(img if keep_float else requantise(img, out_fmt, net.domain))
 
     if net.family == "tuple":
         for t in range(nframes):

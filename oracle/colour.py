@@ -169,8 +169,9 @@ def downsample_chroma(c, subsampling: str, loc: str):
 
 # ---------------------------------------------------------------- ingest / requantise
 
-def ingest(planes, fmt):
-    """Integer Y/U/V planes -> float64 R'G'B' [3][H][W] (network domain RGB, unclamped).
+def ingest(planes, fmt, domain: str = "rgb"):
+    """Integer Y/U/V planes -> float64 R'G'B' [3][H][W] (network domain RGB, unclamped), or
+    the normalised Y'Cb'Cr' planes (chroma upsampled, no matrix) for a YUV-domain network.
 
     fmt: dict with bit_depth, subsampling ('420'|'444'), range ('limited'|'full'),
     chroma_loc ('left'|'center'|'point') and optionally matrix ('bt709' default, 'bt2020').
@@ -179,18 +180,23 @@ def ingest(planes, fmt):
     yp = normalise_luma(planes["Y"], b, rg)
     cb = upsample_chroma(normalise_chroma(planes["U"], b, rg), fmt["subsampling"], fmt["chroma_loc"])
     cr = upsample_chroma(normalise_chroma(planes["V"], b, rg), fmt["subsampling"], fmt["chroma_loc"])
+    if domain == "yuv":
+        return np.stack([yp, cb, cr])
     r, g, bb = ycbcr_to_rgb(yp, cb, cr, fmt.get("matrix", "bt709"))
     return np.stack([r, g, bb])
 
 
-def requantise(rgb, fmt):
+def requantise(rgb, fmt, domain: str = "rgb"):
     """float R'G'B' [3][H][W] -> integer planes {"Y","U","V"} (int64 arrays).
 
     Y'CbCr from RGB, chroma downsampled in float, scaled to the code range,
     rounded half to even and clamped to [0, 2^b - 1].
     """
     b, rg = fmt["bit_depth"], fmt["range"]
-    yp, cb, cr = rgb_to_ycbcr(rgb[0], rgb[1], rgb[2], fmt.get("matrix", "bt709"))
+    if domain == "yuv":  # a YUV-domain network's planes are Y'Cb'Cr' already
+        yp, cb, cr = rgb[0], rgb[1], rgb[2]
+    else:
+        yp, cb, cr = rgb_to_ycbcr(rgb[0], rgb[1], rgb[2], fmt.get("matrix", "bt709"))
     cb = downsample_chroma(cb, fmt["subsampling"], fmt["chroma_loc"])
     cr = downsample_chroma(cr, fmt["subsampling"], fmt["chroma_loc"])
     return {"Y": quantise(scale_luma(yp, b, rg), b),

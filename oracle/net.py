@@ -168,6 +168,7 @@ class Net:
         self.scale = 1
         self.skip = "none"
         self.flags = set()
+        self.domain = "rgb"
         self.align = 1
         self.layers = []
         self.outputs = []
@@ -192,6 +193,8 @@ class Net:
                 self.align = int(tok[1])
             elif key == "flags":
                 self.flags = set(tok[1].split(","))
+            elif key == "domain":
+                self.domain = tok[1]
             elif key in ("conv", "dcn"):
                 attrs = dict(t.split("=", 1) for t in tok[2:])
                 for k in ("cin", "cout", "k", "groups", "ps"):

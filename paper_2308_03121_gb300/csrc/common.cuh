@@ -46,9 +46,10 @@ nvisr_status cuda_status(cudaError_t e, const char *where);
 // ---------------------------------------------------------------------------
 
 // ingest: integer planes -> float32 planar R'G'B' (pitch in floats).
+// yuv: the network works on Y'Cb'Cr' planes (no colour matrix in ingest / requantise).
 cudaError_t launch_ingest(const nvisr_format &fmt, const void *y, int64_t py, const void *u,
                           int64_t pu, const void *v, int64_t pv, float *out, int64_t out_pitch,
-                          cudaStream_t st);
+                          cudaStream_t st, int yuv = 0);
 
 // The network's skip path: the mean of up to two input frames (planar float32
 // [3][h][pitch]) upsampled by an integer scale (1 nearest, 2 bilinear with
@@ -63,7 +64,7 @@ struct SkipArgs {
 // requantise: float32 planar R'G'B' (+ skip) -> integer planes.
 cudaError_t launch_requant(const nvisr_format &fmt, const float *in, int64_t in_pitch, void *y,
                            int64_t py, void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st,
-                           const SkipArgs *skip = nullptr);
+                           const SkipArgs *skip = nullptr, int yuv = 0);
 
 // Up to 8 planar float32 frames of 3 channels each (tuple, frame-major
 // channels) or one planar tensor of C channels -> blocked tensor of dtype dt

@@ -1218,7 +1218,7 @@ nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, int slot) {
     {
         ProfScope ps(f, NVISR_K_REQUANT);
         e = launch_requant(of, f->out_rgb[slot], f->opitch, dst[0], pitch[0], dst[1], pitch[1], dst[2], pitch[2], st,
-                           &f->skip[slot]);
+                           &f->skip[slot], f->net.yuv ? 1 : 0);
     }
     if (e != cudaSuccess) return cuda_status(e, "requant");
     if (out->on_device) return NVISR_OK;
@@ -1633,7 +1633,7 @@ nvisr_status nvisr_push(nvisr_filter *f, const nvisr_planes *in, uint32_t flags)
     {
         ProfScope ps(f, NVISR_K_INGEST);
         e = launch_ingest(f->in_fmt, src[0], pitch[0], src[1], pitch[1], src[2], pitch[2], ring_slot(f, f->pushed),
-                          f->rpitch, st);
+                          f->rpitch, st, f->net.yuv ? 1 : 0);
     }
     if (e != cudaSuccess) return cuda_status(e, "ingest");
     if (!in->on_device) {

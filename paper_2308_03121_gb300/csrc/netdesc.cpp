@@ -80,6 +80,9 @@ bool parse_netdesc(const char *text, int64_t blob_count, NetDesc *net, std::stri
                 else if (f == "double") net->dbl = true;
                 else return fail("unknown flag " + f);
             }
+        } else if (key == "domain") {
+            if (tok.size() != 2 || (tok[1] != "rgb" && tok[1] != "yuv")) return fail("bad domain (rgb or yuv)");
+            net->yuv = tok[1] == "yuv";
         } else if (key == "skip") {
             if (tok.size() != 2) return fail("bad skip");
             if (tok[1] == "none") net->skip = 0;

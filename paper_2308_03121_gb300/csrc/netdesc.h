@@ -38,6 +38,7 @@ struct NetDesc {
     int align = 1;
     bool interp = false, extra = false, dbl = false;
     int skip = 0;                    // 0 none, 1 nearest, 2 bilinear
+    bool yuv = false;                // network domain: R'G'B' (default) or Y'CbCr (Section 3.1)
     std::vector<NetLayer> layers;
     std::vector<NetOutput> outputs;
     int64_t weights_used = 0;

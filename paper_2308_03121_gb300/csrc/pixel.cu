@@ -32,10 +32,12 @@ struct RangeConst {
     // colour matrix (BT.709 or BT.2020 non-constant luminance): luma weights and
     // the derived factors 2(1 - Kr), 2(1 - Kb), 1 / Kg, 1 / (2(1 - Kb)), 1 / (2(1 - Kr))
     float kr, kb, kg, cr_r, cb_b, rkg, cb_s, cr_s;
+    int yuv;  // the network sees Y'Cb'Cr' planes: no matrix either way
 };
 
-RangeConst range_const(int bits, int range, int matrix) {
+RangeConst range_const(int bits, int range, int matrix, int yuv) {
     RangeConst r;
+    r.yuv = yuv;
     r.kr = matrix == NVISR_MATRIX_BT2020 ? 0.2627f : 0.2126f;
     r.kb = matrix == NVISR_MATRIX_BT2020 ? 0.0593f : 0.0722f;
     r.kg = 1.0f - r.kr - r.kb;
@@ -127,9 +129,15 @@ __global__ void __launch_bounds__(256) ingest_kernel(
             cb = chroma_at<S>(up, pu, Hc, Wc, y, x, rc.c_off, rc.c_den);
             cr = chroma_at<S>(vp, pv, Hc, Wc, y, x, rc.c_off, rc.c_den);
         }
-        r[e] = Y + rc.cr_r * cr;
-        b[e] = Y + rc.cb_b * cb;
-        g[e] = (Y - rc.kr * r[e] - rc.kb * b[e]) / rc.kg;
+        if (rc.yuv) {
+            r[e] = Y;
+            g[e] = cb;
+            b[e] = cr;
+        } else {
+            r[e] = Y + rc.cr_r * cr;
+            b[e] = Y + rc.cb_b * cb;
+            g[e] = (Y - rc.kr * r[e] - rc.kb * b[e]) / rc.kg;
+        }
     }
     const int64_t plane = pitch * H;
     float *o = out + (int64_t)y * pitch + x0;
@@ -259,9 +267,15 @@ __global__ void __launch_bounds__(128) ingest420_kernel(
                 cr = vvv[li];
             }
             const float Y = (ys[e] - rc.y_off) * rc.y_rden;
-            r[e] = Y + rc.cr_r * cr;
-            b[e] = Y + rc.cb_b * cb;
-            g[e] = (Y - rc.kr * r[e] - rc.kb * b[e]) * rc.rkg;
+            if (rc.yuv) {
+                r[e] = Y;
+                g[e] = cb;
+                b[e] = cr;
+            } else {
+                r[e] = Y + rc.cr_r * cr;
+                b[e] = Y + rc.cb_b * cb;
+                g[e] = (Y - rc.kr * r[e] - rc.kb * b[e]) * rc.rkg;
+            }
         }
         float *o = out + (int64_t)y * pitch + x0;
         if (vec) {
@@ -333,6 +347,12 @@ __device__ __forceinline__ float out_at(const float *in, int64_t pitch, int64_t 
 
 __device__ __forceinline__ void rgb2ycc(const RangeConst &rc, float r, float g, float b, float &y, float &cb,
                                         float &cr) {
+    if (rc.yuv) {  // channels are Y'Cb'Cr' already
+        y = r;
+        cb = g;
+        cr = b;
+        return;
+    }
     y = rc.kr * r + rc.kg * g + rc.kb * b;
     cb = (b - y) * rc.cb_s;
     cr = (r - y) * rc.cr_s;
@@ -727,8 +747,8 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
 }  // namespace
 
 cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, const void *u, int64_t pu,
-                          const void *v, int64_t pv, float *out, int64_t out_pitch, cudaStream_t st) {
-    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix);
+                          const void *v, int64_t pv, float *out, int64_t out_pitch, cudaStream_t st, int yuv) {
+    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix, yuv);
     if (f.subsampling == NVISR_SUB_420) {
         dim3 blk(128);
         dim3 grd((f.width + 8 * 128 - 1) / (8 * 128), (f.height + 1) / 2, 2);
@@ -757,8 +777,9 @@ cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, cons
 }
 
 cudaError_t launch_requant(const nvisr_format &f, const float *in, int64_t in_pitch, void *y, int64_t py,
-                           void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st, const SkipArgs *skip) {
-    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix);
+                           void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st, const SkipArgs *skip,
+                           int yuv) {
+    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix, yuv);
     SkipArgs sk{};
     if (skip) sk = *skip;
     dim3 block(64);

@@ -170,6 +170,7 @@ class NetSpec:
         frames <T>
         scale <s>
         flags interp,extra,double          (group family)
+        domain rgb|yuv                     (network colour domain, default rgb)
         skip none|nearest|bilinear
         conv <name> in=<a>[,<b>] cin=<C> cout=<N> k=<1|3> act=none|lrelu
              [add=<name>] [ps=<r>] [share=<name>]
@@ -180,10 +181,12 @@ class NetSpec:
     order: weight [cout][cin][k][k] then bias [cout], float32 little endian.
     """
 
-    def __init__(self, family: str, frames: int, scale: int, skip: str, flags: str = ""):
+    def __init__(self, family: str, frames: int, scale: int, skip: str, flags: str = "", domain: str = "rgb"):
         self.lines = ["nvisr-net 1", f"family {family}", f"frames {frames}", f"scale {scale}"]
         if flags:
             self.lines.append(f"flags {flags}")
+        if domain != "rgb":
+            self.lines.append(f"domain {domain}")
         self.lines.append(f"skip {skip}")
         self.blobs = []
 
@@ -239,10 +242,11 @@ OFFSET_GAIN = 2.0
 
 
 def net_tuple(seed: int, frames: int, channels: int, nres: int, scale: int = 2,
-              skip: str = "bilinear", tail_gain: float = TAIL_GAIN, res_gain: float = RES_GAIN):
+              skip: str = "bilinear", tail_gain: float = TAIL_GAIN, res_gain: float = RES_GAIN,
+              domain: str = "rgb"):
     """Sliding-window SR network: conv(3T->C), nres residual blocks, conv(C->3 s^2), PixelShuffle(s)."""
     rng = np.random.default_rng(seed)
-    spec = NetSpec("tuple", frames, scale, skip)
+    spec = NetSpec("tuple", frames, scale, skip, domain=domain)
     spec.conv(rng, "head", "tuple", 3 * frames, channels, act="none")
     prev = "head"
     for i in range(nres):

@@ -339,3 +339,28 @@ def test_filter_bt2020_12bit(prec):
         else:
             mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 12) for k in "YUV"})
             assert mx <= 4, mx  # 12-bit codes: the 10-bit +-1 LSB bound, scaled by 4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_filter_yuv_domain_network(prec):
+    """A network that works on Y'Cb'Cr' (Section 3.1): ingest and requantise skip the colour
+    matrix; 10-bit 4:2:0 in and out, config-1 shapes, a cut on frame 4."""
+    frames = synth.frames_textured(synth.BASE_SEED + 72, 7, 64, 48, 10, "420", "limited")
+    flags = np.zeros(7, bool)
+    flags[4] = True
+    fdi, fdo = fmt_dict(64, 48, 10), fmt_dict(128, 96, 10)
+    text, blob = synth.net_tuple(synth.BASE_SEED + 73, frames=3, channels=32, nres=2, scale=2, domain="yuv")
+    ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(64, 48, 10), nv.fmt(128, 96, 10), prec)
+    assert len(outs) == len(ref) == 7
+    for got, r in zip(outs, ref):
+        # a YUV-domain output is requantised without the matrix
+        b = 10
+        pq = {"Y": oracle.scale_luma(r[0], b, "limited"),
+              "U": oracle.scale_chroma(oracle.downsample_chroma(r[1], "420", "left"), b, "limited"),
+              "V": oracle.scale_chroma(oracle.downsample_chroma(r[2], "420", "left"), b, "limited")}
+        if prec == "fp32":
+            assert_codes_match(got, pq, b)
+        else:
+            mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], b) for k in "YUV"})
+            assert mx <= 1, mx

@@ -480,6 +480,24 @@ def test_zero_residual_nearest_reproduces_input(sub, loc):
             assert np.array_equal(o[k], exp), k
 
 
+@pytest.mark.parametrize("sub,loc", [("444", "left"), ("420", "point")])
+def test_yuv_domain_zero_residual_reproduces_input(sub, loc):
+    """A YUV-domain network (Section 3.1: networks may work on YUV) with zero residual and
+    nearest skip returns its input codes, for any code values (no colour matrix either way)."""
+    text, blob = synth.net_tuple(5, frames=3, channels=8, nres=1, scale=2, skip="nearest", domain="yuv")
+    blob = blob.copy()
+    blob[-(12 * 8 * 9 + 12):] = 0.0
+    rng = np.random.default_rng(3)
+    cw, ch = (16, 12) if sub == "444" else (8, 6)
+    frames = [{"Y": rng.integers(0, 1024, (12, 16)), "U": rng.integers(0, 1024, (ch, cw)),
+               "V": rng.integers(0, 1024, (ch, cw))} for _ in range(4)]
+    fmt = _fmt(10, sub, "full", loc)
+    outs = oracle.run_filter(frames, np.zeros(4, bool), text, blob, fmt, fmt)
+    for f, o in zip(frames, outs):
+        for k in "YUV":
+            assert np.array_equal(o[k], np.repeat(np.repeat(f[k].astype(np.int64), 2, 0), 2, 1)), k
+
+
 def test_scene_cut_never_leaks():
     """Poison every frame outside output t's scene: output t is bit-identical."""
     frames = synth.frames_gradient(synth.BASE_SEED + 1, 8, 16, 16, 8, "420", "full")
