@@ -128,6 +128,12 @@ struct ConvArgs {
     int skip_scale;          // output size / skip frame size
     int skip_h, skip_w;      // skip frame size
     int ps_act;              // activation applied after the shuffle (blocked ps output)
+    // tuple head only: read the tuple's ntup frames (float32 planar [3][H][ring_pitch] ring
+    // slots tslot[] of ring) instead of a packed x
+    const float *ring;
+    int ring_slots, ntup;
+    int64_t ring_pitch;
+    int tslot[8];
     int *err;                // device error word (tensor-core kernels), may be null
 };
 cudaError_t launch_conv_simt(const ConvArgs &a, cudaStream_t st);
@@ -141,6 +147,8 @@ struct RowProblem {  // aligned as its tensor maps (at least 64 bytes)
 };
 // True when launch_conv_rows_multi takes layers of this shape.
 bool rows_kernel_fits(const ConvArgs &a);
+// 3x3 16-channel 16-bit head (packed tuple input, or the ring frames when a.ring is set)
+bool rows_head_fits(const ConvArgs &a);
 // One launch over n problems (same weights, bias, activation and dtypes; each
 // its own x / y / res and size).  host_tab and dev_tab hold n RowProblem
 // entries; the table is written to host_tab, copied to dev_tab on `st`, and

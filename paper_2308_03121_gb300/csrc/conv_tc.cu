@@ -46,6 +46,8 @@ constexpr int TM = 128;
 // (two warps per TMEM lane quadrant, each owning half of the accumulator columns)
 constexpr int NTHREADS = 320;
 constexpr int ROWS_THREADS = 352;     // row kernel: + one warp that performs the MMA issuer's waits
+// the 16-channel head adds a twelfth warp: with warp 0 it converts the tuple's float32 frames
+constexpr int rows_threads(int cin, bool multi) { return cin == 16 && !multi ? 384 : ROWS_THREADS; }
 constexpr int NEPI = 256;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 232448;  // 227 KB per CTA
@@ -73,6 +75,8 @@ struct TcParams {
     ConvArgs skip;  // skip_* fields only
     int ps_act;
     int no_main;                      // row kernel: no 16-bit output, the FP8 copy (y2) is the output
+    int ntup;                         // row kernel, 16-channel head: > 0 = read the tuple's ntup float32
+    int tslot[8];                     //   frames from the ring (slots tslot[]) instead of a packed tensor
     int *err;
 };
 
@@ -555,7 +559,7 @@ struct RowPlan {
 };
 
 template <int IN_DT, int OUT_DT, int CBO, bool MULTI, int NPR, bool PS, int CIN>
-__global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 const __grid_constant__ CUtensorMap ymap,
                                                                 const __grid_constant__ CUtensorMap rmap,
                                                                 const TcParams p, const RowPlan rp,
@@ -671,10 +675,24 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     auto width_of = [&](int pi) { return MULTI ? probs[pi].W : p.W; };
     if (threadIdx.x >= 64 && threadIdx.x < 64 + NPR)
         sbias[threadIdx.x - 64] = p.bias[PSB ? 4 * (threadIdx.x - 64) + slice : slice * NPR + threadIdx.x - 64];
+    // 16-channel head reading the tuple's float32 frames (ntup > 0): warp 0 converts
+    // each row from NST32 float32 staging rows (TMA from the ring) into the stage
+    constexpr int NST32 = 8;
+    constexpr uint32_t BOX32 = 3 * 136 * 4;                    // one frame's three planes of a row, x0-4 .. x0+131
+    constexpr uint32_t FROW32 = (BOX32 + 127u) & ~127u;        // its slot (TMA destinations are 128-byte aligned)
+    constexpr uint32_t SROW32 = 5 * FROW32;                    // a staging row: up to 5 frames
+    constexpr bool TUPF = CIN == 16 && IN_DT != DT_E4M3;
+    const bool tup = TUPF && p.ntup > 0;
+    uint64_t *full32 = reinterpret_cast<uint64_t *>(smem + 320);
+    uint64_t *empty32 = full32 + NST32;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], tup ? 64 : 1);  // TMA completion, or the two converting warps' arrivals
             mbar_init(&empty[s], 1);
+        }
+        for (int k = 0; k < NST32; ++k) {
+            mbar_init(&full32[k], 1);
+            mbar_init(&empty32[k], 64);
         }
         for (int k = 0; k < NSLOT; ++k) {
             mbar_init(&rowdone[k], 1);
@@ -698,7 +716,123 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp == 0) {
+    if ((warp == 0 || warp == 11) && tup) {
+        // ---------------- producer (warps 0 and 11), tuple head: per input row, warp 0 lane 0
+        // keeps up to NST32 rows of the ntup float32 frames in flight (TMA boxes of 136 pixels
+        // from x0 - 4, so the innermost coordinate stays 16-byte aligned; OOB reads as zero),
+        // then the two warps convert the row (warp 0 pixels 0-63, warp 11 pixels 64-129) into the
+        // stage's [2 chunks][130 px][8 channels] 16-bit layout, channels frame-major (the tuple
+        // pack's layout) with round-to-nearest (its rounding).
+        if constexpr (TUPF) {
+        const bool loader = warp == 0;
+        const int px0 = loader ? 0 : 64;
+        using TI = typename Elem<IN_DT>::T;
+        uint8_t *st32 = obuf + 2 * TILEB;
+        if (loader && lane == 0) {
+            mbar_arrive_expect_tx(wbar, 3 * WKX);
+            for (uint32_t off = 0; off < 3 * WKX; off += 32768u)
+                bulk_load(wsm + off, p.wts + off, min(32768u, 3 * WKX - off), wbar);
+        }
+        int t_sidx = cta0, t_r = 0, t_ra = 0, t_rb = 0, t_x0 = 0, t_img = 0, t_pi = 0;
+        bool t_live = false;
+        // positions the load cursor on the next input row in the converting order
+        auto t_next = [&]() -> bool {
+            if (t_live && ++t_r <= t_rb) return true;
+            if (t_live) t_sidx += cstride;
+            t_live = false;
+            if (t_sidx >= nstrips) return false;
+            strip_of(t_sidx, t_img, t_x0, t_ra, t_rb, t_pi);
+            t_r = t_ra - 1;
+            t_live = true;
+            return true;
+        };
+        int gin = 0, issued = 0;
+        bool ok = true;
+        for (int sidx = cta0; sidx < nstrips && ok; sidx += cstride) {
+            int img, x0, ra, rb, pi;
+            strip_of(sidx, img, x0, ra, rb, pi);
+            for (int r = ra - 1; r <= rb; ++r, ++gin) {
+                if (loader && lane == 0) {
+                    while (ok && issued < gin + NST32 && t_next()) {
+                        const int k = issued % NST32;
+                        // the slot's previous row (issued - NST32 < gin) was converted by this warp;
+                        // the wait covers warp 11's half
+                        if (!mbar_wait_bounded(&empty32[k], (uint32_t)((issued / NST32) & 1) ^ 1u, abort, WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full32[k], (uint32_t)p.ntup * BOX32);
+                        for (int f = 0; f < p.ntup; ++f)
+                            tma_load_4d(st32 + (size_t)k * SROW32 + (size_t)f * FROW32, tmap_of(t_pi), &full32[k],
+                                        t_x0 - 4, t_r, 0, p.tslot[f]);
+                        ++issued;
+                    }
+                }
+                const int k = gin % NST32, s = gin % S;
+                bool w = __shfl_sync(0xffffffffu, ok, 0);
+                w = w && mbar_wait_bounded(&full32[k], (uint32_t)((gin / NST32) & 1), abort, WAIT_NS);
+                w = w && mbar_wait_bounded(&empty[s], (uint32_t)((gin / S) & 1) ^ 1u, abort, WAIT_NS);
+                if (!__all_sync(0xffffffffu, w)) {
+                    if (lane == 0) raise_abort(abort, p.err);
+                    ok = false;
+                    break;
+                }
+                // lane l converts stage pixels px0 + l, px0 + l + 32 (warp 11: then lanes 0, 1 pixels
+                // 128, 129): all loads first (conflict-free 4-byte loads), then conversion and one
+                // 16-byte store per chunk and pixel (consecutive across the warp).  Stage pixel px is
+                // staged float px + 3 of each channel row; channels of frames >= ntup read stale
+                // staging and are replaced by zero.
+                const uint32_t src = smem_u32(st32 + (size_t)k * SROW32) + 12u;
+                const uint32_t dst = smem_u32(stage0 + (size_t)s * ROWB);
+                const int nch = 3 * p.ntup;
+                auto chan = [](int ch) { return (uint32_t)((ch / 3) * FROW32 + (ch % 3) * 544); };
+                auto emit = [&](int px, const float (&u)[16]) {
+                    uint4 c0, c1;
+                    c0.x = pack2<TI>(u[0], u[1]);   c0.y = pack2<TI>(u[2], u[3]);
+                    c0.z = pack2<TI>(u[4], u[5]);   c0.w = pack2<TI>(u[6], u[7]);
+                    c1.x = pack2<TI>(u[8], u[9]);   c1.y = pack2<TI>(u[10], u[11]);
+                    c1.z = pack2<TI>(u[12], u[13]); c1.w = pack2<TI>(u[14], u[15]);
+                    st_shared_u4(dst + (uint32_t)px * 16, c0);
+                    st_shared_u4(dst + (uint32_t)(PXS + px) * 16, c1);
+                };
+                {
+                    float v[2][16];
+#pragma unroll
+                    for (int ch = 0; ch < 15; ++ch)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q)
+                            v[q][ch] = ld_shared_f32(src + chan(ch) + (uint32_t)(px0 + lane + 32 * q) * 4);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                        for (int ch = 0; ch < 15; ++ch) v[q][ch] = ch < nch ? v[q][ch] : 0.f;
+                        v[q][15] = 0.f;
+                        emit(px0 + lane + 32 * q, v[q]);
+                    }
+                }
+                static_assert(PXS == 130, "two halves of 64 pixels and a two-pixel tail");
+                if (!loader && lane < 2) {
+                    float v[16];
+#pragma unroll
+                    for (int ch = 0; ch < 15; ++ch) v[ch] = ld_shared_f32(src + chan(ch) + (uint32_t)(128 + lane) * 4);
+#pragma unroll
+                    for (int ch = 0; ch < 15; ++ch) v[ch] = ch < nch ? v[ch] : 0.f;
+                    v[15] = 0.f;
+                    emit(128 + lane, v);
+                }
+                fence_proxy_async();  // shared-memory writes -> the tensor core's async proxy
+                mbar_arrive(&full[s]);
+                mbar_arrive(&empty32[k]);
+            }
+        }
+        if (loader && lane == 0) {
+            // loads still in flight after an early exit land before the CTA ends
+            for (int j = gin; j < issued; ++j)
+                mbar_wait_bounded(&full32[j % NST32], (uint32_t)((j / NST32) & 1), nullptr, WAIT_NS);
+            mbar_wait_bounded(wbar, 0, nullptr, WAIT_NS);
+        }
+        }
+    } else if (warp == 0) {
         if (lane == 0) {
             // ---------------- producer: weights, then one input row per stage
             mbar_arrive_expect_tx(wbar, 3 * WKX);
@@ -901,6 +1035,8 @@ __global__ void __launch_bounds__(ROWS_THREADS, 1) conv_rows_kernel(const __grid
             }
             if (last_slot >= 0) mbar_wait_bounded(&rowdone[last_slot], last_par, nullptr, WAIT_NS);
         }
+    } else if (warp == 11) {
+        // the 16-channel head's second converter; idle unless the head reads the tuple frames
     } else if (warp == 10) {
         if (lane == 0) {
             // ---------------- wait warp: for each input row in the issuer's order, wait
@@ -1592,16 +1728,16 @@ namespace {
 // layer adds a residual, 2 residual tiles (without one, their room goes to
 // deeper input prefetch).
 inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false, int cin = 64, bool f32out = false,
-                       bool f8 = false) {
+                       bool f8 = false, int extra = 0) {
     const uint32_t nchk = f8 ? 4u : 2u;  // 16-byte chunks per pixel of the no-swizzle forms
     const bool sw = cin != 16 && !f8;
     const uint32_t ROWB = sw ? (((uint32_t)(cin / 64) * (TM + 2) * 128 + 1023u) & ~1023u)
                              : ((nchk * (TM + 2) * 16 + 1023u) & ~1023u);
     const uint32_t WB = sw ? 3 * 3 * (uint32_t)(cin / 64) * (uint32_t)npr * 128 : 3 * nchk * 3 * (uint32_t)npr * 16;
     const uint32_t TILES = ps || f32out ? 0u : (res ? 4u : 2u) * TM * 128;
-    int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES) / (int)ROWB;
+    int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES - extra) / (int)ROWB;
     if (stages > 8) stages = 8;
-    *smem = 1024 + SMEM_HDR + (int)WB + stages * (int)ROWB + (int)TILES;
+    *smem = 1024 + SMEM_HDR + (int)WB + stages * (int)ROWB + (int)TILES + extra;
     return stages;
 }
 
@@ -1609,7 +1745,9 @@ template <int IN_DT, int OUT_DT, int CBO, int NPR = 64, bool PS = false, int CIN
 cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUtensorMap &rmap, TcParams p,
                      cudaStream_t st) {
     int smem;
-    p.stages = rows_stages(p.res != nullptr, &smem, NPR, PS, CIN, false, IN_DT == DT_E4M3);
+    // the tuple head's float32 staging rows (8 rows of 5 frames x 3 planes x 136 px, 128-byte slots)
+    const int extra = CIN == 16 && p.ntup > 0 ? 8 * 5 * ((3 * 136 * 4 + 127) & ~127) : 0;
+    p.stages = rows_stages(p.res != nullptr, &smem, NPR, PS, CIN, false, IN_DT == DT_E4M3, extra);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
     auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS, CIN>;
     cudaError_t e = set_smem_limit<conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS, CIN>>(smem);
@@ -1624,7 +1762,7 @@ cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUte
     rp.bands = (p.H + rp.rps - 1) / rp.rps;
     int grid = rp.xtiles * rp.bands * p.nimg;
     if (grid > sms) grid = sms;
-    kern<<<grid, ROWS_THREADS, smem, st>>>(map, ymap, rmap, p, rp, nullptr, 0);
+    kern<<<grid, rows_threads(CIN, false), smem, st>>>(map, ymap, rmap, p, rp, nullptr, 0);
     return cudaGetLastError();
 }
 
@@ -1659,7 +1797,7 @@ cudaError_t run_rows_sliced(const CUtensorMap &map, TcParams p, cudaStream_t st)
     rp.bands = (p.H + rp.rps - 1) / rp.rps;
     const int strips = rp.xtiles * rp.bands * p.nimg;
     const int grid = std::min(ctas, strips) * p.nslice;
-    kern<<<grid, ROWS_THREADS, smem, st>>>(map, map, map, p, rp, nullptr, 0);
+    kern<<<grid, rows_threads(CIN, false), smem, st>>>(map, map, map, p, rp, nullptr, 0);
     return cudaGetLastError();
 }
 
@@ -1813,6 +1951,32 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
         const TcParams p = rows_params(a);
         return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128>(map, ymap, rmap, p, st)
                              : run_rows<DT_F16, DT_F16, 128>(map, ymap, rmap, p, st);
+    }
+    if (rows_head_fits(a) && a.ring) {
+        // the tuple head reading its ntup float32 frames from the ring: [slot][3][H][pitch]
+        if (a.ntup < 1 || a.ntup > 5 || a.ring_pitch % 4) return cudaErrorInvalidValue;
+        ConvArgs b = a;
+        b.x = a.y;  // the 16-bit row map is not used by this form
+        CUtensorMap map, ymap, rmap;
+        cudaError_t e = encode_row_maps(b, &map, &ymap, &rmap);
+        if (e != cudaSuccess) return e;
+        auto enc = encode_fn();
+        if (!enc) return cudaErrorNotSupported;
+        cuuint64_t dims[4] = {(cuuint64_t)a.W, (cuuint64_t)a.H, 3, (cuuint64_t)a.ring_slots};
+        cuuint64_t strides[3] = {(cuuint64_t)a.ring_pitch * 4, (cuuint64_t)a.ring_pitch * a.H * 4,
+                                 (cuuint64_t)a.ring_pitch * a.H * 12};
+        cuuint32_t box[4] = {136, 1, 3, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(a.ring), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        TcParams p = rows_params(a);
+        p.wbytes = (uint32_t)tc_rows16_weight_bytes();
+        p.ntup = a.ntup;
+        for (int k = 0; k < a.ntup; ++k) p.tslot[k] = a.tslot[k];
+        return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128, 64, false, 16>(map, ymap, rmap, p, st)
+                             : run_rows<DT_F16, DT_F16, 128, 64, false, 16>(map, ymap, rmap, p, st);
     }
     if (rows_head_fits(a)) {
         CUtensorMap map, ymap, rmap;

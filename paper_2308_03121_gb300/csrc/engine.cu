@@ -208,6 +208,7 @@ struct nvisr_filter {
     void *dcn_x8 = nullptr;        // DCN input in 8-channel planes (tensor-core path)
     std::vector<Step> steps;
     int pack_t = -1;               // tensor id of the packed tuple
+    int tuple_head = -1;           // the step that alone reads the packed tuple (-1: several or none)
     float *out_rgb[8] = {};   // planar float32 residuals [3][sH][opitch], one per output of a run
     SkipArgs skip[8] = {};    // skip path of each output slot (added by requantise)
     // group family (Section 3.1): n frames per run (+1 with Extra frame), run_out outputs per run
@@ -681,11 +682,19 @@ nvisr_status build_plan(nvisr_filter *f) {
     }
     // liveness-based buffer reuse
     std::vector<int> last_use(f->tensors.size(), -1);
+    int pack_readers = 0;
+    f->tuple_head = -1;
     for (size_t i = 0; i < f->steps.size(); ++i) {
         const Step &s = f->steps[i];
         last_use[s.in_t] = std::max(last_use[s.in_t], (int)i);
         if (s.add_t >= 0) last_use[s.add_t] = std::max(last_use[s.add_t], (int)i);
+        if (s.in_t == f->pack_t) {
+            ++pack_readers;
+            f->tuple_head = (int)i;
+        }
+        if (s.add_t >= 0 && s.add_t == f->pack_t) pack_readers += 2;
     }
+    if (pack_readers != 1) f->tuple_head = -1;
     struct Buf { void *p; size_t bytes; int free_after; };
     std::vector<Buf> pool;
     auto acquire = [&](size_t bytes, int step, void **out) -> nvisr_status {
@@ -1095,6 +1104,33 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
     PackArgs pa{};
     const float *frames[8];
     for (size_t k = 0; k < idx.size(); ++k) frames[k] = pa.src[k] = ring_slot(f, idx[k]);
+    // 16-bit tensor-core head: the conv reads the tuple's frames from the ring itself (same
+    // values, channel order and rounding as the pack), so the packed tensor is not written
+    int fused = -1;
+    ConvArgs ha{};
+    if (f->tc && !calib && f->tuple_head >= 0 && idx.size() <= 5) {
+        int kind = 0;
+        ha = conv_args(f, f->steps[f->tuple_head], frames, false, &kind);
+        ha.ring = f->ring_base;
+        ha.ring_slots = f->ring;
+        ha.ring_pitch = f->rpitch;
+        ha.ntup = (int)idx.size();
+        for (size_t k = 0; k < idx.size(); ++k) ha.tslot[k] = (int)(idx[k] % f->ring);
+        if (rows_head_fits(ha) && ha.nimg == 1 && pk.C == 3 * ha.ntup) fused = f->tuple_head;
+    }
+    if (fused >= 0) {
+        for (size_t i = 0; i < f->steps.size(); ++i) {
+            if ((int)i == fused) {
+                ProfScope ps(f, NVISR_K_CONV_HEAD);
+                cudaError_t e = launch_conv_tc(ha, f->eng->stream);
+                if (e != cudaSuccess) return cuda_status(e, ("conv layer " + f->net.layers[f->steps[i].layer].name).c_str());
+                continue;
+            }
+            nvisr_status st = run_step(f, f->steps[i], frames, calib);
+            if (st != NVISR_OK) return st;
+        }
+        return NVISR_OK;
+    }
     pa.nsrc = (int)idx.size();
     pa.ch_per_src = 3;
     pa.src_pitch = f->rpitch;
