@@ -31,6 +31,7 @@
 
 #include <mutex>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -673,6 +674,7 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
     auto ymap_of = [&](int pi) { return MULTI ? &probs[pi].ymap : &ymap; };
     auto rmap_of = [&](int pi) { return MULTI ? &probs[pi].rmap : &rmap; };
     auto width_of = [&](int pi) { return MULTI ? probs[pi].W : p.W; };
+    griddep_launch_dependents();  // the next layer may take each SM as this CTA leaves it
     if (threadIdx.x >= 64 && threadIdx.x < 64 + NPR)
         sbias[threadIdx.x - 64] = p.bias[PSB ? 4 * (threadIdx.x - 64) + slice : slice * NPR + threadIdx.x - 64];
     // 16-channel head reading the tuple's float32 frames (ntup > 0): warp 0 converts
@@ -706,6 +708,12 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
         grp_stop[1] = 0;
         *ready = 0;
         fence_mbarrier_init();
+        // the weights are written once at filter creation, so they load before the wait
+        // below, while the previous layer may still be running
+        mbar_arrive_expect_tx(wbar, 3 * WKX);
+        const uint8_t *wsrc = p.wts + (size_t)slice * 3 * WKX;
+        for (uint32_t off = 0; off < 3 * WKX; off += 32768u)
+            bulk_load(wsm + off, wsrc + off, min(32768u, 3 * WKX - off), wbar);
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, NCOLS);
@@ -715,6 +723,9 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // activations (inputs, residuals and the buffers this layer overwrites) belong to the
+    // previous kernels of the stream: nothing below touches them before they completed
+    griddep_wait();
 
     if ((warp == 0 || warp == 11) && tup) {
         // ---------------- producer (warps 0 and 11), tuple head: per input row, warp 0 lane 0
@@ -728,11 +739,6 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
         const int px0 = loader ? 0 : 64;
         using TI = typename Elem<IN_DT>::T;
         uint8_t *st32 = obuf + 2 * TILEB;
-        if (loader && lane == 0) {
-            mbar_arrive_expect_tx(wbar, 3 * WKX);
-            for (uint32_t off = 0; off < 3 * WKX; off += 32768u)
-                bulk_load(wsm + off, p.wts + off, min(32768u, 3 * WKX - off), wbar);
-        }
         int t_sidx = cta0, t_r = 0, t_ra = 0, t_rb = 0, t_x0 = 0, t_img = 0, t_pi = 0;
         bool t_live = false;
         // positions the load cursor on the next input row in the converting order
@@ -834,11 +840,8 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
         }
     } else if (warp == 0) {
         if (lane == 0) {
-            // ---------------- producer: weights, then one input row per stage
-            mbar_arrive_expect_tx(wbar, 3 * WKX);
-            const uint8_t *wsrc = p.wts + (size_t)slice * 3 * WKX;
-            for (uint32_t off = 0; off < 3 * WKX; off += 32768u)
-                bulk_load(wsm + off, wsrc + off, min(32768u, 3 * WKX - off), wbar);
+            // ---------------- producer: one input row per stage (the weights were issued
+            // in the prologue)
             int gin = 0;
             bool ok = true;
             for (int sidx = cta0; sidx < nstrips && ok; sidx += cstride) {
@@ -1727,6 +1730,28 @@ namespace {
 // the input-row ring, 2 output staging tiles (16-bit outputs) and, when the
 // layer adds a residual, 2 residual tiles (without one, their room goes to
 // deeper input prefetch).
+// Launches a row kernel with programmatic stream serialization, so that its CTAs may start
+// (barriers, TMEM, weights) while the stream's previous kernel drains; the kernel waits for
+// that kernel's completion before it touches activations.  Plain launch while the stream
+// is being captured into a graph.
+template <typename... P, typename... A>
+cudaError_t launch_dependent(void (*kern)(P...), int grid, int threads, int smem, cudaStream_t st, A &&...args) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+
 inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false, int cin = 64, bool f32out = false,
                        bool f8 = false, int extra = 0) {
     const uint32_t nchk = f8 ? 4u : 2u;  // 16-byte chunks per pixel of the no-swizzle forms
@@ -1762,8 +1787,7 @@ cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUte
     rp.bands = (p.H + rp.rps - 1) / rp.rps;
     int grid = rp.xtiles * rp.bands * p.nimg;
     if (grid > sms) grid = sms;
-    kern<<<grid, rows_threads(CIN, false), smem, st>>>(map, ymap, rmap, p, rp, nullptr, 0);
-    return cudaGetLastError();
+    return launch_dependent(kern, grid, rows_threads(CIN, false), smem, st, map, ymap, rmap, p, rp, nullptr, 0);
 }
 
 // Row kernel over output-channel slices (p.nslice of 64): CTAs per slice =
@@ -1797,8 +1821,7 @@ cudaError_t run_rows_sliced(const CUtensorMap &map, TcParams p, cudaStream_t st)
     rp.bands = (p.H + rp.rps - 1) / rp.rps;
     const int strips = rp.xtiles * rp.bands * p.nimg;
     const int grid = std::min(ctas, strips) * p.nslice;
-    kern<<<grid, rows_threads(CIN, false), smem, st>>>(map, map, map, p, rp, nullptr, 0);
-    return cudaGetLastError();
+    return launch_dependent(kern, grid, rows_threads(CIN, false), smem, st, map, map, map, p, rp, nullptr, 0);
 }
 
 template <int IN_DT, int OUT_DT, int CBO>

@@ -245,6 +245,8 @@ struct nvisr_filter {
     struct Rec { int kind; cudaEvent_t a, b; int n; };  // n launches of one kind, back to back
     std::vector<Rec> recs;
     bool prof_join = false;  // the next scope of the last record's kind may extend it
+    bool prof_hold = false;  // set by the step loops: the next launch is of the same kind
+    bool prof_open = false;  // the last record's end event is not recorded yet
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms[NVISR_K_COUNT] = {0};
     int64_t prof_n[NVISR_K_COUNT] = {0};
@@ -263,7 +265,15 @@ cudaEvent_t take_event(nvisr_filter *f) {
     return e;
 }
 
+// Records the end event a run of same-kind launches left pending.
+void prof_close(nvisr_filter *f) {
+    if (!f->prof_open) return;
+    cudaEventRecord(f->recs.back().b, f->eng->stream);
+    f->prof_open = false;
+}
+
 void flush_profile(nvisr_filter *f) {
+    prof_close(f);
     if (f->recs.empty()) return;
     cudaStreamSynchronize(f->eng->stream);
     for (auto &r : f->recs) {
@@ -280,38 +290,46 @@ void flush_profile(nvisr_filter *f) {
 }
 
 // Records CUDA events around the launches issued during its lifetime.  Back-to-back
-// scopes of one kind (a trunk's 20 body layers) share one event pair: the later
-// scope moves the record's end event, so the timed stream carries few events.
+// scopes of one kind (a trunk's 20 body layers) share one event pair: while the step
+// loop says the next launch is of the same kind (prof_hold) the end event waits, so no
+// event separates two such launches and a launch may overlap its predecessor's drain
+// (programmatic dependent launch).
 struct ProfScope {
     nvisr_filter *f;
     int kind;
     cudaEvent_t a = nullptr;
     bool join = false;
     ProfScope(nvisr_filter *f_, int kind_) : f(f_), kind(kind_) {
-        if (!f->prof) return;
+        if (!f->prof) {
+            prof_close(f);
+            return;
+        }
         join = f->prof_join && !f->recs.empty() && f->recs.back().kind == kind;
         if (!join) {
+            prof_close(f);
             a = take_event(f);
             cudaEventRecord(a, f->eng->stream);
         }
     }
     ~ProfScope() {
         if (join) {
-            cudaEventRecord(f->recs.back().b, f->eng->stream);
             f->recs.back().n += 1;
-            return;
+        } else {
+            if (!a) return;
+            f->recs.push_back({kind, a, take_event(f), 1});
+            f->prof_join = true;
         }
-        if (!a) return;
-        cudaEvent_t b = take_event(f);
-        cudaEventRecord(b, f->eng->stream);
-        f->recs.push_back({kind, a, b, 1});
-        f->prof_join = true;
-        if (f->recs.size() > 4096) flush_profile(f);
+        f->prof_open = true;
+        if (!f->prof_hold) prof_close(f);
+        if (f->recs.size() > 4096 && !f->prof_open) flush_profile(f);
     }
 };
 
 // Stream work outside a ProfScope: the next scope starts a record of its own.
-void prof_gap(nvisr_filter *f) { f->prof_join = false; }
+void prof_gap(nvisr_filter *f) {
+    prof_close(f);
+    f->prof_join = false;
+}
 
 float *ring_slot(nvisr_filter *f, int64_t frame) {
     return f->ring_base + (frame % f->ring) * f->slot_floats;
@@ -993,6 +1011,22 @@ void set_final_skip(nvisr_filter *f, const Step &s, const float *const *frames) 
 
 // Arguments of a conv step (no launch).  For the final layer it also sets the
 // filter's skip arguments (the frames whose upsampled mean requantise adds).
+// Profiling kind of a step's launch.
+int step_kind(const nvisr_filter *f, const Step &s) {
+    if (s.op == OP_DCN) return NVISR_K_DCN;
+    if (s.op == OP_PACK) return NVISR_K_PACK;
+    const NetLayer &L = f->net.layers[s.layer];
+    return s.out_t < 0 ? NVISR_K_CONV_TAIL
+                       : (s.src == SRC_TUPLE ? NVISR_K_CONV_HEAD
+                                             : (L.cin == 64 && L.cout == 64 && L.k == 3 && !L.ps ? NVISR_K_CONV_BODY
+                                                                                                  : NVISR_K_CONV_OTHER));
+}
+
+// Before step i of a forward pass: whether the next launch is of the same profiling kind.
+void hold_if_same_kind(nvisr_filter *f, size_t i) {
+    f->prof_hold = i + 1 < f->steps.size() && step_kind(f, f->steps[i + 1]) == step_kind(f, f->steps[i]);
+}
+
 ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, bool calib, int *kind) {
     const NetLayer &L = f->net.layers[s.layer];
     const Weights &Wt = s.widx >= 0 ? f->wvar[s.widx] : f->weights[s.layer];
@@ -1058,10 +1092,7 @@ ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, b
         a.nskip = 0;
         set_final_skip(f, s, frames);
     }
-    *kind = s.out_t < 0 ? NVISR_K_CONV_TAIL
-                        : (s.src == SRC_TUPLE ? NVISR_K_CONV_HEAD
-                                              : (L.cin == 64 && L.cout == 64 && L.k == 3 && !L.ps ? NVISR_K_CONV_BODY
-                                                                                                   : NVISR_K_CONV_OTHER));
+    *kind = step_kind(f, s);
     return a;
 }
 
@@ -1120,6 +1151,7 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
     }
     if (fused >= 0) {
         for (size_t i = 0; i < f->steps.size(); ++i) {
+            hold_if_same_kind(f, i);
             if ((int)i == fused) {
                 ProfScope ps(f, NVISR_K_CONV_HEAD);
                 cudaError_t e = launch_conv_tc(ha, f->eng->stream);
@@ -1129,6 +1161,7 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
             nvisr_status st = run_step(f, f->steps[i], frames, calib);
             if (st != NVISR_OK) return st;
         }
+        f->prof_hold = false;
         return NVISR_OK;
     }
     pa.nsrc = (int)idx.size();
@@ -1148,10 +1181,12 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
         e = launch_pack(pa, f->eng->stream);
     }
     if (e != cudaSuccess) return cuda_status(e, "pack");
-    for (const Step &s : f->steps) {
-        nvisr_status st = run_step(f, s, frames, calib);
+    for (size_t i = 0; i < f->steps.size(); ++i) {
+        hold_if_same_kind(f, i);
+        nvisr_status st = run_step(f, f->steps[i], frames, calib);
         if (st != NVISR_OK) return st;
     }
+    f->prof_hold = false;
     return NVISR_OK;
 }
 
@@ -1159,7 +1194,9 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
 nvisr_status forward_group(nvisr_filter *f, const std::vector<int64_t> &idx) {
     const float *frames[8];
     for (size_t k = 0; k < idx.size() && k < 8; ++k) frames[k] = ring_slot(f, idx[k]);
-    for (const Step &s : f->steps) {
+    for (size_t i = 0; i < f->steps.size(); ++i) {
+        const Step &s = f->steps[i];
+        hold_if_same_kind(f, i);
         if (s.op == OP_PACK) {
             const Tensor &t = f->tensors[s.out_t];
             PackArgs pa{};
@@ -1186,6 +1223,7 @@ nvisr_status forward_group(nvisr_filter *f, const std::vector<int64_t> &idx) {
         nvisr_status st = run_step(f, s, frames, false);
         if (st != NVISR_OK) return st;
     }
+    f->prof_hold = false;
     return NVISR_OK;
 }
 

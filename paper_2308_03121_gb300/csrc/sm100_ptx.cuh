@@ -199,6 +199,15 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// Programmatic dependent launch.  launch_dependents: this CTA allows the next kernel of
+// the stream (launched with programmatic stream serialization) to be scheduled once every
+// CTA of this grid has signalled or exited.  wait: blocks until the grids this one depends
+// on have completed and their memory is visible; a no-op for a normally launched kernel.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
 // core matrix = 8 rows x 16 bytes contiguous; lbo = byte distance between
 // core matrices along K, sbo = byte distance between 8-row groups along M/N.
