@@ -1732,13 +1732,10 @@ namespace {
 // deeper input prefetch).
 // Launches a row kernel with programmatic stream serialization, so that its CTAs may start
 // (barriers, TMEM, weights) while the stream's previous kernel drains; the kernel waits for
-// that kernel's completion before it touches activations.  Plain launch while the stream
-// is being captured into a graph.
+// that kernel's completion before it touches activations.  Under stream capture the
+// attribute becomes a programmatic edge of the graph.
 template <typename... P, typename... A>
 cudaError_t launch_dependent(void (*kern)(P...), int grid, int threads, int smem, cudaStream_t st, A &&...args) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaError_t e = cudaStreamIsCapturing(st, &cs);
-    if (e != cudaSuccess) return e;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
@@ -1748,7 +1745,7 @@ cudaError_t launch_dependent(void (*kern)(P...), int grid, int threads, int smem
     cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = st;
     cfg.attrs = at;
-    cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
 }
 
@@ -1835,8 +1832,7 @@ cudaError_t run_rows_multi(const CUtensorMap &dummy, TcParams p, const RowProble
     if (e != cudaSuccess) return e;
     RowPlan rp{};
     const int grid = std::min(total, device_sm_count());
-    kern<<<grid, ROWS_THREADS, smem, st>>>(dummy, dummy, dummy, p, rp, dev_tab, n);
-    return cudaGetLastError();
+    return launch_dependent(kern, grid, ROWS_THREADS, smem, st, dummy, dummy, dummy, p, rp, dev_tab, n);
 }
 
 // The row kernel's three tensor maps for one image set (x: 130-pixel row boxes
