@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "nvisr.h"
 
@@ -224,5 +225,25 @@ cudaError_t launch_dcn_tc(const DcnArgs &a, cudaStream_t st);
 cudaError_t launch_dcn_relayout8(const void *x, int cpad, int H, int W, int x_cpc, void *y, cudaStream_t st);
 
 int device_sm_count();
+
+// Launches a tensor-core kernel with programmatic stream serialization, so that its CTAs may
+// start (barriers, TMEM, weights) while the stream's previous kernel drains; the kernel waits
+// (griddepcontrol.wait) for that kernel's completion before it touches activations.  Under
+// stream capture the attribute becomes a programmatic edge of the graph.  Such a kernel reads
+// nothing before that wait but data no kernel writes (weights and biases uploaded by copies).
+template <typename... P, typename... A>
+cudaError_t launch_dependent(void (*kern)(P...), int grid, int threads, int smem, cudaStream_t st, A &&...args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 }  // namespace nvisr

@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    griddep_launch_dependents();  // as in the row kernel: after the TMEM allocation
+    griddep_wait();               // activations only after the previous kernels completed
 
     if (warp == 0) {
         if (lane == 0) {
@@ -674,7 +676,6 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
     auto ymap_of = [&](int pi) { return MULTI ? &probs[pi].ymap : &ymap; };
     auto rmap_of = [&](int pi) { return MULTI ? &probs[pi].rmap : &rmap; };
     auto width_of = [&](int pi) { return MULTI ? probs[pi].W : p.W; };
-    griddep_launch_dependents();  // the next layer may take each SM as this CTA leaves it
     if (threadIdx.x >= 64 && threadIdx.x < 64 + NPR)
         sbias[threadIdx.x - 64] = p.bias[PSB ? 4 * (threadIdx.x - 64) + slice : slice * NPR + threadIdx.x - 64];
     // 16-channel head reading the tuple's float32 frames (ntup > 0): warp 0 converts
@@ -723,8 +724,11 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    // activations (inputs, residuals and the buffers this layer overwrites) belong to the
-    // previous kernels of the stream: nothing below touches them before they completed
+    // The next layer may now be scheduled, taking each SM as this CTA leaves it (signalled
+    // after the TMEM allocation, so a CTA of the next layer never holds TMEM this one waits
+    // for).  Activations (inputs, residuals and the buffers this layer overwrites) belong to
+    // the previous kernels of the stream: nothing below touches them before they completed.
+    griddep_launch_dependents();
     griddep_wait();
 
     if ((warp == 0 || warp == 11) && tup) {
@@ -1546,8 +1550,7 @@ cudaError_t run(const CUtensorMap &map, TcParams p, cudaStream_t st) {
     int per_slice = sms / p.nslice;
     if (per_slice < 1) per_slice = 1;
     if (per_slice > tiles) per_slice = tiles;
-    kern<<<per_slice * p.nslice, NTHREADS, smem, st>>>(map, p);
-    return cudaGetLastError();
+    return launch_dependent(kern, per_slice * p.nslice, NTHREADS, smem, st, map, p);
 }
 
 using Runner = cudaError_t (*)(const CUtensorMap &, TcParams, cudaStream_t);
@@ -1730,25 +1733,6 @@ namespace {
 // the input-row ring, 2 output staging tiles (16-bit outputs) and, when the
 // layer adds a residual, 2 residual tiles (without one, their room goes to
 // deeper input prefetch).
-// Launches a row kernel with programmatic stream serialization, so that its CTAs may start
-// (barriers, TMEM, weights) while the stream's previous kernel drains; the kernel waits for
-// that kernel's completion before it touches activations.  Under stream capture the
-// attribute becomes a programmatic edge of the graph.
-template <typename... P, typename... A>
-cudaError_t launch_dependent(void (*kern)(P...), int grid, int threads, int smem, cudaStream_t st, A &&...args) {
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = (size_t)smem;
-    cfg.stream = st;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
-}
-
 inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false, int cin = 64, bool f32out = false,
                        bool f8 = false, int extra = 0) {
     const uint32_t nchk = f8 ? 4u : 2u;  // 16-byte chunks per pixel of the no-swizzle forms

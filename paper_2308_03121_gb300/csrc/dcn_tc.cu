@@ -135,6 +135,10 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // the next kernel may be scheduled once every CTA got here (after the TMEM allocation);
+    // the features and offsets are read only after the previous kernels completed
+    griddep_launch_dependents();
+    griddep_wait();
 
     if (warp < NGATHER / 32) {
         // ------------------------------------------------ gather producers
@@ -400,8 +404,7 @@ cudaError_t run(const DcnArgs &a, cudaStream_t st) {
     const int tiles = ((a.W + TM - 1) / TM) * a.H;
     int grid = device_sm_count();
     if (grid > tiles) grid = tiles;
-    kern<<<grid, NT, smem, st>>>(a, stages);
-    return cudaGetLastError();
+    return launch_dependent(kern, grid, NT, smem, st, a, stages);
 }
 
 // One thread per (pixel, 8-channel chunk), chunk fastest: a warp reads four
