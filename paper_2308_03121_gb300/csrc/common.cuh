@@ -232,13 +232,13 @@ int device_sm_count();
 // stream capture the attribute becomes a programmatic edge of the graph.  Such a kernel reads
 // nothing before that wait but data no kernel writes (weights and biases uploaded by copies).
 template <typename... P, typename... A>
-cudaError_t launch_dependent(void (*kern)(P...), int grid, int threads, int smem, cudaStream_t st, A &&...args) {
+cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 threads, int smem, cudaStream_t st, A &&...args) {
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)threads);
+    cfg.gridDim = grid;
+    cfg.blockDim = threads;
     cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = st;
     cfg.attrs = at;

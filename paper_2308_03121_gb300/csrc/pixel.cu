@@ -18,6 +18,7 @@
 // consecutive pixels (ingest) or a 2x8 luma block (requantise 4:2:0) with
 // vector loads/stores along rows.
 #include "common.cuh"
+#include "sm100_ptx.cuh"
 
 namespace nvisr {
 
@@ -168,6 +169,9 @@ __global__ void __launch_bounds__(128) ingest420_kernel(
     const uint8_t *__restrict__ yp, int64_t py, const uint8_t *__restrict__ up, int64_t pu,
     const uint8_t *__restrict__ vp, int64_t pv, int H, int W, int loc, RangeConst rc,
     float *__restrict__ out, int64_t pitch) {
+    // launched as a dependent: the ring slot may still be read by the stream's previous kernel
+    griddep_wait();
+    griddep_launch_dependents();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     const int x0 = q * 8;
@@ -401,6 +405,9 @@ __global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict
                                                          int H, int W, int loc, RangeConst rc,
                                                          uint8_t *yp, int64_t py, uint8_t *up,
                                                          int64_t pu, uint8_t *vp, int64_t pv, const __grid_constant__ SkipArgs sk) {
+    // launched as a dependent: the network output comes from the stream's previous kernel
+    griddep_wait();
+    griddep_launch_dependents();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     const int xb = q * 8;
@@ -753,14 +760,12 @@ cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, cons
         dim3 blk(128);
         dim3 grd((f.width + 8 * 128 - 1) / (8 * 128), (f.height + 1) / 2, 2);
         if (f.bit_depth <= 8)
-            ingest420_kernel<uint8_t><<<grd, blk, 0, st>>>((const uint8_t *)y, py, (const uint8_t *)u, pu,
-                                                          (const uint8_t *)v, pv, f.height, f.width, f.chroma_loc,
-                                                          rc, out, out_pitch);
-        else
-            ingest420_kernel<uint16_t><<<grd, blk, 0, st>>>((const uint8_t *)y, py, (const uint8_t *)u, pu,
-                                                           (const uint8_t *)v, pv, f.height, f.width, f.chroma_loc,
-                                                           rc, out, out_pitch);
-        return cudaGetLastError();
+            return launch_dependent(ingest420_kernel<uint8_t>, grd, blk, 0, st, (const uint8_t *)y, py,
+                                    (const uint8_t *)u, pu, (const uint8_t *)v, pv, f.height, f.width, f.chroma_loc,
+                                    rc, out, out_pitch);
+        return launch_dependent(ingest420_kernel<uint16_t>, grd, blk, 0, st, (const uint8_t *)y, py,
+                                (const uint8_t *)u, pu, (const uint8_t *)v, pv, f.height, f.width, f.chroma_loc, rc,
+                                out, out_pitch);
     }
     dim3 block(64);
     dim3 grid((f.width / 4 + 1 + block.x - 1) / block.x, f.height);
@@ -784,14 +789,15 @@ cudaError_t launch_requant(const nvisr_format &f, const float *in, int64_t in_pi
     if (skip) sk = *skip;
     dim3 block(64);
     if (f.subsampling == NVISR_SUB_420) {
+        cudaError_t e = cudaSuccess;
         block = dim3(128);
         dim3 grid((f.width + 8 * 128 - 1) / (8 * 128), f.height / 2);
         const bool skip2 = sk.n == 1 && sk.mode == 2 && sk.scale == 2 && sk.h * 2 == f.height && sk.w * 2 == f.width;
         const bool skip4 = (sk.n == 1 || sk.n == 2) && sk.mode == 2 && sk.scale == 4 && sk.h * 4 == f.height &&
                            sk.w * 4 == f.width;
-#define NVISR_RQ(S_, K_, N_)                                                                                     \
-    requant420_kernel<S_, K_, N_><<<grid, block, 0, st>>>(in, in_pitch, f.height, f.width, f.chroma_loc, rc,  \
-                                                          (uint8_t *)y, py, (uint8_t *)u, pu, (uint8_t *)v, pv, sk)
+#define NVISR_RQ(S_, K_, N_)                                                                                 \
+    e = launch_dependent(requant420_kernel<S_, K_, N_>, grid, block, 0, st, in, in_pitch, f.height, f.width, \
+                         f.chroma_loc, rc, (uint8_t *)y, py, (uint8_t *)u, pu, (uint8_t *)v, pv, sk)
 #define NVISR_RQ_ALL(S_)                  \
     if (skip2) NVISR_RQ(S_, 2, 1);        \
     else if (skip4 && sk.n == 1) NVISR_RQ(S_, 4, 1); \
@@ -804,6 +810,7 @@ cudaError_t launch_requant(const nvisr_format &f, const float *in, int64_t in_pi
         }
 #undef NVISR_RQ_ALL
 #undef NVISR_RQ
+        return e;
     } else {
         dim3 grid((f.width / 4 + 1 + block.x - 1) / block.x, f.height);
         if (f.bit_depth <= 8)
