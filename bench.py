@@ -45,9 +45,9 @@ H2D_BYTES = W * H * 2 + 2 * (W // 2) * (H // 2) * 2
 D2H_BYTES = (W * S) * (H * S) * 2 + 2 * (W * S // 2) * (H * S // 2) * 2
 NFRAMES = 12                                   # distinct resident input frames, cycled
 # DRAM bytes per conv_body launch (mean of a launch with and one without residual:
-# 762.0 MB and 480.2 MB read + written) from an ncu capture of the current kernel
+# 761.0 MB and 482.7 MB read + written) from an ncu capture of the current kernel
 # (profiles/conv_rows_bf16_1080p.md)
-CONV_BODY_TRAFFIC = 621.1e6
+CONV_BODY_TRAFFIC = 621.9e6
 WORKLOAD = ("1080p->4K 2x SR: sliding window T=5, conv 15->64, 10 residual blocks of 64 ch, conv 64->12, "
             "PixelShuffle(2), bilinear skip; 10-bit 4:2:0 limited BT.709 in and out")
 DATA = "synthetic: seeded textured 10-bit 4:2:0 frames with global 0-4 px translation; random-init He-normal weights"
