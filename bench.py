@@ -13,6 +13,9 @@ no L2 flush is needed between steps.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead (the reference arm: there is no reference implementation to run).
+Secondary workloads report under their own keys: ``batched`` (24 streams),
+``config3`` (deformable space-time SR), ``modes`` (same-size and vertical-2x
+scale modes) and ``serving``.
 """
 from __future__ import annotations
 
@@ -208,6 +211,57 @@ def measure(nv, prec, steps, warmup, dev_frames, local, world, clocks=None):
     ms_max = allmax(ms, world)
     eng.close()
     return ms_max, prof, ck
+
+
+def measure_modes(nv, steps, warmup, dev_frames, local):
+    """The scale modes besides 2 x 2 SR (Section 3.2's horizontal and vertical scale): a
+    same-size enhancement (denoise, 1 x 1) and a vertical 2x (deinterlace, 1 x 2) network
+    with the config-2 trunk (T=5, 15->64, 10 residual blocks of 64), BF16, on the 1080p
+    10-bit 4:2:0 frames; device-resident input and output, CUDA events on the engine
+    stream around the timed push/pull loop."""
+    import torch
+    res = {}
+    for name, (sx, sy) in (("denoise_1x1", (1, 1)), ("deinterlace_1x2", (1, 2))):
+        text, blob = synth.net_tuple(synth.BASE_SEED + 2, frames=5, channels=64, nres=10, scale=(sx, sy))
+        eng = nv.Engine(device=local)
+        flt = eng.filter(text, blob, nv.fmt(W, H, 10), nv.fmt(W * sx, H * sy, 10), "bf16", (sx, sy))
+        dev = f"cuda:{local}"
+        out = (torch.empty((H * sy, W * sx), dtype=torch.int16, device=dev),
+               torch.empty((H * sy // 2, W * sx // 2), dtype=torch.int16, device=dev),
+               torch.empty((H * sy // 2, W * sx // 2), dtype=torch.int16, device=dev))
+        k = [0]
+
+        def push():
+            assert flt.push(dev_frames[k[0] % NFRAMES]) == nv.Status.OK
+            k[0] += 1
+
+        while flt.ready() == 0:
+            push()
+        pulled = 0
+        while k[0] - pulled > 4:
+            assert flt.pull(out)[0] == nv.Status.OK
+            pulled += 1
+
+        def step():
+            push()
+            assert flt.pull(out)[0] == nv.Status.OK
+
+        for _ in range(warmup):
+            step()
+        stream = torch.cuda.ExternalStream(eng.stream)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            step()
+        t1.record(stream)
+        t1.synchronize()
+        ms = t0.elapsed_time(t1)
+        eng.close()
+        res[name] = {"metric": "output Mpix/s", "value": steps * W * sx * H * sy / (ms * 1e-3) / 1e6,
+                     "ms_per_frame": ms / steps, "steps": steps, "input": f"{W}x{H}",
+                     "output": f"{W * sx}x{H * sy}"}
+    return res
 
 
 def measure_config3(nv, steps, warmup, local, prec="bf16"):
@@ -519,6 +573,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=12, help="steps of the 24-stream batched run (0 = skip)")
     ap.add_argument("--config3-steps", type=int, default=20, help="runs of the deformable ST-SR network (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving-loop window (0 = skip)")
+    ap.add_argument("--modes-steps", type=int, default=30, help="frames of each 1x1 / 1x2 scale mode (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=6.0, help="clip arrivals per second")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
@@ -565,6 +620,12 @@ def main():
             config3 = measure_config3(nv, args.config3_steps, 3, local)
         except Exception as e:  # the secondary workload must not hide the headline
             errors["config3"] = repr(e)
+    modes = None
+    if args.modes_steps > 0:
+        try:
+            modes = measure_modes(nv, args.modes_steps, 3, dev_frames, local)
+        except Exception as e:  # the secondary workload must not hide the headline
+            errors["modes"] = repr(e)
     serving = None
     if args.serve_seconds > 0:
         try:
@@ -622,6 +683,7 @@ def main():
         "precisions": by_prec,
         "batched": batched,
         "config3": config3,
+        "modes": modes,
         "serving": serving,
         "hbm_peak_gbs": hbm,
     }

@@ -80,7 +80,7 @@ def run_filter(frames, flags, net_text, blob, in_fmt, out_fmt, outputs=None, kee
         return cache[i]
 
     h, w = frames[0]["Y"].shape
-    oh, ow = h * net.scale, w * net.scale
+    oh, ow = h * net.scale_y, w * net.scale
     want = None if outputs is None else set(outputs)
     results = []
 

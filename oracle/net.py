@@ -13,9 +13,13 @@ definitions:
   independent implementation used to pin the first).
 * LeakyReLU(0.1): x >= 0 ? x : 0.1 x.
 * residual add after the activation (no activation after the add).
-* PixelShuffle(r): out[c, r*h+i, r*w+j] = in[c*r*r + i*r + j, h, w].
+* PixelShuffle(r): out[c, r*h+i, r*w+j] = in[c*r*r + i*r + j, h, w]; with separate
+  row / column factors (ry, rx): out[c, ry*h+i, rx*w+j] = in[c*ry*rx + i*rx + j, h, w]
+  (the final layer of a network whose horizontal and vertical scales differ,
+  Section 3.2; ry = rx gives PyTorch's order).
 * skip: upsample of the input frame in the network domain, 'bilinear'
-  (align_corners = False: src = (dst + 0.5)/s - 0.5, edge clamp) or 'nearest'.
+  (align_corners = False per axis: src = (dst + 0.5)/s - 0.5 with that axis's
+  scale, edge clamp) or 'nearest'.
 * DCN v2: see oracle_conv.c; the head's output channels [0, 18G) are offsets
   (dy, dx interleaved per (group, tap)), [18G, 27G) are mask logits and the
   mask is their logistic sigmoid.
@@ -115,35 +119,41 @@ def sigmoid(x):
     return 1.0 / (1.0 + np.exp(-np.asarray(x, np.float64)))
 
 
-def pixel_shuffle(x, r: int):
-    """[C*r*r][H][W] -> [C][H*r][W*r], PyTorch channel order."""
+def pixel_shuffle(x, r: int, rx: int | None = None):
+    """[C*r*rx][H][W] -> [C][H*r][W*rx]: PyTorch channel order for rx = r (the default);
+    row factor r, column factor rx otherwise."""
+    ry = r
+    rx = r if rx is None else rx
     crr, h, w = x.shape
-    c = crr // (r * r)
-    return x.reshape(c, r, r, h, w).transpose(0, 3, 1, 4, 2).reshape(c, h * r, w * r)
+    c = crr // (ry * rx)
+    return x.reshape(c, ry, rx, h, w).transpose(0, 3, 1, 4, 2).reshape(c, h * ry, w * rx)
 
 
-def upsample_bilinear(x, s: int):
-    """align_corners=False bilinear upsample by integer s with edge clamp. x [C][H][W]."""
+def upsample_bilinear(x, s: int, sy: int | None = None):
+    """align_corners=False bilinear upsample with edge clamp, x [C][H][W]: by integer s
+    along both axes, or s along columns and sy along rows."""
     x = np.asarray(x, np.float64)
     _, h, w = x.shape
+    sy = s if sy is None else sy
 
-    def coords(n):
-        src = (np.arange(n * s) + 0.5) / s - 0.5
+    def coords(n, f):
+        src = (np.arange(n * f) + 0.5) / f - 0.5
         src = np.maximum(src, 0.0)
         i0 = np.floor(src).astype(int)
         i0 = np.minimum(i0, n - 1)
         i1 = np.minimum(i0 + 1, n - 1)
         return i0, i1, src - i0
 
-    y0, y1, fy = coords(h)
-    x0, x1, fx = coords(w)
+    y0, y1, fy = coords(h, sy)
+    x0, x1, fx = coords(w, s)
     top = x[:, y0][:, :, x0] * (1 - fx) + x[:, y0][:, :, x1] * fx
     bot = x[:, y1][:, :, x0] * (1 - fx) + x[:, y1][:, :, x1] * fx
     return top * (1 - fy)[None, :, None] + bot * fy[None, :, None]
 
 
-def upsample_nearest(x, s: int):
-    return np.repeat(np.repeat(np.asarray(x, np.float64), s, axis=1), s, axis=2)
+def upsample_nearest(x, s: int, sy: int | None = None):
+    sy = s if sy is None else sy
+    return np.repeat(np.repeat(np.asarray(x, np.float64), sy, axis=1), s, axis=2)
 
 
 # ---------------------------------------------------------------- description
@@ -165,7 +175,8 @@ class Net:
         blob = np.asarray(blob, np.float32).astype(np.float64)
         self.family = "tuple"
         self.frames = 1
-        self.scale = 1
+        self.scale = 1    # horizontal scale
+        self.scale_y = 1  # vertical scale
         self.skip = "none"
         self.flags = set()
         self.domain = "rgb"
@@ -185,8 +196,9 @@ class Net:
                 self.family = tok[1]
             elif key == "frames":
                 self.frames = int(tok[1])
-            elif key == "scale":
+            elif key == "scale":  # "scale s", or "scale sx sy" (horizontal, vertical)
                 self.scale = int(tok[1])
+                self.scale_y = int(tok[2]) if len(tok) > 2 else self.scale
             elif key == "skip":
                 self.skip = tok[1]
             elif key == "align":
@@ -197,7 +209,7 @@ class Net:
                 self.domain = tok[1]
             elif key in ("conv", "dcn"):
                 attrs = dict(t.split("=", 1) for t in tok[2:])
-                for k in ("cin", "cout", "k", "groups", "ps"):
+                for k in ("cin", "cout", "k", "groups", "ps", "psx", "psy"):
                     if k in attrs:
                         attrs[k] = int(attrs[k])
                 if key == "dcn":
@@ -228,10 +240,10 @@ class Net:
 
     def _skip(self, frame_rgb):
         if self.skip == "bilinear":
-            return upsample_bilinear(frame_rgb, self.scale)
+            return upsample_bilinear(frame_rgb, self.scale, self.scale_y)
         if self.skip == "nearest":
-            return upsample_nearest(frame_rgb, self.scale)
-        return np.zeros((3, frame_rgb.shape[1] * self.scale, frame_rgb.shape[2] * self.scale))
+            return upsample_nearest(frame_rgb, self.scale, self.scale_y)
+        return np.zeros((3, frame_rgb.shape[1] * self.scale_y, frame_rgb.shape[2] * self.scale))
 
     def forward(self, frames_rgb, window=None, keep=False):
         """Run the graph on a list of float64 RGB frames [3][H][W].
@@ -263,6 +275,8 @@ class Net:
                 y = y + env[layer.get("add")]
             if layer.get("ps"):
                 y = pixel_shuffle(y, layer.get("ps"))
+            elif layer.get("psx", 1) != 1 or layer.get("psy", 1) != 1:
+                y = pixel_shuffle(y, layer.get("psy", 1), layer.get("psx", 1))
             env[layer.name] = y
         outs = []
         for name, skip in self.outputs:

@@ -407,7 +407,8 @@ class Server:
     def submit(self, net_text, blob, in_fmt, out_fmt, precision="bf16", scale=2, calib_frames=0):
         blob = np.ascontiguousarray(np.asarray(blob, np.float32))
         text = net_text.encode()
-        d = FilterDesc(text, blob.ctypes.data_as(_F32P), blob.size, in_fmt, out_fmt, scale, scale,
+        sw, sh = scale if isinstance(scale, tuple) else (scale, scale)  # (horizontal, vertical)
+        d = FilterDesc(text, blob.ctypes.data_as(_F32P), blob.size, in_fmt, out_fmt, sw, sh,
                        PREC[precision] if isinstance(precision, str) else precision, calib_frames)
         cid = ctypes.c_int64(0)
         _check(_LIB.nvisr_server_submit(self.h, ctypes.byref(d), ctypes.byref(cid)), "nvisr_server_submit")
@@ -469,8 +470,9 @@ class Filter:
         self.engine = engine
         self._blob = np.ascontiguousarray(np.asarray(blob, np.float32))
         self._text = net_text.encode()
+        sw, sh = scale if isinstance(scale, tuple) else (scale, scale)  # (horizontal, vertical)
         d = FilterDesc(self._text, self._blob.ctypes.data_as(_F32P), self._blob.size, in_fmt, out_fmt,
-                       scale, scale, PREC[precision] if isinstance(precision, str) else precision, calib_frames)
+                       sw, sh, PREC[precision] if isinstance(precision, str) else precision, calib_frames)
         h = ctypes.c_void_p()
         _check(_LIB.nvisr_filter_create(engine.h, ctypes.byref(d), ctypes.byref(h)), "nvisr_filter_create")
         self.h = h

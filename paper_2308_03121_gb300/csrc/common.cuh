@@ -60,7 +60,14 @@ struct SkipArgs {
     int n;               // 0 = no skip
     int64_t pitch, plane;
     int h, w, scale, mode;
+    int scale_y;         // vertical scale when it differs from scale (0 = scale)
 };
+
+// A final layer's float32 output, blocked [cpad/4][H][W][4], PixelShuffled by (ry, rx) into
+// planar [C / (ry*rx)][H*ry][dst_pitch]: dst[c][ry*y + i][rx*x + j] = src channel
+// c*ry*rx + i*rx + j at (y, x).  C = 3 * ry * rx.
+cudaError_t launch_shuffle_planar(const float *src, int H, int W, int ry, int rx, float *dst, int64_t dst_pitch,
+                                  cudaStream_t st);
 
 // requantise: float32 planar R'G'B' (+ skip) -> integer planes.
 cudaError_t launch_requant(const nvisr_format &fmt, const float *in, int64_t in_pitch, void *y,

@@ -1568,7 +1568,7 @@ struct Variant {
     NVISR_V16(I, 64, 3, 1, 0, 128, 128), NVISR_V16(I, 16, 3, 1, 1, 128, 16),                             \
     NVISR_V16(I, 64, 1, 1, 0, 128, 128), NVISR_V16(I, 64, 3, 1, 2, 128, 128),                           \
     NVISR_V16(I, 32, 3, 1, 0, 128, 16), NVISR_V16(I, 16, 3, 1, 0, 128, 16),                              \
-    NVISR_V(I, DT_F32, 32, 3, 1, 0, 128, 16),                                                           \
+    NVISR_V(I, DT_F32, 32, 3, 1, 0, 128, 16), NVISR_V(I, DT_F32, 16, 3, 1, 0, 128, 16),                 \
     /* 16-byte-chunk inputs (16 / 32 channels): heads, extract convs, narrow nets */                     \
     NVISR_V16(I, 64, 3, 2, 0, 16, 128), NVISR_V16(I, 64, 3, 4, 0, 16, 128),                              \
     NVISR_V16(I, 32, 3, 2, 0, 16, 16), NVISR_V16(I, 32, 3, 4, 0, 16, 16),                                \

@@ -140,6 +140,10 @@ struct Step {
     int out_index = -1;  // final output number
     bool fp8 = false;
     bool out_f8_only = false;
+    // final output without the 2x2 shuffle (scale 1, or 1 x 2 / 2 x 1): the conv writes
+    // float32 into final_f32, then a shuffle kernel writes the planar output
+    bool plain = false;
+    int psy = 2, psx = 2;
 };
 
 bool fmt_ok(const nvisr_format &f) {
@@ -209,6 +213,8 @@ struct nvisr_filter {
     std::vector<Step> steps;
     int pack_t = -1;               // tensor id of the packed tuple
     int tuple_head = -1;           // the step that alone reads the packed tuple (-1: several or none)
+    bool plain_final = false;      // some output uses a plain final layer (Step::plain)
+    float *final_f32 = nullptr;    // its float32 output, blocked [4][H][W][4]
     float *out_rgb[8] = {};   // planar float32 residuals [3][sH][opitch], one per output of a run
     SkipArgs skip[8] = {};    // skip path of each output slot (added by requantise)
     // group family (Section 3.1): n frames per run (+1 with Extra frame), run_out outputs per run
@@ -657,13 +663,24 @@ nvisr_status build_plan(nvisr_filter *f) {
         if (!L.add.empty()) st.add_t = tensor_of.at(L.add);
         st.fp8 = layer_is_fp8(f, L);
         if (out_index.count(L.name)) {
-            if (!L.ps || L.cout != 12 || src.H != H) return fail(NVISR_UNSUPPORTED_FORMAT, "output layer must be conv ->12 ch + PixelShuffle(2) at input size");
-            if (net.scale != 2) return fail(NVISR_UNSUPPORTED_FORMAT, "tuple networks: scale 2 only");
+            // the output layer: 3 * psy * psx channels at input size, shuffled by the scale
+            // (Section 3.2: horizontal and vertical scale; 2 x 2 super-resolution, 1 x 1
+            // enhancement / denoise, 1 x 2 deinterlace)
+            if (src.H != H || L.k != 3) return fail(NVISR_UNSUPPORTED_FORMAT, "output layer must be a 3x3 conv at input size");
+            if (L.psx != net.scale || L.psy != net.scale_y)
+                return fail(NVISR_UNSUPPORTED_FORMAT, "output layer's PixelShuffle must equal the network scale");
+            if (L.cout != 3 * L.psx * L.psy)
+                return fail(NVISR_UNSUPPORTED_FORMAT, "output layer must give 3 channels after its PixelShuffle");
             st.out_t = -1;
             st.out_index = out_index[L.name];
             st.skip_frames = {(net.frames - 1) / 2};
+            st.psy = L.psy;
+            st.psx = L.psx;
+            st.plain = !(L.psy == 2 && L.psx == 2);
+            f->plain_final = f->plain_final || st.plain;
         } else {
-            if (L.ps) return fail(NVISR_UNSUPPORTED_FORMAT, "inner PixelShuffle in a tuple network");
+            if (L.ps || L.psx != 1 || L.psy != 1)
+                return fail(NVISR_UNSUPPORTED_FORMAT, "inner PixelShuffle in a tuple network");
             Tensor t;
             t.C = L.cout;
             t.cpad = round_up(L.cout, 16);
@@ -788,6 +805,9 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
     f->wvar.clear();
     f->pack_t = -1;
     if (f->precision == NVISR_PREC_FP8) return fail(NVISR_UNSUPPORTED_FORMAT, "group networks run in FP32/BF16/FP16");
+    if (net.scale != net.scale_y) return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: one scale for both axes");
+    for (const NetLayer &L : net.layers)
+        if (L.psx != L.psy) return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: PixelShuffle(2) only");
     f->grp_n = net.frames - (net.extra ? 1 : 0);
     f->grp_need = net.frames;
     f->grp_interp = net.interp;
@@ -1006,11 +1026,10 @@ void set_final_skip(nvisr_filter *f, const Step &s, const float *const *frames) 
     k.h = f->in_fmt.height;
     k.w = f->in_fmt.width;
     k.scale = f->net.scale;
+    k.scale_y = f->net.scale_y;
     k.mode = f->net.skip;
 }
 
-// Arguments of a conv step (no launch).  For the final layer it also sets the
-// filter's skip arguments (the frames whose upsampled mean requantise adds).
 // Profiling kind of a step's launch.
 int step_kind(const nvisr_filter *f, const Step &s) {
     if (s.op == OP_DCN) return NVISR_K_DCN;
@@ -1027,6 +1046,8 @@ void hold_if_same_kind(nvisr_filter *f, size_t i) {
     f->prof_hold = i + 1 < f->steps.size() && step_kind(f, f->steps[i + 1]) == step_kind(f, f->steps[i]);
 }
 
+// Arguments of a conv step (no launch).  For the final layer it also sets the
+// filter's skip arguments (the frames whose upsampled mean requantise adds).
 ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, bool calib, int *kind) {
     const NetLayer &L = f->net.layers[s.layer];
     const Weights &Wt = s.widx >= 0 ? f->wvar[s.widx] : f->weights[s.layer];
@@ -1082,6 +1103,14 @@ ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, b
             }
         }
         if (calib && o.amax_slot >= 0) a.amax = f->amax + o.amax_slot;
+    } else if (s.plain) {
+        // a last layer without the 2 x 2 shuffle: float32 output, shuffled into planar
+        // float32 by its own kernel (run_step); the skip is added by requantise
+        a.y = f->final_f32;
+        a.out_dt = DT_F32;
+        a.out_cpc = 4;
+        a.ps = 0;
+        set_final_skip(f, s, frames);
     } else {
         // the network's last layer: PixelShuffle(2) residual into planar float32; the
         // skip (upsampled input frames) is added by the requantise kernel
@@ -1127,6 +1156,10 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
     ProfScope ps(f, kind);
     cudaError_t e = f->tc ? launch_conv_tc(a, st) : launch_conv_simt(a, st);
     if (e != cudaSuccess) return cuda_status(e, ("conv layer " + L.name).c_str());
+    if (s.plain) {
+        e = launch_shuffle_planar(f->final_f32, a.H, a.W, s.psy, s.psx, f->out_rgb[s.out_index], f->opitch, st);
+        if (e != cudaSuccess) return cuda_status(e, ("output shuffle of " + L.name).c_str());
+    }
     return NVISR_OK;
 }
 
@@ -1358,7 +1391,7 @@ void free_plan(nvisr_batch::Plan &p) {
 
 // Batched tuple members must share the weight blob; launches use member 0's weights.
 bool batchable(const nvisr_filter *f) {
-    return f->net.family == "tuple" && f->tc && f->precision != NVISR_PREC_FP8;
+    return f->net.family == "tuple" && f->tc && f->precision != NVISR_PREC_FP8 && !f->plain_final;
 }
 
 // Conv arguments of step si for a participant, with the (identical) weights of member 0.
@@ -1596,9 +1629,9 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
     std::string err;
     if (!parse_netdesc(d->network_text, d->weights_count, &f->net, &err)) return fail(NVISR_BAD_NETWORK, err);
     const NetDesc &net = f->net;
-    if (d->scale_w != net.scale || d->scale_h != net.scale)
+    if (d->scale_w != net.scale || d->scale_h != net.scale_y)
         return fail(NVISR_INVALID_ARG, "scale does not match the network description");
-    if (d->out_fmt.width != d->in_fmt.width * net.scale || d->out_fmt.height != d->in_fmt.height * net.scale)
+    if (d->out_fmt.width != d->in_fmt.width * net.scale || d->out_fmt.height != d->in_fmt.height * net.scale_y)
         return fail(NVISR_INVALID_ARG, "output size must be scale x input size");
     if (net.align != 1) return fail(NVISR_UNSUPPORTED_FORMAT, "network stride alignment > 1 is not supported");
     if (net.family == "tuple" && (net.frames % 2 == 0 || net.frames > 8))
@@ -1653,13 +1686,17 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
             return cleanup(fail(NVISR_CUDA_ERROR, "cudaEventCreate failed"));
     f->opitch = round_up64((int64_t)W * net.scale, 4);
     for (int k = 0; k < f->run_out; ++k) {
-        if ((s = dalloc(e, sizeof(float) * 3 * f->opitch * H * net.scale, f->owned, &p)) != NVISR_OK)
+        if ((s = dalloc(e, sizeof(float) * 3 * f->opitch * H * net.scale_y, f->owned, &p)) != NVISR_OK)
             return cleanup(s);
         f->out_rgb[k] = (float *)p;
     }
     if ((s = prepare_weights(f.get(), d->weights)) != NVISR_OK) return cleanup(s);
     if ((s = (net.family == "group" ? build_plan_group(f.get(), d->weights) : build_plan(f.get()))) != NVISR_OK)
         return cleanup(s);
+    if (f->plain_final) {
+        if ((s = dalloc(e, sizeof(float) * 16 * (size_t)H * W, f->owned, &p)) != NVISR_OK) return cleanup(s);
+        f->final_f32 = (float *)p;
+    }
     e->filters.push_back(f.get());
     *out = f.release();
     return NVISR_OK;

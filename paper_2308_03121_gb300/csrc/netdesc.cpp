@@ -68,10 +68,18 @@ bool parse_netdesc(const char *text, int64_t blob_count, NetDesc *net, std::stri
         if (key == "family") {
             if (tok.size() != 2 || (tok[1] != "tuple" && tok[1] != "group")) return fail("bad family");
             net->family = tok[1];
-        } else if (key == "frames" || key == "scale" || key == "align") {
+        } else if (key == "scale") {
+            // horizontal and vertical scale (Section 3.2), or one for both
+            int sx, sy;
+            if (tok.size() < 2 || tok.size() > 3 || !to_int(tok[1], &sx) || sx < 1 || sx > 16) return fail("bad scale");
+            sy = sx;
+            if (tok.size() == 3 && (!to_int(tok[2], &sy) || sy < 1 || sy > 16)) return fail("bad scale");
+            net->scale = sx;
+            net->scale_y = sy;
+        } else if (key == "frames" || key == "align") {
             int v;
             if (tok.size() != 2 || !to_int(tok[1], &v) || v < 1 || v > 16) return fail("bad " + key);
-            (key == "frames" ? net->frames : key == "scale" ? net->scale : net->align) = v;
+            (key == "frames" ? net->frames : net->align) = v;
         } else if (key == "flags") {
             if (tok.size() != 2) return fail("bad flags");
             for (const std::string &f : split(tok[1], ',')) {
@@ -118,8 +126,17 @@ bool parse_netdesc(const char *text, int64_t blob_count, NetDesc *net, std::stri
                 L.om = kv["om"];
                 if (!known.count(L.om)) return fail("unknown om source " + L.om);
             }
-            if (kv.count("ps") && (!to_int(kv["ps"], &L.ps) || L.ps != 2 || L.cout % 4))
-                return fail("ps must be 2 with cout divisible by 4");
+            if (kv.count("ps") && (kv.count("psx") || kv.count("psy"))) return fail("ps with psx/psy");
+            if (kv.count("ps")) {
+                if (!to_int(kv["ps"], &L.ps) || L.ps != 2 || L.cout % 4) return fail("ps must be 2 with cout divisible by 4");
+                L.psy = L.psx = 2;
+            } else if (kv.count("psx") || kv.count("psy")) {
+                if ((kv.count("psx") && (!to_int(kv["psx"], &L.psx) || L.psx < 1 || L.psx > 2)) ||
+                    (kv.count("psy") && (!to_int(kv["psy"], &L.psy) || L.psy < 1 || L.psy > 2)))
+                    return fail("psx / psy must be 1 or 2");
+                if (L.cout % (L.psx * L.psy)) return fail("cout must be divisible by psx * psy");
+                if (L.psx == 2 && L.psy == 2) L.ps = 2;  // the same as ps=2
+            }
             if (kv.count("add")) {
                 L.add = kv["add"];
                 if (!known.count(L.add)) return fail("unknown add source " + L.add);

@@ -22,6 +22,9 @@ struct NetLayer {
     std::string add;                 // residual source (added after the activation)
     std::string share;               // layer whose weights are reused
     int cin = 0, cout = 0, k = 3, groups = 1, ps = 0, act = 0;
+    // PixelShuffle factors (rows, columns): ps=r gives (r, r); psy= / psx= give them apart
+    // (out[c, psy*h + i, psx*w + j] = in[c*psy*psx + i*psx + j, h, w]); (1, 1) = none
+    int psy = 1, psx = 1;
     int64_t woff = -1;               // offset of weights in the blob (floats)
     int owner = -1;                  // index of the layer owning the weights
 };
@@ -34,7 +37,8 @@ struct NetOutput {
 struct NetDesc {
     std::string family = "tuple";    // "tuple" | "group"
     int frames = 1;
-    int scale = 1;
+    int scale = 1;                   // horizontal scale (the isotropic scale when scale_y equals it)
+    int scale_y = 1;                 // vertical scale ("scale sx sy"; "scale s" sets both)
     int align = 1;
     bool interp = false, extra = false, dbl = false;
     int skip = 0;                    // 0 none, 1 nearest, 2 bilinear

@@ -324,11 +324,12 @@ __device__ __forceinline__ float skip_at(const SkipArgs &k, int c, int Y, int X)
     for (int f = 0; f < k.n; ++f) {
         const float *p = k.src[f] + (int64_t)c * k.plane;
         float v;
+        const int sv = k.scale_y > 0 ? k.scale_y : k.scale;  // vertical scale
         if (k.mode == 1) {
-            v = p[(int64_t)(Y / k.scale) * k.pitch + X / k.scale];
+            v = p[(int64_t)(Y / sv) * k.pitch + X / k.scale];
         } else {
-            const float inv = 1.0f / (float)k.scale;
-            const float sy = fmaxf(((float)Y + 0.5f) * inv - 0.5f, 0.f);
+            const float inv = 1.0f / (float)k.scale, inv_y = 1.0f / (float)sv;
+            const float sy = fmaxf(((float)Y + 0.5f) * inv_y - 0.5f, 0.f);
             const float sx = fmaxf(((float)X + 0.5f) * inv - 0.5f, 0.f);
             const int y0 = min((int)sy, k.h - 1), x0 = min((int)sx, k.w - 1);
             const int y1 = min(y0 + 1, k.h - 1), x1 = min(x0 + 1, k.w - 1);
@@ -753,6 +754,38 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
 
 }  // namespace
 
+namespace {
+
+// One thread per low-resolution pixel: its 3 * ry * rx channels (float32, 4 per 16-byte
+// unit) scattered to the ry x rx block of each of the 3 planar output channels.
+__global__ void __launch_bounds__(256) shuffle_planar_kernel(const float *__restrict__ src, int H, int W, int ry,
+                                                             int rx, float *__restrict__ dst, int64_t dst_pitch) {
+    griddep_wait();  // launched as a dependent of the layer that produced src
+    griddep_launch_dependents();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const int64_t HW = (int64_t)H * W;
+    const int64_t plane = dst_pitch * H * ry;
+    for (int c = 0; c < 3; ++c)
+        for (int i = 0; i < ry; ++i)
+            for (int j = 0; j < rx; ++j) {
+                const int ch = (c * ry + i) * rx + j;
+                const float v = src[((int64_t)(ch >> 2) * HW + (int64_t)y * W + x) * 4 + (ch & 3)];
+                dst[c * plane + (int64_t)(ry * y + i) * dst_pitch + rx * x + j] = v;
+            }
+}
+
+}  // namespace
+
+cudaError_t launch_shuffle_planar(const float *src, int H, int W, int ry, int rx, float *dst, int64_t dst_pitch,
+                                  cudaStream_t st) {
+    if (H < 1 || W < 1 || ry < 1 || ry > 2 || rx < 1 || rx > 2 || dst_pitch < (int64_t)W * rx)
+        return cudaErrorInvalidValue;
+    return launch_dependent(shuffle_planar_kernel, dim3((unsigned)((W + 255) / 256), (unsigned)H), dim3(256), 0, st,
+                            src, H, W, ry, rx, dst, dst_pitch);
+}
+
 cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, const void *u, int64_t pu,
                           const void *v, int64_t pv, float *out, int64_t out_pitch, cudaStream_t st, int yuv) {
     const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix, yuv);
@@ -792,8 +825,10 @@ cudaError_t launch_requant(const nvisr_format &f, const float *in, int64_t in_pi
         cudaError_t e = cudaSuccess;
         block = dim3(128);
         dim3 grid((f.width + 8 * 128 - 1) / (8 * 128), f.height / 2);
-        const bool skip2 = sk.n == 1 && sk.mode == 2 && sk.scale == 2 && sk.h * 2 == f.height && sk.w * 2 == f.width;
-        const bool skip4 = (sk.n == 1 || sk.n == 2) && sk.mode == 2 && sk.scale == 4 && sk.h * 4 == f.height &&
+        const bool iso = sk.scale_y == 0 || sk.scale_y == sk.scale;
+        const bool skip2 = iso && sk.n == 1 && sk.mode == 2 && sk.scale == 2 && sk.h * 2 == f.height &&
+                           sk.w * 2 == f.width;
+        const bool skip4 = iso && (sk.n == 1 || sk.n == 2) && sk.mode == 2 && sk.scale == 4 && sk.h * 4 == f.height &&
                            sk.w * 4 == f.width;
 #define NVISR_RQ(S_, K_, N_)                                                                                 \
     e = launch_dependent(requant420_kernel<S_, K_, N_>, grid, block, 0, st, in, in_pitch, f.height, f.width, \

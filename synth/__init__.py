@@ -168,12 +168,12 @@ class NetSpec:
         nvisr-net 1
         family tuple|group
         frames <T>
-        scale <s>
+        scale <s> | <sx> <sy>               (horizontal and vertical scale)
         flags interp,extra,double          (group family)
         domain rgb|yuv                     (network colour domain, default rgb)
         skip none|nearest|bilinear
         conv <name> in=<a>[,<b>] cin=<C> cout=<N> k=<1|3> act=none|lrelu
-             [add=<name>] [ps=<r>] [share=<name>]
+             [add=<name>] [ps=<r> | psx=<rx> psy=<ry>] [share=<name>]
         dcn  <name> in=<x> om=<head> cin=<C> cout=<N> groups=<G> [share=<name>]
         out  <name> [skip=<frame>[,<frame>]]
 
@@ -181,8 +181,9 @@ class NetSpec:
     order: weight [cout][cin][k][k] then bias [cout], float32 little endian.
     """
 
-    def __init__(self, family: str, frames: int, scale: int, skip: str, flags: str = "", domain: str = "rgb"):
-        self.lines = ["nvisr-net 1", f"family {family}", f"frames {frames}", f"scale {scale}"]
+    def __init__(self, family: str, frames: int, scale, skip: str, flags: str = "", domain: str = "rgb"):
+        sc = f"{scale[0]} {scale[1]}" if isinstance(scale, tuple) else f"{scale}"
+        self.lines = ["nvisr-net 1", f"family {family}", f"frames {frames}", f"scale {sc}"]
         if flags:
             self.lines.append(f"flags {flags}")
         if domain != "rgb":
@@ -191,12 +192,16 @@ class NetSpec:
         self.blobs = []
 
     def conv(self, rng, name, src, cin, cout, k=3, act="none", add=None, ps=None,
-             share=None, gain=1.0, row_gains=None):
+             share=None, gain=1.0, row_gains=None, psx=None, psy=None):
         line = f"conv {name} in={src} cin={cin} cout={cout} k={k} act={act}"
         if add:
             line += f" add={add}"
         if ps:
             line += f" ps={ps}"
+        if psx:
+            line += f" psx={psx}"
+        if psy:
+            line += f" psy={psy}"
         if share:
             line += f" share={share}"
         else:
@@ -241,19 +246,28 @@ TAIL_GAIN = 0.02
 OFFSET_GAIN = 2.0
 
 
-def net_tuple(seed: int, frames: int, channels: int, nres: int, scale: int = 2,
+def net_tuple(seed: int, frames: int, channels: int, nres: int, scale=2,
               skip: str = "bilinear", tail_gain: float = TAIL_GAIN, res_gain: float = RES_GAIN,
               domain: str = "rgb"):
-    """Sliding-window SR network: conv(3T->C), nres residual blocks, conv(C->3 s^2), PixelShuffle(s)."""
+    """Sliding-window SR network: conv(3T->C), nres residual blocks, conv(C->3 s^2), PixelShuffle(s).
+
+    scale is an int, or (sx, sy) with factors 1 or 2: (1, 1) is a same-size enhancement
+    (denoise) network without a shuffle, (1, 2) a vertical 2x (deinterlace) network.
+    """
     rng = np.random.default_rng(seed)
-    spec = NetSpec("tuple", frames, scale, skip, domain=domain)
+    sx, sy = scale if isinstance(scale, tuple) else (scale, scale)
+    spec = NetSpec("tuple", frames, scale if sx != sy else sx, skip, domain=domain)
     spec.conv(rng, "head", "tuple", 3 * frames, channels, act="none")
     prev = "head"
     for i in range(nres):
         spec.conv(rng, f"r{i}a", prev, channels, channels, act="lrelu")
         spec.conv(rng, f"r{i}b", f"r{i}a", channels, channels, act="none", add=prev, gain=res_gain)
         prev = f"r{i}b"
-    spec.conv(rng, "tail", prev, channels, 3 * scale * scale, act="none", ps=scale, gain=tail_gain)
+    if sx == sy and sx > 1:
+        spec.conv(rng, "tail", prev, channels, 3 * sx * sy, act="none", ps=sx, gain=tail_gain)
+    else:
+        spec.conv(rng, "tail", prev, channels, 3 * sx * sy, act="none", gain=tail_gain,
+                  psx=sx if sx > 1 else None, psy=sy if sy > 1 else None)
     spec.out("tail")
     return spec.build()
 

@@ -86,6 +86,23 @@ def test_network_check_rejects_malformed(mutate, needle):
     assert st == nv.Status.BAD_NETWORK and needle in msg
 
 
+@pytest.mark.parametrize("scale", [(1, 1), (1, 2), (2, 1)])
+def test_network_check_accepts_separate_scales(scale):
+    text, blob = synth.net_tuple(3, frames=3, channels=16, nres=1, scale=scale)
+    st, msg = nv.nvisr_network_check(text, blob.size)
+    assert st == 0, msg
+
+
+@pytest.mark.parametrize("attr,needle", [("psx=3", "psx / psy"), ("ps=2 psx=2", "ps with psx"),
+                                         ("psx=2", "divisible by psx")])
+def test_network_check_rejects_bad_shuffle_factors(attr, needle):
+    text, blob = synth.net_tuple(3, frames=3, channels=16, nres=1, scale=(1, 1))
+    bad = text.replace("conv tail in=r0b cin=16 cout=3 k=3 act=none", "conv tail in=r0b cin=16 cout=3 k=3 act=none " + attr)
+    assert bad != text
+    st, msg = nv.nvisr_network_check(bad, blob.size)
+    assert st == nv.Status.BAD_NETWORK and needle in msg, msg
+
+
 def test_network_check_rejects_blob_size():
     text, blob = synth.net_config1()
     st, msg = nv.nvisr_network_check(text, blob.size + 1)

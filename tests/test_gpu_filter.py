@@ -364,3 +364,28 @@ def test_filter_yuv_domain_network(prec):
         else:
             mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], b) for k in "YUV"})
             assert mx <= 1, mx
+
+
+@pytest.mark.parametrize("sx,sy", [(1, 1), (1, 2)])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_filter_separate_scales(sx, sy, prec):
+    """Section 3.2's horizontal and vertical scale: a same-size enhancement (denoise) network
+    (1 x 1) and a vertical 2x (deinterlace) network (1 x 2), 64 channels, 10-bit 4:2:0 in and
+    out, a cut on frame 3.  The output layer writes float32, shuffled into the planar output
+    by its own kernel."""
+    frames = synth.frames_textured(synth.BASE_SEED + 74, 6, 64, 48, 10, "420", "limited")
+    flags = np.zeros(6, bool)
+    flags[3] = True
+    fdi, fdo = fmt_dict(64, 48, 10), fmt_dict(64 * sx, 48 * sy, 10)
+    text, blob = synth.net_tuple(synth.BASE_SEED + 75, frames=3, channels=64, nres=1, scale=(sx, sy))
+    ref = [prequant(o, fdo) for o in oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)]
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(64, 48, 10), nv.fmt(64 * sx, 48 * sy, 10), prec,
+                      scale=(sx, sy))
+    assert len(outs) == len(ref) == 6
+    for got, pq in zip(outs, ref):
+        assert got["Y"].shape == (48 * sy, 64 * sx)
+        if prec == "fp32":
+            assert_codes_match(got, pq, 10)
+        else:
+            mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 10) for k in "YUV"})
+            assert mx <= 1, mx

@@ -276,6 +276,30 @@ def test_upsample_matches_torch(s):
     assert np.array_equal(oracle.upsample_nearest(x, s), tn)
 
 
+@pytest.mark.parametrize("ry,rx", [(1, 1), (1, 2), (2, 1), (2, 2)])
+def test_pixel_shuffle_separate_factors_inverts_slicing(ry, rx):
+    """PixelShuffle with row factor ry and column factor rx (Section 3.2's separate
+    horizontal / vertical scales): cutting an image into its ry x rx phase images by
+    slicing and stacking them channel-major (c, i, j) must be undone exactly."""
+    img = np.random.default_rng(21 + 3 * ry + rx).normal(size=(3, 4 * ry, 5 * rx))
+    phases = np.stack([img[c, i::ry, j::rx] for c in range(3) for i in range(ry) for j in range(rx)])
+    assert np.array_equal(oracle.pixel_shuffle(phases, ry, rx), img)
+    if ry == rx:
+        assert np.array_equal(oracle.pixel_shuffle(phases, ry), img)
+
+
+@pytest.mark.parametrize("sx,sy", [(1, 1), (1, 2), (2, 1), (2, 4)])
+def test_upsample_separate_scales_match_torch(sx, sy):
+    x = np.random.default_rng(17).normal(size=(3, 5, 7))
+    tb = F.interpolate(torch.from_numpy(x)[None], scale_factor=(sy, sx), mode="bilinear",
+                       align_corners=False)[0].numpy()
+    assert np.abs(oracle.upsample_bilinear(x, sx, sy) - tb).max() < 1e-12
+    tn = F.interpolate(torch.from_numpy(x)[None], scale_factor=(sy, sx), mode="nearest")[0].numpy()
+    assert np.array_equal(oracle.upsample_nearest(x, sx, sy), tn)
+    if (sx, sy) == (1, 1):
+        assert np.array_equal(oracle.upsample_bilinear(x, 1), x)
+
+
 def test_leaky_relu_matches_torch():
     x = np.linspace(-3, 3, 61)
     assert np.array_equal(oracle.leaky_relu(x), F.leaky_relu(torch.from_numpy(x), 0.1).numpy())
@@ -477,6 +501,24 @@ def test_zero_residual_nearest_reproduces_input(sub, loc):
     for f, o in zip(frames, outs):
         for k in "YUV":
             exp = np.repeat(np.repeat(f[k].astype(np.int64), 2, 0), 2, 1)
+            assert np.array_equal(o[k], exp), k
+
+
+@pytest.mark.parametrize("sx,sy", [(1, 1), (1, 2), (2, 1)])
+@pytest.mark.parametrize("sub,loc", [("444", "left"), ("420", "point")])
+def test_zero_residual_nearest_separate_scales_reproduce_input(sx, sy, sub, loc):
+    """Same-size (1 x 1, denoise) and one-axis (1 x 2 deinterlace, 2 x 1) networks with zero
+    residual and nearest skip return their input codes, repeated along the scaled axis."""
+    text, blob = synth.net_tuple(9, frames=3, channels=8, nres=1, scale=(sx, sy), skip="nearest")
+    blob = blob.copy()
+    tail = 3 * sx * sy * (8 * 9 + 1)
+    blob[-tail:] = 0.0
+    frames = synth.frames_gradient(3, 4, 16, 12, 8, sub, "full")
+    fmt_in = _fmt(8, sub, "full", loc)
+    outs = oracle.run_filter(frames, np.zeros(4, bool), text, blob, fmt_in, fmt_in)
+    for f, o in zip(frames, outs):
+        for k in "YUV":
+            exp = np.repeat(np.repeat(f[k].astype(np.int64), sy, 0), sx, 1)
             assert np.array_equal(o[k], exp), k
 
 
