@@ -104,8 +104,11 @@ typedef struct nvisr_filter_desc {
     const float *weights;        /* host FP32 weight blob, in description order */
     int64_t weights_count;       /* number of floats in the blob */
     nvisr_format in_fmt;
-    nvisr_format out_fmt;        /* width/height must equal scale x input */
-    int32_t scale_w, scale_h;    /* spatial scale; must match the description */
+    nvisr_format out_fmt;        /* width = scale_w x input width, height = scale_h x input height */
+    int32_t scale_w, scale_h;    /* horizontal and vertical scale (Section 3.2); must match the
+                                  * description's "scale sx [sy]".  Tuple networks: 2 x 2 (SR),
+                                  * 1 x 1 (same-size enhancement, e.g. denoise), 1 x 2 or 2 x 1
+                                  * (one-axis 2x, e.g. deinterlace); group networks: one scale */
     int32_t precision;           /* nvisr_precision */
     int32_t calib_frames;        /* FP8: frames whose activations set the scales (0 = 4) */
 } nvisr_filter_desc;
