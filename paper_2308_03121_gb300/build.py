@@ -2,7 +2,7 @@
 
 Compiles every translation unit under csrc/ with nvcc in parallel and links a
 shared library exporting the C ABI of include/nvisr.h.  The CUDA runtime is
-linked statically; the driver is reached at run time, so the library loads on
+linked statically; the CUDA driver library is opened at run time, so the library loads on
 a machine without a GPU (calls that need one then fail with CUDA_ERROR).
 """
 from __future__ import annotations
