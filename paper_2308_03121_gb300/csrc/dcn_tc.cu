@@ -220,6 +220,17 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                     v[h][0] = r0 && mc ? __ldg(reinterpret_cast<const uint4 *>(plane + o0)) : make_uint4(0u, 0u, 0u, 0u);
                     v[h][1] = r1 && mc ? __ldg(reinterpret_cast<const uint4 *>(plane + o1)) : make_uint4(0u, 0u, 0u, 0u);
                 }
+                // mask sigmoids: both lanes of a pair need the same values, so lane c computes
+                // those of the passes h with h % 2 == c and the pair swaps them (the same
+                // arithmetic per value, half the instructions per lane)
+                static_assert(NPASS % 2 == 0, "passes shared by a lane pair");
+                float mine[NPASS / 2], theirs[NPASS / 2];
+#pragma unroll
+                for (int i = 0; i < NPASS / 2; ++i) {
+                    const float lg = c ? msk[2 * i + 1] : msk[2 * i];
+                    mine[i] = a.mask_logits ? __frcp_rn(1.f + expf(-lg)) : lg;
+                    theirs[i] = __shfl_xor_sync(0xffffffffu, mine[i], 1);
+                }
 #pragma unroll
                 for (int h = 0; h < NPASS; ++h) {
                     // corner (r, col) weight = row factor x column factor, each zero outside the image
@@ -243,8 +254,7 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                         ffma2(acc[0], wb, unpack_pair<T>(b0));
                         ffma2(acc[1], wb, unpack_pair<T>(b1));
                     }
-                    float mm = msk[h];
-                    if (a.mask_logits) mm = __frcp_rn(1.f + expf(-mm));
+                    const float mm = (h & 1) == c ? mine[h >> 1] : theirs[h >> 1];
                     *reinterpret_cast<uint2 *>(stg + (size_t)(pb + h * 16) * 16) =
                         make_uint2(pack_pair<T>(acc[0].x * mm, acc[0].y * mm), pack_pair<T>(acc[1].x * mm, acc[1].y * mm));
                 }
