@@ -55,7 +55,9 @@ typedef enum nvisr_subsampling { NVISR_SUB_420 = 0, NVISR_SUB_444 = 1 } nvisr_su
 typedef enum nvisr_range { NVISR_RANGE_LIMITED = 0, NVISR_RANGE_FULL = 1 } nvisr_range;
 /* Colour matrix: BT.709, or BT.2020 non-constant luminance (same equations,
  * weights Kr 0.2627 / Kb 0.0593).  No transfer-function change is applied. */
-typedef enum nvisr_matrix { NVISR_MATRIX_BT709 = 0, NVISR_MATRIX_BT2020 = 1 } nvisr_matrix;
+/* NVISR_MATRIX_RGB: the three planes are R', G', B' (4:4:4 only), each with the luma range
+ * equations and no matrix (Section 3.1: RGB I/O); it needs an RGB-domain network. */
+typedef enum nvisr_matrix { NVISR_MATRIX_BT709 = 0, NVISR_MATRIX_BT2020 = 1, NVISR_MATRIX_RGB = 2 } nvisr_matrix;
 /* Chroma siting of 4:2:0 planes: LEFT = ITU-T H.273 type 0 (co-sited
  * horizontally, between rows vertically), CENTER = type 1, POINT = replicate
  * on upsampling and 2x2 mean on downsampling. */
@@ -81,7 +83,7 @@ typedef struct nvisr_format {
     int32_t reserved;
 } nvisr_format;
 
-/* Three planes Y, U (Cb), V (Cr).  pitch = bytes between rows. */
+/* Three planes Y, U (Cb), V (Cr), or R, G, B for NVISR_MATRIX_RGB.  pitch = bytes between rows. */
 typedef struct nvisr_planes {
     void *data[3];
     int64_t pitch[3];

@@ -19,6 +19,8 @@ in the design notes:
   rows vertically), CENTER (centred both ways), POINT (replicate; a test mode).
   Edges clamp to the nearest sample.
 * requantisation: round half to even, clamp to the code range [0, 2^b - 1].
+* RGB integer I/O (matrix 'rgb', 4:4:4): the three planes are R, G, B, each with
+  the luma range equations, and no matrix.
 """
 from __future__ import annotations
 
@@ -170,6 +172,27 @@ def downsample_chroma(c, subsampling: str, loc: str):
 # ---------------------------------------------------------------- ingest / requantise
 
 def ingest(planes, fmt, domain: str = "rgb"):
+    """Integer planes -> float64 network-domain planes [3][H][W]: RGB planes, or Y'CbCr
+    planes through the matrix (or without it for a YUV-domain network)."""
+    if fmt.get("matrix") == "rgb":
+        return ingest_rgb(planes, fmt, domain)
+    return _ingest_ycbcr(planes, fmt, domain)
+
+
+def ingest_rgb(planes, fmt, domain: str = "rgb"):
+    """Integer R'G'B' planes (positions Y, U, V hold R, G, B; 4:4:4) -> float64 R'G'B'.
+
+    Section 3.1 allows RGB as well as YUV I/O.  Reading: each channel takes the
+    luma range equations (limited: (v - 16m) / 219m; full: v / (2^b - 1)), as
+    R'G'B' video does in H.273 / BT.709; no matrix.  Only an RGB-domain network
+    takes RGB planes.
+    """
+    assert fmt["subsampling"] == "444" and domain == "rgb"
+    b, rg = fmt["bit_depth"], fmt["range"]
+    return np.stack([normalise_luma(planes[k], b, rg) for k in "YUV"])
+
+
+def _ingest_ycbcr(planes, fmt, domain: str = "rgb"):
     """Integer Y/U/V planes -> float64 R'G'B' [3][H][W] (network domain RGB, unclamped), or
     the normalised Y'Cb'Cr' planes (chroma upsampled, no matrix) for a YUV-domain network.
 
@@ -187,6 +210,22 @@ def ingest(planes, fmt, domain: str = "rgb"):
 
 
 def requantise(rgb, fmt, domain: str = "rgb"):
+    """float network-domain planes [3][H][W] -> integer planes {"Y","U","V"} (int64)."""
+    if fmt.get("matrix") == "rgb":
+        return requantise_rgb(rgb, fmt, domain)
+    return _requantise_ycbcr(rgb, fmt, domain)
+
+
+def requantise_rgb(rgb, fmt, domain: str = "rgb"):
+    """float R'G'B' [3][H][W] -> integer planes {"Y","U","V"} holding R, G, B (4:4:4):
+    each channel scaled with the luma range equations, rounded half to even and
+    clamped to [0, 2^b - 1]."""
+    assert fmt["subsampling"] == "444" and domain == "rgb"
+    b, rg = fmt["bit_depth"], fmt["range"]
+    return {k: quantise(scale_luma(rgb[i], b, rg), b) for i, k in enumerate("YUV")}
+
+
+def _requantise_ycbcr(rgb, fmt, domain: str = "rgb"):
     """float R'G'B' [3][H][W] -> integer planes {"Y","U","V"} (int64 arrays).
 
     Y'CbCr from RGB, chroma downsampled in float, scaled to the code range,

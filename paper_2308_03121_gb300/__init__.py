@@ -163,7 +163,7 @@ def _check(status, what):
     return status
 
 
-MATRIX = {"bt709": 0, "bt2020": 1}
+MATRIX = {"bt709": 0, "bt2020": 1, "rgb": 2}
 
 
 def fmt(width, height, bit_depth, subsampling="420", range_="limited", chroma_loc="left", matrix="bt709"):

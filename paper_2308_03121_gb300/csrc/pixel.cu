@@ -56,6 +56,11 @@ RangeConst range_const(int bits, int range, int matrix, int yuv) {
         r.y_off = 0.f; r.y_den = top; r.c_off = (float)(1 << (bits - 1)); r.c_den = top;
         r.y_mul = top; r.y_add = 0.f; r.c_mul = top; r.c_add = (float)(1 << (bits - 1));
     }
+    if (matrix == NVISR_MATRIX_RGB) {
+        // R'G'B' planes: every channel takes the luma range equations, no matrix
+        r.c_off = r.y_off; r.c_den = r.y_den; r.c_mul = r.y_mul; r.c_add = r.y_add;
+        r.yuv = 1;
+    }
     r.vmax = (float)((1 << bits) - 1);
     r.y_rden = 1.0f / r.y_den;
     r.c_rden = 1.0f / r.c_den;

@@ -26,6 +26,8 @@ def from_dev(t, bits):
 def prequant(rgb, fmt):
     """Oracle requantisation values before rounding (to locate round-half ties)."""
     b, rg = fmt["bit_depth"], fmt["range"]
+    if fmt.get("matrix") == "rgb":  # R'G'B' planes, luma range equations
+        return {k: oracle.scale_luma(rgb[i], b, rg) for i, k in enumerate("YUV")}
     yp, cb, cr = oracle.rgb_to_ycbcr(rgb[0], rgb[1], rgb[2], fmt.get("matrix", "bt709"))
     cb = oracle.downsample_chroma(cb, fmt["subsampling"], fmt["chroma_loc"])
     cr = oracle.downsample_chroma(cr, fmt["subsampling"], fmt["chroma_loc"])

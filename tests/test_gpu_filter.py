@@ -389,3 +389,39 @@ def test_filter_separate_scales(sx, sy, prec):
         else:
             mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 10) for k in "YUV"})
             assert mx <= 1, mx
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_filter_rgb_planes(prec):
+    """RGB planes in and out (Section 3.1: RGB or YUV I/O): 8-bit full-range 4:4:4 R, G, B,
+    config-1 network (2x), a cut on frame 4."""
+    frames = synth.frames_textured(synth.BASE_SEED + 76, 6, 48, 32, 8, "444", "full")
+    flags = np.zeros(6, bool)
+    flags[4] = True
+    fdi = fmt_dict(48, 32, 8, "444", "full", "left", "rgb")
+    fdo = fmt_dict(96, 64, 8, "444", "full", "left", "rgb")
+    text, blob = synth.net_config1()
+    ref = [prequant(o, fdo) for o in oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)]
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(48, 32, 8, "444", "full", "left", "rgb"),
+                      nv.fmt(96, 64, 8, "444", "full", "left", "rgb"), prec)
+    assert len(outs) == len(ref) == 6
+    for got, pq in zip(outs, ref):
+        if prec == "fp32":
+            assert_codes_match(got, pq, 8)
+        else:
+            mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 8) for k in "YUV"})
+            assert mx <= 1, mx
+
+
+def test_rgb_format_checks():
+    """RGB planes need 4:4:4 and an RGB-domain network."""
+    eng = nv.Engine()
+    text, blob = synth.net_config1()
+    with pytest.raises(Exception, match="UNSUPPORTED_FORMAT|unsupported"):
+        eng.filter(text, blob, nv.fmt(48, 32, 8, "420", "full", "left", "rgb"),
+                   nv.fmt(96, 64, 8, "420", "full", "left", "rgb"), "bf16")
+    ytext, yblob = synth.net_tuple(3, frames=3, channels=16, nres=1, scale=2, domain="yuv")
+    with pytest.raises(Exception, match="UNSUPPORTED_FORMAT|YUV-domain"):
+        eng.filter(ytext, yblob, nv.fmt(48, 32, 8, "444", "full", "left", "rgb"),
+                   nv.fmt(96, 64, 8, "444", "full", "left", "rgb"), "bf16")
+    eng.close()

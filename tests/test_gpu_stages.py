@@ -77,11 +77,13 @@ def test_requant_matches_oracle(W, H, bits, sub, rng, loc):
     assert_codes_match(got, prequant(rgb.astype(np.float64), fd), bits)
 
 
-FORMAT_CASES = [  # BT.2020 and 12 / 16-bit samples (W, H, bits, subsampling, range, siting, matrix)
+FORMAT_CASES = [  # BT.2020, RGB, and 12 / 16-bit samples (W, H, bits, subsampling, range, siting, matrix)
     (96, 40, 12, "420", "limited", "left", "bt2020"),
     (70, 34, 16, "444", "full", "center", "bt2020"),
     (64, 32, 12, "420", "full", "left", "bt709"),
     (130, 66, 16, "420", "limited", "center", "bt709"),
+    (64, 32, 8, "444", "full", "left", "rgb"),       # RGB planes (luma range equations, no matrix)
+    (70, 34, 10, "444", "limited", "center", "rgb"),
 ]
 
 

@@ -124,6 +124,24 @@ def test_range_pins_high_bit_depths(bits):
     assert oracle.quantise(oracle.scale_luma(1.0, bits, "limited"), bits) == 235 * m
 
 
+@pytest.mark.parametrize("bits,rng_name", [(8, "full"), (10, "limited"), (12, "full"), (16, "limited")])
+def test_rgb_io_range_anchors_and_exact_round_trip(bits, rng_name):
+    """RGB planes (Section 3.1: RGB or YUV I/O) take the luma range equations: the range
+    ends map to 0 and 1, and every code comes back unchanged through ingest and
+    requantise (no matrix, no resampling)."""
+    fmt = {"bit_depth": bits, "subsampling": "444", "range": rng_name, "chroma_loc": "left", "matrix": "rgb"}
+    m = 2 ** (bits - 8)
+    lo, hi = (0, 2 ** bits - 1) if rng_name == "full" else (16 * m, 235 * m)
+    codes = np.arange(0, 2 ** bits, max(1, 2 ** bits // 4096), dtype=np.int64)
+    codes = np.concatenate([codes, [lo, hi, 2 ** bits - 1]])
+    planes = {k: np.roll(codes, i).reshape(1, -1) for i, k in enumerate("YUV")}
+    rgb = oracle.ingest(planes, fmt)
+    assert rgb[0][0, -3] == 0.0 and rgb[0][0, -2] == 1.0
+    back = oracle.requantise(rgb, fmt)
+    for k in "YUV":
+        assert np.array_equal(back[k], planes[k]), k
+
+
 @pytest.mark.parametrize("rng_name", ["limited", "full"])
 def test_8bit_round_trip_within_1lsb(rng_name):
     """8-bit YUV -> RGB -> 8-bit RGB -> YUV stays within +-1 LSB for in-gamut colours."""
@@ -520,6 +538,20 @@ def test_zero_residual_nearest_separate_scales_reproduce_input(sx, sy, sub, loc)
         for k in "YUV":
             exp = np.repeat(np.repeat(f[k].astype(np.int64), sy, 0), sx, 1)
             assert np.array_equal(o[k], exp), k
+
+
+def test_rgb_io_zero_residual_nearest_reproduces_input():
+    """RGB planes in and out, zero residual and nearest skip: the output codes are the
+    input codes repeated 2 x 2, for any code values."""
+    text, blob = _identity_net()
+    rng = np.random.default_rng(8)
+    frames = [{k: rng.integers(0, 1024, (12, 16)) for k in "YUV"} for _ in range(4)]
+    fmt = _fmt(10, "444", "limited", "left")
+    fmt["matrix"] = "rgb"
+    outs = oracle.run_filter(frames, np.zeros(4, bool), text, blob, fmt, fmt)
+    for f, o in zip(frames, outs):
+        for k in "YUV":
+            assert np.array_equal(o[k], np.repeat(np.repeat(f[k].astype(np.int64), 2, 0), 2, 1)), k
 
 
 @pytest.mark.parametrize("sub,loc", [("444", "left"), ("420", "point")])
