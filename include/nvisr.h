@@ -55,6 +55,12 @@ typedef enum nvisr_subsampling { NVISR_SUB_420 = 0, NVISR_SUB_444 = 1 } nvisr_su
 typedef enum nvisr_range { NVISR_RANGE_LIMITED = 0, NVISR_RANGE_FULL = 1 } nvisr_range;
 /* Colour matrix: BT.709, or BT.2020 non-constant luminance (same equations,
  * weights Kr 0.2627 / Kb 0.0593).  No transfer-function change is applied. */
+/* Transfer of the coded R'G'B' signal.  NONE: the network sees the coded signal.  PQ
+ * (SMPTE ST 2084) and HLG (BT.2100): the network sees linear light; ingest applies the
+ * PQ EOTF (1.0 = 10000 cd/m^2) or the inverse HLG OETF after the matrix, requantise clamps
+ * to [0, 1] and applies the inverse before it.  Only RGB-domain networks. */
+typedef enum nvisr_transfer { NVISR_TRANSFER_NONE = 0, NVISR_TRANSFER_PQ = 1, NVISR_TRANSFER_HLG = 2 } nvisr_transfer;
+
 /* NVISR_MATRIX_RGB: the three planes are R', G', B' (4:4:4 only), each with the luma range
  * equations and no matrix (Section 3.1: RGB I/O); it needs an RGB-domain network. */
 typedef enum nvisr_matrix { NVISR_MATRIX_BT709 = 0, NVISR_MATRIX_BT2020 = 1, NVISR_MATRIX_RGB = 2 } nvisr_matrix;
@@ -80,7 +86,7 @@ typedef struct nvisr_format {
     int32_t range;               /* nvisr_range */
     int32_t matrix;              /* nvisr_matrix */
     int32_t chroma_loc;          /* nvisr_chroma_loc */
-    int32_t reserved;
+    int32_t transfer;            /* nvisr_transfer */
 } nvisr_format;
 
 /* Three planes Y, U (Cb), V (Cr), or R, G, B for NVISR_MATRIX_RGB.  pitch = bytes between rows. */

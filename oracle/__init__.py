@@ -29,9 +29,10 @@ from __future__ import annotations
 
 import numpy as np
 
-from .colour import (KB, KG, KR, downsample_chroma, ingest, normalise_chroma,
-                     normalise_luma, quantise, requantise, rgb_to_ycbcr,
-                     scale_chroma, scale_luma, upsample_chroma, ycbcr_to_rgb)
+from .colour import (HLG_A, HLG_B, HLG_C, KB, KG, KR, downsample_chroma, hlg_inverse_oetf,
+                     from_linear, hlg_oetf, ingest, normalise_chroma, normalise_luma, pq_eotf,
+                     pq_inverse_eotf, quantise, requantise, rgb_to_ycbcr, scale_chroma,
+                     scale_luma, to_linear, upsample_chroma, ycbcr_to_rgb)
 from .grouping import (fig1_layout, fig1_next_batch_copy, fig1_slot_frames,
                        group_output_count, group_runs, scene_of,
                        scenes_from_flags, tuple_indices, tuple_map)
@@ -40,7 +41,8 @@ from .net import (Net, conv2d_direct, conv2d_im2col, dcn2d, leaky_relu,
                   upsample_nearest)
 
 __all__ = [
-    "KB", "KG", "KR", "Net", "conv2d_direct", "conv2d_im2col", "dcn2d",
+    "HLG_A", "HLG_B", "HLG_C", "KB", "KG", "KR", "Net", "conv2d_direct", "conv2d_im2col", "dcn2d",
+    "from_linear", "hlg_inverse_oetf", "hlg_oetf", "pq_eotf", "pq_inverse_eotf", "to_linear",
     "downsample_chroma", "fig1_layout", "fig1_next_batch_copy", "fig1_slot_frames",
     "group_output_count", "group_runs", "ingest", "leaky_relu", "normalise_chroma",
     "normalise_luma", "oracle_threads", "pad_to_align", "pixel_shuffle", "quantise",

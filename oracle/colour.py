@@ -21,6 +21,11 @@ in the design notes:
 * requantisation: round half to even, clamp to the code range [0, 2^b - 1].
 * RGB integer I/O (matrix 'rgb', 4:4:4): the three planes are R, G, B, each with
   the luma range equations, and no matrix.
+* HDR transfer (transfer 'pq' or 'hlg'): the network sees linear light.  Ingest
+  takes the coded R'G'B' through the SMPTE ST 2084 EOTF (1.0 = 10000 cd/m^2) or
+  the inverse of the BT.2100 HLG OETF (scene light), after clamping the coded
+  value to [0, 1]; requantise clamps the network's output to [0, 1] and
+  applies the inverse functions before the matrix.
 """
 from __future__ import annotations
 
@@ -94,6 +99,66 @@ def rgb_to_ycbcr(r, g, b, matrix: str = "bt709"):
     cb = (b - yp) / (2.0 * (1.0 - kb))
     cr = (r - yp) / (2.0 * (1.0 - kr))
     return yp, cb, cr
+
+
+# ---------------------------------------------------------------- HDR transfer
+
+# SMPTE ST 2084 (PQ) constants, as the standard defines them (exact rationals)
+PQ_M1 = 2610.0 / 16384.0
+PQ_M2 = 2523.0 / 4096.0 * 128.0
+PQ_C1 = 3424.0 / 4096.0
+PQ_C2 = 2413.0 / 4096.0 * 32.0
+PQ_C3 = 2392.0 / 4096.0 * 32.0
+# BT.2100 HLG OETF constants
+HLG_A = 0.17883277
+HLG_B = 1.0 - 4.0 * HLG_A
+HLG_C = 0.5 - HLG_A * np.log(4.0 * HLG_A)
+
+
+def pq_eotf(e):
+    """PQ code value in [0, 1] -> linear light in [0, 1] (1 = 10000 cd/m^2)."""
+    ep = np.power(np.maximum(np.asarray(e, np.float64), 0.0), 1.0 / PQ_M2)
+    return np.power(np.maximum(ep - PQ_C1, 0.0) / (PQ_C2 - PQ_C3 * ep), 1.0 / PQ_M1)
+
+
+def pq_inverse_eotf(y):
+    """Linear light in [0, 1] -> PQ code value."""
+    ym = np.power(np.clip(np.asarray(y, np.float64), 0.0, 1.0), PQ_M1)
+    return np.power((PQ_C1 + PQ_C2 * ym) / (1.0 + PQ_C3 * ym), PQ_M2)
+
+
+def hlg_oetf(e):
+    """Scene light in [0, 1] -> HLG code value."""
+    e = np.clip(np.asarray(e, np.float64), 0.0, 1.0)
+    lo = np.sqrt(3.0 * e)
+    hi = HLG_A * np.log(np.maximum(12.0 * e - HLG_B, 1e-300)) + HLG_C
+    return np.where(e <= 1.0 / 12.0, lo, hi)
+
+
+def hlg_inverse_oetf(ep):
+    """HLG code value -> scene light."""
+    ep = np.maximum(np.asarray(ep, np.float64), 0.0)
+    return np.where(ep <= 0.5, ep * ep / 3.0, (np.exp((ep - HLG_C) / HLG_A) + HLG_B) / 12.0)
+
+
+def to_linear(rgb, transfer: str):
+    """Coded R'G'B' -> the network's linear light (identity for 'none').  The coded value is
+    clamped to [0, 1], where the transfer functions are defined (an out-of-gamut Y'CbCr
+    combination can give R' > 1, where the PQ EOTF has a pole)."""
+    if transfer == "pq":
+        return pq_eotf(np.clip(rgb, 0.0, 1.0))
+    if transfer == "hlg":
+        return hlg_inverse_oetf(np.clip(rgb, 0.0, 1.0))
+    return rgb
+
+
+def from_linear(rgb, transfer: str):
+    """The network's linear light -> coded R'G'B' (clamped to [0, 1] first; identity for 'none')."""
+    if transfer == "pq":
+        return pq_inverse_eotf(rgb)
+    if transfer == "hlg":
+        return hlg_oetf(rgb)
+    return rgb
 
 
 # ---------------------------------------------------------------- chroma (C3)
@@ -189,7 +254,8 @@ def ingest_rgb(planes, fmt, domain: str = "rgb"):
     """
     assert fmt["subsampling"] == "444" and domain == "rgb"
     b, rg = fmt["bit_depth"], fmt["range"]
-    return np.stack([normalise_luma(planes[k], b, rg) for k in "YUV"])
+    rgb = np.stack([normalise_luma(planes[k], b, rg) for k in "YUV"])
+    return to_linear(rgb, fmt.get("transfer", "none"))
 
 
 def _ingest_ycbcr(planes, fmt, domain: str = "rgb"):
@@ -206,7 +272,7 @@ def _ingest_ycbcr(planes, fmt, domain: str = "rgb"):
     if domain == "yuv":
         return np.stack([yp, cb, cr])
     r, g, bb = ycbcr_to_rgb(yp, cb, cr, fmt.get("matrix", "bt709"))
-    return np.stack([r, g, bb])
+    return to_linear(np.stack([r, g, bb]), fmt.get("transfer", "none"))
 
 
 def requantise(rgb, fmt, domain: str = "rgb"):
@@ -222,6 +288,7 @@ def requantise_rgb(rgb, fmt, domain: str = "rgb"):
     clamped to [0, 2^b - 1]."""
     assert fmt["subsampling"] == "444" and domain == "rgb"
     b, rg = fmt["bit_depth"], fmt["range"]
+    rgb = from_linear(np.asarray(rgb, np.float64), fmt.get("transfer", "none"))
     return {k: quantise(scale_luma(rgb[i], b, rg), b) for i, k in enumerate("YUV")}
 
 
@@ -235,6 +302,7 @@ def _requantise_ycbcr(rgb, fmt, domain: str = "rgb"):
     if domain == "yuv":  # a YUV-domain network's planes are Y'Cb'Cr' already
         yp, cb, cr = rgb[0], rgb[1], rgb[2]
     else:
+        rgb = from_linear(np.asarray(rgb, np.float64), fmt.get("transfer", "none"))
         yp, cb, cr = rgb_to_ycbcr(rgb[0], rgb[1], rgb[2], fmt.get("matrix", "bt709"))
     cb = downsample_chroma(cb, fmt["subsampling"], fmt["chroma_loc"])
     cr = downsample_chroma(cr, fmt["subsampling"], fmt["chroma_loc"])

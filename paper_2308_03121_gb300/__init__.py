@@ -47,7 +47,7 @@ class NvisrError(RuntimeError):
 class Format(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("bit_depth", ctypes.c_int32),
                 ("subsampling", ctypes.c_int32), ("range", ctypes.c_int32), ("matrix", ctypes.c_int32),
-                ("chroma_loc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("chroma_loc", ctypes.c_int32), ("transfer", ctypes.c_int32)]
 
 
 class Planes(ctypes.Structure):
@@ -164,10 +164,13 @@ def _check(status, what):
 
 
 MATRIX = {"bt709": 0, "bt2020": 1, "rgb": 2}
+TRANSFER = {"none": 0, "pq": 1, "hlg": 2}
 
 
-def fmt(width, height, bit_depth, subsampling="420", range_="limited", chroma_loc="left", matrix="bt709"):
-    return Format(width, height, bit_depth, SUB[subsampling], RANGE[range_], MATRIX[matrix], LOC[chroma_loc], 0)
+def fmt(width, height, bit_depth, subsampling="420", range_="limited", chroma_loc="left", matrix="bt709",
+        transfer="none"):
+    return Format(width, height, bit_depth, SUB[subsampling], RANGE[range_], MATRIX[matrix], LOC[chroma_loc],
+                  TRANSFER[transfer])
 
 
 def _ptr(t):

@@ -153,6 +153,7 @@ bool fmt_ok(const nvisr_format &f) {
            (f.range == NVISR_RANGE_LIMITED || f.range == NVISR_RANGE_FULL) &&
            (f.matrix == NVISR_MATRIX_BT709 || f.matrix == NVISR_MATRIX_BT2020 ||
             (f.matrix == NVISR_MATRIX_RGB && f.subsampling == NVISR_SUB_444)) &&
+           (f.transfer == NVISR_TRANSFER_NONE || f.transfer == NVISR_TRANSFER_PQ || f.transfer == NVISR_TRANSFER_HLG) &&
            f.chroma_loc >= 0 && f.chroma_loc <= 2 &&
            (f.subsampling == NVISR_SUB_444 || (f.width % 2 == 0 && f.height % 2 == 0));
 }
@@ -1631,6 +1632,8 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
     if (!parse_netdesc(d->network_text, d->weights_count, &f->net, &err)) return fail(NVISR_BAD_NETWORK, err);
     if (f->net.yuv && (d->in_fmt.matrix == NVISR_MATRIX_RGB || d->out_fmt.matrix == NVISR_MATRIX_RGB))
         return fail(NVISR_UNSUPPORTED_FORMAT, "a YUV-domain network takes and gives Y'CbCr planes, not RGB");
+    if (f->net.yuv && (d->in_fmt.transfer != NVISR_TRANSFER_NONE || d->out_fmt.transfer != NVISR_TRANSFER_NONE))
+        return fail(NVISR_UNSUPPORTED_FORMAT, "a YUV-domain network sees the coded signal (no transfer)");
     const NetDesc &net = f->net;
     if (d->scale_w != net.scale || d->scale_h != net.scale_y)
         return fail(NVISR_INVALID_ARG, "scale does not match the network description");

@@ -34,11 +34,13 @@ struct RangeConst {
     // the derived factors 2(1 - Kr), 2(1 - Kb), 1 / Kg, 1 / (2(1 - Kb)), 1 / (2(1 - Kr))
     float kr, kb, kg, cr_r, cb_b, rkg, cb_s, cr_s;
     int yuv;  // the network sees Y'Cb'Cr' planes: no matrix either way
+    int transfer;  // nvisr_transfer: the network sees linear light (PQ / HLG)
 };
 
-RangeConst range_const(int bits, int range, int matrix, int yuv) {
+RangeConst range_const(int bits, int range, int matrix, int yuv, int transfer) {
     RangeConst r;
     r.yuv = yuv;
+    r.transfer = transfer;
     r.kr = matrix == NVISR_MATRIX_BT2020 ? 0.2627f : 0.2126f;
     r.kb = matrix == NVISR_MATRIX_BT2020 ? 0.0593f : 0.0722f;
     r.kg = 1.0f - r.kr - r.kb;
@@ -65,6 +67,36 @@ RangeConst range_const(int bits, int range, int matrix, int yuv) {
     r.y_rden = 1.0f / r.y_den;
     r.c_rden = 1.0f / r.c_den;
     return r;
+}
+
+// HDR transfer (SMPTE ST 2084 PQ, BT.2100 HLG), float32.  to_linear: coded R'G'B' value,
+// clamped to [0, 1] (where the functions are defined; the PQ EOTF has a pole above 1) ->
+// linear light; from_linear: linear light, clamped to [0, 1] -> coded value.
+constexpr float PQ_M1 = 2610.f / 16384.f, PQ_M2 = 2523.f / 4096.f * 128.f;
+constexpr float PQ_C1 = 3424.f / 4096.f, PQ_C2 = 2413.f / 4096.f * 32.f, PQ_C3 = 2392.f / 4096.f * 32.f;
+constexpr float HLG_A = 0.17883277f, HLG_B = 1.f - 4.f * HLG_A, HLG_C = 0.55991073f;
+
+__device__ __forceinline__ float to_linear(int tf, float e) {
+    if (tf == NVISR_TRANSFER_NONE) return e;
+    e = fminf(fmaxf(e, 0.f), 1.f);
+    if (tf == NVISR_TRANSFER_PQ) {
+        const float ep = powf(e, 1.f / PQ_M2);
+        return powf(fmaxf(ep - PQ_C1, 0.f) / (PQ_C2 - PQ_C3 * ep), 1.f / PQ_M1);
+    }
+    if (tf == NVISR_TRANSFER_HLG) return e <= 0.5f ? e * e / 3.f : (expf((e - HLG_C) / HLG_A) + HLG_B) / 12.f;
+    return e;
+}
+
+__device__ __forceinline__ float from_linear(int tf, float l) {
+    if (tf == NVISR_TRANSFER_PQ) {
+        const float ym = powf(fminf(fmaxf(l, 0.f), 1.f), PQ_M1);
+        return powf((PQ_C1 + PQ_C2 * ym) / (1.f + PQ_C3 * ym), PQ_M2);
+    }
+    if (tf == NVISR_TRANSFER_HLG) {
+        const float e = fminf(fmaxf(l, 0.f), 1.f);
+        return e <= 1.f / 12.f ? sqrtf(3.f * e) : HLG_A * logf(12.f * e - HLG_B) + HLG_C;
+    }
+    return l;
 }
 
 template <typename S>
@@ -143,6 +175,11 @@ __global__ void __launch_bounds__(256) ingest_kernel(
             r[e] = Y + rc.cr_r * cr;
             b[e] = Y + rc.cb_b * cb;
             g[e] = (Y - rc.kr * r[e] - rc.kb * b[e]) / rc.kg;
+        }
+        if (rc.transfer) {
+            r[e] = to_linear(rc.transfer, r[e]);
+            g[e] = to_linear(rc.transfer, g[e]);
+            b[e] = to_linear(rc.transfer, b[e]);
         }
     }
     const int64_t plane = pitch * H;
@@ -285,6 +322,11 @@ __global__ void __launch_bounds__(128) ingest420_kernel(
                 b[e] = Y + rc.cb_b * cb;
                 g[e] = (Y - rc.kr * r[e] - rc.kb * b[e]) * rc.rkg;
             }
+            if (rc.transfer) {
+                r[e] = to_linear(rc.transfer, r[e]);
+                g[e] = to_linear(rc.transfer, g[e]);
+                b[e] = to_linear(rc.transfer, b[e]);
+            }
         }
         float *o = out + (int64_t)y * pitch + x0;
         if (vec) {
@@ -357,7 +399,12 @@ __device__ __forceinline__ float out_at(const float *in, int64_t pitch, int64_t 
 
 __device__ __forceinline__ void rgb2ycc(const RangeConst &rc, float r, float g, float b, float &y, float &cb,
                                         float &cr) {
-    if (rc.yuv) {  // channels are Y'Cb'Cr' already
+    if (rc.transfer) {
+        r = from_linear(rc.transfer, r);
+        g = from_linear(rc.transfer, g);
+        b = from_linear(rc.transfer, b);
+    }
+    if (rc.yuv) {  // channels are Y'Cb'Cr' (or R'G'B' planes) already
         y = r;
         cb = g;
         cr = b;
@@ -793,7 +840,7 @@ cudaError_t launch_shuffle_planar(const float *src, int H, int W, int ry, int rx
 
 cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, const void *u, int64_t pu,
                           const void *v, int64_t pv, float *out, int64_t out_pitch, cudaStream_t st, int yuv) {
-    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix, yuv);
+    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix, yuv, f.transfer);
     if (f.subsampling == NVISR_SUB_420) {
         dim3 blk(128);
         dim3 grd((f.width + 8 * 128 - 1) / (8 * 128), (f.height + 1) / 2, 2);
@@ -822,7 +869,7 @@ cudaError_t launch_ingest(const nvisr_format &f, const void *y, int64_t py, cons
 cudaError_t launch_requant(const nvisr_format &f, const float *in, int64_t in_pitch, void *y, int64_t py,
                            void *u, int64_t pu, void *v, int64_t pv, cudaStream_t st, const SkipArgs *skip,
                            int yuv) {
-    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix, yuv);
+    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix, yuv, f.transfer);
     SkipArgs sk{};
     if (skip) sk = *skip;
     dim3 block(64);

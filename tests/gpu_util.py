@@ -5,9 +5,9 @@ import torch
 import oracle
 
 
-def fmt_dict(width, height, bits, sub="420", rng="limited", loc="left", matrix="bt709"):
+def fmt_dict(width, height, bits, sub="420", rng="limited", loc="left", matrix="bt709", transfer="none"):
     return dict(width=width, height=height, bit_depth=bits, subsampling=sub, range=rng, chroma_loc=loc,
-                matrix=matrix)
+                matrix=matrix, transfer=transfer)
 
 
 def to_dev(arr):
@@ -26,6 +26,7 @@ def from_dev(t, bits):
 def prequant(rgb, fmt):
     """Oracle requantisation values before rounding (to locate round-half ties)."""
     b, rg = fmt["bit_depth"], fmt["range"]
+    rgb = oracle.from_linear(np.asarray(rgb, np.float64), fmt.get("transfer", "none"))  # PQ / HLG
     if fmt.get("matrix") == "rgb":  # R'G'B' planes, luma range equations
         return {k: oracle.scale_luma(rgb[i], b, rg) for i, k in enumerate("YUV")}
     yp, cb, cr = oracle.rgb_to_ycbcr(rgb[0], rgb[1], rgb[2], fmt.get("matrix", "bt709"))

@@ -425,3 +425,23 @@ def test_rgb_format_checks():
         eng.filter(ytext, yblob, nv.fmt(48, 32, 8, "444", "full", "left", "rgb"),
                    nv.fmt(96, 64, 8, "444", "full", "left", "rgb"), "bf16")
     eng.close()
+
+
+def test_filter_hdr10_pq_fp32():
+    """HDR10 in and out (PQ, BT.2020, 10-bit 4:2:0 limited): the network runs on linear light.
+    FP32 only: a 16-bit network in linear light moves dark PQ codes by more than 1 (the
+    PQ curve is steep near black)."""
+    frames = synth.frames_textured(synth.BASE_SEED + 77, 5, 48, 32, 10, "420", "limited")
+    flags = np.zeros(5, bool)
+    fdi = fmt_dict(48, 32, 10, "420", "limited", "left", "bt2020", "pq")
+    fdo = fmt_dict(96, 64, 10, "420", "limited", "left", "bt2020", "pq")
+    text, blob = synth.net_config1()
+    ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo)
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(48, 32, 10, "420", "limited", "left", "bt2020", "pq"),
+                      nv.fmt(96, 64, 10, "420", "limited", "left", "bt2020", "pq"), "fp32")
+    assert len(outs) == len(ref) == 5
+    for got, r in zip(outs, ref):
+        for k in "YUV":
+            d = np.abs(got[k] - r[k])
+            assert d.max() <= 1, (k, d.max())
+            assert (d > 0).mean() < 0.01, (k, (d > 0).mean())

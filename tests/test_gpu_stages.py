@@ -120,6 +120,56 @@ def test_requant_matrix_and_depth_match_oracle(W, H, bits, sub, rng, loc, matrix
     assert_codes_match(got, prequant(rgb.astype(np.float64), fd), bits)
 
 
+TRANSFER_CASES = [  # HDR transfer (W, H, bits, subsampling, range, siting, matrix, transfer)
+    (64, 32, 10, "420", "limited", "left", "bt2020", "pq"),   # HDR10
+    (70, 34, 10, "444", "full", "center", "bt2020", "hlg"),
+    (48, 32, 12, "444", "full", "left", "rgb", "pq"),
+]
+
+
+@pytest.mark.parametrize("W,H,bits,sub,rng,loc,matrix,transfer", TRANSFER_CASES)
+def test_ingest_transfer_matches_oracle(W, H, bits, sub, rng, loc, matrix, transfer):
+    """Ingest to linear light (PQ EOTF / inverse HLG OETF after the matrix), float32 vs FP64."""
+    fr = synth.frames_textured(13, 1, W, H, bits, sub, rng)[0]
+    fd = fmt_dict(W, H, bits, sub, rng, loc, matrix, transfer)
+    f = nv.fmt(W, H, bits, sub, rng, loc, matrix, transfer)
+    pitch = (W + 3) // 4 * 4
+    out = torch.full((3, H, pitch), float("nan"), device="cuda")
+    nv.nvisr_ingest(f, to_dev(fr["Y"]), to_dev(fr["U"]), to_dev(fr["V"]), out)
+    torch.cuda.synchronize()
+    ref = oracle.ingest(fr, fd)
+    err = np.abs(out[:, :, :W].double().cpu().numpy() - ref)
+    # float32 powers: a few ulp of relative error, amplified by the PQ exponents
+    assert (err <= 2e-5 * (1.0 + np.abs(ref))).all(), err.max()
+
+
+@pytest.mark.parametrize("W,H,bits,sub,rng,loc,matrix,transfer", TRANSFER_CASES)
+def test_requant_transfer_matches_oracle(W, H, bits, sub, rng, loc, matrix, transfer):
+    """Requantise from linear light: clamp to [0, 1], inverse transfer, matrix.  The PQ
+    inverse raises to the power 78.84, so float32 codes may round apart from FP64 ones by
+    one code a little away from ties: every code within 1, nearly all equal."""
+    rs = np.random.default_rng(W * H + bits + 2)
+    lin = (rs.uniform(0.0, 1.0, size=(3, H, W)) ** 3 * 1.05 - 0.02).astype(np.float32)
+    fd = fmt_dict(W, H, bits, sub, rng, loc, matrix, transfer)
+    f = nv.fmt(W, H, bits, sub, rng, loc, matrix, transfer)
+    pitch = (W + 3) // 4 * 4
+    dev = torch.zeros((3, H, pitch), device="cuda")
+    dev[:, :, :W] = torch.from_numpy(lin).cuda()
+    dt = torch.uint8 if bits <= 8 else torch.int16
+    cw, ch = (W // 2, H // 2) if sub == "420" else (W, H)
+    y = torch.zeros((H, W), dtype=dt, device="cuda")
+    u = torch.zeros((ch, cw), dtype=dt, device="cuda")
+    v = torch.zeros((ch, cw), dtype=dt, device="cuda")
+    nv.nvisr_requant(f, dev, y, u, v)
+    torch.cuda.synchronize()
+    got = {"Y": from_dev(y, bits), "U": from_dev(u, bits), "V": from_dev(v, bits)}
+    ref = oracle.requantise(lin.astype(np.float64), fd)
+    for k in "YUV":
+        d = np.abs(got[k] - ref[k])
+        assert d.max() <= 1, (k, d.max())
+        assert (d > 0).mean() < 0.01, (k, (d > 0).mean())
+
+
 def _bf16(a):
     return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).double().numpy()
 

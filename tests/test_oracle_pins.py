@@ -124,6 +124,46 @@ def test_range_pins_high_bit_depths(bits):
     assert oracle.quantise(oracle.scale_luma(1.0, bits, "limited"), bits) == 235 * m
 
 
+def test_pq_published_anchors_and_round_trip():
+    """SMPTE ST 2084: 100 cd/m^2 (0.01 of the 10000 cd/m^2 range) codes to 0.508078 and
+    1000 cd/m^2 to 0.751827 (the values HDR10 tables give), 10000 cd/m^2 to 1; the EOTF
+    inverts the inverse EOTF."""
+    assert abs(oracle.pq_inverse_eotf(0.01) - 0.508078) < 1e-6
+    assert abs(oracle.pq_inverse_eotf(0.1) - 0.751827) < 1e-6
+    assert abs(oracle.pq_inverse_eotf(1.0) - 1.0) < 1e-15
+    y = np.geomspace(1e-6, 1.0, 200)
+    assert np.abs(oracle.pq_eotf(oracle.pq_inverse_eotf(y)) / y - 1.0).max() < 1e-10
+    e = np.linspace(0.0, 1.0, 101)
+    assert np.all(np.diff(oracle.pq_eotf(e)) >= 0.0)
+
+
+def test_hlg_knee_and_round_trip():
+    """BT.2100 HLG OETF: sqrt(3E) up to E = 1/12 (code 0.5), a ln(12E - b) + c above, the two
+    branches meeting at the knee; E = 1 codes to 1 (to the rounding of a); the inverse
+    inverts it."""
+    assert oracle.hlg_oetf(1.0 / 12.0) == 0.5
+    knee_log = oracle.HLG_A * np.log(12.0 / 12.0 - oracle.HLG_B) + oracle.HLG_C
+    assert abs(knee_log - 0.5) < 1e-12
+    assert abs(oracle.hlg_oetf(1.0) - 1.0) < 1e-7
+    e = np.linspace(0.0, 1.0, 301)
+    assert np.abs(oracle.hlg_inverse_oetf(oracle.hlg_oetf(e)) - e).max() < 1e-12
+
+
+@pytest.mark.parametrize("transfer", ["pq", "hlg"])
+def test_transfer_zero_residual_nearest_reproduces_input(transfer):
+    """A network in linear light (PQ or HLG in and out) with zero residual and nearest skip
+    returns its input codes: ingest's transfer and requantise's inverse cancel."""
+    text, blob = _identity_net()
+    rng = np.random.default_rng(11)
+    frames = [{k: rng.integers(64, 941, (12, 16)) for k in "YUV"} for _ in range(4)]
+    fmt = _fmt(10, "444", "limited", "left")
+    fmt["matrix"], fmt["transfer"] = "rgb", transfer
+    outs = oracle.run_filter(frames, np.zeros(4, bool), text, blob, fmt, fmt)
+    for f, o in zip(frames, outs):
+        for k in "YUV":
+            assert np.array_equal(o[k], np.repeat(np.repeat(f[k].astype(np.int64), 2, 0), 2, 1)), k
+
+
 @pytest.mark.parametrize("bits,rng_name", [(8, "full"), (10, "limited"), (12, "full"), (16, "limited")])
 def test_rgb_io_range_anchors_and_exact_round_trip(bits, rng_name):
     """RGB planes (Section 3.1: RGB or YUV I/O) take the luma range equations: the range
