@@ -17,8 +17,10 @@
  *
  * Conventions for every call:
  *  - Every function returns an nvisr_status (void destroy calls excepted);
- *    nothing throws across the ABI.  nvisr_last_error() gives a message for
- *    the most recent failure on this thread.
+ *    nothing throws across the ABI.  nvisr_last_error(engine) gives a message
+ *    for the most recent failure of a call on that engine (or on one of its
+ *    filters, batches or servers); nvisr_last_error(NULL) the most recent
+ *    failure of any call on this thread.
  *  - "device" pointers are CUDA device pointers of the engine's device;
  *    "host" pointers are ordinary (ideally pinned) host memory.  The caller
  *    owns every buffer it passes and keeps it alive for the call's duration.
@@ -34,7 +36,7 @@
 extern "C" {
 #endif
 
-#define NVISR_ABI_VERSION 1
+#define NVISR_ABI_VERSION 2
 
 typedef enum nvisr_status {
     NVISR_OK = 0,
@@ -121,11 +123,17 @@ typedef struct nvisr_filter_desc {
     int32_t calib_frames;        /* FP8: frames whose activations set the scales (0 = 4) */
 } nvisr_filter_desc;
 
+/* What an output frame is (nvisr_frame_info.kind). */
+enum {
+    NVISR_OUT_NETWORK = 0,       /* computed by the network */
+    NVISR_OUT_PASSTHROUGH = 1    /* an input frame output as it is (Interpolation without Double frame) */
+};
+
 typedef struct nvisr_frame_info {
     int64_t index;               /* output frame index (presentation order) */
     int64_t src_first, src_last; /* input frames the output depends on */
     int32_t scene;               /* scene number of the output's source */
-    int32_t reserved;
+    int32_t kind;                /* NVISR_OUT_NETWORK or NVISR_OUT_PASSTHROUGH */
 } nvisr_frame_info;
 
 typedef struct nvisr_engine nvisr_engine;
@@ -182,11 +190,19 @@ nvisr_status nvisr_flush(nvisr_filter *filter);
  * planes the call returns after the copy completes; while the copy runs (on
  * the engine's copy stream) the next ready output of a filter outside any
  * batch is already computed on the engine's stream.  Device planes are
- * written in stream order.  Group networks (Section 3.1) take n frames per
- * run (+1 with Extra frame, n <= 8 inputs) and emit n outputs per run (2n
- * with Double frame, <= 8); without Interpolation a scene's last run is moved
- * back inside the scene and the outputs an earlier run emitted are skipped
- * (Section 3.3).  info may be NULL. */
+ * written in stream order.
+ * Group networks (Section 3.1 flags, Section 3.3 rules) consume n frames per
+ * run and take n (+1 with Extra frame) frames, <= 8; the network computes n
+ * outputs per run (2n with Double frame, <= 8).  Runs tile each scene by n;
+ * frames past the scene end repeat its last frame; a run whose consumed
+ * frames would pass the scene end is moved back to end there when the scene
+ * holds n frames.  Every input frame gives 2 outputs with Interpolation or
+ * Double frame (doubled frame rate), else 1, each emitted once.  With
+ * Interpolation and without Double frame a frame's outputs are the frame
+ * itself (kind NVISR_OUT_PASSTHROUGH: its planes copied unchanged when the
+ * input and output formats are equal, else converted to the output format by
+ * ingest and requantise) then the network output that follows it; such
+ * filters need spatial scale 1.  info may be NULL. */
 nvisr_status nvisr_pull(nvisr_filter *filter, nvisr_planes *out, nvisr_frame_info *info);
 
 /* Number of outputs the filter can currently pull without more input. */
@@ -220,7 +236,12 @@ nvisr_status nvisr_filter_profile(nvisr_filter *filter, int32_t enable);
 nvisr_status nvisr_filter_profile_read(nvisr_filter *filter, nvisr_profile *out);
 
 const char *nvisr_status_string(nvisr_status status);
-const char *nvisr_last_error(void);
+/* Message of the most recent failure on `engine` (calls on the engine or on its
+ * filters, batches and servers), or, for NULL, of the calling thread's most
+ * recent failed call (the only record for calls that take no engine: stage
+ * entry points, host-only calls, a failed nvisr_engine_create).  The string is
+ * owned by the library and valid until the next failing call of that kind. */
+const char *nvisr_last_error(nvisr_engine *engine);
 
 /* ----------------------------------------------------------------------------
  * Stage entry points (each runs one hot-path stage on caller-owned device
@@ -248,12 +269,25 @@ nvisr_status nvisr_requant(const nvisr_format *fmt, const float *in_rgb, int64_t
 nvisr_status nvisr_tuple_map(const uint8_t *flags, int32_t nframes, int32_t T, int32_t *out);
 
 /* Group-model runs of one scene [s0, s1] (Section 3.1 flags, Section 3.3 rules):
- * runs of n (+1 with extra) frames; out_inputs receives runs*need indices and
- * out_skip the number of leading already-covered frames per run.  *nruns
- * receives the run count; max_runs bounds the output arrays. */
-nvisr_status nvisr_group_runs(int32_t s0, int32_t s1, int32_t n, int32_t extra, int32_t interp,
-                              int32_t max_runs, int32_t *out_inputs, int32_t *out_skip,
+ * runs consuming n frames and taking need = n (+1 with extra) frames;
+ * out_inputs receives runs*need indices, out_skip the number of leading
+ * consumed frames an earlier run covered and out_count the number the run
+ * covers first (the counts add up to the scene's length).  *nruns receives the
+ * run count; max_runs bounds the output arrays.  Host only. */
+nvisr_status nvisr_group_runs(int32_t s0, int32_t s1, int32_t n, int32_t extra, int32_t max_runs,
+                              int32_t *out_inputs, int32_t *out_skip, int32_t *out_count,
                               int32_t *nruns);
+
+/* Every output of a group-network stream of nframes frames, in presentation
+ * order, as nvisr_pull describes them after a flush (the filter's own
+ * bookkeeping, run without a device): kind[o] (nvisr_frame_info.kind),
+ * src_first[o], src_last[o] and net_k[o] (the network output index, -1 for a
+ * passed-through frame).  flags[k] != 0: frame k starts a scene.  *nout
+ * receives the output count; max_out bounds the arrays.  Host only. */
+nvisr_status nvisr_group_outputs(const uint8_t *flags, int32_t nframes, int32_t n, int32_t extra,
+                                 int32_t interp, int32_t dbl, int32_t max_out, int32_t *kind,
+                                 int32_t *src_first, int32_t *src_last, int32_t *net_k,
+                                 int32_t *nout);
 
 /* Frame-store layout of Section 3.3, Figure 1 for a batch of b groups of n+1
  * frames: cell_frame[(n+1)*b] receives, per column-first address, the frame
@@ -361,13 +395,17 @@ nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_
  *    any device work.  Need: (cin_pad + cout_pad * (res ? 2 : 1)) * H * W
  *    element bytes plus the weight image; 64 -> 64 channels with a residual
  *    fit ~43k pixels in FP32 and ~87k in BF16 / FP16;
- *  - precision is FP32, BF16 or FP16 (FP8 returns NVISR_UNSUPPORTED_FORMAT);
- *  - the area is shared by every call on a device: calls that overlap in time
- *    on one device (several threads or streams) race and must be serialised
- *    by the caller;
- *  - the first call on each device, made with that device current, looks up
- *    the area's address; make that first call before any stream capture.
- * Returns after the stream has finished the layer (it reads the error word). */
+ *  - precision is FP32, BF16 or FP16 (FP8 returns NVISR_UNSUPPORTED_FORMAT, an
+ *    unknown precision NVISR_INVALID_ARG);
+ *  - the area is shared by every call on a device, and keeps what the last
+ *    call left in it (each call clears what must start at zero): calls that
+ *    overlap in time on one device (several threads or streams) race and must
+ *    be serialised by the caller;
+ *  - the first call on each device (and again after the device's context is
+ *    re-created, e.g. by cudaDeviceReset), made with that device current,
+ *    looks up the area's address; make that first call before any stream
+ *    capture.
+ * Returns after synchronising `stream`: it reads the error word back. */
 nvisr_status nvisr_conv2d_static(int32_t precision, const float *x, int32_t cin, int32_t h, int32_t w,
                                  const float *weight, const float *bias, int32_t cout, int32_t k,
                                  int32_t act, const float *res, float *y, void *stream);
@@ -380,6 +418,16 @@ nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t
                          const float *offsets, const float *mask, int32_t groups,
                          const float *weight, const float *bias, int32_t cout, float *y,
                          void *stream);
+
+/* Fault drill for tests of the NVISR_DEVICE_TIMEOUT path (no counterpart in
+ * the paper).  While on (on != 0), the tensor-core kernels (convolutions and
+ * DCN) launched by the calling thread load no input, so their first pipeline
+ * wait runs out after its time bound (2 s): the CTA raises its abort flag,
+ * records the timeout in the engine's error word, lets its own copies and MMAs
+ * finish, frees its TMEM and returns, and the call that reads the error word
+ * returns NVISR_DEVICE_TIMEOUT.  Outputs of such calls are undefined.  0 turns
+ * the drill off; later calls run normally.  Host only; always returns OK. */
+nvisr_status nvisr_test_starve(int32_t on);
 
 /* Tensor-core self test: one 128x16 MMA of BF16 (K = 16) and one of FP8 E4M3
  * (K = 32) small-integer operands through shared-memory descriptors, TMEM

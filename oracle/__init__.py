@@ -34,8 +34,8 @@ from .colour import (HLG_A, HLG_B, HLG_C, KB, KG, KR, downsample_chroma, hlg_inv
                      pq_inverse_eotf, quantise, requantise, rgb_to_ycbcr, scale_chroma,
                      scale_luma, to_linear, upsample_chroma, ycbcr_to_rgb)
 from .grouping import (fig1_layout, fig1_next_batch_copy, fig1_slot_frames,
-                       group_output_count, group_runs, scene_of,
-                       scenes_from_flags, tuple_indices, tuple_map)
+                       group_output_count, group_outputs, group_runs, outputs_per_frame,
+                       scene_of, scenes_from_flags, tuple_indices, tuple_map)
 from .net import (Net, conv2d_direct, conv2d_im2col, dcn2d, leaky_relu,
                   oracle_threads, pixel_shuffle, sigmoid, upsample_bilinear,
                   upsample_nearest)
@@ -44,7 +44,8 @@ __all__ = [
     "HLG_A", "HLG_B", "HLG_C", "KB", "KG", "KR", "Net", "conv2d_direct", "conv2d_im2col", "dcn2d",
     "from_linear", "hlg_inverse_oetf", "hlg_oetf", "pq_eotf", "pq_inverse_eotf", "to_linear",
     "downsample_chroma", "fig1_layout", "fig1_next_batch_copy", "fig1_slot_frames",
-    "group_output_count", "group_runs", "ingest", "leaky_relu", "normalise_chroma",
+    "group_output_count", "group_outputs", "group_runs", "ingest", "outputs_per_frame",
+    "passthrough", "leaky_relu", "normalise_chroma",
     "normalise_luma", "oracle_threads", "pad_to_align", "pixel_shuffle", "quantise",
     "requantise", "rgb_to_ycbcr", "run_filter", "scale_chroma", "scale_luma",
     "scene_of", "scenes_from_flags", "sigmoid", "tuple_indices", "tuple_map",
@@ -62,6 +63,26 @@ def pad_to_align(rgb, align: int):
     return np.pad(rgb, ((0, 0), (0, ph), (0, pw)), mode="edge")
 
 
+def _same_format(a, b):
+    keys = ("width", "height", "bit_depth", "subsampling", "range", "chroma_loc", "matrix", "transfer")
+    dflt = {"matrix": "bt709", "transfer": "none"}
+    return all(a.get(k, dflt.get(k)) == b.get(k, dflt.get(k)) for k in keys)
+
+
+def passthrough(frame, in_fmt, out_fmt, domain="rgb", keep_float=False):
+    """An input frame output as it is (Interpolation without Double frame, Section 3.1).
+
+    Reading: with equal input and output formats the frame's planes are copied
+    unchanged; otherwise the frame is converted to the output format by the
+    filter's own format path with no network (ingest, then requantise).  With
+    keep_float the converted frame is returned before requantisation.
+    """
+    if _same_format(in_fmt, out_fmt):
+        return {k: np.array(frame[k]) for k in ("Y", "U", "V")}
+    rgb = ingest(frame, in_fmt, domain)
+    return rgb if keep_float else requantise(rgb, out_fmt, domain)
+
+
 def run_filter(frames, flags, net_text, blob, in_fmt, out_fmt, outputs=None, keep_float=False):
     """Run the whole filter over a clip.
 
@@ -69,7 +90,9 @@ def run_filter(frames, flags, net_text, blob, in_fmt, out_fmt, outputs=None, kee
     flags; in_fmt/out_fmt: dicts (bit_depth, subsampling, range, chroma_loc).
     outputs: optional iterable of output indices to compute (others skipped).
     Returns a list (presentation order) of output planes, or of float RGB
-    images when keep_float is set; skipped outputs are None.
+    images when keep_float is set; skipped outputs are None.  An input frame
+    passed through (Interpolation without Double frame) is a dict of integer
+    planes when it is copied unchanged, whatever keep_float says.
     """
     net = Net(net_text, blob)
     nframes = len(frames)
@@ -86,9 +109,9 @@ def run_filter(frames, flags, net_text, blob, in_fmt, out_fmt, outputs=None, kee
     want = None if outputs is None else set(outputs)
     results = []
 
-    def emit(img):
+    def finish(img):
         img = img[:, :oh, :ow]
-        results.append(img if keep_float else requantise(img, out_fmt, net.domain))
+        return img if keep_float else requantise(img, out_fmt, net.domain)
 
     if net.family == "tuple":
         for t in range(nframes):
@@ -96,20 +119,21 @@ def run_filter(frames, flags, net_text, blob, in_fmt, out_fmt, outputs=None, kee
                 results.append(None)
                 continue
             idx = tuple_indices(t, net.frames, *scene_of(t, scenes))
-            emit(net.forward([rgb(i) for i in idx])[0])
-    else:
-        interp = "interp" in net.flags
-        extra = "extra" in net.flags
-        double = "double" in net.flags
-        n = net.frames - (1 if extra else 0)
-        per_run = group_output_count(n, interp, double)
-        for s0, s1 in scenes:
-            for inputs, skip in group_runs(s0, s1, n, extra, interp):
-                base = len(results)
-                if want is not None and not any(base + k in want for k in range(per_run)):
-                    results.extend([None] * (per_run - skip))
-                    continue
-                outs = net.forward([rgb(i) for i in inputs])
-                for img in outs[skip:per_run]:
-                    emit(img)
+            results.append(finish(net.forward([rgb(i) for i in idx])[0]))
+        return results
+    extra = "extra" in net.flags
+    n = net.frames - (1 if extra else 0)
+    plan = group_outputs(flags, nframes, n, extra, "interp" in net.flags, "double" in net.flags)
+    run_cache = {}
+    for o, entry in enumerate(plan):
+        if want is not None and o not in want:
+            results.append(None)
+        elif entry[0] == "pass":
+            results.append(passthrough(frames[entry[1]], in_fmt, out_fmt, net.domain, keep_float))
+        else:
+            _, inputs, k = entry
+            if inputs not in run_cache:
+                run_cache.clear()
+                run_cache[inputs] = net.forward([rgb(i) for i in inputs])
+            results.append(finish(run_cache[inputs][k]))
     return results

@@ -14,11 +14,20 @@ arrive as a per-frame property (Section 3.2, "End User Usage").  Readings:
   j_k = clamp(t - r + k, s0(t), s1(t)), k = 0..T-1 (edge frames replicated,
   never mixed across a cut);
 * group model with n consumed frames per run (Section 3.1 flags): with the
-  Extra-frame flag a run takes n+1 frames; runs tile the scene by n; indices
-  past the scene end take the scene's last frame (interpolation: the last frame
-  duplicated; short scene: further duplication); a short last group of a
-  non-interpolating network is shifted back to end at the scene end
-  (recycling earlier frames) as long as the scene is long enough.
+  Extra-frame flag a run takes n+1 frames, the last being the next group's
+  first; runs tile the scene by n; indices past the scene end take the
+  scene's last frame (the interpolation network's last frame duplicated, and
+  a scene shorter than n duplicated further); a last group whose consumed
+  frames pass the scene end is moved back to end there, recycling frames of
+  the previous group, when the scene holds n frames;
+* every consumed frame of the scene gives its outputs exactly once
+  ("a complete set of rules to always output required number of frames"):
+  2 per frame with Interpolation (doubled frame rate) or Double frame (2n
+  network outputs per run), else 1; outputs an earlier run already emitted,
+  and outputs of duplicated frames past the scene end, are not emitted;
+* Interpolation without Double frame: the run's input frames are output as
+  they are, each followed by the network output that is its intermediate
+  frame (Section 3.1, "Double frame" flag).
 """
 from __future__ import annotations
 
@@ -49,31 +58,62 @@ def tuple_map(flags, nframes: int, T: int):
     return [tuple_indices(t, T, *scene_of(t, scenes)) for t in range(nframes)]
 
 
-def group_runs(s0: int, s1: int, n: int, extra: bool, interp: bool):
+def group_runs(s0: int, s1: int, n: int, extra: bool):
     """Network runs covering one scene [s0, s1] under the group model.
 
-    Returns a list of (inputs, skip): the run's input frame indices and how
-    many of its leading frames were already covered by an earlier run.
-    Runs nominally start at s0, s0+n, ...; each takes n (+1 with Extra frame)
-    frames; indices past s1 take s1 (duplication of the scene's last frame).
-    A non-interpolating network's last run that would pass s1 is moved back to
-    end at s1 when the scene holds enough frames (recycling frames of the
-    previous group); ``skip`` then counts the recycled frames.
+    Returns a list of (inputs, skip, count): the run's input frame indices, how
+    many of its leading consumed frames an earlier run already covered, and
+    how many consumed frames it covers for the first time.  Runs nominally
+    start at s0, s0+n, ...; each consumes n frames and takes n (+1 with Extra
+    frame) frames; indices past s1 take s1 (duplication of the scene's last
+    frame).  A run whose consumed frames would pass s1 is moved back to end at
+    s1 when the scene holds n frames (recycling frames of the previous group);
+    ``skip`` then counts the recycled frames.  The counts of a scene add up to
+    its length.
     """
     need = n + (1 if extra else 0)
     length = s1 - s0 + 1
     runs = []
     for nominal in range(s0, s1 + 1, n):
         start = nominal
-        if not interp and start + need - 1 > s1 and length >= need:
-            start = s1 - need + 1
-        runs.append(([min(start + k, s1) for k in range(need)], nominal - start))
+        if start + n - 1 > s1 and length >= n:
+            start = s1 - n + 1
+        count = min(start + n - 1, s1) - nominal + 1
+        runs.append(([min(start + k, s1) for k in range(need)], nominal - start, count))
     return runs
 
 
 def group_output_count(n: int, interp: bool, double: bool) -> int:
-    """Frames emitted per run: 2n with Double frame, else n (Section 3.1 flags)."""
+    """Network outputs per run: 2n with Double frame, else n (Section 3.1 flags)."""
     return 2 * n if double else n
+
+
+def outputs_per_frame(interp: bool, double: bool) -> int:
+    """Output frames per consumed input frame: 2 at doubled frame rate (Interpolation,
+    or Double frame's 2n outputs per n frames), else 1."""
+    return 2 if (interp or double) else 1
+
+
+def group_outputs(flags, nframes: int, n: int, extra: bool, interp: bool, double: bool):
+    """Every output of a group-model stream, in presentation order.
+
+    Each entry is ("net", inputs, k) -- output k of the network run on frames
+    ``inputs`` -- or ("pass", i) -- input frame i output as it is.  A run's
+    consumed frame j gives, with Interpolation and without Double frame, the
+    frame itself then network output j (its intermediate frame); with Double
+    frame, network outputs 2j and 2j+1; otherwise network output j.
+    """
+    q = outputs_per_frame(interp, double)
+    out = []
+    for s0, s1 in scenes_from_flags(flags, nframes):
+        for inputs, skip, count in group_runs(s0, s1, n, extra):
+            for j in range(skip, skip + count):
+                if interp and not double:
+                    out.append(("pass", inputs[j]))
+                    out.append(("net", tuple(inputs), j))
+                else:
+                    out.extend(("net", tuple(inputs), q * j + e) for e in range(q))
+    return out
 
 
 def fig1_layout(n: int, b: int):

@@ -19,7 +19,8 @@ from . import build as _build
 
 __all__ = [
     "Batch", "Engine", "Filter", "NvisrError", "Server", "PREC", "Status", "fmt", "lib", "load",
-    "nvisr_conv2d", "nvisr_conv2d_static", "nvisr_dcn2d", "nvisr_fig1_layout", "nvisr_group_runs",
+    "nvisr_conv2d", "nvisr_conv2d_static", "nvisr_dcn2d", "nvisr_fig1_layout", "nvisr_group_outputs",
+    "nvisr_group_runs",
     "nvisr_ingest", "nvisr_network_check", "nvisr_requant", "nvisr_selftest",
     "nvisr_tuple_map",
 ]
@@ -76,7 +77,10 @@ class FilterDesc(ctypes.Structure):
 
 class FrameInfo(ctypes.Structure):
     _fields_ = [("index", ctypes.c_int64), ("src_first", ctypes.c_int64), ("src_last", ctypes.c_int64),
-                ("scene", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("scene", ctypes.c_int32), ("kind", ctypes.c_int32)]
+
+
+OUT_NETWORK, OUT_PASSTHROUGH = 0, 1
 
 
 class Profile(ctypes.Structure):
@@ -105,17 +109,19 @@ _SIGS = {
     "nvisr_filter_profile": (_I32, [_VP, _I32]),
     "nvisr_filter_profile_read": (_I32, [_VP, ctypes.POINTER(Profile)]),
     "nvisr_status_string": (ctypes.c_char_p, [_I32]),
-    "nvisr_last_error": (ctypes.c_char_p, []),
+    "nvisr_last_error": (ctypes.c_char_p, [_VP]),
     "nvisr_network_check": (_I32, [ctypes.c_char_p, _I64]),
     "nvisr_ingest": (_I32, [ctypes.POINTER(Format), ctypes.POINTER(Planes), _VP, _I64, _VP]),
     "nvisr_requant": (_I32, [ctypes.POINTER(Format), _VP, _I64, ctypes.POINTER(Planes), _VP]),
     "nvisr_tuple_map": (_I32, [_U8P, _I32, _I32, _I32P]),
-    "nvisr_group_runs": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32P, _I32P, _I32P]),
+    "nvisr_group_runs": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32P, _I32P, _I32P, _I32P]),
+    "nvisr_group_outputs": (_I32, [_U8P, _I32, _I32, _I32, _I32, _I32, _I32, _I32P, _I32P, _I32P, _I32P, _I32P]),
     "nvisr_fig1_layout": (_I32, [_I32, _I32, _I32P, _I32P, _I32P]),
     "nvisr_conv2d": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _I32, _I32, _VP, _VP, _VP]),
     "nvisr_conv2d_static": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _I32, _I32, _VP, _VP, _VP]),
     "nvisr_dcn2d": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP, _VP, _I32, _VP, _VP]),
     "nvisr_selftest": (_I32, [_I32P, _I32P]),
+    "nvisr_test_starve": (_I32, [_I32]),
     "nvisr_selftest_swizzle": (_I32, [_I32P]),
     "nvisr_batch_create": (_I32, [_VP, ctypes.POINTER(_VP), _I32, ctypes.POINTER(_VP)]),
     "nvisr_batch_step": (_I32, [_VP, _I32P]),
@@ -158,7 +164,7 @@ def lib():
 
 def _check(status, what):
     if status < 0:
-        msg = _LIB.nvisr_last_error().decode(errors="replace")
+        msg = _LIB.nvisr_last_error(None).decode(errors="replace")
         raise NvisrError(status, f"{what}: {msg}")
     return status
 
@@ -269,16 +275,32 @@ def nvisr_tuple_map(flags, T):
     return out
 
 
-def nvisr_group_runs(s0, s1, n, extra, interp):
+def nvisr_group_runs(s0, s1, n, extra):
+    """[(inputs, skip, count)] of the runs covering scene [s0, s1] (host only)."""
     load()
     need = n + (1 if extra else 0)
     maxr = (s1 - s0) // n + 2
     ins = np.zeros(maxr * need, np.int32)
     skip = np.zeros(maxr, np.int32)
+    cnt = np.zeros(maxr, np.int32)
     nr = ctypes.c_int32(0)
-    _check(_LIB.nvisr_group_runs(s0, s1, n, int(extra), int(interp), maxr, ins.ctypes.data_as(_I32P),
-                                 skip.ctypes.data_as(_I32P), ctypes.byref(nr)), "nvisr_group_runs")
-    return [(list(map(int, ins[i * need:(i + 1) * need])), int(skip[i])) for i in range(nr.value)]
+    _check(_LIB.nvisr_group_runs(s0, s1, n, int(extra), maxr, ins.ctypes.data_as(_I32P),
+                                 skip.ctypes.data_as(_I32P), cnt.ctypes.data_as(_I32P), ctypes.byref(nr)),
+           "nvisr_group_runs")
+    return [(list(map(int, ins[i * need:(i + 1) * need])), int(skip[i]), int(cnt[i])) for i in range(nr.value)]
+
+
+def nvisr_group_outputs(flags, n, extra, interp, double):
+    """Every output of a flushed group-network stream: [(kind, src_first, src_last, net_k)] (host only)."""
+    load()
+    flags = np.ascontiguousarray(np.asarray(flags, np.uint8))
+    cap = 2 * len(flags) + 1
+    arrs = [np.zeros(cap, np.int32) for _ in range(4)]
+    nout = ctypes.c_int32(0)
+    _check(_LIB.nvisr_group_outputs(flags.ctypes.data_as(_U8P), len(flags), n, int(extra), int(interp),
+                                    int(double), cap, *[a.ctypes.data_as(_I32P) for a in arrs],
+                                    ctypes.byref(nout)), "nvisr_group_outputs")
+    return [tuple(int(a[o]) for a in arrs) for o in range(nout.value)]
 
 
 def nvisr_fig1_layout(n, b):
@@ -294,7 +316,13 @@ def nvisr_fig1_layout(n, b):
 def nvisr_network_check(text, count):
     load()
     st = _LIB.nvisr_network_check(text.encode(), int(count))
-    return st, _LIB.nvisr_last_error().decode()
+    return st, _LIB.nvisr_last_error(None).decode()
+
+
+def nvisr_test_starve(on):
+    """Fault drill (tests only): tensor-core kernels of this thread load no input while on."""
+    load()
+    _check(_LIB.nvisr_test_starve(1 if on else 0), "nvisr_test_starve")
 
 
 def nvisr_selftest():
@@ -330,6 +358,10 @@ class Engine:
 
     def bytes_in_use(self):
         return int(_LIB.nvisr_engine_bytes_in_use(self.h))
+
+    def last_error(self):
+        """Message of the most recent failed call on this engine or its filters."""
+        return _LIB.nvisr_last_error(self.h).decode(errors="replace")
 
     def step(self, max_outputs=1 << 30):
         n = ctypes.c_int32(0)

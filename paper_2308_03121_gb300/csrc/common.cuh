@@ -32,8 +32,14 @@ inline int layout_cpc(int dt, int cpad) {
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 inline int64_t round_up64(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-// Thread-local last error message (nvisr_last_error).
+// Last error message (nvisr_last_error): kept per thread, and per engine for
+// the calls an ErrScope marks as working on that engine.
 void set_error(const std::string &msg);
+struct ErrScope {
+    explicit ErrScope(nvisr_engine *e);
+    ~ErrScope();
+    nvisr_engine *prev;
+};
 nvisr_status cuda_status(cudaError_t e, const char *where);
 
 #define NVISR_TRY_CUDA(expr)                                                   \
@@ -224,6 +230,7 @@ struct DcnArgs {
     int in_dt, out_dt;
     float acc_scale, out_scale;
     int *err;
+    int starve;              // test drill: the gather loads nothing, the pipeline waits run out
 };
 cudaError_t launch_dcn_simt(const DcnArgs &a, cudaStream_t st);
 cudaError_t launch_dcn_tc(const DcnArgs &a, cudaStream_t st);
@@ -232,6 +239,10 @@ cudaError_t launch_dcn_tc(const DcnArgs &a, cudaStream_t st);
 cudaError_t launch_dcn_relayout8(const void *x, int cpad, int H, int W, int x_cpc, void *y, cudaStream_t st);
 
 int device_sm_count();
+
+// Test drill of the calling thread (nvisr_test_starve): when set, the tensor-core
+// kernels it launches load no input, so their first pipeline wait runs out.
+int test_starve();
 
 // Launches a tensor-core kernel with programmatic stream serialization, so that its CTAs may
 // start (barriers, TMEM, weights) while the stream's previous kernel drains; the kernel waits

@@ -20,6 +20,7 @@
 // per-tensor scale on the host side) is not offered here.
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -33,9 +34,15 @@ nvisr_status cuda_status(cudaError_t e, const char *where);
 
 namespace {
 
-constexpr int kMaxDevices = 64;
+// The area's address per (device, context): a context created anew for a device
+// (after cudaDeviceReset, say) loads the module again, at a new address.
+struct AreaRec {
+    int dev;
+    void *ctx;
+    uint8_t *ptr;
+};
 std::mutex g_area_mu;
-uint8_t *g_area[kMaxDevices] = {nullptr};
+std::vector<AreaRec> g_area;
 
 // SIMT image [cin_pad][k*k][cout_pad] float32, written whole (padding = 0).
 __global__ void simt_weights_kernel(const float *__restrict__ w, int cout, int cin, int kk, int cin_pad,
@@ -114,18 +121,39 @@ nvisr_status fail(nvisr_status s, const std::string &msg) {
         if (e_ != cudaSuccess) return cuda_status(e_, "conv2d_static"); \
     } while (0)
 
-// Looks up (once per device, with that device current) the address of the area.
+// The current context (the driver's cuCtxGetCurrent, reached through the runtime).
+void *current_context() {
+    typedef int (*CtxGetCurrent)(void **);
+    static CtxGetCurrent fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            return (CtxGetCurrent)p;
+        return (CtxGetCurrent) nullptr;
+    }();
+    void *ctx = nullptr;
+    if (fn) fn(&ctx);
+    return ctx;
+}
+
+// Set-up: looks up the address of the area, once per device and context, with
+// that device current.
 nvisr_status area_for_current_device(uint8_t **out) {
     int dev = -1;
     CS_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(NVISR_INVALID_ARG, "conv2d_static: device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_area_mu);
-    if (!g_area[dev]) {
-        void *p = nullptr;
-        CS_TRY(cudaGetSymbolAddress(&p, conv_static_scratch));
-        g_area[dev] = static_cast<uint8_t *>(p);
-    }
-    *out = g_area[dev];
+    if (void *ctx = current_context())
+        for (const AreaRec &r : g_area)
+            if (r.dev == dev && r.ctx == ctx) {
+                *out = r.ptr;
+                return NVISR_OK;
+            }
+    // no context yet, or a new one: the lookup also initialises the device's context
+    void *p = nullptr;
+    CS_TRY(cudaGetSymbolAddress(&p, conv_static_scratch));
+    g_area.push_back({dev, current_context(), static_cast<uint8_t *>(p)});
+    *out = static_cast<uint8_t *>(p);
     return NVISR_OK;
 }
 
@@ -144,7 +172,9 @@ extern "C" nvisr_status nvisr_conv2d_static(int32_t precision, const float *x, i
                                             int32_t act, const float *res, float *y, void *stream) {
     if (!x || !weight || !y || cin < 1 || cout < 1 || h < 1 || w < 1 || (k != 1 && k != 3) || act < 0 || act > 1)
         return fail(NVISR_INVALID_ARG, "conv2d_static: bad arguments");
-    if (precision < NVISR_PREC_FP32 || precision > NVISR_PREC_FP16)
+    if (precision < NVISR_PREC_FP32 || precision > NVISR_PREC_FP8)
+        return fail(NVISR_INVALID_ARG, "conv2d_static: unknown precision");
+    if (precision == NVISR_PREC_FP8)
         return fail(NVISR_UNSUPPORTED_FORMAT, "conv2d_static: precision must be FP32, BF16 or FP16");
     const uint64_t cap = NVISR_CONV2D_STATIC_SCRATCH_BYTES;
     if ((uint64_t)cin > cap || (uint64_t)cout > cap || (uint64_t)h * (uint64_t)w > cap)

@@ -79,6 +79,7 @@ struct TcParams {
     int ntup;                         // row kernel, 16-channel head: > 0 = read the tuple's ntup float32
     int tslot[8];                     //   frames from the ring (slots tslot[]) instead of a packed tensor
     int *err;
+    int starve;                       // test drill: the producer loads no input, the pipeline waits run out
 };
 
 template <int DT>
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
     uint64_t *wbar = tempty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint64_t *drain = reinterpret_cast<uint64_t *>(smem + 256);  // the issuer's MMAs, after an abort
     float *sbias = reinterpret_cast<float *>(smem + 512);  // this slice's NS biases
     uint8_t *wsm = smem + SMEM_HDR;
     uint8_t *stage0 = wsm + ((p.wbytes + 1023) & ~1023u);
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
             mbar_init(&tempty[a], NEPI);
         }
         mbar_init(wbar, 1);
+        mbar_init(drain, 1);
         *abort = 0;
         fence_mbarrier_init();
     }
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
             uint32_t ph = 0;
             int issued = 0;
             bool ok = true;
-            for (int t = cta0; t < ntiles && ok; t += cta_stride) {
+            for (int t = cta0; t < ntiles && ok && !p.starve; t += cta_stride) {
                 const int img = t / (tiles_x * p.H);
                 const int r = t - img * tiles_x * p.H;
                 const int y = r / tiles_x;
@@ -325,6 +328,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
             }
             // drain: MMAs must finish before TMEM is released
             if (last_a >= 0) mbar_wait_bounded(&tfull[last_a], last_par, nullptr, WAIT_NS);
+            if (*abort) {
+                // an early exit may leave MMAs of an unfinished tile, which no tile commit covers
+                umma_commit(drain);
+                mbar_wait_bounded(drain, 0, nullptr, WAIT_NS);
+            }
         }
     } else {
         // ---------------- epilogue: warps 2..9; warp w owns TMEM lane quadrant (w % 4)
@@ -632,6 +640,7 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
     // input rows (global count) whose input has landed and whose fresh TMEM slot is
     // drained, published by the wait warp for the MMA issuer
     int *ready = reinterpret_cast<int *>(tmem_slot + 4);
+    uint64_t *drain = reinterpret_cast<uint64_t *>(smem + 448);  // the issuer's MMAs, after an abort
     float *sbias = reinterpret_cast<float *>(smem + 512);
     uint8_t *wsm = smem + SMEM_HDR;
     uint8_t *stage0 = wsm + 3 * WKX;
@@ -704,6 +713,7 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
         mbar_init(&resfull[0], 1);
         mbar_init(&resfull[1], 1);
         mbar_init(wbar, 1);
+        mbar_init(drain, 1);
         *abort = 0;
         grp_stop[0] = 0;
         grp_stop[1] = 0;
@@ -763,7 +773,7 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
             strip_of(sidx, img, x0, ra, rb, pi);
             for (int r = ra - 1; r <= rb; ++r, ++gin) {
                 if (loader && lane == 0) {
-                    while (ok && issued < gin + NST32 && t_next()) {
+                    while (ok && !p.starve && issued < gin + NST32 && t_next()) {
                         const int k = issued % NST32;
                         // the slot's previous row (issued - NST32 < gin) was converted by this warp;
                         // the wait covers warp 11's half
@@ -848,7 +858,7 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
             // in the prologue)
             int gin = 0;
             bool ok = true;
-            for (int sidx = cta0; sidx < nstrips && ok; sidx += cstride) {
+            for (int sidx = cta0; sidx < nstrips && ok && !p.starve; sidx += cstride) {
                 int img, x0, ra, rb, pi;
                 strip_of(sidx, img, x0, ra, rb, pi);
                 for (int r = ra - 1; r <= rb; ++r, ++gin) {
@@ -1041,6 +1051,11 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                 gout += rb - ra;
             }
             if (last_slot >= 0) mbar_wait_bounded(&rowdone[last_slot], last_par, nullptr, WAIT_NS);
+            if (*abort) {
+                // an early exit may leave MMAs of a strip's first row, which no row commit covers
+                umma_commit(drain);
+                mbar_wait_bounded(drain, 0, nullptr, WAIT_NS);
+            }
         }
     } else if (warp == 11) {
         // the 16-channel head's second converter; idle unless the head reads the tuple frames
@@ -1855,6 +1870,7 @@ TcParams rows_params(const ConvArgs &a) {
     p.acc_scale = a.acc_scale; p.out_scale = a.out_scale; p.res_scale = 1.0f / a.out_scale;
     p.y2 = static_cast<uint8_t *>(a.y2); p.y2_scale = a.y2_scale; p.amax = a.amax;
     p.err = a.err;
+    p.starve = test_starve();
     return p;
 }
 
@@ -2125,6 +2141,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
     p.y2 = static_cast<uint8_t *>(a.y2); p.y2_scale = a.y2_scale; p.amax = a.amax;
     p.ps_out = a.ps_out; p.ps_pitch = a.ps_pitch; p.skip = a; p.ps_act = a.ps_act;
     p.err = a.err;
+    p.starve = test_starve();
     return v->fn(map, p, st);
 }
 

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                 mk[h] = __ldg(a.om + oms + pix4);
             }
         };
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int t = blockIdx.x; t < ntiles && ok && !a.starve; t += gridDim.x) {
             const int y = t / tiles_x;
             const int xb = (t - y * tiles_x) * TM;
             for (int k = 0; k < 9; ++k) {
@@ -442,6 +442,7 @@ cudaError_t launch_dcn_relayout8(const void *x, int cpad, int H, int W, int x_cp
 
 cudaError_t launch_dcn_tc(const DcnArgs &a0, cudaStream_t st) {
     DcnArgs a = a0;
+    a.starve = test_starve();
     if (a.x_cpc == 0) a.x_cpc = 8;
     if (a.y_cpc == 0) a.y_cpc = 8;
     if (a.cin_pad != 64 || a.cout_pad != 64 || (a.cin_pad / a.groups) % 8) return cudaErrorNotSupported;

@@ -29,8 +29,13 @@ int tc_probe_sw128(int *dev_out16, cudaStream_t st);
 // ---------------------------------------------------------------- errors
 
 static thread_local std::string g_last_error;
+static thread_local nvisr_engine *g_err_engine = nullptr;  // engine of the ABI call in progress
+static thread_local int g_test_starve = 0;
 
-void set_error(const std::string &msg) { g_last_error = msg; }
+int test_starve() { return g_test_starve; }
+
+ErrScope::ErrScope(nvisr_engine *e) : prev(g_err_engine) { g_err_engine = e; }
+ErrScope::~ErrScope() { g_err_engine = prev; }
 
 nvisr_status cuda_status(cudaError_t e, const char *where) {
     set_error(std::string(where) + ": " + cudaGetErrorString(e));
@@ -74,7 +79,17 @@ struct nvisr_engine {
     int *err_word = nullptr;  // device error word shared by this engine's kernels
     int *err_host = nullptr;  // pinned host copy of it, read after a pull's copies
     std::vector<nvisr_filter *> filters;
+    std::string last_error;  // message of the most recent failure of a call on this engine
 };
+
+namespace nvisr {
+// The message goes to the calling thread and, inside an ABI call on an engine
+// (or one of its filters, batches or servers), to that engine too.
+void set_error(const std::string &msg) {
+    g_last_error = msg;
+    if (g_err_engine) g_err_engine->last_error = msg;
+}
+}  // namespace nvisr
 
 namespace {
 
@@ -219,9 +234,16 @@ struct nvisr_filter {
     float *final_f32 = nullptr;    // its float32 output, blocked [4][H][W][4]
     float *out_rgb[8] = {};   // planar float32 residuals [3][sH][opitch], one per output of a run
     SkipArgs skip[8] = {};    // skip path of each output slot (added by requantise)
-    // group family (Section 3.1): n frames per run (+1 with Extra frame), run_out outputs per run
+    // group family (Section 3.1): n frames per run (+1 with Extra frame), run_out network
+    // outputs per run
     int grp_n = 1, grp_need = 1, run_out = 1;
-    bool grp_interp = false;
+    // Interpolation without Double frame: input frames are outputs too.  With equal input and
+    // output formats they are copied unchanged from raw[] (the pushed planes, one ring slot
+    // per frame, written on the compute stream); otherwise requantise converts the ring slot.
+    bool passthru = false;
+    bool pass_copy = false;
+    void *raw[3] = {nullptr, nullptr, nullptr};
+    int64_t raw_slot_bytes[3] = {0, 0, 0};
     int64_t opitch = 0;
     void *ostage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // alternate per pull
     int64_t ostage_pitch[3] = {0, 0, 0};
@@ -371,54 +393,74 @@ bool tuple_ready(const nvisr_filter *f, int64_t t, std::vector<int64_t> *idx) {
     return true;
 }
 
-// Group family (n = 1, Extra frame, Interpolation, Double frame): run i uses
-// frames (i, min(i+1, s1)) and emits outputs 2i, 2i+1.
 // Group family: where output o comes from.  Scenes are cut by the per-frame
 // flags; a scene [s0, s1] is covered by runs at nominal starts s0, s0 + n, ...,
-// each taking need = n (+1 with Extra frame) frames, indices past s1 taking s1.
-// Without Interpolation a run that would pass s1 is moved back to end at s1 when
-// the scene holds need frames, and its first (nominal - start) outputs, already
-// emitted by the previous run, are dropped (Section 3.3).  A run is known once
-// its frames are pushed inside its scene, or once the scene is closed (a later
-// cut is known or the stream ended).
+// each consuming n frames and taking need = n (+1 with Extra frame) frames,
+// indices past s1 taking s1 (Section 3.3: the interpolation network's last
+// frame duplicated, a short scene duplicated further).  A run whose consumed
+// frames would pass s1 is moved back to end at s1 when the scene holds n
+// frames (recycling frames of the previous group).  Each consumed frame gives
+// its outputs once: q = 2 of them with Interpolation (doubled frame rate) or
+// Double frame, else 1; the outputs of frames an earlier run covered, and of
+// duplicated frames past s1, are not emitted.  With Interpolation and without
+// Double frame a frame's two outputs are the frame itself, passed through,
+// then the network output that is its intermediate frame (Section 3.1).  A run
+// is known once its frames are pushed inside its scene, or once the scene is
+// closed (a later cut is known or the stream ended).
 struct RunLoc {
     int64_t key = -1;             // nominal start frame (unique per run)
     int64_t oldest = 0;           // earliest frame the run may read (its start once known)
     std::vector<int64_t> inputs;  // the run's input frames (known runs)
-    int k = 0;                    // o's index among the run's outputs
+    int k = 0;                    // network output index (pass = false)
+    bool pass = false;            // o is input frame `frame` passed through
+    int64_t frame = -1;
 };
+
+// Form of the run at `nominal` in scene [s0, s1]: its first frame, the number
+// of leading consumed frames an earlier run covered, and the number it covers first.
+void run_form(int64_t nominal, int64_t s0, int64_t s1, int n, int64_t *start, int *skip, int *count) {
+    int64_t st = nominal;
+    if (st + n - 1 > s1 && s1 - s0 + 1 >= n) st = s1 - n + 1;
+    *start = st;
+    *skip = (int)(nominal - st);
+    *count = (int)(std::min<int64_t>(st + n - 1, s1) - nominal + 1);
+}
+
+// Outputs per consumed frame.
+int group_q(const nvisr_filter *f) { return (f->net.interp || f->net.dbl) ? 2 : 1; }
 
 // True when output o's run is known (and then *loc describes it); false with
 // loc->oldest set to a lower bound of the frames that run will read.
 bool group_locate(const nvisr_filter *f, int64_t o, RunLoc *loc) {
-    const int n = f->grp_n, need = f->grp_need, R = f->run_out;
+    const int n = f->grp_n, need = f->grp_need, q = group_q(f);
+    const bool pass = f->net.interp && !f->net.dbl;
     int64_t base = 0, s0 = 0;
     loc->oldest = 0;
     while (s0 < f->pushed) {
         int64_t s1 = s0;
         while (s1 + 1 < f->pushed && !f->cut[(size_t)(s1 + 1)]) ++s1;
         const bool closed = s1 + 1 < f->pushed || f->eos;
-        const int64_t len = s1 - s0 + 1;
         for (int64_t nominal = s0; nominal <= s1; nominal += n) {
-            int64_t start = nominal;
-            const bool past = start + need - 1 > s1;
-            if (past && !closed) {
+            if (nominal + need - 1 > s1 && !closed) {
                 // the run's frames are not all pushed and its form is not final yet
-                loc->oldest = f->grp_interp ? nominal : std::max<int64_t>(s0, nominal - need + 1);
+                loc->oldest = std::max<int64_t>(s0, nominal - n + 1);
                 return false;
             }
-            if (past && !f->grp_interp && len >= need) start = s1 - need + 1;
-            const int skip = (int)(nominal - start);
-            const int cnt = R - skip;
-            if (o < base + cnt) {
+            int64_t start;
+            int skip, count;
+            run_form(nominal, s0, s1, n, &start, &skip, &count);
+            if (o < base + (int64_t)q * count) {
+                const int j = q * skip + (int)(o - base);  // entry among the run's q * n
                 loc->key = nominal;
                 loc->oldest = start;
                 loc->inputs.clear();
                 for (int k = 0; k < need; ++k) loc->inputs.push_back(std::min(start + k, s1));
-                loc->k = skip + (int)(o - base);
+                loc->pass = pass && j % 2 == 0;
+                loc->frame = loc->pass ? start + j / 2 : -1;
+                loc->k = pass ? j / 2 : j;
                 return true;
             }
-            base += cnt;
+            base += (int64_t)q * count;
         }
         s0 = s1 + 1;
     }
@@ -426,23 +468,8 @@ bool group_locate(const nvisr_filter *f, int64_t o, RunLoc *loc) {
     return false;
 }
 
-// Output count of a group-family stream once it has ended.
-int64_t group_total(const nvisr_filter *f) {
-    const int n = f->grp_n, need = f->grp_need, R = f->run_out;
-    int64_t total = 0, s0 = 0;
-    while (s0 < f->pushed) {
-        int64_t s1 = s0;
-        while (s1 + 1 < f->pushed && !f->cut[(size_t)(s1 + 1)]) ++s1;
-        const int64_t len = s1 - s0 + 1;
-        for (int64_t nominal = s0; nominal <= s1; nominal += n) {
-            int64_t start = nominal;
-            if (start + need - 1 > s1 && !f->grp_interp && len >= need) start = s1 - need + 1;
-            total += R - (nominal - start);
-        }
-        s0 = s1 + 1;
-    }
-    return total;
-}
+// Output count of a group-family stream once it has ended: every frame gives q.
+int64_t group_total(const nvisr_filter *f) { return (int64_t)group_q(f) * f->pushed; }
 
 bool group_ready(const nvisr_filter *f, int64_t o, RunLoc *loc) {
     RunLoc tmp;
@@ -812,8 +839,10 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
         if (L.psx != L.psy) return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: PixelShuffle(2) only");
     f->grp_n = net.frames - (net.extra ? 1 : 0);
     f->grp_need = net.frames;
-    f->grp_interp = net.interp;
     f->run_out = net.dbl ? 2 * f->grp_n : f->grp_n;
+    if (net.interp && !net.dbl && net.scale != 1)
+        return fail(NVISR_UNSUPPORTED_FORMAT, "Interpolation without Double frame outputs the input frames as they "
+                                              "are: the spatial scale must be 1");
     if (f->grp_n < 1 || net.frames > 8 || f->run_out > 8)
         return fail(NVISR_UNSUPPORTED_FORMAT, "group networks: at most 8 input frames and 8 outputs per run");
     if ((int)net.outputs.size() != f->run_out)
@@ -927,9 +956,20 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
             if (st.add_t < 0 || f->tensors[st.add_t].C != L.cout) return fail(NVISR_BAD_NETWORK, "bad add source");
         }
         if (out_index.count(L.name)) {
-            if (L.op != "conv" || L.ps != 2 || L.cout != 12) return fail(NVISR_UNSUPPORTED_FORMAT, "output layers: conv -> 12 ch + PixelShuffle(2)");
-            if (src.H * 2 != H * net.scale || src.W * 2 != W * net.scale)
+            // output layers: conv -> 12 channels + PixelShuffle(2), or at scale 1 a plain
+            // conv -> 3 channels (float32 out, laid out planar by the shuffle kernel)
+            const bool plain = net.scale == 1;
+            if (plain ? (L.op != "conv" || L.ps || L.psx != 1 || L.psy != 1 || L.cout != 3 || L.k != 3)
+                      : (L.op != "conv" || L.ps != 2 || L.cout != 12))
+                return fail(NVISR_UNSUPPORTED_FORMAT, plain ? "output layers at scale 1: 3x3 conv -> 3 channels"
+                                                            : "output layers: conv -> 12 ch + PixelShuffle(2)");
+            if ((plain ? src.H != H || src.W != W : src.H * 2 != H * net.scale || src.W * 2 != W * net.scale))
                 return fail(NVISR_UNSUPPORTED_FORMAT, "output layer " + L.name + ": size is not scale x input");
+            if (plain) {
+                st.plain = true;
+                st.psy = st.psx = 1;
+                f->plain_final = true;
+            }
             st.out_t = -1;
             st.out_index = out_index[L.name];
             for (const std::string &n : net.outputs[st.out_index].skip) {
@@ -1292,6 +1332,7 @@ nvisr_status compute_output(nvisr_filter *f, int64_t o) {
     if (f->net.family == "group") {
         RunLoc loc;
         if (!group_locate(f, o, &loc)) return NVISR_AGAIN;
+        if (loc.pass) return NVISR_OK;                   // an input frame: nothing to compute
         if (f->cached_run == loc.key) return NVISR_OK;  // an earlier output of the same run computed it
         nvisr_status s = forward_group(f, loc.inputs);
         if (s == NVISR_OK) f->cached_run = loc.key;
@@ -1305,16 +1346,33 @@ nvisr_status compute_output(nvisr_filter *f, int64_t o) {
     return forward_tuple(f, idx, false);
 }
 
-int output_slot(const nvisr_filter *f, int64_t o) {
-    if (f->net.family != "group") return 0;
+// Where output o's planes come from: network output slot `slot`, or input frame
+// `frame` passed through (group family, Interpolation without Double frame).
+struct OutSrc {
+    int slot = 0;
+    int64_t frame = -1;
+};
+
+OutSrc output_source(const nvisr_filter *f, int64_t o) {
+    OutSrc r;
+    if (f->net.family != "group") return r;
     RunLoc loc;
-    return group_locate(f, o, &loc) ? loc.k : 0;
+    if (!group_locate(f, o, &loc)) return r;
+    if (loc.pass) r.frame = loc.frame;
+    else r.slot = loc.k;
+    return r;
 }
 
-// Requantises output slot `slot` into the caller's device planes, or into the
-// current staging buffer followed by its D2H copy (and the error word's) on the
-// copy stream; write_output_end waits for those copies.
-nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, int slot) {
+const void *raw_plane(const nvisr_filter *f, int64_t frame, int p) {
+    return (const uint8_t *)f->raw[p] + (frame % f->ring) * f->raw_slot_bytes[p];
+}
+
+// Writes output `src` into the caller's device planes, or into the current
+// staging buffer followed by its D2H copy (and the error word's) on the copy
+// stream; write_output_end waits for those copies.  A network output is
+// requantised (with its skip); a passed-through input frame is copied from its
+// raw planes, or requantised from its ring slot into the output format.
+nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, OutSrc src) {
     cudaStream_t st = f->eng->stream;
     const nvisr_format &of = f->out_fmt;
     void *dst[3];
@@ -1323,13 +1381,23 @@ nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, int slot) {
         dst[p] = out->on_device ? out->data[p] : f->ostage[f->obuf][p];
         pitch[p] = out->on_device ? out->pitch[p] : f->ostage_pitch[p];
     }
-    cudaError_t e;
-    {
-        ProfScope ps(f, NVISR_K_REQUANT);
-        e = launch_requant(of, f->out_rgb[slot], f->opitch, dst[0], pitch[0], dst[1], pitch[1], dst[2], pitch[2], st,
-                           &f->skip[slot], f->net.yuv ? 1 : 0);
+    if (src.frame >= 0 && f->pass_copy) {
+        prof_gap(f);
+        for (int p = 0; p < 3; ++p)
+            NVISR_TRY_CUDA(cudaMemcpy2DAsync(dst[p], pitch[p], raw_plane(f, src.frame, p), f->stage_pitch[p],
+                                             plane_row_bytes(of, p), plane_rows(of, p), cudaMemcpyDeviceToDevice, st));
+    } else {
+        cudaError_t e;
+        SkipArgs none{};
+        const bool pass = src.frame >= 0;
+        {
+            ProfScope ps(f, NVISR_K_REQUANT);
+            e = launch_requant(of, pass ? ring_slot(f, src.frame) : f->out_rgb[src.slot],
+                               pass ? f->rpitch : f->opitch, dst[0], pitch[0], dst[1], pitch[1], dst[2], pitch[2], st,
+                               pass ? &none : &f->skip[src.slot], f->net.yuv ? 1 : 0);
+        }
+        if (e != cudaSuccess) return cuda_status(e, "requant");
     }
-    if (e != cudaSuccess) return cuda_status(e, "requant");
     if (out->on_device) return NVISR_OK;
     cudaStream_t cs = f->eng->copy_stream;
     NVISR_TRY_CUDA(cudaEventRecord(f->ev_req, st));
@@ -1347,7 +1415,17 @@ nvisr_status write_output_end(nvisr_filter *f) {
     f->obuf ^= 1;  // the next requantise writes the other staging buffer
     const int h = *f->eng->err_host;
     if (h != 0) {
-        cudaMemsetAsync(f->eng->err_word, 0, sizeof(int), f->eng->stream);
+        // the error word is the engine's: outputs computed ahead (read-ahead, engine or batch
+        // steps, a cached group run) may come from the failed launches too, so they are
+        // dropped and computed again; the word is cleared once the stream is idle
+        nvisr_engine *e = f->eng;
+        cudaStreamSynchronize(e->stream);
+        cudaMemsetAsync(e->err_word, 0, sizeof(int), e->stream);
+        cudaStreamSynchronize(e->stream);
+        for (nvisr_filter *g : e->filters) {
+            g->produced.clear();
+            g->cached_run = -1;
+        }
         prof_gap(f);
         return fail(NVISR_DEVICE_TIMEOUT, "a device-side wait exceeded its time bound (error word " +
                                               std::to_string(h) + ")");
@@ -1537,7 +1615,7 @@ const char *nvisr_status_string(nvisr_status s) {
     return "UNKNOWN";
 }
 
-const char *nvisr_last_error(void) { return g_last_error.c_str(); }
+const char *nvisr_last_error(nvisr_engine *e) { return e ? e->last_error.c_str() : g_last_error.c_str(); }
 
 nvisr_status nvisr_network_check(const char *text, int64_t weights_count) {
     NetDesc net;
@@ -1619,6 +1697,7 @@ void *nvisr_engine_stream(nvisr_engine *e) { return e ? (void *)e->stream : null
 int64_t nvisr_engine_bytes_in_use(nvisr_engine *e) { return e ? e->used : 0; }
 
 nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nvisr_filter **out) {
+    ErrScope es(e);
     if (!e || !d || !out) return fail(NVISR_INVALID_ARG, "filter_create: NULL argument");
     *out = nullptr;
     if (e->max_filters > 0 && (int)e->filters.size() >= e->max_filters)
@@ -1690,6 +1769,16 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
     for (cudaEvent_t *ev : {&f->ev_h2d, &f->ev_stage, &f->ev_req, &f->ev_d2h})
         if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess)
             return cleanup(fail(NVISR_CUDA_ERROR, "cudaEventCreate failed"));
+    f->passthru = net.family == "group" && net.interp && !net.dbl;
+    f->pass_copy = f->passthru && memcmp(&d->in_fmt, &d->out_fmt, sizeof(nvisr_format)) == 0;
+    if (f->pass_copy)
+        for (int pl = 0; pl < 3; ++pl) {
+            int rows;
+            int64_t pitch;
+            f->raw_slot_bytes[pl] = plane_bytes(d->in_fmt, pl, &pitch, &rows);
+            if ((s = dalloc(e, (size_t)f->raw_slot_bytes[pl] * f->ring, f->owned, &f->raw[pl])) != NVISR_OK)
+                return cleanup(s);
+        }
     f->opitch = round_up64((int64_t)W * net.scale, 4);
     for (int k = 0; k < f->run_out; ++k) {
         if ((s = dalloc(e, sizeof(float) * 3 * f->opitch * H * net.scale_y, f->owned, &p)) != NVISR_OK)
@@ -1709,6 +1798,7 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
 }
 
 nvisr_status nvisr_push(nvisr_filter *f, const nvisr_planes *in, uint32_t flags) {
+    ErrScope es(f ? f->eng : nullptr);
     if (!f || !in) return fail(NVISR_INVALID_ARG, "push: NULL argument");
     if (f->eos) return fail(NVISR_EOS, "push after flush");
     for (int p = 0; p < 3; ++p)
@@ -1753,6 +1843,14 @@ nvisr_status nvisr_push(nvisr_filter *f, const nvisr_planes *in, uint32_t flags)
                           f->rpitch, st, f->net.yuv ? 1 : 0);
     }
     if (e != cudaSuccess) return cuda_status(e, "ingest");
+    if (f->pass_copy) {
+        // the frame's planes, kept for its output as it is (Interpolation without Double frame)
+        prof_gap(f);
+        for (int p = 0; p < 3; ++p)
+            NVISR_TRY_CUDA(cudaMemcpy2DAsync((uint8_t *)f->raw[p] + (f->pushed % f->ring) * f->raw_slot_bytes[p],
+                                             f->stage_pitch[p], src[p], pitch[p], plane_row_bytes(f->in_fmt, p),
+                                             plane_rows(f->in_fmt, p), cudaMemcpyDeviceToDevice, st));
+    }
     if (!in->on_device) {
         NVISR_TRY_CUDA(cudaEventRecord(f->ev_stage, st));
         f->stage_used = true;
@@ -1764,6 +1862,7 @@ nvisr_status nvisr_push(nvisr_filter *f, const nvisr_planes *in, uint32_t flags)
 }
 
 nvisr_status nvisr_flush(nvisr_filter *f) {
+    ErrScope es(f ? f->eng : nullptr);
     if (!f) return fail(NVISR_INVALID_ARG, "flush: NULL filter");
     f->eos = true;
     f->total_out = f->net.family == "group" ? group_total(f) : f->pushed;
@@ -1773,12 +1872,13 @@ nvisr_status nvisr_flush(nvisr_filter *f) {
 int64_t nvisr_filter_ready(nvisr_filter *f) {
     if (!f) return 0;
     int64_t n = 0;
-    const int64_t end = f->eos ? f->total_out : f->pushed * std::max(1, f->run_out);
+    const int64_t end = f->eos ? f->total_out : (f->net.family == "group" ? group_total(f) : f->pushed);
     for (int64_t o = f->next_out; o < end && output_ready(f, o); ++o) ++n;
     return n;
 }
 
 nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *info) {
+    ErrScope es(f ? f->eng : nullptr);
     if (!f || !out) return fail(NVISR_INVALID_ARG, "pull: NULL argument");
     for (int p = 0; p < 3; ++p)
         if (!out->data[p] || out->pitch[p] < plane_row_bytes(f->out_fmt, p))
@@ -1795,7 +1895,7 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
     } else {
         f->produced.pop_front();
     }
-    if ((s = write_output_begin(f, out, output_slot(f, o))) != NVISR_OK) return s;
+    if ((s = write_output_begin(f, out, output_source(f, o))) != NVISR_OK) return s;
     if (!out->on_device) {
         // read-ahead: the next output's network runs on the compute stream while this
         // output's planes are copied out
@@ -1807,10 +1907,15 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
     }
     if (info) {
         std::vector<int64_t> idx;
+        int kind = NVISR_OUT_NETWORK;
         if (f->net.family == "group") {
             RunLoc loc;
             group_locate(f, o, &loc);
             idx = loc.inputs;
+            if (loc.pass) {
+                idx.assign(1, loc.frame);
+                kind = NVISR_OUT_PASSTHROUGH;
+            }
         }
         else tuple_ready(f, o, &idx);
         int scene = 0;
@@ -1819,12 +1924,14 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
         info->src_first = idx.front();
         info->src_last = idx.back();
         info->scene = scene;
+        info->kind = kind;
     }
     f->next_out++;
     return NVISR_OK;
 }
 
 nvisr_status nvisr_filter_profile(nvisr_filter *f, int32_t enable) {
+    ErrScope es(f ? f->eng : nullptr);
     if (!f) return fail(NVISR_INVALID_ARG, "profile: NULL filter");
     flush_profile(f);
     if (enable) {
@@ -1838,6 +1945,7 @@ nvisr_status nvisr_filter_profile(nvisr_filter *f, int32_t enable) {
 }
 
 nvisr_status nvisr_filter_profile_read(nvisr_filter *f, nvisr_profile *out) {
+    ErrScope es(f ? f->eng : nullptr);
     if (!f || !out) return fail(NVISR_INVALID_ARG, "profile_read: NULL argument");
     flush_profile(f);
     for (int k = 0; k < NVISR_K_COUNT; ++k) {
@@ -1848,6 +1956,7 @@ nvisr_status nvisr_filter_profile_read(nvisr_filter *f, nvisr_profile *out) {
 }
 
 nvisr_status nvisr_engine_step(nvisr_engine *e, int32_t max_outputs, int32_t *produced) {
+    ErrScope es(e);
     if (!e) return fail(NVISR_INVALID_ARG, "engine_step: NULL engine");
     int n = 0;
     for (nvisr_filter *f : e->filters) {
@@ -1869,6 +1978,7 @@ nvisr_status nvisr_engine_step(nvisr_engine *e, int32_t max_outputs, int32_t *pr
 // ---------------------------------------------------------------- batched stepping
 
 nvisr_status nvisr_batch_create(nvisr_engine *e, nvisr_filter *const *filters, int32_t n, nvisr_batch **out) {
+    ErrScope es(e);
     if (!e || !filters || n < 1 || !out) return fail(NVISR_INVALID_ARG, "batch_create: bad arguments");
     *out = nullptr;
     std::unique_ptr<nvisr_batch> b(new nvisr_batch());
@@ -1891,6 +2001,7 @@ nvisr_status nvisr_batch_create(nvisr_engine *e, nvisr_filter *const *filters, i
 }
 
 nvisr_status nvisr_batch_step(nvisr_batch *b, int32_t *produced) {
+    ErrScope es(b ? b->eng : nullptr);
     if (!b) return fail(NVISR_INVALID_ARG, "batch_step: NULL batch");
     int nprod = 0;
     nvisr_batch::Plan probe;
@@ -2001,6 +2112,7 @@ nvisr_status nvisr_batch_step(nvisr_batch *b, int32_t *produced) {
 }
 
 nvisr_status nvisr_batch_info(nvisr_batch *b, int32_t *shared, int32_t *graphs, int32_t *rows_per_strip) {
+    ErrScope es(b ? b->eng : nullptr);
     if (!b) return fail(NVISR_INVALID_ARG, "batch_info: NULL batch");
     if (shared) *shared = b->shared ? 1 : 0;
     if (graphs) *graphs = b->graphs;
@@ -2059,21 +2171,54 @@ nvisr_status nvisr_tuple_map(const uint8_t *flags, int32_t nframes, int32_t T, i
     return NVISR_OK;
 }
 
-nvisr_status nvisr_group_runs(int32_t s0, int32_t s1, int32_t n, int32_t extra, int32_t interp, int32_t max_runs,
-                              int32_t *out_inputs, int32_t *out_skip, int32_t *nruns) {
-    if (n < 1 || s1 < s0 || !out_inputs || !out_skip || !nruns) return fail(NVISR_INVALID_ARG, "group_runs: bad arguments");
+nvisr_status nvisr_group_runs(int32_t s0, int32_t s1, int32_t n, int32_t extra, int32_t max_runs,
+                              int32_t *out_inputs, int32_t *out_skip, int32_t *out_count, int32_t *nruns) {
+    if (n < 1 || s1 < s0 || !out_inputs || !out_skip || !out_count || !nruns)
+        return fail(NVISR_INVALID_ARG, "group_runs: bad arguments");
     const int need = n + (extra ? 1 : 0);
-    const int len = s1 - s0 + 1;
-    int count = 0;
-    for (int nominal = s0; nominal <= s1; nominal += n) {
-        if (count >= max_runs) return fail(NVISR_INVALID_ARG, "group_runs: max_runs too small");
-        int start = nominal;
-        if (!interp && start + need - 1 > s1 && len >= need) start = s1 - need + 1;
-        for (int k = 0; k < need; ++k) out_inputs[count * need + k] = std::min(start + k, s1);
-        out_skip[count] = nominal - start;
-        ++count;
+    int runs = 0;
+    for (int64_t nominal = s0; nominal <= s1; nominal += n) {
+        if (runs >= max_runs) return fail(NVISR_INVALID_ARG, "group_runs: max_runs too small");
+        int64_t start;
+        int skip, count;
+        run_form(nominal, s0, s1, n, &start, &skip, &count);
+        for (int k = 0; k < need; ++k) out_inputs[runs * need + k] = (int32_t)std::min<int64_t>(start + k, s1);
+        out_skip[runs] = skip;
+        out_count[runs] = count;
+        ++runs;
     }
-    *nruns = count;
+    *nruns = runs;
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_group_outputs(const uint8_t *flags, int32_t nframes, int32_t n, int32_t extra, int32_t interp,
+                                 int32_t dbl, int32_t max_out, int32_t *kind, int32_t *src_first, int32_t *src_last,
+                                 int32_t *net_k, int32_t *nout) {
+    if (!flags || nframes < 0 || n < 1 || !kind || !src_first || !src_last || !net_k || !nout)
+        return fail(NVISR_INVALID_ARG, "group_outputs: bad arguments");
+    // a filter without a device: only the bookkeeping group_locate reads
+    nvisr_filter f;
+    f.net.family = "group";
+    f.net.interp = interp != 0;
+    f.net.extra = extra != 0;
+    f.net.dbl = dbl != 0;
+    f.net.frames = n + (extra ? 1 : 0);
+    f.grp_n = n;
+    f.grp_need = f.net.frames;
+    for (int k = 0; k < nframes; ++k) f.cut.push_back(k > 0 && flags[k] ? 1 : 0);
+    f.pushed = nframes;
+    f.eos = true;
+    const int64_t total = group_total(&f);
+    if (total > max_out) return fail(NVISR_INVALID_ARG, "group_outputs: max_out too small");
+    for (int64_t o = 0; o < total; ++o) {
+        RunLoc loc;
+        if (!group_locate(&f, o, &loc)) return fail(NVISR_INTERNAL, "group_outputs: output not located");
+        kind[o] = loc.pass ? NVISR_OUT_PASSTHROUGH : NVISR_OUT_NETWORK;
+        src_first[o] = (int32_t)(loc.pass ? loc.frame : loc.inputs.front());
+        src_last[o] = (int32_t)(loc.pass ? loc.frame : loc.inputs.back());
+        net_k[o] = loc.pass ? -1 : loc.k;
+    }
+    *nout = (int32_t)total;
     return NVISR_OK;
 }
 
@@ -2329,6 +2474,11 @@ nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t
     NVISR_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     NVISR_TRY_CUDA(cudaStreamSynchronize(st));
     if (herr) return fail(NVISR_DEVICE_TIMEOUT, "dcn2d: a device-side wait exceeded its bound");
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_test_starve(int32_t on) {
+    g_test_starve = on ? 1 : 0;
     return NVISR_OK;
 }
 

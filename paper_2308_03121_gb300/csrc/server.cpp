@@ -21,6 +21,11 @@
 
 namespace nvisr {
 void set_error(const std::string &msg);
+struct ErrScope {  // defined with the engine: errors of a call also go to its engine
+    explicit ErrScope(nvisr_engine *e);
+    ~ErrScope();
+    nvisr_engine *prev;
+};
 }
 
 struct nvisr_server {
@@ -123,6 +128,7 @@ nvisr_status admit(nvisr_server *s) {
 extern "C" {
 
 nvisr_status nvisr_server_create(nvisr_engine *engine, int32_t max_active, nvisr_server **out) {
+    nvisr::ErrScope es(engine);
     if (!engine || !out) return bad("server_create: NULL argument");
     nvisr_server *s = new nvisr_server();
     s->eng = engine;
@@ -132,6 +138,7 @@ nvisr_status nvisr_server_create(nvisr_engine *engine, int32_t max_active, nvisr
 }
 
 nvisr_status nvisr_server_submit(nvisr_server *s, const nvisr_filter_desc *desc, int64_t *clip) {
+    nvisr::ErrScope es(s ? s->eng : nullptr);
     if (!s || !desc || !clip || !desc->network_text || (!desc->weights && desc->weights_count > 0))
         return bad("server_submit: bad arguments");
     const int64_t id = s->next_id++;
@@ -148,6 +155,7 @@ nvisr_status nvisr_server_submit(nvisr_server *s, const nvisr_filter_desc *desc,
 }
 
 nvisr_status nvisr_server_push(nvisr_server *s, int64_t clip, const nvisr_planes *in, uint32_t flags) {
+    nvisr::ErrScope es(s ? s->eng : nullptr);
     if (!s) return bad("server: NULL server");
     auto it = s->clips.find(clip);
     if (it == s->clips.end()) return bad("server: unknown clip");
@@ -159,6 +167,7 @@ nvisr_status nvisr_server_push(nvisr_server *s, int64_t clip, const nvisr_planes
 }
 
 nvisr_status nvisr_server_flush(nvisr_server *s, int64_t clip) {
+    nvisr::ErrScope es(s ? s->eng : nullptr);
     if (!s) return bad("server: NULL server");
     auto it = s->clips.find(clip);
     if (it == s->clips.end()) return bad("server: unknown clip");
@@ -167,6 +176,7 @@ nvisr_status nvisr_server_flush(nvisr_server *s, int64_t clip) {
 }
 
 nvisr_status nvisr_server_step(nvisr_server *s, int32_t *produced) {
+    nvisr::ErrScope es(s ? s->eng : nullptr);
     if (!s) return bad("server: NULL server");
     nvisr_status st = admit(s);
     if (st != NVISR_OK) return st;
@@ -188,6 +198,7 @@ nvisr_status nvisr_server_step(nvisr_server *s, int32_t *produced) {
 }
 
 nvisr_status nvisr_server_pull(nvisr_server *s, int64_t clip, nvisr_planes *out, nvisr_frame_info *info) {
+    nvisr::ErrScope es(s ? s->eng : nullptr);
     if (!s) return bad("server: NULL server");
     auto it = s->clips.find(clip);
     if (it == s->clips.end()) return bad("server: unknown clip");
@@ -210,6 +221,7 @@ nvisr_status nvisr_server_pull(nvisr_server *s, int64_t clip, nvisr_planes *out,
 }
 
 nvisr_status nvisr_server_close(nvisr_server *s, int64_t clip) {
+    nvisr::ErrScope es(s ? s->eng : nullptr);
     if (!s) return bad("server: NULL server");
     auto it = s->clips.find(clip);
     if (it == s->clips.end()) return bad("server: unknown clip");
@@ -229,6 +241,7 @@ nvisr_status nvisr_server_close(nvisr_server *s, int64_t clip) {
 }
 
 nvisr_status nvisr_server_stats(nvisr_server *s, nvisr_server_stats_t *out) {
+    nvisr::ErrScope es(s ? s->eng : nullptr);
     if (!s || !out) return bad("server_stats: NULL argument");
     std::memset(out, 0, sizeof(*out));
     out->latency_p50_ms = percentile(s->latency_ms, 0.50);

@@ -331,24 +331,28 @@ def net_config3(seed: int = BASE_SEED + 3):
 
 
 def net_group_general(seed: int, n: int, extra: bool, interp: bool, double: bool, feat: int = 16,
-                      tail_gain: float = TAIL_GAIN):
-    """Small group-model network for any n and flag set (2x space).
+                      tail_gain: float = TAIL_GAIN, scale: int = 2):
+    """Small group-model network for any n and flag set (2x space, or same size with scale=1).
 
     need = n (+1 with Extra frame) input frames: a shared extract conv 3->feat per
     frame, a fusion conv over their concatenation (need*feat -> 32, LeakyReLU),
-    and one conv 32->12 + PixelShuffle(2) head per output (n, or 2n with Double
-    frame), output k adding the bilinear skip of input frame k mod need.
+    and one output conv per output (n, or 2n with Double frame): 32->12 +
+    PixelShuffle(2), or 32->3 at scale 1; output k adds the skip of input frame
+    k mod need.
     """
     rng = np.random.default_rng(seed)
     need = n + (1 if extra else 0)
     flags = ",".join(f for f, on in (("interp", interp), ("extra", extra), ("double", double)) if on)
-    spec = NetSpec("group", need, 2, "bilinear", flags=flags)
+    spec = NetSpec("group", need, scale, "bilinear", flags=flags)
     for i in range(need):
         spec.conv(rng, f"e{i}", f"frame{i}", 3, feat, act="lrelu", share="e0" if i else None)
     spec.conv(rng, "fuse", ",".join(f"e{i}" for i in range(need)), need * feat, 32, act="lrelu")
     nout = 2 * n if double else n
     for k in range(nout):
-        spec.conv(rng, f"o{k}", "fuse", 32, 12, act="none", ps=2, gain=tail_gain)
+        if scale == 2:
+            spec.conv(rng, f"o{k}", "fuse", 32, 12, act="none", ps=2, gain=tail_gain)
+        else:
+            spec.conv(rng, f"o{k}", "fuse", 32, 3, act="none", gain=tail_gain)
     for k in range(nout):
         spec.out(f"o{k}", skip=f"frame{k % need}")
     return spec.build()

@@ -25,7 +25,7 @@ def test_library_exports_every_declared_symbol():
     assert len(names) >= 20
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
-    assert lib.nvisr_abi_version() == 1
+    assert lib.nvisr_abi_version() == 2
 
 
 def test_binding_covers_every_declared_symbol():
@@ -50,11 +50,30 @@ def test_tuple_map_config1_cut_on_frame_9():
     assert got[8].tolist() == [7, 8, 8] and got[9].tolist() == [9, 9, 10]
 
 
-@pytest.mark.parametrize("n,extra,interp", [(1, True, True), (3, False, False), (2, True, True),
-                                            (3, True, False), (4, False, False)])
-def test_group_runs_match_oracle(n, extra, interp):
+@pytest.mark.parametrize("n,extra", [(1, True), (3, False), (2, True), (3, True), (4, False)])
+def test_group_runs_match_oracle(n, extra):
     for s0, s1 in [(0, 0), (0, 1), (5, 11), (0, 39), (3, 4), (10, 16)]:
-        assert nv.nvisr_group_runs(s0, s1, n, extra, interp) == oracle.group_runs(s0, s1, n, extra, interp)
+        assert nv.nvisr_group_runs(s0, s1, n, extra) == oracle.group_runs(s0, s1, n, extra)
+
+
+@pytest.mark.parametrize("n,extra,interp,double", [
+    (1, True, True, True), (1, True, True, False), (2, True, True, False), (3, False, False, False),
+    (2, False, False, True), (2, True, True, True), (3, True, False, False), (1, False, True, False)])
+def test_group_outputs_match_oracle(n, extra, interp, double):
+    """The filter's own output bookkeeping (what nvisr_pull reports, run without a device)
+    equals the oracle's presentation order for every flag set, with cuts and short scenes."""
+    rng = np.random.default_rng(n * 16 + extra * 8 + interp * 4 + double * 2)
+    for trial in range(25):
+        nf = int(rng.integers(1, 24))
+        flags = rng.uniform(size=nf) < 0.2
+        got = nv.nvisr_group_outputs(flags, n, extra, interp, double)
+        exp = []
+        for e in oracle.group_outputs(flags, nf, n, extra, interp, double):
+            if e[0] == "pass":
+                exp.append((nv.OUT_PASSTHROUGH, e[1], e[1], -1))
+            else:
+                exp.append((nv.OUT_NETWORK, e[1][0], e[1][-1], e[2]))
+        assert got == exp, (trial, flags)
 
 
 @pytest.mark.parametrize("n,b", [(1, 1), (1, 4), (2, 3), (3, 2), (4, 5), (7, 3)])

@@ -38,7 +38,7 @@ def run_gpu(text, blob, frames, flags, fin, fout, prec, scale=2, device_io=False
             st, info = flt.pull(res)
         if st == nv.Status.OK:
             outs.append({k: r.astype(np.int64) for k, r in zip("YUV", res)})
-            infos.append((info.index, info.src_first, info.src_last))
+            infos.append((info.index, info.src_first, info.src_last, info.kind))
         return st
 
     for i, fr in enumerate(frames):
@@ -84,7 +84,7 @@ def test_config1_filter_within_1lsb(prec, config1_oracle):
                           nv.fmt(128, 128, 8, "420", "full"), prec)
     assert len(outs) == 16
     assert [i[0] for i in infos] == list(range(16))
-    assert infos[8][1:] == (7, 8) and infos[9][1:] == (9, 10)    # scene cut on frame 9
+    assert infos[8][1:3] == (7, 8) and infos[9][1:3] == (9, 10)    # scene cut on frame 9
     for got, pq in zip(outs, config1_oracle):
         if prec == "fp32":
             assert_codes_match(got, pq, 8)
@@ -275,7 +275,7 @@ def test_config3_stvsr_dcn_filter(prec, config3_oracle):
     outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(4 * W, 4 * H, 8), prec, scale=4)
     assert len(outs) == 2 * len(frames)
     assert [i[0] for i in infos] == list(range(8))
-    assert [i[1:] for i in infos] == [(0, 1), (0, 1), (1, 1), (1, 1), (2, 3), (2, 3), (3, 3), (3, 3)]
+    assert [i[1:3] for i in infos] == [(0, 1), (0, 1), (1, 1), (1, 1), (2, 3), (2, 3), (3, 3), (3, 3)]
     worst = 0
     for got, pq in zip(outs, config3_oracle):
         if prec == "fp32":
@@ -289,35 +289,87 @@ def test_config3_stvsr_dcn_filter(prec, config3_oracle):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("n,extra,interp,double", [(2, True, True, True), (3, False, False, False),
-                                                   (2, False, False, True)])
+                                                   (2, False, False, True), (1, True, True, False),
+                                                   (2, True, True, False), (3, True, False, False)])
 def test_group_model_general_n(n, extra, interp, double, prec):
     """Group family with n > 1 and each flag set (Section 3.1 / 3.3): runs of n (+1) frames,
-    2n outputs with Double frame, a non-interpolating scene's last run moved back inside
-    the scene with its recycled outputs dropped; a cut before frame 5."""
+    2n network outputs with Double frame, a scene's last run moved back inside the scene
+    with the outputs of already covered frames dropped, 2 outputs per frame with
+    Interpolation; without Double frame the input frames themselves are outputs (scale 1,
+    copied unchanged).  9 frames, a cut before frame 5."""
     W, H, N = 48, 32, 9
     frames = synth.frames_textured(synth.BASE_SEED + 61, N, W, H, 8, "420", "limited")
     flags = np.zeros(N, bool)
     flags[5] = True
-    text, blob = synth.net_group_general(synth.BASE_SEED + 60, n, extra, interp, double)
-    fdo = fmt_dict(2 * W, 2 * H, 8)
-    ref = [prequant(o, fdo) for o in
-           oracle.run_filter(frames, flags, text, blob, fmt_dict(W, H, 8), fdo, keep_float=True)]
-    # expected source range of every output, from the oracle's run enumeration
-    need, per_run = n + (1 if extra else 0), (2 * n if double else n)
-    src = []
-    for s0, s1 in oracle.scenes_from_flags(flags, N):
-        for inputs, skip in oracle.group_runs(s0, s1, n, extra, interp):
-            src += [(inputs[0], inputs[-1])] * (per_run - skip)
-    outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(2 * W, 2 * H, 8), prec, scale=2)
-    assert len(outs) == len(ref) == len(src)
+    s = 1 if (interp and not double) else 2
+    text, blob = synth.net_group_general(synth.BASE_SEED + 60, n, extra, interp, double, scale=s)
+    fdi, fdo = fmt_dict(W, H, 8), fmt_dict(s * W, s * H, 8)
+    ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
+    # expected source range and kind of every output, from the oracle's presentation order
+    src = [(e[1], e[1], nv.OUT_PASSTHROUGH) if e[0] == "pass" else (e[1][0], e[1][-1], nv.OUT_NETWORK)
+           for e in oracle.group_outputs(flags, N, n, extra, interp, double)]
+    outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(s * W, s * H, 8), prec, scale=s)
+    assert len(outs) == len(ref) == len(src) == N * (2 if (interp or double) else 1)
     assert [i[0] for i in infos] == list(range(len(ref)))
     assert [i[1:] for i in infos] == src
-    for got, pq in zip(outs, ref):
+    for got, r in zip(outs, ref):
+        if isinstance(r, dict):  # an input frame passed through: its planes, unchanged
+            for k in "YUV":
+                assert np.array_equal(got[k], r[k].astype(np.int64)), k
+            continue
+        pq = prequant(r, fdo)
         if prec == "fp32":
             assert_codes_match(got, pq, 8)
         else:
             mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 8) for k in "YUV"})
             assert mx <= 1, mx
+
+
+@pytest.mark.parametrize("device_io", [False, True])
+def test_interpolation_passthrough_into_another_format(device_io):
+    """Interpolation without Double frame with 8-bit 4:2:0 in and 10-bit 4:4:4 out: the
+    passed-through input frames are converted to the output format (ingest, then
+    requantise, no network), the network outputs go between them; FP32, a cut on frame 3."""
+    W, H, N = 40, 24, 6
+    frames = synth.frames_textured(synth.BASE_SEED + 62, N, W, H, 8, "420", "limited")
+    flags = np.zeros(N, bool)
+    flags[3] = True
+    text, blob = synth.net_group_general(synth.BASE_SEED + 63, 1, True, True, False, scale=1)
+    fdi, fdo = fmt_dict(W, H, 8), fmt_dict(W, H, 10, "444")
+    ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
+    outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(W, H, 10, "444"), "fp32", scale=1,
+                          device_io=device_io)
+    assert len(outs) == len(ref) == 2 * N
+    assert [i[3] for i in infos] == [nv.OUT_PASSTHROUGH, nv.OUT_NETWORK] * N
+    assert [i[1] for i in infos[0::2]] == list(range(N))
+    for got, r in zip(outs, ref):
+        assert_codes_match(got, prequant(r, fdo), 10)
+
+
+def test_interpolation_without_double_needs_scale_1():
+    """An input frame passed through cannot be an output of another size: such a filter
+    with spatial scale 2 is rejected."""
+    text, blob = synth.net_group_general(synth.BASE_SEED + 64, 1, True, True, False, scale=2)
+    eng = nv.Engine()
+    with pytest.raises(nv.NvisrError) as ei:
+        eng.filter(text, blob, nv.fmt(32, 32, 8), nv.fmt(64, 64, 8), "fp32", 2)
+    assert ei.value.status == nv.Status.UNSUPPORTED_FORMAT
+    assert "scale must be 1" in eng.last_error()
+    eng.close()
+
+
+def test_last_error_is_kept_per_engine():
+    """nvisr_last_error(engine): a failure on one engine leaves another engine's message."""
+    text, blob = synth.net_group_general(synth.BASE_SEED + 64, 1, True, True, False, scale=2)
+    a, b = nv.Engine(), nv.Engine()
+    with pytest.raises(nv.NvisrError):
+        a.filter(text, blob, nv.fmt(32, 32, 8), nv.fmt(64, 64, 8), "fp32", 2)
+    with pytest.raises(nv.NvisrError):
+        b.filter(text, blob, nv.fmt(32, 32, 8), nv.fmt(32, 32, 8), "fp32", 1)
+    assert "scale must be 1" in a.last_error()
+    assert "scale does not match" in b.last_error()
+    a.close()
+    b.close()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])

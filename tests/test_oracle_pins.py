@@ -479,20 +479,102 @@ def test_tuple_map_brute_force_invariants():
 
 
 def test_group_runs_stvsr_pairs():
-    runs = oracle.group_runs(0, 39, 1, extra=True, interp=True)
+    runs = oracle.group_runs(0, 39, 1, extra=True)
     assert len(runs) == 40
-    assert runs[0] == ([0, 1], 0) and runs[38] == ([38, 39], 0) and runs[39] == ([39, 39], 0)
+    assert runs[0] == ([0, 1], 0, 1) and runs[38] == ([38, 39], 0, 1) and runs[39] == ([39, 39], 0, 1)
     assert oracle.group_output_count(1, True, True) == 2
 
 
 def test_group_runs_recycle_and_duplicate():
-    # n = 3 non-interpolating network, scene of 7 frames: last group recycles 4, 5
-    assert oracle.group_runs(0, 6, 3, extra=False, interp=False) == \
-        [([0, 1, 2], 0), ([3, 4, 5], 0), ([4, 5, 6], 2)]
-    # scene of 2 frames for a 3-frame network: last frame duplicated
-    assert oracle.group_runs(10, 11, 3, extra=False, interp=False) == [([10, 11, 11], 0)]
-    # interpolation network: the scene's last frame is duplicated
-    assert oracle.group_runs(0, 4, 2, extra=True, interp=True)[-1] == ([4, 4, 4], 0)
+    # n = 3 network, scene of 7 frames: the last group recycles 4, 5 and covers frame 6 only
+    assert oracle.group_runs(0, 6, 3, extra=False) == \
+        [([0, 1, 2], 0, 3), ([3, 4, 5], 0, 3), ([4, 5, 6], 2, 1)]
+    # scene of 2 frames for a 3-frame network: last frame duplicated, 2 frames covered
+    assert oracle.group_runs(10, 11, 3, extra=False) == [([10, 11, 11], 0, 2)]
+    # interpolation network (n = 2, Extra frame), scene of 5: the last group recycles
+    # frame 3 and its extra frame duplicates the scene's last frame
+    assert oracle.group_runs(0, 4, 2, extra=True)[-1] == ([3, 4, 4], 1, 1)
+    # n = 2 with Extra frame over 2 frames: one run, the extra frame duplicated
+    assert oracle.group_runs(0, 1, 2, extra=True) == [([0, 1, 1], 0, 2)]
+
+
+def test_group_runs_cover_each_scene_frame_once():
+    """Brute force: the frames a scene's runs cover for the first time are s0..s1 in
+    order, each once, and no run reads outside the scene."""
+    for n in range(1, 6):
+        for extra in (False, True):
+            for s0 in (0, 3):
+                for length in range(1, 14):
+                    s1 = s0 + length - 1
+                    covered = []
+                    for inputs, skip, count in oracle.group_runs(s0, s1, n, extra):
+                        assert len(inputs) == n + extra
+                        assert all(s0 <= i <= s1 for i in inputs)
+                        assert count >= 1 and skip + count <= n
+                        covered += inputs[skip:skip + count]
+                    assert covered == list(range(s0, s1 + 1)), (n, extra, s0, s1)
+
+
+def _plan(flags, n, extra, interp, double):
+    return [("P", e[1]) if e[0] == "pass" else ("N", e[1], e[2])
+            for e in oracle.group_outputs(np.asarray(flags, bool), len(flags), n, extra, interp, double)]
+
+
+def test_group_outputs_interpolation_passes_input_frames_through():
+    """Section 3.1: Interpolation doubles the frame rate; without Double frame the input
+    frames are output as they are and the network's n outputs are the intermediate frames.
+    Written out by hand for n = 1 and n = 2 (Extra frame), one scene."""
+    assert _plan([0, 0, 0, 0], 1, True, True, False) == [
+        ("P", 0), ("N", (0, 1), 0), ("P", 1), ("N", (1, 2), 0),
+        ("P", 2), ("N", (2, 3), 0), ("P", 3), ("N", (3, 3), 0)]
+    assert _plan([0, 0, 0, 0, 0], 2, True, True, False) == [
+        ("P", 0), ("N", (0, 1, 2), 0), ("P", 1), ("N", (0, 1, 2), 1),
+        ("P", 2), ("N", (2, 3, 4), 0), ("P", 3), ("N", (2, 3, 4), 1),
+        ("P", 4), ("N", (3, 4, 4), 1)]
+    # a cut before frame 2: no pair crosses it, the scene's last frame is duplicated
+    assert _plan([0, 0, 1, 0], 1, True, True, False) == [
+        ("P", 0), ("N", (0, 1), 0), ("P", 1), ("N", (1, 1), 0),
+        ("P", 2), ("N", (2, 3), 0), ("P", 3), ("N", (3, 3), 0)]
+
+
+def test_group_outputs_double_and_plain_counts():
+    """Double frame: 2n network outputs per run (2 per consumed frame); neither flag: n.
+    Every stream gives 2 (Interpolation or Double frame) or 1 outputs per input frame."""
+    assert _plan([0, 0, 0], 1, True, True, True) == [
+        ("N", (0, 1), 0), ("N", (0, 1), 1), ("N", (1, 2), 0), ("N", (1, 2), 1),
+        ("N", (2, 2), 0), ("N", (2, 2), 1)]
+    assert _plan([0] * 7, 3, False, False, False) == [
+        ("N", (0, 1, 2), 0), ("N", (0, 1, 2), 1), ("N", (0, 1, 2), 2),
+        ("N", (3, 4, 5), 0), ("N", (3, 4, 5), 1), ("N", (3, 4, 5), 2), ("N", (4, 5, 6), 2)]
+    assert _plan([0, 0, 0], 2, False, False, True) == [
+        ("N", (0, 1), 0), ("N", (0, 1), 1), ("N", (0, 1), 2), ("N", (0, 1), 3),
+        ("N", (1, 2), 2), ("N", (1, 2), 3)]
+    rng = np.random.default_rng(4)
+    for _ in range(40):
+        nf = int(rng.integers(1, 20))
+        flags = rng.uniform(size=nf) < 0.25
+        n = int(rng.integers(1, 4))
+        extra, interp, double = (bool(v) for v in rng.integers(0, 2, size=3))
+        assert len(_plan(flags, n, extra, interp, double)) == nf * (2 if (interp or double) else 1)
+
+
+def test_passthrough_copies_or_converts():
+    """A passed-through frame in the input's own format is the input unchanged; into
+    another format it is converted without a network: 8-bit full range to 10-bit full
+    range is code * 1023 / 255 rounded (closed form), on 4:4:4 planes."""
+    rng = np.random.default_rng(5)
+    fr = {k: rng.integers(0, 256, size=(4, 6)).astype(np.uint8) for k in "YUV"}
+    f8 = dict(width=6, height=4, bit_depth=8, subsampling="444", range="full", chroma_loc="left")
+    same = oracle.passthrough(fr, f8, dict(f8))
+    assert all(np.array_equal(same[k], fr[k]) for k in "YUV")
+    f10 = dict(f8, bit_depth=10)
+    conv = oracle.passthrough(fr, f8, f10)
+    for k in "YUV":
+        if k == "Y":
+            exp = np.rint(fr[k].astype(np.float64) * 1023 / 255)
+        else:  # chroma: C' = (C - 128) / 255 -> C' * 1023 + 512, clamped to the code range
+            exp = np.clip(np.rint((fr[k].astype(np.float64) - 128) * 1023 / 255 + 512), 0, 1023)
+        assert np.array_equal(conv[k], exp.astype(np.int64)), k
 
 
 # ------------------------------------------------------------------ C7 Figure 1
