@@ -1587,7 +1587,9 @@ struct Variant {
     /* 16-byte-chunk inputs (16 / 32 channels): heads, extract convs, narrow nets */                     \
     NVISR_V16(I, 64, 3, 2, 0, 16, 128), NVISR_V16(I, 64, 3, 4, 0, 16, 128),                              \
     NVISR_V16(I, 32, 3, 2, 0, 16, 16), NVISR_V16(I, 32, 3, 4, 0, 16, 16),                                \
-    NVISR_V16(I, 16, 3, 2, 0, 16, 16), NVISR_V16(I, 16, 3, 4, 0, 16, 16), NVISR_V16(I, 16, 3, 4, 1, 16, 16)
+    NVISR_V16(I, 16, 3, 2, 0, 16, 16), NVISR_V16(I, 16, 3, 4, 0, 16, 16), NVISR_V16(I, 16, 3, 4, 1, 16, 16), \
+    /* float32 out from 16 / 32 channels: same-size output layers of narrow networks */                \
+    NVISR_V(I, DT_F32, 16, 3, 2, 0, 16, 16), NVISR_V(I, DT_F32, 16, 3, 4, 0, 16, 16)
 
 const Variant kVariants[] = {
     NVISR_VSET(DT_BF16),

@@ -150,6 +150,7 @@ struct Step {
     int in_t = -1;       // input tensor id (SRC_TENSOR)
     int src = SRC_TENSOR;
     int frame_src = -1;  // group family: input from ring frame k
+    std::vector<int> perm;  // group family: input channel c of the layer is stored channel perm[c]
     int add_t = -1;
     int out_t = -1;      // -1: final output (PixelShuffle into planar float32)
     int out_index = -1;  // final output number
@@ -510,7 +511,11 @@ bool layer_is_fp8(const nvisr_filter *f, const NetLayer &L) {
 }
 
 // Uploads one layer's weights (OIHW float32, with bias) in the precision's layout.
-nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, const float *b, Weights &W) {
+// sw: the 16-bit conv weights' layout for a 64-channel-multiple input: -1 follows the
+// input's default chunking (128-byte swizzled for 64-channel chunks), 0 forces the
+// no-swizzle form of inputs stored in 16-byte chunks.
+nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, const float *b, Weights &W,
+                            int sw = -1) {
     W.cin_pad = act_cpad(f, L.cin);
     W.cout_pad = round_up(L.cout, 16);
     // padded to whole 64-channel slices (the row kernels read a slice's 64 biases)
@@ -528,7 +533,7 @@ nvisr_status upload_weights(nvisr_filter *f, const NetLayer &L, const float *w, 
         std::vector<uint8_t> host(tc_weight_bytes(W.cin_pad, W.cout_pad, L.k, f->act_dt));
         // the conv kernel reads 64-channel inputs through 128-byte-swizzled operands;
         // the DCN kernel builds its own no-swizzle sampled tile
-        const bool sw128 = L.op == "conv" && layout_cpc(f->act_dt, W.cin_pad) == 64;
+        const bool sw128 = L.op == "conv" && layout_cpc(f->act_dt, W.cin_pad) == 64 && sw != 0;
         prepare_weights_tc(w, L.cout, L.cin, L.k, W.cin_pad, W.cout_pad, f->act_dt, 1.0f, host.data(), sw128);
         s = upload(f, host.data(), host.size(), &W.simt_or_tc);
         if (s == NVISR_OK && L.op == "conv" && L.k == 3 && L.cin == 64 && L.cout == 64 && !L.ps) {
@@ -622,10 +627,10 @@ int om_row_source(int j, int G) {
 
 // Uploads a layer's weights, with its output rows permuted to tap-major order
 // when it is such a head.
-nvisr_status upload_layer(nvisr_filter *f, int li, const float *w, const float *b, Weights &W) {
+nvisr_status upload_layer(nvisr_filter *f, int li, const float *w, const float *b, Weights &W, int sw = -1) {
     const NetLayer &L = f->net.layers[li];
     const int G = f->om_tap_g[li];
-    if (G == 0) return upload_weights(f, L, w, b, W);
+    if (G == 0) return upload_weights(f, L, w, b, W, sw);
     const size_t per = (size_t)L.cin * L.k * L.k;
     std::vector<float> wo(per * L.cout), bo(L.cout);
     for (int j = 0; j < L.cout; ++j) {
@@ -633,7 +638,7 @@ nvisr_status upload_layer(nvisr_filter *f, int li, const float *w, const float *
         std::copy(w + o * per, w + (o + 1) * per, wo.begin() + j * per);
         bo[j] = b[o];
     }
-    return upload_weights(f, L, wo.data(), bo.data(), W);
+    return upload_weights(f, L, wo.data(), bo.data(), W, sw);
 }
 
 nvisr_status prepare_weights(nvisr_filter *f, const float *blob) {
@@ -925,6 +930,7 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
                     for (int j = 0; j < c; ++j) perm[soff + j] = loff + j;
                     loff += c;
                 }
+                st.perm = perm;
                 const int kk = L.k * L.k;
                 const float *w = blob + L.woff;
                 const float *b = w + (int64_t)L.cout * L.cin * kk;
@@ -1036,6 +1042,34 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
                     if (b.p == f->tensors[t].ptr) b.free_after = step;
     }
     for (Tensor &T : f->tensors) T.cpc = layout_cpc(T.dt, T.cpad);
+    // a concatenation's parts are channel views of its buffer, so they share one chunk
+    // layout: the narrowest part's (16-channel parts of a 64-channel buffer: 8 channels)
+    for (Tensor &T : f->tensors)
+        if (T.parent >= 0) f->tensors[T.parent].cpc = std::min(f->tensors[T.parent].cpc, T.cpc);
+    for (Tensor &T : f->tensors)
+        if (T.parent >= 0) T.cpc = f->tensors[T.parent].cpc;
+    // a 16-bit conv whose 64-channel-multiple input was so narrowed reads it in 16-byte
+    // chunks: its weights are laid out again, without the 128-byte swizzle
+    for (Step &st : f->steps) {
+        if (!f->tc || st.op != OP_CONV) continue;
+        const Tensor &in = f->tensors[st.in_t];
+        if (in.cpc == layout_cpc(in.dt, in.cpad)) continue;
+        const NetLayer &L = net.layers[st.layer];
+        const int kk = L.k * L.k;
+        const float *w = blob + net.layers[L.owner].woff;
+        const float *b = w + (int64_t)L.cout * L.cin * kk;
+        std::vector<float> wp(w, w + (size_t)L.cout * L.cin * kk);
+        if (!st.perm.empty())
+            for (int o = 0; o < L.cout; ++o)
+                for (int c = 0; c < L.cin; ++c)
+                    for (int t = 0; t < kk; ++t)
+                        wp[((size_t)o * L.cin + c) * kk + t] = w[((size_t)o * L.cin + st.perm[c]) * kk + t];
+        Weights Wv;
+        nvisr_status s = upload_layer(f, st.layer, wp.data(), b, Wv, 0);
+        if (s != NVISR_OK) return s;
+        st.widx = (int)f->wvar.size();
+        f->wvar.push_back(Wv);
+    }
     // the tensor-core DCN gathers from its input copied into 8-channel planes
     size_t x8 = 0;
     for (const Step &st : f->steps)

@@ -1,7 +1,16 @@
-"""Accuracy report of the reduced-precision paths on the config-2 network (ragged
-136x70 clip with a scene cut): codes identical to the FP32 GPU path, max LSB
-and PSNR against the FP64 oracle.  Asserts the bounds the other tests hold
-(BF16 / FP16 within 1 LSB of the oracle, FP8 within 16) and prints the rest."""
+"""Accuracy of the reduced-precision paths on the config-2 network (ragged 136x70
+clip with a scene cut): codes identical to the FP32 GPU path, max LSB and PSNR
+against the FP64 oracle.
+
+The targets are: every precision within 1 LSB (10-bit) of the oracle
+everywhere, and BF16 / FP8 codes identical to the FP32 GPU path on >= 99.9 %
+of samples.  FP32, BF16 and FP16 meet the first.  FP8 measures 2 LSB, and no
+16-bit or 8-bit path meets the second: random-init weights carry the 8-bit
+(BF16) or 3-bit (E4M3) mantissa error of 20 trunk layers to the output, where
+it moves about 5 % (BF16), 0.7 % (FP16) and 22 % (FP8) of the codes by one.
+So the assertions hold each path to what it measures (the worst LSB and the
+identical share, with a small margin): a regression fails, and the gap to the
+target stays visible here and in the design notes."""
 import numpy as np
 import pytest
 import torch
@@ -68,4 +77,10 @@ def test_precision_report():
             psnrs.append(_psnr(got["Y"], r["Y"], 1023))
         print(f"{prec}: identical to FP32 GPU {same / total:.4%}, max |LSB| vs oracle {worst}, "
               f"luma PSNR vs oracle {min(psnrs):.1f} dB")
-        assert worst <= (16 if prec == "fp8" else 1), (prec, worst)
+        assert worst <= MAX_LSB[prec], (prec, worst)
+        assert same / total >= MIN_IDENTICAL[prec], (prec, same / total)
+
+
+# measured on the case above (FP32 GPU path vs the FP64 oracle: 1 LSB at rounding ties)
+MAX_LSB = {"fp32": 1, "bf16": 1, "fp16": 1, "fp8": 2}
+MIN_IDENTICAL = {"fp32": 1.0, "bf16": 0.94, "fp16": 0.99, "fp8": 0.76}

@@ -177,7 +177,7 @@ STVSR_WINDOWS = [(0, 16, 0, 16), (0, 16, 944, 960), (524, 540, 944, 960), (270, 
                  (100, 116, 120, 136)]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_config3_full_size_sampled_windows(prec):
     """960x540 8-bit, the deformable ST-SR network in the bench's launch shapes: both outputs
     of the first run on sampled windows (corners, the ragged last column tile, interior)."""
@@ -202,7 +202,8 @@ def test_config3_full_size_sampled_windows(prec):
 
 
 def test_fp8_filter_reports_error_vs_oracle():
-    """FP8 E4M3 (per-tensor scales from frames 0-3) on the ragged config-2 case: bounded error."""
+    """FP8 E4M3 (per-tensor scales from frames 0-3) on the ragged config-2 case: within the
+    2 LSB it measures (the 1 LSB target is not met by FP8; see test_gpu_accuracy)."""
     W, H = 136, 70
     frames, flags = _config2_small(W, H)
     text, blob = synth.net_config2()
@@ -214,7 +215,7 @@ def test_fp8_filter_reports_error_vs_oracle():
         mx, frac = lsb_stats(got, r)
         worst = max(worst, mx)
     print("fp8 max LSB", worst)
-    assert worst <= 16
+    assert worst <= 2
 
 
 def test_backpressure_full_then_pull():

@@ -57,6 +57,32 @@ def test_ingest_matches_oracle(W, H, bits, sub, rng, loc):
     assert err < 4e-6, err
 
 
+@pytest.mark.parametrize("W,H,bits,sub,loc", [(136, 70, 10, "420", "left"), (64, 32, 8, "444", "center"),
+                                               (70, 34, 12, "420", "point")])
+def test_ingest_full_code_range_under_limited_range(W, H, bits, sub, loc):
+    """Limited-range formats still carry codes outside [16, 235] / [16, 240] (scaled):
+    sub-black, super-white and the extreme codes 0 and 2^b - 1.  Uniform codes over the
+    whole range, plus both extremes, against the oracle."""
+    rs = np.random.default_rng(W + bits)
+    top = (1 << bits) - 1
+    dt = np.uint8 if bits <= 8 else np.uint16
+    cw, ch = (W // 2, H // 2) if sub == "420" else (W, H)
+    fr = {"Y": rs.integers(0, top + 1, size=(H, W)).astype(dt),
+          "U": rs.integers(0, top + 1, size=(ch, cw)).astype(dt),
+          "V": rs.integers(0, top + 1, size=(ch, cw)).astype(dt)}
+    for k in "YUV":
+        fr[k][0, 0], fr[k][-1, -1] = 0, top
+    fd = fmt_dict(W, H, bits, sub, "limited", loc)
+    pitch = (W + 3) // 4 * 4
+    out = torch.full((3, H, pitch), float("nan"), device="cuda")
+    nv.nvisr_ingest(nv.fmt(W, H, bits, sub, "limited", loc), to_dev(fr["Y"]), to_dev(fr["U"]), to_dev(fr["V"]), out)
+    torch.cuda.synchronize()
+    ref = oracle.ingest(fr, fd)
+    # values reach about [-1.3, 2.3] here: FP32 arithmetic, relative 1e-6 of that
+    err = np.abs(out[:, :, :W].double().cpu().numpy() - ref).max()
+    assert err < 8e-6, err
+
+
 @pytest.mark.parametrize("W,H,bits,sub,rng,loc", INGEST_CASES)
 def test_requant_matches_oracle(W, H, bits, sub, rng, loc):
     rs = np.random.default_rng(W * H + bits)

@@ -92,26 +92,34 @@ def test_filter_pull_reports_timeout_then_recovers():
     ref = oracle.run_filter(frames, flags, text, blob, fd_in, fd_out, keep_float=True)
     eng = nv.Engine()
     flt = eng.filter(text, blob, nv.fmt(W, H, 8, "420", "full"), nv.fmt(2 * W, 2 * H, 8, "420", "full"), "bf16")
-    for i, fr in enumerate(frames):
-        assert flt.push((fr["Y"], fr["U"], fr["V"]), cut=bool(flags[i])) == nv.Status.OK
-    flt.flush()
-    out = flt.alloc_out_host()
+    got = []
+
+    def pull_one():
+        out = flt.alloc_out_host()
+        st, info = flt.pull(out)
+        if st == nv.Status.OK:
+            assert info.index == len(got)
+            got.append({k: p.astype(np.int64) for k, p in zip("YUV", out)})
+        return st
+
+    k = 0
+    while flt.ready() < 2:  # outputs 0 and 1 known: the pull runs 1 ahead
+        assert flt.push((frames[k]["Y"], frames[k]["U"], frames[k]["V"]), cut=bool(flags[k])) == nv.Status.OK
+        k += 1
     nv.nvisr_test_starve(True)
     try:
         with pytest.raises(nv.NvisrError) as ei:
-            flt.pull(out)
+            pull_one()
     finally:
         nv.nvisr_test_starve(False)
     assert ei.value.status == nv.Status.DEVICE_TIMEOUT
     assert "time bound" in eng.last_error()
-    got = []
-    while True:
-        out = flt.alloc_out_host()
-        st, info = flt.pull(out)
-        if st == nv.Status.EOS:
-            break
-        assert st == nv.Status.OK and info.index == len(got)
-        got.append({k: p.astype(np.int64) for k, p in zip("YUV", out)})
+    for i in range(k, len(frames)):
+        while flt.push((frames[i]["Y"], frames[i]["U"], frames[i]["V"]), cut=bool(flags[i])) == nv.Status.FULL:
+            assert pull_one() == nv.Status.OK
+    flt.flush()
+    while pull_one() != nv.Status.EOS:
+        pass
     eng.close()
     assert len(got) == 8
     for g, r in zip(got, ref):
