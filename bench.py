@@ -14,8 +14,9 @@ no L2 flush is needed between steps.
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead (the reference arm: there is no reference implementation to run).
 Secondary workloads report under their own keys: ``batched`` (24 streams),
-``config3`` (deformable space-time SR), ``modes`` (same-size and vertical-2x
-scale modes) and ``serving``.
+``config3`` (deformable space-time SR), ``pyramid`` (the same with a
+three-level feature-pyramid extract stage), ``modes`` (same-size and
+vertical-2x scale modes) and ``serving``.
 """
 from __future__ import annotations
 
@@ -270,14 +271,16 @@ def measure_modes(nv, steps, warmup, dev_frames, local):
     return res
 
 
-def measure_config3(nv, steps, warmup, local, prec="bf16"):
+def measure_config3(nv, steps, warmup, local, prec="bf16", pyramid=False):
     """Spatio-temporal SR with deformable alignment: 960x540 8-bit 4:2:0, two
     input frames -> two 3840x2160 outputs per run (the frame and the midpoint),
     BF16, device-resident input.  Reports output Mpix/s and the DCN kernel's
-    time and achieved bytes (features + offsets/mask read, output written)."""
+    time and achieved bytes (features + offsets/mask read, output written).
+    pyramid: the network whose extract stage is a three-level feature pyramid,
+    aligned at every level (its extract features are cached per frame)."""
     import torch
     w, h = 960, 540
-    text, blob = synth.net_config3()
+    text, blob = synth.net_group_pyramid(synth.BASE_SEED + 3) if pyramid else synth.net_config3()
     frs = synth.frames_textured(synth.BASE_SEED + 3, 4, w, h, 8, "420", "limited")
     dev = f"cuda:{local}"
     frames = [tuple(torch.from_numpy(np.ascontiguousarray(f[c])).to(dev) for c in "YUV") for f in frs]
@@ -310,14 +313,20 @@ def measure_config3(nv, steps, warmup, local, prec="bf16"):
     dt = time.perf_counter() - t0
     prof = flt.profile_read()
     flt.profile(False)
+    hits, misses = flt.cache_stats()
     eng.close()
     dcn_ms, dcn_n = prof["dcn"]
     # per DCN application: x (64 ch BF16) + offsets/mask (216 ch float32) read, y (64 ch BF16) written
     dcn_bytes = w * h * (64 * 2 + 216 * 4 + 64 * 2)
-    return {"workload": "960x540 8-bit 4:2:0 -> 2 x 3840x2160 per input frame: extract 3->64, offset/mask head "
-                        "128->216, modulated deformable conv 64->64 (8 groups), 1x1 blend, 6 residual blocks, "
-                        "two PixelShuffle(2) stages; BF16; device-resident input",
+    net_text = ("extract pyramid 3->64, pool + 64->64 at 1/2 and 1/4 size (cached per frame); per level an "
+                "offset/mask head 128->216 and a modulated deformable conv 64->64 (8 groups), coarse-to-fine 1x1 "
+                "blends with the bilinear x2 of the level below" if pyramid else
+                "extract 3->64 (cached per frame), offset/mask head 128->216, modulated deformable conv 64->64 "
+                "(8 groups)")
+    return {"workload": "960x540 8-bit 4:2:0 -> 2 x 3840x2160 per input frame: " + net_text + ", 1x1 blend, "
+                        "6 residual blocks, two PixelShuffle(2) stages; BF16; device-resident input",
             "metric": "output Mpix/s", "value": steps * 2 * 16 * w * h / dt / 1e6, "steps": steps,
+            "extract_cache": {"hits": hits, "misses": misses},
             "kernel_ms_per_run": {kk: round(v[0] / steps, 4) for kk, v in prof.items() if v[1]},
             "dcn": {"us_per_launch": dcn_ms / max(dcn_n, 1) * 1e3, "launches_per_run": dcn_n / steps,
                     "bytes_per_launch": dcn_bytes,
@@ -623,12 +632,16 @@ def main():
     achieved_gbs = BODY_BYTES / (avg_body * 1e-3) / 1e9
     launches = round(sum(n for _, n in prof.values()) * r["steps"] / r["psteps"])
     e2e_total, p50, p99 = measure_e2e(nv, head, args.e2e_steps, pinned, local)
-    config3 = None
+    config3 = pyramid = None
     if args.config3_steps > 0:
         try:
             config3 = measure_config3(nv, args.config3_steps, 3, local)
         except Exception as e:  # the secondary workload must not hide the headline
             errors["config3"] = repr(e)
+        try:
+            pyramid = measure_config3(nv, args.config3_steps, 3, local, pyramid=True)
+        except Exception as e:  # the secondary workload must not hide the headline
+            errors["pyramid"] = repr(e)
     modes = None
     if args.modes_steps > 0:
         try:
@@ -691,6 +704,7 @@ def main():
         "precisions": by_prec,
         "batched": batched,
         "config3": config3,
+        "pyramid": pyramid,
         "modes": modes,
         "serving": serving,
         "hbm_peak_gbs": hbm,

@@ -223,12 +223,20 @@ nvisr_status nvisr_network_check(const char *network_text, int64_t weights_count
 enum {
     NVISR_K_INGEST = 0, NVISR_K_PACK = 1, NVISR_K_CONV_HEAD = 2, NVISR_K_CONV_BODY = 3,
     NVISR_K_CONV_TAIL = 4, NVISR_K_REQUANT = 5, NVISR_K_DCN = 6, NVISR_K_CONV_OTHER = 7,
-    NVISR_K_COUNT = 8
+    NVISR_K_RESAMPLE = 8,            /* feature-pyramid pool / up */
+    NVISR_K_COUNT = 9
 };
 typedef struct nvisr_profile {
     double ms[NVISR_K_COUNT];        /* summed device time per kind */
     int64_t launches[NVISR_K_COUNT]; /* launches per kind */
 } nvisr_profile;
+
+/* Extract-stage cache of a two-frame group filter (Section 3.1: the extract
+ * stage works on one frame, so a frame's features serve every run that takes
+ * it): *hits counts frame slots whose features a run found computed by an
+ * earlier run, *misses those it computed.  Both 0 for filters without the cache
+ * (tuple networks, other group layouts). */
+nvisr_status nvisr_filter_cache_stats(nvisr_filter *filter, int64_t *hits, int64_t *misses);
 
 /* enable != 0 starts recording (clearing earlier totals); 0 stops. */
 nvisr_status nvisr_filter_profile(nvisr_filter *filter, int32_t enable);

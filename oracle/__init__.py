@@ -37,7 +37,7 @@ from .grouping import (fig1_layout, fig1_next_batch_copy, fig1_slot_frames,
                        group_output_count, group_outputs, group_runs, outputs_per_frame,
                        scene_of, scenes_from_flags, tuple_indices, tuple_map)
 from .net import (Net, conv2d_direct, conv2d_im2col, dcn2d, leaky_relu,
-                  oracle_threads, pixel_shuffle, sigmoid, upsample_bilinear,
+                  oracle_threads, pixel_shuffle, pool2, sigmoid, upsample_bilinear,
                   upsample_nearest)
 
 __all__ = [
@@ -46,7 +46,7 @@ __all__ = [
     "downsample_chroma", "fig1_layout", "fig1_next_batch_copy", "fig1_slot_frames",
     "group_output_count", "group_outputs", "group_runs", "ingest", "outputs_per_frame",
     "passthrough", "leaky_relu", "normalise_chroma",
-    "normalise_luma", "oracle_threads", "pad_to_align", "pixel_shuffle", "quantise",
+    "normalise_luma", "oracle_threads", "pad_to_align", "pixel_shuffle", "pool2", "quantise",
     "requantise", "rgb_to_ycbcr", "run_filter", "scale_chroma", "scale_luma",
     "scene_of", "scenes_from_flags", "sigmoid", "tuple_indices", "tuple_map",
     "upsample_bilinear", "upsample_chroma", "upsample_nearest", "ycbcr_to_rgb",

@@ -23,6 +23,10 @@ definitions:
 * DCN v2: see oracle_conv.c; the head's output channels [0, 18G) are offsets
   (dy, dx interleaved per (group, tap)), [18G, 27G) are mask logits and the
   mask is their logistic sigmoid.
+* pool: the 2x2 mean, out[c, y, x] = mean of in[c, 2y + i, 2x + j] (i, j in {0, 1});
+  with up (bilinear x2, align_corners = False, edge clamp) it builds the extract
+  stage's feature pyramid "in different spatial dimensions" (Section 3.1).
+  Reading: both need even sizes (the engine rejects other frame sizes).
 """
 from __future__ import annotations
 
@@ -151,6 +155,14 @@ def upsample_bilinear(x, s: int, sy: int | None = None):
     return top * (1 - fy)[None, :, None] + bot * fy[None, :, None]
 
 
+def pool2(x):
+    """2x2 mean of [C][H][W] (H, W even) -> [C][H/2][W/2]."""
+    x = np.asarray(x, np.float64)
+    c, h, w = x.shape
+    assert h % 2 == 0 and w % 2 == 0
+    return x.reshape(c, h // 2, 2, w // 2, 2).mean(axis=(2, 4))
+
+
 def upsample_nearest(x, s: int, sy: int | None = None):
     sy = s if sy is None else sy
     return np.repeat(np.repeat(np.asarray(x, np.float64), sy, axis=1), s, axis=2)
@@ -228,6 +240,12 @@ class Net:
                     pos += nw + co
                 by_name[layer.name] = layer
                 self.layers.append(layer)
+            elif key in ("pool", "up"):
+                attrs = dict(t.split("=", 1) for t in tok[2:])
+                attrs["cin"] = attrs["cout"] = int(attrs["cin"])
+                layer = Layer(key, tok[1], attrs)
+                by_name[layer.name] = layer
+                self.layers.append(layer)
             elif key == "out":
                 attrs = dict(t.split("=", 1) for t in tok[2:])
                 self.outputs.append((tok[1], attrs.get("skip")))
@@ -263,6 +281,12 @@ class Net:
         for layer in self.layers:
             srcs = layer.get("in").split(",")
             x = np.concatenate([env[s] for s in srcs]) if len(srcs) > 1 else env[srcs[0]]
+            if layer.op == "pool":
+                env[layer.name] = pool2(x)
+                continue
+            if layer.op == "up":
+                env[layer.name] = upsample_bilinear(x, 2)
+                continue
             if layer.op == "conv":
                 y = conv2d_direct(x, layer.w, layer.b)
             else:
@@ -297,7 +321,7 @@ class Net:
         """
         r = 0
         for layer in self.layers:
-            if layer.op == "dcn":
-                raise ValueError("DCN reach is data dependent")
+            if layer.op in ("dcn", "pool", "up"):
+                raise ValueError("DCN reach is data dependent; pyramids change the scale")
             r += (layer.get("k") - 1) // 2
         return r + 1  # +1 for the bilinear skip's neighbours

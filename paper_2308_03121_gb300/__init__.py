@@ -83,11 +83,11 @@ class FrameInfo(ctypes.Structure):
 OUT_NETWORK, OUT_PASSTHROUGH = 0, 1
 
 
+KINDS = ("ingest", "pack", "conv_head", "conv_body", "conv_tail", "requant", "dcn", "conv_other", "resample")
+
+
 class Profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8)]
-
-
-KINDS = ("ingest", "pack", "conv_head", "conv_body", "conv_tail", "requant", "dcn", "conv_other")
+    _fields_ = [("ms", ctypes.c_double * len(KINDS)), ("launches", ctypes.c_int64 * len(KINDS))]
 
 _LIB = None
 _VP, _I32, _I64, _F32P = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_float)
@@ -108,6 +108,7 @@ _SIGS = {
     "nvisr_engine_step": (_I32, [_VP, _I32, _I32P]),
     "nvisr_filter_profile": (_I32, [_VP, _I32]),
     "nvisr_filter_profile_read": (_I32, [_VP, ctypes.POINTER(Profile)]),
+    "nvisr_filter_cache_stats": (_I32, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "nvisr_status_string": (ctypes.c_char_p, [_I32]),
     "nvisr_last_error": (ctypes.c_char_p, [_VP]),
     "nvisr_network_check": (_I32, [ctypes.c_char_p, _I64]),
@@ -536,6 +537,12 @@ class Filter:
 
     def profile(self, enable=True):
         _check(_LIB.nvisr_filter_profile(self.h, 1 if enable else 0), "nvisr_filter_profile")
+
+    def cache_stats(self):
+        """(hits, misses) of the extract-stage cache (two-frame group networks)."""
+        h, m = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(_LIB.nvisr_filter_cache_stats(self.h, ctypes.byref(h), ctypes.byref(m)), "nvisr_filter_cache_stats")
+        return h.value, m.value
 
     def profile_read(self):
         """{kind: (total ms, launches)} since profiling was enabled."""

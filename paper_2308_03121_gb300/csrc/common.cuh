@@ -240,6 +240,12 @@ cudaError_t launch_dcn_relayout8(const void *x, int cpad, int H, int W, int x_cp
 
 int device_sm_count();
 
+// Feature-pyramid resampling on blocked [C/cpc][H][W][cpc] tensors of dtype dt (x: H x W):
+// up = false: 2x2 mean into (H/2) x (W/2) (H, W even); up = true: bilinear x2
+// (align_corners = False, edge clamp) into 2H x 2W.
+cudaError_t launch_resample2(bool up, int dt, const void *x, int xcpc, void *y, int ycpc, int C, int H, int W,
+                             cudaStream_t st);
+
 // Test drill of the calling thread (nvisr_test_starve): when set, the tensor-core
 // kernels it launches load no input, so their first pipeline wait runs out.
 int test_starve();

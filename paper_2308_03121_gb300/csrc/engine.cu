@@ -138,7 +138,7 @@ struct Weights {
 
 enum Src { SRC_TENSOR = 0, SRC_TUPLE = 1 };
 
-enum Op { OP_CONV = 0, OP_DCN = 1, OP_PACK = 2 };
+enum Op { OP_CONV = 0, OP_DCN = 1, OP_PACK = 2, OP_POOL = 3, OP_UP = 4 };
 
 struct Step {
     int op = OP_CONV;
@@ -151,6 +151,11 @@ struct Step {
     int src = SRC_TENSOR;
     int frame_src = -1;  // group family: input from ring frame k
     std::vector<int> perm;  // group family: input channel c of the layer is stored channel perm[c]
+    // extract cache: the frame slot whose features this step computes (-1: none), and for a
+    // reader of a cached pair the weights variant per pair order (frame slot 0's part first, or
+    // frame slot 1's part first)
+    int xslot = -1;
+    int xpair_w[2] = {-2, -2};
     int add_t = -1;
     int out_t = -1;      // -1: final output (PixelShuffle into planar float32)
     int out_index = -1;  // final output number
@@ -260,6 +265,16 @@ struct nvisr_filter {
 
     // group family: run cache (outputs of the last run)
     int64_t cached_run = -1;
+
+    // extract cache (Section 3.1: the extract stage works on one frame): a two-frame group
+    // network whose per-frame features feed channel concatenations of the two frames keeps
+    // those concatenation buffers across runs.  Half h of every such buffer holds the
+    // features of frame xc_tag[h]; a run computes only the frames no half holds.
+    bool xcache = false;
+    int64_t xc_tag[2] = {-1, -1};
+    struct XPair { int parent; int part[2]; };  // part[k]: tensor of frame slot k's features
+    std::vector<XPair> xpairs;
+    int64_t xc_hits = 0, xc_misses = 0;
 
     // FP8 calibration
     bool calibrated = false;
@@ -647,6 +662,7 @@ nvisr_status prepare_weights(nvisr_filter *f, const float *blob) {
     f->om_tap_g = om_tap_major_groups(net);
     for (size_t i = 0; i < net.layers.size(); ++i) {
         const NetLayer &L = net.layers[i];
+        if (L.op == "pool" || L.op == "up") continue;  // no weights
         if (L.owner != (int)i) {
             f->weights[i] = f->weights[L.owner];
             continue;
@@ -916,7 +932,7 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
         const NetLayer &L = net.layers[i];
         Step st;
         st.layer = (int)i;
-        st.op = L.op == "dcn" ? OP_DCN : OP_CONV;
+        st.op = L.op == "dcn" ? OP_DCN : (L.op == "pool" ? OP_POOL : (L.op == "up" ? OP_UP : OP_CONV));
         if (L.in.size() == 1) {
             st.in_t = source(L.in[0]);
         } else {
@@ -986,7 +1002,17 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
             if (st.skip_frames.size() > 2) return fail(NVISR_UNSUPPORTED_FORMAT, "at most two skip frames");
         } else {
             const int C = L.ps ? L.cout / 4 : L.cout;
-            const int h = L.ps ? 2 * src.H : src.H, w = L.ps ? 2 * src.W : src.W;
+            int h = L.ps ? 2 * src.H : src.H, w = L.ps ? 2 * src.W : src.W;
+            if (st.op == OP_POOL) {
+                if (src.H % 2 || src.W % 2)
+                    return fail(NVISR_UNSUPPORTED_FORMAT, "layer " + L.name + ": the 2x2 pool needs even sizes (" +
+                                                              std::to_string(src.W) + "x" + std::to_string(src.H) + ")");
+                h = src.H / 2;
+                w = src.W / 2;
+            } else if (st.op == OP_UP) {
+                h = 2 * src.H;
+                w = 2 * src.W;
+            }
             const int dt = om_names.count(L.name) ? DT_F32 : f->act_dt;
             const int cpad = L.ps ? round_up(C, 16) : round_up(L.cout, 16);
             const int id = new_tensor(C, cpad, h, w, dt);
@@ -1005,9 +1031,115 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
         }
         f->steps.push_back(st);
     }
-    // liveness on root tensors (views count as their parent)
+    // ---- extract cache (Section 3.1: the extract stage works on a single frame, so a
+    // frame's features serve every run that takes it).  Two-frame networks only: a step is
+    // an extract step when it depends on one frame slot and its output is a part of a
+    // concatenation of both frames' features ("pair"), or feeds only extract steps.  The
+    // pairs' buffers persist across runs; each of their halves holds one frame's features.
     const int n = (int)f->tensors.size();
     auto root = [&](int t) { return f->tensors[t].parent >= 0 ? f->tensors[t].parent : t; };
+    f->xcache = false;
+    f->xpairs.clear();
+    std::vector<char> persistent(n, 0);
+    if (net.frames == 2) {
+        std::vector<int> mask(n, 0);                 // frame slots a tensor depends on
+        std::vector<std::string> sig(n);             // the function of its frame that it is
+        std::vector<int> producer(n, -1);
+        for (size_t i = 0; i < f->steps.size(); ++i) {
+            const Step &st = f->steps[i];
+            if (st.out_t < 0) continue;
+            int m = 0;
+            std::string sg;
+            if (st.op == OP_PACK) {
+                m = 1 << st.frame_src;
+                sg = "frame";
+            } else {
+                const NetLayer &L = net.layers[st.layer];
+                const bool weightless = st.op == OP_POOL || st.op == OP_UP;
+                sg = L.op + ":" + (weightless ? std::string("-") : std::to_string(L.owner)) + ":" +
+                     std::to_string(L.act) + ":" + std::to_string(L.ps) + "(";
+                for (int u : {st.in_t, st.add_t, st.om_t})
+                    if (u >= 0) {
+                        m |= mask[u];
+                        sg += sig[u] + ",";
+                    }
+                sg += ")";
+            }
+            mask[st.out_t] |= m;
+            sig[st.out_t] = sg;
+            producer[st.out_t] = (int)i;
+            if (f->tensors[st.out_t].parent >= 0) mask[f->tensors[st.out_t].parent] |= m;
+        }
+        // pairs: concatenations of exactly two parts, the same function of frame slots 0 and 1
+        bool ok = true;
+        std::vector<int> part_of_pair(n, 0);
+        for (int t = 0; t < n && ok; ++t) {
+            std::vector<int> parts;
+            for (int c = 0; c < n; ++c)
+                if (f->tensors[c].parent == t) parts.push_back(c);
+            if (parts.empty()) continue;
+            const bool single = parts.size() == 2 && (mask[parts[0]] == 1 || mask[parts[0]] == 2) &&
+                                (mask[parts[1]] == 1 || mask[parts[1]] == 2);
+            if (!single) {
+                // a concatenation of other tensors (the alignment's blends): not cached, but it
+                // must not hold single-frame parts either
+                for (int c : parts)
+                    if (mask[c] == 1 || mask[c] == 2) ok = false;
+                continue;
+            }
+            if (mask[parts[0]] == mask[parts[1]] || sig[parts[0]] != sig[parts[1]] ||
+                f->tensors[parts[0]].C != f->tensors[parts[1]].C || f->tensors[parts[0]].choff != 0) {
+                ok = false;
+                break;
+            }
+            nvisr_filter::XPair xp;
+            xp.parent = t;
+            for (int c : parts) {
+                xp.part[mask[c] == 1 ? 0 : 1] = c;
+                part_of_pair[c] = 1;
+            }
+            f->xpairs.push_back(xp);
+        }
+        if (f->xpairs.empty()) ok = false;
+        // extract steps, from the last step back: single-frame steps whose output is a pair
+        // part, or is read only by extract steps
+        std::vector<char> is_x(f->steps.size(), 0);
+        for (int i = (int)f->steps.size() - 1; i >= 0 && ok; --i) {
+            const Step &st = f->steps[i];
+            if (st.out_t < 0 || (mask[st.out_t] != 1 && mask[st.out_t] != 2)) continue;
+            bool x = part_of_pair[st.out_t] != 0;
+            if (!x) {
+                int readers = 0;
+                bool all = true;
+                for (size_t j = 0; j < f->steps.size(); ++j) {
+                    const Step &r = f->steps[j];
+                    if (r.in_t == st.out_t || r.add_t == st.out_t || r.om_t == st.out_t) {
+                        ++readers;
+                        all = all && is_x[j];
+                    }
+                }
+                x = readers > 0 && all;
+            }
+            is_x[i] = x;
+        }
+        // readers of a pair's buffer are two-input convolutions (weights per pair order)
+        for (size_t i = 0; i < f->steps.size() && ok; ++i) {
+            const Step &st = f->steps[i];
+            for (const nvisr_filter::XPair &xp : f->xpairs)
+                if (st.in_t == xp.parent && (st.op != OP_CONV || net.layers[st.layer].in.size() != 2)) ok = false;
+            for (int u : {st.add_t, st.om_t})
+                for (const nvisr_filter::XPair &xp : f->xpairs)
+                    if (u == xp.parent) ok = false;
+        }
+        if (ok) {
+            f->xcache = true;
+            for (size_t i = 0; i < f->steps.size(); ++i)
+                if (is_x[i]) f->steps[i].xslot = mask[f->steps[i].out_t] == 1 ? 0 : 1;
+            for (const nvisr_filter::XPair &xp : f->xpairs) persistent[xp.parent] = 1;
+        }
+    }
+
+    // liveness on root tensors (views count as their parent)
     std::vector<int> first_def(n, 1 << 30), last_use(n, -1);
     for (size_t i = 0; i < f->steps.size(); ++i) {
         const Step &st = f->steps[i];
@@ -1017,9 +1149,15 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
     }
     struct Buf { void *p; size_t bytes; int free_after; };
     std::vector<Buf> pool;
+    for (int t = 0; t < n; ++t)
+        if (persistent[t]) {  // cached pairs: their own buffers, kept across runs
+            Tensor &T = f->tensors[t];
+            nvisr_status s = dalloc(f->eng, (size_t)T.cpad * T.H * T.W * dtype_size(T.dt), f->owned, &T.ptr);
+            if (s != NVISR_OK) return s;
+        }
     for (int step = 0; step < (int)f->steps.size(); ++step) {
         for (int t = 0; t < n; ++t) {
-            if (f->tensors[t].parent >= 0 || first_def[t] != step) continue;
+            if (f->tensors[t].parent >= 0 || first_def[t] != step || persistent[t]) continue;
             Tensor &T = f->tensors[t];
             const size_t bytes = (size_t)T.cpad * T.H * T.W * dtype_size(T.dt);
             void *got = nullptr;
@@ -1037,7 +1175,7 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
             T.ptr = got;
         }
         for (int t = 0; t < n; ++t)
-            if (f->tensors[t].parent < 0 && last_use[t] == step && f->tensors[t].ptr)
+            if (f->tensors[t].parent < 0 && last_use[t] == step && f->tensors[t].ptr && !persistent[t])
                 for (Buf &b : pool)
                     if (b.p == f->tensors[t].ptr) b.free_after = step;
     }
@@ -1069,6 +1207,54 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
         if (s != NVISR_OK) return s;
         st.widx = (int)f->wvar.size();
         f->wvar.push_back(Wv);
+    }
+    // extract cache: a pair whose buffer was narrowed to 16-byte chunks is not cached; the
+    // readers of a cached pair get their weights for both orders of its halves
+    for (const nvisr_filter::XPair &xp : f->xpairs) {
+        const Tensor &P = f->tensors[xp.parent];
+        if (P.cpc != layout_cpc(P.dt, P.cpad)) f->xcache = false;
+    }
+    if (!f->xcache) {
+        for (Step &st : f->steps) st.xslot = -1;
+        f->xpairs.clear();
+    }
+    for (Step &st : f->steps) {
+        if (!f->xcache || st.op != OP_CONV) continue;
+        const nvisr_filter::XPair *xp = nullptr;
+        for (const nvisr_filter::XPair &q : f->xpairs)
+            if (st.in_t == q.parent) xp = &q;
+        if (!xp) continue;
+        const NetLayer &L = net.layers[st.layer];
+        const int C = f->tensors[xp->part[0]].C;
+        // the frame slot whose features are the layer's first input
+        int slot_first = -1;
+        for (int k = 0; k < 2; ++k)
+            for (const Step &q : f->steps)
+                if (q.out_t == xp->part[k] && q.op != OP_PACK && net.layers[q.layer].name == L.in[0]) slot_first = k;
+        if (slot_first < 0) return fail(NVISR_INTERNAL, "layer " + L.name + ": pair part not found");
+        const int kk = L.k * L.k;
+        const float *w = blob + net.layers[L.owner].woff;
+        const float *b = w + (int64_t)L.cout * L.cin * kk;
+        for (int order = 0; order < 2; ++order) {
+            // order 0: the buffer holds frame slot 0's features first; 1: slot 1's first
+            const bool swapped = (slot_first != order);
+            if (!swapped) {
+                st.xpair_w[order] = -1;  // the layer's own weights
+                continue;
+            }
+            std::vector<float> wp((size_t)L.cout * L.cin * kk);
+            for (int o = 0; o < L.cout; ++o)
+                for (int c = 0; c < L.cin; ++c) {
+                    const int src = c < C ? c + C : c - C;  // stored channel c holds layer channel src
+                    for (int t = 0; t < kk; ++t)
+                        wp[((size_t)o * L.cin + c) * kk + t] = w[((size_t)o * L.cin + src) * kk + t];
+                }
+            Weights Wv;
+            nvisr_status s = upload_layer(f, st.layer, wp.data(), b, Wv);
+            if (s != NVISR_OK) return s;
+            st.xpair_w[order] = (int)f->wvar.size();
+            f->wvar.push_back(Wv);
+        }
     }
     // the tensor-core DCN gathers from its input copied into 8-channel planes
     size_t x8 = 0;
@@ -1110,6 +1296,7 @@ void set_final_skip(nvisr_filter *f, const Step &s, const float *const *frames) 
 int step_kind(const nvisr_filter *f, const Step &s) {
     if (s.op == OP_DCN) return NVISR_K_DCN;
     if (s.op == OP_PACK) return NVISR_K_PACK;
+    if (s.op == OP_POOL || s.op == OP_UP) return NVISR_K_RESAMPLE;
     const NetLayer &L = f->net.layers[s.layer];
     return s.out_t < 0 ? NVISR_K_CONV_TAIL
                        : (s.src == SRC_TUPLE ? NVISR_K_CONV_HEAD
@@ -1206,6 +1393,14 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
     const Weights &Wt = s.widx >= 0 ? f->wvar[s.widx] : f->weights[s.layer];
     const Tensor &in = f->tensors[s.in_t];
     cudaStream_t st = f->eng->stream;
+    if (s.op == OP_POOL || s.op == OP_UP) {
+        const Tensor &o = f->tensors[s.out_t];
+        ProfScope ps(f, NVISR_K_RESAMPLE);
+        const cudaError_t e =
+            launch_resample2(s.op == OP_UP, in.dt, in.ptr, in.cpc, o.ptr, o.cpc, in.C, in.H, in.W, st);
+        if (e != cudaSuccess) return cuda_status(e, ("resample layer " + L.name).c_str());
+        return NVISR_OK;
+    }
     if (s.op == OP_DCN) {
         const Tensor &om = f->tensors[s.om_t];
         const Tensor &o = f->tensors[s.out_t];
@@ -1299,12 +1494,56 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
     return NVISR_OK;
 }
 
+// Extract cache of a run over frames (a, b): which half of the pair buffers holds each
+// frame slot's features (h[k]) and whether the run computes them (need[k]).  A half keeps
+// the frame it holds until a run needs it for a frame no half holds.
+void xcache_plan(nvisr_filter *f, const std::vector<int64_t> &idx, int h[2], bool need[2]) {
+    const int64_t fr[2] = {idx[0], idx[1]};
+    const int64_t *tag = f->xc_tag;
+    if (fr[0] == fr[1]) {
+        h[0] = 0;
+        h[1] = 1;
+    } else {
+        const int ha = tag[0] == fr[0] ? 0 : (tag[1] == fr[0] ? 1 : -1);
+        const int hb = tag[0] == fr[1] ? 0 : (tag[1] == fr[1] ? 1 : -1);
+        h[0] = ha >= 0 ? ha : (hb >= 0 ? 1 - hb : 0);
+        h[1] = 1 - h[0];
+    }
+    for (int k = 0; k < 2; ++k) need[k] = tag[h[k]] != fr[k];
+}
+
 // Group family: one run over frames (idx[0], idx[1], ...) computing every output.
 nvisr_status forward_group(nvisr_filter *f, const std::vector<int64_t> &idx) {
     const float *frames[8];
     for (size_t k = 0; k < idx.size() && k < 8; ++k) frames[k] = ring_slot(f, idx[k]);
+    int h[2] = {0, 1};
+    bool need[2] = {true, true};
+    if (f->xcache) {
+        xcache_plan(f, idx, h, need);
+        // each frame slot's features: the half of every pair buffer chosen for it
+        for (const nvisr_filter::XPair &xp : f->xpairs) {
+            const Tensor &P = f->tensors[xp.parent];
+            for (int k = 0; k < 2; ++k) {
+                Tensor &T = f->tensors[xp.part[k]];
+                T.choff = h[k] * T.C;
+                T.ptr = (uint8_t *)P.ptr + (size_t)(T.choff / P.cpc) * P.H * P.W * P.cpc * dtype_size(P.dt);
+            }
+        }
+        const int order = h[0] == 0 ? 0 : 1;
+        for (Step &st : f->steps)
+            if (st.xpair_w[order] > -2) st.widx = st.xpair_w[order];
+        for (int k = 0; k < 2; ++k) {
+            if (need[k]) {
+                f->xc_tag[h[k]] = -1;  // set once the run is enqueued
+                ++f->xc_misses;
+            } else {
+                ++f->xc_hits;
+            }
+        }
+    }
     for (size_t i = 0; i < f->steps.size(); ++i) {
         const Step &s = f->steps[i];
+        if (s.xslot >= 0 && !need[s.xslot]) continue;  // features held by the cache
         hold_if_same_kind(f, i);
         if (s.op == OP_PACK) {
             const Tensor &t = f->tensors[s.out_t];
@@ -1333,6 +1572,8 @@ nvisr_status forward_group(nvisr_filter *f, const std::vector<int64_t> &idx) {
         if (st != NVISR_OK) return st;
     }
     f->prof_hold = false;
+    if (f->xcache)
+        for (int k = 0; k < 2; ++k) f->xc_tag[h[k]] = idx[k];
     return NVISR_OK;
 }
 
@@ -1459,6 +1700,7 @@ nvisr_status write_output_end(nvisr_filter *f) {
         for (nvisr_filter *g : e->filters) {
             g->produced.clear();
             g->cached_run = -1;
+            g->xc_tag[0] = g->xc_tag[1] = -1;
         }
         prof_gap(f);
         return fail(NVISR_DEVICE_TIMEOUT, "a device-side wait exceeded its time bound (error word " +
@@ -1961,6 +2203,13 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
         info->kind = kind;
     }
     f->next_out++;
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_filter_cache_stats(nvisr_filter *f, int64_t *hits, int64_t *misses) {
+    if (!f || !hits || !misses) return fail(NVISR_INVALID_ARG, "cache_stats: NULL argument");
+    *hits = f->xc_hits;
+    *misses = f->xc_misses;
     return NVISR_OK;
 }
 

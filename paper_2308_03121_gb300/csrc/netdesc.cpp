@@ -158,6 +158,24 @@ bool parse_netdesc(const char *text, int64_t blob_count, NetDesc *net, std::stri
             }
             known.insert(L.name);
             net->layers.push_back(L);
+        } else if (key == "pool" || key == "up") {
+            // weightless resampling of the extract stage's pyramid (Section 3.1): a 2x2 mean,
+            // or a bilinear x2 upsample; cin = cout = the source's channels
+            if (tok.size() != 4) return fail(key + " needs a name, in= and cin=");
+            NetLayer L;
+            L.op = key;
+            L.name = tok[1];
+            L.k = 1;
+            for (size_t i = 2; i < 4; ++i) {
+                if (tok[i].rfind("in=", 0) == 0) L.in = {tok[i].substr(3)};
+                else if (tok[i].rfind("cin=", 0) == 0 && to_int(tok[i].substr(4), &L.cin)) L.cout = L.cin;
+                else return fail("bad " + key + " attribute " + tok[i]);
+            }
+            if (L.in.size() != 1 || L.cin < 1 || L.cin > 1024) return fail(key + " needs in= and cin=");
+            if (!known.count(L.in[0])) return fail("unknown source " + L.in[0]);
+            L.owner = (int)net->layers.size();
+            known.insert(L.name);
+            net->layers.push_back(L);
         } else if (key == "out") {
             if (tok.size() < 2) return fail("out without name");
             NetOutput o;

@@ -175,6 +175,8 @@ class NetSpec:
         conv <name> in=<a>[,<b>] cin=<C> cout=<N> k=<1|3> act=none|lrelu
              [add=<name>] [ps=<r> | psx=<rx> psy=<ry>] [share=<name>]
         dcn  <name> in=<x> om=<head> cin=<C> cout=<N> groups=<G> [share=<name>]
+        pool <name> in=<x> cin=<C>         (2x2 mean: half the height and width)
+        up   <name> in=<x> cin=<C>         (bilinear x2: twice the height and width)
         out  <name> [skip=<frame>[,<frame>]]
 
     Weights of every non-shared layer are appended to the blob in statement
@@ -215,6 +217,12 @@ class NetSpec:
         else:
             self.blobs.append(_he_normal(rng, cout, cin, 3, gain, None))
         self.lines.append(line)
+
+    def pool(self, name, src, cin):
+        self.lines.append(f"pool {name} in={src} cin={cin}")
+
+    def up(self, name, src, cin):
+        self.lines.append(f"up {name} in={src} cin={cin}")
 
     def out(self, name, skip=None):
         self.lines.append(f"out {name}" + (f" skip={skip}" if skip else ""))
@@ -328,6 +336,61 @@ def net_group_stvsr(seed: int, channels: int = 64, groups: int = 8, nres: int = 
 
 def net_config3(seed: int = BASE_SEED + 3):
     return net_group_stvsr(seed)
+
+
+def net_group_pyramid(seed: int, channels: int = 64, groups: int = 8, nres: int = 6, levels: int = 3,
+                      tail_gain: float = TAIL_GAIN, res_gain: float = RES_GAIN,
+                      offset_gain: float = OFFSET_GAIN):
+    """Two-frame space-time SR network whose extract stage is a feature pyramid (4x, 2x frame rate).
+
+    Extract, per frame (shared weights): e1 = lrelu(conv 3->C), and for each coarser level
+    l, e_l = lrelu(conv C->C (pool(e_{l-1}))) at half the previous height and width.
+    Alignment of frame a (a = 0, 1; shared weights for both) at every level l, coarse to
+    fine: an offset/mask head conv 2C->27G over cat(e_l of a, e_l of the other frame), a
+    modulated deformable conv C->C of e_l of a, and below the coarsest level a 1x1 blend
+    2C->C of that with the upsampled (bilinear x2) alignment of the level below.  Then
+    the midpoint features are a 1x1 blend 2C->C of both frames' finest alignments, and
+    the residual trunk and upsampler of net_group_stvsr run on frame 0's finest
+    features and on the midpoint.  Frame sizes must be multiples of 2^(levels-1).
+    """
+    rng = np.random.default_rng(seed)
+    C, G = channels, groups
+    spec = NetSpec("group", 2, 4, "bilinear", flags="interp,extra,double")
+    head_rows = np.ones(27 * G)
+    head_rows[: 18 * G] = offset_gain
+    for k in range(2):
+        spec.conv(rng, f"e1f{k}", f"frame{k}", 3, C, act="lrelu", share="e1f0" if k else None)
+        for lv in range(2, levels + 1):
+            spec.pool(f"p{lv - 1}f{k}", f"e{lv - 1}f{k}", C)
+            spec.conv(rng, f"e{lv}f{k}", f"p{lv - 1}f{k}", C, C, act="lrelu", share=f"e{lv}f0" if k else None)
+    for a in range(2):
+        b = 1 - a
+        for lv in range(levels, 0, -1):
+            sh = (lambda n: f"{n}a0") if a else (lambda n: None)
+            spec.conv(rng, f"om{lv}a{a}", f"e{lv}f{a},e{lv}f{b}", 2 * C, 27 * G, act="none",
+                      row_gains=head_rows, share=sh(f"om{lv}"))
+            spec.dcn(rng, f"al{lv}a{a}", f"e{lv}f{a}", f"om{lv}a{a}", C, C, G, share=sh(f"al{lv}"))
+            if lv == levels:
+                continue
+            spec.up(f"u{lv}a{a}", f"d{lv + 1}a{a}" if lv + 1 < levels else f"al{lv + 1}a{a}", C)
+            spec.conv(rng, f"d{lv}a{a}", f"al{lv}a{a},u{lv}a{a}", 2 * C, C, k=1, act="none", share=sh(f"d{lv}"))
+    fin = [f"d1a{a}" if levels > 1 else f"al1a{a}" for a in range(2)]
+    spec.conv(rng, "mid", ",".join(fin), 2 * C, C, k=1, act="none")
+    for trunk, src in (("t", "e1f0"), ("m", "mid")):
+        prev = src
+        for i in range(nres):
+            sa = None if trunk == "t" else f"t{i}a"
+            sb = None if trunk == "t" else f"t{i}b"
+            spec.conv(rng, f"{trunk}{i}a", prev, C, C, act="lrelu", share=sa)
+            spec.conv(rng, f"{trunk}{i}b", f"{trunk}{i}a", C, C, act="none", add=prev, share=sb, gain=res_gain)
+            prev = f"{trunk}{i}b"
+        su = None if trunk == "t" else "tu1"
+        sv = None if trunk == "t" else "tu2"
+        spec.conv(rng, f"{trunk}u1", prev, C, 4 * C, act="lrelu", ps=2, share=su)
+        spec.conv(rng, f"{trunk}u2", f"{trunk}u1", C, 12, act="none", ps=2, share=sv, gain=tail_gain)
+    spec.out("tu2", skip="frame0")
+    spec.out("mu2", skip="frame0,frame1")
+    return spec.build()
 
 
 def net_group_general(seed: int, n: int, extra: bool, interp: bool, double: bool, feat: int = 16,

@@ -177,6 +177,60 @@ STVSR_WINDOWS = [(0, 16, 0, 16), (0, 16, 944, 960), (524, 540, 944, 960), (270, 
                  (100, 116, 120, 136)]
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_pyramid_extract_network_matches_oracle(prec):
+    """A two-frame space-time network whose extract stage is a three-level feature pyramid
+    (Section 3.1), aligned by deformable convs at every level: 96x48 8-bit 4:2:0 -> 4x,
+    6 frames with a cut before frame 3, every output against the oracle."""
+    W, H, N = 96, 48, 6
+    frames = synth.frames_textured(synth.BASE_SEED + 80, N, W, H, 8, "420", "limited")
+    flags = np.zeros(N, bool)
+    flags[3] = True
+    text, blob = synth.net_group_pyramid(synth.BASE_SEED + 81, nres=2)
+    fdo = fmt_dict(4 * W, 4 * H, 8)
+    ref = oracle.run_filter(frames, flags, text, blob, fmt_dict(W, H, 8), fdo, keep_float=True)
+    outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(4 * W, 4 * H, 8), prec, scale=4)
+    assert len(outs) == len(ref) == 2 * N
+    assert [i[1:3] for i in infos] == [(0, 1), (0, 1), (1, 2), (1, 2), (2, 2), (2, 2),
+                                       (3, 4), (3, 4), (4, 5), (4, 5), (5, 5), (5, 5)]
+    for got, r in zip(outs, ref):
+        pq = prequant(r, fdo)
+        if prec == "fp32":
+            assert_codes_match(got, pq, 8)
+        else:
+            mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 8) for k in "YUV"})
+            assert mx <= 1, mx
+
+
+@pytest.mark.parametrize("net", ["pyramid", "config3"])
+def test_extract_cache_reuses_each_frames_features(net):
+    """The extract stage's features of a frame are computed once and reused by the next run
+    that takes the frame: 6 frames, a cut before frame 3, runs (0,1) (1,2) (2,2) (3,4) (4,5)
+    (5,5) compute 2, 1, 1, 2, 1, 1 frames' features (4 hits, 8 misses).  The reused
+    features' correctness is what the parity tests of these networks check."""
+    W, H, N = 64, 32, 6
+    frames = synth.frames_textured(synth.BASE_SEED + 82, N, W, H, 8, "420", "limited")
+    flags = np.zeros(N, bool)
+    flags[3] = True
+    text, blob = (synth.net_group_pyramid(synth.BASE_SEED + 81, nres=1) if net == "pyramid"
+                  else synth.net_config3())
+    eng = nv.Engine()
+    flt = eng.filter(text, blob, nv.fmt(W, H, 8), nv.fmt(4 * W, 4 * H, 8), "bf16", 4)
+    for i, fr in enumerate(frames):
+        assert flt.push((fr["Y"], fr["U"], fr["V"]), cut=bool(flags[i])) == nv.Status.OK
+    flt.flush()
+    outs = []
+    while True:
+        o = flt.alloc_out_host()
+        st, _ = flt.pull(o)
+        if st == nv.Status.EOS:
+            break
+        outs.append(o)
+    assert len(outs) == 2 * N
+    assert flt.cache_stats() == (4, 8)
+    eng.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_config3_full_size_sampled_windows(prec):
     """960x540 8-bit, the deformable ST-SR network in the bench's launch shapes: both outputs

@@ -21,7 +21,7 @@ import torch.nn.functional as F
 import oracle
 import synth
 
-torch.set_default_dtype(torch.float64)
+F64 = torch.float64  # every tensor here is FP64 (no process-wide default is changed)
 
 
 class Blob:
@@ -121,9 +121,8 @@ def torch_dcn(x, om, wb, G):
     w, b = wb
     _, C, H, W = x.shape
     cg = C // G
-    yy, xx = torch.meshgrid(torch.arange(H, dtype=torch.float64), torch.arange(W, dtype=torch.float64),
-                            indexing="ij")
-    cols = torch.zeros(C, 9, H, W)
+    yy, xx = torch.meshgrid(torch.arange(H, dtype=F64), torch.arange(W, dtype=F64), indexing="ij")
+    cols = torch.zeros(C, 9, H, W, dtype=F64)
     for g in range(G):
         for k in range(9):
             ky, kx = divmod(k, 3)
@@ -235,3 +234,59 @@ def test_activation_comes_before_the_residual_add():
     want = F.pixel_shuffle(conv(r, rd.take(12, 16, 3)), 2) + up(_t(frames[1]), 2)
     assert rd.done()
     _cmp(oracle.Net(text, blob).forward(frames)[0], want)
+
+
+def torch_pyramid(frames, blob, C, G, nres, levels):
+    """The feature-pyramid space-time network: per-frame extract e1 = lrelu(conv(frame)),
+    e_l = lrelu(conv(avg_pool2x2(e_{l-1}))); per frame a, coarse to fine: offsets from
+    cat(e_l[a], e_l[other]), DCN of e_l[a], and below the coarsest level a 1x1 blend with
+    the bilinear x2 of the coarser alignment; midpoint = 1x1 blend of both; trunk and
+    upsampler as the two-frame network."""
+    rd = Blob(blob)
+    ew = [rd.take(C, 3, 3)] + [rd.take(C, C, 3) for _ in range(levels - 1)]
+    lw = {}
+    for lv in range(levels, 0, -1):
+        lw[lv] = {"om": rd.take(27 * G, 2 * C, 3), "dcn": rd.take(C, C, 3)}
+        if lv < levels:
+            lw[lv]["d"] = rd.take(C, 2 * C, 1)
+    midw = rd.take(C, 2 * C, 1)
+    blocks = [(rd.take(C, C, 3), rd.take(C, C, 3)) for _ in range(nres)]
+    u1 = rd.take(4 * C, C, 3)
+    u2 = rd.take(12, C, 3)
+    assert rd.done()
+    x = [_t(f) for f in frames]
+    e = []
+    for k in range(2):
+        lv = [lrelu(conv(x[k], ew[0]))]
+        for i in range(1, levels):
+            lv.append(lrelu(conv(F.avg_pool2d(lv[-1], 2), ew[i])))
+        e.append(lv)
+    fin = []
+    for a in range(2):
+        b = 1 - a
+        d = None
+        for lv in range(levels, 0, -1):
+            om = conv(torch.cat([e[a][lv - 1], e[b][lv - 1]], 1), lw[lv]["om"])
+            al = torch_dcn(e[a][lv - 1], om, lw[lv]["dcn"], G)
+            d = al if d is None else conv(torch.cat([al, up(d, 2)], 1), lw[lv]["d"])
+        fin.append(d)
+    mid = conv(torch.cat(fin, 1), midw)
+
+    def trunk(h):
+        for wa, wb in blocks:
+            h = h + conv(lrelu(conv(h, wa)), wb)
+        h = lrelu(F.pixel_shuffle(conv(h, u1), 2))
+        return F.pixel_shuffle(conv(h, u2), 2)
+
+    return [trunk(e[0][0]) + up(x[0], 4), trunk(mid) + (up(x[0], 4) + up(x[1], 4)) / 2]
+
+
+def test_pyramid_network_forward_matches_torch_model():
+    text, blob = synth.net_group_pyramid(synth.BASE_SEED + 99, channels=16, groups=2, nres=2, levels=3)
+    blob = _random_blob(text, blob, 99)
+    frames = _frames(99, 2, 12, 16)
+    got = oracle.Net(text, blob).forward(frames)
+    want = torch_pyramid(frames, blob, 16, 2, 2, 3)
+    assert len(got) == 2
+    for g, w in zip(got, want):
+        _cmp(g, w)

@@ -450,6 +450,13 @@ def test_dcn_fractional_offsets_match_scipy_bilinear():
     assert np.abs(got[0] - ref).max() < 1e-12
 
 
+def test_pool2_is_torch_avg_pool():
+    """The extract pyramid's 2x2 mean equals torch's avg_pool2d (kernel 2, stride 2)."""
+    x = np.random.default_rng(31).normal(size=(5, 6, 10))
+    ref = torch.nn.functional.avg_pool2d(torch.from_numpy(x)[None], 2)[0].numpy()
+    assert np.abs(oracle.pool2(x) - ref).max() < 1e-15
+
+
 # ------------------------------------------------------------------ C4/C5 grouping
 
 def test_scenes_and_tuple_map_config1():
