@@ -121,7 +121,16 @@ typedef struct nvisr_filter_desc {
                                   * (one-axis 2x, e.g. deinterlace); group networks: one scale */
     int32_t precision;           /* nvisr_precision */
     int32_t calib_frames;        /* FP8: frames whose activations set the scales (0 = 4) */
+    uint32_t options;            /* NVISR_OPT_* bits (0 = defaults) */
 } nvisr_filter_desc;
+
+/* nvisr_filter_desc.options.  By default a tuple network with a 2 x 2
+ * PixelShuffle output layer, on the tensor cores, with an RGB-domain network
+ * and no transfer function, requantises inside that layer's epilogue (skip,
+ * colour matrix, chroma downsampling, rounding and packing) instead of writing
+ * float32 R'G'B' for a separate requantise kernel; the codes are the same.
+ * NVISR_OPT_UNFUSED_OUTPUT keeps the separate kernel. */
+enum { NVISR_OPT_UNFUSED_OUTPUT = 1 };
 
 /* What an output frame is (nvisr_frame_info.kind). */
 enum {

@@ -72,7 +72,10 @@ class FilterDesc(ctypes.Structure):
     _fields_ = [("network_text", ctypes.c_char_p), ("weights", ctypes.POINTER(ctypes.c_float)),
                 ("weights_count", ctypes.c_int64), ("in_fmt", Format), ("out_fmt", Format),
                 ("scale_w", ctypes.c_int32), ("scale_h", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("calib_frames", ctypes.c_int32)]
+                ("calib_frames", ctypes.c_int32), ("options", ctypes.c_uint32)]
+
+
+OPT_UNFUSED_OUTPUT = 1
 
 
 class FrameInfo(ctypes.Structure):
@@ -369,8 +372,8 @@ class Engine:
         _check(_LIB.nvisr_engine_step(self.h, max_outputs, ctypes.byref(n)), "nvisr_engine_step")
         return n.value
 
-    def filter(self, net_text, blob, in_fmt, out_fmt, precision="fp32", scale=2, calib_frames=0):
-        return Filter(self, net_text, blob, in_fmt, out_fmt, precision, scale, calib_frames)
+    def filter(self, net_text, blob, in_fmt, out_fmt, precision="fp32", scale=2, calib_frames=0, options=0):
+        return Filter(self, net_text, blob, in_fmt, out_fmt, precision, scale, calib_frames, options)
 
     def batch(self, filters):
         return Batch(self, filters)
@@ -445,7 +448,7 @@ class Server:
         text = net_text.encode()
         sw, sh = scale if isinstance(scale, tuple) else (scale, scale)  # (horizontal, vertical)
         d = FilterDesc(text, blob.ctypes.data_as(_F32P), blob.size, in_fmt, out_fmt, sw, sh,
-                       PREC[precision] if isinstance(precision, str) else precision, calib_frames)
+                       PREC[precision] if isinstance(precision, str) else precision, calib_frames, 0)
         cid = ctypes.c_int64(0)
         _check(_LIB.nvisr_server_submit(self.h, ctypes.byref(d), ctypes.byref(cid)), "nvisr_server_submit")
         self.fmts[cid.value] = out_fmt
@@ -502,13 +505,14 @@ class Server:
 class Filter:
     """A filter: push integer frames, pull enhanced frames in presentation order."""
 
-    def __init__(self, engine, net_text, blob, in_fmt, out_fmt, precision="fp32", scale=2, calib_frames=0):
+    def __init__(self, engine, net_text, blob, in_fmt, out_fmt, precision="fp32", scale=2, calib_frames=0,
+                 options=0):
         self.engine = engine
         self._blob = np.ascontiguousarray(np.asarray(blob, np.float32))
         self._text = net_text.encode()
         sw, sh = scale if isinstance(scale, tuple) else (scale, scale)  # (horizontal, vertical)
         d = FilterDesc(self._text, self._blob.ctypes.data_as(_F32P), self._blob.size, in_fmt, out_fmt,
-                       sw, sh, PREC[precision] if isinstance(precision, str) else precision, calib_frames)
+                       sw, sh, PREC[precision] if isinstance(precision, str) else precision, calib_frames, options)
         h = ctypes.c_void_p()
         _check(_LIB.nvisr_filter_create(engine.h, ctypes.byref(d), ctypes.byref(h)), "nvisr_filter_create")
         self.h = h

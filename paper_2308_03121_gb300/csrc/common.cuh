@@ -69,6 +69,32 @@ struct SkipArgs {
     int scale_y;         // vertical scale when it differs from scale (0 = scale)
 };
 
+// Requantisation fused into a 2 x 2 PixelShuffle output layer's epilogue: the layer's
+// residual plus the bilinear x2 skip of one frame, R'G'B' -> Y'CbCr, chroma downsampling
+// (4:2:0) by siting, range scale, round half to even, clamp, packed into integer planes.
+// LEFT-sited 4:2:0 chroma at a 128-pixel strip's first column needs the previous strip's
+// last column: the two CTAs leave their columns' values in `edge`, and
+// launch_rq_edge_fixup finishes those samples.
+struct FusedRq {
+    int on;                   // 0: the layer writes planar float32 (no fusion)
+    int wide;                 // samples of more than 8 bits (16-bit storage)
+    int sub420;               // 4:2:0 (else 4:4:4)
+    int loc;                  // chroma siting (nvisr_chroma_loc)
+    float y_mul, y_add, c_mul, c_add, vmax;
+    float kr, kg, kb, cb_s, cr_s;
+    uint8_t *yp, *up, *vp;    // output planes
+    int64_t py, pu, pv;       // their pitches in bytes
+    const float *skip;        // skip frame, planar float32 [3][H][skip_pitch] (null: no skip)
+    int64_t skip_pitch, skip_plane;
+    float *edge;              // LEFT 4:2:0: 6 floats per (LR row, 128-pixel column tile)
+};
+// Colour constants of an output format for the fused form: false when the format or the
+// network domain is not one it serves (transfer functions, Y'CbCr-domain networks, RGB planes).
+bool fused_rq_format(const nvisr_format &f, int yuv, FusedRq *rq);
+// Finishes the LEFT-sited 4:2:0 chroma samples at the first column of each 128-pixel tile
+// after x = 0 (H low-resolution rows, W low-resolution columns).
+cudaError_t launch_rq_edge_fixup(const FusedRq &rq, int H, int W, cudaStream_t st);
+
 // A final layer's float32 output, blocked [cpad/4][H][W][4], PixelShuffled by (ry, rx) into
 // planar [C / (ry*rx)][H*ry][dst_pitch]: dst[c][ry*y + i][rx*x + j] = src channel
 // c*ry*rx + i*rx + j at (y, x).  C = 3 * ry * rx.
@@ -132,6 +158,7 @@ struct ConvArgs {
     float y2_scale;
     unsigned *amax;          // optional max |y| (float bits) for calibration
     // final layer: PixelShuffle(ps) into planar float32 + skip
+    FusedRq rq;              // 2 x 2 shuffle tail (row kernel): requantise in the epilogue instead
     int ps;                  // 0: blocked store; r: pixel shuffle by r
     float *ps_out;           // planar float32 [cout/(r*r)][rH][rW] (final) or null
     int64_t ps_pitch;

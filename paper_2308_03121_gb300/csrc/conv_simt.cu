@@ -270,6 +270,7 @@ void prepare_weights_simt(const float *w, int cout, int cin, int k, int cin_pad,
 }
 
 cudaError_t launch_conv_simt(const ConvArgs &a, cudaStream_t st) {
+    if (a.rq.on) return cudaErrorNotSupported;  // requantise is fused into tensor-core tails only
     DcnArgs d{};
     if (a.cin_pad % 8 || a.cout_pad % 16) return cudaErrorInvalidValue;
     const int nb = a.cout_pad % 64 == 0 ? 64 : (a.cout_pad % 32 == 0 ? 32 : 16);

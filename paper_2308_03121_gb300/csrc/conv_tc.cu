@@ -36,6 +36,7 @@
 
 #include "common.cuh"
 #include "epilogue.cuh"
+#include "rq_math.cuh"
 #include "sm100_ptx.cuh"
 
 namespace nvisr {
@@ -80,6 +81,7 @@ struct TcParams {
     int tslot[8];                     //   frames from the ring (slots tslot[]) instead of a packed tensor
     int *err;
     int starve;                       // test drill: the producer loads no input, the pipeline waits run out
+    FusedRq rq;                       // 2 x 2 shuffle tail: requantise in the epilogue
 };
 
 template <int DT>
@@ -563,6 +565,89 @@ __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
 // epilogue, which frees its slot.  Per output row: 13 MMAs, one 130-pixel TMA
 // row load (plus 2 halo rows per strip) and a third of the operand traffic of
 // the per-tap form.
+// Fused requantisation (FusedRq) of one low-resolution pixel (o, x) of a 2 x 2 shuffle
+// tail: the same arithmetic, in the same order, as the separate requantise kernels
+// (requant420_kernel's 2x skip form for 4:2:0, the general skip for 4:4:4), so the codes
+// are those of the unfused path.
+// Bilinear x2 skip (align_corners = False, edge clamp) at output (2o + dy, 2x + dx), the
+// general form: source position max((Y + 1/2) / 2 - 1/2, 0) per axis.
+__device__ __forceinline__ float rq_skip_general(const FusedRq &rq, int c, int Y, int X, int H, int W) {
+    const float *pl = rq.skip + (int64_t)c * rq.skip_plane;
+    const float sy = fmaxf(((float)Y + 0.5f) * 0.5f - 0.5f, 0.f);
+    const float sx = fmaxf(((float)X + 0.5f) * 0.5f - 0.5f, 0.f);
+    const int y0 = min((int)sy, H - 1), x0 = min((int)sx, W - 1);
+    const int y1 = min(y0 + 1, H - 1), x1 = min(x0 + 1, W - 1);
+    const float ly = sy - (float)y0, lx = sx - (float)x0;
+    const float *r0 = pl + (int64_t)y0 * rq.skip_pitch;
+    const float *r1 = pl + (int64_t)y1 * rq.skip_pitch;
+    return rq_bilerp(__ldg(r0 + x0), __ldg(r0 + x1), __ldg(r1 + x0), __ldg(r1 + x1), lx, ly);
+}
+
+// Output samples (residual v[4c + 2dy + dx] + skip) -> luma codes yq[dy][dx], full-resolution
+// chroma cb[dy][dx], cr[dy][dx] (before downsampling and rounding).
+__device__ __forceinline__ void rq_pixel(const FusedRq &rq, const float *v, int o, int x, int H, int W,
+                                         float (&yq)[2][2], float (&cb)[2][2], float (&cr)[2][2]) {
+    float smp[3][2][2];
+    if (rq.skip && rq.sub420) {
+        // requant420's 2x form: rows (o-1, o) with (1/4, 3/4) for dy = 0 and (o, o+1) with
+        // (3/4, 1/4) for dy = 1; columns likewise, all clamped to the frame
+        const int rows[3] = {max(o - 1, 0), o, min(o + 1, H - 1)};
+        const int cols[3] = {max(x - 1, 0), x, min(x + 1, W - 1)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float lr[3][3];
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr) {
+                const float *row = rq.skip + (int64_t)c * rq.skip_plane + (int64_t)rows[rr] * rq.skip_pitch;
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) lr[rr][cc] = __ldg(row + cols[cc]);
+            }
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int c0 = dx;
+                    const float wl = dx ? 0.75f : 0.25f, wr = dx ? 0.25f : 0.75f;
+                    const float wt = dy ? 0.75f : 0.25f, wb = dy ? 0.25f : 0.75f;
+                    const float top = rq_blend(lr[dy][c0], wl, lr[dy][c0 + 1], wr);
+                    const float bot = rq_blend(lr[dy + 1][c0], wl, lr[dy + 1][c0 + 1], wr);
+                    smp[c][dy][dx] = __fadd_rn(v[4 * c + 2 * dy + dx], rq_blend(top, wt, bot, wb));
+                }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const float r = v[4 * c + 2 * dy + dx];
+                    smp[c][dy][dx] = rq.skip ? __fadd_rn(r, rq_skip_general(rq, c, 2 * o + dy, 2 * x + dx, H, W)) : r;
+                }
+    }
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            float y;
+            rq_ycc(smp[0][dy][dx], smp[1][dy][dx], smp[2][dy][dx], rq.kr, rq.kg, rq.kb, rq.cb_s, rq.cr_s, y,
+                   cb[dy][dx], cr[dy][dx]);
+            yq[dy][dx] = rq_code(y, rq.y_mul, rq.y_add, rq.vmax);
+        }
+}
+
+// Stores two adjacent codes of row `row` at columns 2x, 2x + 1.
+__device__ __forceinline__ void rq_store2(uint8_t *plane, int64_t pitch, int row, int x, bool wide, float a, float b) {
+    uint8_t *p = plane + (int64_t)row * pitch;
+    if (wide) *reinterpret_cast<uint32_t *>(p + 4 * (int64_t)x) = (uint32_t)(int)a | ((uint32_t)(int)b << 16);
+    else *reinterpret_cast<uint16_t *>(p + 2 * (int64_t)x) = (uint16_t)((uint32_t)(int)a | ((uint32_t)(int)b << 8));
+}
+__device__ __forceinline__ void rq_store1(uint8_t *plane, int64_t pitch, int row, int x, bool wide, float a) {
+    uint8_t *p = plane + (int64_t)row * pitch;
+    if (wide) reinterpret_cast<uint16_t *>(p)[x] = (uint16_t)(int)a;
+    else p[x] = (uint8_t)(int)a;
+}
+
 struct RowPlan {
     int xtiles;   // 128-pixel columns per row
     int bands;    // row bands per column (strips = xtiles * bands * nimg)
@@ -1159,7 +1244,79 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                         if (p.ps_act == 1) ov = lrelu(ov);
                         v[e] = ov;
                     }
-                    if (valid && w) {
+                    if (p.rq.on) {
+                        // requantised here: residual + skip -> integer planes (see rq_pixel)
+                        const FusedRq &rq = p.rq;
+                        const int Wl = width_of(pi), xc = min(x, Wl - 1);
+                        float yq[2][2], cb[2][2], cr[2][2];
+                        rq_pixel(rq, v, o, xc, p.H, Wl, yq, cb, cr);
+                        const bool st = valid && w;
+                        if (st)
+#pragma unroll
+                            for (int dy = 0; dy < 2; ++dy)
+                                rq_store2(rq.yp, rq.py, 2 * o + dy, x, rq.wide, yq[dy][0], yq[dy][1]);
+                        if (!rq.sub420) {
+                            if (st)
+#pragma unroll
+                                for (int dy = 0; dy < 2; ++dy) {
+                                    const float a0 = rq_code(cb[dy][0], rq.c_mul, rq.c_add, rq.vmax);
+                                    const float a1 = rq_code(cb[dy][1], rq.c_mul, rq.c_add, rq.vmax);
+                                    const float b0 = rq_code(cr[dy][0], rq.c_mul, rq.c_add, rq.vmax);
+                                    const float b1 = rq_code(cr[dy][1], rq.c_mul, rq.c_add, rq.vmax);
+                                    rq_store2(rq.up, rq.pu, 2 * o + dy, x, rq.wide, a0, a1);
+                                    rq_store2(rq.vp, rq.pv, 2 * o + dy, x, rq.wide, b0, b1);
+                                }
+                        } else {
+                            // row-pair means of the two full-resolution columns 2x, 2x + 1
+                            const float cbv0 = rq_mean2(cb[0][0], cb[1][0]), cbv1 = rq_mean2(cb[0][1], cb[1][1]);
+                            const float crv0 = rq_mean2(cr[0][0], cr[1][0]), crv1 = rq_mean2(cr[0][1], cr[1][1]);
+                            if (rq.loc != NVISR_CHROMA_LEFT) {
+                                if (st) {
+                                    rq_store1(rq.up, rq.pu, o, x, rq.wide,
+                                              rq_code(rq_mean2(cbv0, cbv1), rq.c_mul, rq.c_add, rq.vmax));
+                                    rq_store1(rq.vp, rq.pv, o, x, rq.wide,
+                                              rq_code(rq_mean2(crv0, crv1), rq.c_mul, rq.c_add, rq.vmax));
+                                }
+                            } else {
+                                // [1 2 1] / 4 over columns 2x - 1, 2x, 2x + 1: column 2x - 1 is the left
+                                // neighbour's odd column (lane - 1; the previous warp's lane 31 through
+                                // shared memory; the previous tile's through rq.edge and the fix-up)
+                                float cbl = __shfl_up_sync(0xffffffffu, cbv1, 1);
+                                float crl = __shfl_up_sync(0xffffffffu, crv1, 1);
+                                float *esm = reinterpret_cast<float *>(smem + 640) + (g * 4 + q) * 2;
+                                if (lane == 31) {
+                                    esm[0] = cbv1;
+                                    esm[1] = crv1;
+                                }
+                                const int tiles = rp.xtiles;
+                                const int tile = x0 / TM;
+                                if (st && m == 0 && x0 > 0) {  // this tile's first column: finished by the fix-up
+                                    float *e = rq.edge + ((int64_t)o * tiles + tile) * 6;
+                                    e[0] = cbv0;
+                                    e[1] = cbv1;
+                                    e[2] = crv0;
+                                    e[3] = crv1;
+                                }
+                                if (st && m == TM - 1 && x0 + TM < Wl) {  // the next tile's left neighbour
+                                    float *e = rq.edge + ((int64_t)o * tiles + tile + 1) * 6;
+                                    e[4] = cbv1;
+                                    e[5] = crv1;
+                                }
+                                named_barrier(bar_id, NGRP);  // the group's lane-31 columns are in shared memory
+                                if (lane == 0) {
+                                    const float *pe = reinterpret_cast<const float *>(smem + 640) + (g * 4 + q - 1) * 2;
+                                    cbl = q > 0 ? pe[0] : cbv0;  // x = 0: the clamped column is 2x itself
+                                    crl = q > 0 ? pe[1] : crv0;
+                                }
+                                if (st && !(m == 0 && x0 > 0)) {
+                                    rq_store1(rq.up, rq.pu, o, x, rq.wide,
+                                              rq_code(rq_121(cbl, cbv0, cbv1), rq.c_mul, rq.c_add, rq.vmax));
+                                    rq_store1(rq.vp, rq.pv, o, x, rq.wide,
+                                              rq_code(rq_121(crl, crv0, crv1), rq.c_mul, rq.c_add, rq.vmax));
+                                }
+                            }
+                        }
+                    } else if (valid && w) {
                         const int64_t plane = p.ps_pitch * 2 * p.H;
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
@@ -2093,10 +2250,15 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
         p.ps_out = a.ps_out;
         p.ps_pitch = a.ps_pitch;
         p.ps_act = a.ps_act;
-        return dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128, 16, true>(map, ymap, rmap, p, st)
-                             : run_rows<DT_F16, DT_F16, 128, 16, true>(map, ymap, rmap, p, st);
+        p.rq = a.rq;
+        if (p.rq.on && a.cout != 12) return cudaErrorInvalidValue;  // requantise needs the 3 shuffled channels
+        e = dt == DT_BF16 ? run_rows<DT_BF16, DT_BF16, 128, 16, true>(map, ymap, rmap, p, st)
+                          : run_rows<DT_F16, DT_F16, 128, 16, true>(map, ymap, rmap, p, st);
+        if (e != cudaSuccess || !p.rq.on) return e;
+        return launch_rq_edge_fixup(p.rq, a.H, a.W, st);
     }
     if (dt == DT_F32) return cudaErrorInvalidValue;
+    if (a.rq.on) return cudaErrorNotSupported;  // only the row kernel's shuffle tail requantises
     const int esz = dtype_size(dt);
     const int in_cpc = a.in_cpc ? a.in_cpc : 16 / esz;
     const int cbi = in_cpc * esz == 128 ? 128 : 16;

@@ -253,7 +253,14 @@ struct nvisr_filter {
     int64_t opitch = 0;
     void *ostage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // alternate per pull
     int64_t ostage_pitch[3] = {0, 0, 0};
-    int obuf = 0;
+    // output o is written into staging buffer o & 1 (requantised by the output layer itself
+    // when fused_rq is set: rq_done[b] is then the output staging buffer b holds, else -1)
+    bool fused_rq = false;
+    FusedRq rq_base{};
+    float *rq_edge = nullptr;
+    int64_t rq_o = -1;             // the output the next forward computes (tuple family)
+    int64_t rq_done[2] = {-1, -1};
+    uint32_t options = 0;
 
     // host-plane copies on the engine's copy stream: the H2D of a push and the
     // D2H of a pull overlap the compute stream's work; a pull of host planes
@@ -1383,6 +1390,23 @@ ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, b
         a.skip_mode = 0;
         a.nskip = 0;
         set_final_skip(f, s, frames);
+        if (f->fused_rq && !calib && !f->batched && f->rq_o >= 0) {
+            // or requantised in the layer's epilogue, into the output's staging buffer
+            const int b = (int)(f->rq_o & 1);
+            a.rq = f->rq_base;
+            a.rq.yp = (uint8_t *)f->ostage[b][0];
+            a.rq.up = (uint8_t *)f->ostage[b][1];
+            a.rq.vp = (uint8_t *)f->ostage[b][2];
+            a.rq.py = f->ostage_pitch[0];
+            a.rq.pu = f->ostage_pitch[1];
+            a.rq.pv = f->ostage_pitch[2];
+            const SkipArgs &k = f->skip[s.out_index];
+            a.rq.skip = k.n ? k.src[0] : nullptr;
+            a.rq.skip_pitch = f->rpitch;
+            a.rq.skip_plane = f->rpitch * f->in_fmt.height;
+            a.rq.edge = f->rq_edge;
+            f->rq_done[b] = f->rq_o;
+        }
     }
     *kind = step_kind(f, s);
     return a;
@@ -1618,7 +1642,11 @@ nvisr_status compute_output(nvisr_filter *f, int64_t o) {
         nvisr_status s = calibrate(f);
         if (s != NVISR_OK) return s;
     }
-    return forward_tuple(f, idx, false);
+    f->rq_o = o;
+    f->rq_done[o & 1] = -1;
+    const nvisr_status s = forward_tuple(f, idx, false);
+    f->rq_o = -1;
+    return s;
 }
 
 // Where output o's planes come from: network output slot `slot`, or input frame
@@ -1647,16 +1675,26 @@ const void *raw_plane(const nvisr_filter *f, int64_t frame, int p) {
 // stream; write_output_end waits for those copies.  A network output is
 // requantised (with its skip); a passed-through input frame is copied from its
 // raw planes, or requantised from its ring slot into the output format.
-nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, OutSrc src) {
+nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, OutSrc src, int64_t o) {
     cudaStream_t st = f->eng->stream;
     const nvisr_format &of = f->out_fmt;
+    const int b = (int)(o & 1);
     void *dst[3];
     int64_t pitch[3];
     for (int p = 0; p < 3; ++p) {
-        dst[p] = out->on_device ? out->data[p] : f->ostage[f->obuf][p];
+        dst[p] = out->on_device ? out->data[p] : f->ostage[b][p];
         pitch[p] = out->on_device ? out->pitch[p] : f->ostage_pitch[p];
     }
-    if (src.frame >= 0 && f->pass_copy) {
+    if (f->rq_done[b] == o) {
+        // the output layer requantised output o into staging buffer b already
+        if (out->on_device) {
+            prof_gap(f);
+            for (int p = 0; p < 3; ++p)
+                NVISR_TRY_CUDA(cudaMemcpy2DAsync(dst[p], pitch[p], f->ostage[b][p], f->ostage_pitch[p],
+                                                 plane_row_bytes(of, p), plane_rows(of, p), cudaMemcpyDeviceToDevice,
+                                                 st));
+        }
+    } else if (src.frame >= 0 && f->pass_copy) {
         prof_gap(f);
         for (int p = 0; p < 3; ++p)
             NVISR_TRY_CUDA(cudaMemcpy2DAsync(dst[p], pitch[p], raw_plane(f, src.frame, p), f->stage_pitch[p],
@@ -1678,7 +1716,7 @@ nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, OutSrc src) 
     NVISR_TRY_CUDA(cudaEventRecord(f->ev_req, st));
     NVISR_TRY_CUDA(cudaStreamWaitEvent(cs, f->ev_req, 0));
     for (int p = 0; p < 3; ++p)
-        NVISR_TRY_CUDA(cudaMemcpy2DAsync(out->data[p], out->pitch[p], f->ostage[f->obuf][p], f->ostage_pitch[p],
+        NVISR_TRY_CUDA(cudaMemcpy2DAsync(out->data[p], out->pitch[p], f->ostage[b][p], f->ostage_pitch[p],
                                          plane_row_bytes(of, p), plane_rows(of, p), cudaMemcpyDeviceToHost, cs));
     NVISR_TRY_CUDA(cudaMemcpyAsync(f->eng->err_host, f->eng->err_word, sizeof(int), cudaMemcpyDeviceToHost, cs));
     NVISR_TRY_CUDA(cudaEventRecord(f->ev_d2h, cs));
@@ -1687,7 +1725,6 @@ nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, OutSrc src) 
 
 nvisr_status write_output_end(nvisr_filter *f) {
     NVISR_TRY_CUDA(cudaEventSynchronize(f->ev_d2h));
-    f->obuf ^= 1;  // the next requantise writes the other staging buffer
     const int h = *f->eng->err_host;
     if (h != 0) {
         // the error word is the engine's: outputs computed ahead (read-ahead, engine or batch
@@ -2068,6 +2105,27 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
         if ((s = dalloc(e, sizeof(float) * 16 * (size_t)H * W, f->owned, &p)) != NVISR_OK) return cleanup(s);
         f->final_f32 = (float *)p;
     }
+    // requantise fused into a 2 x 2 shuffle output layer of 64 input channels (the row
+    // kernel's shuffle tail): tensor-core tuple networks with an RGB domain, no transfer,
+    // a bilinear skip of the centre frame or none
+    f->options = d->options;
+    if (net.family == "tuple" && f->tc && !(d->options & NVISR_OPT_UNFUSED_OUTPUT) &&
+        (net.skip == 0 || net.skip == 2) && !f->steps.empty()) {
+        const Step &last = f->steps.back();
+        const NetLayer &L = net.layers[last.layer];
+        FusedRq rq{};
+        if (last.op == OP_CONV && last.out_t < 0 && !last.plain && L.cin == 64 && L.cout == 12 && L.ps == 2 &&
+            L.k == 3 && last.skip_frames.size() == 1 && fused_rq_format(d->out_fmt, net.yuv, &rq)) {
+            f->fused_rq = true;
+            f->rq_base = rq;
+            const int tiles = (W + 127) / 128;
+            if (rq.sub420 && rq.loc == NVISR_CHROMA_LEFT && tiles > 1) {
+                if ((s = dalloc(e, sizeof(float) * 6 * (size_t)H * tiles, f->owned, &p)) != NVISR_OK)
+                    return cleanup(s);
+                f->rq_edge = (float *)p;
+            }
+        }
+    }
     e->filters.push_back(f.get());
     *out = f.release();
     return NVISR_OK;
@@ -2171,7 +2229,7 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
     } else {
         f->produced.pop_front();
     }
-    if ((s = write_output_begin(f, out, output_source(f, o))) != NVISR_OK) return s;
+    if ((s = write_output_begin(f, out, output_source(f, o), o)) != NVISR_OK) return s;
     if (!out->on_device) {
         // read-ahead: the next output's network runs on the compute stream while this
         // output's planes are copied out

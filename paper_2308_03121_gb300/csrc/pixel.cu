@@ -18,6 +18,7 @@
 // consecutive pixels (ingest) or a 2x8 luma block (requantise 4:2:0) with
 // vector loads/stores along rows.
 #include "common.cuh"
+#include "rq_math.cuh"
 #include "sm100_ptx.cuh"
 
 namespace nvisr {
@@ -360,9 +361,7 @@ __device__ __forceinline__ void st_sample(uint8_t *base, int64_t pitch, int y, i
 
 // Bilinear blend of the corners (row 0: a00, a01; row 1: a10, a11) at fractions (lx, ly).
 __device__ __forceinline__ float bilerp(float a00, float a01, float a10, float a11, float lx, float ly) {
-    const float top = a00 * (1.f - lx) + a01 * lx;
-    const float bot = a10 * (1.f - lx) + a11 * lx;
-    return top * (1.f - ly) + bot * ly;
+    return rq_bilerp(a00, a01, a10, a11, lx, ly);
 }
 
 // Skip value (mean of the skip frames, upsampled) at output (c, Y, X).
@@ -385,7 +384,7 @@ __device__ __forceinline__ float skip_at(const SkipArgs &k, int c, int Y, int X)
             const float *r1 = p + (int64_t)y1 * k.pitch;
             v = bilerp(r0[x0], r0[x1], r1[x0], r1[x1], lx, ly);
         }
-        acc += v;
+        acc = __fadd_rn(acc, v);
     }
     return k.n == 2 ? acc * 0.5f : acc;
 }
@@ -394,7 +393,7 @@ __device__ __forceinline__ float skip_at(const SkipArgs &k, int c, int Y, int X)
 __device__ __forceinline__ float out_at(const float *in, int64_t pitch, int64_t plane, const SkipArgs &k, int c,
                                         int Y, int X) {
     const float v = in[(int64_t)c * plane + (int64_t)Y * pitch + X];
-    return k.n ? v + skip_at(k, c, Y, X) : v;
+    return k.n ? __fadd_rn(v, skip_at(k, c, Y, X)) : v;
 }
 
 __device__ __forceinline__ void rgb2ycc(const RangeConst &rc, float r, float g, float b, float &y, float &cb,
@@ -410,9 +409,7 @@ __device__ __forceinline__ void rgb2ycc(const RangeConst &rc, float r, float g, 
         cr = b;
         return;
     }
-    y = rc.kr * r + rc.kg * g + rc.kb * b;
-    cb = (b - y) * rc.cb_s;
-    cr = (r - y) * rc.cr_s;
+    rq_ycc(r, g, b, rc.kr, rc.kg, rc.kb, rc.cb_s, rc.cr_s, y, cb, cr);
 }
 
 // 4:4:4: one thread per 4 pixels of a row.
@@ -429,9 +426,9 @@ __global__ void __launch_bounds__(256) requant444_kernel(const float *__restrict
         float Y, cb, cr;
         rgb2ycc(rc, out_at(in, pitch, plane, sk, 0, y, x0 + e), out_at(in, pitch, plane, sk, 1, y, x0 + e),
                 out_at(in, pitch, plane, sk, 2, y, x0 + e), Y, cb, cr);
-        st_sample<S>(yp, py, y, x0 + e, quant(Y * rc.y_mul + rc.y_add, rc.vmax));
-        st_sample<S>(up, pu, y, x0 + e, quant(cb * rc.c_mul + rc.c_add, rc.vmax));
-        st_sample<S>(vp, pv, y, x0 + e, quant(cr * rc.c_mul + rc.c_add, rc.vmax));
+        st_sample<S>(yp, py, y, x0 + e, rq_code(Y, rc.y_mul, rc.y_add, rc.vmax));
+        st_sample<S>(up, pu, y, x0 + e, rq_code(cb, rc.c_mul, rc.c_add, rc.vmax));
+        st_sample<S>(vp, pv, y, x0 + e, rq_code(cr, rc.c_mul, rc.c_add, rc.vmax));
     }
 }
 
@@ -545,18 +542,19 @@ __global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict
             float acc = 0.f;
 #pragma unroll
             for (int f = 0; f < NF; ++f)
-                acc += bilerp(l4[f][ch][0][i0], l4[f][ch][0][i0 + 1], l4[f][ch][1][i0], l4[f][ch][1][i0 + 1], lx, ly4[a]);
-            return v + (NF == 2 ? acc * 0.5f : acc);
+                acc = __fadd_rn(acc, bilerp(l4[f][ch][0][i0], l4[f][ch][0][i0 + 1], l4[f][ch][1][i0],
+                                            l4[f][ch][1][i0 + 1], lx, ly4[a]));
+            return __fadd_rn(v, NF == 2 ? acc * 0.5f : acc);
         }
-        if (!SKIP2) return sk.n ? v + skip_at(sk, ch, 2 * j + a, x) : v;
+        if (!SKIP2) return sk.n ? __fadd_rn(v, skip_at(sk, ch, 2 * j + a, x)) : v;
         // horizontal: even c9 -> odd column 2i+1 (3/4 col i, 1/4 col i+1), odd c9 -> even 2i (1/4 col i-1, 3/4 col i)
         const int c0 = (c9 & 1) ? (c9 - 1) / 2 : c9 / 2;
         const float wl = (c9 & 1) ? 0.25f : 0.75f, wr = (c9 & 1) ? 0.75f : 0.25f;
         const int r0 = a;  // a = 0: rows (j-1, j) with (1/4, 3/4); a = 1: rows (j, j+1) with (3/4, 1/4)
         const float wt = a ? 0.75f : 0.25f, wb = a ? 0.25f : 0.75f;
-        const float top = lr[ch][r0][c0] * wl + lr[ch][r0][c0 + 1] * wr;
-        const float bot = lr[ch][r0 + 1][c0] * wl + lr[ch][r0 + 1][c0 + 1] * wr;
-        return v + (top * wt + bot * wb);
+        const float top = rq_blend(lr[ch][r0][c0], wl, lr[ch][r0][c0 + 1], wr);
+        const float bot = rq_blend(lr[ch][r0 + 1][c0], wl, lr[ch][r0 + 1][c0 + 1], wr);
+        return __fadd_rn(v, rq_blend(top, wt, bot, wb));
     };
     // columns xb-1 .. xb+7 (9 columns), clamped; two rows.
     float cbv[9], crv[9];  // row-pair mean of full-resolution chroma
@@ -571,10 +569,10 @@ __global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict
             rgb2ycc(rc, sample(0, rr, c, x), sample(1, rr, c, x), sample(2, rr, c, x), Y, cb, cr);
             cb2[rr] = cb;
             cr2[rr] = cr;
-            if (c >= 1) yq[rr][c - 1] = quant(Y * rc.y_mul + rc.y_add, rc.vmax);
+            if (c >= 1) yq[rr][c - 1] = rq_code(Y, rc.y_mul, rc.y_add, rc.vmax);
         }
-        cbv[c] = 0.5f * (cb2[0] + cb2[1]);
-        crv[c] = 0.5f * (cr2[0] + cr2[1]);
+        cbv[c] = rq_mean2(cb2[0], cb2[1]);
+        crv[c] = rq_mean2(cr2[0], cr2[1]);
     }
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
@@ -604,14 +602,14 @@ __global__ void __launch_bounds__(128) requant420_kernel(const float *__restrict
         const int c = 1 + 2 * e;  // index of column 2i
         float cb, cr;
         if (loc == NVISR_CHROMA_LEFT) {
-            cb = 0.25f * (cbv[c - 1] + 2.0f * cbv[c] + cbv[c + 1]);
-            cr = 0.25f * (crv[c - 1] + 2.0f * crv[c] + crv[c + 1]);
+            cb = rq_121(cbv[c - 1], cbv[c], cbv[c + 1]);
+            cr = rq_121(crv[c - 1], crv[c], crv[c + 1]);
         } else {
-            cb = 0.5f * (cbv[c] + cbv[c + 1]);
-            cr = 0.5f * (crv[c] + crv[c + 1]);
+            cb = rq_mean2(cbv[c], cbv[c + 1]);
+            cr = rq_mean2(crv[c], crv[c + 1]);
         }
-        cq[0][e] = quant(cb * rc.c_mul + rc.c_add, rc.vmax);
-        cq[1][e] = quant(cr * rc.c_mul + rc.c_add, rc.vmax);
+        cq[0][e] = rq_code(cb, rc.c_mul, rc.c_add, rc.vmax);
+        cq[1][e] = rq_code(cr, rc.c_mul, rc.c_add, rc.vmax);
     }
     const int i0 = q * 4;
 #pragma unroll
@@ -983,6 +981,62 @@ cudaError_t launch_unpack(const void *src, int dt, int cpad, int cpc, int C, int
         default: unpack_kernel<__nv_fp8_e4m3><<<grid, block, 0, st>>>(s, cpad, cpc, C, H, W, scale, dst, dst_pitch); break;
     }
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fused requantise helpers
+
+bool fused_rq_format(const nvisr_format &f, int yuv, FusedRq *rq) {
+    if (yuv || f.transfer != NVISR_TRANSFER_NONE || f.matrix == NVISR_MATRIX_RGB) return false;
+    const RangeConst rc = range_const(f.bit_depth, f.range, f.matrix, yuv, f.transfer);
+    rq->on = 1;
+    rq->wide = f.bit_depth > 8;
+    rq->sub420 = f.subsampling == NVISR_SUB_420;
+    rq->loc = f.chroma_loc;
+    rq->y_mul = rc.y_mul;
+    rq->y_add = rc.y_add;
+    rq->c_mul = rc.c_mul;
+    rq->c_add = rc.c_add;
+    rq->vmax = rc.vmax;
+    rq->kr = rc.kr;
+    rq->kg = rc.kg;
+    rq->kb = rc.kb;
+    rq->cb_s = rc.cb_s;
+    rq->cr_s = rc.cr_s;
+    return true;
+}
+
+namespace {
+
+// One thread per (low-resolution row, 128-pixel tile after the first): the LEFT-sited
+// chroma sample at the tile's first column, from the columns the two tiles' CTAs left
+// in rq.edge: [k * 6 + 0..3] = this tile's first pixel (Cb' even, Cb' odd, Cr' even,
+// Cr' odd column, each the mean of its two rows), [k * 6 + 4..5] = the previous tile's
+// last pixel's odd column (Cb', Cr').  The arithmetic is requant420_kernel's.
+template <typename S>
+__global__ void rq_edge_fixup_kernel(FusedRq rq, int H, int W, int tiles) {
+    griddep_wait();  // launched as a dependent of the output layer
+    griddep_launch_dependents();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = H * (tiles - 1);
+    if (i >= n) return;
+    const int o = i / (tiles - 1), t = 1 + i % (tiles - 1);
+    const float *e = rq.edge + ((int64_t)o * tiles + t) * 6;
+    const float cb = rq_121(e[4], e[0], e[1]);
+    const float cr = rq_121(e[5], e[2], e[3]);
+    const int x = t * 128;
+    reinterpret_cast<S *>(rq.up + (int64_t)o * rq.pu)[x] = (S)(int)rq_code(cb, rq.c_mul, rq.c_add, rq.vmax);
+    reinterpret_cast<S *>(rq.vp + (int64_t)o * rq.pv)[x] = (S)(int)rq_code(cr, rq.c_mul, rq.c_add, rq.vmax);
+}
+
+}  // namespace
+
+cudaError_t launch_rq_edge_fixup(const FusedRq &rq, int H, int W, cudaStream_t st) {
+    const int tiles = (W + 127) / 128;
+    if (!rq.on || !rq.sub420 || rq.loc != NVISR_CHROMA_LEFT || tiles < 2) return cudaSuccess;
+    const int n = H * (tiles - 1);
+    const dim3 grid((n + 127) / 128), block(128);
+    return rq.wide ? launch_dependent(rq_edge_fixup_kernel<uint16_t>, grid, block, 0, st, rq, H, W, tiles)
+                   : launch_dependent(rq_edge_fixup_kernel<uint8_t>, grid, block, 0, st, rq, H, W, tiles);
 }
 
 }  // namespace nvisr

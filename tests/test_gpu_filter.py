@@ -19,10 +19,10 @@ def _lib():
     nv.load()
 
 
-def run_gpu(text, blob, frames, flags, fin, fout, prec, scale=2, device_io=False, limit=None):
+def run_gpu(text, blob, frames, flags, fin, fout, prec, scale=2, device_io=False, limit=None, options=0):
     """Push every frame (pulling whenever the ring is full) and pull all outputs."""
     eng = nv.Engine()
-    flt = eng.filter(text, blob, fin, fout, prec, scale)
+    flt = eng.filter(text, blob, fin, fout, prec, scale, options=options)
     outs, infos = [], []
 
     def pull_one():
@@ -175,6 +175,37 @@ def test_config2_full_size_sampled_windows(prec):
 
 STVSR_WINDOWS = [(0, 16, 0, 16), (0, 16, 944, 960), (524, 540, 944, 960), (270, 286, 480, 496),
                  (100, 116, 120, 136)]
+
+
+@pytest.mark.parametrize("bits,sub,loc,prec,device_io", [
+    (10, "420", "left", "bf16", False), (10, "420", "left", "fp16", True), (8, "420", "center", "bf16", False),
+    (8, "420", "point", "bf16", True), (8, "444", "left", "bf16", False), (10, "444", "center", "fp16", False)])
+def test_fused_requantise_equals_separate_kernel(bits, sub, loc, prec, device_io):
+    """Requantise fused into the 2x2 shuffle tail's epilogue (the default for tensor-core tuple
+    networks) gives the same codes as the separate requantise kernel (NVISR_OPT_UNFUSED_OUTPUT),
+    sample for sample: 300 px wide (three 128-pixel tiles, so LEFT-sited 4:2:0 chroma at two tile
+    edges goes through the fix-up), a cut before frame 3; and the oracle within 1 LSB."""
+    W, H, N = 300, 38, 5
+    frames = synth.frames_textured(synth.BASE_SEED + 83, N, W, H, bits, sub, "limited")
+    flags = np.zeros(N, bool)
+    flags[3] = True
+    text, blob = synth.net_tuple(synth.BASE_SEED + 84, frames=5, channels=64, nres=2, scale=2)
+    fi = nv.fmt(W, H, bits, sub, "limited", loc)
+    fo = nv.fmt(2 * W, 2 * H, bits, sub, "limited", loc)
+    fused, _ = run_gpu(text, blob, frames, flags, fi, fo, prec, device_io=device_io)
+    plain, _ = run_gpu(text, blob, frames, flags, fi, fo, prec, device_io=device_io,
+                       options=nv.OPT_UNFUSED_OUTPUT)
+    assert len(fused) == len(plain) == N
+    for a, b in zip(fused, plain):
+        for k in "YUV":
+            assert np.array_equal(a[k], b[k]), (k, np.argwhere(a[k] != b[k])[:5])
+    fdo = fmt_dict(2 * W, 2 * H, bits, sub, "limited", loc)
+    ref = oracle.run_filter(frames, flags, text, blob, fmt_dict(W, H, bits, sub, "limited", loc), fdo,
+                            keep_float=True)
+    for got, r in zip(fused, ref):
+        pq = prequant(r, fdo)
+        mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], bits) for k in "YUV"})
+        assert mx <= 1, mx
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
