@@ -51,8 +51,10 @@ NFRAMES = 12                                   # distinct resident input frames,
 # DRAM bytes (read + written) per conv_body launch, the mean of a launch with and
 # one without residual, from one ncu capture of the body kernel at 1080p; None
 # until the kernel as it stands has been captured
-CONV_BODY_TRAFFIC = None
-CONV_BODY_TRAFFIC_SOURCE = None
+CONV_BODY_TRAFFIC = 621.9e6
+CONV_BODY_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of two body launches (761.2 MB with "
+                            "residual, 482.6 MB without), the 9th and 10th conv_rows_kernel launches of this "
+                            "bench's bf16 run with --steps 3")
 WORKLOAD = ("1080p->4K 2x SR: sliding window T=5, conv 15->64, 10 residual blocks of 64 ch, conv 64->12, "
             "PixelShuffle(2), bilinear skip; 10-bit 4:2:0 limited BT.709 in and out")
 DATA = "synthetic: seeded textured 10-bit 4:2:0 frames with global 0-4 px translation; random-init He-normal weights"
