@@ -260,6 +260,8 @@ struct nvisr_filter {
     float *rq_edge = nullptr;
     int64_t rq_o = -1;             // the output the next forward computes (tuple family)
     int64_t rq_done[2] = {-1, -1};
+    const nvisr_planes *rq_direct = nullptr;  // the caller's device planes, when a pull computes its own output
+    int64_t rq_direct_done = -1;             // the output last requantised straight into them
     uint32_t options = 0;
 
     // host-plane copies on the engine's copy stream: the H2D of a push and the
@@ -1391,7 +1393,8 @@ ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, b
         a.nskip = 0;
         set_final_skip(f, s, frames);
         if (f->fused_rq && !calib && !f->batched && f->rq_o >= 0) {
-            // or requantised in the layer's epilogue, into the output's staging buffer
+            // or requantised in the layer's epilogue, into the output's staging buffer (or straight
+            // into the caller's device planes when the pull that wants them computes the output)
             const int b = (int)(f->rq_o & 1);
             a.rq = f->rq_base;
             a.rq.yp = (uint8_t *)f->ostage[b][0];
@@ -1400,12 +1403,21 @@ ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, b
             a.rq.py = f->ostage_pitch[0];
             a.rq.pu = f->ostage_pitch[1];
             a.rq.pv = f->ostage_pitch[2];
+            if (const nvisr_planes *d = f->rq_direct) {
+                a.rq.yp = (uint8_t *)d->data[0];
+                a.rq.up = (uint8_t *)d->data[1];
+                a.rq.vp = (uint8_t *)d->data[2];
+                a.rq.py = d->pitch[0];
+                a.rq.pu = d->pitch[1];
+                a.rq.pv = d->pitch[2];
+            }
             const SkipArgs &k = f->skip[s.out_index];
             a.rq.skip = k.n ? k.src[0] : nullptr;
             a.rq.skip_pitch = f->rpitch;
             a.rq.skip_plane = f->rpitch * f->in_fmt.height;
             a.rq.edge = f->rq_edge;
-            f->rq_done[b] = f->rq_o;
+            if (f->rq_direct) f->rq_direct_done = f->rq_o;
+            else f->rq_done[b] = f->rq_o;
         }
     }
     *kind = step_kind(f, s);
@@ -1684,6 +1696,11 @@ nvisr_status write_output_begin(nvisr_filter *f, nvisr_planes *out, OutSrc src, 
     for (int p = 0; p < 3; ++p) {
         dst[p] = out->on_device ? out->data[p] : f->ostage[b][p];
         pitch[p] = out->on_device ? out->pitch[p] : f->ostage_pitch[p];
+    }
+    if (out->on_device && f->rq_direct_done == o) {
+        // the output layer requantised output o into these planes already
+        f->rq_direct_done = -1;
+        return NVISR_OK;
     }
     if (f->rq_done[b] == o) {
         // the output layer requantised output o into staging buffer b already
@@ -2224,7 +2241,19 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
     nvisr_status s;
     bool have = !f->produced.empty() && f->produced.front() == o;
     if (!have) {
+        // computed here: a fused output layer may write the caller's device planes itself
+        // (the 16-bit luma stores take 4-byte aligned rows, the chroma ones 2-byte)
+        const bool wide = f->out_fmt.bit_depth > 8;
+        const int64_t ya = wide ? 4 : 2;
+        const int64_t ca = f->out_fmt.subsampling == NVISR_SUB_444 ? ya : (wide ? 2 : 1);  // 4:4:4 chroma: pairs
+        const bool direct = f->fused_rq && out->on_device && !f->batched &&
+                            (uintptr_t)out->data[0] % ya == 0 && out->pitch[0] % ya == 0 &&
+                            (uintptr_t)out->data[1] % ca == 0 && out->pitch[1] % ca == 0 &&
+                            (uintptr_t)out->data[2] % ca == 0 && out->pitch[2] % ca == 0;
+        f->rq_direct = direct ? out : nullptr;
+        f->rq_direct_done = -1;
         s = compute_output(f, o);
+        f->rq_direct = nullptr;
         if (s != NVISR_OK) return s;
     } else {
         f->produced.pop_front();
