@@ -129,8 +129,13 @@ typedef struct nvisr_filter_desc {
  * and no transfer function, requantises inside that layer's epilogue (skip,
  * colour matrix, chroma downsampling, rounding and packing) instead of writing
  * float32 R'G'B' for a separate requantise kernel; the codes are the same.
- * NVISR_OPT_UNFUSED_OUTPUT keeps the separate kernel. */
-enum { NVISR_OPT_UNFUSED_OUTPUT = 1 };
+ * NVISR_OPT_UNFUSED_OUTPUT keeps the separate kernel.
+ * Likewise each residual block of a BF16 / FP16 trunk on the tensor cores
+ * (conv 64 -> 64, LeakyReLU, conv 64 -> 64, + the block input, whose middle
+ * tensor no other layer reads) runs as one launch that keeps the middle
+ * tensor on chip (nvisr_resblock2d); the results are the same as two
+ * launches.  NVISR_OPT_UNFUSED_BLOCKS runs the two layers as two launches. */
+enum { NVISR_OPT_UNFUSED_OUTPUT = 1, NVISR_OPT_UNFUSED_BLOCKS = 2 };
 
 /* What an output frame is (nvisr_frame_info.kind). */
 enum {
@@ -426,6 +431,24 @@ nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_
 nvisr_status nvisr_conv2d_static(int32_t precision, const float *x, int32_t cin, int32_t h, int32_t w,
                                  const float *weight, const float *bias, int32_t cout, int32_t k,
                                  int32_t act, const float *res, float *y, void *stream);
+
+/* Residual block of a trunk (Section 3.1: the networks are stacks of 3x3
+ * convolutions with residual connections): y = x + conv2(LeakyReLU(conv1(x)
+ * + b1)) + b2, both convs 64 -> 64 channels, 3x3, stride 1, zero padding 1,
+ * LeakyReLU slope 0.1.  x, y: planar float32 [64][h][w]; w1, w2: [64][64][3][3]
+ * (out, in, ky, kx); b1, b2: [64] or NULL (zero).  All pointers are device
+ * pointers; y must not overlap x.  precision: BF16 or FP16 (activations and
+ * operands in that type, FP32 accumulation; others return
+ * NVISR_UNSUPPORTED_FORMAT).  fused != 0: one launch of 2-CTA clusters in
+ * which one SM computes conv1 and writes its rows into the other SM's shared
+ * memory, where conv2 reads them (the middle tensor never reaches device
+ * memory); fused == 0: two launches of the single-layer row kernel.  Both
+ * give the same values.  Scratch is allocated per call; returns after
+ * synchronising `stream` (it reads the error word back: NVISR_DEVICE_TIMEOUT
+ * if a device-side wait ran out). */
+nvisr_status nvisr_resblock2d(int32_t precision, const float *x, int32_t h, int32_t w, const float *w1,
+                              const float *b1, const float *w2, const float *b2, float *y, int32_t fused,
+                              void *stream);
 
 /* Modulated deformable convolution 3x3, DCN v2 as in torchvision's
  * deform_conv2d (Section 3.1): offsets [2*G*9][H][W] (dy, dx per group and

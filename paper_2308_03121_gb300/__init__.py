@@ -19,7 +19,7 @@ from . import build as _build
 
 __all__ = [
     "Batch", "Engine", "Filter", "NvisrError", "Server", "PREC", "Status", "fmt", "lib", "load",
-    "nvisr_conv2d", "nvisr_conv2d_static", "nvisr_dcn2d", "nvisr_fig1_layout", "nvisr_group_outputs",
+    "nvisr_conv2d", "nvisr_conv2d_static", "nvisr_dcn2d", "nvisr_resblock2d", "nvisr_fig1_layout", "nvisr_group_outputs",
     "nvisr_group_runs",
     "nvisr_ingest", "nvisr_network_check", "nvisr_requant", "nvisr_selftest",
     "nvisr_tuple_map",
@@ -76,6 +76,7 @@ class FilterDesc(ctypes.Structure):
 
 
 OPT_UNFUSED_OUTPUT = 1
+OPT_UNFUSED_BLOCKS = 2
 
 
 class FrameInfo(ctypes.Structure):
@@ -123,6 +124,7 @@ _SIGS = {
     "nvisr_fig1_layout": (_I32, [_I32, _I32, _I32P, _I32P, _I32P]),
     "nvisr_conv2d": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _I32, _I32, _VP, _VP, _VP]),
     "nvisr_conv2d_static": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _I32, _I32, _VP, _VP, _VP]),
+    "nvisr_resblock2d": (_I32, [_I32, _VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I32, _VP]),
     "nvisr_dcn2d": (_I32, [_I32, _VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP, _VP, _I32, _VP, _VP]),
     "nvisr_selftest": (_I32, [_I32P, _I32P]),
     "nvisr_test_starve": (_I32, [_I32]),
@@ -255,6 +257,20 @@ def nvisr_conv2d_static(precision, x, weight, bias, act=0, res=None, stream=None
                                     res.data_ptr() if res is not None else None, out.data_ptr(),
                                     _stream_ptr(stream)), "nvisr_conv2d_static")
     return out
+
+
+def nvisr_resblock2d(precision, x, w1, b1, w2, b2, fused=True, stream=None):
+    """x [64][H][W] float32 cuda -> x + conv2(LeakyReLU(conv1(x) + b1)) + b2; w1, w2 [64][64][3][3].
+    fused: one launch of 2-CTA clusters (else two single-layer launches)."""
+    import torch
+    load()
+    _, h, w = x.shape
+    y = torch.empty_like(x)
+    _check(_LIB.nvisr_resblock2d(PREC.get(precision, precision), x.data_ptr(), h, w, w1.data_ptr(),
+                                 b1.data_ptr() if b1 is not None else None, w2.data_ptr(),
+                                 b2.data_ptr() if b2 is not None else None, y.data_ptr(), 1 if fused else 0,
+                                 _stream_ptr(stream)), "nvisr_resblock2d")
+    return y
 
 
 def nvisr_dcn2d(precision, x, offsets, mask, weight, bias, groups, stream=None):

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -266,6 +267,16 @@ cudaError_t launch_dcn_tc(const DcnArgs &a, cudaStream_t st);
 cudaError_t launch_dcn_relayout8(const void *x, int cpad, int H, int W, int x_cpc, void *y, cudaStream_t st);
 
 int device_sm_count();
+// The driver's tensor-map encoder (cuTensorMapEncodeTiled), or null when it is missing.
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
+
+// Residual block of a trunk in one launch (csrc/block_tc.cu): c1 = the block's first
+// conv (64 -> 64 3x3, LeakyReLU, input x, output h), c2 = its second (64 -> 64 3x3, no
+// activation, input h, residual x, output y).  h never reaches device memory: c1.y is not
+// written.  fits: shapes, dtypes (BF16 / FP16, unit scales, one image set) and buffers
+// allow it (y must not overlap x); launch returns cudaErrorInvalidValue otherwise.
+bool res_block_fits(const ConvArgs &c1, const ConvArgs &c2);
+cudaError_t launch_res_block(const ConvArgs &c1, const ConvArgs &c2, cudaStream_t st);
 
 // Feature-pyramid resampling on blocked [C/cpc][H][W][cpc] tensors of dtype dt (x: H x W):
 // up = false: 2x2 mean into (H/2) x (W/2) (H, W even); up = true: bilinear x2

@@ -38,6 +38,7 @@
 #include "epilogue.cuh"
 #include "rq_math.cuh"
 #include "sm100_ptx.cuh"
+#include "tc_util.cuh"
 
 namespace nvisr {
 
@@ -83,17 +84,6 @@ struct TcParams {
     int starve;                       // test drill: the producer loads no input, the pipeline waits run out
     FusedRq rq;                       // 2 x 2 shuffle tail: requantise in the epilogue
 };
-
-template <int DT>
-struct Elem;
-template <>
-struct Elem<DT_BF16> { using T = __nv_bfloat16; };
-template <>
-struct Elem<DT_F16> { using T = __half; };
-template <>
-struct Elem<DT_E4M3> { using T = __nv_fp8_e4m3; };
-template <>
-struct Elem<DT_F32> { using T = float; };
 
 template <typename T>
 __device__ __forceinline__ T to_elem(float v);
@@ -499,56 +489,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) conv_tc_kernel(const __grid_const
         tc_fence_after();
         tmem_dealloc(tmem_base, NCOLS);
     }
-}
-
-// Packed two-lane FP32 arithmetic (IEEE round-to-nearest per lane, as the scalar ops).
-__device__ __forceinline__ void add_f32x2(float &a, float &b, float c, float d) {
-    uint64_t x, y;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a), "f"(b));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(c), "f"(d));
-    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(x) : "l"(y));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
-}
-__device__ __forceinline__ void fma_f32x2(float &a, float &b, float s0, float s1, float c0, float c1) {
-    uint64_t x, y, z;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a), "f"(b));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(s0), "f"(s1));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(z) : "f"(c0), "f"(c1));
-    asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x) : "l"(y), "l"(z));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
-}
-__device__ __forceinline__ void mul_f32x2(float &a, float &b, float c, float d) {
-    uint64_t x, y;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a), "f"(b));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(c), "f"(d));
-    asm("mul.rn.f32x2 %0, %0, %1;" : "+l"(x) : "l"(y));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
-}
-// Two 16-bit elements of one 32-bit word (element 0 in the low half) <-> two floats.
-template <typename T>
-__device__ __forceinline__ void unpack2(uint32_t w, float &lo, float &hi);
-template <>
-__device__ __forceinline__ void unpack2<__nv_bfloat16>(uint32_t w, float &lo, float &hi) {
-    lo = __uint_as_float(w << 16);
-    hi = __uint_as_float(w & 0xffff0000u);
-}
-template <>
-__device__ __forceinline__ void unpack2<__half>(uint32_t w, float &lo, float &hi) {
-    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
-    lo = f.x;
-    hi = f.y;
-}
-template <typename T>
-__device__ __forceinline__ uint32_t pack2(float lo, float hi);
-template <>
-__device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&h);
-}
-template <>
-__device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
-    const __half2 h = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 // ---------------------------------------------------------------- row-streaming 3x3 conv
@@ -1015,7 +955,21 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                     const int o_lo = max(r - 1, ra), o_hi = min(r + 1, rb - 1);
                     const bool fresh = r + 1 <= rb - 1;
                     if (!await_row(gin)) return false;
-                    if (o_lo <= o_hi) {
+                    const int sl = (base + r - 1) & (NSLOT - 1);
+                    if (r - 1 >= ra && fresh && sl <= NSLOT - 3) {
+                        // interior row whose three accumulator rows do not wrap the ring (6 of 8
+                        // rows): one N = 3 * NPR run, the same MMAs as below with less set-up
+                        const uint64_t a_base = a_desc();
+                        const uint32_t id0 = instr_desc(TM, 0, AFMT, AFMT);
+                        const uint32_t nstep = (uint32_t)(NPR / 8) << 17;
+                        const uint32_t md = tmem_base + (uint32_t)(sl * NPR);
+                        umma<KIND>(md, a_base, b_base, id0 + nstep * 2u, 1u);
+                        umma<KIND>(md + 2u * NPR, a_base, b_base + (uint64_t)((2 * NPR * (SW ? 128 : 16)) >> 4),
+                                   id0 + nstep, 0u);
+#pragma unroll
+                        for (int t = 1; t < 3 * KSTEPS; ++t)
+                            umma<KIND>(md, a_base + a_off(t), b_base + b_off(t), id0 + nstep * 3u, 1u);
+                    } else if (o_lo <= o_hi) {
                         const uint64_t a_base = a_desc();
                         // Output rows [o_lo, o_hi] occupy one run of contiguous TMEM slots, or two
                         // where the ring wraps.  The first MMA of the row (kx = 0, K step 0) must not
@@ -1676,6 +1630,9 @@ __global__ void __launch_bounds__(128, 1) sw128_probe_kernel(int *out) {
 
 // ---------------------------------------------------------------- host side
 
+}  // namespace
+
+// The driver's tensor-map encoder (looked up once).
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -1689,6 +1646,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     });
     return fn;
 }
+
+namespace {
 
 // Output channels per CTA slice: the largest of 64/32/16 dividing cout_pad whose
 // weights (k*k*cin_bytes per output channel) fit the resident budget.

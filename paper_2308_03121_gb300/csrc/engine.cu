@@ -234,6 +234,7 @@ struct nvisr_filter {
     std::vector<Tensor> tensors;
     void *dcn_x8 = nullptr;        // DCN input in 8-channel planes (tensor-core path)
     std::vector<Step> steps;
+    std::vector<char> blk;           // step i and i + 1 form a residual block run as one fused launch
     int pack_t = -1;               // tensor id of the packed tuple
     int tuple_head = -1;           // the step that alone reads the packed tuple (-1: several or none)
     bool plain_final = false;      // some output uses a plain final layer (Step::plain)
@@ -1424,6 +1425,66 @@ ConvArgs conv_args(nvisr_filter *f, const Step &s, const float *const *frames, b
     return a;
 }
 
+// Residual blocks of a 16-bit tensor-core trunk: steps i, i + 1 = conv 64 -> 64 3x3 with
+// LeakyReLU, then conv 64 -> 64 3x3 without activation that adds step i's input, where
+// nothing else reads step i's output (nor a view of it).  Such a pair runs as one fused
+// launch (launch_res_block) unless NVISR_OPT_UNFUSED_BLOCKS is set.
+void plan_blocks(nvisr_filter *f) {
+    const size_t n = f->steps.size();
+    f->blk.assign(n, 0);
+    if (!f->tc || (f->act_dt != DT_BF16 && f->act_dt != DT_F16) || f->precision == NVISR_PREC_FP8 ||
+        (f->options & NVISR_OPT_UNFUSED_BLOCKS))
+        return;
+    std::vector<int> reads(f->tensors.size(), 0);
+    for (const Step &s : f->steps) {
+        if (s.in_t >= 0) reads[s.in_t]++;
+        if (s.add_t >= 0) reads[s.add_t]++;
+        if (s.om_t >= 0) reads[s.om_t]++;
+    }
+    std::vector<char> viewed(f->tensors.size(), 0);
+    for (const Tensor &t : f->tensors)
+        if (t.parent >= 0) viewed[t.parent] = 1;
+    auto body = [](const NetLayer &L, int act) {
+        return L.op == "conv" && L.cin == 64 && L.cout == 64 && L.k == 3 && L.ps == 0 && L.psx == 1 && L.psy == 1 &&
+               L.act == act;
+    };
+    for (size_t i = 0; i + 1 < n; ++i) {
+        const Step &a = f->steps[i], &b = f->steps[i + 1];
+        if (a.op != OP_CONV || b.op != OP_CONV || a.src != SRC_TENSOR || b.src != SRC_TENSOR || a.fp8 || b.fp8)
+            continue;
+        if (a.out_t < 0 || b.out_t < 0 || a.add_t >= 0 || b.in_t != a.out_t || b.add_t != a.in_t) continue;
+        if (a.xslot != b.xslot || a.xpair_w[0] != -2 || b.xpair_w[0] != -2 || a.frame_src >= 0) continue;
+        if (!body(f->net.layers[a.layer], 1) || !body(f->net.layers[b.layer], 0)) continue;
+        if (reads[a.out_t] != 1 || f->tensors[a.out_t].parent >= 0 || viewed[a.out_t]) continue;
+        f->blk[i] = 1;
+        ++i;  // blocks do not overlap
+    }
+}
+
+nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames, bool calib);
+
+// Steps i, i + 1 (a planned residual block) as one launch; as two where the buffers do not
+// allow it.
+nvisr_status run_block(nvisr_filter *f, size_t i, const float *const *frames) {
+    const Step &s1 = f->steps[i], &s2 = f->steps[i + 1];
+    int k1 = 0, k2 = 0;
+    const ConvArgs a1 = conv_args(f, s1, frames, false, &k1);
+    const ConvArgs a2 = conv_args(f, s2, frames, false, &k2);
+    if (!res_block_fits(a1, a2)) {
+        hold_if_same_kind(f, i);
+        nvisr_status st = run_step(f, s1, frames, false);
+        hold_if_same_kind(f, i + 1);
+        return st == NVISR_OK ? run_step(f, s2, frames, false) : st;
+    }
+    hold_if_same_kind(f, i + 1);
+    ProfScope ps(f, NVISR_K_CONV_BODY);
+    const cudaError_t e = launch_res_block(a1, a2, f->eng->stream);
+    if (e != cudaSuccess)
+        return cuda_status(e, ("residual block " + f->net.layers[s1.layer].name + ", " +
+                               f->net.layers[s2.layer].name).c_str());
+    return NVISR_OK;
+}
+
 nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames, bool calib) {
     const NetLayer &L = f->net.layers[s.layer];
     const Weights &Wt = s.widx >= 0 ? f->wvar[s.widx] : f->weights[s.layer];
@@ -1498,6 +1559,11 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
                 if (e != cudaSuccess) return cuda_status(e, ("conv layer " + f->net.layers[f->steps[i].layer].name).c_str());
                 continue;
             }
+            if (!calib && f->blk[i]) {
+                nvisr_status st = run_block(f, i++, frames);
+                if (st != NVISR_OK) return st;
+                continue;
+            }
             nvisr_status st = run_step(f, f->steps[i], frames, calib);
             if (st != NVISR_OK) return st;
         }
@@ -1522,6 +1588,11 @@ nvisr_status forward_tuple(nvisr_filter *f, const std::vector<int64_t> &idx, boo
     }
     if (e != cudaSuccess) return cuda_status(e, "pack");
     for (size_t i = 0; i < f->steps.size(); ++i) {
+        if (!calib && f->blk[i]) {
+            nvisr_status st = run_block(f, i++, frames);
+            if (st != NVISR_OK) return st;
+            continue;
+        }
         hold_if_same_kind(f, i);
         nvisr_status st = run_step(f, f->steps[i], frames, calib);
         if (st != NVISR_OK) return st;
@@ -1580,6 +1651,11 @@ nvisr_status forward_group(nvisr_filter *f, const std::vector<int64_t> &idx) {
     for (size_t i = 0; i < f->steps.size(); ++i) {
         const Step &s = f->steps[i];
         if (s.xslot >= 0 && !need[s.xslot]) continue;  // features held by the cache
+        if (f->blk[i]) {
+            nvisr_status st = run_block(f, i++, frames);
+            if (st != NVISR_OK) return st;
+            continue;
+        }
         hold_if_same_kind(f, i);
         if (s.op == OP_PACK) {
             const Tensor &t = f->tensors[s.out_t];
@@ -2126,6 +2202,7 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
     // kernel's shuffle tail): tensor-core tuple networks with an RGB domain, no transfer,
     // a bilinear skip of the centre frame or none
     f->options = d->options;
+    plan_blocks(f.get());
     if (net.family == "tuple" && f->tc && !(d->options & NVISR_OPT_UNFUSED_OUTPUT) &&
         (net.skip == 0 || net.skip == 2) && !f->steps.empty()) {
         const Step &last = f->steps.back();
@@ -2757,6 +2834,67 @@ nvisr_status nvisr_conv2d(int32_t precision, const float *x, int32_t cin, int32_
     NVISR_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     NVISR_TRY_CUDA(cudaStreamSynchronize(st));
     if (herr) return fail(NVISR_DEVICE_TIMEOUT, "conv2d: a device-side wait exceeded its bound");
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_resblock2d(int32_t precision, const float *x, int32_t h, int32_t w, const float *w1,
+                              const float *b1, const float *w2, const float *b2, float *y, int32_t fused,
+                              void *stream) {
+    if (!x || !w1 || !w2 || !y || h < 1 || w < 1) return fail(NVISR_INVALID_ARG, "resblock2d: bad arguments");
+    if (precision != NVISR_PREC_BF16 && precision != NVISR_PREC_FP16)
+        return fail(NVISR_UNSUPPORTED_FORMAT, "resblock2d: BF16 or FP16");
+    const size_t plane = (size_t)64 * h * w;
+    if (y < x + plane && x < y + plane) return fail(NVISR_INVALID_ARG, "resblock2d: y overlaps x");
+    const int dt = precision == NVISR_PREC_FP16 ? DT_F16 : DT_BF16;
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc;
+    std::vector<float> hw1((size_t)64 * 64 * 9), hw2(hw1.size()), hb1(64, 0.f), hb2(64, 0.f);
+    NVISR_TRY_CUDA(cudaMemcpyAsync(hw1.data(), w1, hw1.size() * 4, cudaMemcpyDeviceToHost, st));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(hw2.data(), w2, hw2.size() * 4, cudaMemcpyDeviceToHost, st));
+    if (b1) NVISR_TRY_CUDA(cudaMemcpyAsync(hb1.data(), b1, 64 * 4, cudaMemcpyDeviceToHost, st));
+    if (b2) NVISR_TRY_CUDA(cudaMemcpyAsync(hb2.data(), b2, 64 * 4, cudaMemcpyDeviceToHost, st));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+    std::vector<uint8_t> r1(tc_rows_weight_bytes()), r2(tc_rows_weight_bytes());
+    prepare_weights_rows(hw1.data(), dt, r1.data());
+    prepare_weights_rows(hw2.data(), dt, r2.data());
+    void *dr1, *dr2, *db1, *db2, *dx, *dh, *dy;
+    const size_t abytes = plane * 2;
+    NVISR_TRY_CUDA(sc.alloc(r1.size(), &dr1));
+    NVISR_TRY_CUDA(sc.alloc(r2.size(), &dr2));
+    NVISR_TRY_CUDA(sc.alloc(64 * 4, &db1));
+    NVISR_TRY_CUDA(sc.alloc(64 * 4, &db2));
+    NVISR_TRY_CUDA(sc.alloc(abytes, &dx));
+    NVISR_TRY_CUDA(sc.alloc(abytes, &dh));
+    NVISR_TRY_CUDA(sc.alloc(abytes, &dy));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(dr1, r1.data(), r1.size(), cudaMemcpyHostToDevice, st));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(dr2, r2.data(), r2.size(), cudaMemcpyHostToDevice, st));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(db1, hb1.data(), 64 * 4, cudaMemcpyHostToDevice, st));
+    NVISR_TRY_CUDA(cudaMemcpyAsync(db2, hb2.data(), 64 * 4, cudaMemcpyHostToDevice, st));
+    nvisr_status s = pack_planar(x, 64, 64, h, w, dt, 1.f, dx, st, 64);
+    if (s != NVISR_OK) return s;
+    int *err;
+    NVISR_TRY_CUDA(sc.alloc(sizeof(int), (void **)&err));
+    NVISR_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    ConvArgs a1{};
+    a1.x = dx; a1.cin_pad = 64; a1.in_cpc = 64; a1.out_cpc = 64; a1.H = h; a1.W = w; a1.nimg = 1;
+    a1.w_rows = dr1; a1.bias = (const float *)db1; a1.cout = 64; a1.cout_pad = 64; a1.k = 3; a1.act = 1;
+    a1.y = dh; a1.in_dt = dt; a1.out_dt = dt; a1.acc_scale = 1.f; a1.out_scale = 1.f; a1.y2_scale = 1.f; a1.err = err;
+    ConvArgs a2 = a1;
+    a2.x = dh; a2.w_rows = dr2; a2.bias = (const float *)db2; a2.act = 0; a2.res = dx; a2.y = dy;
+    cudaError_t e;
+    if (fused) {
+        if (!res_block_fits(a1, a2)) return fail(NVISR_UNSUPPORTED_FORMAT, "resblock2d: no fused form for these buffers");
+        e = launch_res_block(a1, a2, st);
+    } else {
+        e = launch_conv_tc(a1, st);
+        if (e == cudaSuccess) e = launch_conv_tc(a2, st);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "resblock2d");
+    NVISR_TRY_CUDA(launch_unpack(dy, dt, 64, 64, 64, h, w, 1.f, y, w, st));
+    int herr = 0;
+    NVISR_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(st));
+    if (herr) return fail(NVISR_DEVICE_TIMEOUT, "resblock2d: a device-side wait exceeded its bound");
     return NVISR_OK;
 }
 
