@@ -39,22 +39,21 @@ import synth  # noqa: E402
 METRIC = "output Mpix/s per GB300 at 1080p→4K 2x SR, BF16/FP8 vs FP32 at ±1 LSB; p99 latency"
 W, H, S = 1920, 1080, 2
 OUT_PIX = (W * S) * (H * S)
-BODY_FLOP = 2.0 * W * H * 64 * 9 * 64          # one 64->64 3x3 conv launch at 1080p
+BODY_FLOP = 2.0 * W * H * 64 * 9 * 64          # one 64->64 3x3 conv at 1080p
 ACT_BYTES = W * H * 64 * 2                     # one 64-channel BF16 activation at 1080p (265 MB)
-# algorithmic DRAM bytes of one body launch, averaged over a step's 20 launches:
-# every launch reads x and writes y; the 10 second convolutions of the residual
-# blocks also read the block input (weights, 74 KB, are negligible)
-BODY_BYTES = 2.5 * ACT_BYTES
+# The trunk's 10 residual blocks run as one fused launch each (res_block_kernel: both
+# convs, the middle tensor kept on chip).  Algorithmic DRAM bytes of a block launch: read
+# x, write y (the residual re-read of x is an L2 hit; weights, 2 x 74 KB, are negligible).
+BLOCK_BYTES = 2 * ACT_BYTES
 H2D_BYTES = W * H * 2 + 2 * (W // 2) * (H // 2) * 2
 D2H_BYTES = (W * S) * (H * S) * 2 + 2 * (W * S // 2) * (H * S // 2) * 2
 NFRAMES = 12                                   # distinct resident input frames, cycled
-# DRAM bytes (read + written) per conv_body launch, the mean of a launch with and
-# one without residual, from one ncu capture of the body kernel at 1080p; None
-# until the kernel as it stands has been captured
-CONV_BODY_TRAFFIC = 621.9e6
-CONV_BODY_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of two body launches (761.2 MB with "
-                            "residual, 482.6 MB without), the 9th and 10th conv_rows_kernel launches of this "
-                            "bench's bf16 run with --steps 3")
+# DRAM bytes (read + written) per block launch from one ncu capture of the block kernel at
+# 1080p; None until the kernel as it stands has been captured
+BLOCK_TRAFFIC = 501.0e6
+BLOCK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum (278.7 + 222.3 MB) of the third "
+                        "res_block_kernel launch of this bench's bf16 run with --steps 2 "
+                        "(profiles/res_block_bf16_1080p.md)")
 WORKLOAD = ("1080p->4K 2x SR: sliding window T=5, conv 15->64, 10 residual blocks of 64 ch, conv 64->12, "
             "PixelShuffle(2), bilinear skip; 10-bit 4:2:0 limited BT.709 in and out")
 DATA = "synthetic: seeded textured 10-bit 4:2:0 frames with global 0-4 px translation; random-init He-normal weights"
@@ -630,8 +629,10 @@ def main():
     prof = r["prof"]
     body_ms, body_n = prof["conv_body"]
     avg_body = body_ms / max(body_n, 1)
-    achieved_tf = BODY_FLOP / (avg_body * 1e-3) / 1e12
-    achieved_gbs = BODY_BYTES / (avg_body * 1e-3) / 1e9
+    # 20 trunk convolutions per step in body_n / psteps launches (10 fused blocks)
+    convs = 20 * r["psteps"] / max(body_n, 1)
+    achieved_tf = convs * BODY_FLOP / (avg_body * 1e-3) / 1e12
+    achieved_gbs = convs / 2 * BLOCK_BYTES / (avg_body * 1e-3) / 1e9
     launches = round(sum(n for _, n in prof.values()) * r["steps"] / r["psteps"])
     e2e_total, p50, p99 = measure_e2e(nv, head, args.e2e_steps, pinned, local)
     config3 = pyramid = None
@@ -690,13 +691,15 @@ def main():
         "frames_per_s": world * r["steps"] / (r["ms"] * 1e-3),
         # the body is a dense contraction: its bound is the tensor pipe (BF16, timed inside
         # a long step, so the sustained peak); its HBM fraction is given beside it
-        "roofline": {"kernel": "conv_rows_kernel (64->64 3x3 row-streaming, BF16, 20 launches/step)",
+        "roofline": {"kernel": f"res_block_kernel (residual block of two 64->64 3x3 convs in one launch of 2-CTA "
+                               f"clusters, BF16, {body_n / r['psteps']:g} launches/step)",
                      "bound": "tensor", "achieved": achieved_tf, "peak": bf16_sust, "unit": "TFLOP/s",
                      "frac": achieved_tf / bf16_sust, "peak_source": f"bf16_tflops_sustained of {peak_src}",
-                     "algorithmic_flop_per_launch": BODY_FLOP, "avg_launch_ms": avg_body,
-                     "traffic": CONV_BODY_TRAFFIC, "traffic_source": CONV_BODY_TRAFFIC_SOURCE,
+                     "algorithmic_flop_per_launch": convs * BODY_FLOP, "avg_launch_ms": avg_body,
+                     "traffic": BLOCK_TRAFFIC, "traffic_source": BLOCK_TRAFFIC_SOURCE,
                      "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
-                             "peak_source": f"hbm_gbs of {peak_src}", "algorithmic_bytes_per_launch": BODY_BYTES}},
+                             "peak_source": f"hbm_gbs of {peak_src}",
+                             "algorithmic_bytes_per_launch": convs / 2 * BLOCK_BYTES}},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": H2D_BYTES,
                 "d2h_bytes_per_step": D2H_BYTES, "steps": args.e2e_steps},
