@@ -74,12 +74,14 @@ struct BlockParams {
     int starve;                // test drill: rank 0 loads no input, the pipeline waits run out
 };
 
-template <int DT>
+// MULTI: the images of several streams (one BlockProblem each, any sizes) share the launch;
+// otherwise nimg images of one size stacked along the maps' outer dimension.
+template <int DT, bool MULTI>
 __global__ void __launch_bounds__(BTHREADS, 1)
     res_block_kernel(const __grid_constant__ CUtensorMap xmap,  // x: 130-pixel row boxes, OOB zero
                      const __grid_constant__ CUtensorMap rmap,  // x: 128-pixel row tiles (residual)
                      const __grid_constant__ CUtensorMap ymap,  // y: 126-pixel row tiles
-                     const BlockParams p) {
+                     const BlockParams p, const BlockProblem *__restrict__ probs, int nprob) {
     using TO = typename Elem<DT>::T;
     constexpr int AFMT = DT == DT_BF16 ? 1 : 0;
     extern __shared__ uint8_t smem_raw[];
@@ -111,16 +113,30 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     const bool first = rank == 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t npairs = cluster_count_x(), pair = cluster_id_x();
-    const int64_t total = (int64_t)p.nimg * p.ncols * p.H;
+    const int64_t total = MULTI ? probs[nprob - 1].u0 + (int64_t)probs[nprob - 1].ncols * probs[nprob - 1].H
+                                : (int64_t)p.nimg * p.ncols * p.H;
     const int64_t u_begin = total * pair / npairs, u_end = total * (pair + 1) / npairs;
-    // the strip at position u of this cluster's range: image, column tile, output rows [ra, rb)
-    auto strip_at = [&](int64_t u, int &img, int &col, int &ra, int &rb) {
-        const int64_t cg = u / p.H;
-        ra = (int)(u - cg * p.H);
-        rb = (int)min((int64_t)p.H, (int64_t)ra + (u_end - u));
-        img = (int)(cg / p.ncols);
+    // the strip at position u of this cluster's range: problem (MULTI), image, column tile,
+    // output rows [ra, rb)
+    auto strip_at = [&](int64_t u, int &pi, int &img, int &col, int &ra, int &rb) {
+        int64_t local = u, H = p.H;
+        pi = 0;
+        if (MULTI) {
+            while (pi + 1 < nprob && u >= probs[pi + 1].u0) ++pi;
+            local = u - probs[pi].u0;
+            H = probs[pi].H;
+        }
+        const int64_t cg = local / H;
+        ra = (int)(local - cg * H);
+        rb = (int)min(H, (int64_t)ra + (u_end - u));
+        img = MULTI ? 0 : (int)(cg / p.ncols);
         col = (int)(cg - (int64_t)img * p.ncols);
     };
+    auto xmap_of = [&](int pi) { return MULTI ? &probs[pi].xmap : &xmap; };
+    auto rmap_of = [&](int pi) { return MULTI ? &probs[pi].rmap : &rmap; };
+    auto ymap_of = [&](int pi) { return MULTI ? &probs[pi].ymap : &ymap; };
+    auto height_of = [&](int pi) { return MULTI ? probs[pi].H : p.H; };
+    auto width_of = [&](int pi) { return MULTI ? probs[pi].W : p.W; };
     // rows this CTA's accumulators produce for a strip: h rows [ra - 1, rb + 1) (rank 0) or
     // output rows [ra, rb) (rank 1); its input rows run from oa - 1 to ob
     auto out_rows = [&](int ra, int rb, int &oa, int &ob) {
@@ -188,8 +204,8 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             int gin = 0;
             bool ok = true;
             for (int64_t u = u_begin; u < u_end && ok && !p.starve;) {
-                int img, col, ra, rb;
-                strip_at(u, img, col, ra, rb);
+                int pi, img, col, ra, rb;
+                strip_at(u, pi, img, col, ra, rb);
                 u += rb - ra;
                 const int xb = col * BT - 2;  // box pixel 0 = h pixel col * BT - 1 minus one
                 for (int r = ra - 2; r <= rb + 1; ++r, ++gin) {
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                         break;
                     }
                     mbar_arrive_expect_tx(&full[s], AROW);
-                    tma_load_4d(region + (size_t)s * ROWB, &xmap, &full[s], 0, xb, r, img);
+                    tma_load_4d(region + (size_t)s * ROWB, xmap_of(pi), &full[s], 0, xb, r, img);
                 }
             }
             // copies still in flight after an early exit land before the CTA ends
@@ -242,8 +258,8 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             auto a_off = [](int t) { return (uint64_t)(((t / 4) * 128 + (t % 4) * 32) >> 4); };
             auto b_off = [](int t) { return (uint64_t)(((t / 4) * WKX + (t % 4) * 32) >> 4); };
             for (int64_t u = u_begin; u < u_end && ok;) {
-                int img, col, ra, rb, oa, ob;
-                strip_at(u, img, col, ra, rb);
+                int pi, img, col, ra, rb, oa, ob;
+                strip_at(u, pi, img, col, ra, rb);
                 u += rb - ra;
                 out_rows(ra, rb, oa, ob);
                 const int base = gout - oa;  // global accumulator-row index of row o is base + o
@@ -332,8 +348,8 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             uint32_t ph = 0;
             bool ok = true;
             for (int64_t u = u_begin; u < u_end && ok;) {
-                int img, col, ra, rb, oa, ob;
-                strip_at(u, img, col, ra, rb);
+                int pi, img, col, ra, rb, oa, ob;
+                strip_at(u, pi, img, col, ra, rb);
                 u += rb - ra;
                 out_rows(ra, rb, oa, ob);
                 const int base = gout - oa;
@@ -385,12 +401,13 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         int gout = 0;
         bool ok = true;
         for (int64_t u = u_begin; u < u_end && ok;) {
-            int img, col, ra, rb;
-            strip_at(u, img, col, ra, rb);
+            int pi, img, col, ra, rb;
+            strip_at(u, pi, img, col, ra, rb);
             u += rb - ra;
             const int oa = ra - 1, ob = rb + 1;
             const int px = col * BT - 1 + m;
-            const bool colok = px >= 0 && px < p.W;
+            const bool colok = px >= 0 && px < width_of(pi);
+            const int Hs = height_of(pi);
             int o = oa + ((g - (gout & 1)) & 1);
             for (; o < ob; o += 2) {
                 const int i = gout + (o - oa);
@@ -434,7 +451,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                     v[e] = fmaxf(v[e], t0);
                     v[e + 1] = fmaxf(v[e + 1], t1);
                 }
-                const bool keep = colok && o >= 0 && o < p.H;  // else conv2's zero padding
+                const bool keep = colok && o >= 0 && o < Hs;  // else conv2's zero padding
                 // the h slot's previous row (i - HS) and the staging tile's (i - 4) have been read
                 bool wf = consumed(i - HS) && consumed(i - 4);
                 wf = __all_sync(0xffffffffu, wf);
@@ -486,14 +503,14 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         int res_loads = 0, last_res = -1;
         bool ok = true;
         for (int64_t u = u_begin; u < u_end && ok;) {
-            int img, col, ra, rb;
-            strip_at(u, img, col, ra, rb);
+            int pi, img, col, ra, rb;
+            strip_at(u, pi, img, col, ra, rb);
             u += rb - ra;
             const int x0 = col * BT;
             int o = ra + ((g - (gout & 1)) & 1);
             if (leader && o < rb) {
                 mbar_arrive_expect_tx(&resfull[g], TILEB);
-                tma_load_4d(rbuf + g * TILEB, &rmap, &resfull[g], 0, x0, o, img);
+                tma_load_4d(rbuf + g * TILEB, rmap_of(pi), &resfull[g], 0, x0, o, img);
                 last_res = res_loads++;
             }
             for (; o < rb; o += 2) {
@@ -568,11 +585,11 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                     break;
                 }
                 if (leader) {
-                    tma_store_4d(&ymap, obuf + g * TILEB, 0, x0, o, img);
+                    tma_store_4d(ymap_of(pi), obuf + g * TILEB, 0, x0, o, img);
                     bulk_commit_group();
                     if (o + 2 < rb) {  // this group's next row; the tile's readers are done
                         mbar_arrive_expect_tx(&resfull[g], TILEB);
-                        tma_load_4d(rbuf + g * TILEB, &rmap, &resfull[g], 0, x0, o + 2, img);
+                        tma_load_4d(rbuf + g * TILEB, rmap_of(pi), &resfull[g], 0, x0, o + 2, img);
                         last_res = res_loads++;
                     }
                 }
@@ -612,7 +629,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
 }
 
 // Clusters of this kernel that fit the device at once (one CTA per SM), looked up once per device.
-template <int DT>
+template <int DT, bool MULTI>
 int max_pairs() {
     static int cached[64] = {0};
     int dev = 0;
@@ -630,7 +647,7 @@ int max_pairs() {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, res_block_kernel<DT>, &cfg) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n, res_block_kernel<DT, MULTI>, &cfg) != cudaSuccess || n < 1) {
         (void)cudaGetLastError();
         return 0;
     }
@@ -638,15 +655,15 @@ int max_pairs() {
     return n;
 }
 
-template <int DT>
+// units: output rows x column tiles of the launch (each cluster gets an equal range)
+template <int DT, bool MULTI>
 cudaError_t run_block(const CUtensorMap &xmap, const CUtensorMap &rmap, const CUtensorMap &ymap,
-                      const BlockParams &p, cudaStream_t st) {
-    cudaError_t e = set_smem_limit<res_block_kernel<DT>>(BLOCK_SMEM);
+                      const BlockParams &p, const BlockProblem *probs, int nprob, int64_t units, cudaStream_t st) {
+    cudaError_t e = set_smem_limit<res_block_kernel<DT, MULTI>>(BLOCK_SMEM);
     if (e != cudaSuccess) return e;
-    int npairs = max_pairs<DT>();
+    int npairs = max_pairs<DT, MULTI>();
     if (npairs < 1) return cudaErrorInvalidConfiguration;
     // at least ~16 output rows per cluster: each strip costs conv1 two extra rows
-    const int64_t units = (int64_t)p.nimg * p.ncols * p.H;
     npairs = (int)std::max<int64_t>(1, std::min<int64_t>(npairs, units / 16));
     cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -662,7 +679,7 @@ cudaError_t run_block(const CUtensorMap &xmap, const CUtensorMap &rmap, const CU
     cfg.stream = st;
     cfg.attrs = at;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, res_block_kernel<DT>, xmap, rmap, ymap, p);
+    return cudaLaunchKernelEx(&cfg, res_block_kernel<DT, MULTI>, xmap, rmap, ymap, p, probs, nprob);
 }
 
 cudaError_t encode_block_map(CUtensorMap *map, const void *base, int W, int H, int nimg, int box_px) {
@@ -676,6 +693,29 @@ cudaError_t encode_block_map(CUtensorMap *map, const void *base, int W, int H, i
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t encode_block_maps(const ConvArgs &c1, const ConvArgs &c2, CUtensorMap *xmap, CUtensorMap *rmap,
+                              CUtensorMap *ymap) {
+    cudaError_t e = encode_block_map(xmap, c1.x, c1.W, c1.H, c1.nimg, PXS);
+    if (e == cudaSuccess) e = encode_block_map(rmap, c1.x, c1.W, c1.H, c1.nimg, TMH);
+    if (e == cudaSuccess) e = encode_block_map(ymap, c2.y, c1.W, c1.H, c1.nimg, BT);
+    return e;
+}
+
+BlockParams block_params(const ConvArgs &c1, const ConvArgs &c2) {
+    BlockParams p{};
+    p.H = c1.H;
+    p.W = c1.W;
+    p.nimg = c1.nimg;
+    p.ncols = (c1.W + BT - 1) / BT;
+    p.w1 = static_cast<const uint8_t *>(c1.w_rows);
+    p.w2 = static_cast<const uint8_t *>(c2.w_rows);
+    p.b1 = c1.bias;
+    p.b2 = c2.bias;
+    p.err = c1.err ? c1.err : c2.err;
+    p.starve = test_starve();
+    return p;
 }
 
 }  // namespace
@@ -696,23 +736,45 @@ bool res_block_fits(const ConvArgs &c1, const ConvArgs &c2) {
 cudaError_t launch_res_block(const ConvArgs &c1, const ConvArgs &c2, cudaStream_t st) {
     if (!res_block_fits(c1, c2)) return cudaErrorInvalidValue;
     CUtensorMap xmap, rmap, ymap;
-    cudaError_t e = encode_block_map(&xmap, c1.x, c1.W, c1.H, c1.nimg, PXS);
-    if (e == cudaSuccess) e = encode_block_map(&rmap, c1.x, c1.W, c1.H, c1.nimg, TMH);
-    if (e == cudaSuccess) e = encode_block_map(&ymap, c2.y, c1.W, c1.H, c1.nimg, BT);
+    cudaError_t e = encode_block_maps(c1, c2, &xmap, &rmap, &ymap);
     if (e != cudaSuccess) return e;
-    BlockParams p{};
-    p.H = c1.H;
-    p.W = c1.W;
-    p.nimg = c1.nimg;
-    p.ncols = (c1.W + BT - 1) / BT;
-    p.w1 = static_cast<const uint8_t *>(c1.w_rows);
-    p.w2 = static_cast<const uint8_t *>(c2.w_rows);
-    p.b1 = c1.bias;
-    p.b2 = c2.bias;
-    p.err = c1.err ? c1.err : c2.err;
-    p.starve = test_starve();
-    return c1.in_dt == DT_BF16 ? run_block<DT_BF16>(xmap, rmap, ymap, p, st)
-                               : run_block<DT_F16>(xmap, rmap, ymap, p, st);
+    const BlockParams p = block_params(c1, c2);
+    const int64_t units = (int64_t)p.nimg * p.ncols * p.H;
+    return c1.in_dt == DT_BF16 ? run_block<DT_BF16, false>(xmap, rmap, ymap, p, nullptr, 0, units, st)
+                               : run_block<DT_F16, false>(xmap, rmap, ymap, p, nullptr, 0, units, st);
+}
+
+cudaError_t launch_res_block_multi(const ConvArgs *c1, const ConvArgs *c2, int n, BlockProblem *host_tab,
+                                   BlockProblem *dev_tab, cudaStream_t st, bool copy_table, bool launch) {
+    if (n < 1) return cudaSuccess;
+    for (int i = 0; i < n; ++i) {
+        // one image each; the same weights, biases and dtype
+        if (!res_block_fits(c1[i], c2[i]) || c1[i].nimg != 1 || c1[i].in_dt != c1[0].in_dt ||
+            c1[i].w_rows != c1[0].w_rows || c2[i].w_rows != c2[0].w_rows || c1[i].bias != c1[0].bias ||
+            c2[i].bias != c2[0].bias)
+            return cudaErrorInvalidValue;
+    }
+    int64_t units = 0;
+    for (int i = 0; i < n; ++i) {
+        BlockProblem &q = host_tab[i];
+        cudaError_t e = encode_block_maps(c1[i], c2[i], &q.xmap, &q.rmap, &q.ymap);
+        if (e != cudaSuccess) return e;
+        q.H = c1[i].H;
+        q.W = c1[i].W;
+        q.ncols = (c1[i].W + BT - 1) / BT;
+        q.pad_ = 0;
+        q.u0 = units;
+        units += (int64_t)q.ncols * q.H;
+    }
+    if (copy_table) {
+        cudaError_t e = cudaMemcpyAsync(dev_tab, host_tab, sizeof(BlockProblem) * n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (!launch) return cudaSuccess;
+    const BlockParams p = block_params(c1[0], c2[0]);
+    return c1[0].in_dt == DT_BF16
+               ? run_block<DT_BF16, true>(host_tab[0].xmap, host_tab[0].rmap, host_tab[0].ymap, p, dev_tab, n, units, st)
+               : run_block<DT_F16, true>(host_tab[0].xmap, host_tab[0].rmap, host_tab[0].ymap, p, dev_tab, n, units, st);
 }
 
 }  // namespace nvisr

@@ -277,6 +277,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 // allow it (y must not overlap x); launch returns cudaErrorInvalidValue otherwise.
 bool res_block_fits(const ConvArgs &c1, const ConvArgs &c2);
 cudaError_t launch_res_block(const ConvArgs &c1, const ConvArgs &c2, cudaStream_t st);
+// One image of a batched block launch: its tensor maps (x as 130-pixel boxes, x as 128-pixel
+// residual tiles, y as 126-pixel tiles; in global memory, 64-byte aligned), its size, and
+// its first unit in the launch's (image, column tile, row) sequence.
+struct alignas(64) BlockProblem {
+    CUtensorMap xmap, rmap, ymap;
+    int H, W, ncols, pad_;
+    int64_t u0;
+};
+// One block launch over n images (c1[i], c2[i] as for launch_res_block; the same weights,
+// biases and dtype; each its own x / y and size).  host_tab and dev_tab hold n entries; the
+// table is written to host_tab, copied to dev_tab on `st` when copy_table, and must stay
+// unchanged until the launch has run (a captured graph reuses it).  launch = false only
+// fills (and copies) the table.
+cudaError_t launch_res_block_multi(const ConvArgs *c1, const ConvArgs *c2, int n, BlockProblem *host_tab,
+                                   BlockProblem *dev_tab, cudaStream_t st, bool copy_table, bool launch);
 
 // Feature-pyramid resampling on blocked [C/cpc][H][W][cpc] tensors of dtype dt (x: H x W):
 // up = false: 2x2 mean into (H/2) x (W/2) (H, W even); up = true: bilinear x2

@@ -1851,6 +1851,8 @@ struct nvisr_batch {
         std::vector<int> parts;                       // participating members
         PackArgs *pack_dev = nullptr;                 // per-step pack table (device)
         std::vector<RowProblem *> tab_host, tab_dev;  // per step: shared-launch table, or null
+        // per step starting a residual block: the shared fused launch's table (steps si, si + 1), or null
+        std::vector<BlockProblem *> btab_host, btab_dev;
         int rps = 0;                                  // rows per strip chosen by the autotuner
         cudaGraphExec_t exec = nullptr;
         bool no_graph = false;                        // capture failed: launch directly
@@ -1870,6 +1872,10 @@ void free_plan(nvisr_batch::Plan &p) {
     if (p.pack_dev) cudaFree(p.pack_dev);
     for (RowProblem *t : p.tab_host)
         if (t) cudaFreeHost(t);
+    for (BlockProblem *t : p.btab_host)
+        if (t) cudaFreeHost(t);
+    for (BlockProblem *t : p.btab_dev)
+        if (t) cudaFree(t);
     for (RowProblem *t : p.tab_dev)
         if (t) cudaFree(t);
     p = nvisr_batch::Plan{};
@@ -1904,10 +1910,18 @@ nvisr_status enqueue_forward(nvisr_batch *b, nvisr_batch::Plan &P, const std::ve
     const int n = (int)P.parts.size();
     cudaError_t e = launch_pack_table(pack_host.data(), P.pack_dev, n, st);
     if (e != cudaSuccess) return cuda_status(e, "batched pack");
-    std::vector<ConvArgs> args(n);
+    std::vector<ConvArgs> args(n), args2(n);
     const size_t nsteps = b->members[0]->steps.size();
     for (size_t si = 0; si < nsteps; ++si) {
         for (int i = 0; i < n; ++i) args[i] = member_args(b, b->members[P.parts[i]], si, pf.frames[i].data());
+        if (P.btab_host[si]) {
+            // a residual block (steps si, si + 1) over every participant's image in one launch
+            for (int i = 0; i < n; ++i) args2[i] = member_args(b, b->members[P.parts[i]], si + 1, pf.frames[i].data());
+            e = launch_res_block_multi(args.data(), args2.data(), n, P.btab_host[si], P.btab_dev[si], st, false, true);
+            if (e != cudaSuccess) return cuda_status(e, "batched residual block");
+            ++si;
+            continue;
+        }
         if (P.tab_host[si]) {
             e = launch_conv_rows_multi(args.data(), n, P.tab_host[si], P.tab_dev[si], P.rps, st, false, true);
             if (e != cudaSuccess) return cuda_status(e, "batched conv");
@@ -1969,9 +1983,32 @@ nvisr_status build_batch_plan(nvisr_batch *b, nvisr_batch::Plan &P, const PartFr
     const size_t nsteps = b->members[0]->steps.size();
     P.tab_host.assign(nsteps, nullptr);
     P.tab_dev.assign(nsteps, nullptr);
-    std::vector<ConvArgs> args(n);
+    P.btab_host.assign(nsteps, nullptr);
+    P.btab_dev.assign(nsteps, nullptr);
+    std::vector<ConvArgs> args(n), args2(n);
+    // residual blocks every participant runs fused alone: one shared fused launch each
+    for (size_t si = 0; si + 1 < nsteps; ++si) {
+        bool blk = true;
+        for (int i = 0; i < n && blk; ++i) {
+            nvisr_filter *f = b->members[P.parts[i]];
+            blk = f->blk[si] != 0;
+            if (blk) {
+                args[i] = member_args(b, f, si, pf.frames[i].data());
+                args2[i] = member_args(b, f, si + 1, pf.frames[i].data());
+                blk = res_block_fits(args[i], args2[i]) && args[i].nimg == 1;
+            }
+        }
+        if (!blk) continue;
+        NVISR_TRY_CUDA(cudaMallocHost(&P.btab_host[si], sizeof(BlockProblem) * n));
+        NVISR_TRY_CUDA(cudaMalloc(&P.btab_dev[si], sizeof(BlockProblem) * n));
+        cudaError_t e = launch_res_block_multi(args.data(), args2.data(), n, P.btab_host[si], P.btab_dev[si], st,
+                                               true, false);
+        if (e != cudaSuccess) return cuda_status(e, "batched residual block table");
+        ++si;
+    }
     for (size_t si = 0; si < nsteps; ++si) {
-        bool rows = n > 1 && b->members[0]->steps[si].op == OP_CONV;
+        const bool in_block = P.btab_host[si] || (si > 0 && P.btab_host[si - 1]);
+        bool rows = !in_block && n > 1 && b->members[0]->steps[si].op == OP_CONV;
         for (int i = 0; i < n && rows; ++i) {
             args[i] = member_args(b, b->members[P.parts[i]], si, pf.frames[i].data());
             rows = rows_kernel_fits(args[i]) && !args[i].y2 && !args[i].amax;
