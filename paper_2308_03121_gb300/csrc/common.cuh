@@ -95,6 +95,8 @@ bool fused_rq_format(const nvisr_format &f, int yuv, FusedRq *rq);
 // Finishes the LEFT-sited 4:2:0 chroma samples at the first column of each 128-pixel tile
 // after x = 0 (H low-resolution rows, W low-resolution columns).
 cudaError_t launch_rq_edge_fixup(const FusedRq &rq, int H, int W, cudaStream_t st);
+// Whether launch_rq_edge_fixup launches its kernel for this output (LEFT-sited 4:2:0, 2+ tiles).
+bool rq_edge_fixup_runs(const FusedRq &rq, int W);
 
 // A final layer's float32 output, blocked [cpad/4][H][W][4], PixelShuffled by (ry, rx) into
 // planar [C / (ry*rx)][H*ry][dst_pitch]: dst[c][ry*y + i][rx*x + j] = src channel

@@ -353,6 +353,7 @@ void flush_profile(nvisr_filter *f) {
 struct ProfScope {
     nvisr_filter *f;
     int kind;
+    int launches = 1;  // kernels this scope's call launched
     cudaEvent_t a = nullptr;
     bool join = false;
     ProfScope(nvisr_filter *f_, int kind_) : f(f_), kind(kind_) {
@@ -369,10 +370,10 @@ struct ProfScope {
     }
     ~ProfScope() {
         if (join) {
-            f->recs.back().n += 1;
+            f->recs.back().n += launches;
         } else {
             if (!a) return;
-            f->recs.push_back({kind, a, take_event(f), 1});
+            f->recs.push_back({kind, a, take_event(f), launches});
             f->prof_join = true;
         }
         f->prof_open = true;
@@ -1524,6 +1525,7 @@ nvisr_status run_step(nvisr_filter *f, const Step &s, const float *const *frames
     ProfScope ps(f, kind);
     cudaError_t e = f->tc ? launch_conv_tc(a, st) : launch_conv_simt(a, st);
     if (e != cudaSuccess) return cuda_status(e, ("conv layer " + L.name).c_str());
+    if (f->tc && rq_edge_fixup_runs(a.rq, a.W)) ps.launches = 2;  // the tail's chroma edge fix-up
     if (s.plain) {
         e = launch_shuffle_planar(f->final_f32, a.H, a.W, s.psy, s.psx, f->out_rgb[s.out_index], f->opitch, st);
         if (e != cudaSuccess) return cuda_status(e, ("output shuffle of " + L.name).c_str());

@@ -1030,9 +1030,13 @@ __global__ void rq_edge_fixup_kernel(FusedRq rq, int H, int W, int tiles) {
 
 }  // namespace
 
+bool rq_edge_fixup_runs(const FusedRq &rq, int W) {
+    return rq.on && rq.sub420 && rq.loc == NVISR_CHROMA_LEFT && (W + 127) / 128 >= 2;
+}
+
 cudaError_t launch_rq_edge_fixup(const FusedRq &rq, int H, int W, cudaStream_t st) {
     const int tiles = (W + 127) / 128;
-    if (!rq.on || !rq.sub420 || rq.loc != NVISR_CHROMA_LEFT || tiles < 2) return cudaSuccess;
+    if (!rq_edge_fixup_runs(rq, W)) return cudaSuccess;
     const int n = H * (tiles - 1);
     const dim3 grid((n + 127) / 128), block(128);
     return rq.wide ? launch_dependent(rq_edge_fixup_kernel<uint16_t>, grid, block, 0, st, rq, H, W, tiles)
