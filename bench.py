@@ -50,10 +50,9 @@ D2H_BYTES = (W * S) * (H * S) * 2 + 2 * (W * S // 2) * (H * S // 2) * 2
 NFRAMES = 12                                   # distinct resident input frames, cycled
 # DRAM bytes (read + written) per block launch from one ncu capture of the block kernel at
 # 1080p; None until the kernel as it stands has been captured
-BLOCK_TRAFFIC = 501.0e6
-BLOCK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum (278.7 + 222.3 MB) of the third "
-                        "res_block_kernel launch of this bench's bf16 run with --steps 2 "
-                        "(profiles/res_block_bf16_1080p.md)")
+BLOCK_TRAFFIC = 501.1e6
+BLOCK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum (278.7 + 222.4 MB) of the third "
+                        "res_block_kernel launch of this bench's bf16 run with --steps 2, on the kernel as built")
 WORKLOAD = ("1080p->4K 2x SR: sliding window T=5, conv 15->64, 10 residual blocks of 64 ch, conv 64->12, "
             "PixelShuffle(2), bilinear skip; 10-bit 4:2:0 limited BT.709 in and out")
 DATA = "synthetic: seeded textured 10-bit 4:2:0 frames with global 0-4 px translation; random-init He-normal weights"

@@ -11,7 +11,7 @@
 // sixteen producer warps (a warp per 8-channel chunk and half tile, a lane pair
 // per pixel) read the tap's offsets and mask, issue the bilinear corner loads
 // of all their pixels before using any (so many gathers are in flight at
-// once), blend them in FP32, scale by the mask and store 8-byte halves of the
+// once), blend them in FP32 with the mask folded into the row weights, and store 8-byte halves of the
 // 16-byte rows of the canonical no-swizzle K-major A tile in shared memory (the
 // sampled im2col tile of that tap).  A single thread issues the tap's
 // tcgen05.mma's against the resident weights into a double-buffered TMEM
@@ -162,30 +162,95 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
         const bool tapm = a.om_tap_major != 0;
         const uint8_t *plane = x + (int64_t)((cc * CPC) / xcpc) * HW * xcpc * 2 + ((cc * CPC) % xcpc) * 2;
         const uint32_t pstride = (uint32_t)xcpc * 2;  // bytes per pixel in the plane (the plane is < 2 GiB)
+        const uint32_t rowb = (uint32_t)W * pstride;  // bytes per row of the plane
+        static_assert(NPASS % 2 == 0, "passes shared by a lane pair");
+        constexpr int NP2 = NPASS / 2;
         int s = 0;
         uint32_t ph = 0;
         bool ok = true;
-        // offsets (dy, dx adjacent in one 4-channel unit) and mask of every pass's pixel for tap k
-        auto load_om = [&](int y, int xb, int k, float2 (&d)[NPASS], float (&mk)[NPASS]) {
+        // Corner values.  A corner is loaded only when its weight is nonzero, which the
+        // bounds checks allow only inside the image.  A skipped corner keeps the value
+        // of an earlier load (or zero), which its weight of zero cancels (x is finite).
+        uint4 v[NPASS][2];
+#pragma unroll
+        for (int j = 0; j < NPASS; ++j) v[j][0] = v[j][1] = make_uint4(0u, 0u, 0u, 0u);
+        // offsets and mask of this lane's passes h = 2i + c for tap k of tile t: loaded one
+        // tap ahead of their use, so that their DRAM latency overlaps the previous tap
+        auto load_om = [&](int t, int k, float2 (&d)[NP2], float (&lg)[NP2]) {
+            const int y = t / tiles_x;
+            const int xb = (t - y * tiles_x) * TM;
             const int cd = dcn_off_channel(g, k, G, tapm), cm = dcn_mask_channel(g, k, G, tapm);
             // float offsets in 32 bits (the tensor is < 2^31 floats)
             const uint32_t od = (uint32_t)(cd >> 2) * (uint32_t)HW * 4u + (cd & 3);
             const uint32_t oms = (uint32_t)(cm >> 2) * (uint32_t)HW * 4u + (cm & 3);
 #pragma unroll
-            for (int h = 0; h < NPASS; ++h) {
-                const uint32_t pix4 = (uint32_t)(y * W + min(xb + pb + h * 16, W - 1)) * 4u;
-                d[h] = __ldg(reinterpret_cast<const float2 *>(a.om + od + pix4));
-                mk[h] = __ldg(a.om + oms + pix4);
+            for (int i = 0; i < NP2; ++i) {
+                const int px = xb + pb + (2 * i + c) * 16;
+                const uint32_t pix4 = (uint32_t)(y * W + min(px, W - 1)) * 4u;
+                d[i] = __ldg(reinterpret_cast<const float2 *>(a.om + od + pix4));
+                lg[i] = __ldg(a.om + oms + pix4);
             }
         };
+        float2 nd[NP2];
+        float nlg[NP2];
+        if (blockIdx.x < ntiles && !a.starve) load_om(blockIdx.x, 0, nd, nlg);
         for (int t = blockIdx.x; t < ntiles && ok && !a.starve; t += gridDim.x) {
             const int y = t / tiles_x;
             const int xb = (t - y * tiles_x) * TM;
             for (int k = 0; k < 9; ++k) {
-                float2 dd[NPASS];
-                float msk[NPASS];
-                load_om(y, xb, k, dd, msk);
-                // the shuffles below need the whole warp: it leaves together
+                // The lane pair shares its sample records: lane c computes those of the
+                // passes h = 2i + c (offsets, mask, corner weights, position), and both
+                // lanes then read each pass's record from the lane that computed it.
+                // Record: row weights wy0, wy1 (times the mask), column weights wx0, wx1
+                // (each zero outside the image), and y0 * W + x0.
+                float2 cd2[NP2];
+                float clg[NP2];
+#pragma unroll
+                for (int i = 0; i < NP2; ++i) {
+                    cd2[i] = nd[i];
+                    clg[i] = nlg[i];
+                }
+                if (k < 8) load_om(t, k + 1, nd, nlg);
+                else if (t + (int)gridDim.x < ntiles) load_om(t + gridDim.x, 0, nd, nlg);
+                float ewy0[NP2], ewy1[NP2], ewx0[NP2], ewx1[NP2];
+                uint32_t eb[NP2];
+#pragma unroll
+                for (int i = 0; i < NP2; ++i) {
+                    const int px = xb + pb + (2 * i + c) * 16;
+                    const float2 d = cd2[i];
+                    const float lg = clg[i];
+                    const float m = a.mask_logits ? __frcp_rn(1.f + expf(-lg)) : lg;
+                    const float sy = (float)(y + k / 3 - 1) + d.x;
+                    const float sx = (float)(px + k % 3 - 1) + d.y;
+                    const float fy = floorf(sy), fx = floorf(sx);
+                    const int y0 = (int)fy, x0 = (int)fx;
+                    const float ly = sy - fy, lx = sx - fx;
+                    const bool in = px < W;
+                    ewy0[i] = in && (unsigned)y0 < (unsigned)H ? (1.f - ly) * m : 0.f;
+                    ewy1[i] = in && (unsigned)(y0 + 1) < (unsigned)H ? ly * m : 0.f;
+                    ewx0[i] = (unsigned)x0 < (unsigned)W ? 1.f - lx : 0.f;
+                    ewx1[i] = (unsigned)(x0 + 1) < (unsigned)W ? lx : 0.f;
+                    eb[i] = (uint32_t)y0 * (uint32_t)W + (uint32_t)x0;
+                }
+                // each pass's record from the lane that computed it, then its corner loads
+                // (every load of the tap is issued before the first blend)
+                float wy0[NPASS], wy1[NPASS], wxo[NPASS], wxp[NPASS];
+#pragma unroll
+                for (int h = 0; h < NPASS; ++h) {
+                    const int src = (lane & ~1) | (h & 1);
+                    wy0[h] = __shfl_sync(0xffffffffu, ewy0[h >> 1], src);
+                    wy1[h] = __shfl_sync(0xffffffffu, ewy1[h >> 1], src);
+                    const float x0w = __shfl_sync(0xffffffffu, ewx0[h >> 1], src);
+                    const float x1w = __shfl_sync(0xffffffffu, ewx1[h >> 1], src);
+                    const uint32_t bs = __shfl_sync(0xffffffffu, eb[h >> 1], src);
+                    wxo[h] = c ? x1w : x0w;  // weight of this lane's column x0 + c
+                    wxp[h] = c ? x0w : x1w;  // weight of the partner's column
+                    const uint32_t o0 = (bs + (uint32_t)c) * pstride;
+                    if (wy0[h] != 0.f && wxo[h] != 0.f) v[h][0] = __ldg(reinterpret_cast<const uint4 *>(plane + o0));
+                    if (wy1[h] != 0.f && wxo[h] != 0.f) v[h][1] = __ldg(reinterpret_cast<const uint4 *>(plane + (o0 + rowb)));
+                }
+                // the corner loads are in flight while the warp waits for a free stage; the
+                // shuffles below need the whole warp: it leaves together
                 const bool got = mbar_wait_bounded(&empty[s], ph ^ 1, abort, WAIT_NS);
                 if (!__all_sync(0xffffffffu, got)) {
                     *abort = 1;
@@ -194,69 +259,26 @@ __global__ void __launch_bounds__(NT, 1) dcn_tc_kernel(const DcnArgs a, int stag
                     break;
                 }
                 uint8_t *stg = stage0 + (size_t)s * STAGE + (size_t)cc * LBO + c * 8;
-                // every corner load of every pass first, then the blends
-                uint4 v[NPASS][2];
-                float fly[NPASS], flx[NPASS];  // fractional position
-                uint32_t rin = 0, cin_ = 0;    // bits 2h, 2h + 1: rows y0, y0 + 1 / columns x0, x0 + 1 inside
-                const float oy = (float)(y + k / 3 - 1), ox = (float)(xb + pb + k % 3 - 1);
 #pragma unroll
                 for (int h = 0; h < NPASS; ++h) {
-                    const float sy = oy + dd[h].x;
-                    const float sx = (ox + (float)(h * 16)) + dd[h].y;
-                    const float fy = floorf(sy), fx = floorf(sx);
-                    const int y0 = (int)fy, x0 = (int)fx;
-                    fly[h] = sy - fy;
-                    flx[h] = sx - fx;
-                    const bool py = xb + pb + h * 16 < W;
-                    const bool r0 = py && (unsigned)y0 < (unsigned)H, r1 = py && (unsigned)(y0 + 1) < (unsigned)H;
-                    const bool c0 = (unsigned)x0 < (unsigned)W, c1 = (unsigned)(x0 + 1) < (unsigned)W;
-                    rin |= ((uint32_t)r0 | ((uint32_t)r1 << 1)) << (2 * h);
-                    cin_ |= ((uint32_t)c0 | ((uint32_t)c1 << 1)) << (2 * h);
-                    const bool mc = c ? c1 : c0;
-                    // byte offsets of rows y0 and y0 + 1, each formed in full before it meets
-                    // the pointer (y0 may be -1, where only the second is used)
-                    const uint32_t o0 = (uint32_t)(y0 * W + x0 + c) * pstride;
-                    const uint32_t o1 = o0 + (uint32_t)W * pstride;
-                    v[h][0] = r0 && mc ? __ldg(reinterpret_cast<const uint4 *>(plane + o0)) : make_uint4(0u, 0u, 0u, 0u);
-                    v[h][1] = r1 && mc ? __ldg(reinterpret_cast<const uint4 *>(plane + o1)) : make_uint4(0u, 0u, 0u, 0u);
-                }
-                // mask sigmoids: both lanes of a pair need the same values, so lane c computes
-                // those of the passes h with h % 2 == c and the pair swaps them (the same
-                // arithmetic per value, half the instructions per lane)
-                static_assert(NPASS % 2 == 0, "passes shared by a lane pair");
-                float mine[NPASS / 2], theirs[NPASS / 2];
-#pragma unroll
-                for (int i = 0; i < NPASS / 2; ++i) {
-                    const float lg = c ? msk[2 * i + 1] : msk[2 * i];
-                    mine[i] = a.mask_logits ? __frcp_rn(1.f + expf(-lg)) : lg;
-                    theirs[i] = __shfl_xor_sync(0xffffffffu, mine[i], 1);
-                }
-#pragma unroll
-                for (int h = 0; h < NPASS; ++h) {
-                    // corner (r, col) weight = row factor x column factor, each zero outside the image
-                    const float wy[2] = {(rin >> (2 * h)) & 1u ? 1.f - fly[h] : 0.f, (rin >> (2 * h + 1)) & 1u ? fly[h] : 0.f};
-                    const float wx[2] = {(cin_ >> (2 * h)) & 1u ? 1.f - flx[h] : 0.f,
-                                         (cin_ >> (2 * h + 1)) & 1u ? flx[h] : 0.f};
-                    // row r: swap halves with the partner lane (lane 0 keeps channels 0-3, lane 1
-                    // channels 4-7), then add corners (r, 0) and (r, 1) in corner order, two
-                    // channels per packed FMA
+                    // lane 0 blends channels 0-3 and lane 1 channels 4-7: each keeps its half
+                    // of its own column x0 + c and takes the partner's half of column x0 + 1 - c
                     float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
-                        const uint4 o = v[h][r];
-                        const uint32_t g0 = __shfl_xor_sync(0xffffffffu, c ? o.x : o.z, 1);
-                        const uint32_t g1 = __shfl_xor_sync(0xffffffffu, c ? o.y : o.w, 1);
-                        const uint32_t a0 = c ? g0 : o.x, a1 = c ? g1 : o.y;  // column x0
-                        const uint32_t b0 = c ? o.z : g0, b1 = c ? o.w : g1;  // column x0 + 1
-                        const float wa = wy[r] * wx[0], wb = wy[r] * wx[1];
-                        ffma2(acc[0], wa, unpack_pair<T>(a0));
-                        ffma2(acc[1], wa, unpack_pair<T>(a1));
-                        ffma2(acc[0], wb, unpack_pair<T>(b0));
-                        ffma2(acc[1], wb, unpack_pair<T>(b1));
+                        const uint4 q = v[h][r];
+                        const uint32_t k0 = c ? q.z : q.x, k1 = c ? q.w : q.y;
+                        const uint32_t g0 = __shfl_xor_sync(0xffffffffu, c ? q.x : q.z, 1);
+                        const uint32_t g1 = __shfl_xor_sync(0xffffffffu, c ? q.y : q.w, 1);
+                        const float wr = r ? wy1[h] : wy0[h];
+                        const float wa = wr * wxo[h], wb = wr * wxp[h];
+                        ffma2(acc[0], wa, unpack_pair<T>(k0));
+                        ffma2(acc[1], wa, unpack_pair<T>(k1));
+                        ffma2(acc[0], wb, unpack_pair<T>(g0));
+                        ffma2(acc[1], wb, unpack_pair<T>(g1));
                     }
-                    const float mm = (h & 1) == c ? mine[h >> 1] : theirs[h >> 1];
                     *reinterpret_cast<uint2 *>(stg + (size_t)(pb + h * 16) * 16) =
-                        make_uint2(pack_pair<T>(acc[0].x * mm, acc[0].y * mm), pack_pair<T>(acc[1].x * mm, acc[1].y * mm));
+                        make_uint2(pack_pair<T>(acc[0].x, acc[0].y), pack_pair<T>(acc[1].x, acc[1].y));
                 }
                 fence_proxy_async();  // generic smem writes -> visible to the tensor core
                 mbar_arrive(&full[s]);
