@@ -72,12 +72,14 @@ RangeConst range_const(int bits, int range, int matrix, int yuv, int transfer) {
 
 // HDR transfer (SMPTE ST 2084 PQ, BT.2100 HLG), float32.  to_linear: coded R'G'B' value,
 // clamped to [0, 1] (where the functions are defined; the PQ EOTF has a pole above 1) ->
-// linear light; from_linear: linear light, clamped to [0, 1] -> coded value.
+// linear light; from_linear: linear light, clamped to [0, 1] -> coded value.  Not inlined:
+// each kernel calls them at many sites, and only HDR formats take that branch, so one
+// out-of-line copy keeps the common (SDR) code of the format kernels small.
 constexpr float PQ_M1 = 2610.f / 16384.f, PQ_M2 = 2523.f / 4096.f * 128.f;
 constexpr float PQ_C1 = 3424.f / 4096.f, PQ_C2 = 2413.f / 4096.f * 32.f, PQ_C3 = 2392.f / 4096.f * 32.f;
 constexpr float HLG_A = 0.17883277f, HLG_B = 1.f - 4.f * HLG_A, HLG_C = 0.55991073f;
 
-__device__ __forceinline__ float to_linear(int tf, float e) {
+__device__ __noinline__ float to_linear(int tf, float e) {
     if (tf == NVISR_TRANSFER_NONE) return e;
     e = fminf(fmaxf(e, 0.f), 1.f);
     if (tf == NVISR_TRANSFER_PQ) {
@@ -88,7 +90,7 @@ __device__ __forceinline__ float to_linear(int tf, float e) {
     return e;
 }
 
-__device__ __forceinline__ float from_linear(int tf, float l) {
+__device__ __noinline__ float from_linear(int tf, float l) {
     if (tf == NVISR_TRANSFER_PQ) {
         const float ym = powf(fminf(fmaxf(l, 0.f), 1.f), PQ_M1);
         return powf((PQ_C1 + PQ_C2 * ym) / (1.f + PQ_C3 * ym), PQ_M2);
@@ -347,11 +349,6 @@ __global__ void __launch_bounds__(128) ingest420_kernel(
             }
         }
     }
-}
-
-__device__ __forceinline__ float quant(float v, float vmax) {
-    v = rintf(v);  // round half to even
-    return fminf(fmaxf(v, 0.0f), vmax);
 }
 
 template <typename S>
