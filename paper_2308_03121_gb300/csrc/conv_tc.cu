@@ -1405,25 +1405,24 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                 }
                 if constexpr (PSB) {
                     // output pixel (2o + i, 2x + j) of the shuffled tensor (64 channels, one
-                    // 128-byte line), after the post-shuffle activation
-                    if (valid && w) {
-                        if (p.ps_act == 1) {
+                    // 128-byte line), after the post-shuffle activation: staged 128-byte
+                    // swizzled, and the group's row (every other pixel of output row 2o + i)
+                    // written by one TMA store with an element stride of 2
+                    if (p.ps_act == 1) {
 #pragma unroll
-                            for (int e = 0; e < 64; ++e) v[e] = lrelu(v[e]);
-                        }
-                        const int si = slice >> 1, sj = slice & 1;
-                        uint4 *yo = reinterpret_cast<uint4 *>(p.y) +
-                                    (((int64_t)img * 2 * p.H + 2 * o + si) * (2 * p.W) + 2 * x + sj) * 8;
-#pragma unroll
-                        for (int uu = 0; uu < 8; ++uu) {
-                            uint4 ov;
-                            ov.x = pack2<TO>(v[uu * 8 + 0], v[uu * 8 + 1]);
-                            ov.y = pack2<TO>(v[uu * 8 + 2], v[uu * 8 + 3]);
-                            ov.z = pack2<TO>(v[uu * 8 + 4], v[uu * 8 + 5]);
-                            ov.w = pack2<TO>(v[uu * 8 + 6], v[uu * 8 + 7]);
-                            yo[uu] = ov;
-                        }
+                        for (int e = 0; e < 64; ++e) v[e] = lrelu(v[e]);
                     }
+#pragma unroll
+                    for (int uu = 0; uu < 8; ++uu) {
+                        const int unit = uu ^ (m & 7);
+                        uint4 ov;
+                        ov.x = pack2<TO>(v[uu * 8 + 0], v[uu * 8 + 1]);
+                        ov.y = pack2<TO>(v[uu * 8 + 2], v[uu * 8 + 3]);
+                        ov.z = pack2<TO>(v[uu * 8 + 4], v[uu * 8 + 5]);
+                        ov.w = pack2<TO>(v[uu * 8 + 6], v[uu * 8 + 7]);
+                        *reinterpret_cast<uint4 *>(ot + unit * 16) = ov;
+                    }
+                    fence_proxy_async();  // staging writes before the async proxy
                 } else if constexpr (F32OUT) {
                     // this slice's 16 4-channel units of pixel (o, x), those inside cout_pad;
                     // a warp writes 512 contiguous bytes per unit
@@ -1454,6 +1453,12 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                 if (grp_stop[g]) {
                     ok = false;
                     break;
+                }
+                if (PSB && leader) {
+                    // pixels 2 x0 + j, 2 x0 + j + 2, ... of output row 2o + i; those past the
+                    // image's 2W columns are not written
+                    tma_store_4d(ymap_of(pi), obuf + g * TILEB, 0, 2 * x0 + (slice & 1), 2 * o + (slice >> 1), img);
+                    bulk_commit_group();
                 }
                 if (!F32OUT && !PSB && !p.no_main && leader) {
                     tma_store_4d(ymap_of(pi), obuf + g * TILEB, 0, x0, o, img);
@@ -1873,7 +1878,9 @@ inline int rows_stages(bool res, int *smem, int npr = 64, bool ps = false, int c
     const uint32_t ROWB = sw ? (((uint32_t)(cin / 64) * (TM + 2) * 128 + 1023u) & ~1023u)
                              : ((nchk * (TM + 2) * 16 + 1023u) & ~1023u);
     const uint32_t WB = sw ? 3 * 3 * (uint32_t)(cin / 64) * (uint32_t)npr * 128 : 3 * nchk * 3 * (uint32_t)npr * 16;
-    const uint32_t TILES = ps || f32out ? 0u : (res ? 4u : 2u) * TM * 128;
+    // staging tiles: 16-bit outputs written by TMA stores, including the 64-channel
+    // PixelShuffle slices (npr 64); the 16-channel shuffle tail stores directly
+    const uint32_t TILES = (ps && npr != 64) || f32out ? 0u : (res ? 4u : 2u) * TM * 128;
     int stages = (SMEM_LIMIT - 1024 - SMEM_HDR - (int)WB - (int)TILES - extra) / (int)ROWB;
     if (stages > 8) stages = 8;
     *smem = 1024 + SMEM_HDR + (int)WB + stages * (int)ROWB + (int)TILES + extra;
@@ -1911,7 +1918,7 @@ cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUte
 // 4-channel units; 64 -> 256 channels shuffled by PixelShuffle(2) into a
 // blocked 16-bit tensor.
 template <int IN_DT, int OUT_DT, int CBO, bool PS, int CIN>
-cudaError_t run_rows_sliced(const CUtensorMap &map, TcParams p, cudaStream_t st) {
+cudaError_t run_rows_sliced(const CUtensorMap &map, const CUtensorMap &ymap, TcParams p, cudaStream_t st) {
     int smem;
     p.stages = rows_stages(false, &smem, 64, PS, CIN, OUT_DT == DT_F32);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
@@ -1935,7 +1942,7 @@ cudaError_t run_rows_sliced(const CUtensorMap &map, TcParams p, cudaStream_t st)
     rp.bands = (p.H + rp.rps - 1) / rp.rps;
     const int strips = rp.xtiles * rp.bands * p.nimg;
     const int grid = std::min(ctas, strips) * p.nslice;
-    return launch_dependent(kern, grid, rows_threads(CIN, false), smem, st, map, map, map, p, rp, nullptr, 0);
+    return launch_dependent(kern, grid, rows_threads(CIN, false), smem, st, map, ymap, map, p, rp, nullptr, 0);
 }
 
 template <int IN_DT, int OUT_DT, int CBO>
@@ -2150,8 +2157,8 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
         p.cout_pad = a.cout_pad;
         p.nslice = (a.cout_pad + 63) / 64;
         p.wbytes = (uint32_t)tc_rows128_weight_bytes(1);
-        return dt == DT_BF16 ? run_rows_sliced<DT_BF16, DT_F32, 16, false, 128>(map, p, st)
-                             : run_rows_sliced<DT_F16, DT_F32, 16, false, 128>(map, p, st);
+        return dt == DT_BF16 ? run_rows_sliced<DT_BF16, DT_F32, 16, false, 128>(map, map, p, st)
+                             : run_rows_sliced<DT_F16, DT_F32, 16, false, 128>(map, map, p, st);
     }
     if (rows_f8_fits(a)) {
         auto enc = encode_fn();
@@ -2183,17 +2190,31 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
     }
     if (rows_psb_fits(a)) {
         ConvArgs b = a;
-        b.y = const_cast<void *>(a.x);  // the shuffle epilogue stores directly; the y / residual maps are unused
+        b.y = const_cast<void *>(a.x);  // the residual map is unused
         CUtensorMap map, ymap, rmap;
         cudaError_t e = encode_row_maps(b, &map, &ymap, &rmap);
         if (e != cudaSuccess) return e;
+        // y: the shuffled 2H x 2W tensor of 128-byte pixel lines; a store box covers 128
+        // pixels at a stride of 2 (one slice's pixels of one output row)
+        auto enc = encode_fn();
+        if (!enc) return cudaErrorNotSupported;
+        {
+            cuuint64_t dims[4] = {128, (cuuint64_t)(2 * a.W), (cuuint64_t)(2 * a.H), (cuuint64_t)a.nimg};
+            cuuint64_t strides[3] = {128, (cuuint64_t)(2 * a.W) * 128, (cuuint64_t)(2 * a.W) * (2 * a.H) * 128};
+            cuuint32_t box[4] = {128, (cuuint32_t)(2 * TM), 1, 1};
+            cuuint32_t estr[4] = {1, 2, 1, 1};
+            if (enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, a.y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return cudaErrorInvalidValue;
+        }
         TcParams p = rows_params(a);
         p.cout = a.cout;
         p.cout_pad = a.cout_pad;
         p.nslice = 4;
         p.ps_act = a.ps_act;
-        return dt == DT_BF16 ? run_rows_sliced<DT_BF16, DT_BF16, 128, true, 64>(map, p, st)
-                             : run_rows_sliced<DT_F16, DT_F16, 128, true, 64>(map, p, st);
+        return dt == DT_BF16 ? run_rows_sliced<DT_BF16, DT_BF16, 128, true, 64>(map, ymap, p, st)
+                             : run_rows_sliced<DT_F16, DT_F16, 128, true, 64>(map, ymap, p, st);
     }
     if (rows_ps_fits(a)) {
         ConvArgs b = a;
