@@ -523,25 +523,35 @@ __device__ __forceinline__ float rq_skip_general(const FusedRq &rq, int c, int Y
     return rq_bilerp(__ldg(r0 + x0), __ldg(r0 + x1), __ldg(r1 + x0), __ldg(r1 + x1), lx, ly);
 }
 
+// The skip frame's 3 x 3 neighbourhood of pixel (o, x) per channel (rows o - 1 .. o + 1,
+// columns x - 1 .. x + 1, clamped to the frame): the samples the 4:2:0 2x form of
+// rq_pixel blends.  Loaded ahead of the row's accumulator, so that their latency
+// overlaps the wait for it.
+__device__ __forceinline__ void rq_skip_load(const FusedRq &rq, int o, int x, int H, int W, float (&lr)[3][3][3]) {
+    const int rows[3] = {max(o - 1, 0), o, min(o + 1, H - 1)};
+    const int cols[3] = {max(x - 1, 0), x, min(x + 1, W - 1)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr) {
+            const float *row = rq.skip + (int64_t)c * rq.skip_plane + (int64_t)rows[rr] * rq.skip_pitch;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) lr[c][rr][cc] = __ldg(row + cols[cc]);
+        }
+}
+
 // Output samples (residual v[4c + 2dy + dx] + skip) -> luma codes yq[dy][dx], full-resolution
-// chroma cb[dy][dx], cr[dy][dx] (before downsampling and rounding).
+// chroma cb[dy][dx], cr[dy][dx] (before downsampling and rounding).  lr: the neighbourhood
+// rq_skip_load read, for a 4:2:0 skip.
 __device__ __forceinline__ void rq_pixel(const FusedRq &rq, const float *v, int o, int x, int H, int W,
-                                         float (&yq)[2][2], float (&cb)[2][2], float (&cr)[2][2]) {
+                                         const float (&lr)[3][3][3], float (&yq)[2][2], float (&cb)[2][2],
+                                         float (&cr)[2][2]) {
     float smp[3][2][2];
     if (rq.skip && rq.sub420) {
         // requant420's 2x form: rows (o-1, o) with (1/4, 3/4) for dy = 0 and (o, o+1) with
         // (3/4, 1/4) for dy = 1; columns likewise, all clamped to the frame
-        const int rows[3] = {max(o - 1, 0), o, min(o + 1, H - 1)};
-        const int cols[3] = {max(x - 1, 0), x, min(x + 1, W - 1)};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float lr[3][3];
-#pragma unroll
-            for (int rr = 0; rr < 3; ++rr) {
-                const float *row = rq.skip + (int64_t)c * rq.skip_plane + (int64_t)rows[rr] * rq.skip_pitch;
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) lr[rr][cc] = __ldg(row + cols[cc]);
-            }
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -549,8 +559,8 @@ __device__ __forceinline__ void rq_pixel(const FusedRq &rq, const float *v, int 
                     const int c0 = dx;
                     const float wl = dx ? 0.75f : 0.25f, wr = dx ? 0.25f : 0.75f;
                     const float wt = dy ? 0.75f : 0.25f, wb = dy ? 0.25f : 0.75f;
-                    const float top = rq_blend(lr[dy][c0], wl, lr[dy][c0 + 1], wr);
-                    const float bot = rq_blend(lr[dy + 1][c0], wl, lr[dy + 1][c0 + 1], wr);
+                    const float top = rq_blend(lr[c][dy][c0], wl, lr[c][dy][c0 + 1], wr);
+                    const float bot = rq_blend(lr[c][dy + 1][c0], wl, lr[c][dy + 1][c0 + 1], wr);
                     smp[c][dy][dx] = __fadd_rn(v[4 * c + 2 * dy + dx], rq_blend(top, wt, bot, wb));
                 }
         }
@@ -1168,6 +1178,13 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                 const int slot = i % NSLOT;
                 const int k = i >> 1;  // this group's row count (phase of its residual barrier)
                 if (leader) bulk_wait_group_read<0>();  // the group's previous store finished reading
+                // a fused requantise's 4:2:0 skip neighbourhood, loaded before the row's wait
+                float lr[3][3][3];
+                if constexpr (PS && !PSB)
+                    if (p.rq.on && p.rq.skip && p.rq.sub420) {
+                        const int Wl = width_of(pi);
+                        rq_skip_load(p.rq, o, min(x, Wl - 1), p.H, Wl, lr);
+                    }
                 named_barrier(bar_id, NGRP);
                 bool w = mbar_wait_bounded(&rowdone[slot], (uint32_t)((i / NSLOT) & 1), abort, WAIT_NS);
                 w = __all_sync(0xffffffffu, w);
@@ -1203,7 +1220,7 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                         const FusedRq &rq = p.rq;
                         const int Wl = width_of(pi), xc = min(x, Wl - 1);
                         float yq[2][2], cb[2][2], cr[2][2];
-                        rq_pixel(rq, v, o, xc, p.H, Wl, yq, cb, cr);
+                        rq_pixel(rq, v, o, xc, p.H, Wl, lr, yq, cb, cr);
                         const bool st = valid && w;
                         if (st)
 #pragma unroll
