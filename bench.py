@@ -14,7 +14,7 @@ no L2 flush is needed between steps.
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead (the reference arm: there is no reference implementation to run).
 Secondary workloads report under their own keys: ``batched`` (24 streams),
-``config3`` (deformable space-time SR), ``pyramid`` (the same with a
+``stvsr4x`` (deformable space-time SR), ``pyramid`` (the same with a
 three-level feature-pyramid extract stage), ``modes`` (same-size and
 vertical-2x scale modes) and ``serving``.
 """
@@ -161,7 +161,7 @@ def measure(nv, prec, steps, warmup, dev_frames, local, world, clocks=None, prof
     """Device-timed push/pull loop of one precision.  With profile, per-kernel CUDA
     events are recorded as well (a separate pass: the headline is timed without them)."""
     import torch
-    text, blob = synth.net_config2()
+    text, blob = synth.net_sr2x_t5()
     eng = nv.Engine(device=local)
     flt = eng.filter(text, blob, nv.fmt(W, H, 10), nv.fmt(W * S, H * S, 10), prec, S)
     out = (torch.empty((H * S, W * S), dtype=torch.int16, device=f"cuda:{local}"),
@@ -223,7 +223,7 @@ def measure(nv, prec, steps, warmup, dev_frames, local, world, clocks=None, prof
 def measure_modes(nv, steps, warmup, dev_frames, local):
     """The scale modes besides 2 x 2 SR (Section 3.2's horizontal and vertical scale): a
     same-size enhancement (denoise, 1 x 1) and a vertical 2x (deinterlace, 1 x 2) network
-    with the config-2 trunk (T=5, 15->64, 10 residual blocks of 64), BF16, on the 1080p
+    with the 1080p 2x SR network's trunk (T=5, 15->64, 10 residual blocks of 64), BF16, on the 1080p
     10-bit 4:2:0 frames; device-resident input and output, CUDA events on the engine
     stream around the timed push/pull loop."""
     import torch
@@ -271,7 +271,7 @@ def measure_modes(nv, steps, warmup, dev_frames, local):
     return res
 
 
-def measure_config3(nv, steps, warmup, local, prec="bf16", pyramid=False):
+def measure_stvsr(nv, steps, warmup, local, prec="bf16", pyramid=False):
     """Spatio-temporal SR with deformable alignment: 960x540 8-bit 4:2:0, two
     input frames -> two 3840x2160 outputs per run (the frame and the midpoint),
     BF16, device-resident input.  Reports output Mpix/s and the DCN kernel's
@@ -280,7 +280,7 @@ def measure_config3(nv, steps, warmup, local, prec="bf16", pyramid=False):
     aligned at every level (its extract features are cached per frame)."""
     import torch
     w, h = 960, 540
-    text, blob = synth.net_group_pyramid(synth.BASE_SEED + 3) if pyramid else synth.net_config3()
+    text, blob = synth.net_group_pyramid(synth.BASE_SEED + 3) if pyramid else synth.net_stvsr4x()
     frs = synth.frames_textured(synth.BASE_SEED + 3, 4, w, h, 8, "420", "limited")
     dev = f"cuda:{local}"
     frames = [tuple(torch.from_numpy(np.ascontiguousarray(f[c])).to(dev) for c in "YUV") for f in frs]
@@ -344,7 +344,7 @@ def measure_batched(nv, steps, warmup, local):
     against the per-stream sequential engine step, both with device-resident
     input planes and device outputs.  Scene cuts: geometric gaps, p = 1/40."""
     import torch
-    text, blob = synth.net_config2()
+    text, blob = synth.net_sr2x_t5()
     dev = f"cuda:{local}"
     clips = {}
     for key in set(BATCH_STREAMS):
@@ -402,7 +402,7 @@ def measure_batched(nv, steps, warmup, local):
     dt_s, _ = run(False)
     vb = steps * BATCH_OUT_PIX / dt_b / 1e6
     vs = steps * BATCH_OUT_PIX / dt_s / 1e6
-    return {"workload": "24 streams, config-2 network BF16: 8x 854x480 8-bit 4:2:0, 8x 1280x720 10-bit 4:2:0, "
+    return {"workload": "24 streams, the 2x SR network (T=5, 10 residual blocks of 64) BF16: 8x 854x480 8-bit 4:2:0, 8x 1280x720 10-bit 4:2:0, "
                         "8x 1920x1080 8-bit 4:4:4; one output per stream per step; scene cuts p=1/40",
             "metric": "output Mpix/s", "value": vb, "sequential_value": vs, "speedup": vb / vs,
             "ms_per_step": dt_b / steps * 1e3, "sequential_ms_per_step": dt_s / steps * 1e3, "steps": steps,
@@ -425,7 +425,7 @@ def measure_serving(nv, seconds, rate, budget_gb, local, seed=synth.BASE_SEED + 
     count with the outputs they produced."""
     import torch
     rng = np.random.default_rng(seed)
-    nets = {"c2": (synth.net_config2(), 2), "c3": (synth.net_config3(), 4)}
+    nets = {"sr2x": (synth.net_sr2x_t5(), 2), "stvsr": (synth.net_stvsr4x(), 4)}
     frames = {}
     outbuf = {}
     eng = nv.Engine(device=local, hbm_budget_bytes=int(budget_gb * 2 ** 30))
@@ -442,7 +442,7 @@ def measure_serving(nv, seconds, rate, budget_gb, local, seed=synth.BASE_SEED + 
         while next_arrival <= now:
             w, h = SERVE_RES[rng.integers(len(SERVE_RES))]
             bits = 8 if rng.uniform() < 0.5 else 10
-            net = "c2" if rng.uniform() < 0.5 else "c3"
+            net = "sr2x" if rng.uniform() < 0.5 else "stvsr"
             n = int(round(np.exp(rng.uniform(np.log(30), np.log(600)))))
             (text, blob), sc = nets[net]
             key = (w, h, bits)
@@ -499,7 +499,7 @@ def measure_serving(nv, seconds, rate, budget_gb, local, seed=synth.BASE_SEED + 
 def measure_e2e(nv, prec, steps, pinned, local):
     """Host planes in, host planes out, through nvisr_push / nvisr_pull (copies inside)."""
     import torch
-    text, blob = synth.net_config2()
+    text, blob = synth.net_sr2x_t5()
     eng = nv.Engine(device=local)
     flt = eng.filter(text, blob, nv.fmt(W, H, 10), nv.fmt(W * S, H * S, 10), prec, S)
     out = (torch.empty((H * S, W * S), dtype=torch.int16).pin_memory(),
@@ -540,7 +540,7 @@ def oracle_sample(side_w, side_h, seed=synth.BASE_SEED + 2):
     import oracle
     frames = synth.frames_textured(seed, 5, side_w, side_h, 10, "420", "limited")
     flags = np.zeros(5, bool)
-    text, blob = synth.net_config2()
+    text, blob = synth.net_sr2x_t5()
     fd = dict(bit_depth=10, subsampling="420", range="limited", chroma_loc="left")
     t = time.perf_counter()
     oracle.run_filter(frames, flags, text, blob, fd, fd, outputs=[2])
@@ -586,7 +586,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=12, help="steps of the 24-stream batched run (0 = skip)")
-    ap.add_argument("--config3-steps", type=int, default=20, help="runs of the deformable ST-SR network (0 = skip)")
+    ap.add_argument("--stvsr-steps", type=int, default=20, help="runs of the deformable ST-SR network (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving-loop window (0 = skip)")
     ap.add_argument("--modes-steps", type=int, default=30, help="frames of each 1x1 / 1x2 scale mode (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=6.0, help="clip arrivals per second")
@@ -634,14 +634,14 @@ def main():
     achieved_gbs = convs / 2 * BLOCK_BYTES / (avg_body * 1e-3) / 1e9
     launches = round(sum(n for _, n in prof.values()) * r["steps"] / r["psteps"])
     e2e_total, p50, p99 = measure_e2e(nv, head, args.e2e_steps, pinned, local)
-    config3 = pyramid = None
-    if args.config3_steps > 0:
+    stvsr = pyramid = None
+    if args.stvsr_steps > 0:
         try:
-            config3 = measure_config3(nv, args.config3_steps, 3, local)
+            stvsr = measure_stvsr(nv, args.stvsr_steps, 3, local)
         except Exception as e:  # the secondary workload must not hide the headline
-            errors["config3"] = repr(e)
+            errors["stvsr4x"] = repr(e)
         try:
-            pyramid = measure_config3(nv, args.config3_steps, 3, local, pyramid=True)
+            pyramid = measure_stvsr(nv, args.stvsr_steps, 3, local, pyramid=True)
         except Exception as e:  # the secondary workload must not hide the headline
             errors["pyramid"] = repr(e)
     modes = None
@@ -707,7 +707,7 @@ def main():
         "clocks": r["clocks"],
         "precisions": by_prec,
         "batched": batched,
-        "config3": config3,
+        "stvsr4x": stvsr,
         "pyramid": pyramid,
         "modes": modes,
         "serving": serving,

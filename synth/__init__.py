@@ -280,12 +280,12 @@ def net_tuple(seed: int, frames: int, channels: int, nres: int, scale=2,
     return spec.build()
 
 
-def net_config1(seed: int = BASE_SEED + 1):
+def net_sr2x_t3(seed: int = BASE_SEED + 1):
     """9->32, 4 residual blocks of 32, 32->12, PixelShuffle(2), bilinear skip (T=3)."""
     return net_tuple(seed, frames=3, channels=32, nres=4, scale=2, skip="bilinear")
 
 
-def net_config2(seed: int = BASE_SEED + 2, skip: str = "bilinear"):
+def net_sr2x_t5(seed: int = BASE_SEED + 2, skip: str = "bilinear"):
     """15->64, 10 residual blocks of 64, 64->12, PixelShuffle(2) (T=5)."""
     return net_tuple(seed, frames=5, channels=64, nres=10, scale=2, skip=skip)
 
@@ -334,7 +334,7 @@ def net_group_stvsr(seed: int, channels: int = 64, groups: int = 8, nres: int = 
     return spec.build()
 
 
-def net_config3(seed: int = BASE_SEED + 3):
+def net_stvsr4x(seed: int = BASE_SEED + 3):
     return net_group_stvsr(seed)
 
 

@@ -43,7 +43,7 @@ def test_tuple_map_matches_oracle(T):
         assert np.array_equal(got, exp)
 
 
-def test_tuple_map_config1_cut_on_frame_9():
+def test_tuple_map_t3_cut_on_frame_9():
     flags = np.zeros(16, bool)
     flags[9] = True
     got = nv.nvisr_tuple_map(flags, 3)
@@ -86,8 +86,8 @@ def test_fig1_layout_matches_oracle(n, b):
     assert tuple(copy.tolist()) == oracle.fig1_next_batch_copy(n, b, rolling=False)
 
 
-def test_network_check_accepts_configs():
-    for text, blob in (synth.net_config1(), synth.net_config2(), synth.net_config3()):
+def test_network_check_accepts_the_workload_networks():
+    for text, blob in (synth.net_sr2x_t3(), synth.net_sr2x_t5(), synth.net_stvsr4x()):
         st, msg = nv.nvisr_network_check(text, blob.size)
         assert st == 0, msg
 
@@ -100,7 +100,7 @@ def test_network_check_accepts_configs():
     (lambda t: t + "bogus line\n", "unknown statement"),
 ])
 def test_network_check_rejects_malformed(mutate, needle):
-    text, blob = synth.net_config1()
+    text, blob = synth.net_sr2x_t3()
     st, msg = nv.nvisr_network_check(mutate(text), blob.size)
     assert st == nv.Status.BAD_NETWORK and needle in msg
 
@@ -123,6 +123,6 @@ def test_network_check_rejects_bad_shuffle_factors(attr, needle):
 
 
 def test_network_check_rejects_blob_size():
-    text, blob = synth.net_config1()
+    text, blob = synth.net_sr2x_t3()
     st, msg = nv.nvisr_network_check(text, blob.size + 1)
     assert st == nv.Status.BAD_NETWORK and "weight blob" in msg

@@ -1,4 +1,4 @@
-"""Accuracy of the reduced-precision paths on the config-2 network (ragged 136x70
+"""Accuracy of the reduced-precision paths on the 2x SR network (T=5, 10 residual blocks of 64; ragged 136x70
 clip with a scene cut): codes identical to the FP32 GPU path, max LSB and PSNR
 against the FP64 oracle.
 
@@ -62,7 +62,7 @@ def test_precision_report():
     frames = synth.frames_textured(synth.BASE_SEED + 2, 6, W, H, 10, "420", "limited")
     flags = np.zeros(6, bool)
     flags[3] = True
-    text, blob = synth.net_config2()
+    text, blob = synth.net_sr2x_t5()
     ref = oracle.run_filter(frames, flags, text, blob, fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10))
     outs = {p: _run(text, blob, frames, flags, W, H, p) for p in ("fp32", "bf16", "fp16", "fp8")}
     for prec in ("fp32", "bf16", "fp16", "fp8"):

@@ -105,7 +105,7 @@ def _batched(text, blob, clips, precs):
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_batch_equals_each_stream_alone(prec):
-    text, blob = synth.net_config2()
+    text, blob = synth.net_sr2x_t5()
     clips = [(_frames(k, W, H, bits, sub, n), cut) for k, (W, H, bits, sub, n, cut) in enumerate(STREAMS)]
     got, info = _batched(text, blob, clips, [prec] * len(STREAMS))
     assert info["shared"] and info["graphs"] >= 1 and info["rows_per_strip"] > 0, info
@@ -118,7 +118,7 @@ def test_batch_equals_each_stream_alone(prec):
 
 
 def test_mixed_precision_batch_steps_members_one_by_one():
-    text, blob = synth.net_config2()
+    text, blob = synth.net_sr2x_t5()
     clips = [(_frames(k, W, H, bits, sub, n), cut) for k, (W, H, bits, sub, n, cut) in enumerate(STREAMS)]
     precs = ["bf16", "fp32", "bf16", "bf16"]
     got, info = _batched(text, blob, clips, precs)

@@ -59,7 +59,7 @@ def run_gpu(text, blob, frames, flags, fin, fout, prec, scale=2, device_io=False
     return outs, infos
 
 
-def _config1():
+def _clip64_t3():
     frames = synth.frames_gradient(synth.BASE_SEED + 1, 16, 64, 64, 8, "420", "full")
     flags = np.zeros(16, bool)
     flags[9] = True
@@ -69,23 +69,23 @@ def _config1():
 
 
 @pytest.fixture(scope="module")
-def config1_oracle():
-    frames, flags, fdi, fdo = _config1()
-    text, blob = synth.net_config1()
+def clip64_oracle():
+    frames, flags, fdi, fdo = _clip64_t3()
+    text, blob = synth.net_sr2x_t3()
     flt = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
     return [prequant(o, fdo) for o in flt]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
-def test_config1_filter_within_1lsb(prec, config1_oracle):
-    frames, flags, fdi, fdo = _config1()
-    text, blob = synth.net_config1()
+def test_sr2x_t3_filter_within_1lsb(prec, clip64_oracle):
+    frames, flags, fdi, fdo = _clip64_t3()
+    text, blob = synth.net_sr2x_t3()
     outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(64, 64, 8, "420", "full"),
                           nv.fmt(128, 128, 8, "420", "full"), prec)
     assert len(outs) == 16
     assert [i[0] for i in infos] == list(range(16))
     assert infos[8][1:3] == (7, 8) and infos[9][1:3] == (9, 10)    # scene cut on frame 9
-    for got, pq in zip(outs, config1_oracle):
+    for got, pq in zip(outs, clip64_oracle):
         if prec == "fp32":
             assert_codes_match(got, pq, 8)
         else:
@@ -94,9 +94,9 @@ def test_config1_filter_within_1lsb(prec, config1_oracle):
             assert mx <= 1, mx
 
 
-def test_config1_device_io_matches_host_io():
-    frames, flags, _, _ = _config1()
-    text, blob = synth.net_config1()
+def test_sr2x_t3_device_io_matches_host_io():
+    frames, flags, _, _ = _clip64_t3()
+    text, blob = synth.net_sr2x_t3()
     fi, fo = nv.fmt(64, 64, 8, "420", "full"), nv.fmt(128, 128, 8, "420", "full")
     a, _ = run_gpu(text, blob, frames, flags, fi, fo, "bf16")
     b, _ = run_gpu(text, blob, frames, flags, fi, fo, "bf16", device_io=True)
@@ -107,8 +107,8 @@ def test_config1_device_io_matches_host_io():
 
 def test_scene_cut_poisoning_on_gpu():
     """Frames outside an output's scene never change it (bit-identical)."""
-    frames, flags, _, _ = _config1()
-    text, blob = synth.net_config1()
+    frames, flags, _, _ = _clip64_t3()
+    text, blob = synth.net_sr2x_t3()
     fi, fo = nv.fmt(64, 64, 8, "420", "full"), nv.fmt(128, 128, 8, "420", "full")
     base, _ = run_gpu(text, blob, frames, flags, fi, fo, "bf16")
     poisoned = [dict(f) for f in frames]
@@ -120,7 +120,7 @@ def test_scene_cut_poisoning_on_gpu():
             assert np.array_equal(base[t][k], pz[t][k]), (t, k)
 
 
-def _config2_small(W=136, H=70, n=6):
+def _clip_sr2x_t5_small(W=136, H=70, n=6):
     frames = synth.frames_textured(synth.BASE_SEED + 2, n, W, H, 10, "420", "limited")
     flags = np.zeros(n, bool)
     flags[3] = True
@@ -128,11 +128,11 @@ def _config2_small(W=136, H=70, n=6):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_config2_network_ragged_size_full_frames(prec):
-    """Config-2 network at 136x70 (ragged 128-pixel tiles, a cut on frame 3), every output."""
+def test_sr2x_t5_network_ragged_size_full_frames(prec):
+    """The 2x SR network (T=5, 10 residual blocks of 64) at 136x70 (ragged 128-pixel tiles, a cut on frame 3), every output."""
     W, H = 136, 70
-    frames, flags = _config2_small(W, H)
-    text, blob = synth.net_config2()
+    frames, flags = _clip_sr2x_t5_small(W, H)
+    text, blob = synth.net_sr2x_t5()
     fdi, fdo = fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10)
     ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
     outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 10), nv.fmt(2 * W, 2 * H, 10), prec)
@@ -151,12 +151,12 @@ FULL_WINDOWS = [(0, 16, 0, 16), (0, 16, 1904, 1920), (1064, 1080, 960, 976), (54
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_config2_full_size_sampled_windows(prec):
+def test_sr2x_t5_1080p_sampled_windows(prec):
     """1920x1080 10-bit, T = 5: outputs 0 (scene start, edge replication) and 3 on sampled windows."""
     W, H = 1920, 1080
     frames = synth.frames_textured(synth.BASE_SEED + 2, 6, W, H, 10, "420", "limited")
     flags = np.zeros(6, bool)
-    text, blob = synth.net_config2()
+    text, blob = synth.net_sr2x_t5()
     outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 10), nv.fmt(2 * W, 2 * H, 10), prec, limit=4)
     fdi, fdo = fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10)
     net = oracle.Net(text, blob)
@@ -233,7 +233,7 @@ def test_pyramid_extract_network_matches_oracle(prec):
             assert mx <= 1, mx
 
 
-@pytest.mark.parametrize("net", ["pyramid", "config3"])
+@pytest.mark.parametrize("net", ["pyramid", "stvsr4x"])
 def test_extract_cache_reuses_each_frames_features(net):
     """The extract stage's features of a frame are computed once and reused by the next run
     that takes the frame: 6 frames, a cut before frame 3, runs (0,1) (1,2) (2,2) (3,4) (4,5)
@@ -244,7 +244,7 @@ def test_extract_cache_reuses_each_frames_features(net):
     flags = np.zeros(N, bool)
     flags[3] = True
     text, blob = (synth.net_group_pyramid(synth.BASE_SEED + 81, nres=1) if net == "pyramid"
-                  else synth.net_config3())
+                  else synth.net_stvsr4x())
     eng = nv.Engine()
     flt = eng.filter(text, blob, nv.fmt(W, H, 8), nv.fmt(4 * W, 4 * H, 8), "bf16", 4)
     for i, fr in enumerate(frames):
@@ -263,13 +263,13 @@ def test_extract_cache_reuses_each_frames_features(net):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
-def test_config3_full_size_sampled_windows(prec):
+def test_stvsr4x_540p_sampled_windows(prec):
     """960x540 8-bit, the deformable ST-SR network in the bench's launch shapes: both outputs
     of the first run on sampled windows (corners, the ragged last column tile, interior)."""
     W, H = 960, 540
     frames = synth.frames_textured(synth.BASE_SEED + 3, 2, W, H, 8, "420", "limited")
     flags = np.zeros(2, bool)
-    text, blob = synth.net_config3()
+    text, blob = synth.net_stvsr4x()
     outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(4 * W, 4 * H, 8), prec, scale=4,
                       limit=2)
     fdi, fdo = fmt_dict(W, H, 8), fmt_dict(4 * W, 4 * H, 8)
@@ -287,11 +287,11 @@ def test_config3_full_size_sampled_windows(prec):
 
 
 def test_fp8_filter_reports_error_vs_oracle():
-    """FP8 E4M3 (per-tensor scales from frames 0-3) on the ragged config-2 case: within the
+    """FP8 E4M3 (per-tensor scales from frames 0-3) on the ragged 136x70 case of the 2x SR network: within the
     2 LSB it measures (the 1 LSB target is not met by FP8; see test_gpu_accuracy)."""
     W, H = 136, 70
-    frames, flags = _config2_small(W, H)
-    text, blob = synth.net_config2()
+    frames, flags = _clip_sr2x_t5_small(W, H)
+    text, blob = synth.net_sr2x_t5()
     fdi, fdo = fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10)
     ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo)
     outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 10), nv.fmt(2 * W, 2 * H, 10), "fp8")
@@ -304,8 +304,8 @@ def test_fp8_filter_reports_error_vs_oracle():
 
 
 def test_backpressure_full_then_pull():
-    frames, flags, _, _ = _config1()
-    text, blob = synth.net_config1()
+    frames, flags, _, _ = _clip64_t3()
+    text, blob = synth.net_sr2x_t3()
     eng = nv.Engine()
     flt = eng.filter(text, blob, nv.fmt(64, 64, 8, "420", "full"), nv.fmt(128, 128, 8, "420", "full"), "fp32")
     n = 0
@@ -325,7 +325,7 @@ def test_backpressure_full_then_pull():
 
 
 def test_budget_rejects_filter():
-    text, blob = synth.net_config1()
+    text, blob = synth.net_sr2x_t3()
     eng = nv.Engine(hbm_budget_bytes=1 << 20)
     with pytest.raises(nv.NvisrError) as e:
         eng.filter(text, blob, nv.fmt(64, 64, 8, "420", "full"), nv.fmt(128, 128, 8, "420", "full"), "bf16")
@@ -334,7 +334,7 @@ def test_budget_rejects_filter():
     eng.close()
 
 
-def _config3_small(W=144, H=72, n=4):
+def _clip_stvsr_small(W=144, H=72, n=4):
     frames = synth.frames_textured(synth.BASE_SEED + 3, n, W, H, 8, "420", "limited")
     flags = np.zeros(n, bool)
     flags[2] = True
@@ -342,34 +342,34 @@ def _config3_small(W=144, H=72, n=4):
 
 
 @pytest.fixture(scope="module")
-def config3_oracle():
+def stvsr_oracle():
     W, H = 144, 72
-    frames, flags = _config3_small(W, H)
-    text, blob = synth.net_config3()
+    frames, flags = _clip_stvsr_small(W, H)
+    text, blob = synth.net_stvsr4x()
     fdi, fdo = fmt_dict(W, H, 8), fmt_dict(4 * W, 4 * H, 8)
     outs = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
     return [prequant(o, fdo) for o in outs]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
-def test_config3_stvsr_dcn_filter(prec, config3_oracle):
+def test_stvsr4x_dcn_filter(prec, stvsr_oracle):
     """Two-frame ST-VSR with deformable alignment, 4x space, 2x frame rate, a cut on frame 2:
     2 outputs per input (SR of frame i, midpoint i+1/2), the scene's last pair (s1, s1)."""
     W, H = 144, 72
-    frames, flags = _config3_small(W, H)
-    text, blob = synth.net_config3()
+    frames, flags = _clip_stvsr_small(W, H)
+    text, blob = synth.net_stvsr4x()
     outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 8), nv.fmt(4 * W, 4 * H, 8), prec, scale=4)
     assert len(outs) == 2 * len(frames)
     assert [i[0] for i in infos] == list(range(8))
     assert [i[1:3] for i in infos] == [(0, 1), (0, 1), (1, 1), (1, 1), (2, 3), (2, 3), (3, 3), (3, 3)]
     worst = 0
-    for got, pq in zip(outs, config3_oracle):
+    for got, pq in zip(outs, stvsr_oracle):
         if prec == "fp32":
             assert_codes_match(got, pq, 8)
         else:
             mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 8) for k in "YUV"})
             worst = max(worst, mx)
-    print(prec, "config-3 max LSB vs oracle:", worst)
+    print(prec, "space-time SR max LSB vs oracle:", worst)
     assert worst <= 1
 
 
@@ -460,13 +460,13 @@ def test_last_error_is_kept_per_engine():
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_filter_bt2020_12bit(prec):
-    """The whole filter on 12-bit BT.2020 4:2:0 in and out (config-1 network, a cut on frame 5)."""
+    """The whole filter on 12-bit BT.2020 4:2:0 in and out (the 3-frame 32-channel 2x network, a cut on frame 5)."""
     frames = synth.frames_textured(synth.BASE_SEED + 71, 8, 64, 48, 12, "420", "limited")
     flags = np.zeros(8, bool)
     flags[5] = True
     fdi = fmt_dict(64, 48, 12, "420", "limited", "left", "bt2020")
     fdo = fmt_dict(128, 96, 12, "420", "limited", "left", "bt2020")
-    text, blob = synth.net_config1()
+    text, blob = synth.net_sr2x_t3()
     ref = [prequant(o, fdo) for o in oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)]
     outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(64, 48, 12, "420", "limited", "left", "bt2020"),
                       nv.fmt(128, 96, 12, "420", "limited", "left", "bt2020"), prec)
@@ -482,7 +482,7 @@ def test_filter_bt2020_12bit(prec):
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_filter_yuv_domain_network(prec):
     """A network that works on Y'Cb'Cr' (Section 3.1): ingest and requantise skip the colour
-    matrix; 10-bit 4:2:0 in and out, config-1 shapes, a cut on frame 4."""
+    matrix; 10-bit 4:2:0 in and out, the 3-frame 32-channel 2x network, a cut on frame 4."""
     frames = synth.frames_textured(synth.BASE_SEED + 72, 7, 64, 48, 10, "420", "limited")
     flags = np.zeros(7, bool)
     flags[4] = True
@@ -532,13 +532,13 @@ def test_filter_separate_scales(sx, sy, prec):
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_filter_rgb_planes(prec):
     """RGB planes in and out (Section 3.1: RGB or YUV I/O): 8-bit full-range 4:4:4 R, G, B,
-    config-1 network (2x), a cut on frame 4."""
+    3-frame 32-channel 2x network, a cut on frame 4."""
     frames = synth.frames_textured(synth.BASE_SEED + 76, 6, 48, 32, 8, "444", "full")
     flags = np.zeros(6, bool)
     flags[4] = True
     fdi = fmt_dict(48, 32, 8, "444", "full", "left", "rgb")
     fdo = fmt_dict(96, 64, 8, "444", "full", "left", "rgb")
-    text, blob = synth.net_config1()
+    text, blob = synth.net_sr2x_t3()
     ref = [prequant(o, fdo) for o in oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)]
     outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(48, 32, 8, "444", "full", "left", "rgb"),
                       nv.fmt(96, 64, 8, "444", "full", "left", "rgb"), prec)
@@ -554,7 +554,7 @@ def test_filter_rgb_planes(prec):
 def test_rgb_format_checks():
     """RGB planes need 4:4:4 and an RGB-domain network."""
     eng = nv.Engine()
-    text, blob = synth.net_config1()
+    text, blob = synth.net_sr2x_t3()
     with pytest.raises(Exception, match="UNSUPPORTED_FORMAT|unsupported"):
         eng.filter(text, blob, nv.fmt(48, 32, 8, "420", "full", "left", "rgb"),
                    nv.fmt(96, 64, 8, "420", "full", "left", "rgb"), "bf16")
@@ -573,7 +573,7 @@ def test_filter_hdr10_pq_fp32():
     flags = np.zeros(5, bool)
     fdi = fmt_dict(48, 32, 10, "420", "limited", "left", "bt2020", "pq")
     fdo = fmt_dict(96, 64, 10, "420", "limited", "left", "bt2020", "pq")
-    text, blob = synth.net_config1()
+    text, blob = synth.net_sr2x_t3()
     ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo)
     outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(48, 32, 10, "420", "limited", "left", "bt2020", "pq"),
                       nv.fmt(96, 64, 10, "420", "limited", "left", "bt2020", "pq"), "fp32")

@@ -12,11 +12,11 @@ pytestmark = pytest.mark.gpu
 
 # (network, width, height, bits, frames, cut-before, arrival step)
 CLIPS = [
-    ("c2", 96, 64, 10, 7, 3, 0),
-    ("c3", 64, 48, 8, 4, 2, 0),
-    ("c2", 70, 40, 8, 5, None, 2),
-    ("c2", 96, 64, 10, 6, None, 4),
-    ("c3", 48, 32, 8, 3, None, 5),
+    ("sr2x", 96, 64, 10, 7, 3, 0),
+    ("stvsr", 64, 48, 8, 4, 2, 0),
+    ("sr2x", 70, 40, 8, 5, None, 2),
+    ("sr2x", 96, 64, 10, 6, None, 4),
+    ("stvsr", 48, 32, 8, 3, None, 5),
 ]
 
 
@@ -29,7 +29,7 @@ def _lib():
 
 @pytest.fixture(scope="module")
 def nets():
-    return {"c2": (synth.net_config2(), 2), "c3": (synth.net_config3(), 4)}
+    return {"sr2x": (synth.net_sr2x_t5(), 2), "stvsr": (synth.net_stvsr4x(), 4)}
 
 
 def _frames(k, W, H, bits, n):

@@ -82,12 +82,12 @@ def test_dcn_wait_runs_out_then_next_call_succeeds():
 def test_filter_pull_reports_timeout_then_recovers():
     """A pull whose network launches time out returns DEVICE_TIMEOUT; outputs the filter
     computed ahead in the same state are dropped, and pulling again gives every output
-    within 1 LSB of the oracle (BF16 config-1 network, 8 frames, a cut on frame 5)."""
+    within 1 LSB of the oracle (BF16, the 3-frame 32-channel 2x network, 8 frames, a cut on frame 5)."""
     W = H = 48
     frames = synth.frames_gradient(11, 8, W, H, 8, "420", "full")
     flags = np.zeros(8, bool)
     flags[5] = True
-    text, blob = synth.net_config1()
+    text, blob = synth.net_sr2x_t3()
     fd_in, fd_out = fmt_dict(W, H, 8, rng="full"), fmt_dict(2 * W, 2 * H, 8, rng="full")
     ref = oracle.run_filter(frames, flags, text, blob, fd_in, fd_out, keep_float=True)
     eng = nv.Engine()

@@ -94,7 +94,7 @@ def torch_tuple_net(frames, blob, T, C, nres, s):
     return y + up(_t(frames[(T - 1) // 2]), s)
 
 
-@pytest.mark.parametrize("T,C,nres", [(3, 32, 4), (5, 64, 10)])   # config 1, config 2 shapes
+@pytest.mark.parametrize("T,C,nres", [(3, 32, 4), (5, 64, 10)])   # the 3-frame 32-channel and 5-frame 64-channel 2x networks
 def test_tuple_network_forward_matches_torch_model(T, C, nres):
     text, blob = synth.net_tuple(synth.BASE_SEED + 90 + T, frames=T, channels=C, nres=nres, scale=2)
     blob = _random_blob(text, blob, T)

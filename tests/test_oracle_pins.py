@@ -459,7 +459,7 @@ def test_pool2_is_torch_avg_pool():
 
 # ------------------------------------------------------------------ C4/C5 grouping
 
-def test_scenes_and_tuple_map_config1():
+def test_scenes_and_tuple_map_clip64_t3():
     flags = np.zeros(16, bool)
     flags[9] = True
     assert oracle.scenes_from_flags(flags, 16) == [(0, 8), (9, 15)]
@@ -736,6 +736,6 @@ def test_crop_window_forward_is_exact_in_interior():
 
 
 def test_net_description_rejects_blob_mismatch():
-    text, blob = synth.net_config1()
+    text, blob = synth.net_sr2x_t3()
     with pytest.raises(ValueError):
         oracle.Net(text, blob[:-1])

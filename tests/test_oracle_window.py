@@ -10,7 +10,7 @@ from gpu_util import fmt_dict, prequant, stvsr_window
 def test_stvsr_window_equals_full_forward():
     W, H = 144, 72
     frames = synth.frames_textured(synth.BASE_SEED + 3, 2, W, H, 8, "420", "limited")
-    text, blob = synth.net_config3()
+    text, blob = synth.net_stvsr4x()
     net = oracle.Net(text, blob)
     fdi, fdo = fmt_dict(W, H, 8), fmt_dict(4 * W, 4 * H, 8)
     rgb = [oracle.ingest(f, fdi) for f in frames]
