@@ -453,7 +453,10 @@ nvisr_status nvisr_resblock2d(int32_t precision, const float *x, int32_t h, int3
 /* Modulated deformable convolution 3x3, DCN v2 as in torchvision's
  * deform_conv2d (Section 3.1): offsets [2*G*9][H][W] (dy, dx per group and
  * tap), mask [G*9][H][W] (already in [0,1]), stride 1, padding 1.  Planar
- * float32 device tensors; scratch allocated per call. */
+ * float32 device tensors; scratch allocated per call.  x must be finite: the
+ * tensor-core gather skips the loads of corners whose bilinear weight is zero
+ * (outside the image), and a skipped corner contributes weight x an earlier
+ * sample, which is zero only for a finite sample. */
 nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t h, int32_t w,
                          const float *offsets, const float *mask, int32_t groups,
                          const float *weight, const float *bias, int32_t cout, float *y,
