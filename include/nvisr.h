@@ -134,8 +134,13 @@ typedef struct nvisr_filter_desc {
  * (conv 64 -> 64, LeakyReLU, conv 64 -> 64, + the block input, whose middle
  * tensor no other layer reads) runs as one launch that keeps the middle
  * tensor on chip (nvisr_resblock2d); the results are the same as two
- * launches.  NVISR_OPT_UNFUSED_BLOCKS runs the two layers as two launches. */
-enum { NVISR_OPT_UNFUSED_OUTPUT = 1, NVISR_OPT_UNFUSED_BLOCKS = 2 };
+ * launches.  NVISR_OPT_UNFUSED_BLOCKS runs the two layers as two launches.
+ * NVISR_OPT_GUARD_BANDS surrounds every device buffer of the filter (ring,
+ * staging planes, weights, activations) with two 4 KB guard bands of a known
+ * byte pattern, which nvisr_filter_check_guards verifies: a check for kernels
+ * that write outside their buffers (a debugging aid; it costs 8 KB per buffer
+ * and a copy per check). */
+enum { NVISR_OPT_UNFUSED_OUTPUT = 1, NVISR_OPT_UNFUSED_BLOCKS = 2, NVISR_OPT_GUARD_BANDS = 4 };
 
 /* What an output frame is (nvisr_frame_info.kind). */
 enum {
@@ -461,6 +466,20 @@ nvisr_status nvisr_dcn2d(int32_t precision, const float *x, int32_t cin, int32_t
                          const float *offsets, const float *mask, int32_t groups,
                          const float *weight, const float *bias, int32_t cout, float *y,
                          void *stream);
+
+/* Checks the guard bands of a filter created with NVISR_OPT_GUARD_BANDS (no
+ * counterpart in the paper).  Waits for the engine's streams, then reads every
+ * band back: OK when all hold their pattern; otherwise NVISR_CUDA_ERROR, with
+ * *bad = the number of buffers whose bands were overwritten and the first
+ * such byte named in nvisr_last_error.  NVISR_INVALID_ARG for a filter
+ * without guard bands. */
+nvisr_status nvisr_filter_check_guards(nvisr_filter *f, int32_t *bad);
+
+/* Test of the guard-band check (no counterpart in the paper): writes one byte
+ * from the host (cudaMemset) into the band after the index-th guarded buffer
+ * of the filter, so that the next nvisr_filter_check_guards reports it.
+ * Allocated memory only; NVISR_INVALID_ARG for an index past the buffers. */
+nvisr_status nvisr_test_poke_guard(nvisr_filter *f, int32_t index);
 
 /* Fault drill for tests of the NVISR_DEVICE_TIMEOUT path (no counterpart in
  * the paper).  While on (on != 0), the tensor-core kernels (convolutions and

@@ -77,6 +77,7 @@ class FilterDesc(ctypes.Structure):
 
 OPT_UNFUSED_OUTPUT = 1
 OPT_UNFUSED_BLOCKS = 2
+OPT_GUARD_BANDS = 4
 
 
 class FrameInfo(ctypes.Structure):
@@ -113,6 +114,8 @@ _SIGS = {
     "nvisr_filter_profile": (_I32, [_VP, _I32]),
     "nvisr_filter_profile_read": (_I32, [_VP, ctypes.POINTER(Profile)]),
     "nvisr_filter_cache_stats": (_I32, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "nvisr_filter_check_guards": (_I32, [_VP, ctypes.POINTER(_I32)]),
+    "nvisr_test_poke_guard": (_I32, [_VP, _I32]),
     "nvisr_status_string": (ctypes.c_char_p, [_I32]),
     "nvisr_last_error": (ctypes.c_char_p, [_VP]),
     "nvisr_network_check": (_I32, [ctypes.c_char_p, _I64]),
@@ -557,6 +560,18 @@ class Filter:
 
     def profile(self, enable=True):
         _check(_LIB.nvisr_filter_profile(self.h, 1 if enable else 0), "nvisr_filter_profile")
+
+    def check_guards(self):
+        """Number of buffers whose guard bands were overwritten (filters created
+        with OPT_GUARD_BANDS); 0 when every band holds its pattern."""
+        bad = _I32(0)
+        st = _LIB.nvisr_filter_check_guards(self.h, ctypes.byref(bad))
+        if st not in (Status.OK, Status.CUDA_ERROR):
+            _check(st, "nvisr_filter_check_guards")
+        return bad.value
+
+    def poke_guard(self, index):
+        _check(_LIB.nvisr_test_poke_guard(self.h, index), "nvisr_test_poke_guard")
 
     def cache_stats(self):
         """(hits, misses) of the extract-stage cache (two-frame group networks)."""

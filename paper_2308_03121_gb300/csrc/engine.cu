@@ -95,12 +95,21 @@ namespace {
 
 struct DevBuf {
     nvisr_engine *eng = nullptr;
-    void *ptr = nullptr;
-    size_t bytes = 0;
+    void *ptr = nullptr;   // the allocation (freed with cudaFree)
+    size_t bytes = 0;      // its size
+    size_t guard = 0;      // guard band bytes before and after the buffer (0 = none)
+    size_t user = 0;       // the buffer's requested size, between the two bands
 };
 
-nvisr_status dalloc(nvisr_engine *e, size_t bytes, std::vector<DevBuf> &owned, void **out) {
-    bytes = (size_t)round_up64((int64_t)std::max<size_t>(bytes, 256), 256);
+constexpr size_t GUARD_BYTES = 4096;      // NVISR_OPT_GUARD_BANDS: each band's size
+constexpr unsigned char GUARD_FILL = 0xA5;
+
+// Device allocation counted against the engine's budget.  guard > 0 surrounds
+// the buffer (the requested `bytes`, not rounded) with two bands of that size
+// filled with GUARD_FILL, for nvisr_filter_check_guards.
+nvisr_status dalloc(nvisr_engine *e, size_t bytes, std::vector<DevBuf> &owned, void **out, size_t guard = 0) {
+    const size_t user = bytes;
+    bytes = (size_t)round_up64((int64_t)std::max<size_t>(bytes + 2 * guard, 256), 256);
     if (e->budget > 0 && e->used + (int64_t)bytes > e->budget)
         return fail(NVISR_OVER_BUDGET, "HBM budget exceeded: need " + std::to_string(bytes) + " more bytes, " +
                                            std::to_string(e->budget - e->used) + " left");
@@ -110,9 +119,17 @@ nvisr_status dalloc(nvisr_engine *e, size_t bytes, std::vector<DevBuf> &owned, v
         cudaGetLastError();
         return fail(NVISR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(ce));
     }
+    if (guard) {
+        uint8_t *b = static_cast<uint8_t *>(p);
+        if ((ce = cudaMemset(b, GUARD_FILL, guard)) != cudaSuccess ||
+            (ce = cudaMemset(b + guard + user, GUARD_FILL, bytes - guard - user)) != cudaSuccess) {
+            cudaFree(p);
+            return fail(NVISR_CUDA_ERROR, std::string("guard bands: ") + cudaGetErrorString(ce));
+        }
+    }
     e->used += (int64_t)bytes;
-    owned.push_back({e, p, bytes});
-    *out = p;
+    owned.push_back({e, p, bytes, guard, user});
+    *out = static_cast<uint8_t *>(p) + guard;
     return NVISR_OK;
 }
 
@@ -211,6 +228,7 @@ struct nvisr_filter {
     int act_dt = DT_F32;  // 16-bit / FP32 activation dtype
     bool tc = false;      // tensor-core kernels
     std::vector<DevBuf> owned;
+    size_t guard = 0;  // NVISR_OPT_GUARD_BANDS: guard band bytes around each buffer
 
     // ring of ingested frames (planar float32 [3][H][pitch])
     int ring = 0;
@@ -525,7 +543,7 @@ int act_cpad(const nvisr_filter *f, int C) {
 }
 
 nvisr_status upload(nvisr_filter *f, const void *host, size_t bytes, void **dev) {
-    nvisr_status s = dalloc(f->eng, bytes, f->owned, dev);
+    nvisr_status s = dalloc(f->eng, bytes, f->owned, dev, f->guard);
     if (s != NVISR_OK) return s;
     NVISR_TRY_CUDA(cudaMemcpy(*dev, host, bytes, cudaMemcpyHostToDevice));
     return NVISR_OK;
@@ -770,7 +788,7 @@ nvisr_status build_plan(nvisr_filter *f) {
             if (s.out_t >= 0 && f8_uses[s.out_t] && !other_uses[s.out_t]) s.out_f8_only = true;
         if (slot) {
             void *p;
-            nvisr_status st = dalloc(f->eng, sizeof(unsigned) * slot, f->owned, &p);
+            nvisr_status st = dalloc(f->eng, sizeof(unsigned) * slot, f->owned, &p, f->guard);
             if (st != NVISR_OK) return st;
             f->amax = (unsigned *)p;
             f->act_scale.assign(slot, 1.f);
@@ -801,7 +819,7 @@ nvisr_status build_plan(nvisr_filter *f) {
                 return NVISR_OK;
             }
         void *p;
-        nvisr_status s = dalloc(f->eng, bytes, f->owned, &p);
+        nvisr_status s = dalloc(f->eng, bytes, f->owned, &p, f->guard);
         if (s != NVISR_OK) return s;
         pool.push_back({p, bytes, 1 << 30});
         *out = p;
@@ -845,7 +863,7 @@ nvisr_status build_plan(nvisr_filter *f) {
     if (f->precision == NVISR_PREC_FP8)
         for (Tensor &t : f->tensors)
             if (!t.ptr) {
-                nvisr_status s = dalloc(f->eng, (size_t)t.cpad * t.H * t.W * dtype_size(t.dt), f->owned, &t.ptr);
+                nvisr_status s = dalloc(f->eng, (size_t)t.cpad * t.H * t.W * dtype_size(t.dt), f->owned, &t.ptr, f->guard);
                 if (s != NVISR_OK) return s;
             }
     for (Tensor &T : f->tensors) T.cpc = layout_cpc(T.dt, T.cpad);
@@ -1163,7 +1181,7 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
     for (int t = 0; t < n; ++t)
         if (persistent[t]) {  // cached pairs: their own buffers, kept across runs
             Tensor &T = f->tensors[t];
-            nvisr_status s = dalloc(f->eng, (size_t)T.cpad * T.H * T.W * dtype_size(T.dt), f->owned, &T.ptr);
+            nvisr_status s = dalloc(f->eng, (size_t)T.cpad * T.H * T.W * dtype_size(T.dt), f->owned, &T.ptr, f->guard);
             if (s != NVISR_OK) return s;
         }
     for (int step = 0; step < (int)f->steps.size(); ++step) {
@@ -1179,7 +1197,7 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
                     break;
                 }
             if (!got) {
-                nvisr_status s = dalloc(f->eng, bytes, f->owned, &got);
+                nvisr_status s = dalloc(f->eng, bytes, f->owned, &got, f->guard);
                 if (s != NVISR_OK) return s;
                 pool.push_back({got, bytes, 1 << 30});
             }
@@ -1275,7 +1293,7 @@ nvisr_status build_plan_group(nvisr_filter *f, const float *blob) {
             x8 = std::max(x8, (size_t)T.cpad * T.H * T.W * dtype_size(T.dt));
         }
     if (x8) {
-        nvisr_status s = dalloc(f->eng, x8, f->owned, &f->dcn_x8);
+        nvisr_status s = dalloc(f->eng, x8, f->owned, &f->dcn_x8, f->guard);
         if (s != NVISR_OK) return s;
     }
     for (Tensor &T : f->tensors)
@@ -2192,6 +2210,7 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
         f->owned.clear();
         return st;
     };
+    f->guard = (d->options & NVISR_OPT_GUARD_BANDS) ? GUARD_BYTES : 0;
     // ring of ingested frames
     // ring: a tuple, or a group run plus the frames a recycled last run may reach back to
     f->ring = net.family == "group" ? 2 * net.frames + 2 : net.frames + 2;
@@ -2201,15 +2220,15 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
     f->rpitch = round_up64(W, 4);
     f->slot_floats = 3 * f->rpitch * H;
     void *p;
-    if ((s = dalloc(e, sizeof(float) * f->slot_floats * f->ring, f->owned, &p)) != NVISR_OK) return cleanup(s);
+    if ((s = dalloc(e, sizeof(float) * f->slot_floats * f->ring, f->owned, &p, f->guard)) != NVISR_OK) return cleanup(s);
     f->ring_base = (float *)p;
     for (int pl = 0; pl < 3; ++pl) {
         int rows;
         const int64_t bytes = plane_bytes(d->in_fmt, pl, &f->stage_pitch[pl], &rows);
-        if ((s = dalloc(e, bytes, f->owned, &f->stage[pl])) != NVISR_OK) return cleanup(s);
+        if ((s = dalloc(e, bytes, f->owned, &f->stage[pl], f->guard)) != NVISR_OK) return cleanup(s);
         const int64_t obytes = plane_bytes(d->out_fmt, pl, &f->ostage_pitch[pl], &rows);
         for (int b = 0; b < 2; ++b)
-            if ((s = dalloc(e, obytes, f->owned, &f->ostage[b][pl])) != NVISR_OK) return cleanup(s);
+            if ((s = dalloc(e, obytes, f->owned, &f->ostage[b][pl], f->guard)) != NVISR_OK) return cleanup(s);
     }
     for (cudaEvent_t *ev : {&f->ev_h2d, &f->ev_stage, &f->ev_req, &f->ev_d2h})
         if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess)
@@ -2221,12 +2240,12 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
             int rows;
             int64_t pitch;
             f->raw_slot_bytes[pl] = plane_bytes(d->in_fmt, pl, &pitch, &rows);
-            if ((s = dalloc(e, (size_t)f->raw_slot_bytes[pl] * f->ring, f->owned, &f->raw[pl])) != NVISR_OK)
+            if ((s = dalloc(e, (size_t)f->raw_slot_bytes[pl] * f->ring, f->owned, &f->raw[pl], f->guard)) != NVISR_OK)
                 return cleanup(s);
         }
     f->opitch = round_up64((int64_t)W * net.scale, 4);
     for (int k = 0; k < f->run_out; ++k) {
-        if ((s = dalloc(e, sizeof(float) * 3 * f->opitch * H * net.scale_y, f->owned, &p)) != NVISR_OK)
+        if ((s = dalloc(e, sizeof(float) * 3 * f->opitch * H * net.scale_y, f->owned, &p, f->guard)) != NVISR_OK)
             return cleanup(s);
         f->out_rgb[k] = (float *)p;
     }
@@ -2234,7 +2253,7 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
     if ((s = (net.family == "group" ? build_plan_group(f.get(), d->weights) : build_plan(f.get()))) != NVISR_OK)
         return cleanup(s);
     if (f->plain_final) {
-        if ((s = dalloc(e, sizeof(float) * 16 * (size_t)H * W, f->owned, &p)) != NVISR_OK) return cleanup(s);
+        if ((s = dalloc(e, sizeof(float) * 16 * (size_t)H * W, f->owned, &p, f->guard)) != NVISR_OK) return cleanup(s);
         f->final_f32 = (float *)p;
     }
     // requantise fused into a 2 x 2 shuffle output layer of 64 input channels (the row
@@ -2253,7 +2272,7 @@ nvisr_status nvisr_filter_create(nvisr_engine *e, const nvisr_filter_desc *d, nv
             f->rq_base = rq;
             const int tiles = (W + 127) / 128;
             if (rq.sub420 && rq.loc == NVISR_CHROMA_LEFT && tiles > 1) {
-                if ((s = dalloc(e, sizeof(float) * 6 * (size_t)H * tiles, f->owned, &p)) != NVISR_OK)
+                if ((s = dalloc(e, sizeof(float) * 6 * (size_t)H * tiles, f->owned, &p, f->guard)) != NVISR_OK)
                     return cleanup(s);
                 f->rq_edge = (float *)p;
             }
@@ -2407,6 +2426,58 @@ nvisr_status nvisr_pull(nvisr_filter *f, nvisr_planes *out, nvisr_frame_info *in
     }
     f->next_out++;
     return NVISR_OK;
+}
+
+nvisr_status nvisr_filter_check_guards(nvisr_filter *f, int32_t *bad) {
+    ErrScope es(f ? f->eng : nullptr);
+    if (!f || !bad) return fail(NVISR_INVALID_ARG, "check_guards: NULL argument");
+    *bad = 0;
+    if (!f->guard) return fail(NVISR_INVALID_ARG, "check_guards: the filter was created without NVISR_OPT_GUARD_BANDS");
+    NVISR_TRY_CUDA(cudaSetDevice(f->eng->device));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(f->eng->stream));
+    NVISR_TRY_CUDA(cudaStreamSynchronize(f->eng->copy_stream));
+    std::vector<unsigned char> band;
+    std::string first;
+    for (size_t i = 0; i < f->owned.size(); ++i) {
+        const DevBuf &b = f->owned[i];
+        if (!b.guard) continue;
+        const uint8_t *base = static_cast<const uint8_t *>(b.ptr);
+        const size_t after = b.bytes - b.guard - b.user;  // the post band runs to the allocation's end
+        bool ok = true;
+        for (int side = 0; side < 2 && ok; ++side) {
+            const size_t n = side ? after : b.guard;
+            band.resize(n);
+            NVISR_TRY_CUDA(cudaMemcpy(band.data(), side ? base + b.guard + b.user : base, n, cudaMemcpyDeviceToHost));
+            for (size_t j = 0; j < n; ++j)
+                if (band[j] != GUARD_FILL) {
+                    ok = false;
+                    if (first.empty())
+                        first = "buffer " + std::to_string(i) + " (" + std::to_string(b.user) + " bytes): " +
+                                (side ? "byte " + std::to_string(j) + " after its end"
+                                      : "byte " + std::to_string(b.guard - j) + " before its start");
+                    break;
+                }
+        }
+        if (!ok) ++*bad;
+    }
+    if (*bad) return fail(NVISR_CUDA_ERROR, "guard bands overwritten in " + std::to_string(*bad) + " buffer(s); first: " + first);
+    return NVISR_OK;
+}
+
+nvisr_status nvisr_test_poke_guard(nvisr_filter *f, int32_t index) {
+    ErrScope es(f ? f->eng : nullptr);
+    if (!f || !f->guard) return fail(NVISR_INVALID_ARG, "poke_guard: no filter with guard bands");
+    int32_t k = -1;
+    for (size_t i = 0; i < f->owned.size(); ++i) {
+        const DevBuf &b = f->owned[i];
+        if (b.guard && ++k == index) {
+            NVISR_TRY_CUDA(cudaSetDevice(f->eng->device));
+            NVISR_TRY_CUDA(cudaStreamSynchronize(f->eng->stream));
+            NVISR_TRY_CUDA(cudaMemset(static_cast<uint8_t *>(b.ptr) + b.guard + b.user, 0, 1));
+            return NVISR_OK;
+        }
+    }
+    return fail(NVISR_INVALID_ARG, "poke_guard: no such buffer");
 }
 
 nvisr_status nvisr_filter_cache_stats(nvisr_filter *f, int64_t *hits, int64_t *misses) {
