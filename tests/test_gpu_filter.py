@@ -173,6 +173,60 @@ def test_sr2x_t5_1080p_sampled_windows(prec):
                 assert mx <= 1, (t, (y0, x0), mx)
 
 
+# windows of a 3840 x 2160 input: the four corners (the last column tile of the 126-pixel
+# fused-block tiles is 60 pixels wide), a tile boundary (126 * 15 = 1890) and the interior
+UHD_WINDOWS = [(0, 16, 0, 16), (0, 16, 3824, 3840), (2144, 2160, 0, 16), (2144, 2160, 3824, 3840),
+               (1080, 1096, 1882, 1898), (700, 716, 3776, 3792)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_sr2x_t5_4k_input_sampled_windows(prec):
+    """The largest frames of the 2x SR class: 3840x2160 10-bit in, 7680x4320 out (every
+    activation over 1 GB), outputs 0 and 2 on sampled windows."""
+    W, H = 3840, 2160
+    frames = synth.frames_textured(synth.BASE_SEED + 80, 5, W, H, 10, "420", "limited")
+    flags = np.zeros(5, bool)
+    text, blob = synth.net_sr2x_t5()
+    outs, _ = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 10), nv.fmt(2 * W, 2 * H, 10), prec, limit=3)
+    fdi, fdo = fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10)
+    net = oracle.Net(text, blob)
+    rgb = [oracle.ingest(f, fdi) for f in frames]
+    for t in (0, 2):
+        idx = oracle.tuple_indices(t, 5, 0, 4)
+        for (y0, y1, x0, x1) in UHD_WINDOWS:
+            pq = oracle_window(net, [rgb[i] for i in idx], y0, y1, x0, x1, fdo)
+            got = crop_codes(outs[t], y0, y1, x0, x1, 2, "420")
+            if prec == "fp32":
+                assert_codes_match(got, pq, 10)
+            else:
+                mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 10) for k in "YUV"})
+                assert mx <= 1, (t, (y0, x0), mx)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_seven_frame_tuple_with_one_frame_scenes(prec):
+    """The largest tuple (T = 7, 21 input channels) on a ragged size, with scenes of 3, 1,
+    1 and 4 frames: every tuple slot of a one-frame scene is that frame."""
+    W, H = 136, 38
+    n = 9
+    frames = synth.frames_textured(synth.BASE_SEED + 81, n, W, H, 10, "420", "limited")
+    flags = np.zeros(n, bool)
+    flags[[3, 4, 5]] = True
+    text, blob = synth.net_tuple(synth.BASE_SEED + 82, frames=7, channels=64, nres=2, scale=2)
+    fdi, fdo = fmt_dict(W, H, 10), fmt_dict(2 * W, 2 * H, 10)
+    ref = oracle.run_filter(frames, flags, text, blob, fdi, fdo, keep_float=True)
+    outs, infos = run_gpu(text, blob, frames, flags, nv.fmt(W, H, 10), nv.fmt(2 * W, 2 * H, 10), prec)
+    assert len(outs) == n
+    assert [(i[1], i[2]) for i in infos[3:6]] == [(3, 3), (4, 4), (5, 8)]
+    for got, r in zip(outs, ref):
+        pq = prequant(r, fdo)
+        if prec == "fp32":
+            assert_codes_match(got, pq, 10)
+        else:
+            mx, _ = lsb_stats(got, {k: oracle.quantise(pq[k], 10) for k in "YUV"})
+            assert mx <= 1, mx
+
+
 STVSR_WINDOWS = [(0, 16, 0, 16), (0, 16, 944, 960), (524, 540, 944, 960), (270, 286, 480, 496),
                  (100, 116, 120, 136)]
 
