@@ -55,6 +55,13 @@ constexpr int NEPI = 256;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 232448;  // 227 KB per CTA
 constexpr int SMEM_HDR = 1024;      // barriers + TMEM slot + abort flag
+// The tuple head's float32 staging: HEAD_NSL slots of HEAD_RPB input rows of each of up to 5
+// frames (3 planes x pixels x0 - 4 .. x0 + 131).  One TMA box per frame covers a slot's rows:
+// the boxes, not their bytes, set the rate at which the rows arrive (a second row per box
+// cost no time), so a box carries four rows.
+constexpr int HEAD_RPB = 4;
+constexpr int HEAD_NSL = 4;
+constexpr uint32_t HEAD_FROW32 = (HEAD_RPB * 3 * 136 * 4 + 127u) & ~127u;  // one frame of a slot, 128-byte aligned
 constexpr int W_MAX = 112 * 1024;   // resident weight slice budget
 
 struct TcParams {
@@ -722,12 +729,14 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
     auto width_of = [&](int pi) { return MULTI ? probs[pi].W : p.W; };
     if (threadIdx.x >= 64 && threadIdx.x < 64 + NPR)
         sbias[threadIdx.x - 64] = p.bias[PSB ? 4 * (threadIdx.x - 64) + slice : slice * NPR + threadIdx.x - 64];
-    // 16-channel head reading the tuple's float32 frames (ntup > 0): warp 0 converts
-    // each row from NST32 float32 staging rows (TMA from the ring) into the stage
-    constexpr int NST32 = 8;
-    constexpr uint32_t BOX32 = 3 * 136 * 4;                    // one frame's three planes of a row, x0-4 .. x0+131
-    constexpr uint32_t FROW32 = (BOX32 + 127u) & ~127u;        // its slot (TMA destinations are 128-byte aligned)
-    constexpr uint32_t SROW32 = 5 * FROW32;                    // a staging row: up to 5 frames
+    // 16-channel head reading the tuple's float32 frames (ntup > 0): warps 0 and 11 convert
+    // each row from the float32 staging slots (TMA from the ring) into the stage
+    constexpr int RPB = HEAD_RPB;                              // input rows per staging slot
+    constexpr int NST32 = HEAD_NSL;                            // staging slots
+    constexpr uint32_t PLN32 = RPB * 136 * 4;                  // one plane of a frame: RPB rows of x0-4 .. x0+131
+    constexpr uint32_t BOX32 = 3 * PLN32;                      // one frame's box
+    constexpr uint32_t FROW32 = HEAD_FROW32;                   // its place in a slot
+    constexpr uint32_t SROW32 = 5 * FROW32;                    // a slot: up to 5 frames
     constexpr bool TUPF = CIN == 16 && IN_DT != DT_E4M3;
     const bool tup = TUPF && p.ntup > 0;
     uint64_t *full32 = reinterpret_cast<uint64_t *>(smem + 320);
@@ -777,12 +786,13 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
     griddep_wait();
 
     if ((warp == 0 || warp == 11) && tup) {
-        // ---------------- producer (warps 0 and 11), tuple head: per input row, warp 0 lane 0
-        // keeps up to NST32 rows of the ntup float32 frames in flight (TMA boxes of 136 pixels
-        // from x0 - 4, so the innermost coordinate stays 16-byte aligned; OOB reads as zero),
-        // then the two warps convert the row (warp 0 pixels 0-63, warp 11 pixels 64-129) into the
-        // stage's [2 chunks][130 px][8 channels] 16-bit layout, channels frame-major (the tuple
-        // pack's layout) with round-to-nearest (its rounding).
+        // ---------------- producer (warps 0 and 11), tuple head: warp 0 lane 0 keeps up to
+        // NST32 slots of the ntup float32 frames in flight, each RPB input rows of a strip
+        // (TMA boxes of 136 pixels from x0 - 4, so the innermost coordinate stays 16-byte
+        // aligned; OOB reads as zero); per input row the two warps convert the row (warp 0
+        // pixels 0-63, warp 11 pixels 64-129) into the stage's [2 chunks][130 px][8 channels]
+        // 16-bit layout, channels frame-major (the tuple pack's layout) with round-to-nearest
+        // (its rounding).
         if constexpr (TUPF) {
         const bool loader = warp == 0;
         const int px0 = loader ? 0 : 64;
@@ -790,9 +800,10 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
         uint8_t *st32 = obuf + 2 * TILEB;
         int t_sidx = cta0, t_r = 0, t_ra = 0, t_rb = 0, t_x0 = 0, t_img = 0, t_pi = 0;
         bool t_live = false;
-        // positions the load cursor on the next input row in the converting order
+        // positions the load cursor on the next slot's first input row in the converting order
+        // (a strip's rows ra - 1 .. rb in slots of RPB rows; the last may hold fewer)
         auto t_next = [&]() -> bool {
-            if (t_live && ++t_r <= t_rb) return true;
+            if (t_live && (t_r += RPB) <= t_rb) return true;
             if (t_live) t_sidx += cstride;
             t_live = false;
             if (t_sidx >= nstrips) return false;
@@ -801,17 +812,18 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
             t_live = true;
             return true;
         };
-        int gin = 0, issued = 0;
+        int gin = 0, pin = 0, issued = 0;  // pin: slots whose rows this warp has converted
         bool ok = true;
         for (int sidx = cta0; sidx < nstrips && ok; sidx += cstride) {
             int img, x0, ra, rb, pi;
             strip_of(sidx, img, x0, ra, rb, pi);
             for (int r = ra - 1; r <= rb; ++r, ++gin) {
+                const int h = (r - (ra - 1)) % RPB;  // the row's place in its slot
                 if (loader && lane == 0) {
-                    while (ok && !p.starve && issued < gin + NST32 && t_next()) {
+                    while (ok && !p.starve && issued < pin + NST32 && t_next()) {
                         const int k = issued % NST32;
-                        // the slot's previous row (issued - NST32 < gin) was converted by this warp;
-                        // the wait covers warp 11's half
+                        // the slot's previous rows (slot issued - NST32 < pin) were converted by this
+                        // warp; the wait covers warp 11's half
                         if (!mbar_wait_bounded(&empty32[k], (uint32_t)((issued / NST32) & 1) ^ 1u, abort, WAIT_NS)) {
                             ok = false;
                             break;
@@ -823,9 +835,9 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                         ++issued;
                     }
                 }
-                const int k = gin % NST32, s = gin % S;
+                const int k = pin % NST32, s = gin % S;
                 bool w = __shfl_sync(0xffffffffu, ok, 0);
-                w = w && mbar_wait_bounded(&full32[k], (uint32_t)((gin / NST32) & 1), abort, WAIT_NS);
+                if (h == 0) w = w && mbar_wait_bounded(&full32[k], (uint32_t)((pin / NST32) & 1), abort, WAIT_NS);
                 w = w && mbar_wait_bounded(&empty[s], (uint32_t)((gin / S) & 1) ^ 1u, abort, WAIT_NS);
                 if (!__all_sync(0xffffffffu, w)) {
                     if (lane == 0) raise_abort(abort, p.err);
@@ -837,10 +849,10 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                 // 16-byte store per chunk and pixel (consecutive across the warp).  Stage pixel px is
                 // staged float px + 3 of each channel row; channels of frames >= ntup read stale
                 // staging and are replaced by zero.
-                const uint32_t src = smem_u32(st32 + (size_t)k * SROW32) + 12u;
+                const uint32_t src = smem_u32(st32 + (size_t)k * SROW32) + (uint32_t)h * 544u + 12u;
                 const uint32_t dst = smem_u32(stage0 + (size_t)s * ROWB);
                 const int nch = 3 * p.ntup;
-                auto chan = [](int ch) { return (uint32_t)((ch / 3) * FROW32 + (ch % 3) * 544); };
+                auto chan = [](int ch) { return (uint32_t)((ch / 3) * FROW32 + (ch % 3) * PLN32); };
                 auto emit = [&](int px, const float (&u)[16]) {
                     uint4 c0, c1;
                     c0.x = pack2<TI>(u[0], u[1]);   c0.y = pack2<TI>(u[2], u[3]);
@@ -877,12 +889,15 @@ __global__ void __launch_bounds__(rows_threads(CIN, MULTI), 1) conv_rows_kernel(
                 }
                 fence_proxy_async();  // shared-memory writes -> the tensor core's async proxy
                 mbar_arrive(&full[s]);
-                mbar_arrive(&empty32[k]);
+                if (h == RPB - 1 || r == rb) {  // the slot's last row
+                    mbar_arrive(&empty32[k]);
+                    ++pin;
+                }
             }
         }
         if (loader && lane == 0) {
             // loads still in flight after an early exit land before the CTA ends
-            for (int j = gin; j < issued; ++j)
+            for (int j = pin; j < issued; ++j)
                 mbar_wait_bounded(&full32[j % NST32], (uint32_t)((j / NST32) & 1), nullptr, WAIT_NS);
             mbar_wait_bounded(wbar, 0, nullptr, WAIT_NS);
         }
@@ -1908,8 +1923,8 @@ template <int IN_DT, int OUT_DT, int CBO, int NPR = 64, bool PS = false, int CIN
 cudaError_t run_rows(const CUtensorMap &map, const CUtensorMap &ymap, const CUtensorMap &rmap, TcParams p,
                      cudaStream_t st) {
     int smem;
-    // the tuple head's float32 staging rows (8 rows of 5 frames x 3 planes x 136 px, 128-byte slots)
-    const int extra = CIN == 16 && p.ntup > 0 ? 8 * 5 * ((3 * 136 * 4 + 127) & ~127) : 0;
+    // the tuple head's float32 staging slots
+    const int extra = CIN == 16 && p.ntup > 0 ? HEAD_NSL * 5 * (int)HEAD_FROW32 : 0;
     p.stages = rows_stages(p.res != nullptr, &smem, NPR, PS, CIN, false, IN_DT == DT_E4M3, extra);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
     auto kern = conv_rows_kernel<IN_DT, OUT_DT, CBO, false, NPR, PS, CIN>;
@@ -2126,7 +2141,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
         cuuint64_t dims[4] = {(cuuint64_t)a.W, (cuuint64_t)a.H, 3, (cuuint64_t)a.ring_slots};
         cuuint64_t strides[3] = {(cuuint64_t)a.ring_pitch * 4, (cuuint64_t)a.ring_pitch * a.H * 4,
                                  (cuuint64_t)a.ring_pitch * a.H * 12};
-        cuuint32_t box[4] = {136, 1, 3, 1};
+        cuuint32_t box[4] = {136, (cuuint32_t)HEAD_RPB, 3, 1};
         cuuint32_t estr[4] = {1, 1, 1, 1};
         if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(a.ring), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
